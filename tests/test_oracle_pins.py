@@ -1,0 +1,409 @@
+"""Pins of the FP64 oracle against things other than itself.
+
+Each test fixes a part of the oracle to brute force on dense arrays (library
+filters), to a closed form, to an exact identity, or to a worked example the
+paper prints, chosen so that a dropped term, a wrong sign or index, or a
+transposed operand in oracle.c fails at least one of them.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import dense_twin as dt
+import oracle
+from workload import band_bounds, band512, leaf_values, spheres_particles, tiny_shell
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_examples.txt")
+
+
+def golden():
+    out = {}
+    for line in open(GOLDEN):
+        line = line.split("#", 1)[0].strip()
+        if not line:
+            continue
+        k, v = (s.strip() for s in line.split("=", 1))
+        out[k] = [int(t) for t in v.split()]
+    return out
+
+
+def _coords(b, N, L):
+    return oracle.leaf_coords(b, N, L)
+
+
+# ---------------------------------------------------------------------------
+# Structure: activation, list state, bit layout
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("N,L,r0,r1,strict", [
+    (16, 8, 3.0, 7.5, False),
+    (24, 8, 5.2, 9.9, True),
+    (32, 8, 10.0, 14.0, False),
+    (32, 4, 6.5, 12.25, True),
+    (40, 8, 0.0, 9.0, False),      # ball
+    (64, 8, 22.0, 26.0, False),    # the 64^3 shell of radius 24
+])
+def test_shell_structure_matches_bruteforce(N, L, r0, r1, strict):
+    lo2, hi2 = band_bounds(r0, r1)
+    g = oracle.Grid(N, L, 1)
+    n_new = g.activate_shell(lo2, hi2, strict)
+    act = dt.shell_active(N, lo2, hi2, strict)
+    assert n_new == int(act.sum()) == g.num_active()
+    b, m = g.structure()
+    b2, m2 = dt.structure(act, L)
+    np.testing.assert_array_equal(b, b2)
+    np.testing.assert_array_equal(m, m2)
+    assert np.all(np.diff(b) > 0)            # list in ascending root index
+
+
+def test_shell_counts_64_and_512():
+    """The 64^3 radius-24 shell and the 512^3 |dist-200|<8 band, counted by
+    brute force over every voxel with numpy (independent of the oracle)."""
+    lo2, hi2 = band_bounds(22.0, 26.0)
+    g = oracle.Grid(64, 8, 1)
+    g.activate_shell(lo2, hi2, False)
+    act = dt.shell_active(64, lo2, hi2, False)
+    assert g.num_active() == int(act.sum())
+    assert g.num_leaves() == len(dt.structure(act, 8)[0])
+    s = band512()
+    g2 = oracle.Grid(s.N, s.L, 1)
+    g2.activate_shell(s.lo2, s.hi2, s.lo_strict)
+    c = (2 * np.arange(s.N, dtype=np.int64) + 1 - s.N) ** 2
+    total, leaves = 0, set()
+    for i in range(s.N):
+        D = c[i] + c[:, None] + c[None, :]
+        a = (D > s.lo2) & (D < s.hi2)
+        total += int(a.sum())
+        jj, kk = np.nonzero(a)
+        leaves.update(((i // 8) * 64 + jj // 8) * 64 + kk // 8)
+    assert g2.num_active() == total
+    assert g2.num_leaves() == len(leaves)
+
+
+def test_shell_activation_idempotent():
+    lo2, hi2 = band_bounds(5.0, 9.0)
+    g = oracle.Grid(24, 8, 1)
+    first = g.activate_shell(lo2, hi2, False)
+    assert first > 0
+    assert g.activate_shell(lo2, hi2, False) == 0
+
+
+def test_activate_coords_zero_fill_and_domain():
+    """Activation on write zero-fills (Sec. 3.2 item 3): a voxel activated
+    after values were written reads 0, a new leaf reads 0 everywhere, and
+    coordinates outside the domain are ignored."""
+    N, L = 16, 8
+    g = oracle.Grid(N, L, 2)
+    g.activate_coords([[1, 2, 3], [4, 4, 4]])
+    b, _ = g.structure()
+    g.write_field64(0, np.full((len(b), L ** 3), 5.0))
+    assert g.get(0, 1, 2, 3) == 5.0 and g.get(0, 4, 4, 4) == 5.0
+    assert g.get(0, 1, 2, 4) == 0.0                     # inactive reads ambient 0
+    n = g.activate_coords([[1, 2, 4], [9, 9, 9], [-1, 0, 0], [16, 0, 0], [0, 0, 16]])
+    assert n == 2
+    assert g.get(0, 1, 2, 4) == 0.0 and g.get(0, 9, 9, 9) == 0.0
+    assert g.get(0, 1, 2, 3) == 5.0
+    assert g.num_leaves() == 2 and g.num_active() == 4
+    assert g.activate_coords([[1, 2, 3]]) == 0
+
+
+def test_fig4_activation_on_write_bitmasked():
+    """Fig. 4: for i in x: y[i // 2] += 1 activates y[1], y[3].  Bitmasked
+    leaves activate only the written cells, not their siblings."""
+    gold = golden()
+    x = oracle.Grid(8, 8, 1)
+    x.activate_coords([[0, 0, k] for k in (2, 3, 6, 7)])
+    b, m = x.structure()
+    ks = [l % 8 for l in range(512) if (m[0, l // 32] >> (l % 32)) & 1]
+    y = oracle.Grid(8, 8, 1)
+    y.activate_coords([[0, 0, k // 2] for k in ks])
+    yk = sorted(k for k in range(8) if y.is_active(0, 0, k))
+    assert yk == gold["fig4_written_cells"]
+    for k in gold["fig4_dense_leaf_extra_cells"]:
+        assert not y.is_active(0, 0, k)
+    assert y.num_leaves() == 1
+
+
+def test_deactivate_all():
+    g = oracle.Grid(16, 8, 1)
+    g.activate_coords([[0, 0, 0], [15, 15, 15]])
+    assert g.num_leaves() == 2
+    g.deactivate_all()
+    assert g.num_leaves() == 0 and g.num_active() == 0
+    assert g.get(0, 0, 0, 0) == 0.0
+    g.activate_coords([[15, 15, 15]])
+    assert g.num_leaves() == 1 and g.get(0, 15, 15, 15) == 0.0
+
+
+# ---------------------------------------------------------------------------
+# 7-point diffusion
+# ---------------------------------------------------------------------------
+
+def _box_grid(n, N=32, L=8, F=2):
+    g = oracle.Grid(N, L, F)
+    ii, jj, kk = np.meshgrid(*(np.arange(s) for s in n), indexing="ij")
+    g.activate_coords(np.stack([ii.ravel(), jj.ravel(), kk.ravel()], 1))
+    return g
+
+
+@pytest.mark.parametrize("n,m", [((20, 24, 28), (1, 1, 1)), ((20, 24, 28), (1, 2, 3)),
+                                 ((8, 8, 8), (2, 1, 4)), ((13, 5, 30), (3, 2, 7))])
+def test_diffusion_eigenmode_closed_form(n, m):
+    """On a fully active box [0,n)^3 with zero outside, the discrete Dirichlet
+    mode u = prod_a sin(pi m_a (i_a+1)/(n_a+1)) is an eigenvector of the 7-point
+    step: u_s = lambda^s u_0 with lambda = 1 - 0.1 sum_a (2 - 2 cos(pi m_a/(n_a+1)))."""
+    N, L = 32, 8
+    g = _box_grid(n, N, L)
+    b, _ = g.structure()
+    c = oracle.leaf_coords(b, N, L)
+    u0 = np.ones(c.shape[:2])
+    for a in range(3):
+        u0 *= np.sin(math.pi * m[a] * (c[:, :, a] + 1) / (n[a] + 1))
+    inside = np.all(c < np.array(n), axis=2)
+    u0 = np.where(inside, u0, 0.0)
+    g.write_field64(0, u0)
+    lam = 1.0 - 0.1 * sum(2.0 - 2.0 * math.cos(math.pi * m[a] / (n[a] + 1)) for a in range(3))
+    src, dst = 0, 1
+    amp = np.max(np.abs(u0))
+    for s in range(1, 101):
+        g.diffuse7(src, dst, 0.1)
+        src, dst = dst, src
+        if s in (1, 5, 100):
+            # every mode has |lambda| <= 1, so rounding errors stay below ~s*eps*amp
+            err = np.max(np.abs(g.read_field(src) - lam ** s * u0))
+            assert err <= 1e-13 * s * amp, (s, err)
+
+
+def test_diffusion_mass_identity():
+    """sum(t) - sum(x) = -coef * sum_i x_i b_i, b_i = number of inactive or
+    out-of-domain face neighbours of i (the flux leaving the active set)."""
+    N, L = 32, 8
+    lo2, hi2 = band_bounds(6.0, 13.0)
+    g = oracle.Grid(N, L, 2)
+    g.activate_shell(lo2, hi2, False)
+    b, _ = g.structure()
+    x = leaf_values(7, N, L, b).astype(np.float64)
+    g.write_field64(0, x)
+    g.diffuse7(0, 1, 0.1)
+    act = dt.shell_active(N, lo2, hi2, False)
+    pad = np.pad(act, 1)
+    nb_inactive = np.zeros_like(act, dtype=np.int64)
+    for ax in range(3):
+        for s in (-1, 1):
+            nb_inactive += ~np.roll(pad, s, axis=ax)[1:-1, 1:-1, 1:-1]
+    xd = dt.from_leaves(g.read_field(0), b, N, L)
+    lhs = g.sum(1) - g.sum(0)
+    rhs = -0.1 * float(np.sum(xd * nb_inactive * act))
+    assert abs(lhs - rhs) <= 1e-11 * abs(rhs)
+
+
+@pytest.mark.parametrize("N,L,r0,r1", [(24, 8, 4.0, 10.0), (32, 4, 7.0, 13.0), (16, 8, 0.0, 20.0)])
+def test_diffusion_matches_dense_convolution(N, L, r0, r1):
+    lo2, hi2 = band_bounds(r0, r1)
+    g = oracle.Grid(N, L, 2)
+    g.activate_shell(lo2, hi2, False)
+    b, _ = g.structure()
+    x = leaf_values(3, N, L, b)
+    g.write_field(0, x)
+    g.diffuse7(0, 1, 0.1)
+    act = dt.shell_active(N, lo2, hi2, False)
+    xd = dt.from_leaves(x.astype(np.float64), b, N, L)
+    want = dt.to_leaves(dt.diffuse7(xd, act, 0.1), b, L)
+    np.testing.assert_allclose(g.read_field(1), want, rtol=0, atol=1e-13)
+
+
+# ---------------------------------------------------------------------------
+# 27-point box smoothing and the sum reduction
+# ---------------------------------------------------------------------------
+
+def test_box27_full_domain_is_uniform_filter():
+    """Fully active domain, zero outside: box27 is scipy's uniform_filter of
+    size 3 with constant-zero boundary (a library special case)."""
+    from scipy import ndimage
+    N, L = 16, 8
+    g = oracle.Grid(N, L, 2)
+    g.activate_shell(0, 10 ** 9, False)
+    b, _ = g.structure()
+    t = leaf_values(11, N, L, b).astype(np.float64)
+    g.write_field64(0, t)
+    g.box27(0, 1)
+    td = dt.from_leaves(t, b, N, L)
+    want = dt.to_leaves(ndimage.uniform_filter(td, size=3, mode="constant", cval=0.0), b, L)
+    np.testing.assert_allclose(g.read_field(1), want, rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("N,L,r0,r1", [(24, 8, 4.0, 10.0), (32, 4, 7.0, 13.0)])
+def test_box27_matches_dense_and_sum_identity(N, L, r0, r1):
+    lo2, hi2 = band_bounds(r0, r1)
+    g = oracle.Grid(N, L, 2)
+    g.activate_shell(lo2, hi2, False)
+    b, _ = g.structure()
+    t = leaf_values(5, N, L, b).astype(np.float64)
+    g.write_field64(0, t)
+    g.box27(0, 1)
+    act = dt.shell_active(N, lo2, hi2, False)
+    td = dt.from_leaves(t, b, N, L) * act
+    want = dt.to_leaves(dt.box27(td, act), b, L)
+    np.testing.assert_allclose(g.read_field(1), want, rtol=0, atol=1e-14)
+    # sum x' = (1/27) sum_n t_n c_n, c_n = active voxels in n's 3^3 neighbourhood
+    from scipy import ndimage
+    cnt = ndimage.convolve(act.astype(np.float64), np.ones((3, 3, 3)), mode="constant")
+    rhs = float(np.sum(td * cnt)) / 27.0
+    assert abs(g.sum(1) - rhs) <= 1e-12 * abs(rhs)
+
+
+def test_box27_constant_fixed_point():
+    N, L = 32, 8
+    g = _box_grid((20, 20, 20), N, L)
+    b, _ = g.structure()
+    c = oracle.leaf_coords(b, N, L)
+    inside = np.all(c < 20, axis=2)
+    g.write_field64(0, np.where(inside, 0.75, 0.0))
+    g.box27(0, 1)
+    out = g.read_field(1)
+    interior = np.all((c >= 1) & (c < 19), axis=2)
+    np.testing.assert_allclose(out[interior], 0.75, rtol=0, atol=1e-15)
+    corner = np.all(c == 0, axis=2)
+    np.testing.assert_allclose(out[corner], 0.75 * 8 / 27, rtol=0, atol=1e-15)
+
+
+def test_sum_matches_numpy():
+    N, L = 24, 8
+    lo2, hi2 = band_bounds(3.0, 11.0)
+    g = oracle.Grid(N, L, 1)
+    g.activate_shell(lo2, hi2, False)
+    b, m = g.structure()
+    x = leaf_values(9, N, L, b).astype(np.float64)
+    g.write_field64(0, x)
+    act = dt.to_leaves(dt.shell_active(N, lo2, hi2, False), b, L)
+    assert g.sum(0) == pytest.approx(float(np.sum(x * act)), rel=1e-14)
+
+
+def test_read_write_roundtrip_inactive_zero():
+    N, L = 16, 8
+    g = oracle.Grid(N, L, 1)
+    g.activate_coords([[0, 0, 0], [3, 5, 7]])
+    b, _ = g.structure()
+    g.write_field(0, np.full((1, 512), 2.5, dtype=np.float32))
+    out = g.read_field(0)
+    assert out.sum() == 5.0 and out[0, 0] == 2.5 and out[0, (3 * 8 + 5) * 8 + 7] == 2.5
+
+
+# ---------------------------------------------------------------------------
+# Particle transfers
+# ---------------------------------------------------------------------------
+
+def _small_particles(n=3000, N=32, seed=1):
+    spec = spheres_particles(seed=seed, n=n, N=N, L=4, r_min=0.1, r_max=0.2)
+    return spec
+
+
+def test_p2g_matches_dense_add_at_and_activation_union():
+    spec = _small_particles()
+    N, L = spec.N, spec.L
+    g = oracle.Grid(N, L, 4)
+    g.p2g(spec.x, spec.v, spec.pmass, 0, 1)
+    act, mass, mom = dt.p2g(spec.x, spec.v, N, spec.pmass)
+    b, m = g.structure()
+    b2, m2 = dt.structure(act, L)
+    np.testing.assert_array_equal(b, b2)
+    np.testing.assert_array_equal(m, m2)
+    np.testing.assert_allclose(g.read_field(0), dt.to_leaves(mass, b, L), rtol=0, atol=1e-12)
+    for d in range(3):
+        np.testing.assert_allclose(g.read_field(1 + d), dt.to_leaves(mom[d], b, L), rtol=0, atol=1e-12)
+
+
+def test_p2g_conservation():
+    """Partition of unity: total mass = n * pmass, total momentum =
+    pmass * sum v (all stencils inside the domain)."""
+    spec = _small_particles(n=5000, N=32, seed=4)
+    g = oracle.Grid(spec.N, spec.L, 4)
+    g.p2g(spec.x, spec.v, 2.0, 0, 1)
+    assert g.sum(0) == pytest.approx(2.0 * spec.n, rel=1e-12)
+    for d in range(3):
+        want = 2.0 * float(np.sum(spec.v[:, d].astype(np.float64)))
+        assert abs(g.sum(1 + d) - want) <= 1e-11 * float(np.sum(np.abs(spec.v[:, d])))
+
+
+def test_g2p_reproduces_linear_field():
+    """Quadratic B-splines reproduce linear functions: with grid velocity
+    v(node) = A node*dx + c, G2P returns A x_p + c (up to FP32 storage)."""
+    spec = _small_particles(n=2000, N=32, seed=2)
+    N, L = spec.N, spec.L
+    g = oracle.Grid(N, L, 4)
+    g.p2g(spec.x, spec.v, 1.0, 0, 1)
+    b, _ = g.structure()
+    c = oracle.leaf_coords(b, N, L).astype(np.float64) / N
+    A = np.array([[0.3, -1.2, 0.5], [2.0, 0.1, -0.7], [-0.4, 0.9, 1.1]])
+    off = np.array([0.05, -0.2, 0.3])
+    for d in range(3):
+        g.write_field64(1 + d, c @ A[d] + off[d])
+    x = spec.x.copy()
+    v = np.zeros_like(spec.v)
+    dtime = 1e-3
+    g.g2p(x, v, dtime, 1)
+    xp = (spec.x.astype(np.float32) * np.float32(N)).astype(np.float64) / N
+    want = xp @ A.T + off
+    np.testing.assert_allclose(v, want, rtol=1e-6, atol=1e-6)
+    np.testing.assert_allclose(x, (spec.x.astype(np.float64) + dtime * v.astype(np.float64)),
+                               rtol=0, atol=1e-7)
+
+
+def test_g2p_uniform_velocity_exact():
+    spec = _small_particles(n=500, N=32, seed=3)
+    g = oracle.Grid(spec.N, spec.L, 4)
+    g.p2g(spec.x, spec.v, 1.0, 0, 1)
+    n = g.num_leaves()
+    for d, val in enumerate((0.25, -0.5, 0.125)):
+        g.write_field64(1 + d, np.full((n, 64), val))
+    x = spec.x.copy()
+    v = np.zeros_like(spec.v)
+    g.g2p(x, v, 0.0, 1)
+    np.testing.assert_allclose(v, np.broadcast_to([0.25, -0.5, 0.125], v.shape), rtol=1e-15, atol=0)
+    np.testing.assert_array_equal(x, spec.x)
+
+
+def test_grid_update_hand_case():
+    """v = p/m, v_z -= dt g, then the boundary clamp (index < bound with
+    negative component, index > N - bound with positive component)."""
+    N, L = 16, 4
+    g = oracle.Grid(N, L, 4)
+    nodes = np.array([[8, 8, 8], [1, 8, 8], [15, 8, 8], [8, 14, 2], [5, 5, 5]])
+    g.activate_coords(nodes)
+    b, _ = g.structure()
+    coords = oracle.leaf_coords(b, N, L)
+    mass = np.zeros((len(b), 64))
+    mom = np.zeros((3, len(b), 64))
+    vals = {(8, 8, 8): (2.0, (2.0, -4.0, 6.0)), (1, 8, 8): (1.0, (-1.0, 1.0, 1.0)),
+            (15, 8, 8): (4.0, (4.0, 4.0, 4.0)), (8, 14, 2): (1.0, (0.5, 0.5, -0.5)),
+            (5, 5, 5): (0.0, (0.0, 0.0, 0.0))}
+    for key, (mm, p) in vals.items():
+        sel = np.all(coords == np.array(key), axis=2)
+        mass[sel] = mm
+        for d in range(3):
+            mom[d][sel] = p[d]
+    g.write_field64(0, mass)
+    for d in range(3):
+        g.write_field64(1 + d, mom[d])
+    g.grid_update(0, 1, 0.01, 9.8, 3)
+    got = {key: tuple(g.get(1 + d, *key) for d in range(3)) for key in vals}
+    assert got[(8, 8, 8)] == pytest.approx((1.0, -2.0, 3.0 - 0.098))
+    assert got[(1, 8, 8)] == pytest.approx((0.0, 1.0, 1.0 - 0.098))      # i=1 < 3, v_x<0 -> 0
+    assert got[(15, 8, 8)] == pytest.approx((0.0, 1.0, 1.0 - 0.098))     # i=15 > 13, v_x>0 -> 0
+    assert got[(8, 14, 2)] == pytest.approx((0.5, 0.0, 0.0))             # j>13 v_y>0, k<3 v_z<0
+    assert got[(5, 5, 5)] == (0.0, 0.0, 0.0)                            # massless node
+
+
+def test_inputs_deterministic():
+    a, b = tiny_shell(3), tiny_shell(3)
+    assert (a.lo2, a.hi2) == (b.lo2, b.hi2)
+    v1 = leaf_values(5, 64, 8, np.array([0, 17, 300]))
+    v2 = leaf_values(5, 64, 8, np.array([0, 17, 300]))
+    np.testing.assert_array_equal(v1, v2)
+    assert v1.dtype == np.float32 and v1.min() >= 0.0 and v1.max() < 1.0
+    p1, p2 = spheres_particles(2, n=100, N=32), spheres_particles(2, n=100, N=32)
+    np.testing.assert_array_equal(p1.x, p2.x)
+    lo, hi = 3 / 32, 1 - 3 / 32
+    assert p1.x.min() >= lo and p1.x.max() <= hi
