@@ -1,0 +1,227 @@
+/*
+ * sgrid.h -- C ABI of libsgrid, a GB300 (sm_103a) library for time steps on a
+ * two-level spatially sparse grid: a pointer root over bitmasked leaf blocks.
+ *
+ * The operations follow the problem statement of AsyncTaichi (Hu et al.,
+ * "AsyncTaichi: On-the-fly Inter-kernel Optimizations for Imperative and
+ * Spatially Sparse Programming", 2021):
+ *   - the data structure is Sec. 3.1 / Fig. 3 (pointer cells are active iff
+ *     non-null, bitmasked cells iff their bit is set; Sec. 4 "States");
+ *   - an inactive voxel reads as 0 (Sec. 4 "States", Fig. 5 caption);
+ *   - writing activates and zero-fills (Sec. 3.2 item 3, Fig. 4);
+ *   - struct-for loops run over a generated list of active leaves
+ *     (Sec. 3.2 item 2);
+ *   - calls are queued and launched lazily: flush is explicit and
+ *     non-blocking, and every device-to-host transfer flushes implicitly
+ *     (Sec. 5, Sec. 7.1);
+ *   - on flush the queue goes through list-generation removal (Sec. 6.2),
+ *     activation demotion (Sec. 6.3), task fusion (Sec. 6.4, Supplement
+ *     Sec. 2) and dead-store elimination (Sec. 6.5), each of which can be
+ *     switched off with sg_set_opts; all four off is the eager form that
+ *     regenerates the list and checks activation in every kernel.
+ *
+ * Conventions shared by every call:
+ *   - Return value: SG_OK (0) or one of the SG_ERR_* codes below; no C++
+ *     exception crosses this boundary.  sg_last_error() gives a message for
+ *     the last failing call on the calling thread.
+ *   - Domain: N^3 voxels, N = res, leaves of edge L = 2^leaf_log2, root edge
+ *     R = N / L.  Root index b = (bi*R + bj)*R + bk; local voxel index
+ *     l = (li*L + lj)*L + lk (k fastest); mask bit l is bit (l % 32) of 32-bit
+ *     word l / 32 of the leaf's mask.
+ *   - Fields are FP32 scalar channels identified by an index 0..n_fields-1;
+ *     sg_swap exchanges the storage behind two indices.
+ *   - List order (used by every read and write of per-leaf data) is
+ *     ascending root index b.
+ *   - Device pointers passed to queued calls are BORROWED: they must stay
+ *     valid, and their contents unchanged by the caller, until the next
+ *     sg_sync (or any call documented as an implicit sync) returns.
+ *   - All device work of a grid runs in order on the CUDA stream given to
+ *     sg_create.  A grid must not be used from two threads at once.
+ *   - Device-side errors (pool exhausted, a bounded wait that gave up) are
+ *     latched in the grid and returned by the next sg_sync or implicit sync.
+ */
+#ifndef SGRID_H
+#define SGRID_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define SG_OK 0
+#define SG_ERR_INVALID 1         /* bad argument or call order */
+#define SG_ERR_OOM 2             /* device memory could not be allocated */
+#define SG_ERR_POOL_EXHAUSTED 3  /* an activation needed more than max_leaves leaves */
+#define SG_ERR_TIMEOUT 4         /* a bounded device-side wait gave up */
+#define SG_ERR_CUDA 5            /* a CUDA runtime call failed */
+
+/* ---- optimizer passes (sg_set_opts); all four on is the default ---- */
+#define SG_OPT_LGR 1u  /* list-generation removal, Sec. 6.2 */
+#define SG_OPT_AD 2u   /* activation demotion, Sec. 6.3 */
+#define SG_OPT_FUSE 4u /* task fusion, Sec. 6.4 (needs SG_OPT_LGR) */
+#define SG_OPT_DSE 8u  /* dead-store elimination, Sec. 6.5 */
+#define SG_OPT_ALL 15u
+#define SG_OPT_EAGER 0u
+
+/* ---- stencil operations (sg_launch_stencil) ---- */
+#define SG_CLEAR 0    /* dst = 0 on active voxels */
+#define SG_DIFFUSE7 1 /* dst = src + coef*(sum of 6 face neighbours - 6 src) */
+#define SG_BOX27 2    /* dst = (1/27) * sum over the 3x3x3 neighbourhood of src */
+
+/* ---- sg_desc.flags ---- */
+#define SG_CREATE_DRY_RUN 1u /* no device memory and no launches: the queue and
+                                optimizer run and sg_stats counts what would
+                                have been launched (host-logic testing) */
+
+#define SG_MAX_FIELDS 16
+
+/* Device memory provider.  alloc returns a device pointer of at least `bytes`
+ * bytes aligned to 256 bytes, or NULL; free releases it.  When both are NULL
+ * the library uses cudaMalloc / cudaFree. */
+typedef void *(*sg_alloc_fn)(size_t bytes, void *ctx);
+typedef void (*sg_free_fn)(void *ptr, void *ctx);
+
+typedef struct sg_desc {
+    int32_t res;           /* N: virtual domain edge, a multiple of L, <= 4096 */
+    int32_t leaf_log2;     /* 2 (4^3 leaves) or 3 (8^3 leaves) */
+    int32_t n_fields;      /* FP32 scalar fields, 1..SG_MAX_FIELDS */
+    int32_t max_sums;      /* FP64 reduction result slots (>= 0) */
+    int64_t max_leaves;    /* leaf pool capacity, >= 1 */
+    uint32_t scratch_mask; /* bit f set: field f is scratch -- its contents are
+                              undefined once the flush that wrote it ends, which
+                              licenses dead-store elimination of its stores */
+    uint32_t flags;        /* SG_CREATE_* */
+    sg_alloc_fn alloc;     /* optional device memory provider */
+    sg_free_fn free;
+    void *alloc_ctx;
+} sg_desc;
+
+typedef struct sg_stats {
+    int64_t launches;        /* device kernels launched (copies not counted) */
+    int64_t listgen_run;     /* list-generation kernels launched */
+    int64_t listgen_removed; /* list generations removed on the host (Sec. 6.2) */
+    int64_t act_launched;    /* activation kernels launched */
+    int64_t act_demoted;     /* activations demoted away (Sec. 6.3) */
+    int64_t ops_enqueued;    /* calls queued */
+    int64_t ops_fused;       /* queued ops that ran inside another op's kernel */
+    int64_t stores_removed;  /* dead stores removed (Sec. 6.5) */
+    int64_t flushes;
+    double bytes_model;      /* algorithmic HBM bytes of the launched stencil,
+                                clear and reduction kernels (whole leaves) */
+} sg_stats;
+
+typedef struct sg_grid sg_grid; /* opaque; owned by the library */
+
+/* Create a grid whose device work runs on `cuda_stream` (a cudaStream_t; NULL
+ * is the legacy default stream).  All leaves are inactive.  On success *out
+ * receives the grid.  Errors: SG_ERR_INVALID (bad desc), SG_ERR_OOM. */
+int sg_create(const sg_desc *desc, void *cuda_stream, sg_grid **out);
+
+/* Synchronize the grid's stream, then release the grid and its memory. */
+int sg_destroy(sg_grid *g);
+
+/* Select optimizer passes (SG_OPT_* bits) for ops flushed from now on. */
+int sg_set_opts(sg_grid *g, uint32_t opts);
+
+/* Queue: activate every voxel with lo2 <= D < hi2 (lo2 < D when lo_strict),
+ * D = sum_a (2 i_a + 1 - N)^2 = 4 * (distance from the voxel centre to the
+ * domain centre)^2.  Newly allocated leaves are zero-filled (Sec. 3.2).
+ * With SG_OPT_AD, a call identical to one already applied since the last
+ * sg_deactivate_all activates nothing new and is demoted (Sec. 6.3). */
+int sg_activate_shell(sg_grid *g, int64_t lo2, int64_t hi2, int32_t lo_strict);
+
+/* Queue: activate n voxels given as int32 (i,j,k) triples in device memory
+ * (borrowed).  Triples outside the domain are ignored. */
+int sg_activate_coords(sg_grid *g, const int32_t *dev_xyz, int64_t n);
+
+/* Queue: deactivate every voxel and return every leaf to the pool. */
+int sg_deactivate_all(sg_grid *g);
+
+/* Queue: (re)generate the active-leaf list and its 27-neighbour table.  With
+ * SG_OPT_LGR it is removed when the structure is known unchanged (Sec. 6.2),
+ * and skipped on the device when no activation since the last list changed
+ * anything. */
+int sg_list_gen(sg_grid *g);
+
+/* Queue a struct-for over the active voxels: op is SG_CLEAR (src ignored),
+ * SG_DIFFUSE7 (coef used) or SG_BOX27.  src != dst.  Reads of inactive or
+ * out-of-domain voxels give 0; dst at inactive voxels stays 0. */
+int sg_launch_stencil(sg_grid *g, int32_t op, int32_t src, int32_t dst, float coef);
+
+/* Queue: sum of field src over the active voxels into result slot out_slot
+ * (FP64; per-leaf partials are FP32).  Read with sg_read_sums. */
+int sg_reduce_sum(sg_grid *g, int32_t src, int64_t out_slot);
+
+/* Queue P2G with activation: for each of n particles (positions dev_x and
+ * velocities dev_v, n*3 FP32 in (x,y,z) order, device memory, borrowed) and
+ * each of its 27 quadratic B-spline stencil nodes inside the domain (unit
+ * cube, dx = 1/N): activate the node, add w*pmass to field f_mass and
+ * w*pmass*v to fields f_mom0, f_mom0+1, f_mom0+2 (Sec. 8.3 workload).
+ * Accumulation order is unspecified (FP32 atomics). */
+int sg_p2g(sg_grid *g, const float *dev_x, const float *dev_v, int64_t n,
+           float pmass, int32_t f_mass, int32_t f_mom0);
+
+/* Queue the grid update on active nodes: where mass > 0, v = momentum/mass,
+ * v_z -= dt*gz, and along each axis a node with index < bound loses a negative
+ * component and one with index > N - bound a positive one; massless nodes get
+ * v = 0.  v replaces the momentum in f_mom0..f_mom0+2. */
+int sg_grid_update(sg_grid *g, int32_t f_mass, int32_t f_mom0, float dt,
+                   float gz, int32_t bound);
+
+/* Queue G2P: v_p = sum of w * v over the 27 stencil nodes (fields
+ * f_mom0..f_mom0+2), then x_p += dt * v_p; dev_x and dev_v (n*3 FP32, device,
+ * borrowed) are overwritten. */
+int sg_g2p(sg_grid *g, float *dev_x, float *dev_v, int64_t n, float dt, int32_t f_mom0);
+
+/* Exchange the storage behind field indices a and b (no device work). */
+int sg_swap(sg_grid *g, int32_t a, int32_t b);
+
+/* Optimize and launch every queued op; does not wait (Sec. 7.1). */
+int sg_flush(sg_grid *g);
+
+/* Flush, wait for the stream, and return the first latched device error. */
+int sg_sync(sg_grid *g);
+
+/* Implicit sync, then the number of leaves in the (current) list. */
+int sg_num_leaves(sg_grid *g, int64_t *n_leaves);
+
+/* Implicit sync, then copy the list state to host memory: leaf_b gets the
+ * root index of each leaf in ascending order, masks gets L^3/32 uint32 words
+ * per leaf (either may be NULL).  cap is the number of leaves the buffers
+ * hold; if the list is longer, nothing is copied, *n_leaves is set and
+ * SG_ERR_INVALID is returned. */
+int sg_read_structure(sg_grid *g, int64_t cap, int64_t *n_leaves, int32_t *leaf_b,
+                      uint32_t *masks);
+
+/* Implicit sync, then copy field f to host memory in list order, L^3 values
+ * per leaf, 0 at inactive voxels.  cap = leaves the buffer holds. */
+int sg_read_field(sg_grid *g, int32_t f, int64_t cap, float *host_vals);
+
+/* Set field f from host memory in list order (n_leaves * L^3 FP32 values;
+ * n_leaves must equal the current list length).  Values at inactive voxels
+ * are ignored (stored as 0).  The copy is made before the call returns, so
+ * the host buffer may be reused at once; pinned memory makes it faster. */
+int sg_write_field(sg_grid *g, int32_t f, const float *host_vals, int64_t n_leaves);
+
+/* Implicit sync, then copy result slots [0, n) to host memory. */
+int sg_read_sums(sg_grid *g, double *host, int64_t n);
+
+/* Counters since creation. */
+int sg_get_stats(sg_grid *g, sg_stats *out);
+
+/* Fault injection for testing bounded waits: queue a list generation whose
+ * first CTA also waits on a device flag that nothing ever sets.  The wait
+ * gives up after about 0.2 s and latches SG_ERR_TIMEOUT, which the next sync
+ * returns; the grid stays usable.  No counterpart in the paper. */
+int sg_debug_wait_test(sg_grid *g);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *sg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SGRID_H */

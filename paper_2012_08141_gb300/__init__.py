@@ -1,0 +1,299 @@
+"""Python binding of libsgrid, the GB300 sparse-grid time-stepping library.
+
+Argument marshalling only: every step of the path runs in the library's CUDA
+kernels.  PyTorch provides the device memory (through the library's allocator
+callback) and the stream.  There is no CPU fallback: if libsgrid.so is missing
+or cannot be loaded, importing the library raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+from . import build as _build
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+HEADER = os.path.join(ROOT, "include", "sgrid.h")
+
+SG_OK, SG_ERR_INVALID, SG_ERR_OOM, SG_ERR_POOL_EXHAUSTED, SG_ERR_TIMEOUT, SG_ERR_CUDA = range(6)
+SG_OPT_LGR, SG_OPT_AD, SG_OPT_FUSE, SG_OPT_DSE = 1, 2, 4, 8
+SG_OPT_ALL, SG_OPT_EAGER = 15, 0
+SG_CLEAR, SG_DIFFUSE7, SG_BOX27 = 0, 1, 2
+SG_CREATE_DRY_RUN = 1
+SG_MAX_FIELDS = 16
+
+_ALLOC = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+_FREE = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class SgDesc(ctypes.Structure):
+    _fields_ = [("res", ctypes.c_int32), ("leaf_log2", ctypes.c_int32), ("n_fields", ctypes.c_int32),
+                ("max_sums", ctypes.c_int32), ("max_leaves", ctypes.c_int64), ("scratch_mask", ctypes.c_uint32),
+                ("flags", ctypes.c_uint32), ("alloc", _ALLOC), ("free", _FREE), ("alloc_ctx", ctypes.c_void_p)]
+
+
+class SgStats(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64), ("listgen_run", ctypes.c_int64), ("listgen_removed", ctypes.c_int64),
+                ("act_launched", ctypes.c_int64), ("act_demoted", ctypes.c_int64), ("ops_enqueued", ctypes.c_int64),
+                ("ops_fused", ctypes.c_int64), ("stores_removed", ctypes.c_int64), ("flushes", ctypes.c_int64),
+                ("bytes_model", ctypes.c_double)]
+
+
+class SgError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"sgrid error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def header_functions() -> list[str]:
+    """Names of the functions include/sgrid.h declares."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return re.findall(r"^\s*(?:int|const char \*|void)\s+\**(sg_\w+)\s*\(", text, flags=re.M)
+
+
+def load_library(build: bool = True) -> ctypes.CDLL:
+    """Load libsgrid.so (building it first if its sources are newer)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build:
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise ImportError(f"libsgrid.so not found at {_build.LIB}; run build() first")
+    lib = ctypes.CDLL(_build.LIB)
+    P, I32, I64, U32, F, D = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32,
+                             ctypes.c_float, ctypes.c_double)
+    sigs = {
+        "sg_create": [ctypes.POINTER(SgDesc), P, ctypes.POINTER(P)],
+        "sg_destroy": [P],
+        "sg_set_opts": [P, U32],
+        "sg_activate_shell": [P, I64, I64, I32],
+        "sg_activate_coords": [P, P, I64],
+        "sg_deactivate_all": [P],
+        "sg_list_gen": [P],
+        "sg_launch_stencil": [P, I32, I32, I32, F],
+        "sg_reduce_sum": [P, I32, I64],
+        "sg_p2g": [P, P, P, I64, F, I32, I32],
+        "sg_grid_update": [P, I32, I32, F, F, I32],
+        "sg_g2p": [P, P, P, I64, F, I32],
+        "sg_swap": [P, I32, I32],
+        "sg_flush": [P],
+        "sg_sync": [P],
+        "sg_num_leaves": [P, ctypes.POINTER(I64)],
+        "sg_read_structure": [P, I64, ctypes.POINTER(I64), P, P],
+        "sg_read_field": [P, I32, I64, P],
+        "sg_write_field": [P, I32, P, I64],
+        "sg_read_sums": [P, P, I64],
+        "sg_get_stats": [P, ctypes.POINTER(SgStats)],
+        "sg_debug_wait_test": [P],
+    }
+    for name, args in sigs.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    lib.sg_last_error.argtypes = []
+    lib.sg_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(lib, rc: int):
+    if rc != SG_OK:
+        raise SgError(rc, lib.sg_last_error().decode())
+
+
+def _ptr(t) -> int:
+    """Device or host address of a torch tensor / numpy array."""
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return t.data_ptr()
+
+
+class Grid:
+    """One sparse grid: a pointer root over bitmasked 2^leaf_log2 leaves, with
+    n_fields FP32 fields, living on one CUDA stream.
+
+    Device memory comes from PyTorch's caching allocator; the stream is
+    torch's current stream unless one is given.  Device tensors passed to
+    queued calls are kept referenced until the next sync."""
+
+    def __init__(self, res: int, leaf_log2: int = 3, n_fields: int = 2, max_leaves: int = 4096,
+                 max_sums: int = 1, scratch_mask: int = 0, stream=None, dry_run: bool = False,
+                 device: int | None = None):
+        self.lib = load_library()
+        self.res, self.leaf_log2, self.n_fields = int(res), int(leaf_log2), int(n_fields)
+        self.L = 1 << self.leaf_log2
+        self.V = self.L ** 3
+        self.W = self.V // 32
+        self.max_leaves, self.max_sums = int(max_leaves), int(max_sums)
+        self._borrowed = []
+        self.h = None
+        desc = SgDesc(self.res, self.leaf_log2, self.n_fields, self.max_sums, self.max_leaves, int(scratch_mask),
+                      SG_CREATE_DRY_RUN if dry_run else 0)
+        stream_ptr = None
+        if not dry_run:
+            import torch
+            self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            stream_ptr = self.stream.cuda_stream
+            dev_index, torch_stream = self.device.index, self.stream
+
+            def _alloc(nbytes, ctx):
+                return torch.cuda.caching_allocator_alloc(int(nbytes), dev_index, torch_stream)
+
+            def _free(ptr, ctx):
+                torch.cuda.caching_allocator_delete(ptr)
+
+            self._cb = (_ALLOC(_alloc), _FREE(_free))
+            desc.alloc, desc.free = self._cb
+        h = ctypes.c_void_p()
+        _check(self.lib, self.lib.sg_create(ctypes.byref(desc), stream_ptr, ctypes.byref(h)))
+        self.h = h
+
+    # ---- lifetime ----
+    def close(self):
+        if self.h:
+            rc = self.lib.sg_destroy(self.h)
+            self.h = None
+            self._borrowed.clear()
+            _check(self.lib, rc)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _c(self, rc):
+        _check(self.lib, rc)
+
+    # ---- queued calls ----
+    def set_opts(self, opts: int):
+        self._c(self.lib.sg_set_opts(self.h, int(opts)))
+
+    def activate_shell(self, lo2: int, hi2: int, lo_strict: bool):
+        self._c(self.lib.sg_activate_shell(self.h, int(lo2), int(hi2), int(bool(lo_strict))))
+
+    def activate_coords(self, xyz):
+        """xyz: int32 CUDA tensor (n, 3), borrowed until the next sync."""
+        assert xyz.is_cuda and str(xyz.dtype) == "torch.int32" and xyz.is_contiguous()
+        self._borrowed.append(xyz)
+        self._c(self.lib.sg_activate_coords(self.h, _ptr(xyz), xyz.numel() // 3))
+
+    def deactivate_all(self):
+        self._c(self.lib.sg_deactivate_all(self.h))
+
+    def list_gen(self):
+        self._c(self.lib.sg_list_gen(self.h))
+
+    def stencil(self, op: int, src: int, dst: int, coef: float = 0.0):
+        self._c(self.lib.sg_launch_stencil(self.h, int(op), int(src), int(dst), float(coef)))
+
+    def clear(self, dst: int):
+        self.stencil(SG_CLEAR, dst, dst)
+
+    def diffuse7(self, src: int, dst: int, coef: float):
+        self.stencil(SG_DIFFUSE7, src, dst, coef)
+
+    def box27(self, src: int, dst: int):
+        self.stencil(SG_BOX27, src, dst)
+
+    def reduce_sum(self, src: int, slot: int):
+        self._c(self.lib.sg_reduce_sum(self.h, int(src), int(slot)))
+
+    def p2g(self, x, v, pmass: float, f_mass: int, f_mom0: int):
+        for t in (x, v):
+            assert t.is_cuda and str(t.dtype) == "torch.float32" and t.is_contiguous()
+        self._borrowed += [x, v]
+        self._c(self.lib.sg_p2g(self.h, _ptr(x), _ptr(v), x.numel() // 3, float(pmass), int(f_mass), int(f_mom0)))
+
+    def grid_update(self, f_mass: int, f_mom0: int, dt: float, gz: float, bound: int):
+        self._c(self.lib.sg_grid_update(self.h, int(f_mass), int(f_mom0), float(dt), float(gz), int(bound)))
+
+    def g2p(self, x, v, dt: float, f_mom0: int):
+        for t in (x, v):
+            assert t.is_cuda and str(t.dtype) == "torch.float32" and t.is_contiguous()
+        self._borrowed += [x, v]
+        self._c(self.lib.sg_g2p(self.h, _ptr(x), _ptr(v), x.numel() // 3, float(dt), int(f_mom0)))
+
+    def swap(self, a: int, b: int):
+        self._c(self.lib.sg_swap(self.h, int(a), int(b)))
+
+    def debug_wait_test(self):
+        self._c(self.lib.sg_debug_wait_test(self.h))
+
+    # ---- flush / sync ----
+    def flush(self):
+        self._c(self.lib.sg_flush(self.h))
+
+    def sync(self):
+        rc = self.lib.sg_sync(self.h)
+        self._borrowed.clear()
+        self._c(rc)
+
+    # ---- host reads / writes (implicit sync) ----
+    def num_leaves(self) -> int:
+        n = ctypes.c_int64()
+        self._c(self.lib.sg_num_leaves(self.h, ctypes.byref(n)))
+        self._borrowed.clear()
+        return n.value
+
+    def read_structure(self):
+        """(leaf_b int32[n] ascending, masks uint32[n, W])."""
+        n = self.num_leaves()
+        b = np.empty(n, dtype=np.int32)
+        m = np.empty((n, self.W), dtype=np.uint32)
+        got = ctypes.c_int64()
+        self._c(self.lib.sg_read_structure(self.h, n, ctypes.byref(got), _ptr(b), _ptr(m)))
+        assert got.value == n
+        return b, m
+
+    def read_field(self, f: int, out: np.ndarray | None = None) -> np.ndarray:
+        n = self.num_leaves()
+        if out is None:
+            out = np.empty((n, self.V), dtype=np.float32)
+        self._c(self.lib.sg_read_field(self.h, int(f), n, _ptr(out)))
+        return out
+
+    def write_field(self, f: int, vals):
+        """vals: (n_leaves, L^3) FP32 host array (numpy or pinned torch CPU
+        tensor) in list order."""
+        if isinstance(vals, np.ndarray):
+            a = np.ascontiguousarray(vals, dtype=np.float32)
+            n = a.size // self.V
+            self._c(self.lib.sg_write_field(self.h, int(f), _ptr(a), n))
+        else:
+            assert not vals.is_cuda and vals.is_contiguous()
+            self._c(self.lib.sg_write_field(self.h, int(f), _ptr(vals), vals.numel() // self.V))
+
+    def read_sums(self, n: int | None = None) -> np.ndarray:
+        n = self.max_sums if n is None else int(n)
+        out = np.zeros(n, dtype=np.float64)
+        self._c(self.lib.sg_read_sums(self.h, _ptr(out), n))
+        self._borrowed.clear()
+        return out
+
+    def stats(self) -> dict:
+        s = SgStats()
+        self._c(self.lib.sg_get_stats(self.h, ctypes.byref(s)))
+        return {name: getattr(s, name) for name, _ in SgStats._fields_}
+
+
+def leaf_coords(leaf_b: np.ndarray, N: int, L: int) -> np.ndarray:
+    """Global voxel coordinates (n, L^3, 3) of listed leaves (int64)."""
+    R = N // L
+    b = np.asarray(leaf_b, dtype=np.int64)
+    l = np.arange(L ** 3)
+    out = np.empty((b.size, L ** 3, 3), dtype=np.int64)
+    out[:, :, 0] = (b // (R * R))[:, None] * L + (l // (L * L))[None, :]
+    out[:, :, 1] = ((b // R) % R)[:, None] * L + ((l // L) % L)[None, :]
+    out[:, :, 2] = (b % R)[:, None] * L + (l % L)[None, :]
+    return out

@@ -1,0 +1,760 @@
+// sg_api.cu -- the C ABI of libsgrid: grid lifetime, the deferred op queue,
+// and the inter-kernel optimizer that runs on flush.
+//
+// The queue follows AsyncTaichi's asynchronous engine (Sec. 5, Sec. 7.1):
+// calls only enqueue; sg_flush (explicit, non-blocking) or any host read
+// (implicit) optimizes the queued ops and launches them.  The optimizer works
+// on a fixed op vocabulary instead of a general state-flow graph; what it
+// needs of the SFG (Sec. 4) is the version of each grid's mask and list
+// states, kept on the host across flushes (the partial garbage collection of
+// Sec. 7.1 keeps the latest owners alive for the same purpose):
+//   - list-generation removal (Sec. 6.2): a list generated from the current
+//     mask version is reused; a device flag lets a launched list generation
+//     skip itself when no activation changed anything;
+//   - activation demotion (Sec. 6.3): a shell activation identical to one
+//     applied since the last deactivation is a no-op and is dropped, and
+//     struct-for stores skip the activation check (their targets are the loop
+//     indices over the same, unchanged list);
+//   - task fusion (Sec. 6.4, Supplement Sec. 2): adjacent struct-fors over the
+//     same list are merged when a fused kernel exists for the sequence;
+//   - dead-store elimination (Sec. 6.5): a clear fully overwritten before it
+//     is read is dropped, and a scratch intermediate consumed inside a fused
+//     kernel is never stored.
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <set>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/sgrid.h"
+#include "sg_device.h"
+
+using namespace sg;
+
+namespace {
+
+thread_local std::string t_last_error;
+
+int fail(int code, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
+int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    t_last_error = buf;
+    return code;
+}
+
+enum OpKind { OP_ACT_SHELL, OP_ACT_COORDS, OP_DEACT, OP_LISTGEN, OP_STENCIL, OP_SUM, OP_P2G, OP_GRID_UPDATE, OP_G2P, OP_TEST_WAIT };
+
+struct Op {
+    OpKind kind;
+    int op = 0;          // stencil op code
+    int src = 0, dst = 0;  // physical field indices
+    bool dst_scratch = false;
+    float coef = 0.f;
+    long long lo2 = 0, hi2 = 0;
+    int strict = 0;
+    const void *p0 = nullptr;
+    void *p1 = nullptr, *p2 = nullptr;
+    long long n = 0;
+    float f0 = 0.f, f1 = 0.f;
+    int i0 = 0, i1 = 0, i2 = 0;
+    long long slot = 0;
+};
+
+}  // namespace
+
+struct sg_grid {
+    sg_desc desc{};
+    cudaStream_t stream = nullptr;
+    bool dry = false;
+    DevGrid dev{};
+    LaunchCfg lc{};
+    int num_tiles = 1;
+    int phys[SG_MAX_FIELDS];
+    uint32_t opts = SG_OPT_ALL;
+    std::vector<Op> queue;
+    // host-side state versions (Sec. 4): mask and list of the grid's structure
+    unsigned long long mask_ver = 1, list_ver = 0;
+    std::set<std::tuple<long long, long long, int>> applied_shells;
+    unsigned long long lg_calls = 0;
+    long long known_leaves = 0;
+    sg_stats stats{};
+    int latched = SG_OK;
+    std::vector<void *> blocks;
+    Ctrl *host_ctrl = nullptr;  // pinned
+    size_t staging_bytes = 0;
+};
+
+namespace {
+
+void *dev_alloc(sg_grid *g, size_t bytes)
+{
+    bytes = (bytes + 255) & ~size_t(255);
+    void *p = nullptr;
+    if (g->desc.alloc) {
+        p = g->desc.alloc(bytes, g->desc.alloc_ctx);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (p) g->blocks.push_back(p);
+    return p;
+}
+
+void dev_free_all(sg_grid *g)
+{
+    for (void *p : g->blocks) {
+        if (g->desc.free) g->desc.free(p, g->desc.alloc_ctx);
+        else cudaFree(p);
+    }
+    g->blocks.clear();
+}
+
+int cuda_check(cudaError_t e, const char *what)
+{
+    if (e == cudaSuccess) return SG_OK;
+    return fail(SG_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+int after_launch(sg_grid *g, const char *what)
+{
+    g->stats.launches++;
+    if (g->dry) return SG_OK;
+    return cuda_check(cudaPeekAtLastError(), what);
+}
+
+bool valid_field(const sg_grid *g, int f) { return f >= 0 && f < g->desc.n_fields; }
+
+int push(sg_grid *g, Op op)
+{
+    g->queue.push_back(op);
+    g->stats.ops_enqueued++;
+    return SG_OK;
+}
+
+double leaf_bytes(const sg_grid *g) { return 4.0 * double(g->dev.L) * g->dev.L * g->dev.L; }
+
+// ---- list state ------------------------------------------------------------
+int launch_list(sg_grid *g, bool force, int test_wait)
+{
+    if (!g->dry) launch_listgen(g->dev, g->stream, force ? 1 : 0, g->lg_calls, g->num_tiles, test_wait);
+    g->lg_calls++;
+    g->stats.listgen_run++;
+    return after_launch(g, "list generation");
+}
+
+// Make the list current for a struct-for.  LGR off: the eager form's clear-list
+// and list-generation tasks (Sec. 6.1, Fig. 8).  LGR on: nothing if the list was
+// generated from the current mask version (Sec. 6.2).
+int ensure_list(sg_grid *g)
+{
+    int rc;
+    if (!(g->opts & SG_OPT_LGR)) {
+        if (!g->dry) launch_clear_list(g->dev, g->stream);
+        if ((rc = after_launch(g, "clear list"))) return rc;
+        if ((rc = launch_list(g, true, 0))) return rc;
+        g->list_ver = g->mask_ver;
+        return SG_OK;
+    }
+    if (g->list_ver == g->mask_ver) {
+        g->stats.listgen_removed++;
+        return SG_OK;
+    }
+    if ((rc = launch_list(g, false, 0))) return rc;
+    g->list_ver = g->mask_ver;
+    return SG_OK;
+}
+
+// Is physical field f read (before being fully overwritten) by queue[from..)?
+bool read_later(const sg_grid *g, size_t from, int f)
+{
+    for (size_t i = from; i < g->queue.size(); ++i) {
+        const Op &o = g->queue[i];
+        if ((o.kind == OP_STENCIL && o.op != SG_CLEAR && o.src == f) || (o.kind == OP_SUM && o.src == f)) return true;
+        if (o.kind == OP_P2G || o.kind == OP_GRID_UPDATE || o.kind == OP_G2P) return true;  // conservative
+        if (o.kind == OP_STENCIL && o.dst == f) return false;  // fully overwritten
+    }
+    return false;
+}
+
+// Dead-store test for a clear at queue[i]: the next access to its field in
+// the queue is a full overwrite by a struct-for over the same list.
+bool clear_is_dead(const sg_grid *g, size_t i)
+{
+    const int f = g->queue[i].dst;
+    for (size_t k = i + 1; k < g->queue.size(); ++k) {
+        const Op &o = g->queue[k];
+        if (o.kind != OP_STENCIL && o.kind != OP_SUM) return false;  // structure may change
+        if (o.kind == OP_SUM && o.src == f) return false;
+        if (o.kind == OP_STENCIL && o.op != SG_CLEAR && o.src == f) return false;
+        if (o.kind == OP_STENCIL && o.dst == f) return true;
+    }
+    return false;
+}
+
+int run_struct_for_group(sg_grid *g, size_t &i)
+{
+    int rc;
+    const bool ad = (g->opts & SG_OPT_AD) != 0;
+    const bool fuse = (g->opts & SG_OPT_FUSE) && (g->opts & SG_OPT_LGR);
+    const bool dse = (g->opts & SG_OPT_DSE) != 0;
+    const int check = ad ? 0 : 1;
+    const Op &a = g->queue[i];
+    const double lb = leaf_bytes(g) * double(g->known_leaves);
+
+    if (a.kind == OP_STENCIL && a.op == SG_CLEAR && dse && clear_is_dead(g, i)) {
+        g->stats.stores_removed++;
+        i += 1;
+        return SG_OK;
+    }
+    if ((rc = ensure_list(g))) return rc;
+    auto next = [&](size_t k) -> const Op * { return (i + k < g->queue.size()) ? &g->queue[i + k] : nullptr; };
+
+    if (a.kind == OP_SUM) {
+        if (!g->dry) launch_sum(g->dev, g->stream, a.src, (int)a.slot, g->lc);
+        g->stats.bytes_model += lb;
+        i += 1;
+        return after_launch(g, "sum");
+    }
+    if (a.op == SG_CLEAR) {
+        if (!g->dry) launch_clear(g->dev, g->stream, a.dst, check, g->lc);
+        g->stats.bytes_model += lb;
+        i += 1;
+        return after_launch(g, "clear");
+    }
+    const Op *b = next(1);
+    if (fuse && g->dev.L == 8 && a.op == SG_DIFFUSE7 && b && b->kind == OP_STENCIL && b->op == SG_BOX27 &&
+        b->src == a.dst && a.src != a.dst && b->dst != a.dst && b->dst != a.src) {
+        // fused diffuse7 -> box27 (+ sum of its output)
+        const Op *c = next(2);
+        const bool with_sum = c && c->kind == OP_SUM && c->src == b->dst;
+        const size_t after = i + (with_sum ? 3 : 2);
+        const bool store_t = !(dse && a.dst_scratch && !read_later(g, after, a.dst));
+        if (!store_t) g->stats.stores_removed++;
+        if (!g->dry)
+            launch_diffuse_box(g->dev, g->stream, a.src, a.dst, b->dst, a.coef, store_t ? 1 : 0, check,
+                               with_sum ? (int)c->slot : -1, g->lc);
+        g->stats.ops_fused += with_sum ? 2 : 1;
+        g->stats.bytes_model += lb * (store_t ? 3.0 : 2.0);
+        i = after;
+        return after_launch(g, "fused diffuse7+box27");
+    }
+    const Op *c = b;
+    const bool with_sum = fuse && c && c->kind == OP_SUM && c->src == a.dst;
+    const int sum_slot = with_sum ? (int)c->slot : -1;
+    if (a.op == SG_DIFFUSE7) {
+        if (!g->dry) launch_diffuse7(g->dev, g->stream, a.src, a.dst, a.coef, check, sum_slot, g->lc);
+    } else {
+        if (!g->dry) launch_box27(g->dev, g->stream, a.src, a.dst, check, sum_slot, g->lc);
+    }
+    g->stats.bytes_model += 2.0 * lb;
+    if (with_sum) g->stats.ops_fused += 1;
+    i += with_sum ? 2 : 1;
+    return after_launch(g, "stencil");
+}
+
+int do_flush(sg_grid *g)
+{
+    int rc = SG_OK;
+    g->stats.flushes++;
+    size_t i = 0;
+    while (i < g->queue.size() && rc == SG_OK) {
+        const Op &o = g->queue[i];
+        switch (o.kind) {
+            case OP_ACT_SHELL: {
+                const auto sig = std::make_tuple(o.lo2, o.hi2, o.strict);
+                if ((g->opts & SG_OPT_AD) && g->applied_shells.count(sig)) {
+                    g->stats.act_demoted++;
+                } else {
+                    if (!g->dry) launch_activate_shell(g->dev, g->stream, o.lo2, o.hi2, o.strict);
+                    g->applied_shells.insert(sig);
+                    g->mask_ver++;
+                    g->stats.act_launched++;
+                    rc = after_launch(g, "activate shell");
+                }
+                ++i;
+                break;
+            }
+            case OP_ACT_COORDS: {
+                if (!g->dry) launch_mark_coords(g->dev, g->stream, (const int32_t *)o.p0, o.n);
+                if (!(rc = after_launch(g, "mark coords"))) {
+                    if (!g->dry) launch_alloc_needed(g->dev, g->stream);
+                    if (!(rc = after_launch(g, "allocate"))) {
+                        if (!g->dry) launch_setbits_coords(g->dev, g->stream, (const int32_t *)o.p0, o.n);
+                        rc = after_launch(g, "set bits");
+                    }
+                }
+                g->mask_ver++;
+                g->stats.act_launched++;
+                ++i;
+                break;
+            }
+            case OP_DEACT:
+                if (!g->dry) launch_deactivate_all(g->dev, g->stream);
+                g->mask_ver++;
+                g->applied_shells.clear();
+                rc = after_launch(g, "deactivate");
+                ++i;
+                break;
+            case OP_LISTGEN:
+                rc = ensure_list(g);
+                ++i;
+                break;
+            case OP_TEST_WAIT:
+                rc = launch_list(g, false, 1);
+                ++i;
+                break;
+            case OP_STENCIL:
+            case OP_SUM:
+                rc = run_struct_for_group(g, i);
+                break;
+            case OP_P2G:
+                if (!g->dry) launch_p2g_mark(g->dev, g->stream, (const float *)o.p0, o.n);
+                if (!(rc = after_launch(g, "p2g mark"))) {
+                    if (!g->dry) launch_alloc_needed(g->dev, g->stream);
+                    if (!(rc = after_launch(g, "allocate"))) {
+                        if (!g->dry)
+                            launch_p2g_scatter(g->dev, g->stream, (const float *)o.p0, (const float *)o.p1, o.n, o.f0,
+                                               o.i0, o.i1);
+                        rc = after_launch(g, "p2g scatter");
+                    }
+                }
+                g->mask_ver++;
+                g->stats.act_launched++;
+                ++i;
+                break;
+            case OP_GRID_UPDATE:
+                if (!(rc = ensure_list(g))) {
+                    if (!g->dry) launch_grid_update(g->dev, g->stream, o.i0, o.i1, o.f0, o.f1, o.i2, g->lc);
+                    rc = after_launch(g, "grid update");
+                }
+                ++i;
+                break;
+            case OP_G2P:
+                if (!g->dry) launch_g2p(g->dev, g->stream, (float *)o.p1, (float *)o.p2, o.n, o.f0, o.i0);
+                rc = after_launch(g, "g2p");
+                ++i;
+                break;
+        }
+    }
+    g->queue.clear();
+    return rc;
+}
+
+int map_device_error(int bits)
+{
+    if (bits & kErrPool) return fail(SG_ERR_POOL_EXHAUSTED, "leaf pool exhausted (max_leaves too small)");
+    if (bits & kErrTimeout) return fail(SG_ERR_TIMEOUT, "a bounded device-side wait gave up");
+    return SG_OK;
+}
+
+// Flush, wait, read the control block; latch and clear device errors.
+int do_sync(sg_grid *g)
+{
+    int rc = do_flush(g);
+    if (g->dry) return rc;
+    if (rc) return rc;
+    if ((rc = cuda_check(cudaMemcpyAsync(g->host_ctrl, g->dev.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, g->stream),
+                         "read control block")))
+        return rc;
+    if ((rc = cuda_check(cudaStreamSynchronize(g->stream), "stream synchronize"))) return rc;
+    const int bits = g->host_ctrl->err;
+    if (bits) {
+        cudaMemsetAsync(&g->dev.ctrl->err, 0, sizeof(int32_t), g->stream);
+        cudaStreamSynchronize(g->stream);
+        const int code = map_device_error(bits);
+        if (g->latched == SG_OK) g->latched = code;
+    }
+    if (g->list_ver == g->mask_ver) g->known_leaves = g->host_ctrl->list_n;
+    const int out = g->latched;
+    g->latched = SG_OK;
+    return out;
+}
+
+// Implicit sync with a current list (reads need list order).
+int sync_with_list(sg_grid *g)
+{
+    if (g->dry) return fail(SG_ERR_INVALID, "a dry-run grid holds no data");
+    int rc = do_flush(g);
+    if (rc) return rc;
+    if (g->list_ver != g->mask_ver) {
+        // a read needs the list even when LGR is off; generate it without a clear
+        if ((rc = launch_list(g, false, 0))) return rc;
+        g->list_ver = g->mask_ver;
+    }
+    return do_sync(g);
+}
+
+int ensure_staging(sg_grid *g)
+{
+    const size_t need = size_t(g->desc.max_leaves) * size_t(g->dev.L) * g->dev.L * g->dev.L * 4;
+    if (g->staging_bytes >= need) return SG_OK;
+    void *p = dev_alloc(g, need);
+    if (!p) return fail(SG_ERR_OOM, "staging buffer of %zu bytes", need);
+    g->dev.staging = (float *)p;
+    g->dev.staging_u = (uint32_t *)p;
+    g->staging_bytes = need;
+    return SG_OK;
+}
+
+}  // namespace
+
+// ============================================================================
+// C ABI
+// ============================================================================
+extern "C" {
+
+int sg_create(const sg_desc *desc, void *cuda_stream, sg_grid **out)
+{
+    if (!desc || !out) return fail(SG_ERR_INVALID, "null argument");
+    *out = nullptr;
+    const int lg2 = desc->leaf_log2;
+    if (lg2 != 2 && lg2 != 3) return fail(SG_ERR_INVALID, "leaf_log2 must be 2 or 3");
+    const int L = 1 << lg2;
+    if (desc->res <= 0 || desc->res > 4096 || desc->res % L) return fail(SG_ERR_INVALID, "res must be a positive multiple of the leaf edge <= 4096");
+    if (desc->n_fields < 1 || desc->n_fields > SG_MAX_FIELDS) return fail(SG_ERR_INVALID, "n_fields out of range");
+    if (desc->max_leaves < 1 || desc->max_leaves > (1LL << 30)) return fail(SG_ERR_INVALID, "max_leaves out of range");
+    if (desc->max_sums < 0) return fail(SG_ERR_INVALID, "max_sums < 0");
+    if ((desc->alloc == nullptr) != (desc->free == nullptr)) return fail(SG_ERR_INVALID, "alloc and free come together");
+
+    sg_grid *g = new (std::nothrow) sg_grid();
+    if (!g) return fail(SG_ERR_OOM, "host allocation");
+    g->desc = *desc;
+    g->stream = (cudaStream_t)cuda_stream;
+    g->dry = (desc->flags & SG_CREATE_DRY_RUN) != 0;
+    for (int f = 0; f < SG_MAX_FIELDS; ++f) g->phys[f] = f;
+    DevGrid &d = g->dev;
+    d.N = desc->res;
+    d.L = L;
+    d.lg2 = lg2;
+    d.R = desc->res / L;
+    d.W = (L * L * L) / 32;
+    d.F = desc->n_fields;
+    d.cap = desc->max_leaves;
+    const long long nr = (long long)d.R * d.R * d.R;
+    g->num_tiles = (int)((nr + kListTile - 1) / kListTile);
+    if (g->dry) {
+        g->lc.num_sms = 152;
+        g->lc.persistent_ctas = 152;
+        *out = g;
+        return SG_OK;
+    }
+    int dev = 0;
+    int rc;
+    if ((rc = cuda_check(cudaGetDevice(&dev), "cudaGetDevice")) ||
+        (rc = cuda_check(cudaDeviceGetAttribute(&g->lc.num_sms, cudaDevAttrMultiProcessorCount, dev), "SM count"))) {
+        delete g;
+        return rc;
+    }
+    g->lc.persistent_ctas = g->lc.num_sms;
+    const size_t V = size_t(L) * L * L;
+    const int max_ctas = 8192;
+    struct Need { void **dst; size_t bytes; } needs[] = {
+        {(void **)&d.root, sizeof(int32_t) * nr},
+        {(void **)&d.mask, sizeof(uint32_t) * d.W * d.cap},
+        {(void **)&d.list_slot, sizeof(int32_t) * d.cap},
+        {(void **)&d.list_b, sizeof(int32_t) * d.cap},
+        {(void **)&d.nbr, sizeof(int32_t) * 27 * d.cap},
+        {(void **)&d.need, (size_t)nr},
+        {(void **)&d.tile_status, sizeof(unsigned long long) * g->num_tiles},
+        {(void **)&d.partials, sizeof(double) * max_ctas},
+        {(void **)&d.sums, sizeof(double) * std::max(1, desc->max_sums)},
+        {(void **)&d.ctrl, sizeof(Ctrl)},
+    };
+    for (auto &nd : needs) {
+        *nd.dst = dev_alloc(g, nd.bytes);
+        if (!*nd.dst) {
+            dev_free_all(g);
+            delete g;
+            return fail(SG_ERR_OOM, "device allocation of %zu bytes", nd.bytes);
+        }
+    }
+    for (int f = 0; f < d.F; ++f) {
+        d.field[f] = (float *)dev_alloc(g, sizeof(float) * V * d.cap);
+        if (!d.field[f]) {
+            dev_free_all(g);
+            delete g;
+            return fail(SG_ERR_OOM, "field allocation");
+        }
+    }
+    if (cudaMallocHost((void **)&g->host_ctrl, sizeof(Ctrl)) != cudaSuccess) {
+        cudaGetLastError();
+        dev_free_all(g);
+        delete g;
+        return fail(SG_ERR_OOM, "pinned host control block");
+    }
+    // initial state: all pointers null, empty pool and list, structure dirty
+    cudaStream_t s = g->stream;
+    rc = cuda_check(cudaMemsetAsync(d.root, 0xff, sizeof(int32_t) * nr, s), "init root");
+    if (!rc) rc = cuda_check(cudaMemsetAsync(d.need, 0, (size_t)nr, s), "init need");
+    if (!rc) rc = cuda_check(cudaMemsetAsync(d.tile_status, 0, sizeof(unsigned long long) * g->num_tiles, s), "init status");
+    if (!rc) rc = cuda_check(cudaMemsetAsync(d.sums, 0, sizeof(double) * std::max(1, desc->max_sums), s), "init sums");
+    if (!rc) {
+        Ctrl c{};
+        c.dirty = 1;
+        std::memcpy(g->host_ctrl, &c, sizeof c);
+        rc = cuda_check(cudaMemcpyAsync(d.ctrl, g->host_ctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, s), "init ctrl");
+    }
+    if (!rc) rc = cuda_check(cudaStreamSynchronize(s), "init sync");
+    if (rc) {
+        cudaFreeHost(g->host_ctrl);
+        dev_free_all(g);
+        delete g;
+        return rc;
+    }
+    *out = g;
+    return SG_OK;
+}
+
+int sg_destroy(sg_grid *g)
+{
+    if (!g) return SG_OK;
+    int rc = SG_OK;
+    if (!g->dry) {
+        rc = cuda_check(cudaStreamSynchronize(g->stream), "stream synchronize");
+        dev_free_all(g);
+        if (g->host_ctrl) cudaFreeHost(g->host_ctrl);
+    }
+    delete g;
+    return rc;
+}
+
+int sg_set_opts(sg_grid *g, uint32_t opts)
+{
+    if (!g || (opts & ~SG_OPT_ALL)) return fail(SG_ERR_INVALID, "bad grid or options");
+    g->opts = opts;
+    return SG_OK;
+}
+
+int sg_activate_shell(sg_grid *g, int64_t lo2, int64_t hi2, int32_t lo_strict)
+{
+    if (!g) return fail(SG_ERR_INVALID, "null grid");
+    Op o{OP_ACT_SHELL};
+    o.lo2 = lo2;
+    o.hi2 = hi2;
+    o.strict = lo_strict ? 1 : 0;
+    return push(g, o);
+}
+
+int sg_activate_coords(sg_grid *g, const int32_t *dev_xyz, int64_t n)
+{
+    if (!g || n < 0 || (n > 0 && !dev_xyz)) return fail(SG_ERR_INVALID, "bad coordinates");
+    if (n == 0) return SG_OK;
+    Op o{OP_ACT_COORDS};
+    o.p0 = dev_xyz;
+    o.n = n;
+    return push(g, o);
+}
+
+int sg_deactivate_all(sg_grid *g)
+{
+    if (!g) return fail(SG_ERR_INVALID, "null grid");
+    return push(g, Op{OP_DEACT});
+}
+
+int sg_list_gen(sg_grid *g)
+{
+    if (!g) return fail(SG_ERR_INVALID, "null grid");
+    return push(g, Op{OP_LISTGEN});
+}
+
+int sg_launch_stencil(sg_grid *g, int32_t op, int32_t src, int32_t dst, float coef)
+{
+    if (!g) return fail(SG_ERR_INVALID, "null grid");
+    if (op != SG_CLEAR && op != SG_DIFFUSE7 && op != SG_BOX27) return fail(SG_ERR_INVALID, "unknown stencil op %d", op);
+    if (!valid_field(g, dst) || (op != SG_CLEAR && (!valid_field(g, src) || src == dst)))
+        return fail(SG_ERR_INVALID, "bad field indices src=%d dst=%d", src, dst);
+    Op o{OP_STENCIL};
+    o.op = op;
+    o.src = (op == SG_CLEAR) ? g->phys[dst] : g->phys[src];
+    o.dst = g->phys[dst];
+    o.dst_scratch = (g->desc.scratch_mask >> dst) & 1u;
+    o.coef = coef;
+    return push(g, o);
+}
+
+int sg_reduce_sum(sg_grid *g, int32_t src, int64_t out_slot)
+{
+    if (!g || !valid_field(g, src) || out_slot < 0 || out_slot >= g->desc.max_sums)
+        return fail(SG_ERR_INVALID, "bad reduction arguments");
+    Op o{OP_SUM};
+    o.src = g->phys[src];
+    o.slot = out_slot;
+    return push(g, o);
+}
+
+int sg_p2g(sg_grid *g, const float *dev_x, const float *dev_v, int64_t n, float pmass, int32_t f_mass, int32_t f_mom0)
+{
+    if (!g || n < 0 || (n > 0 && (!dev_x || !dev_v)) || !valid_field(g, f_mass) || !valid_field(g, f_mom0) ||
+        !valid_field(g, f_mom0 + 2) || (f_mass >= f_mom0 && f_mass <= f_mom0 + 2))
+        return fail(SG_ERR_INVALID, "bad p2g arguments");
+    if (n == 0) return SG_OK;
+    Op o{OP_P2G};
+    o.p0 = dev_x;
+    o.p1 = (void *)dev_v;
+    o.n = n;
+    o.f0 = pmass;
+    o.i0 = g->phys[f_mass];
+    o.i1 = g->phys[f_mom0];
+    if (g->phys[f_mom0 + 1] != o.i1 + 1 || g->phys[f_mom0 + 2] != o.i1 + 2)
+        return fail(SG_ERR_INVALID, "momentum fields must be three consecutive unswapped fields");
+    return push(g, o);
+}
+
+int sg_grid_update(sg_grid *g, int32_t f_mass, int32_t f_mom0, float dt, float gz, int32_t bound)
+{
+    if (!g || !valid_field(g, f_mass) || !valid_field(g, f_mom0) || !valid_field(g, f_mom0 + 2))
+        return fail(SG_ERR_INVALID, "bad grid update arguments");
+    Op o{OP_GRID_UPDATE};
+    o.i0 = g->phys[f_mass];
+    o.i1 = g->phys[f_mom0];
+    o.i2 = bound;
+    o.f0 = dt;
+    o.f1 = gz;
+    if (g->phys[f_mom0 + 1] != o.i1 + 1 || g->phys[f_mom0 + 2] != o.i1 + 2)
+        return fail(SG_ERR_INVALID, "momentum fields must be three consecutive unswapped fields");
+    return push(g, o);
+}
+
+int sg_g2p(sg_grid *g, float *dev_x, float *dev_v, int64_t n, float dt, int32_t f_mom0)
+{
+    if (!g || n < 0 || (n > 0 && (!dev_x || !dev_v)) || !valid_field(g, f_mom0) || !valid_field(g, f_mom0 + 2))
+        return fail(SG_ERR_INVALID, "bad g2p arguments");
+    if (n == 0) return SG_OK;
+    Op o{OP_G2P};
+    o.p1 = dev_x;
+    o.p2 = dev_v;
+    o.n = n;
+    o.f0 = dt;
+    o.i0 = g->phys[f_mom0];
+    if (g->phys[f_mom0 + 1] != o.i0 + 1 || g->phys[f_mom0 + 2] != o.i0 + 2)
+        return fail(SG_ERR_INVALID, "momentum fields must be three consecutive unswapped fields");
+    return push(g, o);
+}
+
+int sg_swap(sg_grid *g, int32_t a, int32_t b)
+{
+    if (!g || !valid_field(g, a) || !valid_field(g, b)) return fail(SG_ERR_INVALID, "bad field indices");
+    std::swap(g->phys[a], g->phys[b]);
+    return SG_OK;
+}
+
+int sg_flush(sg_grid *g)
+{
+    if (!g) return fail(SG_ERR_INVALID, "null grid");
+    return do_flush(g);
+}
+
+int sg_sync(sg_grid *g)
+{
+    if (!g) return fail(SG_ERR_INVALID, "null grid");
+    return do_sync(g);
+}
+
+int sg_num_leaves(sg_grid *g, int64_t *n_leaves)
+{
+    if (!g || !n_leaves) return fail(SG_ERR_INVALID, "null argument");
+    if (g->dry) {
+        *n_leaves = 0;
+        return do_flush(g);
+    }
+    int rc = sync_with_list(g);
+    *n_leaves = g->host_ctrl->list_n;
+    return rc;
+}
+
+int sg_read_structure(sg_grid *g, int64_t cap, int64_t *n_leaves, int32_t *leaf_b, uint32_t *masks)
+{
+    if (!g || !n_leaves || cap < 0) return fail(SG_ERR_INVALID, "null argument");
+    int rc = sync_with_list(g);
+    if (rc) return rc;
+    const long long n = g->host_ctrl->list_n;
+    *n_leaves = n;
+    if (n > cap) return fail(SG_ERR_INVALID, "buffer holds %lld leaves, list has %lld", (long long)cap, n);
+    if (n == 0) return SG_OK;
+    if (leaf_b && (rc = cuda_check(cudaMemcpyAsync(leaf_b, g->dev.list_b, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, g->stream),
+                                   "copy list")))
+        return rc;
+    if (masks) {
+        if ((rc = ensure_staging(g))) return rc;
+        launch_gather_masks(g->dev, g->stream, g->lc);
+        if ((rc = after_launch(g, "gather masks"))) return rc;
+        if ((rc = cuda_check(cudaMemcpyAsync(masks, g->dev.staging_u, sizeof(uint32_t) * g->dev.W * n,
+                                             cudaMemcpyDeviceToHost, g->stream),
+                             "copy masks")))
+            return rc;
+    }
+    return cuda_check(cudaStreamSynchronize(g->stream), "stream synchronize");
+}
+
+int sg_read_field(sg_grid *g, int32_t f, int64_t cap, float *host_vals)
+{
+    if (!g || !valid_field(g, f) || !host_vals || cap < 0) return fail(SG_ERR_INVALID, "bad arguments");
+    int rc = sync_with_list(g);
+    if (rc) return rc;
+    const long long n = g->host_ctrl->list_n;
+    if (n > cap) return fail(SG_ERR_INVALID, "buffer holds %lld leaves, list has %lld", (long long)cap, n);
+    if (n == 0) return SG_OK;
+    if ((rc = ensure_staging(g))) return rc;
+    launch_gather_field(g->dev, g->stream, g->phys[f], g->lc);
+    if ((rc = after_launch(g, "gather field"))) return rc;
+    const size_t bytes = sizeof(float) * size_t(n) * g->dev.L * g->dev.L * g->dev.L;
+    if ((rc = cuda_check(cudaMemcpyAsync(host_vals, g->dev.staging, bytes, cudaMemcpyDeviceToHost, g->stream), "copy field")))
+        return rc;
+    return cuda_check(cudaStreamSynchronize(g->stream), "stream synchronize");
+}
+
+int sg_write_field(sg_grid *g, int32_t f, const float *host_vals, int64_t n_leaves)
+{
+    if (!g || !valid_field(g, f) || !host_vals || n_leaves < 0) return fail(SG_ERR_INVALID, "bad arguments");
+    int rc = sync_with_list(g);
+    if (rc) return rc;
+    const long long n = g->host_ctrl->list_n;
+    if (n != n_leaves) return fail(SG_ERR_INVALID, "list has %lld leaves, got %lld", n, (long long)n_leaves);
+    if (n == 0) return SG_OK;
+    if ((rc = ensure_staging(g))) return rc;
+    const size_t bytes = sizeof(float) * size_t(n) * g->dev.L * g->dev.L * g->dev.L;
+    if ((rc = cuda_check(cudaMemcpyAsync(g->dev.staging, host_vals, bytes, cudaMemcpyHostToDevice, g->stream), "copy field")))
+        return rc;
+    launch_scatter_field(g->dev, g->stream, g->phys[f], g->lc);
+    if ((rc = after_launch(g, "scatter field"))) return rc;
+    return cuda_check(cudaStreamSynchronize(g->stream), "stream synchronize");
+}
+
+int sg_read_sums(sg_grid *g, double *host, int64_t n)
+{
+    if (!g || n < 0 || n > g->desc.max_sums || (n > 0 && !host)) return fail(SG_ERR_INVALID, "bad arguments");
+    if (g->dry) return fail(SG_ERR_INVALID, "a dry-run grid holds no data");
+    int rc = do_sync(g);
+    if (rc) return rc;
+    if (n == 0) return SG_OK;
+    if ((rc = cuda_check(cudaMemcpyAsync(host, g->dev.sums, sizeof(double) * n, cudaMemcpyDeviceToHost, g->stream), "copy sums")))
+        return rc;
+    return cuda_check(cudaStreamSynchronize(g->stream), "stream synchronize");
+}
+
+int sg_get_stats(sg_grid *g, sg_stats *out)
+{
+    if (!g || !out) return fail(SG_ERR_INVALID, "null argument");
+    *out = g->stats;
+    return SG_OK;
+}
+
+int sg_debug_wait_test(sg_grid *g)
+{
+    if (!g) return fail(SG_ERR_INVALID, "null grid");
+    return push(g, Op{OP_TEST_WAIT});
+}
+
+const char *sg_last_error(void) { return t_last_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,108 @@
+// sg_device.h -- device-side layout of one sparse grid and the launch
+// wrappers the host queue calls.  Internal to libsgrid.
+//
+// HBM layout of a grid (all arrays allocated once at creation):
+//   root[R^3]            int32   leaf slot of each pointer cell, -1 = null
+//   mask[cap][W]         uint32  W = L^3/32 bit words per leaf slot
+//   field[f][cap][L^3]   float   one array per field (structure of arrays),
+//                                each leaf a contiguous 2 KB (L=8) block
+//   list_slot[cap], list_b[cap]  the active-leaf list, ascending b
+//   nbr[cap][27]         int32   slots of the 3x3x3 leaf neighbourhood of each
+//                                list entry (index (di+1)*9+(dj+1)*3+(dk+1)),
+//                                -1 = null or outside the domain
+//   need[R^3]            uint8   activation requests (coords / particles)
+//   tile_status[tiles]   uint64  list-compaction look-back words
+//   partials[max_ctas]   double  per-CTA reduction partials
+//   sums[max_sums]       double  reduction results
+//   ctrl                 Ctrl    counters and flags below
+// Invariant kept by every kernel: a stored value at an inactive voxel of an
+// allocated leaf is 0, so whole-leaf loads need no mask to read 0 there.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace sg {
+
+constexpr int kMaxFields = 16;
+
+enum ErrBits : int32_t {
+    kErrPool = 1,     // leaf pool exhausted
+    kErrTimeout = 2,  // a bounded wait gave up
+};
+
+struct Ctrl {
+    int32_t pool_count;   // slots handed out (may exceed cap after exhaustion)
+    int32_t dirty;        // structure changed since the list was generated
+    int32_t list_n;       // entries in the active-leaf list
+    int32_t err;          // ErrBits
+    unsigned long long lg_ticket;  // list-compaction tile tickets (monotone)
+    unsigned long long lg_done;    // list-compaction finished tiles (monotone)
+    unsigned int red_ticket;       // reduction finished CTAs (reset by the last)
+    int32_t never_set;    // a flag nothing writes (bounded-wait test)
+    int32_t timeout_site; // which wait gave up (0 none, 1 look-back, 2 test)
+    int32_t pad[6];
+};
+
+struct DevGrid {
+    int32_t N, L, R, lg2, W, F;
+    int64_t cap;
+    int32_t *root;
+    uint32_t *mask;
+    float *field[kMaxFields];
+    int32_t *list_slot;
+    int32_t *list_b;
+    int32_t *nbr;
+    uint8_t *need;
+    unsigned long long *tile_status;
+    double *partials;
+    double *sums;
+    Ctrl *ctrl;
+    float *staging;      // n * L^3 floats for host reads/writes
+    uint32_t *staging_u; // aliases staging for mask gathers
+};
+
+// Launch shapes chosen by the host.
+struct LaunchCfg {
+    int num_sms;
+    int persistent_ctas;  // CTAs of the persistent leaf loops
+};
+
+constexpr int kListTile = 1024;  // root cells per compaction CTA
+constexpr int kListThreads = 256;
+constexpr int kSpinLimit = 1 << 22;  // bounded waits: polls before giving up
+
+// ---- structure kernels (sg_structure.cu) ----
+void launch_activate_shell(const DevGrid &g, cudaStream_t s, long long lo2, long long hi2, int strict);
+void launch_mark_coords(const DevGrid &g, cudaStream_t s, const int32_t *xyz, long long n);
+void launch_alloc_needed(const DevGrid &g, cudaStream_t s);
+void launch_setbits_coords(const DevGrid &g, cudaStream_t s, const int32_t *xyz, long long n);
+void launch_deactivate_all(const DevGrid &g, cudaStream_t s);
+void launch_clear_list(const DevGrid &g, cudaStream_t s);
+void launch_listgen(const DevGrid &g, cudaStream_t s, int force, unsigned long long call_idx,
+                    int num_tiles, int test_wait);
+void launch_gather_field(const DevGrid &g, cudaStream_t s, int f, const LaunchCfg &lc);
+void launch_gather_masks(const DevGrid &g, cudaStream_t s, const LaunchCfg &lc);
+void launch_scatter_field(const DevGrid &g, cudaStream_t s, int f, const LaunchCfg &lc);
+
+// ---- stencil kernels (sg_stencil.cu) ----
+// check_act: eager activation-on-write check on every store (Sec. 6.3 off).
+void launch_clear(const DevGrid &g, cudaStream_t s, int dst, int check_act, const LaunchCfg &lc);
+void launch_diffuse7(const DevGrid &g, cudaStream_t s, int src, int dst, float coef,
+                     int check_act, int sum_slot, const LaunchCfg &lc);
+void launch_box27(const DevGrid &g, cudaStream_t s, int src, int dst, int check_act,
+                  int sum_slot, const LaunchCfg &lc);
+void launch_diffuse_box(const DevGrid &g, cudaStream_t s, int src, int tmp, int dst, float coef,
+                        int store_tmp, int check_act, int sum_slot, const LaunchCfg &lc);
+void launch_sum(const DevGrid &g, cudaStream_t s, int src, int sum_slot, const LaunchCfg &lc);
+int stencil_persistent_ctas(int num_sms, int which);
+
+// ---- particle kernels (sg_particle.cu) ----
+void launch_p2g_mark(const DevGrid &g, cudaStream_t s, const float *x, long long n);
+void launch_p2g_scatter(const DevGrid &g, cudaStream_t s, const float *x, const float *v,
+                        long long n, float pmass, int f_mass, int f_mom0);
+void launch_grid_update(const DevGrid &g, cudaStream_t s, int f_mass, int f_mom0, float dt,
+                        float gz, int bound, const LaunchCfg &lc);
+void launch_g2p(const DevGrid &g, cudaStream_t s, float *x, float *v, long long n, float dt,
+                int f_mom0);
+
+}  // namespace sg

@@ -1,0 +1,463 @@
+// sg_structure.cu -- activation, allocation, list generation and host
+// transfers of the sparse grid's structure.
+//
+// Paper passages: the pointer/bitmask mask states (Sec. 4 "States"),
+// activation on write with zero-fill (Sec. 3.2 item 3, Fig. 4), list
+// generation (Sec. 3.2 item 2) and the allocator state (Sec. 4 "States").
+#include "sg_common.cuh"
+
+namespace sg {
+
+// ---------------------------------------------------------------------------
+// Activation from the shell predicate.  One warp per root cell: the warp culls
+// the cell when the leaf's bounding box cannot meet the band, otherwise it
+// builds the leaf's mask words with one ballot per 32 voxels, allocates the
+// leaf if the pointer is null (zero-filling every field) and ORs the words in.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void axis_range(int i0, int L, int N, long long &mn, long long &mx)
+{
+    long long e0 = 2LL * i0 + 1 - N, e1 = 2LL * (i0 + L - 1) + 1 - N;
+    long long lo;
+    if (e0 > 0) lo = e0;
+    else if (e1 < 0) lo = -e1;
+    else lo = (e0 & 1) ? 1 : 0;  // the progression e0, e0+2, ... crosses zero
+    long long hi = (-e0 > e1) ? -e0 : e1;
+    mn += lo * lo;
+    mx += hi * hi;
+}
+
+__global__ void __launch_bounds__(256) k_activate_shell(DevGrid g, long long lo2, long long hi2, int strict)
+{
+    const int lane = lane_id();
+    const long long nr = (long long)g.R * g.R * g.R;
+    const long long b = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (b >= nr) return;  // warp-uniform
+    const int R = g.R, L = g.L, lg2 = g.lg2, N = g.N;
+    const int bi = (int)(b / ((long long)R * R)), bj = (int)((b / R) % R), bk = (int)(b % R);
+    long long dmin = 0, dmax = 0;
+    axis_range(bi * L, L, N, dmin, dmax);
+    axis_range(bj * L, L, N, dmin, dmax);
+    axis_range(bk * L, L, N, dmin, dmax);
+    const bool lo_possible = strict ? (dmax > lo2) : (dmax >= lo2);
+    if (!lo_possible || dmin >= hi2) return;
+
+    uint32_t bits = 0;
+    for (int w = 0; w < g.W; ++w) {
+        const int l = w * 32 + lane;
+        const int li = l >> (2 * lg2), lj = (l >> lg2) & (L - 1), lk = l & (L - 1);
+        const long long a = 2LL * (bi * L + li) + 1 - N;
+        const long long c = 2LL * (bj * L + lj) + 1 - N;
+        const long long d = 2LL * (bk * L + lk) + 1 - N;
+        const long long D = a * a + c * c + d * d;
+        const bool on = (strict ? (lo2 < D) : (lo2 <= D)) && (D < hi2);
+        const unsigned word = __ballot_sync(kFull, on);
+        if (lane == w) bits = word;
+    }
+    if (!__any_sync(kFull, bits != 0u)) return;
+
+    int slot = 0, fresh = 0;
+    if (lane == 0) {
+        slot = g.root[b];
+        if (slot < 0) {
+            const int s = atomicAdd(&g.ctrl->pool_count, 1);
+            if (s < g.cap) {
+                slot = s;
+                fresh = 1;
+            } else {
+                raise_error(g, kErrPool);
+            }
+        }
+    }
+    slot = __shfl_sync(kFull, slot, 0);
+    fresh = __shfl_sync(kFull, fresh, 0);
+    if (slot < 0) return;
+    const int V = L * L * L;
+    if (fresh) {
+        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int f = 0; f < g.F; ++f) {
+            float4 *p = reinterpret_cast<float4 *>(g.field[f] + (long long)slot * V);
+            for (int q = lane; q < V / 4; q += 32) p[q] = z;
+        }
+        if (lane < g.W) g.mask[(long long)slot * g.W + lane] = bits;
+        __syncwarp();
+        if (lane == 0) {
+            g.root[b] = slot;
+            mark_dirty(g);
+        }
+    } else {
+        bool changed = false;
+        if (lane < g.W) {
+            uint32_t *m = &g.mask[(long long)slot * g.W + lane];
+            const uint32_t old = *m, nw = old | bits;
+            if (nw != old) {
+                *m = nw;
+                changed = true;
+            }
+        }
+        if (__any_sync(kFull, changed) && lane == 0) mark_dirty(g);
+    }
+}
+
+void launch_activate_shell(const DevGrid &g, cudaStream_t s, long long lo2, long long hi2, int strict)
+{
+    const long long nr = (long long)g.R * g.R * g.R;
+    const int warps = 8;
+    const long long blocks = (nr + warps - 1) / warps;
+    k_activate_shell<<<(unsigned)blocks, warps * 32, 0, s>>>(g, lo2, hi2, strict);
+}
+
+// ---------------------------------------------------------------------------
+// Activation of explicit voxels and of particle stencils runs in three steps
+// so that no thread ever waits for another: mark the pointer cells that are
+// needed, allocate the null ones (compaction-style, one atomic per warp), then
+// set the voxel bits with atomicOr.
+// ---------------------------------------------------------------------------
+__global__ void k_mark_coords(DevGrid g, const int32_t *__restrict__ xyz, long long n)
+{
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
+         p += (long long)gridDim.x * blockDim.x) {
+        const int i = xyz[3 * p], j = xyz[3 * p + 1], k = xyz[3 * p + 2];
+        if ((unsigned)i >= (unsigned)g.N || (unsigned)j >= (unsigned)g.N || (unsigned)k >= (unsigned)g.N) continue;
+        const long long b = ((long long)(i >> g.lg2) * g.R + (j >> g.lg2)) * g.R + (k >> g.lg2);
+        g.need[b] = 1;
+    }
+}
+
+void launch_mark_coords(const DevGrid &g, cudaStream_t s, const int32_t *xyz, long long n)
+{
+    if (n <= 0) return;
+    long long blocks = (n + 255) / 256;
+    if (blocks > 65535) blocks = 65535;
+    k_mark_coords<<<(unsigned)blocks, 256, 0, s>>>(g, xyz, n);
+}
+
+__global__ void __launch_bounds__(256) k_alloc_needed(DevGrid g)
+{
+    const long long nr = (long long)g.R * g.R * g.R;
+    const int lane = lane_id();
+    const int V = g.L * g.L * g.L;
+    bool any_alloc = false;
+    for (long long base = (long long)blockIdx.x * blockDim.x; base < nr; base += (long long)gridDim.x * blockDim.x) {
+        const long long b = base + threadIdx.x;
+        bool want = false;
+        if (b < nr && g.need[b]) {
+            g.need[b] = 0;
+            want = g.root[b] < 0;
+        }
+        const unsigned m = __ballot_sync(kFull, want);
+        if (m == 0u) continue;
+        const int leader = __ffs(m) - 1;
+        int first = 0;
+        if (lane == leader) first = atomicAdd(&g.ctrl->pool_count, __popc(m));
+        first = __shfl_sync(kFull, first, leader);
+        int slot = -1;
+        if (want) {
+            const int s = first + __popc(m & lanemask_lt());
+            if (s < g.cap) slot = s;
+            else raise_error(g, kErrPool);
+        }
+        unsigned ok = __ballot_sync(kFull, slot >= 0);
+        while (ok) {
+            const int src = __ffs(ok) - 1;
+            const int s = __shfl_sync(kFull, slot, src);
+            const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int f = 0; f < g.F; ++f) {
+                float4 *p = reinterpret_cast<float4 *>(g.field[f] + (long long)s * V);
+                for (int q = lane; q < V / 4; q += 32) p[q] = z;
+            }
+            for (int w = lane; w < g.W; w += 32) g.mask[(long long)s * g.W + w] = 0u;
+            ok &= ok - 1;
+        }
+        __syncwarp();
+        if (slot >= 0) {
+            g.root[b] = slot;
+            any_alloc = true;
+        }
+    }
+    if (any_alloc) mark_dirty(g);
+}
+
+void launch_alloc_needed(const DevGrid &g, cudaStream_t s)
+{
+    const long long nr = (long long)g.R * g.R * g.R;
+    long long blocks = (nr + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    k_alloc_needed<<<(unsigned)blocks, 256, 0, s>>>(g);
+}
+
+__global__ void k_setbits_coords(DevGrid g, const int32_t *__restrict__ xyz, long long n)
+{
+    bool changed = false;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
+         p += (long long)gridDim.x * blockDim.x) {
+        const int i = xyz[3 * p], j = xyz[3 * p + 1], k = xyz[3 * p + 2];
+        if ((unsigned)i >= (unsigned)g.N || (unsigned)j >= (unsigned)g.N || (unsigned)k >= (unsigned)g.N) continue;
+        const int L = g.L, lg2 = g.lg2;
+        const long long b = ((long long)(i >> lg2) * g.R + (j >> lg2)) * g.R + (k >> lg2);
+        const int slot = g.root[b];
+        if (slot < 0) continue;  // pool was exhausted; the error is latched
+        const int l = (((i & (L - 1)) << lg2) + (j & (L - 1))) * L + (k & (L - 1));
+        const uint32_t bit = 1u << (l & 31);
+        uint32_t *w = &g.mask[(long long)slot * g.W + (l >> 5)];
+        if ((*w & bit) == 0u) {
+            const uint32_t old = atomicOr(w, bit);
+            if ((old & bit) == 0u) changed = true;
+        }
+    }
+    if (changed) mark_dirty(g);
+}
+
+void launch_setbits_coords(const DevGrid &g, cudaStream_t s, const int32_t *xyz, long long n)
+{
+    if (n <= 0) return;
+    long long blocks = (n + 255) / 256;
+    if (blocks > 65535) blocks = 65535;
+    k_setbits_coords<<<(unsigned)blocks, 256, 0, s>>>(g, xyz, n);
+}
+
+// ---------------------------------------------------------------------------
+// Deactivate everything: null pointers, empty pool, empty list.  Leaf slots
+// are zero-filled again when they are next allocated.
+// ---------------------------------------------------------------------------
+__global__ void k_deactivate_all(DevGrid g)
+{
+    const long long nr = (long long)g.R * g.R * g.R;
+    for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < nr; b += (long long)gridDim.x * blockDim.x)
+        g.root[b] = -1;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        g.ctrl->pool_count = 0;
+        g.ctrl->list_n = 0;
+        g.ctrl->dirty = 1;
+    }
+}
+
+void launch_deactivate_all(const DevGrid &g, cudaStream_t s)
+{
+    const long long nr = (long long)g.R * g.R * g.R;
+    long long blocks = (nr + 255) / 256;
+    if (blocks > 2048) blocks = 2048;
+    k_deactivate_all<<<(unsigned)blocks, 256, 0, s>>>(g);
+}
+
+// The clear-list task of the eager form (Sec. 6.1, Fig. 8): empty the list.
+__global__ void k_clear_list(DevGrid g)
+{
+    g.ctrl->list_n = 0;
+    g.ctrl->dirty = 1;
+}
+
+void launch_clear_list(const DevGrid &g, cudaStream_t s) { k_clear_list<<<1, 1, 0, s>>>(g); }
+
+// ---------------------------------------------------------------------------
+// List generation (Sec. 3.2 item 2): compact the non-null pointer cells into a
+// list in ascending b, in one pass with a decoupled look-back prefix sum.
+// Each CTA takes a tile of kListTile root cells in ticket order (so every
+// predecessor tile has started), counts its active cells with a block scan,
+// publishes its aggregate, looks back over its predecessors' published words
+// for its exclusive prefix, writes its list entries, then fills their
+// 27-neighbour slots.  Status words carry (call + 1) << 34 so words left by
+// earlier calls are never taken for current ones.  Every wait is bounded by
+// wall time; a wait that gives up latches kErrTimeout and the kernel returns.
+// Unless `force`, the whole launch is a no-op when no activation since the
+// last generation changed the structure (ctrl->dirty == 0).
+// ---------------------------------------------------------------------------
+constexpr unsigned long long kFlagAgg = 1ull, kFlagIncl = 2ull;
+constexpr unsigned long long kLookbackLimitNs = 1000000000ull;  // 1 s
+constexpr unsigned long long kTestWaitLimitNs = 200000000ull;   // 0.2 s
+
+__global__ void __launch_bounds__(kListThreads) k_listgen(DevGrid g, int force, unsigned long long call_idx,
+                                                          int num_tiles, int test_wait)
+{
+    __shared__ int s_tile, s_skip, s_prefix;
+    __shared__ int s_wsum[kListThreads / 32];
+    __shared__ int s_cells[kListTile];
+    const int tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
+    const unsigned long long tick0 = call_idx * (unsigned long long)num_tiles;
+    const unsigned long long tag = (call_idx + 1ull) << 34;
+    if (tid == 0) {
+        const unsigned long long t = atomicAdd(&g.ctrl->lg_ticket, 1ull);
+        s_tile = (int)(t - tick0);
+        s_skip = (!force && *(volatile int32_t *)&g.ctrl->dirty == 0) ? 1 : 0;
+    }
+    __syncthreads();
+    const int tile = s_tile;
+    if (!s_skip && tile >= 0 && tile < num_tiles) {
+        const long long nr = (long long)g.R * g.R * g.R;
+        const long long c0 = (long long)tile * kListTile + tid * 4;
+        int sl[4];
+        if (c0 + 3 < nr) {
+            const int4 v = *reinterpret_cast<const int4 *>(g.root + c0);
+            sl[0] = v.x; sl[1] = v.y; sl[2] = v.z; sl[3] = v.w;
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) sl[q] = (c0 + q < nr) ? g.root[c0 + q] : -1;
+        }
+        int cnt = (sl[0] >= 0) + (sl[1] >= 0) + (sl[2] >= 0) + (sl[3] >= 0);
+        const int incl = warp_incl_scan(cnt);
+        if (lane == 31) s_wsum[warp] = incl;
+        __syncthreads();
+        int wbase = 0, total = 0;
+#pragma unroll
+        for (int w = 0; w < kListThreads / 32; ++w) {
+            const int v = s_wsum[w];
+            wbase += (w < warp) ? v : 0;
+            total += v;
+        }
+        const int excl = wbase + incl - cnt;
+        if (tid == 0) {
+            const unsigned long long flag = (tile == 0) ? kFlagIncl : kFlagAgg;
+            atomicExch(&g.tile_status[tile], tag | (flag << 32) | (unsigned long long)(unsigned)total);
+        }
+        if (warp == 0) {
+            int prefix = 0;
+            if (tile > 0) {
+                int pred = tile - 1;
+                const unsigned long long t_start = global_timer_ns();
+                for (;;) {
+                    const int idx = pred - lane;
+                    unsigned long long w = tag | (kFlagIncl << 32);
+                    if (idx >= 0) {
+                        for (;;) {
+                            w = *(volatile unsigned long long *)&g.tile_status[idx];
+                            if ((w >> 34) == (call_idx + 1ull)) break;
+                            if (global_timer_ns() - t_start > kLookbackLimitNs) {
+                                raise_error(g, kErrTimeout);
+                                g.ctrl->timeout_site = 1;
+                                w = tag | (kFlagIncl << 32);
+                                break;
+                            }
+                            __nanosleep(32);
+                        }
+                    }
+                    const unsigned long long flag = (w >> 32) & 3ull;
+                    const int val = (int)(w & 0xffffffffull);
+                    const unsigned im = __ballot_sync(kFull, flag == kFlagIncl);
+                    const int upto = im ? (__ffs(im) - 1) : 31;
+                    prefix += warp_sum(lane <= upto ? val : 0);
+                    if (im) break;
+                    pred -= 32;
+                }
+                if (lane == 0)
+                    atomicExch(&g.tile_status[tile],
+                               tag | (kFlagIncl << 32) | (unsigned long long)(unsigned)(prefix + total));
+            }
+            if (lane == 0) s_prefix = prefix;
+        }
+        __syncthreads();
+        const int prefix = s_prefix;
+        int pos = excl;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (sl[q] >= 0) {
+                const int b = (int)(c0 + q);
+                g.list_slot[prefix + pos] = sl[q];
+                g.list_b[prefix + pos] = b;
+                s_cells[pos] = b;
+                ++pos;
+            }
+        }
+        if (tile == num_tiles - 1 && tid == 0) g.ctrl->list_n = prefix + total;
+        __syncthreads();
+        const int R = g.R;
+        for (int idx = tid; idx < total * 27; idx += kListThreads) {
+            const int e = idx / 27, q = idx - e * 27;
+            const int b = s_cells[e];
+            const int bi = b / (R * R) + q / 9 - 1;
+            const int bj = (b / R) % R + (q / 3) % 3 - 1;
+            const int bk = b % R + q % 3 - 1;
+            int v = -1;
+            if ((unsigned)bi < (unsigned)R && (unsigned)bj < (unsigned)R && (unsigned)bk < (unsigned)R)
+                v = g.root[((long long)bi * R + bj) * R + bk];
+            g.nbr[(long long)(prefix + e) * 27 + q] = v;
+        }
+    }
+    if (test_wait && tile == 0 && tid == 0) {
+        // Fault-injection hook: wait on a flag that nothing sets, bounded.
+        const unsigned long long t_start = global_timer_ns();
+        while (*(volatile int32_t *)&g.ctrl->never_set == 0) {
+            if (global_timer_ns() - t_start > kTestWaitLimitNs) {
+                raise_error(g, kErrTimeout);
+                g.ctrl->timeout_site = 2;
+                break;
+            }
+            __nanosleep(1000);
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        const unsigned long long d = atomicAdd(&g.ctrl->lg_done, 1ull) - tick0;
+        if (d == (unsigned long long)num_tiles - 1ull && !s_skip) g.ctrl->dirty = 0;
+    }
+}
+
+void launch_listgen(const DevGrid &g, cudaStream_t s, int force, unsigned long long call_idx, int num_tiles,
+                    int test_wait)
+{
+    k_listgen<<<num_tiles, kListThreads, 0, s>>>(g, force, call_idx, num_tiles, test_wait);
+}
+
+// ---------------------------------------------------------------------------
+// Host transfers: gather leaves in list order into the staging buffer, and
+// scatter from it (applying the mask so inactive voxels stay 0).
+// ---------------------------------------------------------------------------
+__global__ void k_gather_field(DevGrid g, int f)
+{
+    const long long n = g.ctrl->list_n;
+    const int V4 = (g.L * g.L * g.L) >> 2;
+    const float4 *src = reinterpret_cast<const float4 *>(g.field[f]);
+    float4 *dst = reinterpret_cast<float4 *>(g.staging);
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n * V4; q += (long long)gridDim.x * blockDim.x) {
+        const long long e = q / V4;
+        const int r = (int)(q - e * V4);
+        dst[q] = src[(long long)g.list_slot[e] * V4 + r];
+    }
+}
+
+void launch_gather_field(const DevGrid &g, cudaStream_t s, int f, const LaunchCfg &lc)
+{
+    k_gather_field<<<lc.num_sms * 4, 256, 0, s>>>(g, f);
+}
+
+__global__ void k_gather_masks(DevGrid g)
+{
+    const long long n = g.ctrl->list_n;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n * g.W; q += (long long)gridDim.x * blockDim.x) {
+        const long long e = q / g.W;
+        const int w = (int)(q - e * g.W);
+        g.staging_u[q] = g.mask[(long long)g.list_slot[e] * g.W + w];
+    }
+}
+
+void launch_gather_masks(const DevGrid &g, cudaStream_t s, const LaunchCfg &lc)
+{
+    k_gather_masks<<<lc.num_sms * 4, 256, 0, s>>>(g);
+}
+
+__global__ void k_scatter_field(DevGrid g, int f)
+{
+    const long long n = g.ctrl->list_n;
+    const int V4 = (g.L * g.L * g.L) >> 2;
+    const float4 *src = reinterpret_cast<const float4 *>(g.staging);
+    float4 *dst = reinterpret_cast<float4 *>(g.field[f]);
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n * V4; q += (long long)gridDim.x * blockDim.x) {
+        const long long e = q / V4;
+        const int r = (int)(q - e * V4);
+        const int slot = g.list_slot[e];
+        const uint32_t word = g.mask[(long long)slot * g.W + (r >> 3)];
+        const int sh = (r & 7) * 4;
+        float4 v = src[q];
+        v.x = ((word >> (sh + 0)) & 1u) ? v.x : 0.f;
+        v.y = ((word >> (sh + 1)) & 1u) ? v.y : 0.f;
+        v.z = ((word >> (sh + 2)) & 1u) ? v.z : 0.f;
+        v.w = ((word >> (sh + 3)) & 1u) ? v.w : 0.f;
+        dst[(long long)slot * V4 + r] = v;
+    }
+}
+
+void launch_scatter_field(const DevGrid &g, cudaStream_t s, int f, const LaunchCfg &lc)
+{
+    k_scatter_field<<<lc.num_sms * 4, 256, 0, s>>>(g, f);
+}
+
+}  // namespace sg

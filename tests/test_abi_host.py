@@ -1,0 +1,221 @@
+"""CPU tests of the C ABI: the library loads, exports what include/sgrid.h
+declares, validates arguments, and its queue optimizer makes the launch
+decisions the paper describes (dry-run grids: no device work)."""
+import ctypes
+import os
+
+import pytest
+
+import paper_2012_08141_gb300 as sg
+from workload import band512, tiny_shell
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_examples.txt")
+
+
+def golden():
+    out = {}
+    for line in open(GOLDEN):
+        line = line.split("#", 1)[0].strip()
+        if line:
+            k, v = (s.strip() for s in line.split("=", 1))
+            out[k] = [int(t) for t in v.split()]
+    return out
+
+
+def dry(res=64, lg2=3, F=3, scratch=0b010, sums=8):
+    return sg.Grid(res, lg2, F, max_leaves=1024, max_sums=sums, scratch_mask=scratch, dry_run=True)
+
+
+def test_library_exports_every_declared_symbol():
+    lib = sg.load_library()
+    names = sg.header_functions()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_library_is_in_tree():
+    lib = sg.load_library()
+    assert os.path.dirname(os.path.abspath(lib._name)).endswith("paper_2012_08141_gb300")
+
+
+def test_invalid_arguments():
+    lib = sg.load_library()
+    desc = sg.SgDesc(60, 3, 2, 1, 16, 0, sg.SG_CREATE_DRY_RUN)   # 60 is not a multiple of 8
+    h = ctypes.c_void_p()
+    assert lib.sg_create(ctypes.byref(desc), None, ctypes.byref(h)) == sg.SG_ERR_INVALID
+    assert b"multiple" in lib.sg_last_error()
+    g = dry()
+    with pytest.raises(sg.SgError) as e:
+        g.stencil(7, 0, 1)
+    assert e.value.code == sg.SG_ERR_INVALID
+    with pytest.raises(sg.SgError):
+        g.diffuse7(1, 1, 0.1)                      # src == dst
+    with pytest.raises(sg.SgError):
+        g.reduce_sum(0, 8)                         # slot out of range
+    with pytest.raises(sg.SgError):
+        g.set_opts(99)
+    with pytest.raises(sg.SgError):
+        g.read_field(0)                            # dry-run grid holds no data
+
+
+def cfg1_step(g, s):
+    g.activate_shell(s.lo2, s.hi2, s.lo_strict)
+    g.list_gen()
+    g.diffuse7(0, 1, 0.1)
+    g.swap(0, 1)
+
+
+def cfg2_step(g, slot):
+    g.clear(1)
+    g.diffuse7(0, 1, 0.1)
+    g.box27(1, 2)
+    g.swap(0, 2)
+    g.reduce_sum(0, slot)
+
+
+def launches(g, fn):
+    before = g.stats()["launches"]
+    fn()
+    g.flush()
+    return g.stats()["launches"] - before
+
+
+def test_eager_is_three_tasks_per_kernel():
+    """Sec. 6.1 / Fig. 8: each sparse kernel is clear list + list generation +
+    struct-for; two kernels are 6 tasks."""
+    gold = golden()
+    g = dry()
+    g.set_opts(sg.SG_OPT_EAGER)
+    g.activate_shell(100, 400, False)
+    g.flush()
+    n = launches(g, lambda: (g.diffuse7(0, 1, 0.1), g.box27(1, 2)))
+    assert n == gold["two_kernels_tasks_eager"][0] == 2 * gold["tasks_per_sparse_kernel_eager"][0]
+
+
+def test_two_kernels_after_lgr_and_fusion():
+    """Sec. 6.1 / Fig. 9: after list-generation removal and fusion two kernels
+    need at most 3 tasks; this compaction rewrites the whole list, so it needs
+    no clear-list task (one list generation + one fused kernel)."""
+    gold = golden()
+    g = dry()
+    g.activate_shell(100, 400, False)
+    g.flush()
+    n = launches(g, lambda: (g.diffuse7(0, 1, 0.1), g.box27(1, 2)))
+    assert n <= gold["two_kernels_tasks_optimized"][0]
+    st = g.stats()
+    assert st["listgen_run"] == 1 and st["ops_fused"] == 1
+    # with the list current, the same pair is one launch
+    assert launches(g, lambda: (g.diffuse7(0, 1, 0.1), g.box27(1, 2))) == 1
+
+
+def test_fill_array_ten_clears_one_launch():
+    """Supplement Sec. 1 fill_array: 10 fills of one field -> 1 task (here the
+    first nine are dead stores)."""
+    gold = golden()
+    g = dry()
+    g.activate_shell(100, 400, False)
+    g.list_gen()
+    g.flush()
+    n = launches(g, lambda: [g.clear(0) for _ in range(gold["fill_array_kernels"][0])])
+    assert n == gold["fill_array_tasks_optimized"][0]
+
+
+def test_tiny_shell_launch_counts():
+    s = tiny_shell(0)
+    g = dry()
+    g.set_opts(sg.SG_OPT_EAGER)
+    per = [launches(g, lambda: cfg1_step(g, s)) for _ in range(3)]
+    assert per == [6, 6, 6]             # activate + (clear list, listgen) + (clear list, listgen, diffuse)
+    g2 = dry()
+    per2 = [launches(g2, lambda: cfg1_step(g2, s)) for _ in range(4)]
+    assert per2 == [3, 1, 1, 1]         # activation demoted and list reused after the first step
+    st = g2.stats()
+    assert st["act_demoted"] == 3 and st["act_launched"] == 1 and st["listgen_run"] == 1
+
+
+def test_band_step_launch_counts():
+    s = band512()
+    e = dry(512)
+    e.set_opts(sg.SG_OPT_EAGER)
+    e.activate_shell(s.lo2, s.hi2, s.lo_strict)
+    e.flush()
+    assert [launches(e, lambda: cfg2_step(e, 0)) for _ in range(2)] == [12, 12]
+    f = dry(512)
+    f.activate_shell(s.lo2, s.hi2, s.lo_strict)
+    f.list_gen()
+    f.flush()
+    assert [launches(f, lambda: cfg2_step(f, 0)) for _ in range(3)] == [1, 1, 1]
+    st = f.stats()
+    assert st["stores_removed"] == 6        # per step: the clear of t and the store of t
+    assert st["ops_fused"] == 6             # per step: box27 and the sum ride in diffuse7's kernel
+
+
+@pytest.mark.parametrize("opts,expect", [
+    (sg.SG_OPT_ALL & ~sg.SG_OPT_DSE, 2),                         # clear kept (+ t stored)
+    (sg.SG_OPT_ALL & ~sg.SG_OPT_FUSE, 3),                        # diffuse, box27, sum apart
+    (sg.SG_OPT_ALL & ~sg.SG_OPT_LGR, 9),                         # no fusion without LGR; lists per op; clear dead
+    (sg.SG_OPT_ALL & ~sg.SG_OPT_AD, 1),                          # still fused, stores checked
+])
+def test_ablation_launch_counts(opts, expect):
+    s = band512()
+    g = dry(512)
+    g.set_opts(opts)
+    g.activate_shell(s.lo2, s.hi2, s.lo_strict)
+    g.list_gen()
+    g.flush()
+    launches(g, lambda: cfg2_step(g, 0))
+    assert launches(g, lambda: cfg2_step(g, 1)) == expect
+
+
+def test_fusion_negative_cases():
+    """Supplement Sec. 2 criterion (3): tasks that read what another wrote at a
+    different address are not fused unless a fused kernel recomputes it; a
+    chain whose last output overwrites the first input is not fused."""
+    g = dry()
+    g.activate_shell(100, 400, False)
+    g.list_gen()
+    g.flush()
+    assert launches(g, lambda: (g.diffuse7(0, 1, 0.1), g.diffuse7(1, 2, 0.1))) == 2
+    assert launches(g, lambda: (g.diffuse7(0, 1, 0.1), g.box27(1, 0))) == 2
+    assert launches(g, lambda: (g.box27(0, 1), g.diffuse7(1, 2, 0.1))) == 2
+
+
+def test_deactivation_resets_demotion_and_list():
+    g = dry()
+    for _ in range(2):
+        g.activate_shell(100, 400, False)
+    g.list_gen()
+    g.flush()
+    st = g.stats()
+    assert st["act_launched"] == 1 and st["act_demoted"] == 1
+    g.deactivate_all()
+    g.activate_shell(100, 400, False)
+    g.diffuse7(0, 1, 0.1)
+    g.flush()
+    st2 = g.stats()
+    assert st2["act_launched"] == 2 and st2["listgen_run"] == 2
+
+
+def test_lgr_persists_across_flushes():
+    """Sec. 7.1: the latest owner of the list survives a flush, so a later
+    flush still removes list generation."""
+    g = dry()
+    g.activate_shell(100, 400, False)
+    g.list_gen()
+    g.flush()
+    g.sync()
+    assert launches(g, lambda: g.diffuse7(0, 1, 0.1)) == 1
+    assert g.stats()["listgen_removed"] >= 1
+
+
+def test_scratch_read_later_keeps_store():
+    """DSE may drop the scratch intermediate only if nothing reads it later in
+    the flush window."""
+    g = dry()
+    g.activate_shell(100, 400, False)
+    g.list_gen()
+    g.flush()
+    before = g.stats()["stores_removed"]
+    launches(g, lambda: (g.diffuse7(0, 1, 0.1), g.box27(1, 2), g.reduce_sum(1, 0)))
+    assert g.stats()["stores_removed"] == before

@@ -1,0 +1,133 @@
+"""GPU parity of the particle-grid transfers (P2G with activation, grid
+update, G2P) against the FP64 oracle.
+
+The active node set must match bit-exactly (both sides take the base-node
+decision in FP32 from the same FP32 positions).  Grid fields agree within a
+normwise relative L-inf of 1e-4 (the FP32 atomic accumulation order is
+unspecified); particle velocities within 1e-4 of their scale; positions within
+a few FP32 ulps."""
+import numpy as np
+import pytest
+
+import oracle
+from sgtest import rel_linf
+from workload import spheres_particles
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    yield
+
+
+def make(spec, max_leaves):
+    import paper_2012_08141_gb300 as sg
+    g = sg.Grid(spec.N, int(np.log2(spec.L)), 4, max_leaves=max_leaves)
+    og = oracle.Grid(spec.N, spec.L, 4)
+    return g, og
+
+
+def stencil_union_leaves(x, N, L):
+    """Leaves touched by the 27-node stencils of FP32 positions x (numpy)."""
+    X = (x.astype(np.float32) * np.float32(N)).astype(np.float32)
+    base = np.floor(X - np.float32(0.5)).astype(np.int64)
+    R = N // L
+    out = set()
+    for a in range(3):
+        for b in range(3):
+            for c in range(3):
+                i, j, k = base[:, 0] + a, base[:, 1] + b, base[:, 2] + c
+                ok = (i >= 0) & (j >= 0) & (k >= 0) & (i < N) & (j < N) & (k < N)
+                out.update((((i[ok] // L) * R + j[ok] // L) * R + k[ok] // L).tolist())
+    return np.array(sorted(out), dtype=np.int32)
+
+
+def one_step_compare(spec, max_leaves):
+    import torch
+    g, og = make(spec, max_leaves)
+    x = torch.from_numpy(spec.x).cuda()
+    v = torch.from_numpy(spec.v).cuda()
+    ox, ov = spec.x.copy(), spec.v.copy()
+    g.deactivate_all()
+    g.p2g(x, v, spec.pmass, 0, 1)
+    og.deactivate_all()
+    og.p2g(ox, ov, spec.pmass, 0, 1)
+    gb, gm = g.read_structure()
+    ob, om = og.structure()
+    np.testing.assert_array_equal(gb, ob)
+    np.testing.assert_array_equal(gm, om)
+    for f in range(4):
+        assert rel_linf(g.read_field(f), og.read_field(f)) <= TOL, f
+    # totals: partition of unity
+    assert abs(g.read_field(0).astype(np.float64).sum() - spec.n * spec.pmass) <= 1e-4 * spec.n * spec.pmass
+    g.grid_update(0, 1, spec.dt, spec.gravity, spec.bound)
+    og.grid_update(0, 1, spec.dt, spec.gravity, spec.bound)
+    for f in range(1, 4):
+        assert rel_linf(g.read_field(f), og.read_field(f)) <= TOL, f
+    g.g2p(x, v, spec.dt, 1)
+    og.g2p(ox, ov, spec.dt, 1)
+    g.sync()
+    gv, gx = v.cpu().numpy(), x.cpu().numpy()
+    assert rel_linf(gv, ov) <= TOL
+    assert np.max(np.abs(gx.astype(np.float64) - ox)) <= 4e-7
+    g.close()
+
+
+def test_p2g_g2p_small():
+    spec = spheres_particles(seed=3, n=20000, N=64, L=4, r_min=0.1, r_max=0.2)
+    one_step_compare(spec, 8192)
+
+
+def test_p2g_g2p_full_size_one_step():
+    spec = spheres_particles(seed=0)            # 2M particles, 256^3, 4^3 leaves
+    one_step_compare(spec, 262144)
+
+
+def test_particle_steps_full_size():
+    """Five full steps (deactivate, P2G, grid update, G2P) on 2M particles run
+    independently on both sides.  The node set is compared with the union of
+    the 27-node stencils of the GPU's own positions (valid at any size), the
+    particle state with the oracle's."""
+    import torch
+    import paper_2012_08141_gb300 as sg
+    spec = spheres_particles(seed=1)
+    g = sg.Grid(spec.N, 2, 4, max_leaves=262144)
+    og = oracle.Grid(spec.N, spec.L, 4)
+    x = torch.from_numpy(spec.x).cuda()
+    v = torch.from_numpy(spec.v).cuda()
+    ox, ov = spec.x.copy(), spec.v.copy()
+    for _ in range(5):
+        xs = x.cpu().numpy().copy()
+        g.deactivate_all()
+        g.p2g(x, v, spec.pmass, 0, 1)
+        g.list_gen()
+        g.grid_update(0, 1, spec.dt, spec.gravity, spec.bound)
+        gb, _ = g.read_structure()
+        np.testing.assert_array_equal(gb, stencil_union_leaves(xs, spec.N, spec.L))
+        g.g2p(x, v, spec.dt, 1)
+        og.deactivate_all()
+        og.p2g(ox, ov, spec.pmass, 0, 1)
+        og.grid_update(0, 1, spec.dt, spec.gravity, spec.bound)
+        og.g2p(ox, ov, spec.dt, 1)
+    g.sync()
+    assert rel_linf(v.cpu().numpy(), ov) <= TOL
+    assert np.max(np.abs(x.cpu().numpy().astype(np.float64) - ox)) <= 2e-6
+    g.close()
+
+
+def test_p2g_pool_exhaustion():
+    import torch
+    import paper_2012_08141_gb300 as sg
+    spec = spheres_particles(seed=2, n=5000, N=64, L=4, r_min=0.1, r_max=0.2)
+    g = sg.Grid(spec.N, 2, 4, max_leaves=16)
+    g.p2g(torch.from_numpy(spec.x).cuda(), torch.from_numpy(spec.v).cuda(), 1.0, 0, 1)
+    with pytest.raises(sg.SgError) as e:
+        g.sync()
+    assert e.value.code == sg.SG_ERR_POOL_EXHAUSTED
+    g.close()

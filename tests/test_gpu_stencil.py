@@ -1,0 +1,311 @@
+"""GPU parity of the stencil path against the FP64 oracle, through the C ABI.
+
+Structure (lists and masks) must match bit-exactly; FP32 fields within a
+normwise relative L-inf of 2e-5 after the stated number of steps; the
+per-step sums within 2e-5 relative."""
+import numpy as np
+import pytest
+
+import oracle
+from sgtest import mask_bits, rel_linf, shell_pair
+from workload import ShellSpec, band_bounds, band512, leaf_values, tiny_shell
+
+pytestmark = pytest.mark.gpu
+
+TOL = 2e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2012_08141_gb300 as sg
+    sg.load_library()
+    yield
+
+
+def sgmod():
+    import paper_2012_08141_gb300 as sg
+    return sg
+
+
+OPTS = {
+    "fused": 15,
+    "eager": 0,
+    "no_lgr": 15 & ~1,
+    "no_ad": 15 & ~2,
+    "no_fuse": 15 & ~4,
+    "no_dse": 15 & ~8,
+}
+
+
+# ---------------------------------------------------------------------------
+# 64^3 shell, 20 steps of activate -> list -> diffuse7 -> swap
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("mode", list(OPTS))
+@pytest.mark.parametrize("seed", [0, 5])
+def test_tiny_shell_20_steps(mode, seed):
+    spec = tiny_shell(seed)
+    g, og = shell_pair(spec, n_fields=2, opts=OPTS[mode])
+    ob, om = og.structure()
+    cur, oth = 0, 1
+    for _ in range(20):
+        g.activate_shell(spec.lo2, spec.hi2, spec.lo_strict)
+        g.list_gen()
+        g.diffuse7(0, 1, 0.1)
+        g.swap(0, 1)
+        og.diffuse7(cur, oth, 0.1)
+        cur, oth = oth, cur
+    gb, gm = g.read_structure()
+    np.testing.assert_array_equal(gb, ob)
+    np.testing.assert_array_equal(gm, om)
+    got = g.read_field(0)
+    ref = og.read_field(cur)
+    assert rel_linf(got, ref) <= TOL
+    # inactive voxels hold exactly 0
+    assert np.all(got[~mask_bits(gm, 512)] == 0.0)
+    g.close()
+
+
+# ---------------------------------------------------------------------------
+# Band workload: clear(t), diffuse7(x->t), box27(t->y), swap(x,y), sum(x)
+# ---------------------------------------------------------------------------
+
+def run_band(g, og, steps, slot0=0):
+    cur, y = 0, 2
+    sums_ref = []
+    for s in range(steps):
+        g.clear(1)
+        g.diffuse7(0, 1, 0.1)
+        g.box27(1, 2)
+        g.swap(0, 2)
+        g.reduce_sum(0, slot0 + s)
+        og.clear(1)
+        og.diffuse7(cur, 1, 0.1)
+        og.box27(1, y)
+        cur, y = y, cur
+        sums_ref.append(og.sum(cur))
+    return cur, np.array(sums_ref)
+
+
+@pytest.mark.parametrize("mode", list(OPTS))
+def test_band_128_100_steps(mode):
+    lo2, hi2 = band_bounds(40.0, 56.0)
+    spec = ShellSpec(128, 8, lo2, hi2, True, 3)
+    g, og = shell_pair(spec, n_fields=3, opts=OPTS[mode], scratch_mask=0b010)
+    cur, sums_ref = run_band(g, og, 100)
+    sums = g.read_sums(100)
+    assert np.max(np.abs(sums - sums_ref) / np.abs(sums_ref)) <= TOL
+    assert rel_linf(g.read_field(0), og.read_field(cur)) <= TOL
+    if mode in ("fused", "no_dse"):
+        assert g.stats()["ops_fused"] >= 100
+    g.close()
+
+
+def test_band512_full_size_fused_and_eager():
+    """The full 512^3 band (26,104 leaves): 100 steps fused and eager, every
+    per-step sum and the final field compared with one oracle run."""
+    spec = band512()
+    og = oracle.Grid(spec.N, spec.L, 3)
+    og.activate_shell(spec.lo2, spec.hi2, spec.lo_strict)
+    ob, om = og.structure()
+    assert len(ob) == 26104
+    og.write_field(0, leaf_values(spec.seed, spec.N, spec.L, ob))
+    grids = {}
+    for mode in ("fused", "eager"):
+        sg = sgmod()
+        g = sg.Grid(spec.N, 3, 3, max_leaves=32768, max_sums=100, scratch_mask=0b010)
+        g.set_opts(OPTS[mode])
+        g.activate_shell(spec.lo2, spec.hi2, spec.lo_strict)
+        g.list_gen()
+        gb, gm = g.read_structure()
+        np.testing.assert_array_equal(gb, ob)
+        np.testing.assert_array_equal(gm, om)
+        g.write_field(0, leaf_values(spec.seed, spec.N, spec.L, gb))
+        grids[mode] = g
+    cur, y = 0, 2
+    sums_ref = []
+    for s in range(100):
+        for g in grids.values():
+            g.clear(1)
+            g.diffuse7(0, 1, 0.1)
+            g.box27(1, 2)
+            g.swap(0, 2)
+            g.reduce_sum(0, s)
+            g.flush()
+        og.diffuse7(cur, 1, 0.1)
+        og.box27(1, y)
+        cur, y = y, cur
+        sums_ref.append(og.sum(cur))
+    sums_ref = np.array(sums_ref)
+    ref = og.read_field(cur)
+    for mode, g in grids.items():
+        sums = g.read_sums(100)
+        assert np.max(np.abs(sums - sums_ref) / np.abs(sums_ref)) <= TOL, mode
+        assert rel_linf(g.read_field(0), ref) <= TOL, mode
+        g.close()
+
+
+# ---------------------------------------------------------------------------
+# Edge cases
+# ---------------------------------------------------------------------------
+
+def test_empty_grid():
+    sg = sgmod()
+    g = sg.Grid(64, 3, 3, max_leaves=16, max_sums=2)
+    g.list_gen()
+    assert g.num_leaves() == 0
+    g.clear(1)
+    g.diffuse7(0, 1, 0.1)
+    g.box27(1, 2)
+    g.reduce_sum(2, 0)
+    g.diffuse7(0, 1, 0.1)
+    g.reduce_sum(1, 1)
+    np.testing.assert_array_equal(g.read_sums(2), [0.0, 0.0])
+    b, m = g.read_structure()
+    assert b.size == 0 and m.shape == (0, 16)
+    g.close()
+
+
+@pytest.mark.parametrize("N,r0,r1,strict", [(40, 4.0, 17.0, False),   # R=5: 125 root cells, ragged tile
+                                             (8, 0.0, 3.0, False),     # a single leaf
+                                             (200, 60.0, 99.0, True)]) # 15,625 cells, tail tile, leaves on the border
+def test_ragged_domains(N, r0, r1, strict):
+    lo2, hi2 = band_bounds(r0, r1)
+    spec = ShellSpec(N, 8, lo2, hi2, strict, 11)
+    for mode in ("fused", "eager"):
+        g, og = shell_pair(spec, n_fields=3, opts=OPTS[mode], scratch_mask=0b010)
+        cur, sums_ref = run_band(g, og, 7)
+        assert rel_linf(g.read_field(0), og.read_field(cur)) <= TOL
+        sums = g.read_sums(7)
+        assert np.max(np.abs(sums - sums_ref) / np.maximum(np.abs(sums_ref), 1e-30)) <= TOL
+        g.close()
+
+
+def test_full_domain_boundary_reads_zero():
+    """Every voxel active: out-of-domain neighbours read 0 at all six faces."""
+    spec = ShellSpec(24, 8, 0, 10 ** 9, False, 2)
+    for mode in ("fused", "eager"):
+        g, og = shell_pair(spec, n_fields=3, opts=OPTS[mode])
+        cur, _ = run_band(g, og, 5)
+        assert rel_linf(g.read_field(0), og.read_field(cur)) <= TOL
+        g.close()
+
+
+def test_activate_coords_parity():
+    sg = sgmod()
+    import torch
+    rng = np.random.default_rng(4)
+    xyz = rng.integers(-3, 99, size=(5000, 3)).astype(np.int32)   # some outside the 96^3 domain
+    g = sg.Grid(96, 3, 2, max_leaves=2048)
+    og = oracle.Grid(96, 8, 2)
+    g.activate_coords(torch.from_numpy(xyz).cuda())
+    og.activate_coords(xyz)
+    gb, gm = g.read_structure()
+    ob, om = og.structure()
+    np.testing.assert_array_equal(gb, ob)
+    np.testing.assert_array_equal(gm, om)
+    # a second batch: new bits in existing leaves and new leaves
+    xyz2 = rng.integers(0, 96, size=(3000, 3)).astype(np.int32)
+    g.activate_coords(torch.from_numpy(xyz2).cuda())
+    og.activate_coords(xyz2)
+    g.diffuse7(0, 1, 0.1)
+    gb, gm = g.read_structure()
+    ob, om = og.structure()
+    np.testing.assert_array_equal(gb, ob)
+    np.testing.assert_array_equal(gm, om)
+    g.close()
+
+
+def test_activation_zero_fills_after_values():
+    """A voxel activated after its leaf holds values reads 0 (Sec. 3.2)."""
+    sg = sgmod()
+    import torch
+    g = sg.Grid(16, 3, 2, max_leaves=8)
+    g.activate_coords(torch.tensor([[1, 2, 3], [4, 4, 4]], dtype=torch.int32, device="cuda"))
+    g.list_gen()
+    n = g.num_leaves()
+    g.write_field(0, np.full((n, 512), 5.0, dtype=np.float32))
+    g.activate_coords(torch.tensor([[1, 2, 4], [9, 9, 9]], dtype=torch.int32, device="cuda"))
+    b, m = g.read_structure()
+    vals = g.read_field(0)
+    act = mask_bits(m, 512)
+    assert act.sum() == 4
+    assert sorted(vals[act].tolist()) == [0.0, 0.0, 5.0, 5.0]
+    assert np.all(vals[~act] == 0.0)
+    g.close()
+
+
+def test_deactivate_and_reactivate():
+    spec = tiny_shell(1)
+    g, og = shell_pair(spec, n_fields=2)
+    g.deactivate_all()
+    assert g.num_leaves() == 0
+    g.activate_shell(spec.lo2, spec.hi2, spec.lo_strict)
+    b, m = g.read_structure()
+    ob, om = og.structure()
+    np.testing.assert_array_equal(b, ob)
+    np.testing.assert_array_equal(m, om)
+    assert np.all(g.read_field(0) == 0.0)      # fresh leaves are zero-filled
+    g.close()
+
+
+def test_pool_exhaustion_is_reported_and_grid_recovers():
+    sg = sgmod()
+    spec = tiny_shell(0)                    # 248 leaves
+    g = sg.Grid(64, 3, 2, max_leaves=100)
+    g.activate_shell(spec.lo2, spec.hi2, spec.lo_strict)
+    with pytest.raises(sg.SgError) as e:
+        g.sync()
+    assert e.value.code == sg.SG_ERR_POOL_EXHAUSTED
+    g.deactivate_all()
+    lo2, hi2 = band_bounds(0.0, 10.0)
+    g.activate_shell(lo2, hi2, False)
+    g.sync()
+    assert 0 < g.num_leaves() <= 100
+    g.close()
+
+
+def test_bounded_wait_reports_timeout():
+    """A device wait on a flag that nothing sets gives up, the next sync
+    returns SG_ERR_TIMEOUT, and the grid keeps working."""
+    sg = sgmod()
+    spec = tiny_shell(2)
+    g, og = shell_pair(spec, n_fields=2)
+    g.debug_wait_test()
+    with pytest.raises(sg.SgError) as e:
+        g.sync()
+    assert e.value.code == sg.SG_ERR_TIMEOUT
+    g.diffuse7(0, 1, 0.1)
+    og.diffuse7(0, 1, 0.1)
+    assert rel_linf(g.read_field(1), og.read_field(1)) <= TOL
+    g.close()
+
+
+def test_generic_leaf4_stencils():
+    """4^3 leaves run the generic kernels (tree-walk reads)."""
+    lo2, hi2 = band_bounds(6.0, 13.0)
+    spec = ShellSpec(32, 4, lo2, hi2, False, 8)
+    for mode in ("fused", "eager"):
+        g, og = shell_pair(spec, n_fields=3, opts=OPTS[mode], scratch_mask=0b010)
+        cur, sums_ref = run_band(g, og, 10)
+        assert rel_linf(g.read_field(0), og.read_field(cur)) <= TOL
+        assert np.max(np.abs(g.read_sums(10) - sums_ref) / np.abs(sums_ref)) <= TOL
+        g.close()
+
+
+def test_scratch_intermediate_kept_when_read_later():
+    lo2, hi2 = band_bounds(10.0, 20.0)
+    spec = ShellSpec(48, 8, lo2, hi2, False, 9)
+    g, og = shell_pair(spec, n_fields=3, scratch_mask=0b010)
+    g.diffuse7(0, 1, 0.1)
+    g.box27(1, 2)
+    g.reduce_sum(1, 0)      # reads the scratch intermediate: it must be stored
+    og.diffuse7(0, 1, 0.1)
+    og.box27(1, 2)
+    s = g.read_sums(1)[0]
+    assert abs(s - og.sum(1)) <= TOL * abs(og.sum(1))
+    assert rel_linf(g.read_field(2), og.read_field(2)) <= TOL
+    g.close()
