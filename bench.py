@@ -127,9 +127,10 @@ class ClockSampler:
 # our arm
 # ---------------------------------------------------------------------------
 
-def setup_band(sg, spec, opts, x_host):
+def setup_band(sg, spec, opts, x_host, variant=0):
     g = sg.Grid(spec.N, 3, 3, max_leaves=32768, max_sums=1, scratch_mask=0b010)
     g.set_opts(opts)
+    g.set_stencil_variant(variant)
     g.activate_shell(spec.lo2, spec.hi2, spec.lo_strict)
     g.list_gen()
     n = g.num_leaves()
@@ -196,8 +197,8 @@ def run_ours(args):
     x_host = leaf_values(spec.seed, spec.N, spec.L, leaf_b)
     flush_buf = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
-    fused = setup_band(sg, spec, sg.SG_OPT_ALL, x_host)
-    eager = setup_band(sg, spec, sg.SG_OPT_EAGER, x_host)
+    fused = setup_band(sg, spec, sg.SG_OPT_ALL, x_host, args.variant)
+    eager = setup_band(sg, spec, sg.SG_OPT_EAGER, x_host, args.variant)
 
     if dist:
         dist.barrier()
@@ -205,15 +206,18 @@ def run_ours(args):
     with ClockSampler(dev) as clk:
         ms_f, launches_f = time_steps(torch, fused, args.steps, args.warmup, flush_buf, stream)
     torch.cuda.synchronize()
-    ms_e, launches_e = time_steps(torch, eager, max(args.steps // 2, 5), max(args.warmup, 3), flush_buf, stream)
+    if args.only == "fused":
+        ms_e, launches_e = [float("nan")], 0
+    else:
+        ms_e, launches_e = time_steps(torch, eager, max(args.steps // 2, 5), max(args.warmup, 3), flush_buf, stream)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
 
     # end-to-end through the public API: pinned host x in, sum out, every step
     x_pinned = torch.from_numpy(x_host).pin_memory()
-    e2e_steps = max(3, min(args.steps, 20))
-    for _ in range(2):
+    e2e_steps = 0 if args.only == "fused" else max(3, min(args.steps, 20))
+    for _ in range(2 if e2e_steps else 0):
         fused.write_field(0, x_pinned)
         band_step(fused)
         fused.read_sums(1)
@@ -222,7 +226,7 @@ def run_ours(args):
         fused.write_field(0, x_pinned)
         band_step(fused)
         fused.read_sums(1)
-    e2e_s = time.perf_counter() - t0
+    e2e_s = max(time.perf_counter() - t0, 1e-9)
 
     t_f = sum(ms_f) / 1e3
     t_e = sum(ms_e) / 1e3
@@ -236,12 +240,13 @@ def run_ours(args):
     peak, peak_kind = peaks()
     achieved = n_leaves * BYTES_PER_LEAF_FUSED / (avg_ms / 1e3) / 1e9
     achieved_eager = n_leaves * BYTES_PER_LEAF_EAGER / (t_e / len(ms_e)) / 1e9
-    kernel_src = os.path.join(ROOT, "paper_2012_08141_gb300", "csrc", "sg_stencil.cu")
+    kernel_src = os.path.join(ROOT, "paper_2012_08141_gb300", "csrc",
+                              "sg_sweep.cu" if args.variant == 0 else "sg_stencil.cu")
     traffic = traffic_record(kernel_src)
 
     if rank == 0:
         cpu = None
-        if world == 1 and not args.no_cpu_baseline:
+        if world == 1 and not args.no_cpu_baseline and args.only != "fused":
             cpu = cpu_baseline(spec, leaf_b, x_host, n_active, budget_s=args.cpu_budget)
         line = {
             "metric": METRIC,
@@ -262,7 +267,8 @@ def run_ours(args):
                        "l2": "flushed before every timed step (512 MB write)"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                         "kernel": "k_diffuse_box<false,false,true>",
+                         "kernel": ("k_sweep_diffuse_box<false,false,true>" if args.variant == 0
+                                    else "k_diffuse_box<false,false,true>"),
                          "bytes_per_launch": n_leaves * BYTES_PER_LEAF_FUSED},
             "e2e": {"value": world * n_active * e2e_steps / e2e_s, "unit": "voxel-steps/s",
                     "h2d_bytes_per_step": int(x_host.nbytes), "d2h_bytes_per_step": 8},
@@ -356,6 +362,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--variant", type=int, default=0, help="stencil kernel family (0 sweep, 1 smem)")
+    ap.add_argument("--only", choices=["all", "fused"], default="all",
+                    help="fused: time only the fused step (for profiling runs)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

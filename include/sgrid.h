@@ -212,6 +212,14 @@ int sg_read_sums(sg_grid *g, double *host, int64_t n);
 /* Counters since creation. */
 int sg_get_stats(sg_grid *g, sg_stats *out);
 
+/* ---- stencil kernel family for 8^3 leaves (tuning; results are identical
+ * up to FP32 rounding order) ---- */
+#define SG_VARIANT_SWEEP 0 /* register sweep along i, rows via the read-only path */
+#define SG_VARIANT_SMEM 1  /* leaf + halo staged in shared memory */
+
+/* Select the stencil kernel family used by ops flushed from now on. */
+int sg_set_stencil_variant(sg_grid *g, int32_t variant);
+
 /* Fault injection for testing bounded waits: queue a list generation whose
  * first CTA also waits on a device flag that nothing ever sets.  The wait
  * gives up after about 0.2 s and latches SG_ERR_TIMEOUT, which the next sync

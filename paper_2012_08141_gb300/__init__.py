@@ -24,6 +24,7 @@ SG_OPT_LGR, SG_OPT_AD, SG_OPT_FUSE, SG_OPT_DSE = 1, 2, 4, 8
 SG_OPT_ALL, SG_OPT_EAGER = 15, 0
 SG_CLEAR, SG_DIFFUSE7, SG_BOX27 = 0, 1, 2
 SG_CREATE_DRY_RUN = 1
+SG_VARIANT_SWEEP, SG_VARIANT_SMEM = 0, 1
 SG_MAX_FIELDS = 16
 
 _ALLOC = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -94,6 +95,7 @@ def load_library(build: bool = True) -> ctypes.CDLL:
         "sg_read_sums": [P, P, I64],
         "sg_get_stats": [P, ctypes.POINTER(SgStats)],
         "sg_debug_wait_test": [P],
+        "sg_set_stencil_variant": [P, I32],
     }
     for name, args in sigs.items():
         fn = getattr(lib, name)
@@ -178,6 +180,9 @@ class Grid:
     # ---- queued calls ----
     def set_opts(self, opts: int):
         self._c(self.lib.sg_set_opts(self.h, int(opts)))
+
+    def set_stencil_variant(self, variant: int):
+        self._c(self.lib.sg_set_stencil_variant(self.h, int(variant)))
 
     def activate_shell(self, lo2: int, hi2: int, lo_strict: bool):
         self._c(self.lib.sg_activate_shell(self.h, int(lo2), int(hi2), int(bool(lo_strict))))

@@ -742,6 +742,14 @@ int sg_read_sums(sg_grid *g, double *host, int64_t n)
     return cuda_check(cudaStreamSynchronize(g->stream), "stream synchronize");
 }
 
+int sg_set_stencil_variant(sg_grid *g, int32_t variant)
+{
+    if (!g || (variant != SG_VARIANT_SWEEP && variant != SG_VARIANT_SMEM))
+        return fail(SG_ERR_INVALID, "bad grid or variant");
+    g->lc.variant = variant;
+    return SG_OK;
+}
+
 int sg_get_stats(sg_grid *g, sg_stats *out)
 {
     if (!g || !out) return fail(SG_ERR_INVALID, "null argument");

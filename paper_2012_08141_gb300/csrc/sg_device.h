@@ -61,10 +61,17 @@ struct DevGrid {
     uint32_t *staging_u; // aliases staging for mask gathers
 };
 
+// Stencil kernel families for 8^3 leaves (the autotuner picks one).
+enum StencilVariant : int {
+    kVariantSweep = 0,  // register sweep, rows loaded through the read-only path
+    kVariantSmem = 1,   // leaf + halo staged in shared memory by plain loads
+};
+
 // Launch shapes chosen by the host.
 struct LaunchCfg {
     int num_sms;
     int persistent_ctas;  // CTAs of the persistent leaf loops
+    int variant;          // StencilVariant
 };
 
 constexpr int kListTile = 1024;  // root cells per compaction CTA
@@ -95,6 +102,13 @@ void launch_diffuse_box(const DevGrid &g, cudaStream_t s, int src, int tmp, int 
                         int store_tmp, int check_act, int sum_slot, const LaunchCfg &lc);
 void launch_sum(const DevGrid &g, cudaStream_t s, int src, int sum_slot, const LaunchCfg &lc);
 int stencil_persistent_ctas(int num_sms, int which);
+
+// ---- register-sweep stencil kernels (sg_sweep.cu), 8^3 leaves ----
+void launch_sweep_diffuse_box(const DevGrid &g, cudaStream_t s, int src, int tmp, int dst, float coef,
+                              int store_tmp, int check_act, int sum_slot, const LaunchCfg &lc);
+// op: 1 = diffuse7, 2 = box27
+void launch_sweep_single(const DevGrid &g, cudaStream_t s, int op, int src, int dst, float coef, int check_act,
+                         int sum_slot, const LaunchCfg &lc);
 
 // ---- particle kernels (sg_particle.cu) ----
 void launch_p2g_mark(const DevGrid &g, cudaStream_t s, const float *x, long long n);

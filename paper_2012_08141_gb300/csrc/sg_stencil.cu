@@ -448,7 +448,9 @@ static void launch_single(const DevGrid &g, cudaStream_t s, int src, int dst, fl
                           int sum_slot, const LaunchCfg &lc)
 {
     const bool sum = sum_slot >= 0;
-    if (g.L == 8) {
+    if (g.L == 8 && lc.variant == kVariantSweep) {
+        launch_sweep_single(g, s, OP, src, dst, coef, check_act, sum_slot, lc);
+    } else if (g.L == 8) {
         const int ctas = stencil_persistent_ctas(lc.num_sms, 0);
         if (check_act) {
             if (sum) k_stage1<OP, true, true><<<ctas, kStageThreads, 0, s>>>(g, src, dst, coef, sum_slot);
@@ -484,6 +486,10 @@ void launch_box27(const DevGrid &g, cudaStream_t s, int src, int dst, int check_
 void launch_diffuse_box(const DevGrid &g, cudaStream_t s, int src, int tmp, int dst, float coef, int store_tmp,
                         int check_act, int sum_slot, const LaunchCfg &lc)
 {
+    if (lc.variant == kVariantSweep) {
+        launch_sweep_diffuse_box(g, s, src, tmp, dst, coef, store_tmp, check_act, sum_slot, lc);
+        return;
+    }
     const int ctas = stencil_persistent_ctas(lc.num_sms, 1);
     const bool sum = sum_slot >= 0;
 #define SG_DB(ST, CK, SU) k_diffuse_box<ST, CK, SU><<<ctas, kStageThreads, 0, s>>>(g, src, tmp, dst, coef, sum_slot)

@@ -1,0 +1,464 @@
+// sg_sweep.cu -- register-sweep stencil kernels over 8^3 leaves.
+//
+// Same operations as the staged kernels in sg_stencil.cu (7-point diffusion,
+// 27-point box smoothing, and their fusion with the sum; AsyncTaichi Sec. 6.4
+// and Sec. 6.5 for the fusion and the dead intermediate), organised so that
+// the hot loop touches no shared memory:
+//   - a lane owns one k-row column of a leaf's region (all k values of one
+//     (j) column) and sweeps along i, keeping the rows of consecutive i
+//     planes in registers;
+//   - x rows come straight from L2/HBM (read-only path), the row of plane
+//     i+3 being requested while plane i is computed;
+//   - the j-1 / j+1 rows are the neighbouring lanes' rows, taken by warp
+//     shuffle; only the two edge lanes of a leaf load their outer row;
+//   - the 3x3x3 box sum is separable: a j-sum by shuffle, an i-sum over a
+//     sliding window of the last three planes, a k-sum inside the row.
+// A row of the 12^3 (fused) or 10^3 (single) region is gathered from the
+// three leaves (dk = -1, 0, +1) of its column via the 27-neighbour table;
+// a null neighbour reads as zeros, as does an inactive voxel (the stored
+// value there is 0).
+#include "sg_common.cuh"
+
+namespace sg {
+
+constexpr int kSweepThreads = 128;
+
+__device__ __forceinline__ float4 ldg4s(const float *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
+__device__ __forceinline__ float2 ldg2s(const float *p) { return __ldg(reinterpret_cast<const float2 *>(p)); }
+__device__ __forceinline__ void stg4(float *p, float a, float b, float c, float d)
+{
+    *reinterpret_cast<float4 *>(p) = make_float4(a, b, c, d);
+}
+__device__ __forceinline__ float pick(uint32_t bits, int k, float v) { return ((bits >> k) & 1u) ? v : 0.f; }
+
+// Eager activation check of one written 8-voxel row of the own leaf.
+__device__ __forceinline__ void sweep_check_row(const DevGrid &g, int slot, int row, uint32_t bits)
+{
+    uint32_t *w = &g.mask[(long long)slot * 16 + (row >> 2)];
+    const uint32_t want = bits << ((row & 3) * 8);
+    const uint32_t have = *(volatile uint32_t *)w;
+    if ((have & want) != want) {
+        atomicOr(w, want);
+        mark_dirty(g);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Row gathers.
+// row12: region k r = 0..11 <- k- leaf local 6,7 | own 0..7 | k+ leaf local 0,1
+//        (+ 12 mask bits in the same order); used by the 2-voxel-halo fusion.
+// row10: region k r = 0..9  <- k- leaf local 7 | own 0..7 | k+ leaf local 0;
+//        used by the 1-voxel-halo single stencils.
+// `ro` = (li*8 + lj) is the row index inside a leaf.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void row12(const float *__restrict__ x, const uint8_t *__restrict__ mb, int s0, int s1,
+                                      int s2, int ro, float (&v)[12], uint32_t &m)
+{
+    float2 a = make_float2(0.f, 0.f), b = a;
+    float4 c0 = make_float4(0.f, 0.f, 0.f, 0.f), c1 = c0;
+    uint32_t m0 = 0, m1 = 0, m2 = 0;
+    if (s0 >= 0) {
+        a = ldg2s(x + (long long)s0 * 512 + ro * 8 + 6);
+        m0 = __ldg(mb + (long long)s0 * 64 + ro);
+    }
+    if (s1 >= 0) {
+        c0 = ldg4s(x + (long long)s1 * 512 + ro * 8);
+        c1 = ldg4s(x + (long long)s1 * 512 + ro * 8 + 4);
+        m1 = __ldg(mb + (long long)s1 * 64 + ro);
+    }
+    if (s2 >= 0) {
+        b = ldg2s(x + (long long)s2 * 512 + ro * 8);
+        m2 = __ldg(mb + (long long)s2 * 64 + ro);
+    }
+    v[0] = a.x; v[1] = a.y;
+    v[2] = c0.x; v[3] = c0.y; v[4] = c0.z; v[5] = c0.w;
+    v[6] = c1.x; v[7] = c1.y; v[8] = c1.z; v[9] = c1.w;
+    v[10] = b.x; v[11] = b.y;
+    m = (m0 >> 6) | (m1 << 2) | ((m2 & 3u) << 10);
+}
+
+__device__ __forceinline__ void row12v(const float *__restrict__ x, int s0, int s1, int s2, int ro, float (&v)[12])
+{
+    float2 a = make_float2(0.f, 0.f), b = a;
+    float4 c0 = make_float4(0.f, 0.f, 0.f, 0.f), c1 = c0;
+    if (s0 >= 0) a = ldg2s(x + (long long)s0 * 512 + ro * 8 + 6);
+    if (s1 >= 0) {
+        c0 = ldg4s(x + (long long)s1 * 512 + ro * 8);
+        c1 = ldg4s(x + (long long)s1 * 512 + ro * 8 + 4);
+    }
+    if (s2 >= 0) b = ldg2s(x + (long long)s2 * 512 + ro * 8);
+    v[0] = a.x; v[1] = a.y;
+    v[2] = c0.x; v[3] = c0.y; v[4] = c0.z; v[5] = c0.w;
+    v[6] = c1.x; v[7] = c1.y; v[8] = c1.z; v[9] = c1.w;
+    v[10] = b.x; v[11] = b.y;
+}
+
+__device__ __forceinline__ void row10(const float *__restrict__ x, int s0, int s1, int s2, int ro, float (&v)[10])
+{
+    float a = 0.f, b = 0.f;
+    float4 c0 = make_float4(0.f, 0.f, 0.f, 0.f), c1 = c0;
+    if (s0 >= 0) a = __ldg(x + (long long)s0 * 512 + ro * 8 + 7);
+    if (s1 >= 0) {
+        c0 = ldg4s(x + (long long)s1 * 512 + ro * 8);
+        c1 = ldg4s(x + (long long)s1 * 512 + ro * 8 + 4);
+    }
+    if (s2 >= 0) b = __ldg(x + (long long)s2 * 512 + ro * 8);
+    v[0] = a;
+    v[1] = c0.x; v[2] = c0.y; v[3] = c0.z; v[4] = c0.w;
+    v[5] = c1.x; v[6] = c1.y; v[7] = c1.z; v[8] = c1.w;
+    v[9] = b;
+}
+
+template <int N>
+__device__ __forceinline__ void shfl_row(const float (&v)[N], float (&up)[N], float (&dn)[N])
+{
+#pragma unroll
+    for (int q = 0; q < N; ++q) {
+        up[q] = __shfl_up_sync(kFull, v[q], 1);
+        dn[q] = __shfl_down_sync(kFull, v[q], 1);
+    }
+}
+
+// Plane index -> (neighbour row di+1, local i) for a region whose own leaf
+// starts at plane `h` (h = 2: 12^3 region, h = 1: 10^3 region).
+template <int H>
+__device__ __forceinline__ constexpr int plane_di(int ri) { return ri < H ? 0 : (ri < H + 8 ? 1 : 2); }
+template <int H>
+__device__ __forceinline__ constexpr int plane_li(int ri) { return (ri - H) & 7; }
+
+// ---------------------------------------------------------------------------
+// Fused diffuse7 -> box27 (+ sum).  Three leaves per warp: lanes 10*w + tj,
+// w = 0..2, tj = 0..9 own t-region column tj (region column rj = tj + 1) of
+// leaf w; lanes 30, 31 only take part in shuffles.  Step s = 0..9 computes
+// the t plane ti = s (region plane s + 1) from x planes s, s+1, s+2, forms
+// its j-sums P, and once three P planes exist writes output plane s - 2.
+// ---------------------------------------------------------------------------
+template <bool STORE_T, bool CHECK, bool SUM>
+__global__ void __launch_bounds__(kSweepThreads) k_sweep_diffuse_box(DevGrid g, int src, int tmp, int dst, float coef,
+                                                                       int sum_slot)
+{
+    __shared__ double s_red[kSweepThreads / 32];
+    const int n = g.ctrl->list_n;
+    const float *__restrict__ x = g.field[src];
+    float *__restrict__ y = g.field[dst];
+    float *__restrict__ tout = g.field[tmp];
+    const uint8_t *__restrict__ mb = reinterpret_cast<const uint8_t *>(g.mask);
+    const int lane = lane_id();
+    const int sub = lane / 10;
+    const int tj = lane - sub * 10;
+    const int rj = tj + 1;
+    const int djx = (rj < 2) ? 0 : (rj < 10 ? 1 : 2);
+    const int lj = (rj - 2) & 7;
+    const int lje = (tj == 0) ? 6 : 1;      // edge lanes' outer row: region column 0 or 11
+    const bool lo_edge = (tj == 0), hi_edge = (tj == 9);
+    const bool outlane = (tj >= 1 && tj <= 8);
+    const float c6 = 1.f - 6.f * coef;
+    const int warps_total = gridDim.x * (kSweepThreads / 32);
+    const int gw = blockIdx.x * (kSweepThreads / 32) + (threadIdx.x >> 5);
+    double acc = 0.0;
+
+    for (int e0 = gw * 3; e0 < n; e0 += warps_total * 3) {
+        const int e = e0 + sub;
+        const bool valid = (sub < 3) && (e < n);
+        int sl[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) sl[q] = valid ? __ldg(g.nbr + (long long)e * 27 + (q / 3) * 9 + djx * 3 + (q % 3)) : -1;
+        const int own = sl[4];
+        float xa[12], xb[12], xc[12], xn[12], ea[12], eb[12];
+        uint32_t ma, mb1, mc, mn = 0;
+#pragma unroll
+        for (int q = 0; q < 12; ++q) xn[q] = 0.f;
+        // planes 0, 1, 2 and the edge rows of plane 1
+        row12(x, mb, sl[0], sl[1], sl[2], plane_li<2>(0) * 8 + lj, xa, ma);
+        row12(x, mb, sl[0], sl[1], sl[2], plane_li<2>(1) * 8 + lj, xb, mb1);
+        row12(x, mb, sl[3], sl[4], sl[5], plane_li<2>(2) * 8 + lj, xc, mc);
+        {
+            float z[12];
+            if (lo_edge || hi_edge) row12v(x, sl[0], sl[1], sl[2], plane_li<2>(1) * 8 + lje, z);
+            else {
+#pragma unroll
+                for (int q = 0; q < 12; ++q) z[q] = 0.f;
+            }
+#pragma unroll
+            for (int q = 0; q < 12; ++q) ea[q] = z[q];
+        }
+        float p1[10], p2[10];
+        uint32_t mprev = 0;
+        float part = 0.f;
+#pragma unroll
+        for (int s = 0; s < 10; ++s) {
+            // prefetch plane s+3 (centre row) and the edge row of plane s+2
+            if (s + 3 <= 11) {
+                const int ri = s + 3, dx = plane_di<2>(ri) * 3;
+                row12(x, mb, sl[dx], sl[dx + 1], sl[dx + 2], plane_li<2>(ri) * 8 + lj, xn, mn);
+            }
+            {
+                const int ri = s + 2, dx = plane_di<2>(ri) * 3;
+                if (lo_edge || hi_edge) row12v(x, sl[dx], sl[dx + 1], sl[dx + 2], plane_li<2>(ri) * 8 + lje, eb);
+                else {
+#pragma unroll
+                    for (int q = 0; q < 12; ++q) eb[q] = 0.f;
+                }
+            }
+            // t on region plane s+1 (centre xb, i-1 xa, i+1 xc)
+            float up[12], dn[12];
+            shfl_row<12>(xb, up, dn);
+            float t[10];
+#pragma unroll
+            for (int q = 0; q < 10; ++q) {
+                const float jm = lo_edge ? ea[q + 1] : up[q + 1];
+                const float jp = hi_edge ? ea[q + 1] : dn[q + 1];
+                const float nb = ((xb[q] + xb[q + 2]) + (xa[q + 1] + xc[q + 1])) + (jm + jp);
+                t[q] = pick(mb1, q + 1, fmaf(coef, nb, c6 * xb[q + 1]));
+            }
+            if (STORE_T && s >= 1 && s <= 8 && outlane && valid) {
+                const int orow = (s - 1) * 8 + (tj - 1);
+                if (CHECK) sweep_check_row(g, own, orow, (mb1 >> 2) & 0xffu);
+                float *o = tout + (long long)own * 512 + orow * 8;
+                stg4(o, t[1], t[2], t[3], t[4]);
+                stg4(o + 4, t[5], t[6], t[7], t[8]);
+            }
+            // j-sums of t
+            float tu[10], td[10], p0[10];
+#pragma unroll
+            for (int q = 0; q < 10; ++q) {
+                tu[q] = __shfl_up_sync(kFull, t[q], 1);
+                td[q] = __shfl_down_sync(kFull, t[q], 1);
+            }
+#pragma unroll
+            for (int q = 0; q < 10; ++q) p0[q] = (tu[q] + t[q]) + td[q];
+            if (s >= 2) {
+                float S[10];
+#pragma unroll
+                for (int q = 0; q < 10; ++q) S[q] = (p2[q] + p1[q]) + p0[q];
+                const uint32_t bits = (mprev >> 2) & 0xffu;
+                float o[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) o[k] = pick(bits, k, ((S[k] + S[k + 1]) + S[k + 2]) * (1.f / 27.f));
+                if (outlane && valid) {
+                    const int orow = (s - 2) * 8 + (tj - 1);
+                    if (CHECK) sweep_check_row(g, own, orow, bits);
+                    float *op = y + (long long)own * 512 + orow * 8;
+                    stg4(op, o[0], o[1], o[2], o[3]);
+                    stg4(op + 4, o[4], o[5], o[6], o[7]);
+                    if (SUM) part += ((o[0] + o[1]) + (o[2] + o[3])) + ((o[4] + o[5]) + (o[6] + o[7]));
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 10; ++q) {
+                p2[q] = p1[q];
+                p1[q] = p0[q];
+            }
+            mprev = mb1;
+            // slide the plane window
+#pragma unroll
+            for (int q = 0; q < 12; ++q) {
+                xa[q] = xb[q];
+                xb[q] = xc[q];
+                xc[q] = xn[q];
+                ea[q] = eb[q];
+            }
+            ma = mb1;
+            mb1 = mc;
+            mc = mn;
+        }
+        (void)ma;
+        acc += (double)part;
+    }
+    if (SUM) {
+        acc = warp_sum(acc);
+        if (lane_id() == 0) s_red[threadIdx.x >> 5] = acc;
+        __syncthreads();
+        double tot = 0.0;
+        if (threadIdx.x == 0)
+            for (int w = 0; w < kSweepThreads / 32; ++w) tot += s_red[w];
+        finish_reduction(g, tot, sum_slot);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Single stencils with a 1-voxel halo.  Four leaves per warp: lanes 8*w + oj
+// own output column oj (region column oj + 1, always in the own leaf's j
+// range); the edge lanes oj = 0 / 7 also load region column 0 / 9 from the
+// j-1 / j+1 neighbour leaves.
+// ---------------------------------------------------------------------------
+enum { SW_DIFFUSE7 = 1, SW_BOX27 = 2 };
+
+template <int OP, bool CHECK, bool SUM>
+__global__ void __launch_bounds__(kSweepThreads) k_sweep_single(DevGrid g, int src, int dst, float coef, int sum_slot)
+{
+    __shared__ double s_red[kSweepThreads / 32];
+    const int n = g.ctrl->list_n;
+    const float *__restrict__ x = g.field[src];
+    float *__restrict__ y = g.field[dst];
+    const uint8_t *__restrict__ mb = reinterpret_cast<const uint8_t *>(g.mask);
+    const int lane = lane_id();
+    const int sub = lane >> 3;
+    const int oj = lane & 7;
+    const bool lo_edge = (oj == 0), hi_edge = (oj == 7);
+    const int edx = lo_edge ? 0 : 2;        // dj+1 of the edge lanes' outer column
+    const int lje = lo_edge ? 7 : 0;
+    const float c6 = 1.f - 6.f * coef;
+    const int warps_total = gridDim.x * (kSweepThreads / 32);
+    const int gw = blockIdx.x * (kSweepThreads / 32) + (threadIdx.x >> 5);
+    double acc = 0.0;
+
+    for (int e0 = gw * 4; e0 < n; e0 += warps_total * 4) {
+        const int e = e0 + sub;
+        const bool valid = e < n;
+        int sl[9], se[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            const long long base = (long long)e * 27 + (q / 3) * 9 + (q % 3);
+            sl[q] = valid ? __ldg(g.nbr + base + 3) : -1;
+            se[q] = (valid && (lo_edge || hi_edge)) ? __ldg(g.nbr + base + edx * 3) : -1;
+        }
+        const int own = sl[4];
+        float xa[10], xb[10], xc[10], xn[10], ea[10], eb[10], ec[10], en[10];
+#pragma unroll
+        for (int q = 0; q < 10; ++q) xn[q] = en[q] = 0.f;
+        row10(x, sl[0], sl[1], sl[2], plane_li<1>(0) * 8 + oj, xa);
+        row10(x, sl[3], sl[4], sl[5], plane_li<1>(1) * 8 + oj, xb);
+        row10(x, sl[3], sl[4], sl[5], plane_li<1>(2) * 8 + oj, xc);
+        row10(x, se[3], se[4], se[5], plane_li<1>(1) * 8 + lje, eb);
+        row10(x, se[3], se[4], se[5], plane_li<1>(2) * 8 + lje, ec);
+        if (OP == SW_BOX27) row10(x, se[0], se[1], se[2], plane_li<1>(0) * 8 + lje, ea);
+        float p1[10], p2[10];
+        float part = 0.f;
+        if (OP == SW_BOX27) {
+            // j-sums of planes 0 and 1
+            float up[10], dn[10];
+            shfl_row<10>(xa, up, dn);
+#pragma unroll
+            for (int q = 0; q < 10; ++q) p2[q] = ((lo_edge ? ea[q] : up[q]) + xa[q]) + (hi_edge ? ea[q] : dn[q]);
+            shfl_row<10>(xb, up, dn);
+#pragma unroll
+            for (int q = 0; q < 10; ++q) p1[q] = ((lo_edge ? eb[q] : up[q]) + xb[q]) + (hi_edge ? eb[q] : dn[q]);
+        }
+#pragma unroll
+        for (int oi = 0; oi < 8; ++oi) {
+            const uint32_t bits = valid ? __ldg(mb + (long long)own * 64 + oi * 8 + oj) : 0u;
+            float o[8];
+            if (OP == SW_DIFFUSE7) {
+                // prefetch plane oi+3, then t on plane oi+1 from planes oi, oi+1, oi+2
+                if (oi + 3 <= 9) {
+                    const int ri = oi + 3, dx = plane_di<1>(ri) * 3;
+                    row10(x, sl[dx], sl[dx + 1], sl[dx + 2], plane_li<1>(ri) * 8 + oj, xn);
+                    row10(x, se[dx], se[dx + 1], se[dx + 2], plane_li<1>(ri) * 8 + lje, en);
+                }
+                float up[10], dn[10];
+                shfl_row<10>(xb, up, dn);
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const int q = k + 1;
+                    const float jm = lo_edge ? eb[q] : up[q];
+                    const float jp = hi_edge ? eb[q] : dn[q];
+                    const float nb = ((xb[q - 1] + xb[q + 1]) + (xa[q] + xc[q])) + (jm + jp);
+                    o[k] = pick(bits, k, fmaf(coef, nb, c6 * xb[q]));
+                }
+#pragma unroll
+                for (int q = 0; q < 10; ++q) {
+                    xa[q] = xb[q];
+                    xb[q] = xc[q];
+                    xc[q] = xn[q];
+                    eb[q] = ec[q];
+                    ec[q] = en[q];
+                }
+            } else {
+                // prefetch plane oi+3; j-sum of plane oi+2; output plane oi
+                if (oi + 3 <= 9) {
+                    const int ri = oi + 3, dx = plane_di<1>(ri) * 3;
+                    row10(x, sl[dx], sl[dx + 1], sl[dx + 2], plane_li<1>(ri) * 8 + oj, xn);
+                    row10(x, se[dx], se[dx + 1], se[dx + 2], plane_li<1>(ri) * 8 + lje, en);
+                }
+                float up[10], dn[10], p0[10];
+                shfl_row<10>(xc, up, dn);
+#pragma unroll
+                for (int q = 0; q < 10; ++q) p0[q] = ((lo_edge ? ec[q] : up[q]) + xc[q]) + (hi_edge ? ec[q] : dn[q]);
+                float S[10];
+#pragma unroll
+                for (int q = 0; q < 10; ++q) S[q] = (p2[q] + p1[q]) + p0[q];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) o[k] = pick(bits, k, ((S[k] + S[k + 1]) + S[k + 2]) * (1.f / 27.f));
+#pragma unroll
+                for (int q = 0; q < 10; ++q) {
+                    p2[q] = p1[q];
+                    p1[q] = p0[q];
+                    xc[q] = xn[q];
+                    ec[q] = en[q];
+                }
+            }
+            if (valid) {
+                const int orow = oi * 8 + oj;
+                if (CHECK) sweep_check_row(g, own, orow, bits);
+                float *op = y + (long long)own * 512 + orow * 8;
+                stg4(op, o[0], o[1], o[2], o[3]);
+                stg4(op + 4, o[4], o[5], o[6], o[7]);
+                if (SUM) part += ((o[0] + o[1]) + (o[2] + o[3])) + ((o[4] + o[5]) + (o[6] + o[7]));
+            }
+        }
+        acc += (double)part;
+    }
+    if (SUM) {
+        acc = warp_sum(acc);
+        if (lane_id() == 0) s_red[threadIdx.x >> 5] = acc;
+        __syncthreads();
+        double tot = 0.0;
+        if (threadIdx.x == 0)
+            for (int w = 0; w < kSweepThreads / 32; ++w) tot += s_red[w];
+        finish_reduction(g, tot, sum_slot);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Launch wrappers
+// ---------------------------------------------------------------------------
+static int sweep_ctas(int num_sms, int which)
+{
+    static int cache[4] = {0, 0, 0, 0};
+    if (cache[which] == 0) {
+        int per = 1;
+        cudaError_t err;
+        if (which == 0)
+            err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sweep_diffuse_box<false, false, true>, kSweepThreads, 0);
+        else
+            err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sweep_single<SW_BOX27, false, true>, kSweepThreads, 0);
+        if (err != cudaSuccess || per < 1) per = 1;
+        cache[which] = per;
+    }
+    return cache[which] * num_sms;
+}
+
+void launch_sweep_diffuse_box(const DevGrid &g, cudaStream_t s, int src, int tmp, int dst, float coef, int store_tmp,
+                              int check_act, int sum_slot, const LaunchCfg &lc)
+{
+    const int ctas = sweep_ctas(lc.num_sms, 0);
+    const bool sum = sum_slot >= 0;
+#define SG_SW(ST, CK, SU) k_sweep_diffuse_box<ST, CK, SU><<<ctas, kSweepThreads, 0, s>>>(g, src, tmp, dst, coef, sum_slot)
+    if (store_tmp) {
+        if (check_act) { if (sum) SG_SW(true, true, true); else SG_SW(true, true, false); }
+        else { if (sum) SG_SW(true, false, true); else SG_SW(true, false, false); }
+    } else {
+        if (check_act) { if (sum) SG_SW(false, true, true); else SG_SW(false, true, false); }
+        else { if (sum) SG_SW(false, false, true); else SG_SW(false, false, false); }
+    }
+#undef SG_SW
+}
+
+void launch_sweep_single(const DevGrid &g, cudaStream_t s, int op, int src, int dst, float coef, int check_act,
+                         int sum_slot, const LaunchCfg &lc)
+{
+    const int ctas = sweep_ctas(lc.num_sms, 1);
+    const bool sum = sum_slot >= 0;
+#define SG_SS(OP, CK, SU) k_sweep_single<OP, CK, SU><<<ctas, kSweepThreads, 0, s>>>(g, src, dst, coef, sum_slot)
+    if (op == SW_DIFFUSE7) {
+        if (check_act) { if (sum) SG_SS(SW_DIFFUSE7, true, true); else SG_SS(SW_DIFFUSE7, true, false); }
+        else { if (sum) SG_SS(SW_DIFFUSE7, false, true); else SG_SS(SW_DIFFUSE7, false, false); }
+    } else {
+        if (check_act) { if (sum) SG_SS(SW_BOX27, true, true); else SG_SS(SW_BOX27, true, false); }
+        else { if (sum) SG_SS(SW_BOX27, false, true); else SG_SS(SW_BOX27, false, false); }
+    }
+#undef SG_SS
+}
+
+}  // namespace sg

@@ -18,7 +18,7 @@ def rel_linf(got, ref) -> float:
     return float(np.max(np.abs(got - ref))) / scale
 
 
-def shell_pair(spec, n_fields=3, opts=None, scratch_mask=0, max_sums=128, max_leaves=None):
+def shell_pair(spec, n_fields=3, opts=None, scratch_mask=0, max_sums=128, max_leaves=None, variant=None):
     """A GPU grid and an oracle grid activated with the same shell, their
     structures checked identical, field 0 set from the seeded generator."""
     import paper_2012_08141_gb300 as sg
@@ -31,6 +31,8 @@ def shell_pair(spec, n_fields=3, opts=None, scratch_mask=0, max_sums=128, max_le
                 scratch_mask=scratch_mask)
     if opts is not None:
         g.set_opts(opts)
+    if variant is not None:
+        g.set_stencil_variant(variant)
     g.activate_shell(spec.lo2, spec.hi2, spec.lo_strict)
     g.list_gen()
     gb, gm = g.read_structure()

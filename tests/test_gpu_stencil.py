@@ -44,11 +44,12 @@ OPTS = {
 # 64^3 shell, 20 steps of activate -> list -> diffuse7 -> swap
 # ---------------------------------------------------------------------------
 
+@pytest.mark.parametrize("variant", [0, 1])
 @pytest.mark.parametrize("mode", list(OPTS))
 @pytest.mark.parametrize("seed", [0, 5])
-def test_tiny_shell_20_steps(mode, seed):
+def test_tiny_shell_20_steps(mode, seed, variant):
     spec = tiny_shell(seed)
-    g, og = shell_pair(spec, n_fields=2, opts=OPTS[mode])
+    g, og = shell_pair(spec, n_fields=2, opts=OPTS[mode], variant=variant)
     ob, om = og.structure()
     cur, oth = 0, 1
     for _ in range(20):
@@ -90,11 +91,12 @@ def run_band(g, og, steps, slot0=0):
     return cur, np.array(sums_ref)
 
 
+@pytest.mark.parametrize("variant", [0, 1])
 @pytest.mark.parametrize("mode", list(OPTS))
-def test_band_128_100_steps(mode):
+def test_band_128_100_steps(mode, variant):
     lo2, hi2 = band_bounds(40.0, 56.0)
     spec = ShellSpec(128, 8, lo2, hi2, True, 3)
-    g, og = shell_pair(spec, n_fields=3, opts=OPTS[mode], scratch_mask=0b010)
+    g, og = shell_pair(spec, n_fields=3, opts=OPTS[mode], scratch_mask=0b010, variant=variant)
     cur, sums_ref = run_band(g, og, 100)
     sums = g.read_sums(100)
     assert np.max(np.abs(sums - sums_ref) / np.abs(sums_ref)) <= TOL
@@ -175,8 +177,8 @@ def test_empty_grid():
 def test_ragged_domains(N, r0, r1, strict):
     lo2, hi2 = band_bounds(r0, r1)
     spec = ShellSpec(N, 8, lo2, hi2, strict, 11)
-    for mode in ("fused", "eager"):
-        g, og = shell_pair(spec, n_fields=3, opts=OPTS[mode], scratch_mask=0b010)
+    for mode, variant in [("fused", 0), ("eager", 0), ("fused", 1), ("eager", 1)]:
+        g, og = shell_pair(spec, n_fields=3, opts=OPTS[mode], scratch_mask=0b010, variant=variant)
         cur, sums_ref = run_band(g, og, 7)
         assert rel_linf(g.read_field(0), og.read_field(cur)) <= TOL
         sums = g.read_sums(7)
@@ -187,8 +189,8 @@ def test_ragged_domains(N, r0, r1, strict):
 def test_full_domain_boundary_reads_zero():
     """Every voxel active: out-of-domain neighbours read 0 at all six faces."""
     spec = ShellSpec(24, 8, 0, 10 ** 9, False, 2)
-    for mode in ("fused", "eager"):
-        g, og = shell_pair(spec, n_fields=3, opts=OPTS[mode])
+    for mode, variant in [("fused", 0), ("eager", 0), ("fused", 1), ("eager", 1)]:
+        g, og = shell_pair(spec, n_fields=3, opts=OPTS[mode], variant=variant)
         cur, _ = run_band(g, og, 5)
         assert rel_linf(g.read_field(0), og.read_field(cur)) <= TOL
         g.close()
