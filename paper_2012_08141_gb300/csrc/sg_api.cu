@@ -86,6 +86,7 @@ struct sg_grid {
     unsigned long long mask_ver = 1, list_ver = 0;
     std::set<std::tuple<long long, long long, int>> applied_shells;
     unsigned long long lg_calls = 0;
+    unsigned long long rmask_ver = 0;  // list version the region masks were built from (0 = never)
     long long known_leaves = 0;
     sg_stats stats{};
     int latched = SG_OK;
@@ -240,6 +241,12 @@ int run_struct_for_group(sg_grid *g, size_t &i)
         const size_t after = i + (with_sum ? 3 : 2);
         const bool store_t = !(dse && a.dst_scratch && !read_later(g, after, a.dst));
         if (!store_t) g->stats.stores_removed++;
+        if (g->lc.variant == kVariantSweep && g->rmask_ver != g->list_ver) {
+            // region masks are derived from the structure, cached with the list
+            if (!g->dry) launch_region_masks(g->dev, g->stream, g->lc);
+            if ((rc = after_launch(g, "region masks"))) return rc;
+            g->rmask_ver = g->list_ver;
+        }
         if (!g->dry)
             launch_diffuse_box(g->dev, g->stream, a.src, a.dst, b->dst, a.coef, store_t ? 1 : 0, check,
                                with_sum ? (int)c->slot : -1, g->lc);
@@ -460,10 +467,11 @@ int sg_create(const sg_desc *desc, void *cuda_stream, sg_grid **out)
     const int max_ctas = 8192;
     struct Need { void **dst; size_t bytes; } needs[] = {
         {(void **)&d.root, sizeof(int32_t) * nr},
-        {(void **)&d.mask, sizeof(uint32_t) * d.W * d.cap},
+        {(void **)&d.mask, sizeof(uint32_t) * d.W * (d.cap + 1)},
         {(void **)&d.list_slot, sizeof(int32_t) * d.cap},
         {(void **)&d.list_b, sizeof(int32_t) * d.cap},
         {(void **)&d.nbr, sizeof(int32_t) * 27 * d.cap},
+        {(void **)&d.rmask, (L == 8 ? sizeof(uint32_t) * 40 : size_t(4)) * d.cap},
         {(void **)&d.need, (size_t)nr},
         {(void **)&d.tile_status, sizeof(unsigned long long) * g->num_tiles},
         {(void **)&d.partials, sizeof(double) * max_ctas},
@@ -479,7 +487,7 @@ int sg_create(const sg_desc *desc, void *cuda_stream, sg_grid **out)
         }
     }
     for (int f = 0; f < d.F; ++f) {
-        d.field[f] = (float *)dev_alloc(g, sizeof(float) * V * d.cap);
+        d.field[f] = (float *)dev_alloc(g, sizeof(float) * V * (d.cap + 1));
         if (!d.field[f]) {
             dev_free_all(g);
             delete g;
@@ -498,6 +506,10 @@ int sg_create(const sg_desc *desc, void *cuda_stream, sg_grid **out)
     if (!rc) rc = cuda_check(cudaMemsetAsync(d.need, 0, (size_t)nr, s), "init need");
     if (!rc) rc = cuda_check(cudaMemsetAsync(d.tile_status, 0, sizeof(unsigned long long) * g->num_tiles, s), "init status");
     if (!rc) rc = cuda_check(cudaMemsetAsync(d.sums, 0, sizeof(double) * std::max(1, desc->max_sums), s), "init sums");
+    // the zero leaf (slot cap): never allocated, read in place of null neighbours
+    if (!rc) rc = cuda_check(cudaMemsetAsync(d.mask + d.W * d.cap, 0, sizeof(uint32_t) * d.W, s), "init zero leaf");
+    for (int f = 0; f < d.F && !rc; ++f)
+        rc = cuda_check(cudaMemsetAsync(d.field[f] + V * d.cap, 0, sizeof(float) * V, s), "init zero leaf");
     if (!rc) {
         Ctrl c{};
         c.dirty = 1;

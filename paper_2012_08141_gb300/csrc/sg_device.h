@@ -8,8 +8,11 @@
 //                                each leaf a contiguous 2 KB (L=8) block
 //   list_slot[cap], list_b[cap]  the active-leaf list, ascending b
 //   nbr[cap][27]         int32   slots of the 3x3x3 leaf neighbourhood of each
-//                                list entry (index (di+1)*9+(dj+1)*3+(dk+1)),
-//                                -1 = null or outside the domain
+//                                list entry (index (di+1)*9+(dj+1)*3+(dk+1));
+//                                a null or out-of-domain neighbour is slot
+//                                `cap`, the zero leaf: field and mask arrays
+//                                hold cap + 1 leaves and leaf `cap` is never
+//                                allocated, so it reads as zeros everywhere
 //   need[R^3]            uint8   activation requests (coords / particles)
 //   tile_status[tiles]   uint64  list-compaction look-back words
 //   partials[max_ctas]   double  per-CTA reduction partials
@@ -52,6 +55,7 @@ struct DevGrid {
     int32_t *list_slot;
     int32_t *list_b;
     int32_t *nbr;
+    uint32_t *rmask;     // [cap][10][4]: region masks of the fused kernel, see launch_region_masks
     uint8_t *need;
     unsigned long long *tile_status;
     double *partials;
@@ -85,6 +89,11 @@ void launch_alloc_needed(const DevGrid &g, cudaStream_t s);
 void launch_setbits_coords(const DevGrid &g, cudaStream_t s, const int32_t *xyz, long long n);
 void launch_deactivate_all(const DevGrid &g, cudaStream_t s);
 void launch_clear_list(const DevGrid &g, cudaStream_t s);
+// For each list entry (8^3 leaves) and each of the 10 columns tj of the
+// 10^3 region around the leaf, the activity bits of the 10 rows ti = 0..9 of
+// that column: row (ti, tj) covers region voxels (ti+1, tj+1, r+1), r = 0..9,
+// as 10 bits; rows 3w..3w+2 are packed into word w of rmask[e][tj][0..3].
+void launch_region_masks(const DevGrid &g, cudaStream_t s, const LaunchCfg &lc);
 void launch_listgen(const DevGrid &g, cudaStream_t s, int force, unsigned long long call_idx,
                     int num_tiles, int test_wait);
 void launch_gather_field(const DevGrid &g, cudaStream_t s, int f, const LaunchCfg &lc);

@@ -368,7 +368,7 @@ __global__ void __launch_bounds__(kListThreads) k_listgen(DevGrid g, int force, 
             int v = -1;
             if ((unsigned)bi < (unsigned)R && (unsigned)bj < (unsigned)R && (unsigned)bk < (unsigned)R)
                 v = g.root[((long long)bi * R + bj) * R + bk];
-            g.nbr[(long long)(prefix + e) * 27 + q] = v;
+            g.nbr[(long long)(prefix + e) * 27 + q] = (v < 0) ? (int)g.cap : v;  // null -> the zero leaf
         }
     }
     if (test_wait && tile == 0 && tid == 0) {
@@ -395,6 +395,46 @@ void launch_listgen(const DevGrid &g, cudaStream_t s, int force, unsigned long l
                     int test_wait)
 {
     k_listgen<<<num_tiles, kListThreads, 0, s>>>(g, force, call_idx, num_tiles, test_wait);
+}
+
+// ---------------------------------------------------------------------------
+// Region masks of 8^3 leaves (the fused diffuse->box kernel's t activity):
+// one thread per (list entry, region column tj, word w) gathers rows
+// ti = 3w..3w+2 of column tj; region row (ri, rj) = (ti+1, tj+1) takes its
+// bit for k = 1 from the k-1 leaf (local k 7), k = 2..9 from its own leaf
+// column and k = 10 from the k+1 leaf (local k 0), via the 27-neighbour
+// table (null neighbours are the zero leaf, whose mask is 0).
+// ---------------------------------------------------------------------------
+__global__ void k_region_masks(DevGrid g)
+{
+    const long long n = g.ctrl->list_n;
+    const uint8_t *mb = reinterpret_cast<const uint8_t *>(g.mask);
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n * 40; q += (long long)gridDim.x * blockDim.x) {
+        const long long e = q / 40;
+        const int tj = (int)(q % 40) / 4, w = (int)(q % 4);
+        const int rj = tj + 1;
+        const int djx = (rj < 2) ? 0 : (rj < 10 ? 1 : 2), lj = (rj - 2) & 7;
+        uint32_t word = 0;
+        for (int u = 0; u < 3; ++u) {
+            const int ti = 3 * w + u;
+            if (ti > 9) break;
+            const int ri = ti + 1;
+            const int dix = (ri < 2) ? 0 : (ri < 10 ? 1 : 2), li = (ri - 2) & 7;
+            const int *nb = g.nbr + e * 27 + dix * 9 + djx * 3;
+            const int ro = li * 8 + lj;
+            const uint32_t m0 = mb[(long long)nb[0] * 64 + ro];
+            const uint32_t m1 = mb[(long long)nb[1] * 64 + ro];
+            const uint32_t m2 = mb[(long long)nb[2] * 64 + ro];
+            const uint32_t bits = ((m0 >> 7) & 1u) | (m1 << 1) | ((m2 & 1u) << 9);
+            word |= bits << (10 * u);
+        }
+        g.rmask[e * 40 + tj * 4 + w] = word;
+    }
+}
+
+void launch_region_masks(const DevGrid &g, cudaStream_t s, const LaunchCfg &lc)
+{
+    k_region_masks<<<lc.num_sms * 4, 256, 0, s>>>(g);
 }
 
 // ---------------------------------------------------------------------------

@@ -14,9 +14,10 @@
 //   - the 3x3x3 box sum is separable: a j-sum by shuffle, an i-sum over a
 //     sliding window of the last three planes, a k-sum inside the row.
 // A row of the 12^3 (fused) or 10^3 (single) region is gathered from the
-// three leaves (dk = -1, 0, +1) of its column via the 27-neighbour table;
-// a null neighbour reads as zeros, as does an inactive voxel (the stored
-// value there is 0).
+// three leaves (dk = -1, 0, +1) of its column via the 27-neighbour table,
+// the own leaf's 8 floats in one 256-bit load.  A null neighbour is the zero
+// leaf, so every load is unconditional; an inactive voxel reads 0 because
+// the stored value there is 0.
 #include "sg_common.cuh"
 
 namespace sg {
@@ -51,62 +52,45 @@ __device__ __forceinline__ void sweep_check_row(const DevGrid &g, int slot, int 
 //        used by the 1-voxel-halo single stencils.
 // `ro` = (li*8 + lj) is the row index inside a leaf.
 // ---------------------------------------------------------------------------
+// One 32-byte aligned leaf row (8 floats) in a single 256-bit load.
+__device__ __forceinline__ void ldg8(const float *p, float (&v)[8])
+{
+    asm volatile("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
+                 : "l"(p));
+}
+
+// Slots s0, s1, s2 are always valid: a null neighbour is the zero leaf.
+__device__ __forceinline__ void row12v(const float *__restrict__ x, int s0, int s1, int s2, int ro, float (&v)[12])
+{
+    const float2 a = ldg2s(x + (long long)s0 * 512 + ro * 8 + 6);
+    float c[8];
+    ldg8(x + (long long)s1 * 512 + ro * 8, c);
+    const float2 b = ldg2s(x + (long long)s2 * 512 + ro * 8);
+    v[0] = a.x; v[1] = a.y;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q + 2] = c[q];
+    v[10] = b.x; v[11] = b.y;
+}
+
 __device__ __forceinline__ void row12(const float *__restrict__ x, const uint8_t *__restrict__ mb, int s0, int s1,
                                       int s2, int ro, float (&v)[12], uint32_t &m)
 {
-    float2 a = make_float2(0.f, 0.f), b = a;
-    float4 c0 = make_float4(0.f, 0.f, 0.f, 0.f), c1 = c0;
-    uint32_t m0 = 0, m1 = 0, m2 = 0;
-    if (s0 >= 0) {
-        a = ldg2s(x + (long long)s0 * 512 + ro * 8 + 6);
-        m0 = __ldg(mb + (long long)s0 * 64 + ro);
-    }
-    if (s1 >= 0) {
-        c0 = ldg4s(x + (long long)s1 * 512 + ro * 8);
-        c1 = ldg4s(x + (long long)s1 * 512 + ro * 8 + 4);
-        m1 = __ldg(mb + (long long)s1 * 64 + ro);
-    }
-    if (s2 >= 0) {
-        b = ldg2s(x + (long long)s2 * 512 + ro * 8);
-        m2 = __ldg(mb + (long long)s2 * 64 + ro);
-    }
-    v[0] = a.x; v[1] = a.y;
-    v[2] = c0.x; v[3] = c0.y; v[4] = c0.z; v[5] = c0.w;
-    v[6] = c1.x; v[7] = c1.y; v[8] = c1.z; v[9] = c1.w;
-    v[10] = b.x; v[11] = b.y;
+    row12v(x, s0, s1, s2, ro, v);
+    const uint32_t m0 = __ldg(mb + (long long)s0 * 64 + ro);
+    const uint32_t m1 = __ldg(mb + (long long)s1 * 64 + ro);
+    const uint32_t m2 = __ldg(mb + (long long)s2 * 64 + ro);
     m = (m0 >> 6) | (m1 << 2) | ((m2 & 3u) << 10);
-}
-
-__device__ __forceinline__ void row12v(const float *__restrict__ x, int s0, int s1, int s2, int ro, float (&v)[12])
-{
-    float2 a = make_float2(0.f, 0.f), b = a;
-    float4 c0 = make_float4(0.f, 0.f, 0.f, 0.f), c1 = c0;
-    if (s0 >= 0) a = ldg2s(x + (long long)s0 * 512 + ro * 8 + 6);
-    if (s1 >= 0) {
-        c0 = ldg4s(x + (long long)s1 * 512 + ro * 8);
-        c1 = ldg4s(x + (long long)s1 * 512 + ro * 8 + 4);
-    }
-    if (s2 >= 0) b = ldg2s(x + (long long)s2 * 512 + ro * 8);
-    v[0] = a.x; v[1] = a.y;
-    v[2] = c0.x; v[3] = c0.y; v[4] = c0.z; v[5] = c0.w;
-    v[6] = c1.x; v[7] = c1.y; v[8] = c1.z; v[9] = c1.w;
-    v[10] = b.x; v[11] = b.y;
 }
 
 __device__ __forceinline__ void row10(const float *__restrict__ x, int s0, int s1, int s2, int ro, float (&v)[10])
 {
-    float a = 0.f, b = 0.f;
-    float4 c0 = make_float4(0.f, 0.f, 0.f, 0.f), c1 = c0;
-    if (s0 >= 0) a = __ldg(x + (long long)s0 * 512 + ro * 8 + 7);
-    if (s1 >= 0) {
-        c0 = ldg4s(x + (long long)s1 * 512 + ro * 8);
-        c1 = ldg4s(x + (long long)s1 * 512 + ro * 8 + 4);
-    }
-    if (s2 >= 0) b = __ldg(x + (long long)s2 * 512 + ro * 8);
-    v[0] = a;
-    v[1] = c0.x; v[2] = c0.y; v[3] = c0.z; v[4] = c0.w;
-    v[5] = c1.x; v[6] = c1.y; v[7] = c1.z; v[8] = c1.w;
-    v[9] = b;
+    v[0] = __ldg(x + (long long)s0 * 512 + ro * 8 + 7);
+    float c[8];
+    ldg8(x + (long long)s1 * 512 + ro * 8, c);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q + 1] = c[q];
+    v[9] = __ldg(x + (long long)s2 * 512 + ro * 8);
 }
 
 template <int N>
@@ -134,7 +118,7 @@ __device__ __forceinline__ constexpr int plane_li(int ri) { return (ri - H) & 7;
 // its j-sums P, and once three P planes exist writes output plane s - 2.
 // ---------------------------------------------------------------------------
 template <bool STORE_T, bool CHECK, bool SUM>
-__global__ void __launch_bounds__(kSweepThreads) k_sweep_diffuse_box(DevGrid g, int src, int tmp, int dst, float coef,
+__global__ void __launch_bounds__(kSweepThreads, 3) k_sweep_diffuse_box(DevGrid g, int src, int tmp, int dst, float coef,
                                                                        int sum_slot)
 {
     __shared__ double s_red[kSweepThreads / 32];
@@ -142,7 +126,6 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep_diffuse_box(DevGrid g, 
     const float *__restrict__ x = g.field[src];
     float *__restrict__ y = g.field[dst];
     float *__restrict__ tout = g.field[tmp];
-    const uint8_t *__restrict__ mb = reinterpret_cast<const uint8_t *>(g.mask);
     const int lane = lane_id();
     const int sub = lane / 10;
     const int tj = lane - sub * 10;
@@ -153,6 +136,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep_diffuse_box(DevGrid g, 
     const bool lo_edge = (tj == 0), hi_edge = (tj == 9);
     const bool outlane = (tj >= 1 && tj <= 8);
     const float c6 = 1.f - 6.f * coef;
+    const int Z = (int)g.cap;  // the zero leaf
     const int warps_total = gridDim.x * (kSweepThreads / 32);
     const int gw = blockIdx.x * (kSweepThreads / 32) + (threadIdx.x >> 5);
     double acc = 0.0;
@@ -162,26 +146,21 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep_diffuse_box(DevGrid g, 
         const bool valid = (sub < 3) && (e < n);
         int sl[9];
 #pragma unroll
-        for (int q = 0; q < 9; ++q) sl[q] = valid ? __ldg(g.nbr + (long long)e * 27 + (q / 3) * 9 + djx * 3 + (q % 3)) : -1;
+        for (int q = 0; q < 9; ++q) sl[q] = valid ? __ldg(g.nbr + (long long)e * 27 + (q / 3) * 9 + djx * 3 + (q % 3)) : Z;
         const int own = sl[4];
+        const bool edge = lo_edge || hi_edge;
+        // activity bits of this lane's t-region column, 10 rows x 10 bits
+        uint4 rm = make_uint4(0u, 0u, 0u, 0u);
+        if (valid) rm = __ldg(reinterpret_cast<const uint4 *>(g.rmask + (long long)e * 40 + tj * 4));
+        const uint32_t rmw[4] = {rm.x, rm.y, rm.z, rm.w};
         float xa[12], xb[12], xc[12], xn[12], ea[12], eb[12];
-        uint32_t ma, mb1, mc, mn = 0;
 #pragma unroll
         for (int q = 0; q < 12; ++q) xn[q] = 0.f;
         // planes 0, 1, 2 and the edge rows of plane 1
-        row12(x, mb, sl[0], sl[1], sl[2], plane_li<2>(0) * 8 + lj, xa, ma);
-        row12(x, mb, sl[0], sl[1], sl[2], plane_li<2>(1) * 8 + lj, xb, mb1);
-        row12(x, mb, sl[3], sl[4], sl[5], plane_li<2>(2) * 8 + lj, xc, mc);
-        {
-            float z[12];
-            if (lo_edge || hi_edge) row12v(x, sl[0], sl[1], sl[2], plane_li<2>(1) * 8 + lje, z);
-            else {
-#pragma unroll
-                for (int q = 0; q < 12; ++q) z[q] = 0.f;
-            }
-#pragma unroll
-            for (int q = 0; q < 12; ++q) ea[q] = z[q];
-        }
+        row12v(x, sl[0], sl[1], sl[2], plane_li<2>(0) * 8 + lj, xa);
+        row12v(x, sl[0], sl[1], sl[2], plane_li<2>(1) * 8 + lj, xb);
+        row12v(x, sl[3], sl[4], sl[5], plane_li<2>(2) * 8 + lj, xc);
+        row12v(x, edge ? sl[0] : Z, edge ? sl[1] : Z, edge ? sl[2] : Z, plane_li<2>(1) * 8 + lje, ea);
         float p1[10], p2[10];
         uint32_t mprev = 0;
         float part = 0.f;
@@ -190,16 +169,13 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep_diffuse_box(DevGrid g, 
             // prefetch plane s+3 (centre row) and the edge row of plane s+2
             if (s + 3 <= 11) {
                 const int ri = s + 3, dx = plane_di<2>(ri) * 3;
-                row12(x, mb, sl[dx], sl[dx + 1], sl[dx + 2], plane_li<2>(ri) * 8 + lj, xn, mn);
+                row12v(x, sl[dx], sl[dx + 1], sl[dx + 2], plane_li<2>(ri) * 8 + lj, xn);
             }
             {
                 const int ri = s + 2, dx = plane_di<2>(ri) * 3;
-                if (lo_edge || hi_edge) row12v(x, sl[dx], sl[dx + 1], sl[dx + 2], plane_li<2>(ri) * 8 + lje, eb);
-                else {
-#pragma unroll
-                    for (int q = 0; q < 12; ++q) eb[q] = 0.f;
-                }
+                row12v(x, edge ? sl[dx] : Z, edge ? sl[dx + 1] : Z, edge ? sl[dx + 2] : Z, plane_li<2>(ri) * 8 + lje, eb);
             }
+            const uint32_t mt = (rmw[s / 3] >> (10 * (s % 3))) & 0x3ffu;  // t row bits, bit q <-> t[q]
             // t on region plane s+1 (centre xb, i-1 xa, i+1 xc)
             float up[12], dn[12];
             shfl_row<12>(xb, up, dn);
@@ -209,11 +185,11 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep_diffuse_box(DevGrid g, 
                 const float jm = lo_edge ? ea[q + 1] : up[q + 1];
                 const float jp = hi_edge ? ea[q + 1] : dn[q + 1];
                 const float nb = ((xb[q] + xb[q + 2]) + (xa[q + 1] + xc[q + 1])) + (jm + jp);
-                t[q] = pick(mb1, q + 1, fmaf(coef, nb, c6 * xb[q + 1]));
+                t[q] = pick(mt, q, fmaf(coef, nb, c6 * xb[q + 1]));
             }
             if (STORE_T && s >= 1 && s <= 8 && outlane && valid) {
                 const int orow = (s - 1) * 8 + (tj - 1);
-                if (CHECK) sweep_check_row(g, own, orow, (mb1 >> 2) & 0xffu);
+                if (CHECK) sweep_check_row(g, own, orow, (mt >> 1) & 0xffu);
                 float *o = tout + (long long)own * 512 + orow * 8;
                 stg4(o, t[1], t[2], t[3], t[4]);
                 stg4(o + 4, t[5], t[6], t[7], t[8]);
@@ -231,7 +207,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep_diffuse_box(DevGrid g, 
                 float S[10];
 #pragma unroll
                 for (int q = 0; q < 10; ++q) S[q] = (p2[q] + p1[q]) + p0[q];
-                const uint32_t bits = (mprev >> 2) & 0xffu;
+                const uint32_t bits = (mprev >> 1) & 0xffu;  // own voxels of t row s-1
                 float o[8];
 #pragma unroll
                 for (int k = 0; k < 8; ++k) o[k] = pick(bits, k, ((S[k] + S[k + 1]) + S[k + 2]) * (1.f / 27.f));
@@ -249,7 +225,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep_diffuse_box(DevGrid g, 
                 p2[q] = p1[q];
                 p1[q] = p0[q];
             }
-            mprev = mb1;
+            mprev = mt;
             // slide the plane window
 #pragma unroll
             for (int q = 0; q < 12; ++q) {
@@ -258,11 +234,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep_diffuse_box(DevGrid g, 
                 xc[q] = xn[q];
                 ea[q] = eb[q];
             }
-            ma = mb1;
-            mb1 = mc;
-            mc = mn;
         }
-        (void)ma;
         acc += (double)part;
     }
     if (SUM) {
@@ -285,7 +257,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep_diffuse_box(DevGrid g, 
 enum { SW_DIFFUSE7 = 1, SW_BOX27 = 2 };
 
 template <int OP, bool CHECK, bool SUM>
-__global__ void __launch_bounds__(kSweepThreads) k_sweep_single(DevGrid g, int src, int dst, float coef, int sum_slot)
+__global__ void __launch_bounds__(kSweepThreads, 3) k_sweep_single(DevGrid g, int src, int dst, float coef, int sum_slot)
 {
     __shared__ double s_red[kSweepThreads / 32];
     const int n = g.ctrl->list_n;
@@ -299,6 +271,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep_single(DevGrid g, int s
     const int edx = lo_edge ? 0 : 2;        // dj+1 of the edge lanes' outer column
     const int lje = lo_edge ? 7 : 0;
     const float c6 = 1.f - 6.f * coef;
+    const int Z = (int)g.cap;  // the zero leaf
     const int warps_total = gridDim.x * (kSweepThreads / 32);
     const int gw = blockIdx.x * (kSweepThreads / 32) + (threadIdx.x >> 5);
     double acc = 0.0;
@@ -310,8 +283,8 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep_single(DevGrid g, int s
 #pragma unroll
         for (int q = 0; q < 9; ++q) {
             const long long base = (long long)e * 27 + (q / 3) * 9 + (q % 3);
-            sl[q] = valid ? __ldg(g.nbr + base + 3) : -1;
-            se[q] = (valid && (lo_edge || hi_edge)) ? __ldg(g.nbr + base + edx * 3) : -1;
+            sl[q] = valid ? __ldg(g.nbr + base + 3) : Z;
+            se[q] = (valid && (lo_edge || hi_edge)) ? __ldg(g.nbr + base + edx * 3) : Z;
         }
         const int own = sl[4];
         float xa[10], xb[10], xc[10], xn[10], ea[10], eb[10], ec[10], en[10];
