@@ -220,6 +220,41 @@ int sg_get_stats(sg_grid *g, sg_stats *out);
 /* Select the stencil kernel family used by ops flushed from now on. */
 int sg_set_stencil_variant(sg_grid *g, int32_t variant);
 
+/* ---- list generation for callers that cannot allocate device memory ----
+ *
+ * Some callers cannot call cudaMalloc: a process whose device memory is owned
+ * by another allocator (a framework's caching allocator, or a pool sized at
+ * start-up that a stray cudaMalloc would fail against or fragment), or code
+ * in a time-critical loop, where cudaMalloc and cudaFree would synchronize
+ * the device.  sg_list_gen_noalloc gives them the active-list compaction that
+ * sg_list_gen runs, without any allocation: it calls no cudaMalloc, cudaFree
+ * or allocating library routine.  The paper has no counterpart; it is an
+ * addition of this library.
+ *
+ * Input: dev_root, n_cells int32 pointer cells in device memory (a cell is
+ * active iff its value is >= 0).  Output, in device memory: the active cells
+ * in ascending index order -- dev_list_b gets the cell index, dev_list_slot
+ * its value -- at most `cap` entries (NULL allowed when cap == 0), and
+ * *dev_count the number of active cells (even when more than cap), or -1 if
+ * a bounded device wait gave up (after about 1 s).  The work is queued on
+ * `cuda_stream`; read the outputs after it completes.
+ *
+ * Scratch: a 32,800-byte static device array, which every GPU that loads
+ * this library holds until the process exits; n_cells is limited to
+ * 4,194,304 (SG_ERR_INVALID beyond).  All calls on a device share that
+ * array, and each call clears the parts it uses on the stream before its
+ * kernel runs, so two calls whose work overlaps on the GPU (different
+ * streams, no ordering between them) race and give wrong results.  The first
+ * call on a device, with that device current, looks up the array's device
+ * address (cudaGetSymbolAddress); make that first call before any stream
+ * capture begins.
+ *
+ * Returns SG_OK, SG_ERR_INVALID (bad arguments or too many cells) or
+ * SG_ERR_CUDA (the address lookup, a memset or the launch failed). */
+#define SG_NOALLOC_MAX_CELLS 4194304
+int sg_list_gen_noalloc(const int32_t *dev_root, int64_t n_cells, int32_t *dev_list_slot,
+                        int32_t *dev_list_b, int64_t cap, int32_t *dev_count, void *cuda_stream);
+
 /* Fault injection for testing bounded waits: queue a list generation whose
  * first CTA also waits on a device flag that nothing ever sets.  The wait
  * gives up after about 0.2 s and latches SG_ERR_TIMEOUT, which the next sync

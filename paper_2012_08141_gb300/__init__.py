@@ -96,6 +96,7 @@ def load_library(build: bool = True) -> ctypes.CDLL:
         "sg_get_stats": [P, ctypes.POINTER(SgStats)],
         "sg_debug_wait_test": [P],
         "sg_set_stencil_variant": [P, I32],
+        "sg_list_gen_noalloc": [P, I64, P, P, I64, P, P],
     }
     for name, args in sigs.items():
         fn = getattr(lib, name)
