@@ -220,6 +220,111 @@ int sg_get_stats(sg_grid *g, sg_stats *out);
 /* Select the stencil kernel family used by ops flushed from now on. */
 int sg_set_stencil_variant(sg_grid *g, int32_t variant);
 
+/* Implicit sync, then the number of active voxels of the listed leaves. */
+int sg_num_active(sg_grid *g, int64_t *n_active);
+
+/* Queue: set field f at every active voxel (i,j,k) to the uniform [0,1)
+ * value top24(splitmix64(seed * 2^40 + (i*N + j)*N + k)) * 2^-24 (the
+ * splitmix64 output function of Steele, Lea & Flood 2014), and to 0 at
+ * inactive voxels.  0 <= seed < 2^24.  Gives device-side initial values
+ * identical to the ones a host generator with the same definition uploads. */
+int sg_fill_hash(sg_grid *g, int32_t f, int64_t seed);
+
+/* ---- batched stepping: many grids, one persistent launch per step ----
+ *
+ * A batch binds n (1..1024) live grids with 8^3 leaves.  Each sg_batch_step
+ * runs, for every grid, the fused step dst = box27(diffuse7(src, coef)) with
+ * the per-grid sum of dst accumulated, as ONE kernel launch over the
+ * concatenated leaf lists of all grids (a persistent kernel whose warps
+ * stride over leaf triples), then exchanges src and dst in every grid (as
+ * sg_swap).  The intermediate field tmp is not stored (every grid's tmp is
+ * treated as scratch).  Steps are captured as CUDA graphs (one per src/dst
+ * parity) unless disabled.  Results equal stepping each grid alone up to
+ * FP32 rounding order (the fused kernel body is the same).
+ *
+ * sg_batch_create flushes every grid, makes its list, neighbour table and
+ * region masks current, and synchronizes; the structure of the grids must
+ * not change while the batch exists, and between batch steps the grids
+ * must not be used except for reads (which synchronize).  All work runs on
+ * cuda_stream.  Descriptor memory comes from grid 0's allocator and is
+ * released with grid 0. */
+typedef struct sg_batch sg_batch;
+int sg_batch_create(sg_grid *const *grids, int32_t n, int32_t src, int32_t tmp, int32_t dst, float coef,
+                    void *cuda_stream, sg_batch **out);
+/* Enqueue one batched step (no host wait). */
+int sg_batch_step(sg_batch *b);
+/* Wait, then copy the n first grids' sums of the last step to host memory. */
+int sg_batch_read_sums(sg_batch *b, double *host, int32_t n);
+/* Warps per CTA of the persistent kernel (2, 4 or 8: 6, 12 or 24 leaves per
+ * CTA) and whether steps run as captured CUDA graphs. */
+int sg_batch_set(sg_batch *b, int32_t warps_per_cta, int32_t use_graph);
+/* Autotuner: time trial_steps steps with each warps-per-CTA choice (these are
+ * real steps: they advance every grid) and keep the fastest. */
+int sg_batch_autotune(sg_batch *b, int32_t trial_steps, int32_t *chosen_warps);
+int sg_batch_info(sg_batch *b, int64_t *total_leaves, int64_t *launches, int32_t *warps_per_cta);
+int sg_batch_destroy(sg_batch *b);
+
+/* ---- serving: a continuous-batching request loop ----
+ *
+ * Jobs are independent sparse diffusion runs: a shell/band activation
+ * (res, lo2, hi2, lo_strict as in sg_activate_shell, 8^3 leaves), initial
+ * field values from sg_fill_hash(seed), and `steps` fused steps
+ * x <- box27(diffuse7(x, coef)) with the sum of x kept after each step.
+ * sg_server_submit only queues a job.  Each sg_server_tick
+ *   1. admits pending jobs in submission order while a resident slot is free
+ *      and cudaMemGetInfo's free memory covers the job's footprint plus
+ *      hbm_reserve (a job that cannot fit even on an idle server fails);
+ *      an admitted job's grid is created, activated, listed and filled on
+ *      the device and stays resident until the job completes;
+ *   2. runs one batched step (one persistent launch, see sg_batch_create)
+ *      over every resident job, so jobs admitted while others run share it;
+ *   3. retires jobs that reached their step count, keeping their last sum
+ *      and their submit / admit / done times (seconds, host steady clock);
+ * and synchronizes the stream once.  A job's result equals the same job run
+ * alone up to FP32 rounding order. */
+#define SG_JOB_PENDING 0
+#define SG_JOB_RUNNING 1
+#define SG_JOB_DONE 2
+#define SG_JOB_FAILED 3
+
+typedef struct sg_server sg_server;
+typedef struct sg_server_desc {
+    int32_t max_jobs;      /* resident job slots, 1..1024 */
+    int32_t warps_per_cta; /* batched kernel: 2, 4 or 8 */
+    int64_t hbm_reserve;   /* bytes of device memory to leave free when admitting */
+    float coef;            /* diffusion coefficient of every job */
+    sg_alloc_fn alloc;     /* device memory provider for job grids (NULL: cudaMalloc) */
+    sg_free_fn free;
+    void *alloc_ctx;
+} sg_server_desc;
+typedef struct sg_job_desc {
+    int32_t res;      /* N, a multiple of 8 */
+    int32_t lo_strict;
+    int64_t lo2, hi2; /* band, as sg_activate_shell */
+    int32_t steps;    /* >= 1 */
+    int32_t pad;
+    int64_t seed;     /* sg_fill_hash seed, 0 <= seed < 2^24 */
+} sg_job_desc;
+typedef struct sg_job_status {
+    int32_t state;      /* SG_JOB_* */
+    int32_t steps_done;
+    int64_t n_active;   /* active voxels (known once admitted) */
+    double sum;         /* sum of x after the last completed step */
+    double t_submit, t_admit, t_done;
+} sg_job_status;
+typedef struct sg_server_stats {
+    int64_t submitted, completed, failed, ticks, launches, admission_waits;
+    int32_t resident, pending;
+    double voxel_steps; /* sum over ticks of the resident jobs' active voxels */
+} sg_server_stats;
+
+int sg_server_create(const sg_server_desc *desc, void *cuda_stream, sg_server **out);
+int sg_server_submit(sg_server *s, const sg_job_desc *job, int64_t *job_id);
+int sg_server_tick(sg_server *s);
+int sg_server_job(sg_server *s, int64_t job_id, sg_job_status *out);
+int sg_server_get_stats(sg_server *s, sg_server_stats *out);
+int sg_server_destroy(sg_server *s);
+
 /* ---- list generation for callers that cannot allocate device memory ----
  *
  * Some callers cannot call cudaMalloc: a process whose device memory is owned

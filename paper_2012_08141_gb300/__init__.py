@@ -97,6 +97,14 @@ def load_library(build: bool = True) -> ctypes.CDLL:
         "sg_debug_wait_test": [P],
         "sg_set_stencil_variant": [P, I32],
         "sg_list_gen_noalloc": [P, I64, P, P, I64, P, P],
+        "sg_fill_hash": [P, I32, I64],
+        "sg_batch_create": [P, I32, I32, I32, I32, F, P, ctypes.POINTER(P)],
+        "sg_batch_step": [P],
+        "sg_batch_read_sums": [P, P, I32],
+        "sg_batch_set": [P, I32, I32],
+        "sg_batch_autotune": [P, I32, ctypes.POINTER(I32)],
+        "sg_batch_info": [P, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I32)],
+        "sg_batch_destroy": [P],
     }
     for name, args in sigs.items():
         fn = getattr(lib, name)
@@ -303,3 +311,60 @@ def leaf_coords(leaf_b: np.ndarray, N: int, L: int) -> np.ndarray:
     out[:, :, 1] = ((b // R) % R)[:, None] * L + ((l // L) % L)[None, :]
     out[:, :, 2] = (b % R)[:, None] * L + (l % L)[None, :]
     return out
+
+
+def _grid_fill_hash(self, f: int, seed: int):
+    """Queue: field f = counter-based uniform [0,1) values at active voxels."""
+    self._c(self.lib.sg_fill_hash(self.h, int(f), int(seed)))
+
+
+Grid.fill_hash = _grid_fill_hash
+
+
+class Batch:
+    """Many grids stepped by one persistent launch per step (see
+    sg_batch_create in include/sgrid.h)."""
+
+    def __init__(self, grids, src: int, tmp: int, dst: int, coef: float, stream=None):
+        import torch
+        self.lib = load_library()
+        self.grids = list(grids)            # keep the grids alive
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        arr = (ctypes.c_void_p * len(self.grids))(*[g.h.value for g in self.grids])
+        h = ctypes.c_void_p()
+        _check(self.lib, self.lib.sg_batch_create(arr, len(self.grids), int(src), int(tmp), int(dst), float(coef),
+                                                  ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)))
+        self.h = h
+
+    def step(self):
+        _check(self.lib, self.lib.sg_batch_step(self.h))
+
+    def set(self, warps_per_cta: int, use_graph: bool = True):
+        _check(self.lib, self.lib.sg_batch_set(self.h, int(warps_per_cta), int(bool(use_graph))))
+
+    def autotune(self, trial_steps: int = 3) -> int:
+        w = ctypes.c_int32()
+        _check(self.lib, self.lib.sg_batch_autotune(self.h, int(trial_steps), ctypes.byref(w)))
+        return w.value
+
+    def read_sums(self) -> np.ndarray:
+        out = np.zeros(len(self.grids), dtype=np.float64)
+        _check(self.lib, self.lib.sg_batch_read_sums(self.h, out.ctypes.data, len(self.grids)))
+        return out
+
+    def info(self) -> dict:
+        tl, la, w = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
+        _check(self.lib, self.lib.sg_batch_info(self.h, ctypes.byref(tl), ctypes.byref(la), ctypes.byref(w)))
+        return {"total_leaves": tl.value, "launches": la.value, "warps_per_cta": w.value}
+
+    def close(self):
+        if self.h:
+            rc = self.lib.sg_batch_destroy(self.h)
+            self.h = None
+            _check(self.lib, rc)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -52,7 +52,8 @@ int fail(int code, const char *fmt, ...)
     return code;
 }
 
-enum OpKind { OP_ACT_SHELL, OP_ACT_COORDS, OP_DEACT, OP_LISTGEN, OP_STENCIL, OP_SUM, OP_P2G, OP_GRID_UPDATE, OP_G2P, OP_TEST_WAIT };
+enum OpKind { OP_ACT_SHELL, OP_ACT_COORDS, OP_DEACT, OP_LISTGEN, OP_STENCIL, OP_SUM, OP_P2G, OP_GRID_UPDATE, OP_G2P, OP_TEST_WAIT,
+              OP_FILL };
 
 struct Op {
     OpKind kind;
@@ -314,6 +315,13 @@ int do_flush(sg_grid *g)
                 break;
             case OP_LISTGEN:
                 rc = ensure_list(g);
+                ++i;
+                break;
+            case OP_FILL:
+                if (!(rc = ensure_list(g))) {
+                    if (!g->dry) launch_fill_hash(g->dev, g->stream, o.i0, (unsigned long long)o.slot, g->lc);
+                    rc = after_launch(g, "fill");
+                }
                 ++i;
                 break;
             case OP_TEST_WAIT:
@@ -773,6 +781,311 @@ int sg_debug_wait_test(sg_grid *g)
 {
     if (!g) return fail(SG_ERR_INVALID, "null grid");
     return push(g, Op{OP_TEST_WAIT});
+}
+
+int sg_num_active(sg_grid *g, int64_t *n_active)
+{
+    if (!g || !n_active) return fail(SG_ERR_INVALID, "null argument");
+    int rc = sync_with_list(g);
+    if (rc) return rc;
+    launch_count_active(g->dev, g->stream, g->lc);
+    if ((rc = after_launch(g, "count active"))) return rc;
+    if ((rc = do_sync(g))) return rc;
+    *n_active = (int64_t)g->host_ctrl->n_active;
+    return SG_OK;
+}
+
+int sg_fill_hash(sg_grid *g, int32_t f, int64_t seed)
+{
+    if (!g || !valid_field(g, f) || seed < 0 || seed >= (1LL << 24)) return fail(SG_ERR_INVALID, "bad fill arguments");
+    Op o{OP_FILL};
+    o.i0 = g->phys[f];
+    o.slot = seed;
+    return push(g, o);
+}
+
+}  // extern "C"
+
+// ============================================================================
+// Batched stepping: many grids, one persistent launch per step
+// ============================================================================
+struct sg_batch {
+    std::vector<sg_grid *> grids;
+    cudaStream_t stream = nullptr;
+    int32_t src = 0, tmp = 1, dst = 2;
+    float coef = 0.f;
+    int total_tri = 0;
+    long long total_leaves = 0;
+    BatchGrid *dev_items[2] = {nullptr, nullptr};  // parity 0: src -> dst; parity 1: dst -> src
+    double *dev_acc = nullptr;
+    void *blocks[2] = {nullptr, nullptr};
+    int parity = 0;
+    int warps = 4;
+    int use_graph = 1;
+    cudaGraphExec_t exec[2] = {nullptr, nullptr};
+    cudaStream_t own = nullptr;            // capture / replay stream (the caller's may be the legacy stream)
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    int num_sms = 0;
+    long long launches = 0;
+};
+
+namespace {
+
+void batch_drop_graphs(sg_batch *b)
+{
+    for (auto &e : b->exec)
+        if (e) {
+            cudaGraphExecDestroy(e);
+            e = nullptr;
+        }
+}
+
+int batch_enqueue(sg_batch *b, int parity)
+{
+    const size_t nacc = sizeof(double) * b->grids.size();
+    int rc = cuda_check(cudaMemsetAsync(b->dev_acc, 0, nacc, b->stream), "batch accumulator reset");
+    if (rc) return rc;
+    launch_batch_diffuse_box(b->dev_items[parity], (int)b->grids.size(), b->total_tri, b->coef, b->dev_acc, b->warps,
+                             b->num_sms, b->stream);
+    return cuda_check(cudaPeekAtLastError(), "batched step launch");
+}
+
+int batch_capture(sg_batch *b, int parity)
+{
+    cudaGraph_t graph = nullptr;
+    int rc = cuda_check(cudaStreamBeginCapture(b->own, cudaStreamCaptureModeThreadLocal), "begin capture");
+    if (rc) return rc;
+    cudaStream_t user = b->stream;
+    b->stream = b->own;  // enqueue into the capturing stream
+    const int rc_enq = batch_enqueue(b, parity);
+    b->stream = user;
+    rc = cuda_check(cudaStreamEndCapture(b->own, &graph), "end capture");
+    if (rc_enq) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc_enq;
+    }
+    if (rc) return rc;
+    rc = cuda_check(cudaGraphInstantiate(&b->exec[parity], graph, 0), "graph instantiate");
+    cudaGraphDestroy(graph);
+    return rc;
+}
+
+}  // namespace
+
+namespace sg {
+
+int grid_num_sms(const sg_grid *g) { return g->lc.num_sms; }
+
+int grid_prepare_batch(sg_grid *g, int src, int tmp, int dst, BatchGrid out[2], long long *n_active)
+{
+    if (!g || g->dry || g->dev.L != 8) return fail(SG_ERR_INVALID, "batched grids must be live 8^3-leaf grids");
+    if (!valid_field(g, src) || !valid_field(g, tmp) || !valid_field(g, dst) || src == tmp || src == dst || tmp == dst)
+        return fail(SG_ERR_INVALID, "bad field indices");
+    int rc = do_flush(g);
+    if (!rc && g->list_ver != g->mask_ver) {
+        rc = launch_list(g, false, 0);
+        g->list_ver = g->mask_ver;
+    }
+    if (!rc && g->rmask_ver != g->list_ver) {
+        launch_region_masks(g->dev, g->stream, g->lc);
+        rc = after_launch(g, "region masks");
+        g->rmask_ver = g->list_ver;
+    }
+    if (!rc) {
+        launch_count_active(g->dev, g->stream, g->lc);
+        rc = after_launch(g, "count active");
+    }
+    if (!rc) rc = do_sync(g);
+    if (rc) return rc;
+    if (n_active) *n_active = (long long)g->host_ctrl->n_active;
+    const int nl = g->host_ctrl->list_n;
+    for (int p = 0; p < 2; ++p) {
+        BatchGrid it{};
+        it.g = g->dev;
+        it.x = g->dev.field[g->phys[p == 0 ? src : dst]];
+        it.y = g->dev.field[g->phys[p == 0 ? dst : src]];
+        it.t = g->dev.field[g->phys[tmp]];
+        it.n = nl;
+        it.tri0 = 0;
+        out[p] = it;
+    }
+    return SG_OK;
+}
+
+}  // namespace sg
+
+extern "C" {
+
+int sg_batch_create(sg_grid *const *grids, int32_t n, int32_t src, int32_t tmp, int32_t dst, float coef,
+                    void *cuda_stream, sg_batch **out)
+{
+    if (!grids || !out || n < 1 || n > kMaxBatch) return fail(SG_ERR_INVALID, "batch needs 1..%d grids", kMaxBatch);
+    *out = nullptr;
+    for (int i = 0; i < n; ++i) {
+        sg_grid *g = grids[i];
+        if (!g || g->dry || g->dev.L != 8) return fail(SG_ERR_INVALID, "batched grids must be live 8^3-leaf grids");
+        if (!valid_field(g, src) || !valid_field(g, tmp) || !valid_field(g, dst) || src == tmp || src == dst || tmp == dst)
+            return fail(SG_ERR_INVALID, "bad field indices for grid %d", i);
+    }
+    sg_batch *b = new (std::nothrow) sg_batch();
+    if (!b) return fail(SG_ERR_OOM, "host allocation");
+    b->grids.assign(grids, grids + n);
+    b->stream = (cudaStream_t)cuda_stream;
+    b->src = src;
+    b->tmp = tmp;
+    b->dst = dst;
+    b->coef = coef;
+    b->num_sms = grids[0]->lc.num_sms;
+    std::vector<BatchGrid> items[2];
+    int rc = SG_OK;
+    for (int i = 0; i < n && !rc; ++i) {
+        BatchGrid two[2];
+        long long na = 0;
+        rc = grid_prepare_batch(grids[i], src, tmp, dst, two, &na);
+        if (rc) break;
+        for (int p = 0; p < 2; ++p) {
+            two[p].tri0 = b->total_tri;
+            items[p].push_back(two[p]);
+        }
+        b->total_tri += (two[0].n + 2) / 3;
+        b->total_leaves += two[0].n;
+    }
+    if (rc) {
+        delete b;
+        return rc;
+    }
+    sg_grid *g0 = grids[0];
+    for (int p = 0; p < 2 && !rc; ++p) {
+        b->blocks[p] = dev_alloc(g0, sizeof(BatchGrid) * n + (p == 0 ? sizeof(double) * n : 0));
+        if (!b->blocks[p]) rc = fail(SG_ERR_OOM, "batch descriptors");
+    }
+    if (!rc) {
+        b->dev_items[0] = (BatchGrid *)b->blocks[0];
+        b->dev_acc = (double *)((char *)b->blocks[0] + sizeof(BatchGrid) * n);
+        b->dev_items[1] = (BatchGrid *)b->blocks[1];
+        for (int p = 0; p < 2 && !rc; ++p)
+            rc = cuda_check(cudaMemcpyAsync(b->dev_items[p], items[p].data(), sizeof(BatchGrid) * n,
+                                            cudaMemcpyHostToDevice, b->stream),
+                            "batch descriptors");
+        if (!rc) rc = cuda_check(cudaMemsetAsync(b->dev_acc, 0, sizeof(double) * n, b->stream), "batch sums");
+        if (!rc) rc = cuda_check(cudaStreamSynchronize(b->stream), "batch sync");
+    }
+    if (!rc) rc = cuda_check(cudaStreamCreateWithFlags(&b->own, cudaStreamNonBlocking), "batch stream");
+    if (!rc) rc = cuda_check(cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming), "batch event");
+    if (!rc) rc = cuda_check(cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming), "batch event");
+    if (rc) {
+        // blocks belong to grid 0's allocation list and are released with it
+        if (b->ev_in) cudaEventDestroy(b->ev_in);
+        if (b->own) cudaStreamDestroy(b->own);
+        delete b;
+        return rc;
+    }
+    *out = b;
+    return SG_OK;
+}
+
+int sg_batch_set(sg_batch *b, int32_t warps_per_cta, int32_t use_graph)
+{
+    if (!b || (warps_per_cta != 2 && warps_per_cta != 4 && warps_per_cta != 8))
+        return fail(SG_ERR_INVALID, "warps_per_cta must be 2, 4 or 8");
+    if (warps_per_cta != b->warps) batch_drop_graphs(b);
+    b->warps = warps_per_cta;
+    b->use_graph = use_graph ? 1 : 0;
+    return SG_OK;
+}
+
+int sg_batch_step(sg_batch *b)
+{
+    if (!b) return fail(SG_ERR_INVALID, "null batch");
+    int rc;
+    const int p = b->parity;
+    if (b->use_graph) {
+        if (!b->exec[p] && (rc = batch_capture(b, p))) return rc;
+        // replay on the batch's own stream, ordered after and before the caller's stream
+        if ((rc = cuda_check(cudaEventRecord(b->ev_in, b->stream), "event record")) ||
+            (rc = cuda_check(cudaStreamWaitEvent(b->own, b->ev_in, 0), "stream wait")) ||
+            (rc = cuda_check(cudaGraphLaunch(b->exec[p], b->own), "graph launch")) ||
+            (rc = cuda_check(cudaEventRecord(b->ev_out, b->own), "event record")) ||
+            (rc = cuda_check(cudaStreamWaitEvent(b->stream, b->ev_out, 0), "stream wait")))
+            return rc;
+    } else if ((rc = batch_enqueue(b, p))) {
+        return rc;
+    }
+    b->launches++;
+    for (sg_grid *g : b->grids) {
+        std::swap(g->phys[b->src], g->phys[b->dst]);
+        g->stats.launches++;
+        g->stats.ops_fused += 2;
+        g->stats.stores_removed += 1;
+    }
+    b->parity ^= 1;
+    return SG_OK;
+}
+
+int sg_batch_read_sums(sg_batch *b, double *host, int32_t n)
+{
+    if (!b || n < 0 || n > (int32_t)b->grids.size() || (n > 0 && !host)) return fail(SG_ERR_INVALID, "bad arguments");
+    int rc = cuda_check(cudaMemcpyAsync(host, b->dev_acc, sizeof(double) * n, cudaMemcpyDeviceToHost, b->stream),
+                        "copy batch sums");
+    if (rc) return rc;
+    return cuda_check(cudaStreamSynchronize(b->stream), "batch sync");
+}
+
+int sg_batch_info(sg_batch *b, int64_t *total_leaves, int64_t *launches, int32_t *warps_per_cta)
+{
+    if (!b) return fail(SG_ERR_INVALID, "null batch");
+    if (total_leaves) *total_leaves = b->total_leaves;
+    if (launches) *launches = b->launches;
+    if (warps_per_cta) *warps_per_cta = b->warps;
+    return SG_OK;
+}
+
+int sg_batch_autotune(sg_batch *b, int32_t trial_steps, int32_t *chosen)
+{
+    if (!b || trial_steps < 1) return fail(SG_ERR_INVALID, "bad autotune arguments");
+    const int cands[3] = {2, 4, 8};
+    float best = 1e30f;
+    int best_w = b->warps, rc;
+    cudaEvent_t e0, e1;
+    if ((rc = cuda_check(cudaEventCreate(&e0), "event"))) return rc;
+    if ((rc = cuda_check(cudaEventCreate(&e1), "event"))) {
+        cudaEventDestroy(e0);
+        return rc;
+    }
+    for (int w : cands) {
+        if ((rc = sg_batch_set(b, w, b->use_graph))) break;
+        if ((rc = sg_batch_step(b))) break;  // warm-up (and graph capture)
+        if ((rc = cuda_check(cudaEventRecord(e0, b->stream), "event"))) break;
+        for (int s = 0; s < trial_steps && !rc; ++s) rc = sg_batch_step(b);
+        if (rc) break;
+        if ((rc = cuda_check(cudaEventRecord(e1, b->stream), "event"))) break;
+        if ((rc = cuda_check(cudaEventSynchronize(e1), "event sync"))) break;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+            best = ms;
+            best_w = w;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    if ((rc = sg_batch_set(b, best_w, b->use_graph))) return rc;
+    if (chosen) *chosen = best_w;
+    return SG_OK;
+}
+
+int sg_batch_destroy(sg_batch *b)
+{
+    if (!b) return SG_OK;
+    int rc = cuda_check(cudaStreamSynchronize(b->stream), "batch sync");
+    if (b->own) cudaStreamSynchronize(b->own);
+    batch_drop_graphs(b);
+    if (b->ev_in) cudaEventDestroy(b->ev_in);
+    if (b->ev_out) cudaEventDestroy(b->ev_out);
+    if (b->own) cudaStreamDestroy(b->own);
+    delete b;  // descriptor blocks are released with grid 0
+    return rc;
 }
 
 const char *sg_last_error(void) { return t_last_error.c_str(); }

@@ -24,6 +24,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "../../include/sgrid.h"
+
 namespace sg {
 
 constexpr int kMaxFields = 16;
@@ -40,10 +42,11 @@ struct Ctrl {
     int32_t err;          // ErrBits
     unsigned long long lg_ticket;  // list-compaction tile tickets (monotone)
     unsigned long long lg_done;    // list-compaction finished tiles (monotone)
+    unsigned long long n_active;   // active voxels of the listed leaves (count kernel)
     unsigned int red_ticket;       // reduction finished CTAs (reset by the last)
     int32_t never_set;    // a flag nothing writes (bounded-wait test)
     int32_t timeout_site; // which wait gave up (0 none, 1 look-back, 2 test)
-    int32_t pad[6];
+    int32_t pad[3];
 };
 
 struct DevGrid {
@@ -111,6 +114,35 @@ void launch_diffuse_box(const DevGrid &g, cudaStream_t s, int src, int tmp, int 
                         int store_tmp, int check_act, int sum_slot, const LaunchCfg &lc);
 void launch_sum(const DevGrid &g, cudaStream_t s, int src, int sum_slot, const LaunchCfg &lc);
 int stencil_persistent_ctas(int num_sms, int which);
+
+// ---- batched fused step over many grids (sg_sweep.cu) ----
+constexpr int kMaxBatch = 1024;
+struct BatchGrid {
+    DevGrid g;
+    const float *x;  // diffuse7 input
+    float *y;        // box27 output
+    float *t;        // intermediate (not stored by the batched kernel)
+    int n;           // list length
+    int tri0;        // first global triple index of this grid
+};
+// One launch: every grid's fused diffuse7 -> box27 step, per-grid sums
+// added to acc[grid] (acc zeroed by the caller).  warps = warps per CTA.
+void launch_batch_diffuse_box(const BatchGrid *items, int n_grids, int total_tri, float coef, double *acc, int warps,
+                              int num_sms, cudaStream_t s);
+int batch_ctas(int num_sms, int warps);
+
+// ---- active-voxel count of the listed leaves into ctrl->n_active ----
+void launch_count_active(const DevGrid &g, cudaStream_t s, const LaunchCfg &lc);
+
+// ---- host helpers shared by the batch and the server (sg_api.cu) ----
+// Flush the grid, make its list, neighbour table and region masks current,
+// count its active voxels, synchronize, and fill the descriptors of both
+// src/dst parities (tri0 left 0).  Returns an SG_* code.
+int grid_prepare_batch(sg_grid *g, int src, int tmp, int dst, BatchGrid out[2], long long *n_active);
+int grid_num_sms(const sg_grid *g);
+
+// ---- device-side fill with the counter-based generator (sg_structure.cu) ----
+void launch_fill_hash(const DevGrid &g, cudaStream_t s, int f, unsigned long long seed, const LaunchCfg &lc);
 
 // ---- register-sweep stencil kernels (sg_sweep.cu), 8^3 leaves ----
 void launch_sweep_diffuse_box(const DevGrid &g, cudaStream_t s, int src, int tmp, int dst, float coef,

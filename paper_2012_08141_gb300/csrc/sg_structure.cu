@@ -438,6 +438,49 @@ void launch_region_masks(const DevGrid &g, cudaStream_t s, const LaunchCfg &lc)
 }
 
 // ---------------------------------------------------------------------------
+// Device-side initial values: at every active voxel of the listed leaves,
+// the top 24 bits of splitmix64 (Steele, Lea & Flood 2014) applied to
+// seed * 2^40 + (i*N + j)*N + k, times 2^-24 (exact in FP32); 0 at inactive
+// voxels.  The same published generator as the harness's input module, so a
+// grid filled here holds the values the harness would upload.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long z)
+{
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__global__ void k_fill_hash(DevGrid g, int f, unsigned long long seed)
+{
+    const long long n = g.ctrl->list_n;
+    const int L = g.L, lg2 = g.lg2, R = g.R, V = L * L * L;
+    float *out = g.field[f];
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n * V; q += (long long)gridDim.x * blockDim.x) {
+        const long long e = q >> (3 * lg2);
+        const int l = (int)(q - (e << (3 * lg2)));
+        const int slot = g.list_slot[e], b = g.list_b[e];
+        const bool on = (g.mask[(long long)slot * g.W + (l >> 5)] >> (l & 31)) & 1u;
+        float v = 0.f;
+        if (on) {
+            const unsigned long long i = (unsigned long long)((b / (R * R)) * L + (l >> (2 * lg2)));
+            const unsigned long long j = (unsigned long long)(((b / R) % R) * L + ((l >> lg2) & (L - 1)));
+            const unsigned long long k = (unsigned long long)((b % R) * L + (l & (L - 1)));
+            const unsigned long long lin = (i * (unsigned long long)g.N + j) * (unsigned long long)g.N + k;
+            const unsigned long long h = splitmix64((seed << 40) + lin);
+            v = (float)(h >> 40) * (1.0f / 16777216.0f);
+        }
+        out[(long long)slot * V + l] = v;
+    }
+}
+
+void launch_fill_hash(const DevGrid &g, cudaStream_t s, int f, unsigned long long seed, const LaunchCfg &lc)
+{
+    k_fill_hash<<<lc.num_sms * 8, 256, 0, s>>>(g, f, seed);
+}
+
+// ---------------------------------------------------------------------------
 // Host transfers: gather leaves in list order into the staging buffer, and
 // scatter from it (applying the mask so inactive voxels stay 0).
 // ---------------------------------------------------------------------------
@@ -498,6 +541,29 @@ __global__ void k_scatter_field(DevGrid g, int f)
 void launch_scatter_field(const DevGrid &g, cudaStream_t s, int f, const LaunchCfg &lc)
 {
     k_scatter_field<<<lc.num_sms * 4, 256, 0, s>>>(g, f);
+}
+
+}  // namespace sg
+
+namespace sg {
+
+// Active voxels of the listed leaves: popcount of their mask words.
+__global__ void k_count_active(DevGrid g)
+{
+    const long long n = g.ctrl->list_n;
+    unsigned long long c = 0;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n * g.W; q += (long long)gridDim.x * blockDim.x) {
+        const long long e = q / g.W;
+        c += __popc(g.mask[(long long)g.list_slot[e] * g.W + (q - e * g.W)]);
+    }
+    c = warp_sum(c);
+    if (lane_id() == 0 && c) atomicAdd(&g.ctrl->n_active, c);
+}
+
+void launch_count_active(const DevGrid &g, cudaStream_t s, const LaunchCfg &lc)
+{
+    cudaMemsetAsync(&g.ctrl->n_active, 0, sizeof(unsigned long long), s);
+    k_count_active<<<lc.num_sms * 4, 256, 0, s>>>(g);
 }
 
 }  // namespace sg

@@ -117,15 +117,12 @@ __device__ __forceinline__ constexpr int plane_li(int ri) { return (ri - H) & 7;
 // the t plane ti = s (region plane s + 1) from x planes s, s+1, s+2, forms
 // its j-sums P, and once three P planes exist writes output plane s - 2.
 // ---------------------------------------------------------------------------
+// One warp, one leaf triple: list entries e0, e0+1, e0+2 of grid g (entries
+// >= n are skipped).  Returns this lane's FP32 sum of the outputs it wrote.
 template <bool STORE_T, bool CHECK, bool SUM>
-__global__ void __launch_bounds__(kSweepThreads, 3) k_sweep_diffuse_box(DevGrid g, int src, int tmp, int dst, float coef,
-                                                                       int sum_slot)
+__device__ __forceinline__ float sweep_db_triple(const DevGrid &g, const float *__restrict__ x, float *__restrict__ y,
+                                                 float *__restrict__ tout, float coef, int e0, int n)
 {
-    __shared__ double s_red[kSweepThreads / 32];
-    const int n = g.ctrl->list_n;
-    const float *__restrict__ x = g.field[src];
-    float *__restrict__ y = g.field[dst];
-    float *__restrict__ tout = g.field[tmp];
     const int lane = lane_id();
     const int sub = lane / 10;
     const int tj = lane - sub * 10;
@@ -137,11 +134,7 @@ __global__ void __launch_bounds__(kSweepThreads, 3) k_sweep_diffuse_box(DevGrid 
     const bool outlane = (tj >= 1 && tj <= 8);
     const float c6 = 1.f - 6.f * coef;
     const int Z = (int)g.cap;  // the zero leaf
-    const int warps_total = gridDim.x * (kSweepThreads / 32);
-    const int gw = blockIdx.x * (kSweepThreads / 32) + (threadIdx.x >> 5);
-    double acc = 0.0;
-
-    for (int e0 = gw * 3; e0 < n; e0 += warps_total * 3) {
+    {
         const int e = e0 + sub;
         const bool valid = (sub < 3) && (e < n);
         int sl[9];
@@ -235,8 +228,23 @@ __global__ void __launch_bounds__(kSweepThreads, 3) k_sweep_diffuse_box(DevGrid 
                 ea[q] = eb[q];
             }
         }
-        acc += (double)part;
+        return part;
     }
+}
+
+// Fused diffuse7 -> box27 (+ sum) over one grid's list: warps stride over
+// leaf triples.
+template <bool STORE_T, bool CHECK, bool SUM>
+__global__ void __launch_bounds__(kSweepThreads, 3) k_sweep_diffuse_box(DevGrid g, int src, int tmp, int dst, float coef,
+                                                                       int sum_slot)
+{
+    __shared__ double s_red[kSweepThreads / 32];
+    const int n = g.ctrl->list_n;
+    const int warps_total = gridDim.x * (kSweepThreads / 32);
+    const int gw = blockIdx.x * (kSweepThreads / 32) + (threadIdx.x >> 5);
+    double acc = 0.0;
+    for (int e0 = gw * 3; e0 < n; e0 += warps_total * 3)
+        acc += (double)sweep_db_triple<STORE_T, CHECK, SUM>(g, g.field[src], g.field[dst], g.field[tmp], coef, e0, n);
     if (SUM) {
         acc = warp_sum(acc);
         if (lane_id() == 0) s_red[threadIdx.x >> 5] = acc;
@@ -432,6 +440,62 @@ void launch_sweep_single(const DevGrid &g, cudaStream_t s, int op, int src, int 
         else { if (sum) SG_SS(SW_BOX27, false, true); else SG_SS(SW_BOX27, false, false); }
     }
 #undef SG_SS
+}
+
+// ---------------------------------------------------------------------------
+// Batched fused step: one persistent launch steps many grids.  The global
+// work list is the concatenation of every grid's leaf triples; warps stride
+// over it, find their grid by binary search over the triples' prefix sums
+// (in shared memory) and run the same per-triple body as the single-grid
+// kernel.  Each triple's output sum is added to its grid's FP64 accumulator
+// (zeroed before the launch).
+// ---------------------------------------------------------------------------
+template <int WARPS>
+__global__ void __launch_bounds__(WARPS * 32, 12 / WARPS) k_batch_diffuse_box(const BatchGrid *__restrict__ items,
+                                                                              int n_grids, int total_tri, float coef,
+                                                                              double *acc)
+{
+    __shared__ int s_off[kMaxBatch + 1];
+    for (int i = threadIdx.x; i <= n_grids; i += WARPS * 32) s_off[i] = (i < n_grids) ? items[i].tri0 : total_tri;
+    __syncthreads();
+    const int warps_total = gridDim.x * WARPS;
+    for (int T = blockIdx.x * WARPS + (threadIdx.x >> 5); T < total_tri; T += warps_total) {
+        int lo = 0, hi = n_grids - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_off[mid] <= T) lo = mid;
+            else hi = mid - 1;
+        }
+        const BatchGrid &it = items[lo];
+        const float part = sweep_db_triple<false, false, true>(it.g, it.x, it.y, it.t, coef, (T - s_off[lo]) * 3, it.n);
+        const double w = warp_sum((double)part);
+        if (lane_id() == 0) atomicAdd(&acc[lo], w);
+    }
+}
+
+int batch_ctas(int num_sms, int warps)
+{
+    static int cache[9] = {0};
+    if (warps < 1 || warps > 8) return num_sms;
+    if (cache[warps] == 0) {
+        int per = 1;
+        cudaError_t err = cudaErrorInvalidValue;
+        if (warps == 2) err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_diffuse_box<2>, 64, 0);
+        if (warps == 4) err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_diffuse_box<4>, 128, 0);
+        if (warps == 8) err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_diffuse_box<8>, 256, 0);
+        if (err != cudaSuccess || per < 1) per = 1;
+        cache[warps] = per;
+    }
+    return cache[warps] * num_sms;
+}
+
+void launch_batch_diffuse_box(const BatchGrid *items, int n_grids, int total_tri, float coef, double *acc, int warps,
+                              int num_sms, cudaStream_t s)
+{
+    const int ctas = batch_ctas(num_sms, warps);
+    if (warps == 2) k_batch_diffuse_box<2><<<ctas, 64, 0, s>>>(items, n_grids, total_tri, coef, acc);
+    else if (warps == 8) k_batch_diffuse_box<8><<<ctas, 256, 0, s>>>(items, n_grids, total_tri, coef, acc);
+    else k_batch_diffuse_box<4><<<ctas, 128, 0, s>>>(items, n_grids, total_tri, coef, acc);
 }
 
 }  // namespace sg

@@ -1,0 +1,134 @@
+"""Python binding of the serving loop (sg_server_*) and of sg_num_active.
+
+Argument marshalling only; the scheduler (admission by free device memory,
+continuous batching of every resident job's step into one launch,
+retirement) runs in libsgrid.
+"""
+from __future__ import annotations
+
+import ctypes
+
+from . import Grid, SgError, _check, load_library
+
+SG_JOB_PENDING, SG_JOB_RUNNING, SG_JOB_DONE, SG_JOB_FAILED = 0, 1, 2, 3
+
+_ALLOC = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+_FREE = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class ServerDesc(ctypes.Structure):
+    _fields_ = [("max_jobs", ctypes.c_int32), ("warps_per_cta", ctypes.c_int32), ("hbm_reserve", ctypes.c_int64),
+                ("coef", ctypes.c_float), ("alloc", _ALLOC), ("free", _FREE), ("alloc_ctx", ctypes.c_void_p)]
+
+
+class JobDesc(ctypes.Structure):
+    _fields_ = [("res", ctypes.c_int32), ("lo_strict", ctypes.c_int32), ("lo2", ctypes.c_int64),
+                ("hi2", ctypes.c_int64), ("steps", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("seed", ctypes.c_int64)]
+
+
+class JobStatus(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int32), ("steps_done", ctypes.c_int32), ("n_active", ctypes.c_int64),
+                ("sum", ctypes.c_double), ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double),
+                ("t_done", ctypes.c_double)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
+                ("ticks", ctypes.c_int64), ("launches", ctypes.c_int64), ("admission_waits", ctypes.c_int64),
+                ("resident", ctypes.c_int32), ("pending", ctypes.c_int32), ("voxel_steps", ctypes.c_double)]
+
+
+def _lib():
+    lib = load_library()
+    if not getattr(lib, "_serve_sigs", False):
+        P = ctypes.c_void_p
+        sigs = {
+            "sg_server_create": [ctypes.POINTER(ServerDesc), P, ctypes.POINTER(P)],
+            "sg_server_submit": [P, ctypes.POINTER(JobDesc), ctypes.POINTER(ctypes.c_int64)],
+            "sg_server_tick": [P],
+            "sg_server_job": [P, ctypes.c_int64, ctypes.POINTER(JobStatus)],
+            "sg_server_get_stats": [P, ctypes.POINTER(ServerStats)],
+            "sg_server_destroy": [P],
+            "sg_num_active": [P, ctypes.POINTER(ctypes.c_int64)],
+        }
+        for name, args in sigs.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = ctypes.c_int
+        lib._serve_sigs = True
+    return lib
+
+
+def _grid_num_active(self) -> int:
+    """Active voxels of the listed leaves (implicit sync)."""
+    n = ctypes.c_int64()
+    _check(_lib(), _lib().sg_num_active(self.h, ctypes.byref(n)))
+    return n.value
+
+
+Grid.num_active = _grid_num_active
+
+
+class Server:
+    """Continuous-batching request loop over resident sparse diffusion jobs."""
+
+    def __init__(self, max_jobs: int = 256, warps_per_cta: int = 4, hbm_reserve: int = 4 << 30, coef: float = 0.1,
+                 stream=None):
+        import torch
+        self.lib = _lib()
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        dev, st = torch.cuda.current_device(), self.stream
+
+        def _alloc(nbytes, ctx):
+            return torch.cuda.caching_allocator_alloc(int(nbytes), dev, st)
+
+        def _free(ptr, ctx):
+            torch.cuda.caching_allocator_delete(ptr)
+
+        self._cb = (_ALLOC(_alloc), _FREE(_free))
+        d = ServerDesc(int(max_jobs), int(warps_per_cta), int(hbm_reserve), float(coef), self._cb[0], self._cb[1],
+                       None)
+        h = ctypes.c_void_p()
+        rc = self.lib.sg_server_create(ctypes.byref(d), ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
+        if rc:
+            raise SgError(rc, "sg_server_create failed")
+        self.h = h
+
+    def submit(self, spec, steps: int) -> int:
+        """spec: a workload.ShellSpec with 8^3 leaves."""
+        j = JobDesc(int(spec.N), int(bool(spec.lo_strict)), int(spec.lo2), int(spec.hi2), int(steps), 0,
+                    int(spec.seed) % (1 << 24))
+        jid = ctypes.c_int64()
+        rc = self.lib.sg_server_submit(self.h, ctypes.byref(j), ctypes.byref(jid))
+        if rc:
+            raise SgError(rc, "sg_server_submit failed")
+        return jid.value
+
+    def tick(self):
+        rc = self.lib.sg_server_tick(self.h)
+        if rc:
+            raise SgError(rc, "sg_server_tick failed")
+
+    def job(self, job_id: int) -> dict:
+        st = JobStatus()
+        rc = self.lib.sg_server_job(self.h, int(job_id), ctypes.byref(st))
+        if rc:
+            raise SgError(rc, "unknown job")
+        return {name: getattr(st, name) for name, _ in JobStatus._fields_}
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        self.lib.sg_server_get_stats(self.h, ctypes.byref(st))
+        return {name: getattr(st, name) for name, _ in ServerStats._fields_}
+
+    def close(self):
+        if self.h:
+            self.lib.sg_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

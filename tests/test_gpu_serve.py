@@ -1,0 +1,87 @@
+"""GPU tests of the continuous-batching request loop: jobs admitted while
+others run share the batched launch, and every job's result equals the same
+job run alone (within the stencil tolerance)."""
+import numpy as np
+import pytest
+
+from workload import batched_mix
+
+pytestmark = pytest.mark.gpu
+
+TOL = 2e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    yield
+
+
+def alone_sum(spec, steps):
+    import paper_2012_08141_gb300 as sg
+    R = spec.N // 8
+    g = sg.Grid(spec.N, 3, 3, max_leaves=R ** 3, max_sums=1, scratch_mask=0b010)
+    g.activate_shell(spec.lo2, spec.hi2, spec.lo_strict)
+    g.list_gen()
+    g.fill_hash(0, spec.seed % (1 << 24))
+    for _ in range(steps):
+        g.clear(1)
+        g.diffuse7(0, 1, 0.1)
+        g.box27(1, 2)
+        g.swap(0, 2)
+        g.reduce_sum(0, 0)
+    s = g.read_sums(1)[0]
+    g.close()
+    return s
+
+
+def test_jobs_in_the_mix_equal_jobs_alone():
+    from paper_2012_08141_gb300.serve import SG_JOB_DONE, Server
+    specs = batched_mix(21, n_grids=7, lo=1e3, hi=2e5)
+    rng = np.random.default_rng(2)
+    steps = [int(rng.integers(3, 13)) for _ in specs]
+    srv = Server(max_jobs=4, warps_per_cta=4, hbm_reserve=1 << 30)
+    ids = [srv.submit(s, k) for s, k in zip(specs[:3], steps[:3])]
+    max_resident = 0
+    for _ in range(2):
+        srv.tick()
+        max_resident = max(max_resident, srv.stats()["resident"])
+    ids += [srv.submit(s, k) for s, k in zip(specs[3:], steps[3:])]   # arrive while others run
+    for _ in range(200):
+        st = srv.stats()
+        if st["completed"] + st["failed"] == len(specs):
+            break
+        srv.tick()
+        max_resident = max(max_resident, srv.stats()["resident"])
+    st = srv.stats()
+    assert st["completed"] == len(specs) and st["failed"] == 0
+    assert max_resident >= 2                      # work of several jobs shared launches
+    jobs = [srv.job(i) for i in ids]
+    assert any(jobs[k]["t_admit"] < jobs[0]["t_done"] for k in range(3, len(jobs)))  # admitted while job 0 ran
+    for spec, k, jb in zip(specs, steps, jobs):
+        assert jb["state"] == SG_JOB_DONE and jb["steps_done"] == k
+        ref = alone_sum(spec, k)
+        assert abs(jb["sum"] - ref) <= TOL * abs(ref)
+        assert jb["t_submit"] <= jb["t_admit"] <= jb["t_done"]
+    assert st["voxel_steps"] == pytest.approx(sum(j["n_active"] * k for j, k in zip(jobs, steps)))
+    srv.close()
+
+
+def test_job_that_cannot_fit_fails_and_server_continues():
+    import torch
+    from paper_2012_08141_gb300.serve import SG_JOB_DONE, SG_JOB_FAILED, Server
+    free, total = torch.cuda.mem_get_info()
+    srv = Server(max_jobs=2, hbm_reserve=int(total) * 2)   # reserve more than the device has
+    spec = batched_mix(5, n_grids=1, lo=1e3, hi=2e3)[0]
+    jid = srv.submit(spec, 3)
+    srv.tick()
+    assert srv.job(jid)["state"] == SG_JOB_FAILED
+    srv.close()
+    srv = Server(max_jobs=2, hbm_reserve=0)
+    jid = srv.submit(spec, 3)
+    for _ in range(5):
+        srv.tick()
+    assert srv.job(jid)["state"] == SG_JOB_DONE
+    srv.close()
