@@ -1,18 +1,28 @@
-"""Benchmark of the fused sparse-grid step on GB300.
+"""Benchmark of the sparse-grid hot path on GB300.  Prints ONE JSON line.
 
-Workload (default): the 512^3 narrow band |dist - 200| < 8 over 8^3 leaves
+Headline workload: the 512^3 narrow band |dist - 200| < 8 over 8^3 leaves
 (26,104 leaves, 8,047,608 active voxels); one step = clear(t), diffuse7(x->t),
 box27(t->y), swap(x,y), sum(x), through the library's queue with every
-inter-kernel pass on (one fused launch).  The eager form (list regenerated and
-activation checked in every kernel, 12 launches) is timed beside it.
+inter-kernel pass on (one fused launch).  The eager form (list regenerated
+and activation checked in every kernel, 12 launches per step) is timed beside
+it.  Further legs (skipped with --only fused or on more than one rank):
+  batched   64 independent band/ball grids, active sizes log-uniform in
+            1e3..5e6, one persistent launch per step in a CUDA graph
+            (autotuned warps per CTA), against the same grids stepped one
+            after another, fused and eager;
+  particles 2M particles in 3 spheres, 256^3 grid of 4^3 leaves: deactivate,
+            P2G with activation, grid update, G2P per step;
+  serving   Poisson arrivals of band jobs (1e4..1e7 voxels, 10..200 steps)
+            into the continuous-batching server: p50/p99 job latency;
+  band1024  the 1024^3 band |dist - 400| < 8, far larger than L2.
 
-Timing: W untimed warm-up steps, then K timed steps; before every timed step
-a 512 MB buffer is written to flush L2 (the band's fields fit in L2), and each
-step is bracketed by CUDA events on the grid's stream.  Prints ONE JSON line.
+Timing: W untimed warm-up steps, then K timed steps, each bracketed by CUDA
+events on the launching stream; before every timed step of the band
+workloads a 512 MB buffer is written to flush L2.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
---impl reference times the FP64 CPU oracle on the host cores on the same
+--impl reference times the FP64 CPU oracle on the host cores on the headline
 workload (each step one full oracle step) and prints its line.
 """
 from __future__ import annotations
@@ -20,6 +30,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -32,10 +43,10 @@ sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
 
-from workload import band512, leaf_values, spheres_particles  # noqa: E402
+from workload import ShellSpec, band512, batched_mix, leaf_values, serving_arrivals, spheres_particles  # noqa: E402
 
 METRIC = "active voxel-steps/s"
-BYTES_PER_LEAF_FUSED = 2 * 2048 + 27 * 4 + 64 + 4  # x read, y written, nbr row, mask, list entry
+BYTES_PER_LEAF_FUSED = 2 * 2048 + 27 * 4 + 64 + 4  # x read, x' written, nbr row, mask, list entry
 BYTES_PER_LEAF_EAGER = 6 * 2048                    # clear W, diffuse R+W, box27 R+W, sum R (leaf passes)
 
 
@@ -67,7 +78,7 @@ def traffic_record(kernel_src: str):
 
 
 class ClockSampler:
-    """nvidia-smi clock and throttle-reason samples during the timed region."""
+    """nvidia-smi clock and throttle-reason samples during a timed region."""
 
     def __init__(self, index: int):
         self.index = index
@@ -119,23 +130,24 @@ class ClockSampler:
                     reasons.add(n)
         if not sm:
             return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
 # ---------------------------------------------------------------------------
-# our arm
+# our arm: band workloads
 # ---------------------------------------------------------------------------
 
-def setup_band(sg, spec, opts, x_host, variant=0):
-    g = sg.Grid(spec.N, 3, 3, max_leaves=32768, max_sums=1, scratch_mask=0b010)
+def setup_band(sg, spec, opts, x_host, variant=0, cap=32768):
+    g = sg.Grid(spec.N, 3, 3, max_leaves=cap, max_sums=1, scratch_mask=0b010)
     g.set_opts(opts)
     g.set_stencil_variant(variant)
     g.activate_shell(spec.lo2, spec.hi2, spec.lo_strict)
     g.list_gen()
-    n = g.num_leaves()
-    assert n == x_host.shape[0]
-    g.write_field(0, x_host)
+    if x_host is None:
+        g.fill_hash(0, spec.seed % (1 << 24))
+    else:
+        assert g.num_leaves() == x_host.shape[0]
+        g.write_field(0, x_host)
     return g
 
 
@@ -148,25 +160,150 @@ def band_step(g):
     g.flush()
 
 
-def time_steps(torch, g, steps, warmup, flush_buf, stream):
+def time_steps(torch, step_fn, steps, warmup, flush_buf, stream, launches_fn=None):
     for _ in range(warmup):
-        band_step(g)
+        step_fn()
     torch.cuda.synchronize()
-    l0 = g.stats()["launches"]
+    l0 = launches_fn() if launches_fn else 0
     evs = []
     with torch.cuda.stream(stream):
         for _ in range(steps):
-            flush_buf.zero_()                      # evict L2 between timed steps
+            if flush_buf is not None:
+                flush_buf.zero_()                      # evict L2 between timed steps
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            band_step(g)
+            step_fn()
             b.record(stream)
             evs.append((a, b))
     torch.cuda.synchronize()
     ms = [a.elapsed_time(b) for a, b in evs]
-    launches = g.stats()["launches"] - l0
+    launches = (launches_fn() - l0) if launches_fn else 0
     return ms, launches
+
+
+def leaves_of(sg, spec):
+    R = spec.N // spec.L
+    p = sg.Grid(spec.N, 3, 1, max_leaves=R ** 3)
+    p.activate_shell(spec.lo2, spec.hi2, spec.lo_strict)
+    n = p.num_leaves()
+    p.close()
+    return n
+
+
+def bench_band1024(torch, sg, steps, warmup, flush_buf, stream):
+    spec = ShellSpec(1024, 8, int(4 * 392 ** 2), int(4 * 408 ** 2), True, 5, "band r=400 h=8")
+    n = leaves_of(sg, spec)
+    g = setup_band(sg, spec, sg.SG_OPT_ALL, None, cap=n)
+    act = g.num_active()
+    ms, _ = time_steps(torch, lambda: band_step(g), steps, warmup, flush_buf, stream)
+    t = sum(ms) / 1e3
+    peak, kind = peaks()
+    ach = n * BYTES_PER_LEAF_FUSED / (t / steps) / 1e9
+    g.close()
+    return {"workload": "1024^3 band |dist-400|<8, 8^3 leaves", "active_voxels": act, "leaves": n,
+            "value": act * steps / t, "ms_per_step": t * 1e3 / steps, "achieved_gbs": ach, "frac": ach / peak}
+
+
+def bench_batched(torch, sg, steps, warmup, flush_buf, stream):
+    specs = batched_mix(0, n_grids=64, lo=1e3, hi=5e6)
+    grids = []
+    for s in specs:
+        g = sg.Grid(s.N, 3, 3, max_leaves=max(1, leaves_of(sg, s)), max_sums=1, scratch_mask=0b010)
+        g.activate_shell(s.lo2, s.hi2, s.lo_strict)
+        g.list_gen()
+        g.fill_hash(0, s.seed % (1 << 24))
+        grids.append(g)
+    active = sum(g.num_active() for g in grids)
+    leaves = sum(g.num_leaves() for g in grids)
+    bt = sg.Batch(grids, 0, 1, 2, 0.1)
+    w = bt.autotune(3)
+    l0 = bt.info()["launches"]
+    ms, _ = time_steps(torch, bt.step, steps, warmup, flush_buf, stream)
+    launches = (bt.info()["launches"] - l0) / (steps + warmup)
+    t_b = sum(ms) / 1e3
+    bt.close()
+
+    def seq_step():
+        for g in grids:
+            band_step(g)
+
+    k2 = max(3, steps // 3)
+    res = {}
+    for name, opts in (("sequential_fused", sg.SG_OPT_ALL), ("sequential_eager", sg.SG_OPT_EAGER)):
+        for g in grids:
+            g.set_opts(opts)
+        l0 = sum(g.stats()["launches"] for g in grids)
+        ms2, _ = time_steps(torch, seq_step, k2, 2, flush_buf, stream)
+        l1 = sum(g.stats()["launches"] for g in grids)
+        t2 = sum(ms2) / 1e3
+        res[name] = {"value": active * k2 / t2, "ms_per_step": t2 * 1e3 / k2, "launches_per_step": (l1 - l0) / (k2 + 2)}
+    for g in grids:
+        g.close()
+    return {"workload": "64 band/ball grids, active sizes log-uniform 1e3..5e6 (seed 0)", "grids": len(grids),
+            "active_voxels": active, "leaves": leaves, "value": active * steps / t_b,
+            "ms_per_step": t_b * 1e3 / steps, "launches_per_step": launches, "warps_per_cta": w,
+            "cuda_graph": True, **res,
+            "over_sequential_eager": (active * steps / t_b) / res["sequential_eager"]["value"]}
+
+
+def bench_particles(torch, sg, steps, warmup, stream):
+    spec = spheres_particles(0)
+    g = sg.Grid(spec.N, 2, 4, max_leaves=(spec.N // 4) ** 3, max_sums=1)
+    x = torch.from_numpy(spec.x).cuda()
+    v = torch.from_numpy(spec.v).cuda()
+
+    def step():
+        g.deactivate_all()
+        g.p2g(x, v, spec.pmass, 0, 1)
+        g.grid_update(0, 1, spec.dt, spec.gravity, spec.bound)
+        g.g2p(x, v, spec.dt, 1)
+        g.flush()
+
+    ms, launches = time_steps(torch, step, steps, warmup, None, stream, lambda: g.stats()["launches"])
+    t = sum(ms) / 1e3
+    g.sync()
+    leaves = g.num_leaves()
+    g.close()
+    return {"workload": "2M particles in 3 spheres, 256^3 grid of 4^3 leaves, P2G+grid update+G2P",
+            "particles": spec.n, "leaves": leaves, "value": spec.n * steps / t, "unit": "particle-steps/s",
+            "ms_per_step": t * 1e3 / steps, "launches_per_step": launches / steps,
+            "stream_bytes_per_particle": 72}
+
+
+def bench_serving(torch, sg, rates=(50, 200, 1000), duration=2.0, cap_s=60.0):
+    from paper_2012_08141_gb300.serve import Server
+    out = []
+    for rate in rates:
+        jobs = serving_arrivals(1000 + rate, rate, duration)
+        srv = Server(max_jobs=256, warps_per_cta=4, hbm_reserve=8 << 30)
+        ids, k = [], 0
+        t0 = time.perf_counter()
+        while True:
+            now = time.perf_counter() - t0
+            while k < len(jobs) and jobs[k].arrival_s <= now:
+                ids.append(srv.submit(jobs[k].spec, jobs[k].steps))
+                k += 1
+            st = srv.stats()
+            if k == len(jobs) and st["completed"] + st["failed"] == len(jobs):
+                break
+            if now > duration + cap_s:
+                break
+            if st["resident"] or st["pending"]:
+                srv.tick()
+            else:
+                time.sleep(min(1e-4, max(0.0, jobs[k].arrival_s - now)) if k < len(jobs) else 0)
+        elapsed = time.perf_counter() - t0
+        st = srv.stats()
+        lat = sorted(srv.job(i)["t_done"] - srv.job(i)["t_submit"] for i in ids if srv.job(i)["state"] == 2)
+        out.append({"rate_per_s": rate, "jobs": len(jobs), "completed": st["completed"], "failed": st["failed"],
+                    "p50_ms": 1e3 * lat[len(lat) // 2] if lat else None,
+                    "p99_ms": 1e3 * lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)] if lat else None,
+                    "voxel_steps_per_s": st["voxel_steps"] / elapsed, "ticks": st["ticks"],
+                    "wall_s": elapsed})
+        srv.close()
+    return {"workload": "Poisson arrivals of band jobs, 1e4..1e7 voxels, 10..200 steps", "duration_s": duration,
+            "rates": out}
 
 
 def run_ours(args):
@@ -204,15 +341,17 @@ def run_ours(args):
         dist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(dev) as clk:
-        ms_f, launches_f = time_steps(torch, fused, args.steps, args.warmup, flush_buf, stream)
-    torch.cuda.synchronize()
-    if args.only == "fused":
-        ms_e, launches_e = [float("nan")], 0
-    else:
-        ms_e, launches_e = time_steps(torch, eager, max(args.steps // 2, 5), max(args.warmup, 3), flush_buf, stream)
+        ms_f, launches_f = time_steps(torch, lambda: band_step(fused), args.steps, args.warmup, flush_buf, stream,
+                                      lambda: fused.stats()["launches"])
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
+    if args.only == "fused":
+        ms_e, launches_e = [float("nan")], 0
+    else:
+        ms_e, launches_e = time_steps(torch, lambda: band_step(eager), max(args.steps // 2, 5), max(args.warmup, 3),
+                                      flush_buf, stream, lambda: eager.stats()["launches"])
+    torch.cuda.synchronize()
 
     # end-to-end through the public API: pinned host x in, sum out, every step
     x_pinned = torch.from_numpy(x_host).pin_memory()
@@ -227,6 +366,8 @@ def run_ours(args):
         band_step(fused)
         fused.read_sums(1)
     e2e_s = max(time.perf_counter() - t0, 1e-9)
+    fused.close()
+    eager.close()
 
     t_f = sum(ms_f) / 1e3
     t_e = sum(ms_e) / 1e3
@@ -243,6 +384,21 @@ def run_ours(args):
     kernel_src = os.path.join(ROOT, "paper_2012_08141_gb300", "csrc",
                               "sg_sweep.cu" if args.variant == 0 else "sg_stencil.cu")
     traffic = traffic_record(kernel_src)
+
+    extra = {}
+    if world == 1 and args.only == "all":
+        k = max(5, min(args.steps, 20))
+        for name, fn in (("band1024", lambda: bench_band1024(torch, sg, k, 3, flush_buf, stream)),
+                         ("batched", lambda: bench_batched(torch, sg, k, 3, flush_buf, stream)),
+                         ("particles", lambda: bench_particles(torch, sg, k, 3, stream)),
+                         ("serving", lambda: bench_serving(torch, sg))):
+            try:
+                t0 = time.perf_counter()
+                extra[name] = fn()
+                extra[name]["bench_wall_s"] = time.perf_counter() - t0
+            except Exception as exc:  # report, keep the headline line
+                extra[name] = {"error": repr(exc)}
+            torch.cuda.synchronize()
 
     if rank == 0:
         cpu = None
@@ -270,7 +426,7 @@ def run_ours(args):
                          "kernel": ("k_sweep_diffuse_box<false,false,true>" if args.variant == 0
                                     else "k_diffuse_box<false,false,true>"),
                          "bytes_per_launch": n_leaves * BYTES_PER_LEAF_FUSED},
-            "e2e": {"value": world * n_active * e2e_steps / e2e_s, "unit": "voxel-steps/s",
+            "e2e": {"value": world * n_active * e2e_steps / e2e_s if e2e_steps else None, "unit": "voxel-steps/s",
                     "h2d_bytes_per_step": int(x_host.nbytes), "d2h_bytes_per_step": 8},
             "gpu_launches": int(launches_f),
             "launches_per_step": launches_f / args.steps,
@@ -279,10 +435,9 @@ def run_ours(args):
             "fused_over_eager": value / eager_value,
             "clocks": clk.summary(),
             "cpu_baseline": cpu,
+            "extra": extra,
         }
         print(json.dumps(line), flush=True)
-    fused.close()
-    eager.close()
     if dist:
         dist.barrier()
         dist.destroy_process_group()
@@ -364,7 +519,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--variant", type=int, default=0, help="stencil kernel family (0 sweep, 1 smem)")
     ap.add_argument("--only", choices=["all", "fused"], default="all",
-                    help="fused: time only the fused step (for profiling runs)")
+                    help="fused: time only the fused headline step (for profiling runs)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

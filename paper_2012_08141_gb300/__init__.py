@@ -105,6 +105,7 @@ def load_library(build: bool = True) -> ctypes.CDLL:
         "sg_batch_autotune": [P, I32, ctypes.POINTER(I32)],
         "sg_batch_info": [P, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I32)],
         "sg_batch_destroy": [P],
+        "sg_num_active": [P, ctypes.POINTER(I64)],
     }
     for name, args in sigs.items():
         fn = getattr(lib, name)
@@ -318,7 +319,16 @@ def _grid_fill_hash(self, f: int, seed: int):
     self._c(self.lib.sg_fill_hash(self.h, int(f), int(seed)))
 
 
+def _grid_num_active(self) -> int:
+    """Active voxels of the listed leaves (implicit sync)."""
+    n = ctypes.c_int64()
+    self._c(self.lib.sg_num_active(self.h, ctypes.byref(n)))
+    self._borrowed.clear()
+    return n.value
+
+
 Grid.fill_hash = _grid_fill_hash
+Grid.num_active = _grid_num_active
 
 
 class Batch:

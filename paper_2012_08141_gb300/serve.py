@@ -1,4 +1,4 @@
-"""Python binding of the serving loop (sg_server_*) and of sg_num_active.
+"""Python binding of the serving loop (sg_server_*).
 
 Argument marshalling only; the scheduler (admission by free device memory,
 continuous batching of every resident job's step into one launch,
@@ -8,7 +8,7 @@ from __future__ import annotations
 
 import ctypes
 
-from . import Grid, SgError, _check, load_library
+from . import SgError, load_library
 
 SG_JOB_PENDING, SG_JOB_RUNNING, SG_JOB_DONE, SG_JOB_FAILED = 0, 1, 2, 3
 
@@ -50,7 +50,6 @@ def _lib():
             "sg_server_job": [P, ctypes.c_int64, ctypes.POINTER(JobStatus)],
             "sg_server_get_stats": [P, ctypes.POINTER(ServerStats)],
             "sg_server_destroy": [P],
-            "sg_num_active": [P, ctypes.POINTER(ctypes.c_int64)],
         }
         for name, args in sigs.items():
             fn = getattr(lib, name)
@@ -58,16 +57,6 @@ def _lib():
             fn.restype = ctypes.c_int
         lib._serve_sigs = True
     return lib
-
-
-def _grid_num_active(self) -> int:
-    """Active voxels of the listed leaves (implicit sync)."""
-    n = ctypes.c_int64()
-    _check(_lib(), _lib().sg_num_active(self.h, ctypes.byref(n)))
-    return n.value
-
-
-Grid.num_active = _grid_num_active
 
 
 class Server:
