@@ -54,6 +54,23 @@ def log(*a):
     print(*a, file=sys.stderr, flush=True)
 
 
+def aggregate_max(values, dist=None, device="cpu"):
+    """Per-quantity maximum over ranks (the slowest rank bounds the job's
+    time); identity on one rank."""
+    if dist is None:
+        return [float(v) for v in values]
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def job_throughput(world: int, units_per_rank: float, steps: int, seconds: float) -> float:
+    """Whole-job throughput: every rank processes its own replica of the
+    workload (weak scaling), so the units of all ranks over the slowest time."""
+    return world * units_per_rank * steps / seconds
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -371,12 +388,9 @@ def run_ours(args):
 
     t_f = sum(ms_f) / 1e3
     t_e = sum(ms_e) / 1e3
-    if dist:
-        tt = torch.tensor([t_f, t_e, e2e_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_f, t_e, e2e_s = tt.tolist()
-    value = world * n_active * args.steps / t_f
-    eager_value = world * n_active * len(ms_e) / t_e
+    t_f, t_e, e2e_s = aggregate_max([t_f, t_e, e2e_s], dist, "cuda")
+    value = job_throughput(world, n_active, args.steps, t_f)
+    eager_value = job_throughput(world, n_active, len(ms_e), t_e)
     avg_ms = t_f * 1e3 / args.steps
     peak, peak_kind = peaks()
     achieved = n_leaves * BYTES_PER_LEAF_FUSED / (avg_ms / 1e3) / 1e9
