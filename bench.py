@@ -285,7 +285,8 @@ def bench_particles(torch, sg, steps, warmup, stream):
     return {"workload": "2M particles in 3 spheres, 256^3 grid of 4^3 leaves, P2G+grid update+G2P",
             "particles": spec.n, "leaves": leaves, "value": spec.n * steps / t, "unit": "particle-steps/s",
             "ms_per_step": t * 1e3 / steps, "launches_per_step": launches / steps,
-            "stream_bytes_per_particle": 72}
+            "stream_bytes_per_particle": 72,
+            "grid_atomics_per_s": spec.n * 27 * 4 * steps / t}
 
 
 def bench_serving(torch, sg, rates=(50, 200, 1000), duration=2.0, cap_s=60.0):
@@ -363,7 +364,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    if args.only == "fused":
+    if args.only != "all":
         ms_e, launches_e = [float("nan")], 0
     else:
         ms_e, launches_e = time_steps(torch, lambda: band_step(eager), max(args.steps // 2, 5), max(args.warmup, 3),
@@ -372,7 +373,7 @@ def run_ours(args):
 
     # end-to-end through the public API: pinned host x in, sum out, every step
     x_pinned = torch.from_numpy(x_host).pin_memory()
-    e2e_steps = 0 if args.only == "fused" else max(3, min(args.steps, 20))
+    e2e_steps = 0 if args.only != "all" else max(3, min(args.steps, 20))
     for _ in range(2 if e2e_steps else 0):
         fused.write_field(0, x_pinned)
         band_step(fused)
@@ -400,12 +401,14 @@ def run_ours(args):
     traffic = traffic_record(kernel_src)
 
     extra = {}
-    if world == 1 and args.only == "all":
+    if world == 1 and args.only != "fused":
         k = max(5, min(args.steps, 20))
         for name, fn in (("band1024", lambda: bench_band1024(torch, sg, k, 3, flush_buf, stream)),
                          ("batched", lambda: bench_batched(torch, sg, k, 3, flush_buf, stream)),
                          ("particles", lambda: bench_particles(torch, sg, k, 3, stream)),
                          ("serving", lambda: bench_serving(torch, sg))):
+            if args.only not in ("all", name):
+                continue
             try:
                 t0 = time.perf_counter()
                 extra[name] = fn()
@@ -416,7 +419,7 @@ def run_ours(args):
 
     if rank == 0:
         cpu = None
-        if world == 1 and not args.no_cpu_baseline and args.only != "fused":
+        if world == 1 and not args.no_cpu_baseline and args.only == "all":
             cpu = cpu_baseline(spec, leaf_b, x_host, n_active, budget_s=args.cpu_budget)
         line = {
             "metric": METRIC,
@@ -532,8 +535,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--variant", type=int, default=0, help="stencil kernel family (0 sweep, 1 smem)")
-    ap.add_argument("--only", choices=["all", "fused"], default="all",
-                    help="fused: time only the fused headline step (for profiling runs)")
+    ap.add_argument("--only", choices=["all", "fused", "band1024", "batched", "particles", "serving"], default="all",
+                    help="fused: only the fused headline step; a leg name: the headline step and that leg "
+                         "(for profiling runs)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
