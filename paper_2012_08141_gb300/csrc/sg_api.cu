@@ -94,6 +94,9 @@ struct sg_grid {
     std::vector<void *> blocks;
     Ctrl *host_ctrl = nullptr;  // pinned
     size_t staging_bytes = 0;
+    long long perm_cap = 0;  // particles the binned-P2G order array holds
+    const void *p2g_x = nullptr;  // positions and count the order array was built for
+    long long p2g_n = 0;
 };
 
 namespace {
@@ -270,6 +273,29 @@ int run_struct_for_group(sg_grid *g, size_t &i)
     return after_launch(g, "stencil");
 }
 
+// Binned-P2G scratch: bin counts and offsets over the root cells, the count
+// scan's tile sums, and a particle order array of at least n entries.
+int ensure_p2g_scratch(sg_grid *g, long long n)
+{
+    if (g->dry) return SG_OK;
+    const long long nbins = (long long)g->dev.R * g->dev.R * g->dev.R;
+    if (!g->dev.bin_count) {
+        g->dev.bin_count = (int32_t *)dev_alloc(g, sizeof(int32_t) * (nbins + 1));
+        g->dev.bin_off = (int32_t *)dev_alloc(g, sizeof(int32_t) * (nbins + 1));
+        g->dev.tile_sum = (int32_t *)dev_alloc(g, sizeof(int32_t) * (nbins / 1024 + 2));
+        g->dev.bin_list = (int32_t *)dev_alloc(g, sizeof(int32_t) * (nbins + 1));
+        if (!g->dev.bin_count || !g->dev.bin_off || !g->dev.tile_sum || !g->dev.bin_list)
+            return fail(SG_ERR_OOM, "p2g bins");
+    }
+    if (n > g->perm_cap) {
+        const long long cap = std::max(n, g->perm_cap * 2);
+        g->dev.perm = (int32_t *)dev_alloc(g, sizeof(int32_t) * cap);
+        if (!g->dev.perm) return fail(SG_ERR_OOM, "p2g order of %lld particles", cap);
+        g->perm_cap = cap;
+    }
+    return SG_OK;
+}
+
 int do_flush(sg_grid *g)
 {
     int rc = SG_OK;
@@ -333,15 +359,14 @@ int do_flush(sg_grid *g)
                 rc = run_struct_for_group(g, i);
                 break;
             case OP_P2G:
-                if (!g->dry) launch_p2g_mark(g->dev, g->stream, (const float *)o.p0, o.n);
-                if (!(rc = after_launch(g, "p2g mark"))) {
-                    if (!g->dry) launch_alloc_needed(g->dev, g->stream);
-                    if (!(rc = after_launch(g, "allocate"))) {
-                        if (!g->dry)
-                            launch_p2g_scatter(g->dev, g->stream, (const float *)o.p0, (const float *)o.p1, o.n, o.f0,
-                                               o.i0, o.i1);
-                        rc = after_launch(g, "p2g scatter");
-                    }
+                if (!(rc = ensure_p2g_scratch(g, o.n))) {
+                    const int k = g->dry ? 7
+                                         : launch_p2g_binned(g->dev, g->stream, (const float *)o.p0,
+                                                             (const float *)o.p1, o.n, o.f0, o.i0, o.i1, g->lc);
+                    g->stats.launches += k - 1;
+                    rc = after_launch(g, "binned p2g");
+                    g->p2g_x = o.p0;
+                    g->p2g_n = o.n;
                 }
                 g->mask_ver++;
                 g->stats.act_launched++;
@@ -355,7 +380,9 @@ int do_flush(sg_grid *g)
                 ++i;
                 break;
             case OP_G2P:
-                if (!g->dry) launch_g2p(g->dev, g->stream, (float *)o.p1, (float *)o.p2, o.n, o.f0, o.i0);
+                if (!g->dry)
+                    launch_g2p(g->dev, g->stream, (float *)o.p1, (float *)o.p2, o.n, o.f0, o.i0,
+                               (o.p1 == g->p2g_x && o.n == g->p2g_n) ? g->dev.perm : nullptr);
                 rc = after_launch(g, "g2p");
                 ++i;
                 break;
