@@ -33,7 +33,7 @@ def build(force: bool = False) -> str:
                  or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC))
         if force or stale:
             tmp = _LIB_PATH + f".tmp{os.getpid()}"
-            cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared",
+            cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
                    "-o", tmp, _SRC, "-lm"]
             subprocess.run(cmd, check=True)
             os.replace(tmp, _LIB_PATH)

@@ -279,10 +279,11 @@ int ensure_p2g_scratch(sg_grid *g, long long n)
 {
     if (g->dry) return SG_OK;
     const long long nbins = (long long)g->dev.R * g->dev.R * g->dev.R;
+    const long long nkeys = p2g_num_keys(g->dev.R);
     if (!g->dev.bin_count) {
-        g->dev.bin_count = (int32_t *)dev_alloc(g, sizeof(int32_t) * (nbins + 1));
-        g->dev.bin_off = (int32_t *)dev_alloc(g, sizeof(int32_t) * (nbins + 1));
-        g->dev.tile_sum = (int32_t *)dev_alloc(g, sizeof(int32_t) * (nbins / 1024 + 2));
+        g->dev.bin_count = (int32_t *)dev_alloc(g, sizeof(int32_t) * nkeys);
+        g->dev.bin_off = (int32_t *)dev_alloc(g, sizeof(int32_t) * nkeys);
+        g->dev.tile_sum = (int32_t *)dev_alloc(g, sizeof(int32_t) * (nkeys / 1024 + 2));
         g->dev.bin_list = (int32_t *)dev_alloc(g, sizeof(int32_t) * (nbins + 1));
         if (!g->dev.bin_count || !g->dev.bin_off || !g->dev.tile_sum || !g->dev.bin_list)
             return fail(SG_ERR_OOM, "p2g bins");
@@ -382,7 +383,7 @@ int do_flush(sg_grid *g)
             case OP_G2P:
                 if (!g->dry)
                     launch_g2p(g->dev, g->stream, (float *)o.p1, (float *)o.p2, o.n, o.f0, o.i0,
-                               (o.p1 == g->p2g_x && o.n == g->p2g_n) ? g->dev.perm : nullptr);
+                               o.p1 == g->p2g_x && o.n == g->p2g_n, g->lc);
                 rc = after_launch(g, "g2p");
                 ++i;
                 break;

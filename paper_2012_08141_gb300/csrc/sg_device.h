@@ -46,7 +46,7 @@ struct Ctrl {
     unsigned int red_ticket;       // reduction finished CTAs (reset by the last)
     int32_t never_set;    // a flag nothing writes (bounded-wait test)
     int32_t timeout_site; // which wait gave up (0 none, 1 look-back, 2 test)
-    int32_t bins_used;    // non-empty bins of the last binned P2G
+    int32_t bins_used;    // leaves holding particles in the last binned P2G
     int32_t pad[2];
 };
 
@@ -67,13 +67,13 @@ struct DevGrid {
     Ctrl *ctrl;
     float *staging;      // n * L^3 floats for host reads/writes
     uint32_t *staging_u; // aliases staging for mask gathers
-    // binned P2G scratch (allocated at the first P2G): per-bin counts/cursors
-    // and offsets (R^3 each), tile sums of the count scan, particle order
+    // binned P2G scratch (allocated at the first P2G): per-key counts/cursors
+    // and offsets, tile sums of the count scan, particle order
     int32_t *bin_count;
     int32_t *bin_off;
     int32_t *tile_sum;
     int32_t *perm;
-    int32_t *bin_list;  // the non-empty bins, in no particular order
+    int32_t *bin_list;  // the leaves holding particles, in no particular order
 };
 
 // Stencil kernel families for 8^3 leaves (the autotuner picks one).
@@ -160,18 +160,19 @@ void launch_sweep_single(const DevGrid &g, cudaStream_t s, int op, int src, int 
                          int sum_slot, const LaunchCfg &lc);
 
 // ---- particle kernels (sg_particle.cu) ----
-void launch_p2g_mark(const DevGrid &g, cudaStream_t s, const float *x, long long n);
-void launch_p2g_scatter(const DevGrid &g, cudaStream_t s, const float *x, const float *v,
-                        long long n, float pmass, int f_mass, int f_mom0);
 // Binned P2G (count, allocate, scan, order, accumulate per bin); returns the
-// number of kernels launched.  Needs bin_count/bin_off/tile_sum/perm.
+// number of kernels launched.  Needs bin_count/bin_off (p2g_num_keys each),
+// tile_sum, perm and bin_list (R^3).  Keys: 8 reach classes per leaf plus one
+// for particles whose stencil misses the domain.
+constexpr long long p2g_num_keys(int R) { return 8LL * R * R * R + 1; }
 int launch_p2g_binned(const DevGrid &g, cudaStream_t s, const float *x, const float *v, long long n, float pmass,
                       int f_mass, int f_mom0, const LaunchCfg &lc);
 void launch_grid_update(const DevGrid &g, cudaStream_t s, int f_mass, int f_mom0, float dt,
                         float gz, int bound, const LaunchCfg &lc);
-// order: NULL, or a permutation of [0, n) to visit particles in (the bin
-// order of the last binned P2G over the same positions, for locality).
-void launch_g2p(const DevGrid &g, cudaStream_t s, float *x, float *v, long long n, float dt, int f_mom0,
-                const int32_t *order);
+// binned: use the bins of the last binned P2G over the same particles (the
+// particle order, leaf list and key ranges) to stage each leaf's
+// neighbourhood of node velocities in shared memory; otherwise input order.
+void launch_g2p(const DevGrid &g, cudaStream_t s, float *x, float *v, long long n, float dt, int f_mom0, int binned,
+                const LaunchCfg &lc);
 
 }  // namespace sg

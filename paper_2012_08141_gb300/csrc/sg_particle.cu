@@ -12,107 +12,21 @@ struct Spline {
     float w[3];
 };
 
-// base = floor(X - 0.5), fx = X - base, X = x*N, all in FP32.
+// base = floor(X - 0.5), fx = X - base, X = x*N, all in FP32, each operation
+// rounded on its own (no contraction), so that every kernel that bins a
+// particle takes the same base.
 __device__ __forceinline__ Spline bspline(float x, int N)
 {
     Spline s;
-    const float X = x * (float)N;
-    const float bf = floorf(X - 0.5f);
-    const float fx = X - bf;
+    const float X = __fmul_rn(x, (float)N);
+    const float bf = floorf(__fsub_rn(X, 0.5f));
+    const float fx = __fsub_rn(X, bf);
     s.base = (int)bf;
     const float a = 1.5f - fx, c = fx - 1.0f, d = fx - 0.5f;
     s.w[0] = 0.5f * a * a;
     s.w[1] = 0.75f - c * c;
     s.w[2] = 0.5f * d * d;
     return s;
-}
-
-// Mark the pointer cells the particle's 27 stencil nodes fall in.
-__global__ void k_p2g_mark(DevGrid g, const float *__restrict__ x, long long n)
-{
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
-        int lo[3], hi[3];
-        bool empty = false;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const Spline s = bspline(__ldg(x + 3 * p + a), g.N);
-            const int n0 = max(s.base, 0), n1 = min(s.base + 2, g.N - 1);
-            if (n0 > n1) empty = true;
-            lo[a] = n0 >> g.lg2;
-            hi[a] = n1 >> g.lg2;
-        }
-        if (empty) continue;
-        for (int bi = lo[0]; bi <= hi[0]; ++bi)
-            for (int bj = lo[1]; bj <= hi[1]; ++bj)
-                for (int bk = lo[2]; bk <= hi[2]; ++bk) g.need[((long long)bi * g.R + bj) * g.R + bk] = 1;
-    }
-}
-
-void launch_p2g_mark(const DevGrid &g, cudaStream_t s, const float *x, long long n)
-{
-    if (n <= 0) return;
-    long long blocks = (n + 255) / 256;
-    if (blocks > 1 << 20) blocks = 1 << 20;
-    k_p2g_mark<<<(unsigned)blocks, 256, 0, s>>>(g, x, n);
-}
-
-// Scatter: set the node bits and accumulate mass and momentum with FP32
-// atomics (the accumulation order is unspecified).
-__global__ void __launch_bounds__(256) k_p2g_scatter(DevGrid g, const float *__restrict__ x, const float *__restrict__ v,
-                                                     long long n, float pmass, int f_mass, int f_mom0)
-{
-    const int L = g.L, lg2 = g.lg2, N = g.N;
-    float *fm = g.field[f_mass];
-    float *f0 = g.field[f_mom0], *f1 = g.field[f_mom0 + 1], *f2 = g.field[f_mom0 + 2];
-    bool changed = false;
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
-        const Spline sx = bspline(__ldg(x + 3 * p + 0), N);
-        const Spline sy = bspline(__ldg(x + 3 * p + 1), N);
-        const Spline sz = bspline(__ldg(x + 3 * p + 2), N);
-        const float vx = __ldg(v + 3 * p + 0), vy = __ldg(v + 3 * p + 1), vz = __ldg(v + 3 * p + 2);
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const int i = sx.base + a;
-            if ((unsigned)i >= (unsigned)N) continue;
-#pragma unroll
-            for (int b = 0; b < 3; ++b) {
-                const int j = sy.base + b;
-                if ((unsigned)j >= (unsigned)N) continue;
-                const float wxy = sx.w[a] * sy.w[b];
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    const int k = sz.base + c;
-                    if ((unsigned)k >= (unsigned)N) continue;
-                    const long long lb = ((long long)(i >> lg2) * g.R + (j >> lg2)) * g.R + (k >> lg2);
-                    const int slot = g.root[lb];
-                    if (slot < 0) continue;  // pool exhausted; error latched
-                    const int l = (((i & (L - 1)) << lg2) + (j & (L - 1))) * L + (k & (L - 1));
-                    uint32_t *mw = &g.mask[(long long)slot * g.W + (l >> 5)];
-                    const uint32_t bit = 1u << (l & 31);
-                    if (!(*mw & bit)) {
-                        const uint32_t old = atomicOr(mw, bit);
-                        if (!(old & bit)) changed = true;
-                    }
-                    const long long idx = ((long long)slot << (3 * lg2)) + l;
-                    const float wm = wxy * sz.w[c] * pmass;
-                    atomicAdd(fm + idx, wm);
-                    atomicAdd(f0 + idx, wm * vx);
-                    atomicAdd(f1 + idx, wm * vy);
-                    atomicAdd(f2 + idx, wm * vz);
-                }
-            }
-        }
-    }
-    if (changed) mark_dirty(g);
-}
-
-void launch_p2g_scatter(const DevGrid &g, cudaStream_t s, const float *x, const float *v, long long n, float pmass,
-                        int f_mass, int f_mom0)
-{
-    if (n <= 0) return;
-    long long blocks = (n + 255) / 256;
-    if (blocks > 1 << 20) blocks = 1 << 20;
-    k_p2g_scatter<<<(unsigned)blocks, 256, 0, s>>>(g, x, v, n, pmass, f_mass, f_mom0);
 }
 
 // Grid update over the active nodes of the listed leaves.
@@ -154,59 +68,188 @@ void launch_grid_update(const DevGrid &g, cudaStream_t s, int f_mass, int f_mom0
     k_grid_update<<<lc.num_sms * 8, 256, 0, s>>>(g, f_mass, f_mom0, dt, gz, bound);
 }
 
-// G2P: gather the node velocities (a stored value at an inactive node is 0)
-// and advect the particle.
-__global__ void __launch_bounds__(256) k_g2p(DevGrid g, float *__restrict__ x, float *__restrict__ v, long long n, float dt,
-                                             int f_mom0, const int32_t *__restrict__ order)
+// G2P velocity of one particle read node by node from the grid (a stored
+// value at an inactive node is 0; out-of-domain and unallocated nodes are
+// skipped).
+__device__ __forceinline__ float3 g2p_from_grid(const DevGrid &g, const float *__restrict__ f0,
+                                               const float *__restrict__ f1, const float *__restrict__ f2,
+                                               const Spline &sx, const Spline &sy, const Spline &sz)
 {
     const int L = g.L, lg2 = g.lg2, N = g.N;
-    const float *f0 = g.field[f_mom0], *f1 = g.field[f_mom0 + 1], *f2 = g.field[f_mom0 + 2];
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
-        const long long p = order ? (long long)__ldg(order + q) : q;  // any order: particles are independent
-        const float px = x[3 * p], py = x[3 * p + 1], pz = x[3 * p + 2];
-        const Spline sx = bspline(px, N), sy = bspline(py, N), sz = bspline(pz, N);
-        float ux = 0.f, uy = 0.f, uz = 0.f;
+    float ux = 0.f, uy = 0.f, uz = 0.f;
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const int i = sx.base + a;
-            if ((unsigned)i >= (unsigned)N) continue;
+    for (int a = 0; a < 3; ++a) {
+        const int i = sx.base + a;
+        if ((unsigned)i >= (unsigned)N) continue;
 #pragma unroll
-            for (int b = 0; b < 3; ++b) {
-                const int j = sy.base + b;
-                if ((unsigned)j >= (unsigned)N) continue;
-                const float wxy = sx.w[a] * sy.w[b];
+        for (int b = 0; b < 3; ++b) {
+            const int j = sy.base + b;
+            if ((unsigned)j >= (unsigned)N) continue;
+            const float wxy = sx.w[a] * sy.w[b];
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    const int k = sz.base + c;
-                    if ((unsigned)k >= (unsigned)N) continue;
-                    const long long lb = ((long long)(i >> lg2) * g.R + (j >> lg2)) * g.R + (k >> lg2);
-                    const int slot = __ldg(g.root + lb);
-                    if (slot < 0) continue;
-                    const int l = (((i & (L - 1)) << lg2) + (j & (L - 1))) * L + (k & (L - 1));
-                    const long long idx = ((long long)slot << (3 * lg2)) + l;
-                    const float w = wxy * sz.w[c];
-                    ux += w * __ldg(f0 + idx);
-                    uy += w * __ldg(f1 + idx);
-                    uz += w * __ldg(f2 + idx);
-                }
+            for (int c = 0; c < 3; ++c) {
+                const int k = sz.base + c;
+                if ((unsigned)k >= (unsigned)N) continue;
+                const long long lb = ((long long)(i >> lg2) * g.R + (j >> lg2)) * g.R + (k >> lg2);
+                const int slot = __ldg(g.root + lb);
+                if (slot < 0) continue;
+                const int l = (((i & (L - 1)) << lg2) + (j & (L - 1))) * L + (k & (L - 1));
+                const long long idx = ((long long)slot << (3 * lg2)) + l;
+                const float w = wxy * sz.w[c];
+                ux += w * __ldg(f0 + idx);
+                uy += w * __ldg(f1 + idx);
+                uz += w * __ldg(f2 + idx);
             }
         }
-        v[3 * p] = ux;
-        v[3 * p + 1] = uy;
-        v[3 * p + 2] = uz;
-        x[3 * p] = px + dt * ux;
-        x[3 * p + 1] = py + dt * uy;
-        x[3 * p + 2] = pz + dt * uz;
+    }
+    return make_float3(ux, uy, uz);
+}
+
+// A float triple at a[3p..3p+2]; with pair set (the array is 8-byte
+// aligned) in two accesses: the aligned pair (elements 0,1 for even p, 1,2
+// for odd p) and the remaining single.
+__device__ __forceinline__ float3 load3(const float *__restrict__ a, long long p, bool pair)
+{
+    const float *q = a + 3 * p;
+    if (!pair) return make_float3(q[0], q[1], q[2]);
+    if (p & 1) {
+        const float2 hi = *reinterpret_cast<const float2 *>(q + 1);
+        return make_float3(q[0], hi.x, hi.y);
+    }
+    const float2 lo = *reinterpret_cast<const float2 *>(q);
+    return make_float3(lo.x, lo.y, q[2]);
+}
+
+__device__ __forceinline__ void store3(float *__restrict__ a, long long p, float3 t, bool pair)
+{
+    float *q = a + 3 * p;
+    if (!pair) {
+        q[0] = t.x;
+        q[1] = t.y;
+        q[2] = t.z;
+    } else if (p & 1) {
+        q[0] = t.x;
+        *reinterpret_cast<float2 *>(q + 1) = make_float2(t.y, t.z);
+    } else {
+        *reinterpret_cast<float2 *>(q) = make_float2(t.x, t.y);
+        q[2] = t.z;
     }
 }
 
-void launch_g2p(const DevGrid &g, cudaStream_t s, float *x, float *v, long long n, float dt, int f_mom0,
-                const int32_t *order)
+__device__ __forceinline__ void g2p_store(float *__restrict__ x, float *__restrict__ v, long long p, float px, float py,
+                                          float pz, float3 u, float dt, bool pair)
+{
+    store3(v, p, u, pair);
+    store3(x, p, make_float3(px + dt * u.x, py + dt * u.y, pz + dt * u.z), pair);
+}
+
+// G2P in input order, every node read from the grid.
+__global__ void __launch_bounds__(256) k_g2p(DevGrid g, float *__restrict__ x, float *__restrict__ v, long long n, float dt,
+                                             int f_mom0)
+{
+    const float *f0 = g.field[f_mom0], *f1 = g.field[f_mom0 + 1], *f2 = g.field[f_mom0 + 2];
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
+        const float px = x[3 * p], py = x[3 * p + 1], pz = x[3 * p + 2];
+        const Spline sx = bspline(px, g.N), sy = bspline(py, g.N), sz = bspline(pz, g.N);
+        g2p_store(x, v, p, px, py, pz, g2p_from_grid(g, f0, f1, f2, sx, sy, sz), dt, false);
+    }
+}
+
+// G2P over the bins of the last binned P2G: per leaf, the node velocities of
+// the (L+4)^3 nodes from o - 2 to o + L + 1 (o the leaf origin; every node a
+// stencil with base in [o - 2, o + L - 1] reaches) are staged in shared
+// memory, 0 outside the domain or the allocated leaves, and the leaf's
+// particles read their 27 nodes there.  A particle whose base lies outside
+// that range (its position changed since the binning) reads the grid node by
+// node, as do the particles whose stencil misses the domain (the last key).
+template <int L>
+__global__ void __launch_bounds__(256, 6) k_g2p_binned(DevGrid g, float *__restrict__ x, float *__restrict__ v, float dt,
+                                                       int f_mom0, bool pair)
+{
+    constexpr int LG2 = (L == 8) ? 3 : 2, B = L + 4, NB = B * B * B;
+    __shared__ float s_u[3][NB];
+    const int N = g.N, R = g.R;
+    const float *f0 = g.field[f_mom0], *f1 = g.field[f_mom0 + 1], *f2 = g.field[f_mom0 + 2];
+    const int used = g.ctrl->bins_used;
+    const long long oob_key = 8LL * R * R * R;
+    for (int bl = blockIdx.x; bl <= used; bl += gridDim.x) {
+        int beg, end, oi = 0, oj = 0, ok = 0;
+        if (bl < used) {
+            const long long b = g.bin_list[bl];
+            beg = g.bin_off[8 * b];
+            end = g.bin_count[8 * b + 7];
+            oi = (int)(b / ((long long)R * R)) * L;
+            oj = (int)((b / R) % R) * L;
+            ok = (int)(b % R) * L;
+            for (int nd = threadIdx.x; nd < NB; nd += 256) {
+                const int i = oi - 2 + nd / (B * B), j = oj - 2 + (nd / B) % B, k = ok - 2 + nd % B;
+                float u0 = 0.f, u1 = 0.f, u2 = 0.f;
+                if ((unsigned)i < (unsigned)N && (unsigned)j < (unsigned)N && (unsigned)k < (unsigned)N) {
+                    const int slot = __ldg(g.root + ((long long)(i >> LG2) * R + (j >> LG2)) * R + (k >> LG2));
+                    if (slot >= 0) {
+                        const long long idx =
+                            ((long long)slot << (3 * LG2)) + (((i & (L - 1)) << LG2) + (j & (L - 1))) * L + (k & (L - 1));
+                        u0 = __ldg(f0 + idx);
+                        u1 = __ldg(f1 + idx);
+                        u2 = __ldg(f2 + idx);
+                    }
+                }
+                s_u[0][nd] = u0;
+                s_u[1][nd] = u1;
+                s_u[2][nd] = u2;
+            }
+            __syncthreads();
+        } else {
+            beg = g.bin_off[oob_key];
+            end = g.bin_count[oob_key];
+        }
+        for (int q = beg + threadIdx.x; q < end; q += blockDim.x) {
+            const long long p = g.perm[q];
+            const float3 xp = load3(x, p, pair);
+            const float px = xp.x, py = xp.y, pz = xp.z;
+            const Spline sx = bspline(px, N), sy = bspline(py, N), sz = bspline(pz, N);
+            const int ri = sx.base - oi + 2, rj = sy.base - oj + 2, rk = sz.base - ok + 2;
+            float3 u;
+            if (bl < used && (unsigned)ri <= (unsigned)(L + 1) && (unsigned)rj <= (unsigned)(L + 1) &&
+                (unsigned)rk <= (unsigned)(L + 1)) {
+                float ux = 0.f, uy = 0.f, uz = 0.f;
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+#pragma unroll
+                    for (int b = 0; b < 3; ++b) {
+                        const float wxy = sx.w[a] * sy.w[b];
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            const int nd = ((ri + a) * B + (rj + b)) * B + (rk + c);
+                            const float w = wxy * sz.w[c];
+                            ux += w * s_u[0][nd];
+                            uy += w * s_u[1][nd];
+                            uz += w * s_u[2][nd];
+                        }
+                    }
+                u = make_float3(ux, uy, uz);
+            } else {
+                u = g2p_from_grid(g, f0, f1, f2, sx, sy, sz);
+            }
+            g2p_store(x, v, p, px, py, pz, u, dt, pair);
+        }
+        __syncthreads();  // s_u is restaged for the next leaf
+    }
+}
+
+void launch_g2p(const DevGrid &g, cudaStream_t s, float *x, float *v, long long n, float dt, int f_mom0, int binned,
+                const LaunchCfg &lc)
 {
     if (n <= 0) return;
+    if (binned) {
+        const bool pair = ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(v)) & 7) == 0;
+        if (g.L == 4) k_g2p_binned<4><<<lc.num_sms * 6, 256, 0, s>>>(g, x, v, dt, f_mom0, pair);
+        else k_g2p_binned<8><<<lc.num_sms * 6, 256, 0, s>>>(g, x, v, dt, f_mom0, pair);
+        return;
+    }
     long long blocks = (n + 255) / 256;
     if (blocks > 1 << 20) blocks = 1 << 20;
-    k_g2p<<<(unsigned)blocks, 256, 0, s>>>(g, x, v, n, dt, f_mom0, order);
+    k_g2p<<<(unsigned)blocks, 256, 0, s>>>(g, x, v, n, dt, f_mom0);
 }
 
 }  // namespace sg
@@ -217,70 +260,75 @@ void launch_g2p(const DevGrid &g, cudaStream_t s, float *x, float *v, long long 
 // accumulate into a shared-memory block of (L+2)^3 nodes (every node their
 // stencils can reach), and each block is added to the grid once.  Global
 // atomics drop from 27 x 4 per particle to 4 per touched block node, and
-// inside a block no atomic is needed at all (a gather per node).
-//   1. k_p2g_bin     mark the pointer cells to activate; count particles per bin
-//   2. (allocation of the marked cells: k_alloc_needed)
-//   3. k_bin_scan_*  exclusive scan of the counts (tile sums, top scan, apply);
-//                    the count array becomes each bin's insertion cursor
+// shared-memory atomics to 27 x 4 per occupied cell.
+//   1. k_p2g_bin     count particles per key (bin leaf x reach class)
+//   2. k_bin_scan_tiles  tile sums of the counts; mark the leaves the occupied
+//                    keys reach; k_alloc_needed allocates them
+//   3. k_bin_scan_top / _apply  exclusive scan of the counts (the count array
+//                    becomes each key's insertion cursor); list of occupied leaves
 //   4. k_p2g_perm    write particle indices in bin order
 //   5. k_p2g_gather  per bin: sort the bin's particles by cell in shared
-//                    memory, sum each block node's contributions in registers,
-//                    then add the touched nodes to the grid and set their bits
+//                    memory, sum each cell's contributions to its 27 nodes in
+//                    registers (one warp per cell) into shared node sums, then
+//                    add the touched nodes to the grid and set their bits
 // ===========================================================================
 namespace sg {
 
 constexpr int kBinTile = 1024;
 
-__device__ __forceinline__ int p2g_bin_of(const float *__restrict__ x, long long p, int N, int lg2, int R)
+// Bin key of a particle: 8 * (leaf of its base node) + reach class, where
+// bit 2 / 1 / 0 of the class says that the in-domain part of the stencil
+// extends into the next leaf along i / j / k.  A particle with no stencil
+// node inside the domain gets the key 8 R^3, one past the last leaf.  The
+// base leaf is that of max(base, 0): base is at least -2 for a non-empty
+// stencil, and -2 / -1 lie below leaf 0.
+__device__ __forceinline__ long long p2g_key_of(const float *__restrict__ x, long long p, int N, int lg2, int R)
 {
-    int c[3];
+    long long leaf = 0;
+    int cls = 0;
+    bool empty = false;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         const Spline s = bspline(__ldg(x + 3 * p + a), N);
-        c[a] = min(max(s.base, 0), N - 1) >> lg2;
+        const int n0 = max(s.base, 0), n1 = min(s.base + 2, N - 1);
+        empty |= n0 > n1;
+        leaf = leaf * R + (n0 >> lg2);
+        cls = (cls << 1) | ((n1 >> lg2) != (n0 >> lg2) ? 1 : 0);
     }
-    return (c[0] * R + c[1]) * R + c[2];
+    return empty ? 8LL * R * R * R : leaf * 8 + cls;
 }
 
 __global__ void k_p2g_bin(DevGrid g, const float *__restrict__ x, long long n)
 {
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
-        int lo[3], hi[3], c[3];
-        bool empty = false;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const Spline s = bspline(__ldg(x + 3 * p + a), g.N);
-            const int n0 = max(s.base, 0), n1 = min(s.base + 2, g.N - 1);
-            if (n0 > n1) empty = true;
-            lo[a] = n0 >> g.lg2;
-            hi[a] = n1 >> g.lg2;
-            c[a] = min(max(s.base, 0), g.N - 1) >> g.lg2;
-        }
-        const long long nbins = (long long)g.R * g.R * g.R;
-        if (empty) {  // no stencil node inside the domain: the extra bin nbins
-            atomicAdd(&g.bin_count[nbins], 1);
-            continue;
-        }
-        for (int bi = lo[0]; bi <= hi[0]; ++bi)
-            for (int bj = lo[1]; bj <= hi[1]; ++bj)
-                for (int bk = lo[2]; bk <= hi[2]; ++bk) {
-                    uint8_t *nd = &g.need[((long long)bi * g.R + bj) * g.R + bk];
-                    // most cells are marked already: read through L2 (coherent across SMs) and skip
-                    // the same-address store
-                    if (!__ldcg(nd)) *nd = 1;
-                }
-        atomicAdd(&g.bin_count[((long long)c[0] * g.R + c[1]) * g.R + c[2]], 1);
-    }
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x)
+        atomicAdd(&g.bin_count[p2g_key_of(x, p, g.N, g.lg2, g.R)], 1);
 }
 
-// Sum of each tile of kBinTile counts.
-__global__ void __launch_bounds__(256) k_bin_scan_tiles(DevGrid g, long long nbins)
+// Sum of each tile of kBinTile counts; for every occupied key, mark the
+// leaves its particles' stencils reach (the base leaf plus the neighbours in
+// the directions of its reach class) for allocation.
+__global__ void __launch_bounds__(256) k_bin_scan_tiles(DevGrid g, long long nkeys)
 {
     __shared__ int s_w[8];
     const long long base = (long long)blockIdx.x * kBinTile;
+    const long long nleaf_keys = nkeys - 1;  // the last key holds particles outside the domain
+    const int R = g.R;
     int v = 0;
-    for (int q = threadIdx.x; q < kBinTile; q += 256)
-        if (base + q < nbins) v += g.bin_count[base + q];
+    for (int q = threadIdx.x; q < kBinTile; q += 256) {
+        const long long key = base + q;
+        const int c = (key < nkeys) ? g.bin_count[key] : 0;
+        v += c;
+        if (c > 0 && key < nleaf_keys) {
+            const long long leaf = key >> 3;
+            const int cls = (int)(key & 7);
+            const int li = (int)(leaf / ((long long)R * R)), lj = (int)((leaf / R) % R), lk = (int)(leaf % R);
+            for (int sub = cls;; sub = (sub - 1) & cls) {  // every subset of the class, itself and 0 included
+                const long long t = ((long long)(li + (sub >> 2)) * R + (lj + ((sub >> 1) & 1))) * R + (lk + (sub & 1));
+                g.need[t] = 1;
+                if (sub == 0) break;
+            }
+        }
+    }
     v = warp_sum(v);
     if (lane_id() == 0) s_w[threadIdx.x >> 5] = v;
     __syncthreads();
@@ -343,95 +391,94 @@ __global__ void __launch_bounds__(256) k_bin_scan_apply(DevGrid g, long long nbi
         }
         run += v[q];
     }
-    // list of the non-empty bins of the grid (the last, out-of-domain bin excluded)
-    const long long real = nbins - 1;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const bool want = (base + q < real) && v[q] > 0;
-        const unsigned m = __ballot_sync(kFull, want);
-        if (!m) continue;
+    // list of the leaves with particles (the 8 keys of a leaf are held by an
+    // even and the next odd thread; the out-of-domain key is excluded)
+    const long long nleaves = (nbins - 1) >> 3;
+    const int mine = t + __shfl_xor_sync(kFull, t, 1);
+    const long long leaf = base >> 3;
+    const bool want = !(threadIdx.x & 1) && mine > 0 && leaf < nleaves;
+    const unsigned m = __ballot_sync(kFull, want);
+    if (m) {
         const int leader = __ffs(m) - 1;
         int first = 0;
         if (lane_id() == leader) first = atomicAdd(&g.ctrl->bins_used, __popc(m));
         first = __shfl_sync(kFull, first, leader);
-        if (want) g.bin_list[first + __popc(m & lanemask_lt())] = (int32_t)(base + q);
+        if (want) g.bin_list[first + __popc(m & lanemask_lt())] = (int32_t)leaf;
     }
 }
 
 __global__ void k_p2g_perm(DevGrid g, const float *__restrict__ x, long long n)
 {
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
-        bool empty = false;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const Spline s = bspline(__ldg(x + 3 * p + a), g.N);
-            if (max(s.base, 0) > min(s.base + 2, g.N - 1)) empty = true;
-        }
-        const int b = empty ? g.R * g.R * g.R : p2g_bin_of(x, p, g.N, g.lg2, g.R);
-        const int pos = atomicAdd(&g.bin_count[b], 1);
+        const int pos = atomicAdd(&g.bin_count[p2g_key_of(x, p, g.N, g.lg2, g.R)], 1);
         g.perm[pos] = (int)p;
     }
 }
 
 // Per bin: stage the bin's particles (stencil weights and pmass * velocity)
-// in shared memory sorted by their base cell, then let one thread per block
-// node sum, in registers, the contributions of the particles in the 27 cells
-// whose stencils reach that node.  A node whose stencil set is non-empty is
-// activated (all 27 stencil nodes of every particle are, whatever their
-// weight) and its sums are added to the grid.  Bins with more particles than
-// the staging capacity are processed in chunks.
+// in shared memory sorted by their base cell.  One warp then takes one
+// occupied cell at a time: lane (a, c, d) < 27 owns the stencil node
+// base + (a, c, d) shared by every particle of that cell and walks the
+// cell's particles in step with the other lanes (each shared-memory read is a
+// broadcast), summing its node's contributions in registers; the cell's 27
+// sums are then added to a shared block of (L+2)^3 node accumulators.  A node
+// reached by any stencil is activated (all 27 stencil nodes of every particle
+// are, whatever their weight) and its sums are added to the grid once.  Bins
+// with more particles than the staging capacity are processed in chunks.
+//
+// Base cells are indexed relative to the leaf origin o shifted by +2: a
+// particle binned to leaf o has base in [o, o + L - 1], or base -2 / -1 at the
+// low domain face (its bin is clamped to leaf 0), so the shifted index is in
+// [0, L + 1].  Block node n (0 <= n < L + 2 per axis) is grid node o + n.
 template <int L>
 __global__ void __launch_bounds__(256) k_p2g_gather(DevGrid g, const float *__restrict__ x, const float *__restrict__ v,
                                                     float pmass, int f_mass, int f_mom0)
 {
     constexpr int B = L + 2, NB = B * B * B, LG2 = (L == 8) ? 3 : 2;
-    constexpr int C1 = L + 1, NC = C1 * C1 * C1;  // base cells relative to the leaf origin, shifted by +1
-    constexpr int CAP = (L == 8) ? 512 : 768;       // staged particles per chunk
-    constexpr int NPER = (NB + 255) / 256;          // block nodes per thread
-    __shared__ float s_w[CAP][9];                   // weights w[axis][0..2]
-    __shared__ float s_mv[CAP][4];                  // pmass, pmass * v
-    __shared__ uint16_t s_cell[CAP];
-    __shared__ uint16_t s_sorted[CAP];
+    constexpr int C1 = L + 2, NC = C1 * C1 * C1;  // shifted base cells
+    constexpr int CAP = (L == 8) ? 256 : 512;       // staged particles per chunk
+    constexpr int PPT = CAP / 256;                  // staged particles per thread
+    constexpr int NWARP = 8;
+    __shared__ float s_w[CAP][9];                   // weights w[axis][0..2], sorted by cell
+    __shared__ float4 s_mv[CAP];                    // pmass, pmass * v
+    __shared__ float s_acc[4][NB];                  // block node sums
+    __shared__ uint8_t s_hit[NB];
     __shared__ int s_cnt[NC + 1];
     __shared__ int s_start[NC + 1];
     const int N = g.N, R = g.R;
+    const int warp = threadIdx.x >> 5, lane = lane_id();
+    // this lane's stencil offset (lanes 27..31 idle in the cell loop)
+    const int la = lane / 9, lc = (lane / 3) % 3, ld = lane % 3;
     float *fm = g.field[f_mass];
     float *f0 = g.field[f_mom0], *f1 = g.field[f_mom0 + 1], *f2 = g.field[f_mom0 + 2];
     bool changed = false;
     const int used = g.ctrl->bins_used;
     for (int bl = blockIdx.x; bl < used; bl += gridDim.x) {
-        const long long b = g.bin_list[bl];
-        const int beg = g.bin_off[b], end = g.bin_count[b];
+        const long long b = g.bin_list[bl];  // a leaf; its 8 keys are contiguous in the particle order
+        const int beg = g.bin_off[8 * b], end = g.bin_count[8 * b + 7];
         const int oi = (int)(b / ((long long)R * R)) * L, oj = (int)((b / R) % R) * L, ok = (int)(b % R) * L;
-        float acc[NPER][4];
-        bool hit[NPER];
-#pragma unroll
-        for (int u = 0; u < NPER; ++u) {
-            acc[u][0] = acc[u][1] = acc[u][2] = acc[u][3] = 0.f;
-            hit[u] = false;
+        for (int q = threadIdx.x; q < NB; q += 256) {
+            s_acc[0][q] = s_acc[1][q] = s_acc[2][q] = s_acc[3][q] = 0.f;
+            s_hit[q] = 0;
         }
         for (int c0 = beg; c0 < end; c0 += CAP) {
             const int cnt = min(CAP, end - c0);
             for (int q = threadIdx.x; q <= NC; q += 256) s_cnt[q] = 0;
             __syncthreads();
-            for (int q = threadIdx.x; q < cnt; q += 256) {
-                const long long p = g.perm[c0 + q];
-                const Spline sx = bspline(__ldg(x + 3 * p + 0), N);
-                const Spline sy = bspline(__ldg(x + 3 * p + 1), N);
-                const Spline sz = bspline(__ldg(x + 3 * p + 2), N);
+            // pass 1: each particle's cell and its rank among the cell's particles
+            int rcell[PPT], rrank[PPT], rp[PPT];
 #pragma unroll
-                for (int t = 0; t < 3; ++t) {
-                    s_w[q][t] = sx.w[t];
-                    s_w[q][3 + t] = sy.w[t];
-                    s_w[q][6 + t] = sz.w[t];
-                }
-                s_mv[q][0] = pmass;
-                s_mv[q][1] = pmass * __ldg(v + 3 * p + 0);
-                s_mv[q][2] = pmass * __ldg(v + 3 * p + 1);
-                s_mv[q][3] = pmass * __ldg(v + 3 * p + 2);
-                const int cell = ((sx.base - oi + 1) * C1 + (sy.base - oj + 1)) * C1 + (sz.base - ok + 1);
-                s_cell[q] = (uint16_t)cell;
-                atomicAdd(&s_cnt[cell], 1);
+            for (int u = 0; u < PPT; ++u) {
+                const int q = threadIdx.x + u * 256;
+                rcell[u] = -1;
+                if (q >= cnt) continue;
+                const int p = g.perm[c0 + q];
+                const int bi = bspline(__ldg(x + 3 * (long long)p + 0), N).base;
+                const int bj = bspline(__ldg(x + 3 * (long long)p + 1), N).base;
+                const int bk = bspline(__ldg(x + 3 * (long long)p + 2), N).base;
+                rcell[u] = ((bi - oi + 2) * C1 + (bj - oj + 2)) * C1 + (bk - ok + 2);
+                rrank[u] = atomicAdd(&s_cnt[rcell[u]], 1);
+                rp[u] = p;
             }
             __syncthreads();
             if (threadIdx.x < 32) {  // exclusive scan of the cell counts
@@ -446,45 +493,54 @@ __global__ void __launch_bounds__(256) k_p2g_gather(DevGrid g, const float *__re
                 if (threadIdx.x == 0) s_start[NC] = carry;
             }
             __syncthreads();
-            for (int q = threadIdx.x; q < NC; q += 256) s_cnt[q] = s_start[q];  // cursors
-            __syncthreads();
-            for (int q = threadIdx.x; q < cnt; q += 256) s_sorted[atomicAdd(&s_cnt[s_cell[q]], 1)] = (uint16_t)q;
-            __syncthreads();
+            // pass 2: stage the particles at their sorted positions (x and v are
+            // read again, from L1)
 #pragma unroll
-            for (int u = 0; u < NPER; ++u) {
-                const int nd = threadIdx.x + u * 256;
-                if (nd >= NB) break;
-                const int ni = nd / (B * B), nj = (nd / B) % B, nk = nd % B;
-                for (int a = 0; a < 3; ++a) {
-                    const int ci = ni - a + 1;
-                    if (ci < 0 || ci >= C1) continue;
-                    for (int c = 0; c < 3; ++c) {
-                        const int cj = nj - c + 1;
-                        if (cj < 0 || cj >= C1) continue;
-                        for (int d = 0; d < 3; ++d) {
-                            const int ck = nk - d + 1;
-                            if (ck < 0 || ck >= C1) continue;
-                            const int cell = (ci * C1 + cj) * C1 + ck;
-                            const int p0 = s_start[cell], p1 = s_start[cell + 1];
-                            if (p0 < p1) hit[u] = true;
-                            for (int pp = p0; pp < p1; ++pp) {
-                                const int q = s_sorted[pp];
-                                const float wt = s_w[q][a] * s_w[q][3 + c] * s_w[q][6 + d];
-                                acc[u][0] += wt * s_mv[q][0];
-                                acc[u][1] += wt * s_mv[q][1];
-                                acc[u][2] += wt * s_mv[q][2];
-                                acc[u][3] += wt * s_mv[q][3];
-                            }
-                        }
-                    }
+            for (int u = 0; u < PPT; ++u) {
+                if (rcell[u] < 0) continue;
+                const int pos = s_start[rcell[u]] + rrank[u];
+                const long long p = rp[u];
+                const Spline sx = bspline(__ldg(x + 3 * p + 0), N);
+                const Spline sy = bspline(__ldg(x + 3 * p + 1), N);
+                const Spline sz = bspline(__ldg(x + 3 * p + 2), N);
+#pragma unroll
+                for (int t = 0; t < 3; ++t) {
+                    s_w[pos][t] = sx.w[t];
+                    s_w[pos][3 + t] = sy.w[t];
+                    s_w[pos][6 + t] = sz.w[t];
+                }
+                s_mv[pos] = make_float4(pmass, pmass * __ldg(v + 3 * p + 0), pmass * __ldg(v + 3 * p + 1),
+                                        pmass * __ldg(v + 3 * p + 2));
+                g.perm[c0 + pos] = rp[u];  // the chunk's order becomes cell order (G2P reads it)
+            }
+            __syncthreads();
+            for (int cell = warp; cell < NC; cell += NWARP) {
+                const int p0 = s_start[cell], p1 = s_start[cell + 1];
+                if (p0 == p1) continue;  // uniform across the warp
+                const int ci = cell / (C1 * C1), cj = (cell / C1) % C1, ck = cell % C1;
+                float m = 0.f, m0 = 0.f, m1 = 0.f, m2 = 0.f;
+                for (int pp = p0; pp < p1; ++pp) {
+                    const float wt = s_w[pp][la] * s_w[pp][3 + lc] * s_w[pp][6 + ld];
+                    const float4 mv = s_mv[pp];
+                    m += wt * mv.x;
+                    m0 += wt * mv.y;
+                    m1 += wt * mv.z;
+                    m2 += wt * mv.w;
+                }
+                const int ni = ci - 2 + la, nj = cj - 2 + lc, nk = ck - 2 + ld;
+                if (lane < 27 && ni >= 0 && nj >= 0 && nk >= 0) {  // negative: outside the domain
+                    const int nd = (ni * B + nj) * B + nk;
+                    atomicAdd(&s_acc[0][nd], m);
+                    atomicAdd(&s_acc[1][nd], m0);
+                    atomicAdd(&s_acc[2][nd], m1);
+                    atomicAdd(&s_acc[3][nd], m2);
+                    s_hit[nd] = 1;
                 }
             }
             __syncthreads();
         }
-#pragma unroll
-        for (int u = 0; u < NPER; ++u) {
-            const int nd = threadIdx.x + u * 256;
-            if (nd >= NB || !hit[u]) continue;
+        for (int nd = threadIdx.x; nd < NB; nd += 256) {
+            if (!s_hit[nd]) continue;
             const int i = oi + nd / (B * B), j = oj + (nd / B) % B, k = ok + nd % B;
             if (i >= N || j >= N || k >= N) continue;
             const long long lb = ((long long)(i >> LG2) * R + (j >> LG2)) * R + (k >> LG2);
@@ -498,11 +554,12 @@ __global__ void __launch_bounds__(256) k_p2g_gather(DevGrid g, const float *__re
                 if (!(old & bit)) changed = true;
             }
             const long long idx = ((long long)slot << (3 * LG2)) + l;
-            atomicAdd(fm + idx, acc[u][0]);
-            atomicAdd(f0 + idx, acc[u][1]);
-            atomicAdd(f1 + idx, acc[u][2]);
-            atomicAdd(f2 + idx, acc[u][3]);
+            atomicAdd(fm + idx, s_acc[0][nd]);
+            atomicAdd(f0 + idx, s_acc[1][nd]);
+            atomicAdd(f1 + idx, s_acc[2][nd]);
+            atomicAdd(f2 + idx, s_acc[3][nd]);
         }
+        __syncthreads();  // the accumulators are zeroed for the next bin
     }
     if (changed) mark_dirty(g);
 }
@@ -510,8 +567,7 @@ __global__ void __launch_bounds__(256) k_p2g_gather(DevGrid g, const float *__re
 int launch_p2g_binned(const DevGrid &g, cudaStream_t s, const float *x, const float *v, long long n, float pmass,
                       int f_mass, int f_mom0, const LaunchCfg &lc)
 {
-    const long long nbins = (long long)g.R * g.R * g.R;
-    const long long nscan = nbins + 1;  // plus the bin of particles with no stencil node in the domain
+    const long long nscan = p2g_num_keys(g.R);
     const int ntiles = (int)((nscan + kBinTile - 1) / kBinTile);
     long long pblocks = (n + 255) / 256;
     if (pblocks > 1 << 20) pblocks = 1 << 20;
@@ -519,16 +575,14 @@ int launch_p2g_binned(const DevGrid &g, cudaStream_t s, const float *x, const fl
     cudaMemsetAsync(g.bin_count, 0, sizeof(int32_t) * nscan, s);
     cudaMemsetAsync(&g.ctrl->bins_used, 0, sizeof(int32_t), s);
     k_p2g_bin<<<(unsigned)pblocks, 256, 0, s>>>(g, x, n);
-    ++launches;
-    launch_alloc_needed(g, s);
-    ++launches;
     k_bin_scan_tiles<<<ntiles, 256, 0, s>>>(g, nscan);
+    launch_alloc_needed(g, s);
     k_bin_scan_top<<<1, 1024, 0, s>>>(g, ntiles);
     k_bin_scan_apply<<<ntiles, 256, 0, s>>>(g, nscan);
-    launches += 3;
+    launches += 5;
     k_p2g_perm<<<(unsigned)pblocks, 256, 0, s>>>(g, x, n);
     ++launches;
-    if (g.L == 4) k_p2g_gather<4><<<lc.num_sms * 4, 256, 0, s>>>(g, x, v, pmass, f_mass, f_mom0);
+    if (g.L == 4) k_p2g_gather<4><<<lc.num_sms * 5, 256, 0, s>>>(g, x, v, pmass, f_mass, f_mom0);
     else k_p2g_gather<8><<<lc.num_sms * 2, 256, 0, s>>>(g, x, v, pmass, f_mass, f_mom0);
     ++launches;
     return launches;

@@ -11,7 +11,7 @@ import pytest
 
 import oracle
 from sgtest import rel_linf
-from workload import spheres_particles
+from workload import cube_particles, spheres_particles
 
 pytestmark = pytest.mark.gpu
 
@@ -48,7 +48,7 @@ def stencil_union_leaves(x, N, L):
     return np.array(sorted(out), dtype=np.int32)
 
 
-def one_step_compare(spec, max_leaves):
+def one_step_compare(spec, max_leaves, interior=True):
     import torch
     g, og = make(spec, max_leaves)
     x = torch.from_numpy(spec.x).cuda()
@@ -64,8 +64,8 @@ def one_step_compare(spec, max_leaves):
     np.testing.assert_array_equal(gm, om)
     for f in range(4):
         assert rel_linf(g.read_field(f), og.read_field(f)) <= TOL, f
-    # totals: partition of unity
-    assert abs(g.read_field(0).astype(np.float64).sum() - spec.n * spec.pmass) <= 1e-4 * spec.n * spec.pmass
+    if interior:  # totals: partition of unity
+        assert abs(g.read_field(0).astype(np.float64).sum() - spec.n * spec.pmass) <= 1e-4 * spec.n * spec.pmass
     g.grid_update(0, 1, spec.dt, spec.gravity, spec.bound)
     og.grid_update(0, 1, spec.dt, spec.gravity, spec.bound)
     for f in range(1, 4):
@@ -82,6 +82,70 @@ def one_step_compare(spec, max_leaves):
 def test_p2g_g2p_small():
     spec = spheres_particles(seed=3, n=20000, N=64, L=4, r_min=0.1, r_max=0.2)
     one_step_compare(spec, 8192)
+
+
+@pytest.mark.parametrize("L", [4, 8])
+def test_p2g_g2p_domain_faces(L):
+    """Particles across every face of the domain and beyond it: stencils cut by
+    the faces, bases at -2 and -1 (binned to leaf 0), and particles with no
+    stencil node inside the domain (no activation, zero velocity)."""
+    spec = cube_particles(seed=11 + L, n=3000, N=64, L=L, pad_cells=3.0)
+    one_step_compare(spec, (64 // L) ** 3, interior=False)
+
+
+def test_g2p_positions_moved_after_p2g():
+    """G2P over the bins of the last P2G when the positions have changed since
+    (shifted by up to 6 cells, some out of the domain): particles that left
+    their bin's staged neighbourhood read the grid node by node."""
+    import torch
+    spec = spheres_particles(seed=4, n=20000, N=64, L=4, r_min=0.1, r_max=0.2)
+    g, og = make(spec, 4096)
+    x = torch.from_numpy(spec.x).cuda()
+    v = torch.from_numpy(spec.v).cuda()
+    ox, ov = spec.x.copy(), spec.v.copy()
+    g.p2g(x, v, spec.pmass, 0, 1)
+    g.grid_update(0, 1, spec.dt, spec.gravity, spec.bound)
+    og.p2g(ox, ov, spec.pmass, 0, 1)
+    og.grid_update(0, 1, spec.dt, spec.gravity, spec.bound)
+    g.sync()
+    rng = np.random.default_rng(5)
+    shift = rng.uniform(-6.0, 6.0, size=ox.shape) / spec.N
+    shift[rng.random(spec.n) < 0.5] = 0.0                   # half keep their bin
+    xm = (ox + shift).astype(np.float32)
+    x.copy_(torch.from_numpy(xm))
+    torch.cuda.synchronize()
+    ox = xm.copy()
+    g.g2p(x, v, spec.dt, 1)
+    og.g2p(ox, ov, spec.dt, 1)
+    g.sync()
+    assert rel_linf(v.cpu().numpy(), ov) <= TOL
+    assert np.max(np.abs(x.cpu().numpy().astype(np.float64) - ox)) <= 4e-7
+    g.close()
+
+
+def test_p2g_g2p_unaligned_views():
+    """Positions and velocities in views that start 4 bytes past an 8-byte
+    boundary (the G2P stores fall back to single floats)."""
+    import torch
+    spec = spheres_particles(seed=6, n=9999, N=64, L=4, r_min=0.1, r_max=0.2)
+    g, og = make(spec, 4096)
+    xb = torch.zeros(3 * spec.n + 1, dtype=torch.float32, device="cuda")
+    vb = torch.zeros(3 * spec.n + 1, dtype=torch.float32, device="cuda")
+    x, v = xb[1:], vb[1:]
+    assert x.data_ptr() % 8 == 4
+    x.copy_(torch.from_numpy(spec.x.reshape(-1)))
+    v.copy_(torch.from_numpy(spec.v.reshape(-1)))
+    torch.cuda.synchronize()
+    ox, ov = spec.x.copy(), spec.v.copy()
+    for G, X, V in ((g, x, v), (og, ox, ov)):
+        G.p2g(X, V, spec.pmass, 0, 1)
+        G.grid_update(0, 1, spec.dt, spec.gravity, spec.bound)
+        G.g2p(X, V, spec.dt, 1)
+    g.sync()
+    assert rel_linf(v.cpu().numpy().reshape(-1, 3), ov) <= TOL
+    assert np.max(np.abs(x.cpu().numpy().reshape(-1, 3).astype(np.float64) - ox)) <= 4e-7
+    assert xb[0].item() == 0.0 and vb[0].item() == 0.0
+    g.close()
 
 
 def test_p2g_g2p_full_size_one_step():

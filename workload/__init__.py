@@ -152,6 +152,19 @@ def spheres_particles(seed: int = 0, n: int = 2_000_000, N: int = 256, L: int = 
                         note="3 spheres, split by volume")
 
 
+def cube_particles(seed: int, n: int, N: int, L: int, pad_cells: float = 3.0,
+                   v_sigma: float = 0.1) -> ParticleSpec:
+    """n particles uniform in the cube [-pad, 1 + pad]^3 (pad = pad_cells / N):
+    every face of the domain is crossed, and some particles have no stencil
+    node inside it.  Velocities N(0, v_sigma) per component; float32 (n, 3)."""
+    rng = np.random.default_rng(seed)
+    pad = pad_cells / N
+    x = rng.uniform(-pad, 1.0 + pad, size=(n, 3)).astype(np.float32)
+    v = rng.normal(0.0, v_sigma, size=(n, 3)).astype(np.float32)
+    return ParticleSpec(N, L, n, np.zeros((3, 3)), np.zeros(3), np.ascontiguousarray(x), np.ascontiguousarray(v),
+                        note="uniform over the domain and a band around it")
+
+
 # ---------------------------------------------------------------------------
 # Batched and serving size mixes
 # ---------------------------------------------------------------------------
