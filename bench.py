@@ -264,7 +264,7 @@ def bench_batched(torch, sg, steps, warmup, flush_buf, stream):
             "over_sequential_eager": (active * steps / t_b) / res["sequential_eager"]["value"]}
 
 
-def bench_particles(torch, sg, steps, warmup, stream):
+def bench_particles(torch, sg, steps, warmup, flush_buf, stream):
     spec = spheres_particles(0)
     g = sg.Grid(spec.N, 2, 4, max_leaves=(spec.N // 4) ** 3, max_sums=1)
     x = torch.from_numpy(spec.x).cuda()
@@ -277,7 +277,7 @@ def bench_particles(torch, sg, steps, warmup, stream):
         g.g2p(x, v, spec.dt, 1)
         g.flush()
 
-    ms, launches = time_steps(torch, step, steps, warmup, None, stream, lambda: g.stats()["launches"])
+    ms, launches = time_steps(torch, step, steps, warmup, flush_buf, stream, lambda: g.stats()["launches"])
     t = sum(ms) / 1e3
     g.sync()
     leaves = g.num_leaves()
@@ -285,6 +285,7 @@ def bench_particles(torch, sg, steps, warmup, stream):
     return {"workload": "2M particles in 3 spheres, 256^3 grid of 4^3 leaves, P2G+grid update+G2P",
             "particles": spec.n, "leaves": leaves, "value": spec.n * steps / t, "unit": "particle-steps/s",
             "ms_per_step": t * 1e3 / steps, "launches_per_step": launches / steps,
+            "l2": "flushed before every timed step (512 MB write)",
             "stream_bytes_per_particle": 72,
             "grid_atomics_per_s": spec.n * 27 * 4 * steps / t}
 
@@ -352,40 +353,44 @@ def run_ours(args):
     x_host = leaf_values(spec.seed, spec.N, spec.L, leaf_b)
     flush_buf = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
-    fused = setup_band(sg, spec, sg.SG_OPT_ALL, x_host, args.variant)
-    eager = setup_band(sg, spec, sg.SG_OPT_EAGER, x_host, args.variant)
-
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    with ClockSampler(dev) as clk:
-        ms_f, launches_f = time_steps(torch, lambda: band_step(fused), args.steps, args.warmup, flush_buf, stream,
-                                      lambda: fused.stats()["launches"])
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    if args.only != "all":
-        ms_e, launches_e = [float("nan")], 0
+    if args.skip_headline:  # profiling runs of one extra leg
+        ms_f, launches_f, ms_e, launches_e, e2e_steps, e2e_s = [float("nan")], 0, [float("nan")], 0, 0, 1.0
+        clk = None
     else:
-        ms_e, launches_e = time_steps(torch, lambda: band_step(eager), max(args.steps // 2, 5), max(args.warmup, 3),
-                                      flush_buf, stream, lambda: eager.stats()["launches"])
-    torch.cuda.synchronize()
+        fused = setup_band(sg, spec, sg.SG_OPT_ALL, x_host, args.variant)
+        eager = setup_band(sg, spec, sg.SG_OPT_EAGER, x_host, args.variant)
 
-    # end-to-end through the public API: pinned host x in, sum out, every step
-    x_pinned = torch.from_numpy(x_host).pin_memory()
-    e2e_steps = 0 if args.only != "all" else max(3, min(args.steps, 20))
-    for _ in range(2 if e2e_steps else 0):
-        fused.write_field(0, x_pinned)
-        band_step(fused)
-        fused.read_sums(1)
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        fused.write_field(0, x_pinned)
-        band_step(fused)
-        fused.read_sums(1)
-    e2e_s = max(time.perf_counter() - t0, 1e-9)
-    fused.close()
-    eager.close()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        with ClockSampler(dev) as clk:
+            ms_f, launches_f = time_steps(torch, lambda: band_step(fused), args.steps, args.warmup, flush_buf, stream,
+                                          lambda: fused.stats()["launches"])
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        if args.only != "all":
+            ms_e, launches_e = [float("nan")], 0
+        else:
+            ms_e, launches_e = time_steps(torch, lambda: band_step(eager), max(args.steps // 2, 5), max(args.warmup, 3),
+                                          flush_buf, stream, lambda: eager.stats()["launches"])
+        torch.cuda.synchronize()
+
+        # end-to-end through the public API: pinned host x in, sum out, every step
+        x_pinned = torch.from_numpy(x_host).pin_memory()
+        e2e_steps = 0 if args.only != "all" else max(3, min(args.steps, 20))
+        for _ in range(2 if e2e_steps else 0):
+            fused.write_field(0, x_pinned)
+            band_step(fused)
+            fused.read_sums(1)
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            fused.write_field(0, x_pinned)
+            band_step(fused)
+            fused.read_sums(1)
+        e2e_s = max(time.perf_counter() - t0, 1e-9)
+        fused.close()
+        eager.close()
 
     t_f = sum(ms_f) / 1e3
     t_e = sum(ms_e) / 1e3
@@ -405,7 +410,7 @@ def run_ours(args):
         k = max(5, min(args.steps, 20))
         for name, fn in (("band1024", lambda: bench_band1024(torch, sg, k, 3, flush_buf, stream)),
                          ("batched", lambda: bench_batched(torch, sg, k, 3, flush_buf, stream)),
-                         ("particles", lambda: bench_particles(torch, sg, k, 3, stream)),
+                         ("particles", lambda: bench_particles(torch, sg, k, 3, flush_buf, stream)),
                          ("serving", lambda: bench_serving(torch, sg))):
             if args.only not in ("all", name):
                 continue
@@ -450,7 +455,7 @@ def run_ours(args):
             "eager": {"value": eager_value, "ms_per_step": t_e * 1e3 / len(ms_e),
                       "launches_per_step": launches_e / len(ms_e), "achieved_gbs": achieved_eager},
             "fused_over_eager": value / eager_value,
-            "clocks": clk.summary(),
+            "clocks": clk.summary() if clk else None,
             "cpu_baseline": cpu,
             "extra": extra,
         }
@@ -538,6 +543,8 @@ def main():
     ap.add_argument("--only", choices=["all", "fused", "band1024", "batched", "particles", "serving"], default="all",
                     help="fused: only the fused headline step; a leg name: the headline step and that leg "
                          "(for profiling runs)")
+    ap.add_argument("--skip-headline", action="store_true",
+                    help="with --only <leg>: time that leg alone (profiling runs; the headline keys are NaN)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
