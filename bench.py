@@ -290,13 +290,14 @@ def bench_particles(torch, sg, steps, warmup, flush_buf, stream):
             "grid_atomics_per_s": spec.n * 27 * 4 * steps / t}
 
 
-def bench_serving(torch, sg, rates=(50, 200, 1000), duration=2.0, cap_s=60.0):
+def bench_serving(torch, sg, rates=(50, 100, 200, 500, 1000, 2000), duration=2.0, cap_s=60.0):
     from paper_2012_08141_gb300.serve import Server
     out = []
     for rate in rates:
         jobs = serving_arrivals(1000 + rate, rate, duration)
         srv = Server(max_jobs=256, warps_per_cta=4, hbm_reserve=8 << 30)
         ids, k = [], 0
+        max_pending = max_resident = 0
         t0 = time.perf_counter()
         while True:
             now = time.perf_counter() - t0
@@ -304,6 +305,8 @@ def bench_serving(torch, sg, rates=(50, 200, 1000), duration=2.0, cap_s=60.0):
                 ids.append(srv.submit(jobs[k].spec, jobs[k].steps))
                 k += 1
             st = srv.stats()
+            max_pending = max(max_pending, st["pending"])
+            max_resident = max(max_resident, st["resident"])
             if k == len(jobs) and st["completed"] + st["failed"] == len(jobs):
                 break
             if now > duration + cap_s:
@@ -319,6 +322,7 @@ def bench_serving(torch, sg, rates=(50, 200, 1000), duration=2.0, cap_s=60.0):
                     "p50_ms": 1e3 * lat[len(lat) // 2] if lat else None,
                     "p99_ms": 1e3 * lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)] if lat else None,
                     "voxel_steps_per_s": st["voxel_steps"] / elapsed, "ticks": st["ticks"],
+                    "admission_waits": st["admission_waits"], "max_queued": max_pending, "max_resident": max_resident,
                     "wall_s": elapsed})
         srv.close()
     return {"workload": "Poisson arrivals of band jobs, 1e4..1e7 voxels, 10..200 steps", "duration_s": duration,
@@ -445,6 +449,7 @@ def run_ours(args):
                        "l2": "flushed before every timed step (512 MB write)"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                         "achieved_active_only": n_active * 8 / (avg_ms / 1e3) / 1e9,
                          "kernel": ("k_sweep_diffuse_box<false,false,true>" if args.variant == 0
                                     else "k_diffuse_box<false,false,true>"),
                          "bytes_per_launch": n_leaves * BYTES_PER_LEAF_FUSED},

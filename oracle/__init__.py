@@ -66,6 +66,8 @@ def _load():
         "og_p2g": (None, [P, P, P, I64, D, I32, I32]),
         "og_grid_update": (None, [P, I32, I32, D, D, I32]),
         "og_g2p": (None, [P, P, P, I64, D, I32]),
+        "og_p2g_apic": (None, [P, P, P, P, I64, D, I32, I32]),
+        "og_g2p_apic": (None, [P, P, P, P, I64, D, I32]),
         "og_get_voxel": (D, [P, I32, I64, I64, I64]),
         "og_voxel_active": (I32, [P, I64, I64, I64]),
     }
@@ -192,6 +194,22 @@ class Grid:
         assert x.dtype == np.float32 and v.dtype == np.float32
         assert x.flags.c_contiguous and v.flags.c_contiguous
         self.lib.og_g2p(self.h, _ptr(x), _ptr(v), x.size // 3, float(dt), int(f_mom0))
+
+    def p2g_apic(self, x, v, C, pmass: float, f_mass: int, f_mom0: int):
+        """APIC P2G: C is (n, 9) FP32, row-major 3x3 per particle."""
+        xa = np.ascontiguousarray(x, dtype=np.float32)
+        va = np.ascontiguousarray(v, dtype=np.float32)
+        ca = np.ascontiguousarray(C, dtype=np.float32)
+        n = xa.size // 3
+        assert ca.size == 9 * n
+        self.lib.og_p2g_apic(self.h, _ptr(xa), _ptr(va), _ptr(ca), n, float(pmass), int(f_mass), int(f_mom0))
+
+    def g2p_apic(self, x: np.ndarray, v: np.ndarray, C: np.ndarray, dt: float, f_mom0: int):
+        """APIC G2P; updates x, v (n x 3) and C (n x 9), FP32 C-contiguous, in place."""
+        for a in (x, v, C):
+            assert a.dtype == np.float32 and a.flags.c_contiguous
+        assert C.size == 3 * x.size
+        self.lib.og_g2p_apic(self.h, _ptr(x), _ptr(v), _ptr(C), x.size // 3, float(dt), int(f_mom0))
 
 
 def leaf_coords(leaf_b: np.ndarray, N: int, L: int) -> np.ndarray:

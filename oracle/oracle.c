@@ -430,6 +430,82 @@ void og_g2p(og_grid *g, float *x, float *vel, int64_t n, double dt, int32_t f_mo
     }
 }
 
+/* ---------------------------------------------------------------------------
+ * Affine (APIC) transfers, the particle-grid transfers of MLS-MPM (Sec. 8.3).
+ * The paper does not print them; these are the affine particle-in-cell
+ * transfers with quadratic B-splines, for which the inertia-like tensor
+ * D_p = sum_n w_pn d_pn d_pn^T equals dx^2/4 times the identity.  Each
+ * particle carries a 3x3 matrix C_p, stored row-major as 9 FP32 values
+ * (C[9p + 3a + b] = C_ab), acting as (C d)_a = sum_b C_ab d_b.  The offset of
+ * stencil node base + (a,b,c) from the particle is d = ((a,b,c) - fx) * dx
+ * with fx the per-axis spline offsets X - base (X = x * N in FP32).
+ * ------------------------------------------------------------------------- */
+
+/* APIC P2G with activation: as og_p2g, with the momentum contribution
+ *   mom_n += w_pn * pmass * (v_p + C_p d_pn). */
+void og_p2g_apic(og_grid *g, const float *x, const float *vel, const float *C, int64_t n,
+                 double pmass, int32_t f_mass, int32_t f_mom0)
+{
+    int64_t v = cube(g->L);
+    double dx = 1.0 / (double)g->N;
+    for (int64_t p = 0; p < n; p++) {
+        int64_t base[3];
+        double w[3][3], fx[3];
+        for (int a = 0; a < 3; a++) {
+            og_bspline(x[3 * p + a], g->N, &base[a], w[a]);
+            fx[a] = (double)(x[3 * p + a] * (float)g->N) - (double)base[a];
+        }
+        for (int a = 0; a < 3; a++)
+            for (int b = 0; b < 3; b++)
+                for (int c = 0; c < 3; c++) {
+                    int64_t i = base[0] + a, j = base[1] + b, k = base[2] + c;
+                    if (!in_domain(g, i, j, k)) continue;
+                    og_activate_voxel(g, i, j, k);
+                    int64_t idx = (int64_t)g->root[root_of(g, i, j, k)] * v + local_of(g, i, j, k);
+                    double d[3] = {((double)a - fx[0]) * dx, ((double)b - fx[1]) * dx, ((double)c - fx[2]) * dx};
+                    double wm = w[0][a] * w[1][b] * w[2][c] * pmass;
+                    g->val[f_mass][idx] += wm;
+                    for (int e = 0; e < 3; e++) {
+                        double u = (double)vel[3 * p + e];
+                        for (int f = 0; f < 3; f++) u += (double)C[9 * p + 3 * e + f] * d[f];
+                        g->val[f_mom0 + e][idx] += wm * u;
+                    }
+                }
+    }
+}
+
+/* APIC G2P: v_p = sum_n w_pn v_n, C_p = (4 / dx^2) sum_n w_pn v_n d_pn^T,
+ * x_p += dt * v_p.  x, vel and C are stored back as FP32. */
+void og_g2p_apic(og_grid *g, float *x, float *vel, float *C, int64_t n, double dt, int32_t f_mom0)
+{
+    double dx = 1.0 / (double)g->N, inv_d = 4.0 / (dx * dx);
+#pragma omp parallel for schedule(static)
+    for (int64_t p = 0; p < n; p++) {
+        int64_t base[3];
+        double w[3][3], fx[3], u[3] = {0.0, 0.0, 0.0}, B[3][3] = {{0.0}};
+        for (int a = 0; a < 3; a++) {
+            og_bspline(x[3 * p + a], g->N, &base[a], w[a]);
+            fx[a] = (double)(x[3 * p + a] * (float)g->N) - (double)base[a];
+        }
+        for (int a = 0; a < 3; a++)
+            for (int b = 0; b < 3; b++)
+                for (int c = 0; c < 3; c++) {
+                    double wt = w[0][a] * w[1][b] * w[2][c];
+                    double d[3] = {((double)a - fx[0]) * dx, ((double)b - fx[1]) * dx, ((double)c - fx[2]) * dx};
+                    for (int e = 0; e < 3; e++) {
+                        double vn = og_get(g, f_mom0 + e, base[0] + a, base[1] + b, base[2] + c);
+                        u[e] += wt * vn;
+                        for (int f = 0; f < 3; f++) B[e][f] += wt * vn * d[f];
+                    }
+                }
+        for (int e = 0; e < 3; e++) {
+            vel[3 * p + e] = (float)u[e];
+            x[3 * p + e] = (float)((double)x[3 * p + e] + dt * u[e]);
+            for (int f = 0; f < 3; f++) C[9 * p + 3 * e + f] = (float)(inv_d * B[e][f]);
+        }
+    }
+}
+
 /* Value of one voxel of a field read through the mask (for sampled checks). */
 double og_get_voxel(const og_grid *g, int32_t f, int64_t i, int64_t j, int64_t k)
 {

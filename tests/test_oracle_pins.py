@@ -365,6 +365,75 @@ def test_g2p_uniform_velocity_exact():
     np.testing.assert_array_equal(x, spec.x)
 
 
+def test_g2p_apic_reproduces_affine_field():
+    """APIC G2P on an affine grid velocity v(node) = A node*dx + c returns
+    v_p = A x_p + c and C_p = A: quadratic B-splines reproduce linear
+    functions and sum_n w d d^T = dx^2/4 I, so (4/dx^2) sum_n w v_n d^T = A.
+    A is not symmetric, so a transposed C fails, as do a wrong sign of d or a
+    wrong 4/dx^2 factor."""
+    spec = _small_particles(n=2000, N=32, seed=5)
+    N, L = spec.N, spec.L
+    g = oracle.Grid(N, L, 4)
+    g.p2g(spec.x, spec.v, 1.0, 0, 1)
+    b, _ = g.structure()
+    c = oracle.leaf_coords(b, N, L).astype(np.float64) / N
+    A = np.array([[0.3, -1.2, 0.5], [2.0, 0.1, -0.7], [-0.4, 0.9, 1.1]])
+    off = np.array([0.05, -0.2, 0.3])
+    for d in range(3):
+        g.write_field64(1 + d, c @ A[d] + off[d])
+    x = spec.x.copy()
+    v = np.zeros_like(spec.v)
+    C = np.zeros((spec.n, 9), dtype=np.float32)
+    dtime = 1e-3
+    g.g2p_apic(x, v, C, dtime, 1)
+    xp = (spec.x.astype(np.float32) * np.float32(N)).astype(np.float64) / N
+    np.testing.assert_allclose(v, xp @ A.T + off, rtol=1e-6, atol=1e-6)
+    np.testing.assert_allclose(C.reshape(-1, 3, 3), np.broadcast_to(A, (spec.n, 3, 3)), rtol=1e-5, atol=1e-5)
+    np.testing.assert_allclose(x, (spec.x.astype(np.float64) + dtime * v.astype(np.float64)), rtol=0, atol=1e-7)
+
+
+def test_p2g_apic_zero_affine_is_pic():
+    """With C = 0 the APIC P2G reduces to the PIC P2G: identical fields and
+    structure (v + 0 is exact)."""
+    spec = _small_particles(n=3000, N=32, seed=6)
+    g1, g2 = oracle.Grid(spec.N, spec.L, 4), oracle.Grid(spec.N, spec.L, 4)
+    g1.p2g(spec.x, spec.v, 1.25, 0, 1)
+    g2.p2g_apic(spec.x, spec.v, np.zeros((spec.n, 9), np.float32), 1.25, 0, 1)
+    b1, m1 = g1.structure()
+    b2, m2 = g2.structure()
+    np.testing.assert_array_equal(b1, b2)
+    np.testing.assert_array_equal(m1, m2)
+    for f in range(4):
+        np.testing.assert_array_equal(g1.read_field(f), g2.read_field(f))
+
+
+def test_p2g_apic_momentum_and_angular_momentum():
+    """APIC P2G conserves linear momentum (sum_n w d = 0) and transfers the
+    affine part as angular momentum: with every stencil inside the domain,
+    sum_n x_n x p_n = pmass * sum_p [x_p x v_p + dx^2/4 (C21 - C12, C02 - C20,
+    C10 - C01)], from sum_n w d d^T = dx^2/4 I."""
+    spec = _small_particles(n=4000, N=32, seed=7)
+    N, L, pm = spec.N, spec.L, 1.5
+    rng = np.random.default_rng(8)
+    C = rng.normal(0.0, 5.0, size=(spec.n, 9)).astype(np.float32)
+    g = oracle.Grid(N, L, 4)
+    g.p2g_apic(spec.x, spec.v, C, pm, 0, 1)
+    assert g.sum(0) == pytest.approx(pm * spec.n, rel=1e-12)
+    v64 = spec.v.astype(np.float64)
+    for d in range(3):
+        assert abs(g.sum(1 + d) - pm * v64[:, d].sum()) <= 1e-10 * pm * np.abs(v64[:, d]).sum()
+    b, _ = g.structure()
+    xn = (oracle.leaf_coords(b, N, L).astype(np.float64) / N).reshape(-1, 3)
+    pn = np.stack([g.read_field(1 + d).reshape(-1) for d in range(3)], axis=1)
+    got = np.cross(xn, pn).sum(axis=0)
+    xp = (spec.x.astype(np.float32) * np.float32(N)).astype(np.float64) / N
+    Cm = C.astype(np.float64).reshape(-1, 3, 3)
+    spin = np.stack([Cm[:, 2, 1] - Cm[:, 1, 2], Cm[:, 0, 2] - Cm[:, 2, 0], Cm[:, 1, 0] - Cm[:, 0, 1]], axis=1)
+    want = pm * (np.cross(xp, v64).sum(axis=0) + (1.0 / N) ** 2 / 4.0 * spin.sum(axis=0))
+    scale = pm * (np.abs(np.cross(xp, v64)).sum() + np.abs(spin).sum() / (4.0 * N * N))
+    assert np.max(np.abs(got - want)) <= 1e-11 * scale
+
+
 def test_grid_update_hand_case():
     """v = p/m, v_z -= dt g, then the boundary clamp (index < bound with
     negative component, index > N - bound with positive component)."""
