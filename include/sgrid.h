@@ -176,6 +176,20 @@ int sg_grid_update(sg_grid *g, int32_t f_mass, int32_t f_mom0, float dt,
  * borrowed) are overwritten. */
 int sg_g2p(sg_grid *g, float *dev_x, float *dev_v, int64_t n, float dt, int32_t f_mom0);
 
+/* Queue APIC P2G with activation (the affine transfer of MLS-MPM, Sec. 8.3):
+ * as sg_p2g, with the momentum contribution of particle p to stencil node n
+ *   w * pmass * (v_p + C_p (x_n - x_p)),
+ * where dev_C holds one 3x3 matrix per particle, n*9 FP32 row-major
+ * ((C d)_a = sum_b C[9p + 3a + b] d_b), device memory, borrowed until the
+ * next sync.  dev_C == NULL is the PIC transfer of sg_p2g. */
+int sg_p2g_apic(sg_grid *g, const float *dev_x, const float *dev_v, const float *dev_C, int64_t n,
+                float pmass, int32_t f_mass, int32_t f_mom0);
+
+/* Queue APIC G2P: as sg_g2p, and C_p = (4/dx^2) sum_n w v_n (x_n - x_p)^T
+ * (quadratic B-splines: sum_n w d d^T = dx^2/4 I) is written to dev_C (n*9
+ * FP32 row-major, device, borrowed).  dev_C == NULL is sg_g2p. */
+int sg_g2p_apic(sg_grid *g, float *dev_x, float *dev_v, float *dev_C, int64_t n, float dt, int32_t f_mom0);
+
 /* Exchange the storage behind field indices a and b (no device work). */
 int sg_swap(sg_grid *g, int32_t a, int32_t b);
 

@@ -85,6 +85,8 @@ def load_library(build: bool = True) -> ctypes.CDLL:
         "sg_p2g": [P, P, P, I64, F, I32, I32],
         "sg_grid_update": [P, I32, I32, F, F, I32],
         "sg_g2p": [P, P, P, I64, F, I32],
+        "sg_p2g_apic": [P, P, P, P, I64, F, I32, I32],
+        "sg_g2p_apic": [P, P, P, P, I64, F, I32],
         "sg_swap": [P, I32, I32],
         "sg_flush": [P],
         "sg_sync": [P],
@@ -232,6 +234,23 @@ class Grid:
 
     def grid_update(self, f_mass: int, f_mom0: int, dt: float, gz: float, bound: int):
         self._c(self.lib.sg_grid_update(self.h, int(f_mass), int(f_mom0), float(dt), float(gz), int(bound)))
+
+    def p2g_apic(self, x, v, C, pmass: float, f_mass: int, f_mom0: int):
+        """APIC P2G; C is (n, 9) FP32 on the device (row-major 3x3 per particle)."""
+        for t in (x, v, C):
+            assert t.is_cuda and str(t.dtype) == "torch.float32" and t.is_contiguous()
+        assert C.numel() == 3 * x.numel()
+        self._borrowed += [x, v, C]
+        self._c(self.lib.sg_p2g_apic(self.h, _ptr(x), _ptr(v), _ptr(C), x.numel() // 3, float(pmass), int(f_mass),
+                                     int(f_mom0)))
+
+    def g2p_apic(self, x, v, C, dt: float, f_mom0: int):
+        """APIC G2P: overwrites x, v and C (n, 9)."""
+        for t in (x, v, C):
+            assert t.is_cuda and str(t.dtype) == "torch.float32" and t.is_contiguous()
+        assert C.numel() == 3 * x.numel()
+        self._borrowed += [x, v, C]
+        self._c(self.lib.sg_g2p_apic(self.h, _ptr(x), _ptr(v), _ptr(C), x.numel() // 3, float(dt), int(f_mom0)))
 
     def g2p(self, x, v, dt: float, f_mom0: int):
         for t in (x, v):

@@ -64,7 +64,7 @@ struct Op {
     long long lo2 = 0, hi2 = 0;
     int strict = 0;
     const void *p0 = nullptr;
-    void *p1 = nullptr, *p2 = nullptr;
+    void *p1 = nullptr, *p2 = nullptr, *p3 = nullptr;
     long long n = 0;
     float f0 = 0.f, f1 = 0.f;
     int i0 = 0, i1 = 0, i2 = 0;
@@ -363,7 +363,8 @@ int do_flush(sg_grid *g)
                 if (!(rc = ensure_p2g_scratch(g, o.n))) {
                     const int k = g->dry ? 7
                                          : launch_p2g_binned(g->dev, g->stream, (const float *)o.p0,
-                                                             (const float *)o.p1, o.n, o.f0, o.i0, o.i1, g->lc);
+                                                             (const float *)o.p1, (const float *)o.p3, o.n, o.f0,
+                                                             o.i0, o.i1, g->lc);
                     g->stats.launches += k - 1;
                     rc = after_launch(g, "binned p2g");
                     g->p2g_x = o.p0;
@@ -382,7 +383,7 @@ int do_flush(sg_grid *g)
                 break;
             case OP_G2P:
                 if (!g->dry)
-                    launch_g2p(g->dev, g->stream, (float *)o.p1, (float *)o.p2, o.n, o.f0, o.i0,
+                    launch_g2p(g->dev, g->stream, (float *)o.p1, (float *)o.p2, (float *)o.p3, o.n, o.f0, o.i0,
                                o.p1 == g->p2g_x && o.n == g->p2g_n, g->lc);
                 rc = after_launch(g, "g2p");
                 ++i;
@@ -642,6 +643,12 @@ int sg_reduce_sum(sg_grid *g, int32_t src, int64_t out_slot)
 
 int sg_p2g(sg_grid *g, const float *dev_x, const float *dev_v, int64_t n, float pmass, int32_t f_mass, int32_t f_mom0)
 {
+    return sg_p2g_apic(g, dev_x, dev_v, nullptr, n, pmass, f_mass, f_mom0);
+}
+
+int sg_p2g_apic(sg_grid *g, const float *dev_x, const float *dev_v, const float *dev_C, int64_t n, float pmass,
+                int32_t f_mass, int32_t f_mom0)
+{
     if (!g || n < 0 || (n > 0 && (!dev_x || !dev_v)) || !valid_field(g, f_mass) || !valid_field(g, f_mom0) ||
         !valid_field(g, f_mom0 + 2) || (f_mass >= f_mom0 && f_mass <= f_mom0 + 2))
         return fail(SG_ERR_INVALID, "bad p2g arguments");
@@ -649,6 +656,7 @@ int sg_p2g(sg_grid *g, const float *dev_x, const float *dev_v, int64_t n, float 
     Op o{OP_P2G};
     o.p0 = dev_x;
     o.p1 = (void *)dev_v;
+    o.p3 = (void *)dev_C;
     o.n = n;
     o.f0 = pmass;
     o.i0 = g->phys[f_mass];
@@ -675,12 +683,18 @@ int sg_grid_update(sg_grid *g, int32_t f_mass, int32_t f_mom0, float dt, float g
 
 int sg_g2p(sg_grid *g, float *dev_x, float *dev_v, int64_t n, float dt, int32_t f_mom0)
 {
+    return sg_g2p_apic(g, dev_x, dev_v, nullptr, n, dt, f_mom0);
+}
+
+int sg_g2p_apic(sg_grid *g, float *dev_x, float *dev_v, float *dev_C, int64_t n, float dt, int32_t f_mom0)
+{
     if (!g || n < 0 || (n > 0 && (!dev_x || !dev_v)) || !valid_field(g, f_mom0) || !valid_field(g, f_mom0 + 2))
         return fail(SG_ERR_INVALID, "bad g2p arguments");
     if (n == 0) return SG_OK;
     Op o{OP_G2P};
     o.p1 = dev_x;
     o.p2 = dev_v;
+    o.p3 = dev_C;
     o.n = n;
     o.f0 = dt;
     o.i0 = g->phys[f_mom0];

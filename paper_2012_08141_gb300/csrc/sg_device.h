@@ -165,14 +165,16 @@ void launch_sweep_single(const DevGrid &g, cudaStream_t s, int op, int src, int 
 // tile_sum, perm and bin_list (R^3).  Keys: 8 reach classes per leaf plus one
 // for particles whose stencil misses the domain.
 constexpr long long p2g_num_keys(int R) { return 8LL * R * R * R + 1; }
-int launch_p2g_binned(const DevGrid &g, cudaStream_t s, const float *x, const float *v, long long n, float pmass,
-                      int f_mass, int f_mom0, const LaunchCfg &lc);
+// C: NULL for PIC, else the APIC matrices (n x 9 FP32, row-major).
+int launch_p2g_binned(const DevGrid &g, cudaStream_t s, const float *x, const float *v, const float *C, long long n,
+                      float pmass, int f_mass, int f_mom0, const LaunchCfg &lc);
 void launch_grid_update(const DevGrid &g, cudaStream_t s, int f_mass, int f_mom0, float dt,
                         float gz, int bound, const LaunchCfg &lc);
 // binned: use the bins of the last binned P2G over the same particles (the
 // particle order, leaf list and key ranges) to stage each leaf's
 // neighbourhood of node velocities in shared memory; otherwise input order.
-void launch_g2p(const DevGrid &g, cudaStream_t s, float *x, float *v, long long n, float dt, int f_mom0, int binned,
-                const LaunchCfg &lc);
+// C: NULL for PIC, else APIC, the matrices written there (n x 9 FP32).
+void launch_g2p(const DevGrid &g, cudaStream_t s, float *x, float *v, float *C, long long n, float dt, int f_mom0,
+                int binned, const LaunchCfg &lc);
 
 }  // namespace sg

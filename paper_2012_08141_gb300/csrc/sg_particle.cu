@@ -1,14 +1,19 @@
 // sg_particle.cu -- particle-grid transfers on the sparse grid (the hybrid
 // Lagrangian-Eulerian workload of AsyncTaichi Sec. 8.3): P2G with activation,
-// the grid velocity update, and G2P.  Quadratic B-spline weights, PIC
-// transfers; the unit cube holds N^3 nodes, dx = 1/N, node (i,j,k) at
-// (i,j,k)*dx, particle component a maps to grid axis a (z -> k).
+// the grid velocity update, and G2P, as PIC transfers or as affine (APIC)
+// transfers with a per-particle 3x3 matrix C (the transfers of MLS-MPM);
+// quadratic B-spline weights.  The unit cube holds N^3 nodes, dx = 1/N, node
+// (i,j,k) at (i,j,k)*dx, particle component a maps to grid axis a (z -> k).
+// C is stored row-major, 9 floats per particle: (C d)_a = sum_b C[3a+b] d_b.
+// For quadratic B-splines sum_n w d d^T = dx^2/4 I, so the APIC G2P matrix is
+// C = (4/dx^2) sum_n w v_n d^T with d = node - x_p = ((a,b,c) - fx) dx.
 #include "sg_common.cuh"
 
 namespace sg {
 
 struct Spline {
     int base;
+    float fx;  // X - base, in [0.5, 1.5)
     float w[3];
 };
 
@@ -22,6 +27,7 @@ __device__ __forceinline__ Spline bspline(float x, int N)
     const float bf = floorf(__fsub_rn(X, 0.5f));
     const float fx = __fsub_rn(X, bf);
     s.base = (int)bf;
+    s.fx = fx;
     const float a = 1.5f - fx, c = fx - 1.0f, d = fx - 0.5f;
     s.w[0] = 0.5f * a * a;
     s.w[1] = 0.75f - c * c;
@@ -68,15 +74,18 @@ void launch_grid_update(const DevGrid &g, cudaStream_t s, int f_mass, int f_mom0
     k_grid_update<<<lc.num_sms * 8, 256, 0, s>>>(g, f_mass, f_mom0, dt, gz, bound);
 }
 
-// G2P velocity of one particle read node by node from the grid (a stored
-// value at an inactive node is 0; out-of-domain and unallocated nodes are
-// skipped).
-__device__ __forceinline__ float3 g2p_from_grid(const DevGrid &g, const float *__restrict__ f0,
-                                               const float *__restrict__ f1, const float *__restrict__ f2,
-                                               const Spline &sx, const Spline &sy, const Spline &sz)
+// G2P of one particle read node by node from the grid (a stored value at an
+// inactive node is 0; out-of-domain and unallocated nodes are skipped).
+// Returns v_p in u and, for APIC, C_p in c.
+template <bool APIC>
+__device__ __forceinline__ void g2p_from_grid(const DevGrid &g, const float *__restrict__ f0,
+                                              const float *__restrict__ f1, const float *__restrict__ f2,
+                                              const Spline &sx, const Spline &sy, const Spline &sz, float3 &u,
+                                              float (&c)[9])
 {
     const int L = g.L, lg2 = g.lg2, N = g.N;
     float ux = 0.f, uy = 0.f, uz = 0.f;
+    float S[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};  // sum w v_e t_f
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         const int i = sx.base + a;
@@ -87,22 +96,38 @@ __device__ __forceinline__ float3 g2p_from_grid(const DevGrid &g, const float *_
             if ((unsigned)j >= (unsigned)N) continue;
             const float wxy = sx.w[a] * sy.w[b];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const int k = sz.base + c;
+            for (int cc = 0; cc < 3; ++cc) {
+                const int k = sz.base + cc;
                 if ((unsigned)k >= (unsigned)N) continue;
                 const long long lb = ((long long)(i >> lg2) * g.R + (j >> lg2)) * g.R + (k >> lg2);
                 const int slot = __ldg(g.root + lb);
                 if (slot < 0) continue;
                 const int l = (((i & (L - 1)) << lg2) + (j & (L - 1))) * L + (k & (L - 1));
                 const long long idx = ((long long)slot << (3 * lg2)) + l;
-                const float w = wxy * sz.w[c];
-                ux += w * __ldg(f0 + idx);
-                uy += w * __ldg(f1 + idx);
-                uz += w * __ldg(f2 + idx);
+                const float w = wxy * sz.w[cc];
+                const float wv[3] = {w * __ldg(f0 + idx), w * __ldg(f1 + idx), w * __ldg(f2 + idx)};
+                ux += wv[0];
+                uy += wv[1];
+                uz += wv[2];
+                if (APIC) {
+#pragma unroll
+                    for (int e = 0; e < 3; ++e) {
+                        S[e][0] = fmaf((float)a, wv[e], S[e][0]);
+                        S[e][1] = fmaf((float)b, wv[e], S[e][1]);
+                        S[e][2] = fmaf((float)cc, wv[e], S[e][2]);
+                    }
+                }
             }
         }
     }
-    return make_float3(ux, uy, uz);
+    u = make_float3(ux, uy, uz);
+    if (APIC) {
+        const float s4 = 4.f * (float)N, fx[3] = {sx.fx, sy.fx, sz.fx}, ue[3] = {ux, uy, uz};
+#pragma unroll
+        for (int e = 0; e < 3; ++e)
+#pragma unroll
+            for (int f = 0; f < 3; ++f) c[3 * e + f] = s4 * fmaf(-fx[f], ue[e], S[e][f]);
+    }
 }
 
 // A float triple at a[3p..3p+2]; with pair set (the array is 8-byte
@@ -136,22 +161,31 @@ __device__ __forceinline__ void store3(float *__restrict__ a, long long p, float
     }
 }
 
-__device__ __forceinline__ void g2p_store(float *__restrict__ x, float *__restrict__ v, long long p, float px, float py,
-                                          float pz, float3 u, float dt, bool pair)
+template <bool APIC>
+__device__ __forceinline__ void g2p_store(float *__restrict__ x, float *__restrict__ v, float *__restrict__ C,
+                                          long long p, float3 xp, float3 u, const float (&c)[9], float dt, bool pair)
 {
     store3(v, p, u, pair);
-    store3(x, p, make_float3(px + dt * u.x, py + dt * u.y, pz + dt * u.z), pair);
+    store3(x, p, make_float3(xp.x + dt * u.x, xp.y + dt * u.y, xp.z + dt * u.z), pair);
+    if (APIC) {
+#pragma unroll
+        for (int q = 0; q < 9; ++q) C[9 * p + q] = c[q];
+    }
 }
 
 // G2P in input order, every node read from the grid.
-__global__ void __launch_bounds__(256) k_g2p(DevGrid g, float *__restrict__ x, float *__restrict__ v, long long n, float dt,
-                                             int f_mom0)
+template <bool APIC>
+__global__ void __launch_bounds__(256) k_g2p(DevGrid g, float *__restrict__ x, float *__restrict__ v,
+                                             float *__restrict__ C, long long n, float dt, int f_mom0)
 {
     const float *f0 = g.field[f_mom0], *f1 = g.field[f_mom0 + 1], *f2 = g.field[f_mom0 + 2];
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
-        const float px = x[3 * p], py = x[3 * p + 1], pz = x[3 * p + 2];
-        const Spline sx = bspline(px, g.N), sy = bspline(py, g.N), sz = bspline(pz, g.N);
-        g2p_store(x, v, p, px, py, pz, g2p_from_grid(g, f0, f1, f2, sx, sy, sz), dt, false);
+        const float3 xp = load3(x, p, false);
+        const Spline sx = bspline(xp.x, g.N), sy = bspline(xp.y, g.N), sz = bspline(xp.z, g.N);
+        float3 u;
+        float c[9];
+        g2p_from_grid<APIC>(g, f0, f1, f2, sx, sy, sz, u, c);
+        g2p_store<APIC>(x, v, C, p, xp, u, c, dt, false);
     }
 }
 
@@ -163,10 +197,78 @@ __global__ void __launch_bounds__(256) k_g2p(DevGrid g, float *__restrict__ x, f
 // that range (its position changed since the binning) reads the grid node by
 // node, as do the particles whose stencil misses the domain (the last key).
 template <int L>
-__global__ void __launch_bounds__(256, 6) k_g2p_binned(DevGrid g, float *__restrict__ x, float *__restrict__ v, float dt,
-                                                       int f_mom0, bool pair)
+__device__ __forceinline__ void stage_velocities(const DevGrid &g, const float *__restrict__ f0,
+                                                 const float *__restrict__ f1, const float *__restrict__ f2, int oi,
+                                                 int oj, int ok, float (*s_u)[(L + 4) * (L + 4) * (L + 4)])
 {
     constexpr int LG2 = (L == 8) ? 3 : 2, B = L + 4, NB = B * B * B;
+    const int N = g.N, R = g.R;
+    for (int nd = threadIdx.x; nd < NB; nd += blockDim.x) {
+        const int i = oi - 2 + nd / (B * B), j = oj - 2 + (nd / B) % B, k = ok - 2 + nd % B;
+        float u0 = 0.f, u1 = 0.f, u2 = 0.f;
+        if ((unsigned)i < (unsigned)N && (unsigned)j < (unsigned)N && (unsigned)k < (unsigned)N) {
+            const int slot = __ldg(g.root + ((long long)(i >> LG2) * R + (j >> LG2)) * R + (k >> LG2));
+            if (slot >= 0) {
+                const long long idx =
+                    ((long long)slot << (3 * LG2)) + (((i & (L - 1)) << LG2) + (j & (L - 1))) * L + (k & (L - 1));
+                u0 = __ldg(f0 + idx);
+                u1 = __ldg(f1 + idx);
+                u2 = __ldg(f2 + idx);
+            }
+        }
+        s_u[0][nd] = u0;
+        s_u[1][nd] = u1;
+        s_u[2][nd] = u2;
+    }
+}
+
+// G2P of one particle from a staged block (ri, rj, rk: its base relative to
+// the block's first node).  APIC as in g2p_from_grid.
+template <int B, bool APIC>
+__device__ __forceinline__ void g2p_from_block(const float (*s_u)[B * B * B], int ri, int rj, int rk, int N,
+                                               const Spline &sx, const Spline &sy, const Spline &sz, float3 &u,
+                                               float (&c)[9])
+{
+    float ux = 0.f, uy = 0.f, uz = 0.f;
+    float S[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const float wxy = sx.w[a] * sy.w[b];
+#pragma unroll
+            for (int cc = 0; cc < 3; ++cc) {
+                const int nd = ((ri + a) * B + (rj + b)) * B + (rk + cc);
+                const float w = wxy * sz.w[cc];
+                const float wv[3] = {w * s_u[0][nd], w * s_u[1][nd], w * s_u[2][nd]};
+                ux += wv[0];
+                uy += wv[1];
+                uz += wv[2];
+                if (APIC) {
+#pragma unroll
+                    for (int e = 0; e < 3; ++e) {
+                        if (a) S[e][0] = fmaf((float)a, wv[e], S[e][0]);
+                        if (b) S[e][1] = fmaf((float)b, wv[e], S[e][1]);
+                        if (cc) S[e][2] = fmaf((float)cc, wv[e], S[e][2]);
+                    }
+                }
+            }
+        }
+    u = make_float3(ux, uy, uz);
+    if (APIC) {
+        const float s4 = 4.f * (float)N, fx[3] = {sx.fx, sy.fx, sz.fx}, ue[3] = {ux, uy, uz};
+#pragma unroll
+        for (int e = 0; e < 3; ++e)
+#pragma unroll
+            for (int f = 0; f < 3; ++f) c[3 * e + f] = s4 * fmaf(-fx[f], ue[e], S[e][f]);
+    }
+}
+
+template <int L, bool APIC>
+__global__ void __launch_bounds__(256, APIC ? 4 : 6) k_g2p_binned(DevGrid g, float *__restrict__ x, float *__restrict__ v,
+                                                       float *__restrict__ C, float dt, int f_mom0, bool pair)
+{
+    constexpr int B = L + 4, NB = B * B * B;
     __shared__ float s_u[3][NB];
     const int N = g.N, R = g.R;
     const float *f0 = g.field[f_mom0], *f1 = g.field[f_mom0 + 1], *f2 = g.field[f_mom0 + 2];
@@ -181,23 +283,7 @@ __global__ void __launch_bounds__(256, 6) k_g2p_binned(DevGrid g, float *__restr
             oi = (int)(b / ((long long)R * R)) * L;
             oj = (int)((b / R) % R) * L;
             ok = (int)(b % R) * L;
-            for (int nd = threadIdx.x; nd < NB; nd += 256) {
-                const int i = oi - 2 + nd / (B * B), j = oj - 2 + (nd / B) % B, k = ok - 2 + nd % B;
-                float u0 = 0.f, u1 = 0.f, u2 = 0.f;
-                if ((unsigned)i < (unsigned)N && (unsigned)j < (unsigned)N && (unsigned)k < (unsigned)N) {
-                    const int slot = __ldg(g.root + ((long long)(i >> LG2) * R + (j >> LG2)) * R + (k >> LG2));
-                    if (slot >= 0) {
-                        const long long idx =
-                            ((long long)slot << (3 * LG2)) + (((i & (L - 1)) << LG2) + (j & (L - 1))) * L + (k & (L - 1));
-                        u0 = __ldg(f0 + idx);
-                        u1 = __ldg(f1 + idx);
-                        u2 = __ldg(f2 + idx);
-                    }
-                }
-                s_u[0][nd] = u0;
-                s_u[1][nd] = u1;
-                s_u[2][nd] = u2;
-            }
+            stage_velocities<L>(g, f0, f1, f2, oi, oj, ok, s_u);
             __syncthreads();
         } else {
             beg = g.bin_off[oob_key];
@@ -206,50 +292,52 @@ __global__ void __launch_bounds__(256, 6) k_g2p_binned(DevGrid g, float *__restr
         for (int q = beg + threadIdx.x; q < end; q += blockDim.x) {
             const long long p = g.perm[q];
             const float3 xp = load3(x, p, pair);
-            const float px = xp.x, py = xp.y, pz = xp.z;
-            const Spline sx = bspline(px, N), sy = bspline(py, N), sz = bspline(pz, N);
+            const Spline sx = bspline(xp.x, N), sy = bspline(xp.y, N), sz = bspline(xp.z, N);
             const int ri = sx.base - oi + 2, rj = sy.base - oj + 2, rk = sz.base - ok + 2;
             float3 u;
+            float c[9];
             if (bl < used && (unsigned)ri <= (unsigned)(L + 1) && (unsigned)rj <= (unsigned)(L + 1) &&
-                (unsigned)rk <= (unsigned)(L + 1)) {
-                float ux = 0.f, uy = 0.f, uz = 0.f;
-#pragma unroll
-                for (int a = 0; a < 3; ++a)
-#pragma unroll
-                    for (int b = 0; b < 3; ++b) {
-                        const float wxy = sx.w[a] * sy.w[b];
-#pragma unroll
-                        for (int c = 0; c < 3; ++c) {
-                            const int nd = ((ri + a) * B + (rj + b)) * B + (rk + c);
-                            const float w = wxy * sz.w[c];
-                            ux += w * s_u[0][nd];
-                            uy += w * s_u[1][nd];
-                            uz += w * s_u[2][nd];
-                        }
-                    }
-                u = make_float3(ux, uy, uz);
-            } else {
-                u = g2p_from_grid(g, f0, f1, f2, sx, sy, sz);
-            }
-            g2p_store(x, v, p, px, py, pz, u, dt, pair);
+                (unsigned)rk <= (unsigned)(L + 1))
+                g2p_from_block<B, APIC>(s_u, ri, rj, rk, N, sx, sy, sz, u, c);
+            else
+                g2p_from_grid<APIC>(g, f0, f1, f2, sx, sy, sz, u, c);
+            g2p_store<APIC>(x, v, C, p, xp, u, c, dt, pair);
         }
         __syncthreads();  // s_u is restaged for the next leaf
     }
 }
 
-void launch_g2p(const DevGrid &g, cudaStream_t s, float *x, float *v, long long n, float dt, int f_mom0, int binned,
-                const LaunchCfg &lc)
+// CTAs of a persistent per-bin kernel: as many as fit on every SM at once.
+template <typename K>
+static int resident_ctas(K kernel, int num_sms)
+{
+    int per = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, 256, 0) != cudaSuccess || per < 1) per = 1;
+    return per * num_sms;
+}
+
+void launch_g2p(const DevGrid &g, cudaStream_t s, float *x, float *v, float *C, long long n, float dt, int f_mom0,
+                int binned, const LaunchCfg &lc)
 {
     if (n <= 0) return;
     if (binned) {
         const bool pair = ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(v)) & 7) == 0;
-        if (g.L == 4) k_g2p_binned<4><<<lc.num_sms * 6, 256, 0, s>>>(g, x, v, dt, f_mom0, pair);
-        else k_g2p_binned<8><<<lc.num_sms * 6, 256, 0, s>>>(g, x, v, dt, f_mom0, pair);
+#define SG_G2PB(LL, AP) k_g2p_binned<LL, AP><<<resident_ctas(k_g2p_binned<LL, AP>, lc.num_sms), 256, 0, s>>>( \
+        g, x, v, C, dt, f_mom0, pair)
+        if (C) {
+            if (g.L == 4) SG_G2PB(4, true);
+            else SG_G2PB(8, true);
+        } else {
+            if (g.L == 4) SG_G2PB(4, false);
+            else SG_G2PB(8, false);
+        }
+#undef SG_G2PB
         return;
     }
     long long blocks = (n + 255) / 256;
     if (blocks > 1 << 20) blocks = 1 << 20;
-    k_g2p<<<(unsigned)blocks, 256, 0, s>>>(g, x, v, n, dt, f_mom0);
+    if (C) k_g2p<true><<<(unsigned)blocks, 256, 0, s>>>(g, x, v, C, n, dt, f_mom0);
+    else k_g2p<false><<<(unsigned)blocks, 256, 0, s>>>(g, x, v, C, n, dt, f_mom0);
 }
 
 }  // namespace sg
@@ -271,6 +359,7 @@ void launch_g2p(const DevGrid &g, cudaStream_t s, float *x, float *v, long long 
 //                    memory, sum each cell's contributions to its 27 nodes in
 //                    registers (one warp per cell) into shared node sums, then
 //                    add the touched nodes to the grid and set their bits
+//                    (PIC, or APIC with the per-particle matrix C)
 // ===========================================================================
 namespace sg {
 
@@ -415,40 +504,61 @@ __global__ void k_p2g_perm(DevGrid g, const float *__restrict__ x, long long n)
     }
 }
 
-// Per bin: stage the bin's particles (stencil weights and pmass * velocity)
-// in shared memory sorted by their base cell.  One warp then takes one
-// occupied cell at a time: lane (a, c, d) < 27 owns the stencil node
-// base + (a, c, d) shared by every particle of that cell and walks the
-// cell's particles in step with the other lanes (each shared-memory read is a
-// broadcast), summing its node's contributions in registers; the cell's 27
-// sums are then added to a shared block of (L+2)^3 node accumulators.  A node
-// reached by any stencil is activated (all 27 stencil nodes of every particle
-// are, whatever their weight) and its sums are added to the grid once.  Bins
-// with more particles than the staging capacity are processed in chunks.
+// Quadratic B-spline weight of stencil offset t (0, 1, 2) at spline offset f
+// as a polynomial in f: 0.5(1.5-f)^2, 0.75-(f-1)^2, 0.5(f-0.5)^2.
+struct BsPoly {
+    float a2, a1, a0;
+};
+__device__ __forceinline__ BsPoly bs_poly(int t)
+{
+    BsPoly c;
+    c.a2 = (t == 1) ? -1.f : 0.5f;
+    c.a1 = (t == 0) ? -1.5f : ((t == 1) ? 2.f : -0.5f);
+    c.a0 = (t == 0) ? 1.125f : ((t == 1) ? -0.25f : 0.125f);
+    return c;
+}
+__device__ __forceinline__ float bs_eval(const BsPoly &c, float f) { return fmaf(fmaf(c.a2, f, c.a1), f, c.a0); }
+
+// Per bin: stage the bin's particles in shared memory sorted by their base
+// cell, as float4 records: (fx_i, fx_j, fx_k, m) and the momentum terms --
+// PIC: m v; APIC: q = m v - m dx C fx and the 9 entries of m dx C, so that
+// the momentum a particle gives stencil node base + t is w (q + m dx C t).
+// One warp then takes one occupied cell at a time: lane t = (a, b, c) < 27
+// owns the stencil node base + t shared by every particle of that cell and
+// walks the cell's particles in step with the other lanes (each shared read
+// is a broadcast), computing its own weights from fx and summing its node's
+// contributions in registers; the cell's 27 sums are then added to a shared
+// block of (L+2)^3 node accumulators.  A node reached by any stencil is
+// activated (all 27 stencil nodes of every particle are, whatever their
+// weight) and its sums are added to the grid once.  Bins with more particles
+// than the staging capacity are processed in chunks.
 //
 // Base cells are indexed relative to the leaf origin o shifted by +2: a
 // particle binned to leaf o has base in [o, o + L - 1], or base -2 / -1 at the
 // low domain face (its bin is clamped to leaf 0), so the shifted index is in
 // [0, L + 1].  Block node n (0 <= n < L + 2 per axis) is grid node o + n.
-template <int L>
+template <int L, bool APIC>
 __global__ void __launch_bounds__(256) k_p2g_gather(DevGrid g, const float *__restrict__ x, const float *__restrict__ v,
-                                                    float pmass, int f_mass, int f_mom0)
+                                                    const float *__restrict__ C, float pmass, int f_mass, int f_mom0)
 {
     constexpr int B = L + 2, NB = B * B * B, LG2 = (L == 8) ? 3 : 2;
     constexpr int C1 = L + 2, NC = C1 * C1 * C1;  // shifted base cells
     constexpr int CAP = (L == 8) ? 256 : 512;       // staged particles per chunk
     constexpr int PPT = CAP / 256;                  // staged particles per thread
+    constexpr int NREC = APIC ? 4 : 2;              // float4 records per particle
     constexpr int NWARP = 8;
-    __shared__ float s_w[CAP][9];                   // weights w[axis][0..2], sorted by cell
-    __shared__ float4 s_mv[CAP];                    // pmass, pmass * v
+    __shared__ float4 s_rec[NREC][CAP];
     __shared__ float s_acc[4][NB];                  // block node sums
     __shared__ uint8_t s_hit[NB];
     __shared__ int s_cnt[NC + 1];
     __shared__ int s_start[NC + 1];
     const int N = g.N, R = g.R;
+    const float dx = 1.f / (float)N;
     const int warp = threadIdx.x >> 5, lane = lane_id();
     // this lane's stencil offset (lanes 27..31 idle in the cell loop)
     const int la = lane / 9, lc = (lane / 3) % 3, ld = lane % 3;
+    const BsPoly pa = bs_poly(la), pb = bs_poly(lc), pc = bs_poly(ld);
+    const float ta = (float)la, tb = (float)lc, tc = (float)ld;
     float *fm = g.field[f_mass];
     float *f0 = g.field[f_mom0], *f1 = g.field[f_mom0 + 1], *f2 = g.field[f_mom0 + 2];
     bool changed = false;
@@ -500,17 +610,26 @@ __global__ void __launch_bounds__(256) k_p2g_gather(DevGrid g, const float *__re
                 if (rcell[u] < 0) continue;
                 const int pos = s_start[rcell[u]] + rrank[u];
                 const long long p = rp[u];
-                const Spline sx = bspline(__ldg(x + 3 * p + 0), N);
-                const Spline sy = bspline(__ldg(x + 3 * p + 1), N);
-                const Spline sz = bspline(__ldg(x + 3 * p + 2), N);
+                const float fx = bspline(__ldg(x + 3 * p + 0), N).fx;
+                const float fy = bspline(__ldg(x + 3 * p + 1), N).fx;
+                const float fz = bspline(__ldg(x + 3 * p + 2), N).fx;
+                const float mv0 = pmass * __ldg(v + 3 * p + 0), mv1 = pmass * __ldg(v + 3 * p + 1),
+                            mv2 = pmass * __ldg(v + 3 * p + 2);
+                s_rec[0][pos] = make_float4(fx, fy, fz, pmass);
+                if (!APIC) {
+                    s_rec[1][pos] = make_float4(mv0, mv1, mv2, 0.f);
+                } else {
+                    float m[9];
+                    const float md = pmass * dx;
 #pragma unroll
-                for (int t = 0; t < 3; ++t) {
-                    s_w[pos][t] = sx.w[t];
-                    s_w[pos][3 + t] = sy.w[t];
-                    s_w[pos][6 + t] = sz.w[t];
+                    for (int e = 0; e < 9; ++e) m[e] = md * __ldg(C + 9 * p + e);
+                    const float q0 = mv0 - (m[0] * fx + m[1] * fy + m[2] * fz);
+                    const float q1 = mv1 - (m[3] * fx + m[4] * fy + m[5] * fz);
+                    const float q2 = mv2 - (m[6] * fx + m[7] * fy + m[8] * fz);
+                    s_rec[1][pos] = make_float4(q0, q1, q2, m[0]);
+                    s_rec[2][pos] = make_float4(m[1], m[2], m[3], m[4]);
+                    s_rec[3][pos] = make_float4(m[5], m[6], m[7], m[8]);
                 }
-                s_mv[pos] = make_float4(pmass, pmass * __ldg(v + 3 * p + 0), pmass * __ldg(v + 3 * p + 1),
-                                        pmass * __ldg(v + 3 * p + 2));
                 g.perm[c0 + pos] = rp[u];  // the chunk's order becomes cell order (G2P reads it)
             }
             __syncthreads();
@@ -520,12 +639,24 @@ __global__ void __launch_bounds__(256) k_p2g_gather(DevGrid g, const float *__re
                 const int ci = cell / (C1 * C1), cj = (cell / C1) % C1, ck = cell % C1;
                 float m = 0.f, m0 = 0.f, m1 = 0.f, m2 = 0.f;
                 for (int pp = p0; pp < p1; ++pp) {
-                    const float wt = s_w[pp][la] * s_w[pp][3 + lc] * s_w[pp][6 + ld];
-                    const float4 mv = s_mv[pp];
-                    m += wt * mv.x;
-                    m0 += wt * mv.y;
-                    m1 += wt * mv.z;
-                    m2 += wt * mv.w;
+                    const float4 r0 = s_rec[0][pp];
+                    const float w = bs_eval(pa, r0.x) * bs_eval(pb, r0.y) * bs_eval(pc, r0.z);
+                    const float4 r1 = s_rec[1][pp];
+                    m = fmaf(w, r0.w, m);
+                    if (!APIC) {
+                        m0 = fmaf(w, r1.x, m0);
+                        m1 = fmaf(w, r1.y, m1);
+                        m2 = fmaf(w, r1.z, m2);
+                    } else {
+                        const float4 r2 = s_rec[2][pp], r3 = s_rec[3][pp];
+                        // rows of m dx C: (r1.w, r2.x, r2.y), (r2.z, r2.w, r3.x), (r3.y, r3.z, r3.w)
+                        const float u0 = fmaf(r1.w, ta, fmaf(r2.x, tb, fmaf(r2.y, tc, r1.x)));
+                        const float u1 = fmaf(r2.z, ta, fmaf(r2.w, tb, fmaf(r3.x, tc, r1.y)));
+                        const float u2 = fmaf(r3.y, ta, fmaf(r3.z, tb, fmaf(r3.w, tc, r1.z)));
+                        m0 = fmaf(w, u0, m0);
+                        m1 = fmaf(w, u1, m1);
+                        m2 = fmaf(w, u2, m2);
+                    }
                 }
                 const int ni = ci - 2 + la, nj = cj - 2 + lc, nk = ck - 2 + ld;
                 if (lane < 27 && ni >= 0 && nj >= 0 && nk >= 0) {  // negative: outside the domain
@@ -564,8 +695,8 @@ __global__ void __launch_bounds__(256) k_p2g_gather(DevGrid g, const float *__re
     if (changed) mark_dirty(g);
 }
 
-int launch_p2g_binned(const DevGrid &g, cudaStream_t s, const float *x, const float *v, long long n, float pmass,
-                      int f_mass, int f_mom0, const LaunchCfg &lc)
+int launch_p2g_binned(const DevGrid &g, cudaStream_t s, const float *x, const float *v, const float *C, long long n,
+                      float pmass, int f_mass, int f_mom0, const LaunchCfg &lc)
 {
     const long long nscan = p2g_num_keys(g.R);
     const int ntiles = (int)((nscan + kBinTile - 1) / kBinTile);
@@ -582,8 +713,16 @@ int launch_p2g_binned(const DevGrid &g, cudaStream_t s, const float *x, const fl
     launches += 5;
     k_p2g_perm<<<(unsigned)pblocks, 256, 0, s>>>(g, x, n);
     ++launches;
-    if (g.L == 4) k_p2g_gather<4><<<lc.num_sms * 5, 256, 0, s>>>(g, x, v, pmass, f_mass, f_mom0);
-    else k_p2g_gather<8><<<lc.num_sms * 2, 256, 0, s>>>(g, x, v, pmass, f_mass, f_mom0);
+#define SG_GATHER(LL, AP) k_p2g_gather<LL, AP><<<resident_ctas(k_p2g_gather<LL, AP>, lc.num_sms), 256, 0, s>>>( \
+        g, x, v, C, pmass, f_mass, f_mom0)
+    if (C) {
+        if (g.L == 4) SG_GATHER(4, true);
+        else SG_GATHER(8, true);
+    } else {
+        if (g.L == 4) SG_GATHER(4, false);
+        else SG_GATHER(8, false);
+    }
+#undef SG_GATHER
     ++launches;
     return launches;
 }

@@ -148,6 +148,71 @@ def test_p2g_g2p_unaligned_views():
     g.close()
 
 
+def apic_step_compare(spec, max_leaves, C0, interior=True, shift=None):
+    """APIC P2G, grid update, APIC G2P against the oracle: structure exact,
+    fields, v and C within TOL normwise, x within a few ulps.  shift, if
+    given, moves the positions between the grid update and G2P (same shift on
+    both sides)."""
+    import torch
+    g, og = make(spec, max_leaves)
+    x = torch.from_numpy(spec.x).cuda()
+    v = torch.from_numpy(spec.v).cuda()
+    C = torch.from_numpy(C0).cuda()
+    ox, ov, oC = spec.x.copy(), spec.v.copy(), C0.copy()
+    g.p2g_apic(x, v, C, spec.pmass, 0, 1)
+    og.p2g_apic(ox, ov, oC, spec.pmass, 0, 1)
+    gb, gm = g.read_structure()
+    ob, om = og.structure()
+    np.testing.assert_array_equal(gb, ob)
+    np.testing.assert_array_equal(gm, om)
+    for f in range(4):
+        assert rel_linf(g.read_field(f), og.read_field(f)) <= TOL, f
+    g.grid_update(0, 1, spec.dt, spec.gravity, spec.bound)
+    og.grid_update(0, 1, spec.dt, spec.gravity, spec.bound)
+    if shift is not None:
+        g.sync()
+        xm = (ox + shift).astype(np.float32)
+        x.copy_(torch.from_numpy(xm))
+        torch.cuda.synchronize()
+        ox = xm.copy()
+    g.g2p_apic(x, v, C, spec.dt, 1)
+    og.g2p_apic(ox, ov, oC, spec.dt, 1)
+    g.sync()
+    assert rel_linf(v.cpu().numpy(), ov) <= TOL
+    assert rel_linf(C.cpu().numpy(), oC) <= TOL
+    assert np.max(np.abs(x.cpu().numpy().astype(np.float64) - ox)) <= 4e-7
+    g.close()
+
+
+def _affine(n, seed, scale=5.0):
+    return np.random.default_rng(seed).normal(0.0, scale, size=(n, 9)).astype(np.float32)
+
+
+@pytest.mark.parametrize("L", [4, 8])
+def test_apic_p2g_g2p_small(L):
+    spec = spheres_particles(seed=21, n=20000, N=64, L=L, r_min=0.1, r_max=0.2)
+    apic_step_compare(spec, (64 // L) ** 3, _affine(spec.n, 22))
+
+
+@pytest.mark.parametrize("L", [4, 8])
+def test_apic_domain_faces(L):
+    spec = cube_particles(seed=23 + L, n=3000, N=64, L=L, pad_cells=3.0)
+    apic_step_compare(spec, (64 // L) ** 3, _affine(spec.n, 24), interior=False)
+
+
+def test_apic_g2p_positions_moved():
+    spec = spheres_particles(seed=25, n=20000, N=64, L=4, r_min=0.1, r_max=0.2)
+    rng = np.random.default_rng(26)
+    shift = rng.uniform(-6.0, 6.0, size=spec.x.shape) / spec.N
+    shift[rng.random(spec.n) < 0.5] = 0.0
+    apic_step_compare(spec, 4096, _affine(spec.n, 27), shift=shift)
+
+
+def test_apic_full_size_one_step():
+    spec = spheres_particles(seed=0)            # 2M particles, 256^3, 4^3 leaves
+    apic_step_compare(spec, 262144, _affine(spec.n, 28))
+
+
 def test_p2g_g2p_full_size_one_step():
     spec = spheres_particles(seed=0)            # 2M particles, 256^3, 4^3 leaves
     one_step_compare(spec, 262144)
