@@ -190,6 +190,25 @@ int sg_p2g_apic(sg_grid *g, const float *dev_x, const float *dev_v, const float 
  * FP32 row-major, device, borrowed).  dev_C == NULL is sg_g2p. */
 int sg_g2p_apic(sg_grid *g, float *dev_x, float *dev_v, float *dev_C, int64_t n, float dt, int32_t f_mom0);
 
+/* Fused G2P2G (Sec. 8.3): the APIC G2P of one step and the APIC P2G of the
+ * next in one pass over the particles, the affine matrix C held on chip and
+ * never stored (Sec. 6.5, dead-store elimination).  The result is that of
+ *   sg_g2p_apic(src, dev_x, dev_v, C, n, dt, f_vel0);
+ *   sg_p2g_apic(dst, dev_x, dev_v, C, n, pmass, f_mass, f_mom0);
+ * for some C that is then discarded: velocities are read from src fields
+ * f_vel0..f_vel0+2 (after its grid update), x and v are overwritten, and
+ * dst's stencil nodes of the new positions are activated (its leaves are
+ * allocated inside the kernel) and receive mass and affine momentum.  src and
+ * dst are distinct grids with the same res and leaf size created on the same
+ * stream; a binned P2G over the same dev_x and n must have run on src or dst
+ * (its particle order and bins are reused; particles that have since left
+ * their bin's neighbourhood take slower exact paths).  Flushes src, then
+ * queues and flushes the op on dst; dev_x, dev_v borrowed until the next sync
+ * of dst.  Errors: SG_ERR_INVALID (arguments, no bins), pool exhaustion and
+ * timeouts latched on dst. */
+int sg_g2p2g(sg_grid *src, sg_grid *dst, float *dev_x, float *dev_v, int64_t n, float dt, int32_t f_vel0,
+             float pmass, int32_t f_mass, int32_t f_mom0);
+
 /* Exchange the storage behind field indices a and b (no device work). */
 int sg_swap(sg_grid *g, int32_t a, int32_t b);
 

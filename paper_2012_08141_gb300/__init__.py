@@ -87,6 +87,7 @@ def load_library(build: bool = True) -> ctypes.CDLL:
         "sg_g2p": [P, P, P, I64, F, I32],
         "sg_p2g_apic": [P, P, P, P, I64, F, I32, I32],
         "sg_g2p_apic": [P, P, P, P, I64, F, I32],
+        "sg_g2p2g": [P, P, P, P, I64, F, I32, F, I32, I32],
         "sg_swap": [P, I32, I32],
         "sg_flush": [P],
         "sg_sync": [P],
@@ -251,6 +252,15 @@ class Grid:
         assert C.numel() == 3 * x.numel()
         self._borrowed += [x, v, C]
         self._c(self.lib.sg_g2p_apic(self.h, _ptr(x), _ptr(v), _ptr(C), x.numel() // 3, float(dt), int(f_mom0)))
+
+    def g2p2g(self, dst: "Grid", x, v, dt: float, f_vel0: int, pmass: float, f_mass: int, f_mom0: int):
+        """Fused APIC G2P from this grid and APIC P2G into dst (C never stored)."""
+        for t in (x, v):
+            assert t.is_cuda and str(t.dtype) == "torch.float32" and t.is_contiguous()
+        self._borrowed += [x, v]
+        dst._borrowed += [x, v]
+        self._c(self.lib.sg_g2p2g(self.h, dst.h, _ptr(x), _ptr(v), x.numel() // 3, float(dt), int(f_vel0),
+                                  float(pmass), int(f_mass), int(f_mom0)))
 
     def g2p(self, x, v, dt: float, f_mom0: int):
         for t in (x, v):

@@ -53,7 +53,7 @@ int fail(int code, const char *fmt, ...)
 }
 
 enum OpKind { OP_ACT_SHELL, OP_ACT_COORDS, OP_DEACT, OP_LISTGEN, OP_STENCIL, OP_SUM, OP_P2G, OP_GRID_UPDATE, OP_G2P, OP_TEST_WAIT,
-              OP_FILL };
+              OP_FILL, OP_G2P2G };
 
 struct Op {
     OpKind kind;
@@ -65,6 +65,7 @@ struct Op {
     int strict = 0;
     const void *p0 = nullptr;
     void *p1 = nullptr, *p2 = nullptr, *p3 = nullptr;
+    const sg_grid *peer = nullptr, *bins = nullptr;  // G2P2G: source grid, holder of the particle bins
     long long n = 0;
     float f0 = 0.f, f1 = 0.f;
     int i0 = 0, i1 = 0, i2 = 0;
@@ -381,6 +382,15 @@ int do_flush(sg_grid *g)
                 }
                 ++i;
                 break;
+            case OP_G2P2G:
+                if (!g->dry)
+                    launch_g2p2g(o.peer->dev, g->dev, o.bins->dev, g->stream, (float *)o.p1, (float *)o.p2, o.n, o.f0,
+                                 o.i0, o.f1, o.i1, o.i2, g->lc);
+                rc = after_launch(g, "g2p2g");
+                g->mask_ver++;
+                g->stats.act_launched++;
+                ++i;
+                break;
             case OP_G2P:
                 if (!g->dry)
                     launch_g2p(g->dev, g->stream, (float *)o.p1, (float *)o.p2, (float *)o.p3, o.n, o.f0, o.i0,
@@ -398,6 +408,7 @@ int map_device_error(int bits)
 {
     if (bits & kErrPool) return fail(SG_ERR_POOL_EXHAUSTED, "leaf pool exhausted (max_leaves too small)");
     if (bits & kErrTimeout) return fail(SG_ERR_TIMEOUT, "a bounded device-side wait gave up");
+    if (bits & kErrCheck) return fail(SG_ERR_CUDA, "a kernel's address self-check failed (the access was skipped)");
     return SG_OK;
 }
 
@@ -701,6 +712,43 @@ int sg_g2p_apic(sg_grid *g, float *dev_x, float *dev_v, float *dev_C, int64_t n,
     if (g->phys[f_mom0 + 1] != o.i0 + 1 || g->phys[f_mom0 + 2] != o.i0 + 2)
         return fail(SG_ERR_INVALID, "momentum fields must be three consecutive unswapped fields");
     return push(g, o);
+}
+
+int sg_g2p2g(sg_grid *src, sg_grid *dst, float *dev_x, float *dev_v, int64_t n, float dt, int32_t f_vel0, float pmass,
+             int32_t f_mass, int32_t f_mom0)
+{
+    if (!src || !dst || src == dst || n < 0 || (n > 0 && (!dev_x || !dev_v)))
+        return fail(SG_ERR_INVALID, "bad g2p2g arguments");
+    if (src->dev.N != dst->dev.N || src->dev.L != dst->dev.L || src->stream != dst->stream || src->dry != dst->dry)
+        return fail(SG_ERR_INVALID, "g2p2g grids must share resolution, leaf size and stream");
+    if (!valid_field(src, f_vel0) || !valid_field(src, f_vel0 + 2) || !valid_field(dst, f_mass) ||
+        !valid_field(dst, f_mom0) || !valid_field(dst, f_mom0 + 2) || (f_mass >= f_mom0 && f_mass <= f_mom0 + 2))
+        return fail(SG_ERR_INVALID, "bad g2p2g field indices");
+    Op o{OP_G2P2G};
+    o.i0 = src->phys[f_vel0];
+    o.i1 = dst->phys[f_mass];
+    o.i2 = dst->phys[f_mom0];
+    if (src->phys[f_vel0 + 1] != o.i0 + 1 || src->phys[f_vel0 + 2] != o.i0 + 2 || dst->phys[f_mom0 + 1] != o.i2 + 1 ||
+        dst->phys[f_mom0 + 2] != o.i2 + 2)
+        return fail(SG_ERR_INVALID, "velocity and momentum fields must be three consecutive unswapped fields");
+    if (n == 0) return SG_OK;
+    // queued work of both grids (src's P2G and grid update, dst's deactivation)
+    // runs first on the shared stream
+    int rc = do_flush(src);
+    if (rc || (rc = do_flush(dst))) return rc;
+    const sg_grid *bins = (src->p2g_x == dev_x && src->p2g_n == n)   ? src
+                          : (dst->p2g_x == dev_x && dst->p2g_n == n) ? dst
+                                                                     : nullptr;
+    if (!bins) return fail(SG_ERR_INVALID, "g2p2g needs a binned P2G over the same particles on src or dst first");
+    o.p1 = dev_x;
+    o.p2 = dev_v;
+    o.n = n;
+    o.f0 = dt;
+    o.f1 = pmass;
+    o.peer = src;
+    o.bins = bins;
+    if ((rc = push(dst, o))) return rc;
+    return do_flush(dst);  // launched now: later src ops cannot run before it
 }
 
 int sg_swap(sg_grid *g, int32_t a, int32_t b)

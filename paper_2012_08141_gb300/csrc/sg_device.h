@@ -33,6 +33,7 @@ constexpr int kMaxFields = 16;
 enum ErrBits : int32_t {
     kErrPool = 1,     // leaf pool exhausted
     kErrTimeout = 2,  // a bounded wait gave up
+    kErrCheck = 4,    // a kernel's own address check failed; the access was skipped
 };
 
 struct Ctrl {
@@ -45,7 +46,8 @@ struct Ctrl {
     unsigned long long n_active;   // active voxels of the listed leaves (count kernel)
     unsigned int red_ticket;       // reduction finished CTAs (reset by the last)
     int32_t never_set;    // a flag nothing writes (bounded-wait test)
-    int32_t timeout_site; // which wait gave up (0 none, 1 look-back, 2 test)
+    int32_t timeout_site; // which wait gave up (0 none, 1 look-back, 2 test, 3 leaf allocation)
+                          // or, with kErrCheck, 100 + the failed check
     int32_t bins_used;    // leaves holding particles in the last binned P2G
     int32_t pad[2];
 };
@@ -176,5 +178,12 @@ void launch_grid_update(const DevGrid &g, cudaStream_t s, int f_mass, int f_mom0
 // C: NULL for PIC, else APIC, the matrices written there (n x 9 FP32).
 void launch_g2p(const DevGrid &g, cudaStream_t s, float *x, float *v, float *C, long long n, float dt, int f_mom0,
                 int binned, const LaunchCfg &lc);
+
+// ---- fused G2P2G (sg_g2p2g.cu) ----
+// APIC G2P from src (velocities f_vel0..+2) then APIC P2G with activation
+// into dst (f_mass, f_mom0..+2), C kept on chip; the particles visited in the
+// order and bins of the last binned P2G held by `bins` (src or dst).
+void launch_g2p2g(const DevGrid &src, const DevGrid &dst, const DevGrid &bins, cudaStream_t s, float *x, float *v,
+                  long long n, float dt, int f_vel0, float pmass, int f_mass, int f_mom0, const LaunchCfg &lc);
 
 }  // namespace sg

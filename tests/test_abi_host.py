@@ -220,3 +220,32 @@ def test_scratch_read_later_keeps_store():
     before = g.stats()["stores_removed"]
     launches(g, lambda: (g.diffuse7(0, 1, 0.1), g.box27(1, 2), g.reduce_sum(1, 0)))
     assert g.stats()["stores_removed"] == before
+
+
+def test_g2p2g_argument_checks_and_launches():
+    """sg_g2p2g: distinct grids of the same geometry, momentum/velocity fields
+    consecutive, a binned P2G over the same particles on src or dst; it flushes
+    src and launches one kernel on dst."""
+    lib = sg.load_library()
+    a, b = dry(64, 2, 4), dry(64, 2, 4)
+    c8 = dry(64, 3, 4)
+    x, v, n = 0x10000, 0x20000, 1000
+    args = (ctypes.c_void_p(x), ctypes.c_void_p(v), n, 1e-4, 1, 1.0, 0, 1)
+    assert lib.sg_g2p2g(a.h, a.h, *args) == sg.SG_ERR_INVALID          # src == dst
+    assert lib.sg_g2p2g(a.h, c8.h, *args) == sg.SG_ERR_INVALID         # leaf sizes differ
+    assert lib.sg_g2p2g(a.h, b.h, *args) == sg.SG_ERR_INVALID          # no bins for these particles
+    assert b"binned" in lib.sg_last_error()
+    bad = (ctypes.c_void_p(x), ctypes.c_void_p(v), n, 1e-4, 1, 1.0, 1, 1)   # mass inside momentum
+    assert lib.sg_g2p2g(a.h, b.h, *bad) == sg.SG_ERR_INVALID
+    assert lib.sg_p2g_apic(a.h, ctypes.c_void_p(x), ctypes.c_void_p(v), ctypes.c_void_p(0x30000), n, 1.0, 0, 1) == 0
+    assert lib.sg_flush(a.h) == 0
+    la, lb = a.stats()["launches"], b.stats()["launches"]
+    a.grid_update(0, 1, 1e-4, 9.8, 3)
+    b.deactivate_all()
+    assert lib.sg_g2p2g(a.h, b.h, *args) == 0
+    assert a.stats()["launches"] > la                                   # src flushed (list + update)
+    assert b.stats()["launches"] == lb + 2                              # dst: deactivate + the fused kernel
+    c = dry(64, 2, 4)
+    assert lib.sg_p2g_apic(c.h, ctypes.c_void_p(x), ctypes.c_void_p(v), ctypes.c_void_p(0x30000), n, 1.0, 0, 1) == 0
+    assert lib.sg_g2p2g(c.h, a.h, *args) == 0                           # src's queued P2G counts
+    assert lib.sg_g2p2g(b.h, a.h, *args) == 0                           # bins held by dst (a) also work
