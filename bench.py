@@ -12,6 +12,8 @@ it.  Further legs (skipped with --only fused or on more than one rank):
             after another, fused and eager;
   particles 2M particles in 3 spheres, 256^3 grid of 4^3 leaves: deactivate,
             P2G with activation, grid update, G2P per step;
+  mpm_apic  the same particles with APIC transfers on two grids in turn:
+            separate G2P (C stored) + P2G against the fused G2P2G (C on chip);
   serving   Poisson arrivals of band jobs (1e4..1e7 voxels, 10..200 steps)
             into the continuous-batching server: p50/p99 job latency;
   band1024  the 1024^3 band |dist - 400| < 8, far larger than L2.
@@ -290,6 +292,52 @@ def bench_particles(torch, sg, steps, warmup, flush_buf, stream):
             "grid_atomics_per_s": spec.n * 27 * 4 * steps / t}
 
 
+def bench_mpm_apic(torch, sg, steps, warmup, flush_buf, stream):
+    """2M particles, APIC transfers, two grids used in turn.  Separate form:
+    deactivate, APIC G2P (C stored), APIC P2G (binned again), grid update.
+    Fused form: deactivate, G2P2G (C kept on chip), grid update."""
+    spec = spheres_particles(0)
+    C0 = np.zeros((spec.n, 9), np.float32)
+    out = {"workload": "2M particles in 3 spheres, 256^3 grid of 4^3 leaves, APIC transfers (MLS-MPM, Sec. 8.3)",
+           "particles": spec.n}
+    for form in ("separate", "fused"):
+        A = sg.Grid(spec.N, 2, 4, max_leaves=(spec.N // 4) ** 3, max_sums=1)
+        B = sg.Grid(spec.N, 2, 4, max_leaves=(spec.N // 4) ** 3, max_sums=1)
+        x = torch.from_numpy(spec.x).cuda()
+        v = torch.from_numpy(spec.v).cuda()
+        C = torch.from_numpy(C0).cuda()
+        A.p2g_apic(x, v, C, spec.pmass, 0, 1)
+        A.grid_update(0, 1, spec.dt, spec.gravity, spec.bound)
+        st = {"src": A, "dst": B}
+
+        def step():
+            src, dst = st["src"], st["dst"]
+            dst.deactivate_all()
+            if form == "fused":
+                src.g2p2g(dst, x, v, spec.dt, 1, spec.pmass, 0, 1)
+            else:
+                src.g2p_apic(x, v, C, spec.dt, 1)
+                src.flush()
+                dst.p2g_apic(x, v, C, spec.pmass, 0, 1)
+            dst.grid_update(0, 1, spec.dt, spec.gravity, spec.bound)
+            dst.flush()
+            st["src"], st["dst"] = dst, src
+
+        launches = lambda: A.stats()["launches"] + B.stats()["launches"]
+        ms, nl = time_steps(torch, step, steps, warmup, flush_buf, stream, launches)
+        t = sum(ms) / 1e3
+        A.sync()
+        B.sync()
+        out[form] = {"value": spec.n * steps / t, "unit": "particle-steps/s", "ms_per_step": t * 1e3 / steps,
+                     "launches_per_step": nl / steps}
+        A.close()
+        B.close()
+    out["fused_over_separate"] = out["fused"]["value"] / out["separate"]["value"]
+    out["C_bytes_not_moved_per_step"] = spec.n * 72
+    out["l2"] = "flushed before every timed step (512 MB write)"
+    return out
+
+
 def bench_serving(torch, sg, rates=(50, 100, 200, 500, 1000, 2000), duration=2.0, cap_s=60.0):
     from paper_2012_08141_gb300.serve import Server
     out = []
@@ -415,6 +463,7 @@ def run_ours(args):
         for name, fn in (("band1024", lambda: bench_band1024(torch, sg, k, 3, flush_buf, stream)),
                          ("batched", lambda: bench_batched(torch, sg, k, 3, flush_buf, stream)),
                          ("particles", lambda: bench_particles(torch, sg, k, 3, flush_buf, stream)),
+                         ("mpm_apic", lambda: bench_mpm_apic(torch, sg, k, 3, flush_buf, stream)),
                          ("serving", lambda: bench_serving(torch, sg))):
             if args.only not in ("all", name):
                 continue
@@ -545,7 +594,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--variant", type=int, default=0, help="stencil kernel family (0 sweep, 1 smem)")
-    ap.add_argument("--only", choices=["all", "fused", "band1024", "batched", "particles", "serving"], default="all",
+    ap.add_argument("--only", choices=["all", "fused", "band1024", "batched", "particles", "mpm_apic", "serving"],
+                    default="all",
                     help="fused: only the fused headline step; a leg name: the headline step and that leg "
                          "(for profiling runs)")
     ap.add_argument("--skip-headline", action="store_true",

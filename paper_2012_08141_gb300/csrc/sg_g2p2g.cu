@@ -15,19 +15,20 @@
 // (a leaf o with the particles whose base node was in it when binned).
 //   1. stage src's velocities of nodes o-2 .. o+L+1 in shared memory;
 //   2. per particle: G2P from the staged block (or node by node from the grid
-//      when its base has left [o-2, o+L-1]), store x', v'; its new base lies
-//      in [o-3, o+L] when it moved less than a cell; count it in its new base
+//      when its base has left [o-2, o+L-1]), store x', v'; a particle of the
+//      bin that moved less than a cell has its new base in [o-1, o+L] (bases
+//      o-2 and o-1 of the low domain face excepted); count it in its new base
 //      cell and keep its P2G record (spline offsets, m, q = m v - m dx C fx
 //      and m dx C) in registers;
 //   3. counting sort by new base cell, records staged in shared memory;
 //   4. one warp per occupied cell: lane t < 27 sums its node's contributions
 //      (as in the binned P2G gather) into shared accumulators of the dst
-//      nodes o-3 .. o+L+2;
+//      nodes o-1 .. o+L+2;
 //   5. flush the touched nodes: the dst leaves they fall in are allocated
 //      in-kernel if null (see ensure_leaf), bits set, 4 FP32 atomics per node.
-// A particle whose new base is outside [o-3, o+L] (it moved a cell or more),
-// and every particle of the out-of-domain key, is scattered node by node
-// straight into dst with the same in-kernel allocation.
+// A particle whose new base is outside [o-1, o+L], and every particle of the
+// out-of-domain key, is scattered node by node straight into dst with the same
+// in-kernel allocation.
 #include "sg_particle.cuh"
 
 namespace sg {
@@ -207,14 +208,14 @@ template <int L>
 struct G2P2GSmem {
     static constexpr int BU = L + 4;          // staged src nodes per axis (o-2 .. o+L+1)
     static constexpr int NU = BU * BU * BU;
-    static constexpr int BD = L + 6;          // dst block nodes per axis (o-3 .. o+L+2)
+    static constexpr int BD = L + 4;          // dst block nodes per axis (o-1 .. o+L+2)
     static constexpr int ND = BD * BD * BD;
-    static constexpr int C1 = L + 4;          // new base cells per axis (o-3 .. o+L)
+    static constexpr int C1 = L + 2;          // new base cells per axis (o-1 .. o+L)
     static constexpr int NC = C1 * C1 * C1;
     static constexpr int CAP = 256;           // particles per chunk (one per thread)
     static constexpr size_t off_rec = 0;                                   // float4 [4][CAP]
-    static constexpr size_t off_u = off_rec + sizeof(float4) * 4 * CAP;    // float [3][NU]
-    static constexpr size_t off_acc = off_u + sizeof(float) * 3 * NU;      // float [4][ND]
+    static constexpr size_t off_u = off_rec + sizeof(float4) * 4 * CAP;    // float4 [NU]
+    static constexpr size_t off_acc = off_u + sizeof(float4) * NU;         // float [4][ND]
     static constexpr size_t off_cnt = off_acc + sizeof(float) * 4 * ND;    // int [NC + 1]
     static constexpr size_t off_start = off_cnt + sizeof(int) * (NC + 1);  // int [NC + 1]
     static constexpr size_t off_slot = off_start + sizeof(int) * (NC + 1); // int [27]
@@ -223,7 +224,7 @@ struct G2P2GSmem {
 };
 
 template <int L>
-__global__ void __launch_bounds__(256) k_g2p2g(DevGrid src, DevGrid dst, const int32_t *__restrict__ bin_list,
+__global__ void __launch_bounds__(256, L == 4 ? 3 : 2) k_g2p2g(DevGrid src, DevGrid dst, const int32_t *__restrict__ bin_list,
                                                const int32_t *__restrict__ bin_off, const int32_t *bin_end,
                                                int32_t *perm, const int32_t *bins_used, float *__restrict__ x,
                                                float *__restrict__ v, float dt, int f_vel0, float pmass, int f_mass,
@@ -233,7 +234,7 @@ __global__ void __launch_bounds__(256) k_g2p2g(DevGrid src, DevGrid dst, const i
     constexpr int LG2 = (L == 8) ? 3 : 2, BD = S::BD, C1 = S::C1, NC = S::NC, ND = S::ND;
     extern __shared__ __align__(16) unsigned char smem[];
     float4(*s_rec)[S::CAP] = reinterpret_cast<float4(*)[S::CAP]>(smem + S::off_rec);
-    float(*s_u)[S::NU] = reinterpret_cast<float(*)[S::NU]>(smem + S::off_u);
+    float4 *s_u = reinterpret_cast<float4 *>(smem + S::off_u);
     float(*s_acc)[ND] = reinterpret_cast<float(*)[ND]>(smem + S::off_acc);
     int *s_cnt = reinterpret_cast<int *>(smem + S::off_cnt);
     int *s_start = reinterpret_cast<int *>(smem + S::off_start);
@@ -298,7 +299,7 @@ __global__ void __launch_bounds__(256) k_g2p2g(DevGrid src, DevGrid dst, const i
                 store3_checked(dst, x, p, xn, pair);
                 const Spline nx = bspline(xn.x, N), ny = bspline(xn.y, N), nz = bspline(xn.z, N);
                 rec = make_rec(nx.fx, ny.fx, nz.fx, pmass, u, c, dx);
-                const int ci = nx.base - oi + 3, cj = ny.base - oj + 3, ck = nz.base - ok + 3;
+                const int ci = nx.base - oi + 1, cj = ny.base - oj + 1, ck = nz.base - ok + 1;
                 if (binned && (unsigned)ci < (unsigned)C1 && (unsigned)cj < (unsigned)C1 && (unsigned)ck < (unsigned)C1) {
                     rcell = (ci * C1 + cj) * C1 + ck;
                     rrank = atomicAdd(&s_cnt[rcell], 1);
@@ -353,7 +354,7 @@ __global__ void __launch_bounds__(256) k_g2p2g(DevGrid src, DevGrid dst, const i
                     m1 = fmaf(w, q1, m1);
                     m2 = fmaf(w, q2, m2);
                 }
-                if (lane < 27) {  // block node (ci + la, cj + lc, ck + ld) = grid node o - 3 + that
+                if (lane < 27) {  // block node (ci + la, cj + lc, ck + ld) = grid node o - 1 + that
                     const int nd = ((ci + la) * BD + (cj + lc)) * BD + (ck + ld);
                     atomicAdd(&s_acc[0][nd], m);
                     atomicAdd(&s_acc[1][nd], m0);
@@ -372,7 +373,7 @@ __global__ void __launch_bounds__(256) k_g2p2g(DevGrid src, DevGrid dst, const i
         const int li0 = (oi >> LG2) - 1, lj0 = (oj >> LG2) - 1, lk0 = (ok >> LG2) - 1;
         for (int nd = threadIdx.x; nd < ND; nd += blockDim.x) {
             if (!s_hit[nd]) continue;
-            const int i = oi - 3 + nd / (BD * BD), j = oj - 3 + (nd / BD) % BD, k = ok - 3 + nd % BD;
+            const int i = oi - 1 + nd / (BD * BD), j = oj - 1 + (nd / BD) % BD, k = ok - 1 + nd % BD;
             if ((unsigned)i >= (unsigned)N || (unsigned)j >= (unsigned)N || (unsigned)k >= (unsigned)N) continue;
             s_slot[((i >> LG2) - li0) * 9 + ((j >> LG2) - lj0) * 3 + ((k >> LG2) - lk0)] = 1;
         }
@@ -391,7 +392,7 @@ __global__ void __launch_bounds__(256) k_g2p2g(DevGrid src, DevGrid dst, const i
         __syncthreads();
         for (int nd = threadIdx.x; nd < ND; nd += blockDim.x) {
             if (!s_hit[nd]) continue;
-            const int i = oi - 3 + nd / (BD * BD), j = oj - 3 + (nd / BD) % BD, k = ok - 3 + nd % BD;
+            const int i = oi - 1 + nd / (BD * BD), j = oj - 1 + (nd / BD) % BD, k = ok - 1 + nd % BD;
             if ((unsigned)i >= (unsigned)N || (unsigned)j >= (unsigned)N || (unsigned)k >= (unsigned)N) continue;
             const int slot = s_slot[((i >> LG2) - li0) * 9 + ((j >> LG2) - lj0) * 3 + ((k >> LG2) - lk0)];
             if (slot < 0) continue;  // pool exhausted; the error is latched

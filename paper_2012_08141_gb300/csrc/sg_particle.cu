@@ -74,11 +74,11 @@ __global__ void __launch_bounds__(256) k_g2p(DevGrid g, float *__restrict__ x, f
 // that range (its position changed since the binning) reads the grid node by
 // node, as do the particles whose stencil misses the domain (the last key).
 template <int L, bool APIC>
-__global__ void __launch_bounds__(256, APIC ? 4 : 6) k_g2p_binned(DevGrid g, float *__restrict__ x, float *__restrict__ v,
+__global__ void __launch_bounds__(256, 4) k_g2p_binned(DevGrid g, float *__restrict__ x, float *__restrict__ v,
                                                        float *__restrict__ C, float dt, int f_mom0, bool pair)
 {
     constexpr int B = L + 4, NB = B * B * B;
-    __shared__ float s_u[3][NB];
+    __shared__ float4 s_u[NB];
     const int N = g.N, R = g.R;
     const float *f0 = g.field[f_mom0], *f1 = g.field[f_mom0 + 1], *f2 = g.field[f_mom0 + 2];
     const int used = g.ctrl->bins_used;

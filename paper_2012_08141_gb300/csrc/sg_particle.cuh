@@ -131,38 +131,37 @@ __device__ __forceinline__ void g2p_store(float *__restrict__ x, float *__restri
     }
 }
 
+// Stage the velocities of the (L+4)^3 nodes from o - 2 to o + L + 1 of a
+// leaf with origin o as one float4 (u0, u1, u2, 0) per node: 0 outside the
+// domain or the allocated leaves.
 template <int L>
 __device__ __forceinline__ void stage_velocities(const DevGrid &g, const float *__restrict__ f0,
                                                  const float *__restrict__ f1, const float *__restrict__ f2, int oi,
-                                                 int oj, int ok, float (*s_u)[(L + 4) * (L + 4) * (L + 4)])
+                                                 int oj, int ok, float4 *s_u)
 {
     constexpr int LG2 = (L == 8) ? 3 : 2, B = L + 4, NB = B * B * B;
     const int N = g.N, R = g.R;
     for (int nd = threadIdx.x; nd < NB; nd += blockDim.x) {
         const int i = oi - 2 + nd / (B * B), j = oj - 2 + (nd / B) % B, k = ok - 2 + nd % B;
-        float u0 = 0.f, u1 = 0.f, u2 = 0.f;
+        float4 u = make_float4(0.f, 0.f, 0.f, 0.f);
         if ((unsigned)i < (unsigned)N && (unsigned)j < (unsigned)N && (unsigned)k < (unsigned)N) {
             const int slot = __ldg(g.root + ((long long)(i >> LG2) * R + (j >> LG2)) * R + (k >> LG2));
             if (slot >= 0) {
                 const long long idx =
                     ((long long)slot << (3 * LG2)) + (((i & (L - 1)) << LG2) + (j & (L - 1))) * L + (k & (L - 1));
-                u0 = __ldg(f0 + idx);
-                u1 = __ldg(f1 + idx);
-                u2 = __ldg(f2 + idx);
+                u = make_float4(__ldg(f0 + idx), __ldg(f1 + idx), __ldg(f2 + idx), 0.f);
             }
         }
-        s_u[0][nd] = u0;
-        s_u[1][nd] = u1;
-        s_u[2][nd] = u2;
+        s_u[nd] = u;
     }
 }
 
-// G2P of one particle from a staged block (ri, rj, rk: its base relative to
-// the block's first node).  APIC as in g2p_from_grid.
+// G2P of one particle from a staged block of B^3 float4 node velocities (ri,
+// rj, rk: its base relative to the block's first node).  APIC as in
+// g2p_from_grid.
 template <int B, bool APIC>
-__device__ __forceinline__ void g2p_from_block(const float (*s_u)[B * B * B], int ri, int rj, int rk, int N,
-                                               const Spline &sx, const Spline &sy, const Spline &sz, float3 &u,
-                                               float (&c)[9])
+__device__ __forceinline__ void g2p_from_block(const float4 *s_u, int ri, int rj, int rk, int N, const Spline &sx,
+                                               const Spline &sy, const Spline &sz, float3 &u, float (&c)[9])
 {
     float ux = 0.f, uy = 0.f, uz = 0.f;
     float S[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
@@ -173,9 +172,9 @@ __device__ __forceinline__ void g2p_from_block(const float (*s_u)[B * B * B], in
             const float wxy = sx.w[a] * sy.w[b];
 #pragma unroll
             for (int cc = 0; cc < 3; ++cc) {
-                const int nd = ((ri + a) * B + (rj + b)) * B + (rk + cc);
+                const float4 n = s_u[((ri + a) * B + (rj + b)) * B + (rk + cc)];
                 const float w = wxy * sz.w[cc];
-                const float wv[3] = {w * s_u[0][nd], w * s_u[1][nd], w * s_u[2][nd]};
+                const float wv[3] = {w * n.x, w * n.y, w * n.z};
                 ux += wv[0];
                 uy += wv[1];
                 uz += wv[2];
