@@ -67,6 +67,8 @@ def _load():
         "og_grid_update": (None, [P, I32, I32, D, D, I32]),
         "og_g2p": (None, [P, P, P, I64, D, I32]),
         "og_p2g_apic": (None, [P, P, P, P, I64, D, I32, I32]),
+        "og_restrict": (None, [P, P, I32, I32, D]),
+        "og_prolong": (None, [P, P, I32, I32, D]),
         "og_g2p_apic": (None, [P, P, P, P, I64, D, I32]),
         "og_get_voxel": (D, [P, I32, I64, I64, I64]),
         "og_voxel_active": (I32, [P, I64, I64, I64]),
@@ -194,6 +196,17 @@ class Grid:
         assert x.dtype == np.float32 and v.dtype == np.float32
         assert x.flags.c_contiguous and v.flags.c_contiguous
         self.lib.og_g2p(self.h, _ptr(x), _ptr(v), x.size // 3, float(dt), int(f_mom0))
+
+    def restrict_to(self, coarse: "Grid", f_src: int, f_dst: int, w: float):
+        """coarse[f_dst][i // 2] += w * self[f_src][i] over the active voxels i,
+        activating i // 2 on the coarse grid (its edge is half of this one's)."""
+        assert coarse.N * 2 == self.N
+        self.lib.og_restrict(self.h, coarse.h, int(f_src), int(f_dst), float(w))
+
+    def prolong_from(self, coarse: "Grid", f_src: int, f_dst: int, w: float):
+        """self[f_dst][i] += w * coarse[f_src][i // 2] over the active voxels i."""
+        assert coarse.N * 2 == self.N
+        self.lib.og_prolong(coarse.h, self.h, int(f_src), int(f_dst), float(w))
 
     def p2g_apic(self, x, v, C, pmass: float, f_mass: int, f_mom0: int):
         """APIC P2G: C is (n, 9) FP32, row-major 3x3 per particle."""

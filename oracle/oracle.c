@@ -506,6 +506,45 @@ void og_g2p_apic(og_grid *g, float *x, float *vel, float *C, int64_t n, double d
     }
 }
 
+/* ---------------------------------------------------------------------------
+ * Grid transfers between a fine grid and a coarse grid of half its edge, the
+ * restriction / prolongation pattern of multigrid solvers that Sec. 6.3 uses
+ * to motivate activation demotion (Fig. 13, the loop y[i // 2] += x[i] * w).
+ * ------------------------------------------------------------------------- */
+
+/* Restriction with activation on write: for every active fine voxel i,
+ * activate coarse voxel i // 2 (componentwise floor division) and add
+ * w * x_i to coarse field f_dst there.  coarse->N == fine->N / 2.  Serial, in
+ * list order. */
+void og_restrict(const og_grid *fine, og_grid *coarse, int32_t f_src, int32_t f_dst, double w)
+{
+    int64_t v = cube(fine->L), vc = cube(coarse->L);
+    for (int64_t q = 0; q < fine->n * v; q++) {
+        if (!fine->act[q]) continue;
+        int64_t i, j, k;
+        coords_of(fine, q / v, q % v, &i, &j, &k);
+        og_activate_voxel(coarse, i / 2, j / 2, k / 2);
+        int64_t idx = (int64_t)coarse->root[root_of(coarse, i / 2, j / 2, k / 2)] * vc
+                    + local_of(coarse, i / 2, j / 2, k / 2);
+        coarse->val[f_dst][idx] += w * fine->val[f_src][q];
+    }
+}
+
+/* Prolongation: for every active fine voxel i, x_i += w * y_{i // 2}, with y
+ * (coarse field f_src) read through the coarse mask (an inactive or absent
+ * coarse voxel reads 0).  No activation. */
+void og_prolong(const og_grid *coarse, og_grid *fine, int32_t f_src, int32_t f_dst, double w)
+{
+    int64_t v = cube(fine->L);
+#pragma omp parallel for schedule(static)
+    for (int64_t q = 0; q < fine->n * v; q++) {
+        if (!fine->act[q]) continue;
+        int64_t i, j, k;
+        coords_of(fine, q / v, q % v, &i, &j, &k);
+        fine->val[f_dst][q] += w * og_get(coarse, f_src, i / 2, j / 2, k / 2);
+    }
+}
+
 /* Value of one voxel of a field read through the mask (for sampled checks). */
 double og_get_voxel(const og_grid *g, int32_t f, int64_t i, int64_t j, int64_t k)
 {

@@ -103,3 +103,14 @@ def p2g(x: np.ndarray, v: np.ndarray, N: int, pmass: float):
                 for d in range(3):
                     np.add.at(mom[d], idx, wt * v[ok, d].astype(np.float64))
     return active, mass, mom
+
+
+def restrict(x: np.ndarray, active: np.ndarray, w: float):
+    """Dense restriction onto the half-edge grid: coarse activity = any active
+    child (the 2x2x2 block), coarse value = w * sum of the active children
+    (block sums by reshape)."""
+    N = x.shape[0]
+    n = N // 2
+    xa = np.where(active, x, 0.0).reshape(n, 2, n, 2, n, 2)
+    act = active.reshape(n, 2, n, 2, n, 2).any(axis=(1, 3, 5))
+    return w * xa.sum(axis=(1, 3, 5)), act

@@ -12,6 +12,7 @@ import numpy as np
 import pytest
 
 import dense_twin as dt
+from sgtest import mask_bits
 import oracle
 from workload import band_bounds, band512, leaf_values, spheres_particles, tiny_shell
 
@@ -432,6 +433,77 @@ def test_p2g_apic_momentum_and_angular_momentum():
     want = pm * (np.cross(xp, v64).sum(axis=0) + (1.0 / N) ** 2 / 4.0 * spin.sum(axis=0))
     scale = pm * (np.abs(np.cross(xp, v64)).sum() + np.abs(spin).sum() / (4.0 * N * N))
     assert np.max(np.abs(got - want)) <= 1e-11 * scale
+
+
+# ---------------------------------------------------------------------------
+# Restriction / prolongation between a grid and its half-edge coarse grid
+# ---------------------------------------------------------------------------
+
+def _fine_grid(N, L, seed, frac=0.05):
+    rng = np.random.default_rng(seed)
+    pts = rng.integers(0, N, size=(int(frac * N ** 3), 3)).astype(np.int32)
+    g = oracle.Grid(N, L, 2)
+    g.activate_coords(pts)
+    b, _ = g.structure()
+    g.write_field64(0, rng.uniform(-1.0, 1.0, size=(len(b), L ** 3)))
+    return g
+
+
+@pytest.mark.parametrize("N,L", [(32, 8), (32, 4), (16, 2)])
+def test_restrict_matches_dense_block_sums(N, L):
+    """Coarse structure = the set of i // 2 over active fine voxels (bit-exact)
+    and coarse values = w * the sum of the active children, against a dense
+    block-sum twin."""
+    f = _fine_grid(N, L, seed=N + L)
+    c = oracle.Grid(N // 2, L, 2)
+    f.restrict_to(c, 0, 1, 0.125)
+    fb, fm = f.structure()
+    x = dt.from_leaves(f.read_field(0), fb, N, L)
+    act = dt.from_leaves(mask_bits(fm, L ** 3).astype(float), fb, N, L) > 0
+    want, want_act = dt.restrict(x, act, 0.125)
+    cb, cm = c.structure()
+    b2, m2 = dt.structure(want_act, L)
+    np.testing.assert_array_equal(cb, b2)
+    np.testing.assert_array_equal(cm, m2)
+    np.testing.assert_allclose(c.read_field(1), dt.to_leaves(want, cb, L), rtol=0, atol=1e-13)
+
+
+def test_restrict_conservation_and_accumulation():
+    """sum(coarse) = w * sum(fine); a second restriction adds the same amount
+    again and activates nothing new."""
+    f = _fine_grid(32, 8, seed=3, frac=0.2)
+    c = oracle.Grid(16, 8, 2)
+    f.restrict_to(c, 0, 1, 0.25)
+    b1, m1 = c.structure()
+    s1 = c.sum(1)
+    assert s1 == pytest.approx(0.25 * f.sum(0), rel=1e-12, abs=1e-12)
+    f.restrict_to(c, 0, 1, 0.25)
+    b2, m2 = c.structure()
+    np.testing.assert_array_equal(b1, b2)
+    np.testing.assert_array_equal(m1, m2)
+    assert c.sum(1) == pytest.approx(2 * s1, rel=1e-12, abs=1e-12)
+
+
+def test_prolong_then_restrict_closed_form():
+    """With every fine voxel of a box active, restricting the prolongation of
+    y gives 8 * w_r * w_p * y on every coarse voxel of the box's image."""
+    N, L = 16, 4
+    f = oracle.Grid(N, L, 2)
+    box = np.stack(np.meshgrid(*[np.arange(4, 12)] * 3, indexing="ij"), -1).reshape(-1, 3)
+    f.activate_coords(box)
+    c = oracle.Grid(N // 2, L, 2)
+    c.activate_coords(box // 2)
+    cb, _ = c.structure()
+    rng = np.random.default_rng(9)
+    y = rng.uniform(-2.0, 2.0, size=(len(cb), L ** 3))
+    c.write_field64(0, y)
+    f.prolong_from(c, 0, 0, 0.5)
+    f.restrict_to(c, 0, 1, 0.125)
+    cc = oracle.leaf_coords(cb, N // 2, L)
+    inside = np.all((cc >= 2) & (cc < 6), axis=2)
+    got, y0 = c.read_field(1), c.read_field(0)
+    np.testing.assert_allclose(got[inside], 8 * 0.125 * 0.5 * y0[inside], rtol=1e-14, atol=1e-15)
+    assert np.all(got[~inside] == 0.0)
 
 
 def test_grid_update_hand_case():
