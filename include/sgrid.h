@@ -209,6 +209,26 @@ int sg_g2p_apic(sg_grid *g, float *dev_x, float *dev_v, float *dev_C, int64_t n,
 int sg_g2p2g(sg_grid *src, sg_grid *dst, float *dev_x, float *dev_v, int64_t n, float dt, int32_t f_vel0,
              float pmass, int32_t f_mass, int32_t f_mom0);
 
+/* Restriction onto a grid of half the edge (the multigrid pattern of Sec. 6.3,
+ * Fig. 13): for every active voxel i of `fine`, activate voxel i // 2
+ * (componentwise) of `coarse` and add w * fine[f_src][i] to coarse[f_dst]
+ * there.  fine and coarse are distinct grids with fine res = 2 * coarse res,
+ * the same leaf size, created on the same stream.  Both grids' queued work is
+ * flushed first (a scratch field's contents are undefined after a flush), the
+ * fine list is made current, and the restriction is launched at once on the
+ * stream.  With SG_OPT_AD on `coarse`, a restriction from the same fine grid
+ * whose mask has not changed since one already applied (and no deactivation
+ * of coarse since) is demoted: it adds values without activating, and
+ * coarse's structure stays unchanged, so its list generation can be removed
+ * (Sec. 6.3).  Errors: SG_ERR_INVALID; pool exhaustion latched on coarse. */
+int sg_restrict(sg_grid *fine, sg_grid *coarse, int32_t f_src, int32_t f_dst, float w);
+
+/* Prolongation: for every active voxel i of `fine`, fine[f_dst][i] +=
+ * w * coarse[f_src][i // 2], reading coarse through its mask (an inactive or
+ * absent coarse voxel reads 0).  No activation.  Same grid requirements and
+ * flushing as sg_restrict; launched at once on the stream. */
+int sg_prolong(sg_grid *coarse, sg_grid *fine, int32_t f_src, int32_t f_dst, float w);
+
 /* Exchange the storage behind field indices a and b (no device work). */
 int sg_swap(sg_grid *g, int32_t a, int32_t b);
 

@@ -88,6 +88,8 @@ def load_library(build: bool = True) -> ctypes.CDLL:
         "sg_p2g_apic": [P, P, P, P, I64, F, I32, I32],
         "sg_g2p_apic": [P, P, P, P, I64, F, I32],
         "sg_g2p2g": [P, P, P, P, I64, F, I32, F, I32, I32],
+        "sg_restrict": [P, P, I32, I32, F],
+        "sg_prolong": [P, P, I32, I32, F],
         "sg_swap": [P, I32, I32],
         "sg_flush": [P],
         "sg_sync": [P],
@@ -261,6 +263,15 @@ class Grid:
         dst._borrowed += [x, v]
         self._c(self.lib.sg_g2p2g(self.h, dst.h, _ptr(x), _ptr(v), x.numel() // 3, float(dt), int(f_vel0),
                                   float(pmass), int(f_mass), int(f_mom0)))
+
+    def restrict_to(self, coarse: "Grid", f_src: int, f_dst: int, w: float):
+        """coarse[f_dst][i // 2] += w * self[f_src][i] over this grid's active
+        voxels, activating i // 2 on coarse (res half of this grid's)."""
+        self._c(self.lib.sg_restrict(self.h, coarse.h, int(f_src), int(f_dst), float(w)))
+
+    def prolong_from(self, coarse: "Grid", f_src: int, f_dst: int, w: float):
+        """self[f_dst][i] += w * coarse[f_src][i // 2] over this grid's active voxels."""
+        self._c(self.lib.sg_prolong(coarse.h, self.h, int(f_src), int(f_dst), float(w)))
 
     def g2p(self, x, v, dt: float, f_mom0: int):
         for t in (x, v):

@@ -87,6 +87,8 @@ struct sg_grid {
     // host-side state versions (Sec. 4): mask and list of the grid's structure
     unsigned long long mask_ver = 1, list_ver = 0;
     std::set<std::tuple<long long, long long, int>> applied_shells;
+    // restrictions applied since the last deactivation: (fine grid, its mask version)
+    std::set<std::pair<const sg_grid *, unsigned long long>> applied_restrict;
     unsigned long long lg_calls = 0;
     unsigned long long rmask_ver = 0;  // list version the region masks were built from (0 = never)
     long long known_leaves = 0;
@@ -338,6 +340,7 @@ int do_flush(sg_grid *g)
                 if (!g->dry) launch_deactivate_all(g->dev, g->stream);
                 g->mask_ver++;
                 g->applied_shells.clear();
+                g->applied_restrict.clear();
                 rc = after_launch(g, "deactivate");
                 ++i;
                 break;
@@ -749,6 +752,54 @@ int sg_g2p2g(sg_grid *src, sg_grid *dst, float *dev_x, float *dev_v, int64_t n, 
     o.bins = bins;
     if ((rc = push(dst, o))) return rc;
     return do_flush(dst);  // launched now: later src ops cannot run before it
+}
+
+// Both grids: distinct, same leaf size and stream, fine edge twice the coarse.
+static int check_pair(const sg_grid *fine, const sg_grid *coarse, const char *what)
+{
+    if (!fine || !coarse || fine == coarse) return fail(SG_ERR_INVALID, "%s: two distinct grids are needed", what);
+    if (fine->dev.N != 2 * coarse->dev.N || fine->dev.L != coarse->dev.L || fine->stream != coarse->stream ||
+        fine->dry != coarse->dry)
+        return fail(SG_ERR_INVALID, "%s: the fine grid's res must be twice the coarse one's, same leaf size and stream",
+                    what);
+    return SG_OK;
+}
+
+int sg_restrict(sg_grid *fine, sg_grid *coarse, int32_t f_src, int32_t f_dst, float w)
+{
+    int rc = check_pair(fine, coarse, "restrict");
+    if (rc) return rc;
+    if (!valid_field(fine, f_src) || !valid_field(coarse, f_dst)) return fail(SG_ERR_INVALID, "bad restrict fields");
+    // queued work of both grids runs first; the loop runs over the fine list
+    if ((rc = do_flush(fine)) || (rc = do_flush(coarse)) || (rc = ensure_list(fine))) return rc;
+    const auto key = std::make_pair((const sg_grid *)fine, fine->mask_ver);
+    const bool demote = (coarse->opts & SG_OPT_AD) && coarse->applied_restrict.count(key);
+    if (demote) {
+        coarse->stats.act_demoted++;
+    } else {
+        if (!coarse->dry) launch_restrict_mark(fine->dev, coarse->dev, coarse->stream, coarse->lc);
+        if ((rc = after_launch(coarse, "restrict: mark"))) return rc;
+        if (!coarse->dry) launch_alloc_needed(coarse->dev, coarse->stream);
+        if ((rc = after_launch(coarse, "restrict: allocate"))) return rc;
+        coarse->applied_restrict.insert(key);
+        coarse->mask_ver++;
+        coarse->stats.act_launched++;
+    }
+    if (!coarse->dry)
+        launch_restrict(fine->dev, coarse->dev, coarse->stream, fine->phys[f_src], coarse->phys[f_dst], w, !demote,
+                        coarse->lc);
+    return after_launch(coarse, "restrict");
+}
+
+int sg_prolong(sg_grid *coarse, sg_grid *fine, int32_t f_src, int32_t f_dst, float w)
+{
+    int rc = check_pair(fine, coarse, "prolong");
+    if (rc) return rc;
+    if (!valid_field(coarse, f_src) || !valid_field(fine, f_dst)) return fail(SG_ERR_INVALID, "bad prolong fields");
+    if ((rc = do_flush(coarse)) || (rc = do_flush(fine)) || (rc = ensure_list(fine))) return rc;
+    if (!fine->dry)
+        launch_prolong(coarse->dev, fine->dev, fine->stream, coarse->phys[f_src], fine->phys[f_dst], w, fine->lc);
+    return after_launch(fine, "prolong");
 }
 
 int sg_swap(sg_grid *g, int32_t a, int32_t b)

@@ -179,6 +179,15 @@ void launch_grid_update(const DevGrid &g, cudaStream_t s, int f_mass, int f_mom0
 void launch_g2p(const DevGrid &g, cudaStream_t s, float *x, float *v, float *C, long long n, float dt, int f_mom0,
                 int binned, const LaunchCfg &lc);
 
+// ---- restriction / prolongation to a half-edge grid (sg_multigrid.cu) ----
+void launch_restrict_mark(const DevGrid &fine, const DevGrid &coarse, cudaStream_t s, const LaunchCfg &lc);
+// activate: set the coarse bits (the coarse leaves are allocated); else the
+// activation is demoted (bits known to be set).
+void launch_restrict(const DevGrid &fine, const DevGrid &coarse, cudaStream_t s, int f_src, int f_dst, float w,
+                     bool activate, const LaunchCfg &lc);
+void launch_prolong(const DevGrid &coarse, const DevGrid &fine, cudaStream_t s, int f_src, int f_dst, float w,
+                    const LaunchCfg &lc);
+
 // ---- fused G2P2G (sg_g2p2g.cu) ----
 // APIC G2P from src (velocities f_vel0..+2) then APIC P2G with activation
 // into dst (f_mass, f_mom0..+2), C kept on chip; the particles visited in the

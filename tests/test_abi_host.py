@@ -249,3 +249,57 @@ def test_g2p2g_argument_checks_and_launches():
     assert lib.sg_p2g_apic(c.h, ctypes.c_void_p(x), ctypes.c_void_p(v), ctypes.c_void_p(0x30000), n, 1.0, 0, 1) == 0
     assert lib.sg_g2p2g(c.h, a.h, *args) == 0                           # src's queued P2G counts
     assert lib.sg_g2p2g(b.h, a.h, *args) == 0                           # bins held by dst (a) also work
+
+
+def test_restriction_activation_demotion():
+    """sg_restrict activates on the coarse grid the first time (mark, allocate,
+    restrict); with SG_OPT_AD a repeat from an unchanged fine grid is demoted
+    to one launch and leaves the coarse structure, so the coarse list is not
+    generated again (Sec. 6.3).  Without AD every restriction activates."""
+    fine, coarse = dry(64, 3, 2), dry(32, 3, 2)
+    fine.activate_shell(100, 400, False)
+    fine.list_gen()
+    coarse.list_gen()
+    fine.flush()
+    coarse.flush()
+    base = coarse.stats()
+    fine.restrict_to(coarse, 0, 1, 0.125)
+    s1 = coarse.stats()
+    assert s1["launches"] - base["launches"] == 3 and s1["act_launched"] == base["act_launched"] + 1
+    coarse.list_gen()
+    coarse.flush()
+    s2 = coarse.stats()
+    assert s2["listgen_run"] == s1["listgen_run"] + 1          # structure changed: list made again
+    fine.restrict_to(coarse, 0, 1, 0.125)
+    coarse.list_gen()
+    coarse.flush()
+    s3 = coarse.stats()
+    assert s3["launches"] - s2["launches"] == 1                # demoted: the restriction alone
+    assert s3["act_demoted"] == s2["act_demoted"] + 1
+    assert s3["listgen_run"] == s2["listgen_run"]              # list generation removed
+    fine.activate_shell(500, 900, False)                       # the fine structure changes
+    fine.restrict_to(coarse, 0, 1, 0.125)
+    assert coarse.stats()["act_launched"] == s3["act_launched"] + 1
+    coarse.deactivate_all()
+    coarse.flush()
+    fine.restrict_to(coarse, 0, 1, 0.125)                      # deactivation forgets the restriction
+    assert coarse.stats()["act_launched"] == s3["act_launched"] + 2
+    # activation demotion off: every restriction activates
+    f2, c2 = dry(64, 3, 2), dry(32, 3, 2)
+    c2.set_opts(sg.SG_OPT_ALL & ~sg.SG_OPT_AD)
+    f2.activate_shell(100, 400, False)
+    for _ in range(3):
+        f2.restrict_to(c2, 0, 1, 0.125)
+    st = c2.stats()
+    assert st["act_launched"] == 3 and st["act_demoted"] == 0
+
+
+def test_restriction_argument_checks():
+    lib = sg.load_library()
+    a, b = dry(64, 3, 2), dry(32, 3, 2)
+    assert lib.sg_restrict(a.h, a.h, 0, 1, 1.0) == sg.SG_ERR_INVALID       # same grid
+    assert lib.sg_restrict(b.h, a.h, 0, 1, 1.0) == sg.SG_ERR_INVALID       # coarse is not half of fine
+    assert lib.sg_restrict(a.h, dry(32, 2, 2).h, 0, 1, 1.0) == sg.SG_ERR_INVALID   # leaf sizes differ
+    assert lib.sg_restrict(a.h, b.h, 0, 5, 1.0) == sg.SG_ERR_INVALID       # field out of range
+    assert lib.sg_prolong(b.h, a.h, 0, 1, 1.0) == 0
+    assert lib.sg_prolong(a.h, b.h, 0, 1, 1.0) == sg.SG_ERR_INVALID        # arguments swapped
