@@ -14,6 +14,8 @@ it.  Further legs (skipped with --only fused or on more than one rank):
             P2G with activation, grid update, G2P per step;
   mpm_apic  the same particles with APIC transfers on two grids in turn:
             separate G2P (C stored) + P2G against the fused G2P2G (C on chip);
+  multigrid a 4-level V-cycle (restrict, smooth, prolong) from the 512^3 band,
+            with and without activation demotion, and eager;
   serving   Poisson arrivals of band jobs (1e4..1e7 voxels, 10..200 steps)
             into the continuous-batching server: p50/p99 job latency;
   band1024  the 1024^3 band |dist - 400| < 8, far larger than L2.
@@ -338,6 +340,53 @@ def bench_mpm_apic(torch, sg, steps, warmup, flush_buf, stream):
     return out
 
 
+def bench_multigrid(torch, sg, steps, warmup, flush_buf, stream):
+    """V-cycle pattern over four levels (the 512^3 band, then 256^3, 128^3,
+    64^3, 8^3 leaves): down, clear b on the coarse level, restrict, smooth;
+    up, prolong and smooth.  The coarse levels' structure comes only from the
+    restrictions, so with activation demotion (Sec. 6.3) the repeated
+    restrictions leave it unchanged and their list generations are removed.
+    Timed with all passes, without activation demotion, and eager."""
+    spec = band512()
+    out = {"workload": "4-level V-cycle: 512^3 band |dist-200|<8 and its 256^3, 128^3, 64^3 restrictions, 8^3 leaves",
+           "l2": "flushed before every timed step (512 MB write)"}
+    for name, opts in (("all_passes", sg.SG_OPT_ALL), ("no_demotion", sg.SG_OPT_ALL & ~sg.SG_OPT_AD),
+                       ("eager", sg.SG_OPT_EAGER)):
+        G = [sg.Grid(512 >> l, 3, 3, max_leaves=32768, max_sums=1) for l in range(4)]
+        for g in G:
+            g.set_opts(opts)
+        G[0].activate_shell(spec.lo2, spec.hi2, spec.lo_strict)
+        G[0].fill_hash(0, 3)
+
+        def cycle():
+            for l in range(3):
+                G[l + 1].clear(1)
+                G[l].restrict_to(G[l + 1], 0, 1, 0.125)
+                G[l + 1].diffuse7(1, 0, 0.1)
+            for l in (2, 1, 0):
+                G[l].prolong_from(G[l + 1], 0, 0, 0.5)
+                G[l].diffuse7(0, 2, 0.1)
+                G[l].swap(0, 2)
+            for g in G:
+                g.flush()
+
+        stat = lambda key: sum(g.stats()[key] for g in G)
+        cycle()                                    # the first cycle activates the coarse levels
+        for g in G:
+            g.sync()
+        l0, g0 = stat("launches"), stat("listgen_run")
+        ms, _ = time_steps(torch, cycle, steps, warmup, flush_buf, stream)
+        l1, g1 = stat("launches"), stat("listgen_run")
+        n = steps + warmup
+        out[name] = {"ms_per_cycle": sum(ms) / len(ms), "launches_per_cycle": (l1 - l0) / n,
+                     "listgen_per_cycle": (g1 - g0) / n, "leaves": [g.num_leaves() for g in G]}
+        for g in G:
+            g.close()
+    out["no_demotion_over_all_passes"] = out["no_demotion"]["ms_per_cycle"] / out["all_passes"]["ms_per_cycle"]
+    out["eager_over_all_passes"] = out["eager"]["ms_per_cycle"] / out["all_passes"]["ms_per_cycle"]
+    return out
+
+
 def bench_serving(torch, sg, rates=(50, 100, 200, 500, 1000, 2000), duration=2.0, cap_s=60.0):
     from paper_2012_08141_gb300.serve import Server
     out = []
@@ -464,6 +513,7 @@ def run_ours(args):
                          ("batched", lambda: bench_batched(torch, sg, k, 3, flush_buf, stream)),
                          ("particles", lambda: bench_particles(torch, sg, k, 3, flush_buf, stream)),
                          ("mpm_apic", lambda: bench_mpm_apic(torch, sg, k, 3, flush_buf, stream)),
+                         ("multigrid", lambda: bench_multigrid(torch, sg, k, 3, flush_buf, stream)),
                          ("serving", lambda: bench_serving(torch, sg))):
             if args.only not in ("all", name):
                 continue
@@ -594,7 +644,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--variant", type=int, default=0, help="stencil kernel family (0 sweep, 1 smem)")
-    ap.add_argument("--only", choices=["all", "fused", "band1024", "batched", "particles", "mpm_apic", "serving"],
+    ap.add_argument("--only", choices=["all", "fused", "band1024", "batched", "particles", "mpm_apic", "multigrid",
+                                       "serving"],
                     default="all",
                     help="fused: only the fused headline step; a leg name: the headline step and that leg "
                          "(for profiling runs)")
