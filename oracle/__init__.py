@@ -68,6 +68,7 @@ def _load():
         "og_g2p": (None, [P, P, P, I64, D, I32]),
         "og_p2g_apic": (None, [P, P, P, P, I64, D, I32, I32]),
         "og_restrict": (None, [P, P, I32, I32, D]),
+        "og_ew": (None, [P, I32, I32, I32, D, D, D, D]),
         "og_prolong": (None, [P, P, I32, I32, D]),
         "og_g2p_apic": (None, [P, P, P, P, I64, D, I32]),
         "og_get_voxel": (D, [P, I32, I64, I64, I64]),
@@ -196,6 +197,11 @@ class Grid:
         assert x.dtype == np.float32 and v.dtype == np.float32
         assert x.flags.c_contiguous and v.flags.c_contiguous
         self.lib.og_g2p(self.h, _ptr(x), _ptr(v), x.size // 3, float(dt), int(f_mom0))
+
+    def ew(self, dst: int, a: int = -1, b: int = -1, alpha: float = 0.0, beta: float = 0.0, gamma: float = 0.0,
+           delta: float = 0.0):
+        """dst = alpha a + beta b + gamma a b + delta on the active voxels (-1: absent field)."""
+        self.lib.og_ew(self.h, int(dst), int(a), int(b), float(alpha), float(beta), float(gamma), float(delta))
 
     def restrict_to(self, coarse: "Grid", f_src: int, f_dst: int, w: float):
         """coarse[f_dst][i // 2] += w * self[f_src][i] over the active voxels i,

@@ -545,6 +545,23 @@ void og_prolong(const og_grid *coarse, og_grid *fine, int32_t f_src, int32_t f_d
     }
 }
 
+/* Element-wise struct-for (the general kernels of the paper's
+ * microbenchmarks, Supp. Sec. 1: chain_copy, increments, fill_array,
+ * sparse_saxpy, autodiff): on every active voxel
+ *   dst = alpha * a + beta * b + gamma * a * b + delta,
+ * with a, b read at the same voxel (field index -1: absent, reads 0); dst
+ * stays 0 at inactive voxels.  dst may equal a or b. */
+void og_ew(og_grid *g, int32_t dst, int32_t a, int32_t b, double alpha, double beta, double gamma, double delta)
+{
+    int64_t total = g->n * cube(g->L);
+#pragma omp parallel for schedule(static)
+    for (int64_t q = 0; q < total; q++) {
+        if (!g->act[q]) { g->val[dst][q] = 0.0; continue; }
+        double va = a >= 0 ? g->val[a][q] : 0.0, vb = b >= 0 ? g->val[b][q] : 0.0;
+        g->val[dst][q] = alpha * va + beta * vb + gamma * va * vb + delta;
+    }
+}
+
 /* Value of one voxel of a field read through the mask (for sampled checks). */
 double og_get_voxel(const og_grid *g, int32_t f, int64_t i, int64_t j, int64_t k)
 {

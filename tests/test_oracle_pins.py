@@ -506,6 +506,51 @@ def test_prolong_then_restrict_closed_form():
     assert np.all(got[~inside] == 0.0)
 
 
+# ---------------------------------------------------------------------------
+# Element-wise struct-fors (the microbenchmark kernels)
+# ---------------------------------------------------------------------------
+
+def _shell_grid(F=4, seed=1):
+    spec = tiny_shell(seed)
+    g = oracle.Grid(spec.N, spec.L, F)
+    g.activate_shell(spec.lo2, spec.hi2, spec.lo_strict)
+    b, m = g.structure()
+    g.write_field(0, leaf_values(seed, spec.N, spec.L, b))
+    return g, b, m
+
+
+def test_ew_algebra_identities():
+    """2a - a = a exactly; a * a - a^2 via gamma = 0; fill gives delta on the
+    active voxels and 0 elsewhere; ten increments add 10."""
+    g, b, m = _shell_grid()
+    x = g.read_field(0)
+    act = mask_bits(m, 512)
+    g.ew(1, 0, 0, 2.0, -1.0)                       # 2x - x
+    np.testing.assert_array_equal(g.read_field(1), x)
+    g.ew(2, 0, 0, gamma=1.0)                       # x * x
+    np.testing.assert_array_equal(g.read_field(2), np.where(act, x * x, 0.0))
+    g.ew(3, delta=0.75)                            # fill
+    np.testing.assert_array_equal(g.read_field(3), np.where(act, 0.75, 0.0))
+    assert g.sum(3) == pytest.approx(0.75 * act.sum(), rel=1e-15)
+    for _ in range(10):
+        g.ew(1, 1, alpha=1.0, delta=1.0)           # increments
+    np.testing.assert_allclose(g.read_field(1), np.where(act, x + 10.0, 0.0), rtol=0, atol=1e-12)
+
+
+def test_ew_saxpy_chain_in_place():
+    """z = 3x + y; y = y - z (in place, reads its own old value); against the
+    same arithmetic on the dense values."""
+    g, b, m = _shell_grid(seed=2)
+    act = mask_bits(m, 512)
+    g.ew(1, 0, alpha=0.5, delta=-0.25)             # y = 0.5 x - 0.25
+    x, y = g.read_field(0), g.read_field(1)
+    g.ew(2, 0, 1, 3.0, 1.0)
+    g.ew(1, 1, 2, 1.0, -1.0)
+    z = np.where(act, 3.0 * x + y, 0.0)
+    np.testing.assert_allclose(g.read_field(2), z, rtol=1e-15, atol=0)
+    np.testing.assert_allclose(g.read_field(1), np.where(act, y - z, 0.0), rtol=1e-15, atol=1e-15)
+
+
 def test_grid_update_hand_case():
     """v = p/m, v_z -= dt g, then the boundary clamp (index < bound with
     negative component, index > N - bound with positive component)."""
