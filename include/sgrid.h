@@ -151,9 +151,28 @@ int sg_list_gen(sg_grid *g);
  * out-of-domain voxels give 0; dst at inactive voxels stays 0. */
 int sg_launch_stencil(sg_grid *g, int32_t op, int32_t src, int32_t dst, float coef);
 
+/* Queue an element-wise struct-for: on every active voxel
+ *   dst = alpha * a + beta * b + gamma * a * b + delta,
+ * a and b read at the same voxel (field index -1: absent, reads 0); dst
+ * keeps 0 at inactive voxels; dst may equal a or b.  It covers the general
+ * kernels of the paper's microbenchmarks (copies, increments, fills, saxpy,
+ * products; Supp. Sec. 1).  With SG_OPT_FUSE (and SG_OPT_LGR) a run of
+ * consecutive element-wise ops, with at most one reduction among them, is one
+ * launch (Sec. 6.4; at most sg_set_max_fuse ops, default 16, and 8 distinct
+ * fields); with SG_OPT_DSE a scratch field written in the run and read by no
+ * later queued op is not stored (Sec. 6.5). */
+int sg_launch_ew(sg_grid *g, int32_t dst, int32_t a, int32_t b, float alpha, float beta, float gamma,
+                 float delta);
+
+/* Largest number of element-wise ops fused into one launch (>= 1; the
+ * role of the paper's async_max_fuse_per_task, Supp. Sec. 2 item 4). */
+int sg_set_max_fuse(sg_grid *g, int32_t max_ops);
+
 /* Queue: sum of field src over the active voxels into result slot out_slot
  * (FP64; per-leaf partials are FP32).  Read with sg_read_sums. */
 int sg_reduce_sum(sg_grid *g, int32_t src, int64_t out_slot);
+/* (With SG_OPT_DSE, a reduction whose result slot a later queued reduction
+ * overwrites within the same flush is not run: nothing reads it.) */
 
 /* Queue P2G with activation: for each of n particles (positions dev_x and
  * velocities dev_v, n*3 FP32 in (x,y,z) order, device memory, borrowed) and

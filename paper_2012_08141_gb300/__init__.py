@@ -89,6 +89,8 @@ def load_library(build: bool = True) -> ctypes.CDLL:
         "sg_g2p_apic": [P, P, P, P, I64, F, I32],
         "sg_g2p2g": [P, P, P, P, I64, F, I32, F, I32, I32],
         "sg_restrict": [P, P, I32, I32, F],
+        "sg_launch_ew": [P, I32, I32, I32, F, F, F, F],
+        "sg_set_max_fuse": [P, I32],
         "sg_prolong": [P, P, I32, I32, F],
         "sg_swap": [P, I32, I32],
         "sg_flush": [P],
@@ -225,6 +227,15 @@ class Grid:
 
     def box27(self, src: int, dst: int):
         self.stencil(SG_BOX27, src, dst)
+
+    def ew(self, dst: int, a: int = -1, b: int = -1, alpha: float = 0.0, beta: float = 0.0, gamma: float = 0.0,
+           delta: float = 0.0):
+        """Queue dst = alpha a + beta b + gamma a b + delta on the active voxels (-1: absent field)."""
+        self._c(self.lib.sg_launch_ew(self.h, int(dst), int(a), int(b), float(alpha), float(beta), float(gamma),
+                                      float(delta)))
+
+    def set_max_fuse(self, max_ops: int):
+        self._c(self.lib.sg_set_max_fuse(self.h, int(max_ops)))
 
     def reduce_sum(self, src: int, slot: int):
         self._c(self.lib.sg_reduce_sum(self.h, int(src), int(slot)))

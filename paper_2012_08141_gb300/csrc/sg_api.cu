@@ -53,7 +53,7 @@ int fail(int code, const char *fmt, ...)
 }
 
 enum OpKind { OP_ACT_SHELL, OP_ACT_COORDS, OP_DEACT, OP_LISTGEN, OP_STENCIL, OP_SUM, OP_P2G, OP_GRID_UPDATE, OP_G2P, OP_TEST_WAIT,
-              OP_FILL, OP_G2P2G };
+              OP_FILL, OP_G2P2G, OP_EW };
 
 struct Op {
     OpKind kind;
@@ -67,7 +67,7 @@ struct Op {
     void *p1 = nullptr, *p2 = nullptr, *p3 = nullptr;
     const sg_grid *peer = nullptr, *bins = nullptr;  // G2P2G: source grid, holder of the particle bins
     long long n = 0;
-    float f0 = 0.f, f1 = 0.f;
+    float f0 = 0.f, f1 = 0.f, f2 = 0.f;
     int i0 = 0, i1 = 0, i2 = 0;
     long long slot = 0;
 };
@@ -91,6 +91,7 @@ struct sg_grid {
     std::set<std::pair<const sg_grid *, unsigned long long>> applied_restrict;
     unsigned long long lg_calls = 0;
     unsigned long long rmask_ver = 0;  // list version the region masks were built from (0 = never)
+    int max_fuse = kMaxEwOps;          // element-wise ops per fused launch
     long long known_leaves = 0;
     sg_stats stats{};
     int latched = SG_OK;
@@ -188,6 +189,8 @@ bool read_later(const sg_grid *g, size_t from, int f)
     for (size_t i = from; i < g->queue.size(); ++i) {
         const Op &o = g->queue[i];
         if ((o.kind == OP_STENCIL && o.op != SG_CLEAR && o.src == f) || (o.kind == OP_SUM && o.src == f)) return true;
+        if (o.kind == OP_EW && (o.src == f || o.i0 == f)) return true;
+        if (o.kind == OP_EW && o.dst == f) return false;  // fully overwritten
         if (o.kind == OP_P2G || o.kind == OP_GRID_UPDATE || o.kind == OP_G2P) return true;  // conservative
         if (o.kind == OP_STENCIL && o.dst == f) return false;  // fully overwritten
     }
@@ -201,6 +204,11 @@ bool clear_is_dead(const sg_grid *g, size_t i)
     const int f = g->queue[i].dst;
     for (size_t k = i + 1; k < g->queue.size(); ++k) {
         const Op &o = g->queue[k];
+        if (o.kind == OP_EW) {
+            if (o.src == f || o.i0 == f) return false;
+            if (o.dst == f) return true;
+            continue;
+        }
         if (o.kind != OP_STENCIL && o.kind != OP_SUM) return false;  // structure may change
         if (o.kind == OP_SUM && o.src == f) return false;
         if (o.kind == OP_STENCIL && o.op != SG_CLEAR && o.src == f) return false;
@@ -276,6 +284,105 @@ int run_struct_for_group(sg_grid *g, size_t &i)
     return after_launch(g, "stencil");
 }
 
+// A run of element-wise ops from queue[i] (and at most one reduction inside
+// it) as one launch (Sec. 6.4): consecutive ops over the same list whose
+// accesses are all at the iteration's voxel, at most max_fuse ops and
+// kMaxEwSlots distinct fields.  Fields read before written are loaded once;
+// a written field is stored once, and not at all when it is scratch and no
+// later queued op reads it (Sec. 6.5).  Without fusion each op is a launch.
+int run_ew_group(sg_grid *g, size_t &i)
+{
+    int rc;
+    if ((rc = ensure_list(g))) return rc;
+    const bool fuse = (g->opts & SG_OPT_FUSE) && (g->opts & SG_OPT_LGR);
+    const bool dse = (g->opts & SG_OPT_DSE) != 0;
+    const int limit = fuse ? std::max(1, std::min(g->max_fuse, kMaxEwOps)) : 1;
+    EwProgram p{};
+    p.sum_out = -1;
+    int slot_of[kMaxFields];
+    for (int f = 0; f < kMaxFields; ++f) slot_of[f] = -1;
+    bool written[kMaxEwSlots] = {}, scratch[kMaxEwSlots] = {};
+    int writes[kMaxEwSlots] = {};
+    auto needed = [&](int f) { return (f >= 0 && slot_of[f] < 0) ? 1 : 0; };
+    auto use = [&](int f, bool write) -> int8_t {
+        if (f < 0) return -1;
+        if (slot_of[f] < 0) {
+            slot_of[f] = p.n_slots;
+            p.field[p.n_slots++] = f;
+        }
+        const int k = slot_of[f];
+        if (!write && !written[k]) p.load[k] = 1;
+        return (int8_t)k;
+    };
+    size_t j = i;
+    int nops = 0;
+    while (j < g->queue.size()) {
+        const Op &o = g->queue[j];
+        if (o.kind == OP_EW && nops < limit) {
+            int add = needed(o.src) + needed(o.i0);
+            add += (o.dst != o.src && o.dst != o.i0) ? needed(o.dst) : 0;
+            if (p.n_slots + add > kMaxEwSlots) break;
+            EwOp e;
+            e.a = use(o.src, false);
+            e.b = use(o.i0, false);
+            e.dst = use(o.dst, true);
+            e.alpha = o.f0;
+            e.beta = o.f1;
+            e.gamma = o.coef;
+            e.delta = o.f2;
+            p.op[p.n_ops++] = e;
+            written[e.dst] = true;
+            scratch[e.dst] = o.dst_scratch;
+            writes[e.dst]++;
+            ++nops;
+            ++j;
+        } else if (fuse && o.kind == OP_SUM && p.sum_out < 0 && nops > 0 && p.n_slots + needed(o.src) <= kMaxEwSlots) {
+            EwOp e{};
+            e.dst = -1;
+            e.a = use(o.src, false);
+            e.b = -1;
+            p.op[p.n_ops++] = e;
+            p.sum_out = (int)o.slot;
+            ++j;
+        } else {
+            break;
+        }
+    }
+    int stores = 0, loads = 0;
+    for (int k = 0; k < p.n_slots; ++k) {
+        loads += p.load[k];
+        if (!written[k]) continue;
+        p.store[k] = !(dse && scratch[k] && !read_later(g, j, p.field[k]));
+        stores += p.store[k];
+        g->stats.stores_removed += writes[k] - (p.store[k] ? 1 : 0);
+    }
+    if (!g->dry) launch_ew(g->dev, g->stream, p, g->lc);
+    g->stats.ops_fused += (int64_t)(j - i) - 1;
+    g->stats.bytes_model += leaf_bytes(g) * double(g->known_leaves) * double(loads + stores);
+    i = j;
+    return after_launch(g, "element-wise");
+}
+
+// Dead-store elimination of reductions: within one flush nothing on the
+// device reads a result slot, so a reduction whose slot a later reduction in
+// the queue overwrites is dead (the autodiff microbenchmark's pattern).
+void drop_dead_sums(sg_grid *g)
+{
+    if (!(g->opts & SG_OPT_DSE)) return;
+    std::vector<Op> kept;
+    kept.reserve(g->queue.size());
+    for (size_t k = 0; k < g->queue.size(); ++k) {
+        const Op &o = g->queue[k];
+        bool dead = false;
+        if (o.kind == OP_SUM)
+            for (size_t m = k + 1; m < g->queue.size() && !dead; ++m)
+                dead = g->queue[m].kind == OP_SUM && g->queue[m].slot == o.slot;
+        if (dead) g->stats.stores_removed++;
+        else kept.push_back(o);
+    }
+    g->queue.swap(kept);
+}
+
 // Binned-P2G scratch: bin counts and offsets over the root cells, the count
 // scan's tile sums, and a particle order array of at least n entries.
 int ensure_p2g_scratch(sg_grid *g, long long n)
@@ -304,6 +411,7 @@ int do_flush(sg_grid *g)
 {
     int rc = SG_OK;
     g->stats.flushes++;
+    drop_dead_sums(g);
     size_t i = 0;
     while (i < g->queue.size() && rc == SG_OK) {
         const Op &o = g->queue[i];
@@ -362,6 +470,9 @@ int do_flush(sg_grid *g)
             case OP_STENCIL:
             case OP_SUM:
                 rc = run_struct_for_group(g, i);
+                break;
+            case OP_EW:
+                rc = run_ew_group(g, i);
                 break;
             case OP_P2G:
                 if (!(rc = ensure_p2g_scratch(g, o.n))) {
@@ -643,6 +754,29 @@ int sg_launch_stencil(sg_grid *g, int32_t op, int32_t src, int32_t dst, float co
     o.dst_scratch = (g->desc.scratch_mask >> dst) & 1u;
     o.coef = coef;
     return push(g, o);
+}
+
+int sg_launch_ew(sg_grid *g, int32_t dst, int32_t a, int32_t b, float alpha, float beta, float gamma, float delta)
+{
+    if (!g || !valid_field(g, dst) || (a != -1 && !valid_field(g, a)) || (b != -1 && !valid_field(g, b)))
+        return fail(SG_ERR_INVALID, "bad element-wise fields dst=%d a=%d b=%d", dst, a, b);
+    Op o{OP_EW};
+    o.dst = g->phys[dst];
+    o.src = a >= 0 ? g->phys[a] : -1;
+    o.i0 = b >= 0 ? g->phys[b] : -1;
+    o.dst_scratch = (g->desc.scratch_mask >> dst) & 1u;
+    o.f0 = alpha;
+    o.f1 = beta;
+    o.coef = gamma;
+    o.f2 = delta;
+    return push(g, o);
+}
+
+int sg_set_max_fuse(sg_grid *g, int32_t max_ops)
+{
+    if (!g || max_ops < 1) return fail(SG_ERR_INVALID, "max_fuse must be >= 1");
+    g->max_fuse = max_ops;
+    return SG_OK;
 }
 
 int sg_reduce_sum(sg_grid *g, int32_t src, int64_t out_slot)

@@ -179,6 +179,26 @@ void launch_grid_update(const DevGrid &g, cudaStream_t s, int f_mass, int f_mom0
 void launch_g2p(const DevGrid &g, cudaStream_t s, float *x, float *v, float *C, long long n, float dt, int f_mom0,
                 int binned, const LaunchCfg &lc);
 
+// ---- fused element-wise struct-fors (sg_elementwise.cu) ----
+constexpr int kMaxEwOps = 16;   // ops (and at most one reduction) per fused launch
+constexpr int kMaxEwSlots = 8;  // distinct fields per fused launch
+// r[dst] = alpha r[a] + beta r[b] + gamma r[a] r[b] + delta on the active
+// voxels (0 elsewhere); a, b = -1: absent (0).  dst = -1: add the active
+// values of r[a] to the launch's reduction.
+struct EwOp {
+    int8_t dst, a, b;
+    float alpha, beta, gamma, delta;
+};
+struct EwProgram {
+    int n_ops, n_slots;
+    int field[kMaxEwSlots];      // physical field of each slot
+    uint8_t load[kMaxEwSlots];   // read before written: load it
+    uint8_t store[kMaxEwSlots];  // final value live: store it
+    EwOp op[kMaxEwOps + 1];
+    int sum_out;                 // result index of the reduction, -1 none
+};
+void launch_ew(const DevGrid &g, cudaStream_t s, const EwProgram &prog, const LaunchCfg &lc);
+
 // ---- restriction / prolongation to a half-edge grid (sg_multigrid.cu) ----
 void launch_restrict_mark(const DevGrid &fine, const DevGrid &coarse, cudaStream_t s, const LaunchCfg &lc);
 // activate: set the coarse bits (the coarse leaves are allocated); else the

@@ -303,3 +303,81 @@ def test_restriction_argument_checks():
     assert lib.sg_restrict(a.h, b.h, 0, 5, 1.0) == sg.SG_ERR_INVALID       # field out of range
     assert lib.sg_prolong(b.h, a.h, 0, 1, 1.0) == 0
     assert lib.sg_prolong(a.h, b.h, 0, 1, 1.0) == sg.SG_ERR_INVALID        # arguments swapped
+
+
+# ---------------------------------------------------------------------------
+# The paper's microbenchmarks (Supp. Sec. 1) as launch counts on element-wise
+# struct-fors: each case runs once to make the list, then its ops are counted.
+# ---------------------------------------------------------------------------
+
+def _micro(opts=sg.SG_OPT_ALL, scratch=0b1000, F=5):
+    g = dry(64, 3, F, scratch=scratch)
+    g.set_opts(opts)
+    g.activate_shell(100, 900, False)
+    g.list_gen()
+    g.flush()
+    return g
+
+
+def _launches(g, fn):
+    s0 = g.stats()
+    fn(g)
+    g.flush()
+    s1 = g.stats()
+    return {k: s1[k] - s0[k] for k in s1}
+
+
+def test_micro_chain_copy():
+    d = _launches(_micro(), lambda g: (g.ew(1, 0, alpha=1.0, delta=1.0), g.ew(2, 1, alpha=1.0, delta=4.0)))
+    assert d["launches"] == 1 and d["ops_fused"] == 1
+
+
+def test_micro_increments_and_max_fuse():
+    d = _launches(_micro(), lambda g: [g.ew(0, 0, alpha=1.0, delta=1.0) for _ in range(10)])
+    assert d["launches"] == 1 and d["ops_fused"] == 9
+    g = _micro()
+    g.set_max_fuse(4)
+    d = _launches(g, lambda g: [g.ew(0, 0, alpha=1.0, delta=1.0) for _ in range(10)])
+    assert d["launches"] == 3                      # 4 + 4 + 2
+
+
+def test_micro_fill_array():
+    d = _launches(_micro(), lambda g: [g.ew(2, delta=float(k)) for k in range(10)])
+    assert d["launches"] == 1 and d["stores_removed"] == 9
+
+
+def test_micro_sparse_saxpy():
+    def body(g):
+        g.ew(2, 0, 1, 2.0, 1.0)                     # z = 2x + y
+        g.ew(1, 2, 0, 3.0, 1.0)                     # y = 3z + x
+        g.ew(2, 2, 1, 1.0, 1.0)                     # z = z + y
+    assert _launches(_micro(), body)["launches"] == 1
+    e = _launches(_micro(sg.SG_OPT_EAGER), body)
+    assert e["launches"] == 9 and e["listgen_run"] == 3     # clear-list + list + kernel per op
+
+
+def test_micro_autodiff_dead_forward_passes():
+    """Ten iterations of: tmp = x * x (scratch), loss = sum(tmp), grad += 2x.
+    Only the last loss is read, so nine reductions are dead; the element-wise
+    ops fuse into two launches (16 ops per launch)."""
+    def body(g):
+        for _ in range(10):
+            g.ew(3, 0, 0, gamma=1.0)
+            g.reduce_sum(3, 0)
+            g.ew(4, 4, 0, 1.0, 2.0)
+    d = _launches(_micro(), body)
+    assert d["launches"] == 2 and d["stores_removed"] >= 9
+    e = _launches(_micro(sg.SG_OPT_EAGER), body)
+    assert e["launches"] == 90
+
+
+def test_micro_not_fusible_across_a_stencil():
+    """An element-wise op, a neighbour-reading stencil, an element-wise op: the
+    stencil depends on the first and the second on the stencil (criterion 1),
+    so three launches; the list is still made only once (Sec. 6.2)."""
+    def body(g):
+        g.ew(1, 0, alpha=2.0)
+        g.diffuse7(1, 2, 0.1)
+        g.ew(0, 2, alpha=1.0, delta=1.0)
+    d = _launches(_micro(), body)
+    assert d["launches"] == 3 and d["listgen_run"] == 0
