@@ -16,6 +16,8 @@ it.  Further legs (skipped with --only fused or on more than one rank):
             separate G2P (C stored) + P2G against the fused G2P2G (C on chip);
   multigrid a 4-level V-cycle (restrict, smooth, prolong) from the 512^3 band,
             with and without activation demotion, and eager;
+  micro     the paper's microbenchmarks (chain_copy, increments, fill_array,
+            sparse_saxpy, autodiff, stencil_reduction) on the 512^3 band;
   serving   Poisson arrivals of band jobs (1e4..1e7 voxels, 10..200 steps)
             into the continuous-batching server: p50/p99 job latency;
   band1024  the 1024^3 band |dist - 400| < 8, far larger than L2.
@@ -387,6 +389,47 @@ def bench_multigrid(torch, sg, steps, warmup, flush_buf, stream):
     return out
 
 
+MICRO = {
+    # the paper's microbenchmarks (Supp. Sec. 1) as element-wise struct-fors on
+    # fields 0 (x), 1 (y), 2 (z), 3 (scratch), 4 (grad)
+    "chain_copy": lambda g: (g.ew(1, 0, alpha=1.0, delta=1.0), g.ew(2, 1, alpha=1.0, delta=4.0)),
+    "increments": lambda g: [g.ew(0, 0, alpha=1.0, delta=1.0) for _ in range(10)],
+    "fill_array": lambda g: [g.ew(2, delta=float(k)) for k in range(10)],
+    "sparse_saxpy": lambda g: (g.ew(2, 0, 1, 2.0, 1.0), g.ew(1, 2, 0, 3.0, 1.0), g.ew(2, 2, 1, 1.0, 1.0)),
+    "autodiff": lambda g: [(g.ew(3, 0, 0, gamma=1.0), g.reduce_sum(3, 0), g.ew(4, 4, 0, 1.0, 2.0))
+                           for _ in range(10)],
+    "stencil_reduction": lambda g: (g.diffuse7(0, 1, 0.1), g.reduce_sum(1, 0)),
+}
+
+
+def bench_micro(torch, sg, steps, warmup, flush_buf, stream):
+    """The microbenchmarks on the 512^3 band (26,104 leaves, 5 fields), each
+    case flushed as one program: all passes against eager."""
+    spec = band512()
+    out = {"workload": "paper microbenchmarks as element-wise struct-fors on the 512^3 band",
+           "l2": "flushed before every timed step (512 MB write)"}
+    for name, body in MICRO.items():
+        row = {}
+        for mode, opts in (("all_passes", sg.SG_OPT_ALL), ("eager", sg.SG_OPT_EAGER)):
+            g = sg.Grid(512, 3, 5, max_leaves=32768, max_sums=1, scratch_mask=0b01000)
+            g.set_opts(opts)
+            g.activate_shell(spec.lo2, spec.hi2, spec.lo_strict)
+            g.fill_hash(0, 1)
+            g.fill_hash(1, 2)
+            g.sync()
+
+            def step():
+                body(g)
+                g.flush()
+
+            ms, nl = time_steps(torch, step, steps, warmup, flush_buf, stream, lambda: g.stats()["launches"])
+            row[mode] = {"ms": sum(ms) / len(ms), "launches": nl / len(ms)}
+            g.close()
+        row["speedup"] = row["eager"]["ms"] / row["all_passes"]["ms"]
+        out[name] = row
+    return out
+
+
 def bench_serving(torch, sg, rates=(50, 100, 200, 500, 1000, 2000), duration=2.0, cap_s=60.0):
     from paper_2012_08141_gb300.serve import Server
     out = []
@@ -514,6 +557,7 @@ def run_ours(args):
                          ("particles", lambda: bench_particles(torch, sg, k, 3, flush_buf, stream)),
                          ("mpm_apic", lambda: bench_mpm_apic(torch, sg, k, 3, flush_buf, stream)),
                          ("multigrid", lambda: bench_multigrid(torch, sg, k, 3, flush_buf, stream)),
+                         ("micro", lambda: bench_micro(torch, sg, k, 3, flush_buf, stream)),
                          ("serving", lambda: bench_serving(torch, sg))):
             if args.only not in ("all", name):
                 continue
@@ -645,7 +689,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--variant", type=int, default=0, help="stencil kernel family (0 sweep, 1 smem)")
     ap.add_argument("--only", choices=["all", "fused", "band1024", "batched", "particles", "mpm_apic", "multigrid",
-                                       "serving"],
+                                       "micro", "serving"],
                     default="all",
                     help="fused: only the fused headline step; a leg name: the headline step and that leg "
                          "(for profiling runs)")
