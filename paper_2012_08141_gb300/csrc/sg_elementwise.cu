@@ -56,11 +56,19 @@ __global__ void __launch_bounds__(256) k_ew(DevGrid g, EwProgram prog)
     }
 }
 
+template <int L>
+static int ew_ctas(int num_sms)
+{
+    static int per = 0;
+    if (!per && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_ew<L>, 256, 0) != cudaSuccess || per < 1))
+        per = 1;
+    return per * num_sms;  // all resident at once (one reduction partial each)
+}
+
 void launch_ew(const DevGrid &g, cudaStream_t s, const EwProgram &prog, const LaunchCfg &lc)
 {
-    const int ctas = lc.persistent_ctas * 4;
-    if (g.L == 8) k_ew<8><<<ctas, 256, 0, s>>>(g, prog);
-    else k_ew<4><<<ctas, 256, 0, s>>>(g, prog);
+    if (g.L == 8) k_ew<8><<<ew_ctas<8>(lc.num_sms), 256, 0, s>>>(g, prog);
+    else k_ew<4><<<ew_ctas<4>(lc.num_sms), 256, 0, s>>>(g, prog);
 }
 
 }  // namespace sg
