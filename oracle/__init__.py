@@ -69,6 +69,9 @@ def _load():
         "og_p2g_apic": (None, [P, P, P, P, I64, D, I32, I32]),
         "og_restrict": (None, [P, P, I32, I32, D]),
         "og_ew": (None, [P, I32, I32, I32, D, D, D, D]),
+        "og_activate_tube": (I64, [P, I64, I64]),
+        "og_advect": (None, [P, I32, I32, I32, D]),
+        "og_maccormack": (None, [P, I32, I32, I32, I32, I32, D]),
         "og_prolong": (None, [P, P, I32, I32, D]),
         "og_g2p_apic": (None, [P, P, P, P, I64, D, I32]),
         "og_get_voxel": (D, [P, I32, I64, I64, I64]),
@@ -197,6 +200,18 @@ class Grid:
         assert x.dtype == np.float32 and v.dtype == np.float32
         assert x.flags.c_contiguous and v.flags.c_contiguous
         self.lib.og_g2p(self.h, _ptr(x), _ptr(v), x.size // 3, float(dt), int(f_mom0))
+
+    def activate_tube(self, lo2: int, hi2: int) -> int:
+        """Activate the voxels with lo2 <= (2i+1-N)^2 + (2j+1-N)^2 < hi2 (a tube along k)."""
+        return int(self.lib.og_activate_tube(self.h, int(lo2), int(hi2)))
+
+    def advect(self, dst: int, src: int, v0: int, dt: float):
+        """dst = src at the RK3 backtrace over dt (trilinear, through the mask)."""
+        self.lib.og_advect(self.h, int(dst), int(src), int(v0), float(dt))
+
+    def maccormack(self, dst: int, q: int, qhat: int, qtilde: int, v0: int, dt: float):
+        """dst = clamp(qhat + (q - qtilde) / 2) to the forward sample's 8 values of q."""
+        self.lib.og_maccormack(self.h, int(dst), int(q), int(qhat), int(qtilde), int(v0), float(dt))
 
     def ew(self, dst: int, a: int = -1, b: int = -1, alpha: float = 0.0, beta: float = 0.0, gamma: float = 0.0,
            delta: float = 0.0):

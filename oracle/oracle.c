@@ -180,6 +180,22 @@ int64_t og_activate_shell(og_grid *g, int64_t lo2, int64_t hi2, int32_t lo_stric
 
 /* Activate explicit voxels given as n (i,j,k) int32 triples.  Coordinates
  * outside the domain are ignored.  Returns the number newly activated. */
+/* Activate every voxel whose cell centre lies in the tube lo2 <= D < hi2
+ * around the k axis through the domain centre, D = (2i+1-N)^2 + (2j+1-N)^2
+ * (4 N^2 times the squared distance from the axis), at every k.  Returns the
+ * number of newly activated voxels. */
+int64_t og_activate_tube(og_grid *g, int64_t lo2, int64_t hi2)
+{
+    int64_t N = g->N, cnt = 0;
+    for (int64_t i = 0; i < N; i++)
+        for (int64_t j = 0; j < N; j++) {
+            int64_t a = 2 * i + 1 - N, b = 2 * j + 1 - N, D = a * a + b * b;
+            if (D < lo2 || D >= hi2) continue;
+            for (int64_t k = 0; k < N; k++) cnt += og_activate_voxel(g, i, j, k);
+        }
+    return cnt;
+}
+
 int64_t og_activate_coords(og_grid *g, const int32_t *xyz, int64_t n)
 {
     int64_t cnt = 0;
@@ -559,6 +575,104 @@ void og_ew(og_grid *g, int32_t dst, int32_t a, int32_t b, double alpha, double b
         if (!g->act[q]) { g->val[dst][q] = 0.0; continue; }
         double va = a >= 0 ? g->val[a][q] : 0.0, vb = b >= 0 ? g->val[b][q] : 0.0;
         g->val[dst][q] = alpha * va + beta * vb + gamma * va * vb + delta;
+    }
+}
+
+/* ---------------------------------------------------------------------------
+ * MacCormack advection with RK3 path integration (Sec. 8.2; Supp. Sec. 4.2).
+ * Collocated grid: every field lives at cell centres, voxel (i,j,k) at grid
+ * position (i+0.5, j+0.5, k+0.5) in cell units.  Velocities are in domain
+ * units (the unit cube) per time, so a time step dt moves h = dt * N cells
+ * per unit velocity.  Samples between cells are trilinear over the 8
+ * surrounding cell centres, each read through the mask (inactive or
+ * out-of-domain cells read 0).  The paper does not print the scheme; the
+ * readings are: Ralston's third-order Runge-Kutta for the backtrace, and the
+ * MacCormack correction of Selle et al. clamped to the 8 values the forward
+ * sample interpolates.
+ * ------------------------------------------------------------------------- */
+
+/* Trilinear sample of field f at position p (cell units); optionally the
+ * min / max of the 8 cell values it interpolates. */
+static double og_trilinear(const og_grid *g, int f, const double p[3], double *mn, double *mx)
+{
+    double X[3], fr[3];
+    int64_t b[3];
+    for (int a = 0; a < 3; a++) {
+        X[a] = p[a] - 0.5;
+        b[a] = (int64_t)floor(X[a]);
+        fr[a] = X[a] - (double)b[a];
+    }
+    double s = 0.0, lo = INFINITY, hi = -INFINITY;
+    for (int a = 0; a < 2; a++)
+        for (int c = 0; c < 2; c++)
+            for (int d = 0; d < 2; d++) {
+                double v = og_get(g, f, b[0] + a, b[1] + c, b[2] + d);
+                double w = (a ? fr[0] : 1.0 - fr[0]) * (c ? fr[1] : 1.0 - fr[1]) * (d ? fr[2] : 1.0 - fr[2]);
+                s += w * v;
+                if (v < lo) lo = v;
+                if (v > hi) hi = v;
+            }
+    if (mn) *mn = lo;
+    if (mx) *mx = hi;
+    return s;
+}
+
+/* Velocity (fields v0, v0+1, v0+2) interpolated at p. */
+static void og_velocity(const og_grid *g, int v0, const double p[3], double u[3])
+{
+    for (int a = 0; a < 3; a++) u[a] = og_trilinear(g, v0 + a, p, NULL, NULL);
+}
+
+/* Backtrace of the centre of voxel (i,j,k) over h cells per unit velocity
+ * with Ralston's RK3: k1 = u(x), k2 = u(x - h/2 k1), k3 = u(x - 3h/4 k2),
+ * x_back = x - h (2 k1 + 3 k2 + 4 k3) / 9. */
+static void og_backtrace(const og_grid *g, int v0, double h, int64_t i, int64_t j, int64_t k, double out[3])
+{
+    double x[3] = {(double)i + 0.5, (double)j + 0.5, (double)k + 0.5}, k1[3], k2[3], k3[3], p[3];
+    og_velocity(g, v0, x, k1);
+    for (int a = 0; a < 3; a++) p[a] = x[a] - 0.5 * h * k1[a];
+    og_velocity(g, v0, p, k2);
+    for (int a = 0; a < 3; a++) p[a] = x[a] - 0.75 * h * k2[a];
+    og_velocity(g, v0, p, k3);
+    for (int a = 0; a < 3; a++) out[a] = x[a] - h * (2.0 * k1[a] + 3.0 * k2[a] + 4.0 * k3[a]) / 9.0;
+}
+
+/* Semi-Lagrangian advection: dst = src sampled at the backtrace of every
+ * active voxel over time step dt (negative: backward); 0 at inactive voxels.
+ * dst must differ from src and the velocity fields. */
+void og_advect(og_grid *g, int32_t dst, int32_t src, int32_t v0, double dt)
+{
+    int64_t v = cube(g->L), total = g->n * v;
+    double h = dt * (double)g->N;
+#pragma omp parallel for schedule(static)
+    for (int64_t q = 0; q < total; q++) {
+        if (!g->act[q]) { g->val[dst][q] = 0.0; continue; }
+        int64_t i, j, k;
+        double p[3];
+        coords_of(g, q / v, q % v, &i, &j, &k);
+        og_backtrace(g, v0, h, i, j, k, p);
+        g->val[dst][q] = og_trilinear(g, src, p, NULL, NULL);
+    }
+}
+
+/* MacCormack correction: dst = qhat + (q - qtilde) / 2 at every active voxel,
+ * clamped to the min / max of the 8 values of q that the forward sample (the
+ * backtrace over dt) interpolates; 0 at inactive voxels.  dst must differ
+ * from q and the velocity fields. */
+void og_maccormack(og_grid *g, int32_t dst, int32_t qf, int32_t qhat, int32_t qtilde, int32_t v0, double dt)
+{
+    int64_t v = cube(g->L), total = g->n * v;
+    double h = dt * (double)g->N;
+#pragma omp parallel for schedule(static)
+    for (int64_t q = 0; q < total; q++) {
+        if (!g->act[q]) { g->val[dst][q] = 0.0; continue; }
+        int64_t i, j, k;
+        double p[3], lo, hi;
+        coords_of(g, q / v, q % v, &i, &j, &k);
+        og_backtrace(g, v0, h, i, j, k, p);
+        og_trilinear(g, qf, p, &lo, &hi);
+        double r = g->val[qhat][q] + 0.5 * (g->val[qf][q] - g->val[qtilde][q]);
+        g->val[dst][q] = r < lo ? lo : (r > hi ? hi : r);
     }
 }
 

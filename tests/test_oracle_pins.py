@@ -551,6 +551,106 @@ def test_ew_saxpy_chain_in_place():
     np.testing.assert_allclose(g.read_field(1), np.where(act, y - z, 0.0), rtol=1e-15, atol=1e-15)
 
 
+# ---------------------------------------------------------------------------
+# Tube activation and MacCormack / RK3 advection
+# ---------------------------------------------------------------------------
+
+def test_tube_structure_matches_bruteforce():
+    N, L = 32, 8
+    lo2, hi2 = 4 * N * N * 0.32 ** 2, 4 * N * N * 0.45 ** 2
+    lo2, hi2 = int(np.ceil(lo2)), int(np.ceil(hi2))
+    g = oracle.Grid(N, L, 1)
+    n = g.activate_tube(lo2, hi2)
+    c = (2 * np.arange(N) + 1 - N) ** 2
+    D = c[:, None] + c[None, :]
+    act2 = (D >= lo2) & (D < hi2)
+    act = np.broadcast_to(act2[:, :, None], (N, N, N))
+    assert n == int(act.sum())
+    b, m = g.structure()
+    b2, m2 = dt.structure(act, L)
+    np.testing.assert_array_equal(b, b2)
+    np.testing.assert_array_equal(m, m2)
+
+
+def _box_advect_grid(N=32, L=8, lo=4, hi=28, F=6):
+    g = oracle.Grid(N, L, F)
+    r = np.arange(lo, hi)
+    box = np.stack(np.meshgrid(r, r, r, indexing="ij"), -1).reshape(-1, 3).astype(np.int32)
+    g.activate_coords(box)
+    b, _ = g.structure()
+    cells = oracle.leaf_coords(b, N, L).astype(np.float64) + 0.5      # cell centres, cell units
+    return g, b, cells
+
+
+def test_advect_uniform_integer_shift_is_exact():
+    """Uniform velocity moving exactly (2, -1, 0) cells per step: every voxel
+    whose source stays inside the box gets the source value exactly."""
+    N, dtime = 32, 0.01
+    g, b, cells = _box_advect_grid(N)
+    shift = np.array([2.0, -1.0, 0.0])
+    u = shift / (dtime * N)
+    for a in range(3):
+        g.write_field64(1 + a, np.full(cells.shape[:2], u[a]))
+    q = np.sin(cells[..., 0]) + 0.1 * cells[..., 1] * cells[..., 2]
+    g.write_field64(0, q)
+    g.advect(4, 0, 1, dtime)
+    src = cells - shift
+    inside = np.all((src > 4) & (src < 28), axis=2) & np.all((cells > 7) & (cells < 25), axis=2)
+    want = np.sin(src[..., 0]) + 0.1 * src[..., 1] * src[..., 2]
+    got = g.read_field(4)
+    np.testing.assert_allclose(got[inside], want[inside], rtol=0, atol=1e-12)
+
+
+def test_advect_linear_fields_rk3_taylor():
+    """Linear velocity u(c) = B (c - c0) and linear scalar q(c) = w . (c - c0)
+    + q0, both reproduced exactly by trilinear interpolation: the RK3
+    backtrace of a linear ODE is the third-order Taylor polynomial of
+    exp(-hB), so q_hat(c) = w . T (c - c0) + q0 with T = I - hB + (hB)^2/2 -
+    (hB)^3/6 on voxels whose stages stay inside the box.  A wrong RK3
+    coefficient or a sign of h changes T."""
+    N, dtime = 32, 0.004          # displacements below 2 cells: every sample stays in the box
+    g, b, cells = _box_advect_grid(N)
+    c0 = np.array([16.0, 16.0, 16.0])
+    B = np.array([[0.3, -1.1, 0.2], [0.9, 0.1, -0.4], [-0.2, 0.5, -0.3]])
+    d = cells - c0
+    for a in range(3):
+        g.write_field64(1 + a, d @ B[a])
+    w, q0 = np.array([0.7, -0.3, 1.2]), 2.5
+    g.write_field64(0, d @ w + q0)
+    g.advect(4, 0, 1, dtime)
+    hB = dtime * N * B
+    T = np.eye(3) - hB + hB @ hB / 2 - hB @ hB @ hB / 6
+    want = (d @ T.T) @ w + q0
+    inside = np.all(np.abs(d) < 8.5, axis=2)
+    np.testing.assert_allclose(g.read_field(4)[inside], want[inside], rtol=0, atol=1e-11)
+
+
+def test_maccormack_linear_field_and_clamp():
+    """Uniform fractional velocity on a linear field: q_hat = q(x - d),
+    q_tilde = q, so the correction returns q_hat exactly; the corrected value
+    always lies within the forward sample's 8 values."""
+    N, dtime = 32, 0.01
+    g, b, cells = _box_advect_grid(N)
+    u = np.array([0.7, -0.35, 1.3]) / (dtime * N)
+    for a in range(3):
+        g.write_field64(1 + a, np.full(cells.shape[:2], u[a]))
+    w = np.array([0.5, 1.5, -0.25])
+    g.write_field64(0, (cells - 16.0) @ w)
+    g.advect(4, 0, 1, dtime)
+    g.advect(5, 4, 1, -dtime)
+    g.maccormack(3, 0, 4, 5, 1, dtime)
+    inside = np.all(np.abs(cells - 16.0) < 8, axis=2)
+    np.testing.assert_allclose(g.read_field(3)[inside], g.read_field(4)[inside], rtol=0, atol=1e-12)
+    # bounds on a rough field
+    rng = np.random.default_rng(4)
+    g.write_field64(0, rng.uniform(-1, 1, size=cells.shape[:2]))
+    g.advect(4, 0, 1, dtime)
+    g.advect(5, 4, 1, -dtime)
+    g.maccormack(3, 0, 4, 5, 1, dtime)
+    q, r = g.read_field(0), g.read_field(3)
+    assert np.all(r <= max(q.max(), 0.0) + 1e-15) and np.all(r >= min(q.min(), 0.0) - 1e-15)
+
+
 def test_grid_update_hand_case():
     """v = p/m, v_z -= dt g, then the boundary clamp (index < bound with
     negative component, index > N - bound with positive component)."""
