@@ -151,6 +151,34 @@ int sg_list_gen(sg_grid *g);
  * out-of-domain voxels give 0; dst at inactive voxels stays 0. */
 int sg_launch_stencil(sg_grid *g, int32_t op, int32_t src, int32_t dst, float coef);
 
+/* Queue activation of a tube along the k axis: every voxel with
+ * lo2 <= (2i+1-N)^2 + (2j+1-N)^2 < hi2 (4 N^2 times the squared distance of
+ * its cell centre from the axis through the domain centre), at every k (the
+ * advection domain of Sec. 8.2 / Supp. Sec. 4.2).  Activation demotion as for
+ * sg_activate_shell. */
+int sg_activate_tube(sg_grid *g, int64_t lo2, int64_t hi2);
+
+/* Queue semi-Lagrangian advection (Sec. 8.2): on every active voxel, dst =
+ * src sampled at the cell centre's backtrace over dt (negative: backward)
+ * through the velocity fields v0, v0+1, v0+2 (domain units per time; three
+ * consecutive unswapped fields).  Collocated cells, Ralston's RK3 for the
+ * backtrace, trilinear samples read through the mask (inactive or
+ * out-of-domain cells read 0); dst keeps 0 at inactive voxels.  dst must
+ * differ from src and the velocity fields. */
+int sg_advect(sg_grid *g, int32_t dst, int32_t src, int32_t v0, float dt);
+
+/* Queue the MacCormack correction (Selle et al., as used in Sec. 8.2): on
+ * every active voxel dst = qhat + (q - qtilde) / 2, clamped to the min / max
+ * of the 8 values of q that the forward sample (the backtrace over dt)
+ * interpolates; dst keeps 0 at inactive voxels and differs from every input.
+ * With SG_OPT_FUSE (and SG_OPT_LGR) the queue schedules a run of advection
+ * ops by their field dependencies: independent advections with the same
+ * velocity and step are one launch of up to three channels sharing the
+ * backtrace, and a backward advection whose output a correction reads is
+ * fused with it (that output, if scratch and read later by nothing, is not
+ * stored) -- the channel fusion of Sec. 8.2. */
+int sg_maccormack(sg_grid *g, int32_t dst, int32_t q, int32_t qhat, int32_t qtilde, int32_t v0, float dt);
+
 /* Queue an element-wise struct-for: on every active voxel
  *   dst = alpha * a + beta * b + gamma * a * b + delta,
  * a and b read at the same voxel (field index -1: absent, reads 0); dst

@@ -90,6 +90,9 @@ def load_library(build: bool = True) -> ctypes.CDLL:
         "sg_g2p2g": [P, P, P, P, I64, F, I32, F, I32, I32],
         "sg_restrict": [P, P, I32, I32, F],
         "sg_launch_ew": [P, I32, I32, I32, F, F, F, F],
+        "sg_activate_tube": [P, I64, I64],
+        "sg_advect": [P, I32, I32, I32, F],
+        "sg_maccormack": [P, I32, I32, I32, I32, I32, F],
         "sg_set_max_fuse": [P, I32],
         "sg_prolong": [P, P, I32, I32, F],
         "sg_swap": [P, I32, I32],
@@ -233,6 +236,18 @@ class Grid:
         """Queue dst = alpha a + beta b + gamma a b + delta on the active voxels (-1: absent field)."""
         self._c(self.lib.sg_launch_ew(self.h, int(dst), int(a), int(b), float(alpha), float(beta), float(gamma),
                                       float(delta)))
+
+    def activate_tube(self, lo2: int, hi2: int):
+        """Queue activation of the tube lo2 <= (2i+1-N)^2 + (2j+1-N)^2 < hi2 along k."""
+        self._c(self.lib.sg_activate_tube(self.h, int(lo2), int(hi2)))
+
+    def advect(self, dst: int, src: int, v0: int, dt: float):
+        """Queue dst = src at the RK3 backtrace over dt through velocity fields v0..v0+2."""
+        self._c(self.lib.sg_advect(self.h, int(dst), int(src), int(v0), float(dt)))
+
+    def maccormack(self, dst: int, q: int, qhat: int, qtilde: int, v0: int, dt: float):
+        """Queue dst = clamp(qhat + (q - qtilde) / 2) to the forward sample's values of q."""
+        self._c(self.lib.sg_maccormack(self.h, int(dst), int(q), int(qhat), int(qtilde), int(v0), float(dt)))
 
     def set_max_fuse(self, max_ops: int):
         self._c(self.lib.sg_set_max_fuse(self.h, int(max_ops)))

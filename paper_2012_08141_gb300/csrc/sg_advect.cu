@@ -1,0 +1,214 @@
+// sg_advect.cu -- MacCormack advection with RK3 path integration over the
+// sparse grid (AsyncTaichi Sec. 8.2): semi-Lagrangian advection of up to
+// three channels per launch sharing one backtrace, and the backward advection
+// fused with the MacCormack correction (the intermediate q~ kept in registers
+// unless a later op reads it).
+//
+// Collocated grid: voxel (i,j,k) sits at (i+0.5, j+0.5, k+0.5) in cell units;
+// velocities are in domain units per time, h = dt * N cells per unit
+// velocity.  A sample between cells is trilinear over the 8 surrounding cell
+// centres; each value is read from its leaf found through the list entry's
+// 27-neighbour table (a null or out-of-domain neighbour is the zero leaf, and
+// a stored value at an inactive voxel is 0, so every read is unconditional),
+// or through the root when the sample lies more than a leaf away.
+// Backtrace: Ralston's RK3, x_back = x - h (2 k1 + 3 k2 + 4 k3) / 9 with
+// k1 = u(x), k2 = u(x - h/2 k1), k3 = u(x - 3h/4 k2).  Correction: q' =
+// q^ + (q - q~) / 2 clamped to the 8 values of q the forward sample uses.
+#include "sg_common.cuh"
+
+namespace sg {
+
+namespace {
+
+constexpr int kMaxAdvectChannels = 3;
+
+struct AdvectArgs {
+    int C;                            // channels
+    int dst[kMaxAdvectChannels];      // outputs
+    int src[kMaxAdvectChannels];      // advect: sampled field; mac: q
+    int qhat[kMaxAdvectChannels];     // mac: q^
+    int qtil[kMaxAdvectChannels];     // mac: q~ (fused: its output, -1 = not stored)
+    int v0;                           // velocity fields v0 .. v0+2
+    float h;                          // dt * N (the forward step)
+};
+
+// Slot of the leaf holding cell (ci, cj, ck), relative to the list entry's
+// leaf (bi, bj, bk): through the neighbour table within one leaf, else the root.
+template <int L>
+__device__ __forceinline__ int leaf_slot(const DevGrid &g, const int32_t *nb, int bi, int bj, int bk, int ci, int cj,
+                                         int ck)
+{
+    constexpr int LG2 = (L == 8) ? 3 : 2;
+    const int di = (ci >> LG2) - bi, dj = (cj >> LG2) - bj, dk = (ck >> LG2) - bk;
+    if ((unsigned)(di + 1) <= 2u && (unsigned)(dj + 1) <= 2u && (unsigned)(dk + 1) <= 2u)
+        return __ldg(nb + (di + 1) * 9 + (dj + 1) * 3 + (dk + 1));
+    if ((unsigned)ci >= (unsigned)g.N || (unsigned)cj >= (unsigned)g.N || (unsigned)ck >= (unsigned)g.N)
+        return (int)g.cap;  // out of the domain: the zero leaf
+    const int s = __ldg(g.root + ((long long)(ci >> LG2) * g.R + (cj >> LG2)) * g.R + (ck >> LG2));
+    return s < 0 ? (int)g.cap : s;
+}
+
+// The 8 corners of a sample at p (cell units): their value offsets within a
+// field and trilinear weights.
+template <int L>
+struct Corners {
+    long long off[8];
+    float w[8];
+};
+
+template <int L>
+__device__ __forceinline__ void corners(const DevGrid &g, const int32_t *nb, int bi, int bj, int bk, float px,
+                                        float py, float pz, Corners<L> &cr)
+{
+    constexpr int LG2 = (L == 8) ? 3 : 2;
+    const float X = px - 0.5f, Y = py - 0.5f, Z = pz - 0.5f;
+    const float fx0 = floorf(X), fy0 = floorf(Y), fz0 = floorf(Z);
+    const int i0 = (int)fx0, j0 = (int)fy0, k0 = (int)fz0;
+    const float fx = X - fx0, fy = Y - fy0, fz = Z - fz0;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const int a = c >> 2, b = (c >> 1) & 1, d = c & 1;
+        const int ci = i0 + a, cj = j0 + b, ck = k0 + d;
+        const int s = leaf_slot<L>(g, nb, bi, bj, bk, ci, cj, ck);
+        cr.off[c] = ((long long)s << (3 * LG2)) + (((ci & (L - 1)) << LG2) + (cj & (L - 1))) * L + (ck & (L - 1));
+        cr.w[c] = (a ? fx : 1.f - fx) * (b ? fy : 1.f - fy) * (d ? fz : 1.f - fz);
+    }
+}
+
+template <int L>
+__device__ __forceinline__ float sample(const float *__restrict__ f, const Corners<L> &cr)
+{
+    float s = 0.f;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) s = fmaf(cr.w[c], __ldg(f + cr.off[c]), s);
+    return s;
+}
+
+template <int L>
+__device__ __forceinline__ void velocity(const DevGrid &g, const int32_t *nb, int bi, int bj, int bk, int v0, float px,
+                                         float py, float pz, float (&u)[3])
+{
+    Corners<L> cr;
+    corners<L>(g, nb, bi, bj, bk, px, py, pz, cr);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) u[a] = sample<L>(g.field[v0 + a], cr);
+}
+
+// RK3 backtrace of cell centre x over h; returns the corners of the sample.
+template <int L>
+__device__ __forceinline__ void backtrace(const DevGrid &g, const int32_t *nb, int bi, int bj, int bk, int v0, float h,
+                                          const float (&x)[3], Corners<L> &cr)
+{
+    float k1[3], k2[3], k3[3];
+    velocity<L>(g, nb, bi, bj, bk, v0, x[0], x[1], x[2], k1);
+    velocity<L>(g, nb, bi, bj, bk, v0, x[0] - 0.5f * h * k1[0], x[1] - 0.5f * h * k1[1], x[2] - 0.5f * h * k1[2], k2);
+    velocity<L>(g, nb, bi, bj, bk, v0, x[0] - 0.75f * h * k2[0], x[1] - 0.75f * h * k2[1], x[2] - 0.75f * h * k2[2],
+                k3);
+    const float c = h / 9.f;
+    corners<L>(g, nb, bi, bj, bk, x[0] - c * (2.f * k1[0] + 3.f * k2[0] + 4.f * k3[0]),
+               x[1] - c * (2.f * k1[1] + 3.f * k2[1] + 4.f * k3[1]), x[2] - c * (2.f * k1[2] + 3.f * k2[2] + 4.f * k3[2]),
+               cr);
+}
+
+// MODE 0: advect (dst = src at the backtrace over h);
+// MODE 1: backward advect of q^ over -h fused with the correction;
+// MODE 2: correction alone (q~ read from its field).
+template <int L, int C, int MODE>
+__global__ void __launch_bounds__(256) k_advect(DevGrid g, AdvectArgs A)
+{
+    constexpr int V = L * L * L, LG2 = (L == 8) ? 3 : 2;
+    const long long n = g.ctrl->list_n;
+    const int R = g.R;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n * V;
+         q += (long long)gridDim.x * blockDim.x) {
+        const long long e = q >> (3 * LG2);
+        const int l = (int)(q & (V - 1));
+        const int slot = g.list_slot[e];
+        const long long idx = ((long long)slot << (3 * LG2)) + l;
+        const bool act = (g.mask[(long long)slot * g.W + (l >> 5)] >> (l & 31)) & 1u;
+        if (!act) {  // inactive voxels keep 0
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                g.field[A.dst[c]][idx] = 0.f;
+                if (MODE == 1 && A.qtil[c] >= 0) g.field[A.qtil[c]][idx] = 0.f;
+            }
+            continue;
+        }
+        const int b = g.list_b[e];
+        const int bi = b / (R * R), bj = (b / R) % R, bk = b % R;
+        const int32_t *nb = g.nbr + e * 27;
+        const float x[3] = {(float)((bi << LG2) + (l >> (2 * LG2))) + 0.5f,
+                            (float)((bj << LG2) + ((l >> LG2) & (L - 1))) + 0.5f,
+                            (float)((bk << LG2) + (l & (L - 1))) + 0.5f};
+        Corners<L> fw;
+        backtrace<L>(g, nb, bi, bj, bk, A.v0, A.h, x, fw);
+        if (MODE == 0) {
+#pragma unroll
+            for (int c = 0; c < C; ++c) g.field[A.dst[c]][idx] = sample<L>(g.field[A.src[c]], fw);
+            continue;
+        }
+        float qt[C];
+        if (MODE == 1) {
+            Corners<L> bw;
+            backtrace<L>(g, nb, bi, bj, bk, A.v0, -A.h, x, bw);
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                qt[c] = sample<L>(g.field[A.qhat[c]], bw);
+                if (A.qtil[c] >= 0) g.field[A.qtil[c]][idx] = qt[c];
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < C; ++c) qt[c] = g.field[A.qtil[c]][idx];
+        }
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            const float *qf = g.field[A.src[c]];
+            float lo = __ldg(qf + fw.off[0]), hi = lo;
+#pragma unroll
+            for (int k = 1; k < 8; ++k) {
+                const float v = __ldg(qf + fw.off[k]);
+                lo = fminf(lo, v);
+                hi = fmaxf(hi, v);
+            }
+            const float r = g.field[A.qhat[c]][idx] + 0.5f * (qf[idx] - qt[c]);
+            g.field[A.dst[c]][idx] = fminf(fmaxf(r, lo), hi);
+        }
+    }
+}
+
+template <int L, int MODE>
+void launch_L(const DevGrid &g, cudaStream_t s, const AdvectArgs &a, int ctas)
+{
+    if (a.C == 1) k_advect<L, 1, MODE><<<ctas, 256, 0, s>>>(g, a);
+    else if (a.C == 2) k_advect<L, 2, MODE><<<ctas, 256, 0, s>>>(g, a);
+    else k_advect<L, 3, MODE><<<ctas, 256, 0, s>>>(g, a);
+}
+
+}  // namespace
+
+void launch_advect_group(const DevGrid &g, cudaStream_t s, int mode, int C, const int *dst, const int *src,
+                         const int *qhat, const int *qtil, int v0, float h, const LaunchCfg &lc)
+{
+    AdvectArgs a{};
+    a.C = C;
+    for (int c = 0; c < C; ++c) {
+        a.dst[c] = dst[c];
+        a.src[c] = src[c];
+        a.qhat[c] = qhat ? qhat[c] : -1;
+        a.qtil[c] = qtil ? qtil[c] : -1;
+    }
+    a.v0 = v0;
+    a.h = h;
+    const int ctas = lc.num_sms * 8;
+    if (g.L == 8) {
+        if (mode == 0) launch_L<8, 0>(g, s, a, ctas);
+        else if (mode == 1) launch_L<8, 1>(g, s, a, ctas);
+        else launch_L<8, 2>(g, s, a, ctas);
+    } else {
+        if (mode == 0) launch_L<4, 0>(g, s, a, ctas);
+        else if (mode == 1) launch_L<4, 1>(g, s, a, ctas);
+        else launch_L<4, 2>(g, s, a, ctas);
+    }
+}
+
+}  // namespace sg

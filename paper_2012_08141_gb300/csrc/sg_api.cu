@@ -53,7 +53,7 @@ int fail(int code, const char *fmt, ...)
 }
 
 enum OpKind { OP_ACT_SHELL, OP_ACT_COORDS, OP_DEACT, OP_LISTGEN, OP_STENCIL, OP_SUM, OP_P2G, OP_GRID_UPDATE, OP_G2P, OP_TEST_WAIT,
-              OP_FILL, OP_G2P2G, OP_EW };
+              OP_FILL, OP_G2P2G, OP_EW, OP_ADVECT, OP_MAC };
 
 struct Op {
     OpKind kind;
@@ -86,7 +86,7 @@ struct sg_grid {
     std::vector<Op> queue;
     // host-side state versions (Sec. 4): mask and list of the grid's structure
     unsigned long long mask_ver = 1, list_ver = 0;
-    std::set<std::tuple<long long, long long, int>> applied_shells;
+    std::set<std::tuple<long long, long long, int, int>> applied_shells;
     // restrictions applied since the last deactivation: (fine grid, its mask version)
     std::set<std::pair<const sg_grid *, unsigned long long>> applied_restrict;
     unsigned long long lg_calls = 0;
@@ -190,6 +190,9 @@ bool read_later(const sg_grid *g, size_t from, int f)
         const Op &o = g->queue[i];
         if ((o.kind == OP_STENCIL && o.op != SG_CLEAR && o.src == f) || (o.kind == OP_SUM && o.src == f)) return true;
         if (o.kind == OP_EW && (o.src == f || o.i0 == f)) return true;
+        if ((o.kind == OP_ADVECT || o.kind == OP_MAC) &&
+            (o.src == f || (f >= o.i0 && f < o.i0 + 3) || (o.kind == OP_MAC && (o.i1 == f || o.i2 == f))))
+            return true;
         if (o.kind == OP_EW && o.dst == f) return false;  // fully overwritten
         if (o.kind == OP_P2G || o.kind == OP_GRID_UPDATE || o.kind == OP_G2P) return true;  // conservative
         if (o.kind == OP_STENCIL && o.dst == f) return false;  // fully overwritten
@@ -363,6 +366,154 @@ int run_ew_group(sg_grid *g, size_t &i)
     return after_launch(g, "element-wise");
 }
 
+// ---- MacCormack advection: a run of OP_ADVECT / OP_MAC ops ----------------
+// Read and write sets of an advection op (physical fields).
+static void advect_sets(const Op &o, std::vector<int> &r, std::vector<int> &w)
+{
+    r = {o.src, o.i0, o.i0 + 1, o.i0 + 2};
+    if (o.kind == OP_MAC) {
+        r.push_back(o.i1);
+        r.push_back(o.i2);
+    }
+    w = {o.dst};
+}
+
+static bool intersects(const std::vector<int> &a, const std::vector<int> &b)
+{
+    for (int x : a)
+        for (int y : b)
+            if (x == y) return true;
+    return false;
+}
+
+// The run queue[i .. end) of advection ops as fused launches (Sec. 6.4,
+// Supp. Sec. 2).  The ops' dependencies come from their read / write sets
+// (the state-flow edges between them); ops whose dependencies are all issued
+// are ready and mutually independent.  Ready backward advections whose output
+// q~ a correction reads at the voxel (an element-wise connection) are fused
+// with that correction, q~ then stored only if a later op reads it (Sec. 6.5);
+// other ready ops with the same velocity and step are grouped, up to three
+// channels per launch.  Without fusion each op is a launch, in queue order.
+int run_advect_run(sg_grid *g, size_t &i)
+{
+    int rc;
+    size_t end = i;
+    while (end < g->queue.size() && (g->queue[end].kind == OP_ADVECT || g->queue[end].kind == OP_MAC)) ++end;
+    const int n = (int)(end - i);
+    const bool fuse = (g->opts & SG_OPT_FUSE) && (g->opts & SG_OPT_LGR);
+    const bool dse = (g->opts & SG_OPT_DSE) != 0;
+    std::vector<std::vector<int>> R(n), W(n), deps(n);
+    for (int a = 0; a < n; ++a) advect_sets(g->queue[i + a], R[a], W[a]);
+    for (int b = 0; b < n; ++b)
+        for (int a = 0; a < b; ++a)
+            if (intersects(W[a], R[b]) || intersects(W[a], W[b]) || intersects(R[a], W[b])) deps[b].push_back(a);
+    std::vector<char> done(n, 0);
+    auto issued = [&](int b, int except) {
+        for (int a : deps[b])
+            if (!done[a] && a != except) return false;
+        return true;
+    };
+    auto launch = [&](int mode, const std::vector<int> &ops, const std::vector<int> &macs) -> int {
+        int r2;
+        if ((r2 = ensure_list(g))) return r2;
+        const Op &f = g->queue[i + ops[0]];
+        int dst[3], src[3], qh[3], qt[3];
+        const int C = (int)ops.size();
+        for (int c = 0; c < C; ++c) {
+            const Op &o = g->queue[i + ops[c]];
+            if (mode == 0) {
+                dst[c] = o.dst;
+                src[c] = o.src;
+                qh[c] = qt[c] = -1;
+            } else if (mode == 2) {
+                dst[c] = o.dst;
+                src[c] = o.src;
+                qh[c] = o.i1;
+                qt[c] = o.i2;
+            } else {  // ops[c]: the backward advection, macs[c]: its correction
+                const Op &m = g->queue[i + macs[c]];
+                dst[c] = m.dst;
+                src[c] = m.src;
+                qh[c] = m.i1;
+                const bool live = !(dse && o.dst_scratch && !read_later(g, end, o.dst));
+                bool read_in_run = false;
+                for (int b = 0; b < n; ++b)
+                    if (!done[b] && b != ops[c] && b != macs[c] && std::count(R[b].begin(), R[b].end(), o.dst))
+                        read_in_run = true;
+                qt[c] = (live || read_in_run) ? o.dst : -1;
+                if (qt[c] < 0) g->stats.stores_removed++;
+            }
+        }
+        const float h = (mode == 1 ? g->queue[i + macs[0]].f0 : f.f0) * (float)g->dev.N;
+        if (!g->dry) launch_advect_group(g->dev, g->stream, mode, C, dst, src, qh, qt, f.i0, h, g->lc);
+        g->stats.ops_fused += (int64_t)(mode == 1 ? 2 * C : C) - 1;
+        for (int c : ops) done[c] = 1;
+        for (int c : macs) done[c] = 1;
+        return after_launch(g, "advection");
+    };
+    if (!fuse) {
+        for (int a = 0; a < n; ++a) {
+            const int mode = g->queue[i + a].kind == OP_ADVECT ? 0 : 2;
+            rc = launch(mode, std::vector<int>{a}, std::vector<int>{});
+            if (rc) return rc;
+        }
+        i = end;
+        return SG_OK;
+    }
+    int left = n;
+    while (left > 0) {
+        std::vector<int> ops, macs;
+        // (1) ready backward advections fused with the corrections that read their output
+        for (int a = 0; a < n && ops.size() < 3; ++a) {
+            const Op &o = g->queue[i + a];
+            if (done[a] || o.kind != OP_ADVECT || o.f0 >= 0.f || !issued(a, -1)) continue;
+            for (int m = a + 1; m < n; ++m) {
+                const Op &c = g->queue[i + m];
+                if (done[m] || c.kind != OP_MAC || c.i2 != o.dst || c.i0 != o.i0 || c.f0 != -o.f0 || !issued(m, a))
+                    continue;
+                if (!ops.empty()) {
+                    const Op &o0 = g->queue[i + ops[0]];
+                    if (o0.i0 != o.i0 || o0.f0 != o.f0) continue;
+                }
+                ops.push_back(a);
+                macs.push_back(m);
+                break;
+            }
+        }
+        int mode = 1;
+        if (ops.empty()) {  // (2) ready advections with the same velocity and step
+            mode = 0;
+            for (int a = 0; a < n && ops.size() < 3; ++a) {
+                const Op &o = g->queue[i + a];
+                if (done[a] || o.kind != OP_ADVECT || !issued(a, -1)) continue;
+                if (!ops.empty()) {
+                    const Op &o0 = g->queue[i + ops[0]];
+                    if (o0.i0 != o.i0 || o0.f0 != o.f0) continue;
+                }
+                ops.push_back(a);
+            }
+        }
+        if (ops.empty()) {  // (3) ready corrections
+            mode = 2;
+            for (int a = 0; a < n && ops.size() < 3; ++a) {
+                const Op &o = g->queue[i + a];
+                if (done[a] || o.kind != OP_MAC || !issued(a, -1)) continue;
+                if (!ops.empty()) {
+                    const Op &o0 = g->queue[i + ops[0]];
+                    if (o0.i0 != o.i0 || o0.f0 != o.f0) continue;
+                }
+                ops.push_back(a);
+            }
+        }
+        if (ops.empty()) return fail(SG_ERR_INVALID, "advection run has no ready op");  // cannot happen: deps are acyclic
+        rc = launch(mode, ops, macs);
+        if (rc) return rc;
+        left -= (int)(ops.size() + macs.size());
+    }
+    i = end;
+    return SG_OK;
+}
+
 // Dead-store elimination of reductions: within one flush nothing on the
 // device reads a result slot, so a reduction whose slot a later reduction in
 // the queue overwrites is dead (the autodiff microbenchmark's pattern).
@@ -417,11 +568,14 @@ int do_flush(sg_grid *g)
         const Op &o = g->queue[i];
         switch (o.kind) {
             case OP_ACT_SHELL: {
-                const auto sig = std::make_tuple(o.lo2, o.hi2, o.strict);
+                const auto sig = std::make_tuple(o.lo2, o.hi2, o.strict, o.op);
                 if ((g->opts & SG_OPT_AD) && g->applied_shells.count(sig)) {
                     g->stats.act_demoted++;
                 } else {
-                    if (!g->dry) launch_activate_shell(g->dev, g->stream, o.lo2, o.hi2, o.strict);
+                    if (!g->dry) {
+                        if (o.op) launch_activate_tube(g->dev, g->stream, o.lo2, o.hi2);
+                        else launch_activate_shell(g->dev, g->stream, o.lo2, o.hi2, o.strict);
+                    }
                     g->applied_shells.insert(sig);
                     g->mask_ver++;
                     g->stats.act_launched++;
@@ -473,6 +627,10 @@ int do_flush(sg_grid *g)
                 break;
             case OP_EW:
                 rc = run_ew_group(g, i);
+                break;
+            case OP_ADVECT:
+            case OP_MAC:
+                rc = run_advect_run(g, i);
                 break;
             case OP_P2G:
                 if (!(rc = ensure_p2g_scratch(g, o.n))) {
@@ -769,6 +927,53 @@ int sg_launch_ew(sg_grid *g, int32_t dst, int32_t a, int32_t b, float alpha, flo
     o.f1 = beta;
     o.coef = gamma;
     o.f2 = delta;
+    return push(g, o);
+}
+
+int sg_activate_tube(sg_grid *g, int64_t lo2, int64_t hi2)
+{
+    if (!g || lo2 < 0 || hi2 < lo2) return fail(SG_ERR_INVALID, "bad tube bounds");
+    Op o{OP_ACT_SHELL};
+    o.lo2 = lo2;
+    o.hi2 = hi2;
+    o.op = 1;  // tube
+    return push(g, o);
+}
+
+// Velocity fields v0, v0+1, v0+2 valid and stored consecutively.
+static bool valid_velocity(const sg_grid *g, int v0)
+{
+    return valid_field(g, v0) && valid_field(g, v0 + 2) && g->phys[v0 + 1] == g->phys[v0] + 1 &&
+           g->phys[v0 + 2] == g->phys[v0] + 2;
+}
+
+int sg_advect(sg_grid *g, int32_t dst, int32_t src, int32_t v0, float dt)
+{
+    if (!g || !valid_field(g, dst) || !valid_field(g, src) || !valid_velocity(g, v0) || dst == src ||
+        (dst >= v0 && dst <= v0 + 2))
+        return fail(SG_ERR_INVALID, "bad advection fields dst=%d src=%d vel=%d", dst, src, v0);
+    Op o{OP_ADVECT};
+    o.dst = g->phys[dst];
+    o.src = g->phys[src];
+    o.i0 = g->phys[v0];
+    o.f0 = dt;
+    o.dst_scratch = (g->desc.scratch_mask >> dst) & 1u;
+    return push(g, o);
+}
+
+int sg_maccormack(sg_grid *g, int32_t dst, int32_t q, int32_t qhat, int32_t qtilde, int32_t v0, float dt)
+{
+    if (!g || !valid_field(g, dst) || !valid_field(g, q) || !valid_field(g, qhat) || !valid_field(g, qtilde) ||
+        !valid_velocity(g, v0) || dst == q || dst == qhat || dst == qtilde || (dst >= v0 && dst <= v0 + 2))
+        return fail(SG_ERR_INVALID, "bad MacCormack fields");
+    Op o{OP_MAC};
+    o.dst = g->phys[dst];
+    o.src = g->phys[q];
+    o.i0 = g->phys[v0];
+    o.i1 = g->phys[qhat];
+    o.i2 = g->phys[qtilde];
+    o.f0 = dt;
+    o.dst_scratch = (g->desc.scratch_mask >> dst) & 1u;
     return push(g, o);
 }
 

@@ -179,6 +179,15 @@ void launch_grid_update(const DevGrid &g, cudaStream_t s, int f_mass, int f_mom0
 void launch_g2p(const DevGrid &g, cudaStream_t s, float *x, float *v, float *C, long long n, float dt, int f_mom0,
                 int binned, const LaunchCfg &lc);
 
+// ---- MacCormack / RK3 advection (sg_advect.cu) ----
+// mode 0: dst[c] = src[c] at the RK3 backtrace over h = dt * N;
+// mode 1: backward advection of qhat[c] over -h fused with the correction
+//         dst[c] = clamp(qhat + (src - q~) / 2), q~ stored to qtil[c] if >= 0;
+// mode 2: the correction with q~ read from qtil[c].  C <= 3 channels.
+void launch_advect_group(const DevGrid &g, cudaStream_t s, int mode, int C, const int *dst, const int *src,
+                         const int *qhat, const int *qtil, int v0, float h, const LaunchCfg &lc);
+void launch_activate_tube(const DevGrid &g, cudaStream_t s, long long lo2, long long hi2);
+
 // ---- fused element-wise struct-fors (sg_elementwise.cu) ----
 constexpr int kMaxEwOps = 16;   // ops (and at most one reduction) per fused launch
 constexpr int kMaxEwSlots = 8;  // distinct fields per fused launch

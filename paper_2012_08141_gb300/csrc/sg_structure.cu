@@ -26,7 +26,9 @@ __device__ __forceinline__ void axis_range(int i0, int L, int N, long long &mn, 
     mx += hi * hi;
 }
 
-__global__ void __launch_bounds__(256) k_activate_shell(DevGrid g, long long lo2, long long hi2, int strict)
+// tube: the predicate ignores the k axis (a cylinder along k through the
+// domain centre) instead of using all three.
+__global__ void __launch_bounds__(256) k_activate_shell(DevGrid g, long long lo2, long long hi2, int strict, int tube)
 {
     const int lane = lane_id();
     const long long nr = (long long)g.R * g.R * g.R;
@@ -37,7 +39,7 @@ __global__ void __launch_bounds__(256) k_activate_shell(DevGrid g, long long lo2
     long long dmin = 0, dmax = 0;
     axis_range(bi * L, L, N, dmin, dmax);
     axis_range(bj * L, L, N, dmin, dmax);
-    axis_range(bk * L, L, N, dmin, dmax);
+    if (!tube) axis_range(bk * L, L, N, dmin, dmax);
     const bool lo_possible = strict ? (dmax > lo2) : (dmax >= lo2);
     if (!lo_possible || dmin >= hi2) return;
 
@@ -48,7 +50,7 @@ __global__ void __launch_bounds__(256) k_activate_shell(DevGrid g, long long lo2
         const long long a = 2LL * (bi * L + li) + 1 - N;
         const long long c = 2LL * (bj * L + lj) + 1 - N;
         const long long d = 2LL * (bk * L + lk) + 1 - N;
-        const long long D = a * a + c * c + d * d;
+        const long long D = a * a + c * c + (tube ? 0 : d * d);
         const bool on = (strict ? (lo2 < D) : (lo2 <= D)) && (D < hi2);
         const unsigned word = __ballot_sync(kFull, on);
         if (lane == w) bits = word;
@@ -103,7 +105,15 @@ void launch_activate_shell(const DevGrid &g, cudaStream_t s, long long lo2, long
     const long long nr = (long long)g.R * g.R * g.R;
     const int warps = 8;
     const long long blocks = (nr + warps - 1) / warps;
-    k_activate_shell<<<(unsigned)blocks, warps * 32, 0, s>>>(g, lo2, hi2, strict);
+    k_activate_shell<<<(unsigned)blocks, warps * 32, 0, s>>>(g, lo2, hi2, strict, 0);
+}
+
+void launch_activate_tube(const DevGrid &g, cudaStream_t s, long long lo2, long long hi2)
+{
+    const long long nr = (long long)g.R * g.R * g.R;
+    const int warps = 8;
+    const long long blocks = (nr + warps - 1) / warps;
+    k_activate_shell<<<(unsigned)blocks, warps * 32, 0, s>>>(g, lo2, hi2, 0, 1);
 }
 
 // ---------------------------------------------------------------------------

@@ -381,3 +381,55 @@ def test_micro_not_fusible_across_a_stencil():
         g.ew(0, 2, alpha=1.0, delta=1.0)
     d = _launches(_micro(), body)
     assert d["launches"] == 3 and d["listgen_run"] == 0
+
+
+def test_advection_channel_fusion_launches():
+    """Three channels written channel by channel (forward advect, backward
+    advect, correction each): the queue reorders by field dependencies into
+    one forward launch for all channels and one fused backward+correction
+    launch (q~ scratch, not stored) -- against 9 launches without fusion and
+    27 eager (clear-list + list + kernel each)."""
+    def step(g):
+        for c in range(3):
+            q, qh, qt, qn = 3 + 4 * c, 4 + 4 * c, 5 + 4 * c, 6 + 4 * c
+            g.advect(qh, q, 0, 1e-3)
+            g.advect(qt, qh, 0, -1e-3)
+            g.maccormack(qn, q, qh, qt, 0, 1e-3)
+    scratch = sum(1 << (5 + 4 * c) for c in range(3))
+    counts = {}
+    for name, opts in (("all", sg.SG_OPT_ALL), ("nofuse", sg.SG_OPT_ALL & ~sg.SG_OPT_FUSE), ("eager", 0)):
+        g = sg.Grid(64, 3, 15, max_leaves=1024, scratch_mask=scratch, dry_run=True)
+        g.set_opts(opts)
+        g.activate_tube(4 * 64 * 64 * 0.32 ** 2, 4 * 64 * 64 * 0.45 ** 2)
+        g.list_gen()
+        g.flush()
+        s0 = g.stats()
+        step(g)
+        g.flush()
+        s1 = g.stats()
+        counts[name] = {k: s1[k] - s0[k] for k in s1}
+    assert counts["all"]["launches"] == 2 and counts["all"]["stores_removed"] == 3
+    assert counts["all"]["ops_fused"] == 7
+    assert counts["nofuse"]["launches"] == 9
+    assert counts["eager"]["launches"] == 27
+
+
+def test_advection_dependencies_respected():
+    """A correction whose output a later advection reads is issued before it;
+    a second forward advection of the corrected field waits for the first
+    channel's correction (no fusion across that dependency)."""
+    g = sg.Grid(64, 3, 8, max_leaves=1024, dry_run=True)
+    g.activate_tube(1000, 3000)
+    g.list_gen()
+    g.flush()
+    s0 = g.stats()["launches"]
+    g.advect(4, 3, 0, 1e-3)          # a: q^ = A(q)
+    g.advect(5, 4, 0, -1e-3)         # b: q~ = A(q^, -dt)
+    g.maccormack(6, 3, 4, 5, 0, 1e-3)  # m: q' from q, q^, q~
+    g.advect(7, 6, 0, 1e-3)          # c: reads q' -> after m
+    g.flush()
+    assert g.stats()["launches"] - s0 == 3      # a | b+m fused | c
+    lib = sg.load_library()
+    assert lib.sg_advect(g.h, 3, 3, 0, 1e-3) == sg.SG_ERR_INVALID            # dst == src
+    assert lib.sg_advect(g.h, 1, 3, 0, 1e-3) == sg.SG_ERR_INVALID            # dst is a velocity field
+    assert lib.sg_maccormack(g.h, 4, 3, 4, 5, 0, 1e-3) == sg.SG_ERR_INVALID  # dst == qhat

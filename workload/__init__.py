@@ -166,6 +166,48 @@ def cube_particles(seed: int, n: int, N: int, L: int, pad_cells: float = 3.0,
 
 
 # ---------------------------------------------------------------------------
+# Advection over a tube (MacCormack workload): bounds and initial fields
+# ---------------------------------------------------------------------------
+
+
+@dataclass
+class TubeSpec:
+    N: int
+    L: int
+    lo2: int          # (2i+1-N)^2 + (2j+1-N)^2 >= lo2
+    hi2: int          # ... < hi2
+    omega: float      # swirl rate about the tube axis (radians per unit time)
+    axial: float      # velocity along k (domain units per unit time)
+    dt: float
+
+
+def tube(N: int = 256, L: int = 8, r_in: float = 0.32, r_out: float = 0.45, omega: float = 2.0,
+         axial: float = 0.3) -> TubeSpec:
+    """The tube inner radius r_in <= r < r_out (domain units) around the k axis
+    through the domain centre: integer bounds on D = 4 N^2 r^2 (ceil, so that
+    D >= ceil(4 N^2 r_in^2) <=> r >= r_in for integer D), a solid-body swirl
+    plus an axial drift, and dt = 1 / N (under a cell per step)."""
+    lo2 = math.ceil(4.0 * N * N * r_in * r_in)
+    hi2 = math.ceil(4.0 * N * N * r_out * r_out)
+    return TubeSpec(N, L, int(lo2), int(hi2), omega, axial, 1.0 / N)
+
+
+def tube_fields(spec: TubeSpec, cells: np.ndarray):
+    """Initial velocity (3 arrays) and three scalar channels at cell centres
+    `cells` (..., 3) in cell units: the swirl u = omega (-(y - 1/2), x - 1/2,
+    0) + (0, 0, axial) in domain units, and smooth channels (temperature,
+    colour, density) as products of sines; float32."""
+    x = (cells[..., 0] + 0.5) / spec.N
+    y = (cells[..., 1] + 0.5) / spec.N
+    z = (cells[..., 2] + 0.5) / spec.N
+    vel = [(-spec.omega * (y - 0.5)), spec.omega * (x - 0.5), np.full_like(x, spec.axial)]
+    ch = [0.5 + 0.5 * np.sin(2 * np.pi * x) * np.cos(2 * np.pi * y),
+          0.5 + 0.4 * np.sin(4 * np.pi * z + 1.0) * np.sin(2 * np.pi * (x + y)),
+          np.exp(-((x - 0.5) ** 2 + (y - 0.88) ** 2 + (z - 0.5) ** 2) / 0.01)]
+    return [v.astype(np.float32) for v in vel], [c.astype(np.float32) for c in ch]
+
+
+# ---------------------------------------------------------------------------
 # Batched and serving size mixes
 # ---------------------------------------------------------------------------
 
