@@ -18,6 +18,8 @@ it.  Further legs (skipped with --only fused or on more than one rank):
             with and without activation demotion, and eager;
   micro     the paper's microbenchmarks (chain_copy, increments, fill_array,
             sparse_saxpy, autodiff, stencil_reduction) on the 512^3 band;
+  advection MacCormack/RK3 advection of 3 channels over the 256^3 tube, all
+            passes against no fusion and eager;
   serving   Poisson arrivals of band jobs (1e4..1e7 voxels, 10..200 steps)
             into the continuous-batching server: p50/p99 job latency;
   band1024  the 1024^3 band |dist - 400| < 8, far larger than L2.
@@ -49,7 +51,8 @@ sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
 
-from workload import ShellSpec, band512, batched_mix, leaf_values, serving_arrivals, spheres_particles  # noqa: E402
+from workload import (ShellSpec, band512, batched_mix, leaf_values, serving_arrivals, spheres_particles,  # noqa: E402
+                      tube, tube_fields)
 
 METRIC = "active voxel-steps/s"
 BYTES_PER_LEAF_FUSED = 2 * 2048 + 27 * 4 + 64 + 4  # x read, x' written, nbr row, mask, list entry
@@ -430,6 +433,54 @@ def bench_micro(torch, sg, steps, warmup, flush_buf, stream):
     return out
 
 
+def bench_advection(torch, sg, steps, warmup, flush_buf, stream):
+    """MacCormack / RK3 advection of three channels over the 256^3 tube
+    (inner radius 0.32, outer 0.45; Sec. 8.2, Supp. Sec. 4.2), written channel
+    by channel (forward advection, backward advection, correction, swap):
+    all passes, without task fusion, and eager."""
+    spec = tube(256, 8)
+    out = {"workload": "MacCormack/RK3 advection of 3 channels, 256^3 tube r in [0.32, 0.45), 8^3 leaves",
+           "l2": "flushed before every timed step (512 MB write)"}
+    scratch = sum(1 << (5 + 4 * c) for c in range(3))
+    for name, opts in (("all_passes", sg.SG_OPT_ALL), ("no_fusion", sg.SG_OPT_ALL & ~sg.SG_OPT_FUSE),
+                       ("eager", sg.SG_OPT_EAGER)):
+        g = sg.Grid(256, 3, 15, max_leaves=32768, scratch_mask=scratch)
+        g.set_opts(opts)
+        g.activate_tube(spec.lo2, spec.hi2)
+        b, _ = g.read_structure()
+        R = 256 // 8
+        bi, bj, bk = b // (R * R), (b // R) % R, b % R
+        l = np.arange(512)
+        cells = np.stack([bi[:, None] * 8 + l[None, :] // 64, bj[:, None] * 8 + (l[None, :] // 8) % 8,
+                          bk[:, None] * 8 + l[None, :] % 8], -1).astype(np.float64)
+        vel, ch = tube_fields(spec, cells)
+        for a in range(3):
+            g.write_field(a, vel[a])
+        for c in range(3):
+            g.write_field(3 + 4 * c, ch[c])
+        n_active = g.num_active()
+
+        def step():
+            for c in range(3):
+                q, qh, qt, qn = 3 + 4 * c, 4 + 4 * c, 5 + 4 * c, 6 + 4 * c
+                g.advect(qh, q, 0, spec.dt)
+                g.advect(qt, qh, 0, -spec.dt)
+                g.maccormack(qn, q, qh, qt, 0, spec.dt)
+                g.swap(q, qn)
+            g.flush()
+
+        ms, nl = time_steps(torch, step, steps, warmup, flush_buf, stream, lambda: g.stats()["launches"])
+        t = sum(ms) / 1e3
+        out[name] = {"ms_per_step": t * 1e3 / steps, "launches_per_step": nl / steps,
+                     "value": 3 * n_active * steps / t, "unit": "channel voxel-steps/s"}
+        out["active_voxels"] = n_active
+        out["leaves"] = len(b)
+        g.close()
+    out["all_over_no_fusion"] = out["no_fusion"]["ms_per_step"] / out["all_passes"]["ms_per_step"]
+    out["all_over_eager"] = out["eager"]["ms_per_step"] / out["all_passes"]["ms_per_step"]
+    return out
+
+
 def bench_serving(torch, sg, rates=(50, 100, 200, 500, 1000, 2000), duration=2.0, cap_s=60.0):
     from paper_2012_08141_gb300.serve import Server
     out = []
@@ -558,6 +609,7 @@ def run_ours(args):
                          ("mpm_apic", lambda: bench_mpm_apic(torch, sg, k, 3, flush_buf, stream)),
                          ("multigrid", lambda: bench_multigrid(torch, sg, k, 3, flush_buf, stream)),
                          ("micro", lambda: bench_micro(torch, sg, k, 3, flush_buf, stream)),
+                         ("advection", lambda: bench_advection(torch, sg, k, 3, flush_buf, stream)),
                          ("serving", lambda: bench_serving(torch, sg))):
             if args.only not in ("all", name):
                 continue
@@ -689,7 +741,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--variant", type=int, default=0, help="stencil kernel family (0 sweep, 1 smem)")
     ap.add_argument("--only", choices=["all", "fused", "band1024", "batched", "particles", "mpm_apic", "multigrid",
-                                       "micro", "serving"],
+                                       "micro", "advection", "serving"],
                     default="all",
                     help="fused: only the fused headline step; a leg name: the headline step and that leg "
                          "(for profiling runs)")

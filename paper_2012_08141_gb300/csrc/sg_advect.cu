@@ -95,12 +95,15 @@ __device__ __forceinline__ void velocity(const DevGrid &g, const int32_t *nb, in
 }
 
 // RK3 backtrace of cell centre x over h; returns the corners of the sample.
+// k1 = u(x) at the cell centre itself is the voxel's stored velocity (the
+// trilinear weights there are 1, 0, ..., 0), read directly at idx.
 template <int L>
 __device__ __forceinline__ void backtrace(const DevGrid &g, const int32_t *nb, int bi, int bj, int bk, int v0, float h,
-                                          const float (&x)[3], Corners<L> &cr)
+                                          const float (&x)[3], long long idx, Corners<L> &cr)
 {
     float k1[3], k2[3], k3[3];
-    velocity<L>(g, nb, bi, bj, bk, v0, x[0], x[1], x[2], k1);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) k1[a] = g.field[v0 + a][idx];
     velocity<L>(g, nb, bi, bj, bk, v0, x[0] - 0.5f * h * k1[0], x[1] - 0.5f * h * k1[1], x[2] - 0.5f * h * k1[2], k2);
     velocity<L>(g, nb, bi, bj, bk, v0, x[0] - 0.75f * h * k2[0], x[1] - 0.75f * h * k2[1], x[2] - 0.75f * h * k2[2],
                 k3);
@@ -141,7 +144,7 @@ __global__ void __launch_bounds__(256) k_advect(DevGrid g, AdvectArgs A)
                             (float)((bj << LG2) + ((l >> LG2) & (L - 1))) + 0.5f,
                             (float)((bk << LG2) + (l & (L - 1))) + 0.5f};
         Corners<L> fw;
-        backtrace<L>(g, nb, bi, bj, bk, A.v0, A.h, x, fw);
+        backtrace<L>(g, nb, bi, bj, bk, A.v0, A.h, x, idx, fw);
         if (MODE == 0) {
 #pragma unroll
             for (int c = 0; c < C; ++c) g.field[A.dst[c]][idx] = sample<L>(g.field[A.src[c]], fw);
@@ -150,7 +153,7 @@ __global__ void __launch_bounds__(256) k_advect(DevGrid g, AdvectArgs A)
         float qt[C];
         if (MODE == 1) {
             Corners<L> bw;
-            backtrace<L>(g, nb, bi, bj, bk, A.v0, -A.h, x, bw);
+            backtrace<L>(g, nb, bi, bj, bk, A.v0, -A.h, x, idx, bw);
 #pragma unroll
             for (int c = 0; c < C; ++c) {
                 qt[c] = sample<L>(g.field[A.qhat[c]], bw);
