@@ -65,13 +65,33 @@ __device__ __forceinline__ void corners(const DevGrid &g, const int32_t *nb, int
     const float fx0 = floorf(X), fy0 = floorf(Y), fz0 = floorf(Z);
     const int i0 = (int)fx0, j0 = (int)fy0, k0 = (int)fz0;
     const float fx = X - fx0, fy = Y - fy0, fz = Z - fz0;
+    // per axis: the leaf offsets (relative to the entry's leaf) and local indices
+    // of the two corner layers
+    const int di0 = (i0 >> LG2) - bi, dj0 = (j0 >> LG2) - bj, dk0 = (k0 >> LG2) - bk;
+    const int di1 = ((i0 + 1) >> LG2) - bi, dj1 = ((j0 + 1) >> LG2) - bj, dk1 = ((k0 + 1) >> LG2) - bk;
+    const int li[2] = {i0 & (L - 1), (i0 + 1) & (L - 1)}, lj[2] = {j0 & (L - 1), (j0 + 1) & (L - 1)},
+              lk[2] = {k0 & (L - 1), (k0 + 1) & (L - 1)};
+    const float wx[2] = {1.f - fx, fx}, wy[2] = {1.f - fy, fy}, wz[2] = {1.f - fz, fz};
+    const bool near = di0 >= -1 && di1 <= 1 && dj0 >= -1 && dj1 <= 1 && dk0 >= -1 && dk1 <= 1;
+    if (near) {  // within the 27-neighbourhood: table lookups only
+        const int ti[2] = {(di0 + 1) * 9, (di1 + 1) * 9}, tj[2] = {(dj0 + 1) * 3, (dj1 + 1) * 3},
+                  tk[2] = {dk0 + 1, dk1 + 1};
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        const int a = c >> 2, b = (c >> 1) & 1, d = c & 1;
-        const int ci = i0 + a, cj = j0 + b, ck = k0 + d;
-        const int s = leaf_slot<L>(g, nb, bi, bj, bk, ci, cj, ck);
-        cr.off[c] = ((long long)s << (3 * LG2)) + (((ci & (L - 1)) << LG2) + (cj & (L - 1))) * L + (ck & (L - 1));
-        cr.w[c] = (a ? fx : 1.f - fx) * (b ? fy : 1.f - fy) * (d ? fz : 1.f - fz);
+        for (int c = 0; c < 8; ++c) {
+            const int a = c >> 2, b = (c >> 1) & 1, d = c & 1;
+            const int slot = __ldg(nb + ti[a] + tj[b] + tk[d]);
+            cr.off[c] = ((long long)slot << (3 * LG2)) + (((li[a] << LG2) + lj[b]) << LG2) + lk[d];
+            cr.w[c] = wx[a] * wy[b] * wz[d];
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const int a = c >> 2, b = (c >> 1) & 1, d = c & 1;
+            const int ci = i0 + a, cj = j0 + b, ck = k0 + d;
+            const int slot = leaf_slot<L>(g, nb, bi, bj, bk, ci, cj, ck);
+            cr.off[c] = ((long long)slot << (3 * LG2)) + (((li[a] << LG2) + lj[b]) << LG2) + lk[d];
+            cr.w[c] = wx[a] * wy[b] * wz[d];
+        }
     }
 }
 
