@@ -192,6 +192,12 @@ int sg_maccormack(sg_grid *g, int32_t dst, int32_t q, int32_t qhat, int32_t qtil
 int sg_launch_ew(sg_grid *g, int32_t dst, int32_t a, int32_t b, float alpha, float beta, float gamma,
                  float delta);
 
+/* Flush the queue automatically once it holds `ops` queued ops (the flush
+ * period of the paper's asynchronous engine, Sec. 7.1; 1 issues every op as
+ * it is queued, as a synchronous engine would; 0, the default, flushes only on
+ * sg_flush and on implicit syncs).  Optimizations apply within a flush. */
+int sg_set_flush_period(sg_grid *g, int32_t ops);
+
 /* Largest number of element-wise ops fused into one launch (>= 1; the
  * role of the paper's async_max_fuse_per_task, Supp. Sec. 2 item 4). */
 int sg_set_max_fuse(sg_grid *g, int32_t max_ops);

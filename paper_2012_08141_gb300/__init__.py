@@ -94,6 +94,7 @@ def load_library(build: bool = True) -> ctypes.CDLL:
         "sg_advect": [P, I32, I32, I32, F],
         "sg_maccormack": [P, I32, I32, I32, I32, I32, F],
         "sg_set_max_fuse": [P, I32],
+        "sg_set_flush_period": [P, I32],
         "sg_prolong": [P, P, I32, I32, F],
         "sg_swap": [P, I32, I32],
         "sg_flush": [P],
@@ -248,6 +249,10 @@ class Grid:
     def maccormack(self, dst: int, q: int, qhat: int, qtilde: int, v0: int, dt: float):
         """Queue dst = clamp(qhat + (q - qtilde) / 2) to the forward sample's values of q."""
         self._c(self.lib.sg_maccormack(self.h, int(dst), int(q), int(qhat), int(qtilde), int(v0), float(dt)))
+
+    def set_flush_period(self, ops: int):
+        """Flush automatically once `ops` ops are queued (0: only on flush / sync)."""
+        self._c(self.lib.sg_set_flush_period(self.h, int(ops)))
 
     def set_max_fuse(self, max_ops: int):
         self._c(self.lib.sg_set_max_fuse(self.h, int(max_ops)))

@@ -92,6 +92,7 @@ struct sg_grid {
     unsigned long long lg_calls = 0;
     unsigned long long rmask_ver = 0;  // list version the region masks were built from (0 = never)
     int max_fuse = kMaxEwOps;          // element-wise ops per fused launch
+    int flush_period = 0;              // flush once the queue holds this many ops (0: on sync / sg_flush only)
     long long known_leaves = 0;
     sg_stats stats{};
     int latched = SG_OK;
@@ -143,10 +144,13 @@ int after_launch(sg_grid *g, const char *what)
 
 bool valid_field(const sg_grid *g, int f) { return f >= 0 && f < g->desc.n_fields; }
 
+int do_flush(sg_grid *g);
+
 int push(sg_grid *g, Op op)
 {
     g->queue.push_back(op);
     g->stats.ops_enqueued++;
+    if (g->flush_period > 0 && (int)g->queue.size() >= g->flush_period) return do_flush(g);
     return SG_OK;
 }
 
@@ -975,6 +979,13 @@ int sg_maccormack(sg_grid *g, int32_t dst, int32_t q, int32_t qhat, int32_t qtil
     o.f0 = dt;
     o.dst_scratch = (g->desc.scratch_mask >> dst) & 1u;
     return push(g, o);
+}
+
+int sg_set_flush_period(sg_grid *g, int32_t ops)
+{
+    if (!g || ops < 0) return fail(SG_ERR_INVALID, "flush period must be >= 0");
+    g->flush_period = ops;
+    return SG_OK;
 }
 
 int sg_set_max_fuse(sg_grid *g, int32_t max_ops)

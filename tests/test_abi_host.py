@@ -433,3 +433,23 @@ def test_advection_dependencies_respected():
     assert lib.sg_advect(g.h, 3, 3, 0, 1e-3) == sg.SG_ERR_INVALID            # dst == src
     assert lib.sg_advect(g.h, 1, 3, 0, 1e-3) == sg.SG_ERR_INVALID            # dst is a velocity field
     assert lib.sg_maccormack(g.h, 4, 3, 4, 5, 0, 1e-3) == sg.SG_ERR_INVALID  # dst == qhat
+
+
+def test_flush_period():
+    """With a flush period of 1 every op is issued as it is queued, so nothing
+    can be fused; a period covering the whole step keeps the fused form."""
+    def body(g):
+        for c in range(3):
+            g.ew(0, 0, alpha=1.0, delta=1.0)
+        g.diffuse7(0, 1, 0.1)
+        g.box27(1, 2)
+    res = {}
+    for period in (0, 1, 5):
+        g = _micro()
+        g.set_flush_period(period)
+        _launches(g, body)                      # the first fused stencil pair also builds region masks
+        res[period] = _launches(g, body)["launches"]
+    assert res[0] == 2 and res[5] == 2          # increments fused; diffuse7 + box27 fused
+    assert res[1] == 5                          # one launch per op
+    with pytest.raises(sg.SgError):
+        _micro().set_flush_period(-1)
