@@ -57,6 +57,7 @@ extern "C" {
 #define SG_ERR_POOL_EXHAUSTED 3  /* an activation needed more than max_leaves leaves */
 #define SG_ERR_TIMEOUT 4         /* a bounded device-side wait gave up */
 #define SG_ERR_CUDA 5            /* a CUDA runtime call failed */
+#define SG_ERR_CHECK 6           /* an invariant check of a checking grid failed (sg_check) */
 
 /* ---- optimizer passes (sg_set_opts); all four on is the default ---- */
 #define SG_OPT_LGR 1u  /* list-generation removal, Sec. 6.2 */
@@ -75,6 +76,11 @@ extern "C" {
 #define SG_CREATE_DRY_RUN 1u /* no device memory and no launches: the queue and
                                 optimizer run and sg_stats counts what would
                                 have been launched (host-logic testing) */
+#define SG_CREATE_CHECK 2u   /* checking grid: every sync also runs sg_check's
+                                invariant checks (the list-dependent ones when
+                                the list is current) and a violation is
+                                returned as SG_ERR_CHECK.  A debugging mode:
+                                each sync costs a few extra kernels */
 
 #define SG_MAX_FIELDS 16
 
@@ -312,6 +318,21 @@ int sg_read_field(sg_grid *g, int32_t f, int64_t cap, float *host_vals);
  * the host buffer may be reused at once; pinned memory makes it faster. */
 int sg_write_field(sg_grid *g, int32_t f, const float *host_vals, int64_t n_leaves);
 
+/* Replace the whole structure with a saved one (the restore half of a
+ * checkpoint whose save half is sg_read_structure + sg_read_field): leaf_b
+ * holds n_leaves root indices in strictly ascending order, each in [0, R^3),
+ * and masks holds L^3/32 uint32 words per leaf, in the layout
+ * sg_read_structure writes (the voxel bit of local index (li*L + lj)*L + lk,
+ * Sec. 3).  Implicit sync: queued work runs first and its latched error, if
+ * any, is returned without changing the structure.  Every field of the
+ * restored leaves is zero afterwards (write them with sg_write_field); the
+ * list is current and in leaf_b's order; reduction slots are untouched.
+ * Both host buffers are copied before the call returns.  Errors:
+ * SG_ERR_INVALID (null buffers with n_leaves > 0, order or range of leaf_b,
+ * a dry-run grid), SG_ERR_POOL_EXHAUSTED (n_leaves > max_leaves; nothing is
+ * changed). */
+int sg_write_structure(sg_grid *g, int64_t n_leaves, const int32_t *leaf_b, const uint32_t *masks);
+
 /* Implicit sync, then copy result slots [0, n) to host memory. */
 int sg_read_sums(sg_grid *g, double *host, int64_t n);
 
@@ -471,6 +492,37 @@ int sg_list_gen_noalloc(const int32_t *dev_root, int64_t n_cells, int32_t *dev_l
  * gives up after about 0.2 s and latches SG_ERR_TIMEOUT, which the next sync
  * returns; the grid stays usable.  No counterpart in the paper. */
 int sg_debug_wait_test(sg_grid *g);
+
+/* Invariant checks of the structure and the stored values, counted per kind
+ * (0 everywhere for a sound grid).  The structure is the two-level tree of
+ * Sec. 3: a root of R^3 pointer cells over a pool of bitmasked leaves. */
+typedef struct sg_check_report {
+    int64_t root_bad;         /* root cells neither null (-1) nor a handed-out slot < max_leaves */
+    int64_t slot_shared;      /* slots referenced by more than one root cell */
+    int64_t list_bad;         /* list entries whose slot is not root[b] or whose b are not
+                                 strictly ascending, plus |list length - allocated leaves| */
+    int64_t nbr_bad;          /* neighbour-table entries differing from the root's */
+    int64_t zero_leaf_bad;    /* nonzero mask words or values in the zero leaf */
+    int64_t inactive_nonzero; /* nonzero values stored at inactive voxels of listed leaves
+                                 (fields not marked scratch) */
+    int64_t leaves;           /* allocated leaves found in the root */
+} sg_check_report;
+
+/* Implicit sync (with a current list), then run every check and fill *out.
+ * Returns SG_OK whatever the counts are; errors are those of the sync, or
+ * SG_ERR_INVALID (null arguments, a dry-run grid), SG_ERR_OOM (scratch for
+ * the checks).  Not part of the paper's method: a debugging aid. */
+int sg_check(sg_grid *g, sg_check_report *out);
+
+/* Test hook for the checks above: after an implicit sync, overwrite one
+ * 32-bit word of the grid's device arrays behind the queue's back (no host
+ * state changes).  array 0 = root (index < R^3; bits, read as int32, must lie
+ * in [-1, max_leaves), so every later access stays in bounds), 1 = mask words
+ * (index < (max_leaves + 1) * L^3/32), 2 + f = field f (index <
+ * (max_leaves + 1) * L^3; bits are the FP32 pattern).  The last leaf of the
+ * mask and field arrays is the zero leaf.  Errors: SG_ERR_INVALID (an index or
+ * value outside those ranges, a dry-run grid). */
+int sg_debug_poke(sg_grid *g, int32_t array, int64_t index, uint32_t bits);
 
 /* Message of the last failing call on this thread ("" if none). */
 const char *sg_last_error(void);

@@ -19,11 +19,11 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 HEADER = os.path.join(ROOT, "include", "sgrid.h")
 
-SG_OK, SG_ERR_INVALID, SG_ERR_OOM, SG_ERR_POOL_EXHAUSTED, SG_ERR_TIMEOUT, SG_ERR_CUDA = range(6)
+SG_OK, SG_ERR_INVALID, SG_ERR_OOM, SG_ERR_POOL_EXHAUSTED, SG_ERR_TIMEOUT, SG_ERR_CUDA, SG_ERR_CHECK = range(7)
 SG_OPT_LGR, SG_OPT_AD, SG_OPT_FUSE, SG_OPT_DSE = 1, 2, 4, 8
 SG_OPT_ALL, SG_OPT_EAGER = 15, 0
 SG_CLEAR, SG_DIFFUSE7, SG_BOX27 = 0, 1, 2
-SG_CREATE_DRY_RUN = 1
+SG_CREATE_DRY_RUN, SG_CREATE_CHECK = 1, 2
 SG_VARIANT_SWEEP, SG_VARIANT_SMEM = 0, 1
 SG_MAX_FIELDS = 16
 
@@ -42,6 +42,12 @@ class SgStats(ctypes.Structure):
                 ("act_launched", ctypes.c_int64), ("act_demoted", ctypes.c_int64), ("ops_enqueued", ctypes.c_int64),
                 ("ops_fused", ctypes.c_int64), ("stores_removed", ctypes.c_int64), ("flushes", ctypes.c_int64),
                 ("bytes_model", ctypes.c_double)]
+
+
+class SgCheckReport(ctypes.Structure):
+    _fields_ = [("root_bad", ctypes.c_int64), ("slot_shared", ctypes.c_int64), ("list_bad", ctypes.c_int64),
+                ("nbr_bad", ctypes.c_int64), ("zero_leaf_bad", ctypes.c_int64), ("inactive_nonzero", ctypes.c_int64),
+                ("leaves", ctypes.c_int64)]
 
 
 class SgError(RuntimeError):
@@ -103,6 +109,7 @@ def load_library(build: bool = True) -> ctypes.CDLL:
         "sg_read_structure": [P, I64, ctypes.POINTER(I64), P, P],
         "sg_read_field": [P, I32, I64, P],
         "sg_write_field": [P, I32, P, I64],
+        "sg_write_structure": [P, I64, P, P],
         "sg_read_sums": [P, P, I64],
         "sg_get_stats": [P, ctypes.POINTER(SgStats)],
         "sg_debug_wait_test": [P],
@@ -117,6 +124,8 @@ def load_library(build: bool = True) -> ctypes.CDLL:
         "sg_batch_info": [P, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I32)],
         "sg_batch_destroy": [P],
         "sg_num_active": [P, ctypes.POINTER(I64)],
+        "sg_check": [P, ctypes.POINTER(SgCheckReport)],
+        "sg_debug_poke": [P, I32, I64, U32],
     }
     for name, args in sigs.items():
         fn = getattr(lib, name)
@@ -150,7 +159,9 @@ class Grid:
 
     def __init__(self, res: int, leaf_log2: int = 3, n_fields: int = 2, max_leaves: int = 4096,
                  max_sums: int = 1, scratch_mask: int = 0, stream=None, dry_run: bool = False,
-                 device: int | None = None):
+                 device: int | None = None, checking: bool | None = None):
+        """checking: run the invariant checks at every sync (SG_CREATE_CHECK);
+        by default on when the environment variable SG_CHECK is set to 1."""
         self.lib = load_library()
         self.res, self.leaf_log2, self.n_fields = int(res), int(leaf_log2), int(n_fields)
         self.L = 1 << self.leaf_log2
@@ -159,8 +170,11 @@ class Grid:
         self.max_leaves, self.max_sums = int(max_leaves), int(max_sums)
         self._borrowed = []
         self.h = None
+        if checking is None:
+            checking = os.environ.get("SG_CHECK", "0") == "1"
+        flags = (SG_CREATE_DRY_RUN if dry_run else 0) | (SG_CREATE_CHECK if checking else 0)
         desc = SgDesc(self.res, self.leaf_log2, self.n_fields, self.max_sums, self.max_leaves, int(scratch_mask),
-                      SG_CREATE_DRY_RUN if dry_run else 0)
+                      flags)
         stream_ptr = None
         if not dry_run:
             import torch
@@ -360,12 +374,30 @@ class Grid:
             assert not vals.is_cuda and vals.is_contiguous()
             self._c(self.lib.sg_write_field(self.h, int(f), _ptr(vals), vals.numel() // self.V))
 
+    def write_structure(self, leaf_b, masks):
+        """Replace the structure with (leaf_b int32[n] ascending, masks
+        uint32[n, W]) as read_structure returns them; every field of the
+        restored leaves is zero afterwards."""
+        b = np.ascontiguousarray(leaf_b, dtype=np.int32)
+        m = np.ascontiguousarray(masks, dtype=np.uint32)
+        assert m.shape == (b.size, self.W), (m.shape, b.size, self.W)
+        self._c(self.lib.sg_write_structure(self.h, b.size, _ptr(b), _ptr(m)))
+        self._borrowed.clear()
+
     def read_sums(self, n: int | None = None) -> np.ndarray:
         n = self.max_sums if n is None else int(n)
         out = np.zeros(n, dtype=np.float64)
         self._c(self.lib.sg_read_sums(self.h, _ptr(out), n))
         self._borrowed.clear()
         return out
+
+    def check(self) -> dict:
+        """Invariant-violation counts of the structure and stored values
+        (implicit sync; all zero for a sound grid) and the leaves found."""
+        r = SgCheckReport()
+        self._c(self.lib.sg_check(self.h, ctypes.byref(r)))
+        self._borrowed.clear()
+        return {name: getattr(r, name) for name, _ in SgCheckReport._fields_}
 
     def stats(self) -> dict:
         s = SgStats()

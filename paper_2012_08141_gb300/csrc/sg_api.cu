@@ -102,6 +102,7 @@ struct sg_grid {
     long long perm_cap = 0;  // particles the binned-P2G order array holds
     const void *p2g_x = nullptr;  // positions and count the order array was built for
     long long p2g_n = 0;
+    unsigned long long *chk_cnt = nullptr;  // invariant-check counters (allocated at the first check)
 };
 
 namespace {
@@ -688,6 +689,43 @@ int map_device_error(int bits)
     return SG_OK;
 }
 
+int ensure_staging(sg_grid *g);
+
+// The invariant checks of sg_check; the list-dependent ones only with a
+// current list.  Check kernels are not counted in sg_stats.
+int run_checks(sg_grid *g, sg_check_report *r, bool with_list)
+{
+    *r = sg_check_report{};
+    int rc;
+    if (!g->chk_cnt && !(g->chk_cnt = (unsigned long long *)dev_alloc(g, sizeof(unsigned long long) * kNumChk)))
+        return fail(SG_ERR_OOM, "check counters");
+    if ((rc = ensure_staging(g))) return rc;  // slot -> root cell map
+    uint32_t field_bits = 0;
+    for (int f = 0; f < g->dev.F; ++f)
+        if (!((g->desc.scratch_mask >> f) & 1u)) field_bits |= 1u << g->phys[f];
+    cudaStream_t s = g->stream;
+    if ((rc = cuda_check(cudaMemsetAsync(g->chk_cnt, 0, sizeof(unsigned long long) * kNumChk, s), "check counters")) ||
+        (rc = cuda_check(cudaMemsetAsync(g->dev.staging_u, 0xff, sizeof(uint32_t) * g->dev.cap, s), "owner map")))
+        return rc;
+    launch_checks(g->dev, s, g->dev.staging_u, g->chk_cnt, with_list, field_bits, g->lc);
+    if ((rc = cuda_check(cudaPeekAtLastError(), "invariant checks"))) return rc;
+    unsigned long long c[kNumChk];
+    if ((rc = cuda_check(cudaMemcpyAsync(c, g->chk_cnt, sizeof c, cudaMemcpyDeviceToHost, s), "read check counters")) ||
+        (rc = cuda_check(cudaStreamSynchronize(s), "stream synchronize")))
+        return rc;
+    r->root_bad = (int64_t)c[kChkRoot];
+    r->slot_shared = (int64_t)c[kChkShared];
+    r->leaves = (int64_t)c[kChkLeaves];
+    r->zero_leaf_bad = (int64_t)c[kChkZero];
+    if (with_list) {
+        const long long d = (long long)g->host_ctrl->list_n - (long long)c[kChkLeaves];
+        r->list_bad = (int64_t)c[kChkList] + (d < 0 ? -d : d);
+        r->nbr_bad = (int64_t)c[kChkNbr];
+        r->inactive_nonzero = (int64_t)c[kChkInactive];
+    }
+    return SG_OK;
+}
+
 // Flush, wait, read the control block; latch and clear device errors.
 int do_sync(sg_grid *g)
 {
@@ -704,6 +742,17 @@ int do_sync(sg_grid *g)
         cudaStreamSynchronize(g->stream);
         const int code = map_device_error(bits);
         if (g->latched == SG_OK) g->latched = code;
+    }
+    if ((g->desc.flags & SG_CREATE_CHECK) && g->latched == SG_OK) {
+        sg_check_report r;
+        const bool with_list = g->list_ver == g->mask_ver;
+        if ((rc = run_checks(g, &r, with_list))) return rc;
+        if (r.root_bad | r.slot_shared | r.list_bad | r.nbr_bad | r.zero_leaf_bad | r.inactive_nonzero)
+            g->latched = fail(SG_ERR_CHECK,
+                              "invariant check: root %lld, shared slots %lld, list %lld, neighbours %lld, zero leaf %lld, "
+                              "inactive values %lld",
+                              (long long)r.root_bad, (long long)r.slot_shared, (long long)r.list_bad,
+                              (long long)r.nbr_bad, (long long)r.zero_leaf_bad, (long long)r.inactive_nonzero);
     }
     if (g->list_ver == g->mask_ver) g->known_leaves = g->host_ctrl->list_n;
     const int out = g->latched;
@@ -1239,6 +1288,77 @@ int sg_write_field(sg_grid *g, int32_t f, const float *host_vals, int64_t n_leav
     launch_scatter_field(g->dev, g->stream, g->phys[f], g->lc);
     if ((rc = after_launch(g, "scatter field"))) return rc;
     return cuda_check(cudaStreamSynchronize(g->stream), "stream synchronize");
+}
+
+int sg_check(sg_grid *g, sg_check_report *out)
+{
+    if (!g || !out) return fail(SG_ERR_INVALID, "null argument");
+    if (g->dry) return fail(SG_ERR_INVALID, "a dry-run grid holds no data");
+    int rc = sync_with_list(g);
+    if (rc && rc != SG_ERR_CHECK) return rc;  // a checking grid's own sync counts the same violations
+    return run_checks(g, out, true);
+}
+
+int sg_debug_poke(sg_grid *g, int32_t array, int64_t index, uint32_t bits)
+{
+    if (!g || g->dry || array < 0 || array >= 2 + g->desc.n_fields || index < 0)
+        return fail(SG_ERR_INVALID, "bad poke target");
+    const long long nr = (long long)g->dev.R * g->dev.R * g->dev.R;
+    const long long V = (long long)g->dev.L * g->dev.L * g->dev.L;
+    void *dst = nullptr;
+    if (array == 0) {
+        const int32_t v = (int32_t)bits;
+        if (index >= nr || v < -1 || v >= g->dev.cap) return fail(SG_ERR_INVALID, "root poke out of range");
+        dst = g->dev.root + index;
+    } else if (array == 1) {
+        if (index >= (g->dev.cap + 1) * g->dev.W) return fail(SG_ERR_INVALID, "mask poke out of range");
+        dst = g->dev.mask + index;
+    } else {
+        if (index >= (g->dev.cap + 1) * V) return fail(SG_ERR_INVALID, "field poke out of range");
+        dst = g->dev.field[g->phys[array - 2]] + index;
+    }
+    int rc = do_sync(g);
+    if (rc) return rc;
+    if ((rc = cuda_check(cudaMemcpyAsync(dst, &bits, sizeof bits, cudaMemcpyHostToDevice, g->stream), "poke")))
+        return rc;
+    return cuda_check(cudaStreamSynchronize(g->stream), "stream synchronize");
+}
+
+int sg_write_structure(sg_grid *g, int64_t n_leaves, const int32_t *leaf_b, const uint32_t *masks)
+{
+    if (!g || n_leaves < 0 || (n_leaves > 0 && (!leaf_b || !masks))) return fail(SG_ERR_INVALID, "bad arguments");
+    const long long nr = (long long)g->dev.R * g->dev.R * g->dev.R;
+    for (long long e = 0; e < n_leaves; ++e)
+        if (leaf_b[e] < 0 || leaf_b[e] >= nr || (e > 0 && leaf_b[e] <= leaf_b[e - 1]))
+            return fail(SG_ERR_INVALID, "leaf_b[%lld] = %d out of range or order", e, leaf_b[e]);
+    if (n_leaves > g->dev.cap)
+        return fail(SG_ERR_POOL_EXHAUSTED, "%lld saved leaves, max_leaves %lld", (long long)n_leaves,
+                    (long long)g->dev.cap);
+    if (g->dry) return fail(SG_ERR_INVALID, "a dry-run grid holds no data");
+    int rc = do_sync(g);
+    if (rc) return rc;
+    const long long n = n_leaves;
+    // both arrays go through the staging buffer: n * (1 + W) words <= cap * L^3
+    if (n > 0 && (rc = ensure_staging(g))) return rc;
+    const size_t b_words = (size_t(n) + 3) & ~size_t(3);  // masks start 16-byte aligned
+    int32_t *dev_b = (int32_t *)g->dev.staging_u;
+    uint32_t *dev_m = g->dev.staging_u + b_words;
+    launch_deactivate_all(g->dev, g->stream);
+    if ((rc = after_launch(g, "deactivate"))) return rc;
+    if (n > 0) {
+        if ((rc = cuda_check(cudaMemcpyAsync(dev_b, leaf_b, sizeof(int32_t) * n, cudaMemcpyHostToDevice, g->stream),
+                             "copy leaf_b")) ||
+            (rc = cuda_check(cudaMemcpyAsync(dev_m, masks, sizeof(uint32_t) * g->dev.W * n, cudaMemcpyHostToDevice,
+                                             g->stream),
+                             "copy masks")))
+            return rc;
+        launch_restore_structure(g->dev, g->stream, dev_b, dev_m, n, g->lc);
+        if ((rc = after_launch(g, "restore structure"))) return rc;
+    }
+    g->mask_ver++;
+    g->applied_shells.clear();
+    g->applied_restrict.clear();
+    return sync_with_list(g);
 }
 
 int sg_read_sums(sg_grid *g, double *host, int64_t n)

@@ -101,6 +101,16 @@ void launch_mark_coords(const DevGrid &g, cudaStream_t s, const int32_t *xyz, lo
 void launch_alloc_needed(const DevGrid &g, cudaStream_t s);
 void launch_setbits_coords(const DevGrid &g, cudaStream_t s, const int32_t *xyz, long long n);
 void launch_deactivate_all(const DevGrid &g, cudaStream_t s);
+// Invariant checks (sg_check): violation counters, indexed by CheckKind.
+enum CheckKind { kChkRoot, kChkShared, kChkList, kChkNbr, kChkZero, kChkInactive, kChkLeaves, kNumChk };
+// owner: cap words set to 0xffffffff before the launch (slot -> root cell);
+// cnt: kNumChk zeroed counters.  The list checks need a current list.
+void launch_checks(const DevGrid &g, cudaStream_t s, uint32_t *owner, unsigned long long *cnt, bool with_list,
+                   uint32_t field_bits, const LaunchCfg &lc);
+// Slot e <- saved leaf e: root[leaf_b[e]] = e, mask words copied, fields
+// zeroed; pool_count = n.  Runs after launch_deactivate_all.
+void launch_restore_structure(const DevGrid &g, cudaStream_t s, const int32_t *leaf_b, const uint32_t *masks,
+                              long long n, const LaunchCfg &lc);
 void launch_clear_list(const DevGrid &g, cudaStream_t s);
 // For each list entry (8^3 leaves) and each of the 10 columns tj of the
 // 10^3 region around the leaf, the activity bits of the 10 rows ti = 0..9 of

@@ -249,6 +249,36 @@ void launch_deactivate_all(const DevGrid &g, cudaStream_t s)
     k_deactivate_all<<<(unsigned)blocks, 256, 0, s>>>(g);
 }
 
+// Restore a saved structure (checkpoint): one warp per saved leaf e takes
+// slot e, so the slots come out in the saved (ascending root index) order.
+__global__ void __launch_bounds__(256) k_restore_structure(DevGrid g, const int32_t *__restrict__ leaf_b,
+                                                           const uint32_t *__restrict__ masks, long long n)
+{
+    const int lane = lane_id();
+    const int V = g.L * g.L * g.L;
+    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (long long e = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; e < n; e += warps) {
+        for (int f = 0; f < g.F; ++f) {
+            float4 *p = reinterpret_cast<float4 *>(g.field[f] + e * V);
+            for (int q = lane; q < V / 4; q += 32) p[q] = z;
+        }
+        for (int w = lane; w < g.W; w += 32) g.mask[e * g.W + w] = masks[e * g.W + w];
+        if (lane == 0) g.root[leaf_b[e]] = (int)e;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        g.ctrl->pool_count = (int)n;
+        g.ctrl->list_n = 0;
+        g.ctrl->dirty = 1;
+    }
+}
+
+void launch_restore_structure(const DevGrid &g, cudaStream_t s, const int32_t *leaf_b, const uint32_t *masks,
+                              long long n, const LaunchCfg &lc)
+{
+    k_restore_structure<<<lc.num_sms * 4, 256, 0, s>>>(g, leaf_b, masks, n);
+}
+
 // The clear-list task of the eager form (Sec. 6.1, Fig. 8): empty the list.
 __global__ void k_clear_list(DevGrid g)
 {

@@ -63,16 +63,29 @@ class Server:
     """Continuous-batching request loop over resident sparse diffusion jobs."""
 
     def __init__(self, max_jobs: int = 256, warps_per_cta: int = 4, hbm_reserve: int = 4 << 30, coef: float = 0.1,
-                 stream=None):
+                 stream=None, fail_alloc=None):
+        """fail_alloc: optional fault-injection hook, called as
+        fail_alloc(call_index, nbytes) before each device allocation the
+        server or its jobs make; a true result makes that allocation fail
+        (return NULL) as an out-of-memory device would."""
         import torch
         self.lib = _lib()
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         dev, st = torch.cuda.current_device(), self.stream
+        self.alloc_calls = 0
+        self.live = {}  # device address -> bytes, for leak checks
 
         def _alloc(nbytes, ctx):
-            return torch.cuda.caching_allocator_alloc(int(nbytes), dev, st)
+            i = self.alloc_calls
+            self.alloc_calls += 1
+            if fail_alloc is not None and fail_alloc(i, int(nbytes)):
+                return None
+            p = torch.cuda.caching_allocator_alloc(int(nbytes), dev, st)
+            self.live[p] = int(nbytes)
+            return p
 
         def _free(ptr, ctx):
+            self.live.pop(ptr, None)
             torch.cuda.caching_allocator_delete(ptr)
 
         self._cb = (_ALLOC(_alloc), _FREE(_free))

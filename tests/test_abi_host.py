@@ -453,3 +453,27 @@ def test_flush_period():
     assert res[1] == 5                          # one launch per op
     with pytest.raises(sg.SgError):
         _micro().set_flush_period(-1)
+
+
+def test_write_structure_argument_checks():
+    """Order, range and capacity of a saved structure are checked on the host
+    before any device work; a dry-run grid holds no data to restore into."""
+    import numpy as np
+    g = dry()                                   # 64^3, 8^3 leaves: R^3 = 512, max_leaves 1024
+    lib = g.lib
+    m = np.zeros((3, g.W), dtype=np.uint32)
+    cases = [
+        (np.array([5, 5, 9], np.int32), sg.SG_ERR_INVALID),        # not strictly ascending
+        (np.array([9, 5, 7], np.int32), sg.SG_ERR_INVALID),
+        (np.array([-1, 5, 7], np.int32), sg.SG_ERR_INVALID),       # out of [0, R^3)
+        (np.array([1, 5, 512], np.int32), sg.SG_ERR_INVALID),
+        (np.array([1, 5, 511], np.int32), sg.SG_ERR_INVALID),      # valid, but a dry-run grid
+    ]
+    for b, rc in cases:
+        assert lib.sg_write_structure(g.h, 3, b.ctypes.data, m.ctypes.data) == rc, b
+    assert lib.sg_write_structure(g.h, 3, None, m.ctypes.data) == sg.SG_ERR_INVALID
+    assert lib.sg_write_structure(g.h, -1, None, None) == sg.SG_ERR_INVALID
+    small = sg.Grid(64, 3, 1, max_leaves=2, dry_run=True)
+    b = np.array([1, 5, 7], np.int32)
+    assert lib.sg_write_structure(small.h, 3, b.ctypes.data, m.ctypes.data) == sg.SG_ERR_POOL_EXHAUSTED
+    assert b"max_leaves" in lib.sg_last_error()

@@ -1,0 +1,172 @@
+"""GPU tests of checkpoint and restore (sg_write_structure + sg_write_field
+behind paper_2012_08141_gb300.checkpoint): a restored grid has the saved
+structure bit-exact, the saved fields bit-exact, and time steps continued from
+it give bit-identical fields, and sums equal to FP64 rounding, to the
+original grid's."""
+import numpy as np
+import pytest
+
+import oracle
+from workload import leaf_values, tiny_shell
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    yield
+
+
+def _stepped(L, seed=4):
+    import paper_2012_08141_gb300 as sg
+    spec = tiny_shell(seed, N=64, L=L)
+    g = sg.Grid(spec.N, int(np.log2(L)), 3, max_leaves=(64 // L) ** 3, max_sums=2)
+    g.activate_shell(spec.lo2, spec.hi2, spec.lo_strict)
+    b, _ = g.read_structure()
+    g.write_field(0, leaf_values(seed, spec.N, L, b))
+    g.diffuse7(0, 1, 0.1)
+    g.box27(1, 2)
+    g.diffuse7(2, 0, 0.05)
+    return spec, g
+
+
+def _continue(g):
+    g.diffuse7(0, 1, 0.1)
+    g.box27(1, 2)
+    g.reduce_sum(2, 0)
+    g.diffuse7(2, 0, 0.1)
+    g.reduce_sum(0, 1)
+
+
+def _same(a, b, fields):
+    ab, am = a.read_structure()
+    bb, bm = b.read_structure()
+    np.testing.assert_array_equal(ab, bb)
+    np.testing.assert_array_equal(am, bm)
+    for f in fields:
+        np.testing.assert_array_equal(a.read_field(f), b.read_field(f))
+
+
+@pytest.mark.parametrize("L", [8, 4])
+def test_round_trip_then_identical_steps(L, tmp_path):
+    from paper_2012_08141_gb300 import checkpoint
+    spec, g = _stepped(L)
+    path = tmp_path / "ck.npz"
+    checkpoint.save(g, path)
+    h = checkpoint.load(path, max_sums=2)
+    _same(g, h, range(3))
+    og = oracle.Grid(spec.N, L, 1)               # the restored structure is the shell's, by definition
+    og.activate_shell(spec.lo2, spec.hi2, spec.lo_strict)
+    ob, om = og.structure()
+    hb, hm = h.read_structure()
+    np.testing.assert_array_equal(hb, ob)
+    np.testing.assert_array_equal(hm, om)
+    for grid in (g, h):
+        _continue(grid)
+    _same(g, h, range(3))
+    np.testing.assert_allclose(g.read_sums(2), h.read_sums(2), rtol=1e-12)   # FP64 partials
+    g.close()
+    h.close()
+
+
+def test_restore_replaces_an_existing_structure(tmp_path):
+    """Restoring into a grid that holds another shell drops its leaves and
+    values; fields left out of the checkpoint read 0; a later activation of the
+    saved shell is launched (not demoted) and changes nothing."""
+    import paper_2012_08141_gb300 as sg
+    from paper_2012_08141_gb300 import checkpoint
+    spec, g = _stepped(8)
+    path = tmp_path / "ck.npz"
+    checkpoint.save(g, path, fields=[0, 2])
+    other = tiny_shell(9, N=64, L=8)
+    h = sg.Grid(64, 3, 3, max_leaves=512, max_sums=2)
+    h.activate_shell(other.lo2 // 2, other.hi2 * 2, False)
+    h.fill_hash(0, 3)
+    h.fill_hash(1, 4)
+    assert h.num_leaves() != g.num_leaves()
+    checkpoint.restore(h, path)
+    _same(g, h, [0, 2])
+    assert not h.read_field(1).any()
+    d0 = h.stats()["act_demoted"]
+    h.activate_shell(spec.lo2, spec.hi2, spec.lo_strict)
+    h.flush()
+    assert h.stats()["act_demoted"] == d0
+    _same(g, h, [0, 2])
+    g.close()
+    h.close()
+
+
+def test_empty_and_maskless_leaves(tmp_path):
+    """An empty structure restores to an empty grid; leaves whose masks are all
+    zero are kept (allocated, no active voxel) and listed in order."""
+    import paper_2012_08141_gb300 as sg
+    g = sg.Grid(64, 3, 1, max_leaves=512)
+    g.fill_hash(0, 1)
+    g.write_structure(np.zeros(0, np.int32), np.zeros((0, g.W), np.uint32))
+    assert g.num_leaves() == 0 and g.num_active() == 0
+    b = np.array([0, 7, 64, 511], np.int32)
+    m = np.zeros((4, g.W), np.uint32)
+    m[1, 3] = 0x80000001
+    m[3, g.W - 1] = 0xffffffff
+    g.write_structure(b, m)
+    gb, gm = g.read_structure()
+    np.testing.assert_array_equal(gb, b)
+    np.testing.assert_array_equal(gm, m)
+    assert g.num_active() == 34
+    g.fill_hash(0, 2)
+    v = g.read_field(0)
+    bits = np.unpackbits(m.view(np.uint8), bitorder="little").reshape(4, g.V).astype(bool)
+    assert (v[~bits] == 0).all() and (v[bits] > 0).sum() >= 30
+    g.close()
+
+
+def test_too_many_leaves_leaves_the_grid_unchanged(tmp_path):
+    import paper_2012_08141_gb300 as sg
+    from paper_2012_08141_gb300 import checkpoint
+    spec, g = _stepped(8)
+    path = tmp_path / "ck.npz"
+    checkpoint.save(g, path)
+    small = sg.Grid(64, 3, 3, max_leaves=8)
+    import torch
+    small.activate_coords(torch.tensor([[1, 2, 3]], dtype=torch.int32).cuda())
+    small.fill_hash(0, 5)
+    before_b, before_m = small.read_structure()
+    before_v = small.read_field(0)
+    with pytest.raises(sg.SgError) as e:
+        checkpoint.restore(small, path)
+    assert e.value.code == sg.SG_ERR_POOL_EXHAUSTED
+    b, m = small.read_structure()
+    np.testing.assert_array_equal(b, before_b)
+    np.testing.assert_array_equal(m, before_m)
+    np.testing.assert_array_equal(small.read_field(0), before_v)
+    with pytest.raises(ValueError):
+        checkpoint.restore(sg.Grid(32, 3, 3, max_leaves=64), path)   # another resolution
+    g.close()
+    small.close()
+
+
+def test_band512_round_trip(tmp_path):
+    """The 512^3 band (26,104 leaves of 8^3): structure and a hashed field
+    round-trip bit-exact; one fused step from each gives the same sum."""
+    import paper_2012_08141_gb300 as sg
+    from paper_2012_08141_gb300 import checkpoint
+    from workload import band512
+    spec = band512()
+    g = sg.Grid(512, 3, 3, max_leaves=32768, max_sums=1, scratch_mask=0b010)
+    g.activate_shell(spec.lo2, spec.hi2, spec.lo_strict)
+    g.fill_hash(0, 17)
+    path = tmp_path / "band.npz"
+    checkpoint.save(g, path, fields=[0])
+    h = checkpoint.load(path, max_sums=1, scratch_mask=0b010)
+    _same(g, h, [0])
+    for grid in (g, h):
+        grid.diffuse7(0, 1, 0.1)
+        grid.box27(1, 2)
+        grid.reduce_sum(2, 0)
+    np.testing.assert_allclose(g.read_sums(1), h.read_sums(1), rtol=1e-12)
+    np.testing.assert_array_equal(g.read_field(2), h.read_field(2))
+    g.close()
+    h.close()

@@ -85,3 +85,40 @@ def test_job_that_cannot_fit_fails_and_server_continues():
         srv.tick()
     assert srv.job(jid)["state"] == SG_JOB_DONE
     srv.close()
+
+
+def test_injected_allocation_failure_fails_one_job_only():
+    """Host-side fault injection: the fifth device allocation of one job's
+    admission fails.  That job is failed with its partial allocations freed;
+    the jobs around it run to the same results as alone; after close nothing
+    the server allocated is left."""
+    from paper_2012_08141_gb300.serve import SG_JOB_DONE, SG_JOB_FAILED, Server
+    target = {}
+
+    def fail_alloc(i, nbytes):
+        return "at" in target and i == target["at"]
+
+    srv = Server(max_jobs=4, hbm_reserve=0, fail_alloc=fail_alloc)
+    specs = batched_mix(11, n_grids=3, lo=1e3, hi=4e3)
+    a = srv.submit(specs[0], 3)
+    srv.tick()
+    assert srv.job(a)["state"] != SG_JOB_FAILED
+    live_a = dict(srv.live)
+    target["at"] = srv.alloc_calls + 4          # inside the next admission's grid creation
+    b = srv.submit(specs[1], 3)
+    c = srv.submit(specs[2], 2)
+    srv.tick()
+    assert srv.job(b)["state"] == SG_JOB_FAILED
+    assert srv.job(c)["state"] != SG_JOB_FAILED
+    for _ in range(6):
+        srv.tick()
+    st = srv.stats()
+    assert st["failed"] == 1 and st["completed"] == 2
+    for jid, spec, k in ((a, specs[0], 3), (c, specs[2], 2)):
+        jb = srv.job(jid)
+        assert jb["state"] == SG_JOB_DONE and jb["steps_done"] == k
+        ref = alone_sum(spec, k)
+        assert abs(jb["sum"] - ref) <= TOL * abs(ref)
+    assert set(srv.live) <= set(live_a)         # b's partial grid and finished jobs freed
+    srv.close()
+    assert not srv.live
