@@ -298,6 +298,38 @@ int run_struct_for_group(sg_grid *g, size_t &i)
 // kMaxEwSlots distinct fields.  Fields read before written are loaded once;
 // a written field is stored once, and not at all when it is scratch and no
 // later queued op reads it (Sec. 6.5).  Without fusion each op is a launch.
+//
+// Dead ops of a fused run: an op whose result is overwritten before anything
+// reads it, and that is not the slot's final stored value, is removed (the
+// register-level counterpart of the dead stores above); the loads are then
+// the slots the remaining ops read before writing.
+void drop_dead_ew_ops(EwProgram &p)
+{
+    bool live[kMaxEwSlots];
+    for (int k = 0; k < p.n_slots; ++k) live[k] = p.store[k] != 0;
+    bool keep[kMaxEwOps + 1];
+    for (int i = p.n_ops - 1; i >= 0; --i) {
+        const EwOp &o = p.op[i];
+        keep[i] = o.kind == kEwSum || live[o.dst];
+        if (!keep[i]) continue;
+        if (o.kind != kEwSum) live[o.dst] = false;
+        if (o.kind != kEwFill) live[o.a] = true;
+        if (o.kind == kEwAxby || o.kind == kEwGeneral) live[o.b] = true;
+    }
+    int n = 0;
+    for (int i = 0; i < p.n_ops; ++i)
+        if (keep[i]) p.op[n++] = p.op[i];
+    p.n_ops = n;
+    bool written[kMaxEwSlots] = {};
+    for (int k = 0; k < p.n_slots; ++k) p.load[k] = 0;
+    for (int i = 0; i < p.n_ops; ++i) {
+        const EwOp &o = p.op[i];
+        if (o.kind != kEwFill && !written[o.a]) p.load[o.a] = 1;
+        if ((o.kind == kEwAxby || o.kind == kEwGeneral) && !written[o.b]) p.load[o.b] = 1;
+        if (o.kind != kEwSum) written[o.dst] = true;
+    }
+}
+
 int run_ew_group(sg_grid *g, size_t &i)
 {
     int rc;
@@ -338,6 +370,7 @@ int run_ew_group(sg_grid *g, size_t &i)
             e.beta = o.f1;
             e.gamma = o.coef;
             e.delta = o.f2;
+            ew_kind(e);
             p.op[p.n_ops++] = e;
             written[e.dst] = true;
             scratch[e.dst] = o.dst_scratch;
@@ -349,6 +382,7 @@ int run_ew_group(sg_grid *g, size_t &i)
             e.dst = -1;
             e.a = use(o.src, false);
             e.b = -1;
+            ew_kind(e);
             p.op[p.n_ops++] = e;
             p.sum_out = (int)o.slot;
             ++j;
@@ -358,12 +392,13 @@ int run_ew_group(sg_grid *g, size_t &i)
     }
     int stores = 0, loads = 0;
     for (int k = 0; k < p.n_slots; ++k) {
-        loads += p.load[k];
         if (!written[k]) continue;
         p.store[k] = !(dse && scratch[k] && !read_later(g, j, p.field[k]));
         stores += p.store[k];
         g->stats.stores_removed += writes[k] - (p.store[k] ? 1 : 0);
     }
+    if (dse) drop_dead_ew_ops(p);
+    for (int k = 0; k < p.n_slots; ++k) loads += p.load[k];
     if (!g->dry) launch_ew(g->dev, g->stream, p, g->lc);
     g->stats.ops_fused += (int64_t)(j - i) - 1;
     g->stats.bytes_model += leaf_bytes(g) * double(g->known_leaves) * double(loads + stores);

@@ -203,11 +203,38 @@ constexpr int kMaxEwOps = 16;   // ops (and at most one reduction) per fused lau
 constexpr int kMaxEwSlots = 8;  // distinct fields per fused launch
 // r[dst] = alpha r[a] + beta r[b] + gamma r[a] r[b] + delta on the active
 // voxels (0 elsewhere); a, b = -1: absent (0).  dst = -1: add the active
-// values of r[a] to the launch's reduction.
+// values of r[a] to the launch's reduction.  `kind` names the terms present
+// (set by the host with ew_kind), so the kernel evaluates only those.
+enum EwKind : int8_t {
+    kEwGeneral = 0,  // gamma a b + alpha a + beta b + delta
+    kEwFill = 1,     // delta                      (a, b absent)
+    kEwAx = 2,       // alpha a + delta            (b absent)
+    kEwAxby = 3,     // alpha a + beta b + delta   (gamma = 0)
+    kEwSum = 4,      // reduction of r[a]
+};
 struct EwOp {
-    int8_t dst, a, b;
+    int8_t dst, a, b, kind;
     float alpha, beta, gamma, delta;
 };
+// Normalise an op and set its kind: an op reading only b is rewritten to read
+// a; kinds follow from the absent operands and gamma == 0.
+inline void ew_kind(EwOp &o)
+{
+    if (o.dst < 0) {
+        o.kind = kEwSum;
+        return;
+    }
+    if (o.a < 0 && o.b >= 0) {
+        o.a = o.b;
+        o.alpha = o.beta;
+        o.b = -1;
+        o.beta = 0.f;
+    }
+    if (o.a < 0) o.kind = kEwFill;
+    else if (o.b < 0) o.kind = kEwAx;
+    else if (o.gamma == 0.f) o.kind = kEwAxby;
+    else o.kind = kEwGeneral;
+}
 struct EwProgram {
     int n_ops, n_slots;
     int field[kMaxEwSlots];      // physical field of each slot
@@ -215,6 +242,7 @@ struct EwProgram {
     uint8_t store[kMaxEwSlots];  // final value live: store it
     EwOp op[kMaxEwOps + 1];
     int sum_out;                 // result index of the reduction, -1 none
+    float *fp[kMaxEwSlots];      // field[field[k]], filled in by launch_ew
 };
 void launch_ew(const DevGrid &g, cudaStream_t s, const EwProgram &prog, const LaunchCfg &lc);
 

@@ -10,65 +10,143 @@
 
 namespace sg {
 
-// One thread handles four consecutive voxels (a float4) of a listed leaf.
-template <int L>
-__global__ void __launch_bounds__(256) k_ew(DevGrid g, EwProgram prog)
+__device__ __forceinline__ float4 f4_fma(float al, float4 a, float4 c)
 {
-    constexpr int V = L * L * L, Q = V / 4, LG2 = (L == 8) ? 3 : 2;
-    __shared__ float4 s_reg[kMaxEwSlots][256];
-    __shared__ double s_red[8];
+    return make_float4(fmaf(al, a.x, c.x), fmaf(al, a.y, c.y), fmaf(al, a.z, c.z), fmaf(al, a.w, c.w));
+}
+__device__ __forceinline__ float4 f4_splat(float v) { return make_float4(v, v, v, v); }
+__device__ __forceinline__ float4 f4_mask(uint32_t bits, float4 v)
+{
+    return make_float4((bits & 1u) ? v.x : 0.f, (bits & 2u) ? v.y : 0.f, (bits & 4u) ? v.z : 0.f,
+                       (bits & 8u) ? v.w : 0.f);
+}
+
+__device__ __forceinline__ void ld8(const float *p, float4 &a, float4 &b)
+{
+    asm volatile("ld.global.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+                 : "l"(p));
+}
+__device__ __forceinline__ void st8(float *p, float4 a, float4 b)
+{
+    asm volatile("st.global.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "f"(a.x), "f"(a.y), "f"(a.z),
+                 "f"(a.w), "f"(b.x), "f"(b.y), "f"(b.z), "f"(b.w)
+                 : "memory");
+}
+
+constexpr int kEwThreads = 128;
+
+// One thread handles eight consecutive voxels (a 32-byte row piece) of a
+// listed leaf, as two float4 halves h = 0, 1.  The op loop is unrolled, so
+// each op's fields are compile-time offsets into the kernel's parameters and
+// its kind a uniform branch.  Values at inactive voxels are carried unmasked
+// through the run (ops are voxel-wise, so they never reach an active voxel)
+// and set to 0 where they leave it: at the stores and in the reduction.
+template <int L>
+__global__ void __launch_bounds__(kEwThreads, 8) k_ew(DevGrid g, EwProgram prog)
+{
+    constexpr int V = L * L * L, Q = V / 8, LG2 = (L == 8) ? 3 : 2;
+    extern __shared__ float4 s_reg[];  // [n_slots][2][kEwThreads]
+    __shared__ double s_red[kEwThreads / 32];
     const long long n = g.ctrl->list_n;
-    float4 *reg = &s_reg[0][threadIdx.x];  // slot k at reg[k * 256]
+    float4 *reg = s_reg + threadIdx.x;  // slot k, half h at reg[(2k + h) * kEwThreads]
+    constexpr int S = kEwThreads;
     float part = 0.f;
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n * Q;
-         q += (long long)gridDim.x * blockDim.x) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    // the slot of the next iteration is read one iteration ahead, so the mask
+    // word and the field rows of an iteration are requested together
+    int slot_next = q < n * Q ? g.list_slot[q / Q] : 0;
+    for (; q < n * Q; q += stride) {
         const long long e = q / Q;
         const int c = (int)(q - e * Q);
-        const int slot = g.list_slot[e];
-        const int l = 4 * c;
-        const uint32_t bits = (g.mask[(long long)slot * g.W + (l >> 5)] >> (l & 31)) & 0xfu;
+        const int slot = slot_next;
+        if (q + stride < n * Q) slot_next = g.list_slot[(q + stride) / Q];
+        const int l = 8 * c;
+        const uint32_t bits = (g.mask[(long long)slot * g.W + (l >> 5)] >> (l & 31)) & 0xffu;
+        const uint32_t b0 = bits & 0xfu, b1 = bits >> 4;
         const long long base = ((long long)slot << (3 * LG2)) + l;
-        for (int k = 0; k < prog.n_slots; ++k)
-            if (prog.load[k]) reg[k * 256] = *reinterpret_cast<const float4 *>(g.field[prog.field[k]] + base);
-        for (int i = 0; i < prog.n_ops; ++i) {
-            const EwOp &o = prog.op[i];
-            if (o.dst < 0) {  // reduction of slot o.a at this point of the run
-                const float4 v = reg[o.a * 256];
-                part += ((bits & 1u) ? v.x : 0.f) + ((bits & 2u) ? v.y : 0.f) + ((bits & 4u) ? v.z : 0.f) +
-                        ((bits & 8u) ? v.w : 0.f);
-                continue;
+#pragma unroll
+        for (int k = 0; k < kMaxEwSlots; ++k)
+            if (k < prog.n_slots && prog.load[k]) {
+                float4 a, b;
+                ld8(prog.fp[k] + base, a, b);
+                reg[(2 * k) * S] = a;
+                reg[(2 * k + 1) * S] = b;
             }
-            const float4 a = o.a >= 0 ? reg[o.a * 256] : make_float4(0.f, 0.f, 0.f, 0.f);
-            const float4 b = o.b >= 0 ? reg[o.b * 256] : make_float4(0.f, 0.f, 0.f, 0.f);
-            float4 r;
-            r.x = (bits & 1u) ? fmaf(o.gamma * a.x, b.x, fmaf(o.alpha, a.x, fmaf(o.beta, b.x, o.delta))) : 0.f;
-            r.y = (bits & 2u) ? fmaf(o.gamma * a.y, b.y, fmaf(o.alpha, a.y, fmaf(o.beta, b.y, o.delta))) : 0.f;
-            r.z = (bits & 4u) ? fmaf(o.gamma * a.z, b.z, fmaf(o.alpha, a.z, fmaf(o.beta, b.z, o.delta))) : 0.f;
-            r.w = (bits & 8u) ? fmaf(o.gamma * a.w, b.w, fmaf(o.alpha, a.w, fmaf(o.beta, b.w, o.delta))) : 0.f;
-            reg[o.dst * 256] = r;
+#pragma unroll
+        for (int i = 0; i < kMaxEwOps + 1; ++i) {
+            if (i >= prog.n_ops) break;
+            const EwOp &o = prog.op[i];
+            float4 *d = reg + 2 * o.dst * S;
+            const float4 *ra = reg + 2 * o.a * S, *rb = reg + 2 * o.b * S;
+            switch (o.kind) {
+            case kEwFill:
+                d[0] = f4_splat(o.delta);
+                d[S] = f4_splat(o.delta);
+                break;
+            case kEwAx: {
+                const float4 a0 = ra[0], a1 = ra[S];
+                d[0] = f4_fma(o.alpha, a0, f4_splat(o.delta));
+                d[S] = f4_fma(o.alpha, a1, f4_splat(o.delta));
+                break;
+            }
+            case kEwAxby: {
+                const float4 a0 = ra[0], a1 = ra[S], c0 = rb[0], c1 = rb[S];
+                d[0] = f4_fma(o.alpha, a0, f4_fma(o.beta, c0, f4_splat(o.delta)));
+                d[S] = f4_fma(o.alpha, a1, f4_fma(o.beta, c1, f4_splat(o.delta)));
+                break;
+            }
+            case kEwSum: {
+                const float4 v0 = f4_mask(b0, ra[0]), v1 = f4_mask(b1, ra[S]);
+                part += ((v0.x + v0.y) + (v0.z + v0.w)) + ((v1.x + v1.y) + (v1.z + v1.w));
+                break;
+            }
+            default: {
+                const float4 a0 = ra[0], a1 = ra[S], c0 = rb[0], c1 = rb[S];
+                const float4 r0 = f4_fma(o.alpha, a0, f4_fma(o.beta, c0, f4_splat(o.delta)));
+                const float4 r1 = f4_fma(o.alpha, a1, f4_fma(o.beta, c1, f4_splat(o.delta)));
+                d[0] = make_float4(fmaf(o.gamma * a0.x, c0.x, r0.x), fmaf(o.gamma * a0.y, c0.y, r0.y),
+                                   fmaf(o.gamma * a0.z, c0.z, r0.z), fmaf(o.gamma * a0.w, c0.w, r0.w));
+                d[S] = make_float4(fmaf(o.gamma * a1.x, c1.x, r1.x), fmaf(o.gamma * a1.y, c1.y, r1.y),
+                                   fmaf(o.gamma * a1.z, c1.z, r1.z), fmaf(o.gamma * a1.w, c1.w, r1.w));
+                break;
+            }
+            }
         }
-        for (int k = 0; k < prog.n_slots; ++k)
-            if (prog.store[k]) *reinterpret_cast<float4 *>(g.field[prog.field[k]] + base) = reg[k * 256];
+#pragma unroll
+        for (int k = 0; k < kMaxEwSlots; ++k)
+            if (k < prog.n_slots && prog.store[k])
+                st8(prog.fp[k] + base, f4_mask(b0, reg[(2 * k) * S]), f4_mask(b1, reg[(2 * k + 1) * S]));
     }
     if (prog.sum_out >= 0) {
-        const double tot = block_sum_f64<256>((double)part, s_red);
+        const double tot = block_sum_f64<kEwThreads>((double)part, s_red);
         finish_reduction(g, tot, prog.sum_out);
     }
 }
 
+// CTAs resident per SM for a program of n_slots slots (dynamic shared memory
+// 4 KB per slot), all launched at once (one reduction partial each).
 template <int L>
-static int ew_ctas(int num_sms)
+static int ew_ctas(int num_sms, int n_slots)
 {
-    static int per = 0;
-    if (!per && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_ew<L>, 256, 0) != cudaSuccess || per < 1))
-        per = 1;
-    return per * num_sms;  // all resident at once (one reduction partial each)
+    static int per[kMaxEwSlots + 1] = {};
+    const size_t smem = sizeof(float4) * 2 * kEwThreads * n_slots;
+    if (!per[n_slots] &&
+        (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per[n_slots], k_ew<L>, kEwThreads, smem) != cudaSuccess ||
+         per[n_slots] < 1))
+        per[n_slots] = 1;
+    return per[n_slots] * num_sms;
 }
 
 void launch_ew(const DevGrid &g, cudaStream_t s, const EwProgram &prog, const LaunchCfg &lc)
 {
-    if (g.L == 8) k_ew<8><<<ew_ctas<8>(lc.num_sms), 256, 0, s>>>(g, prog);
-    else k_ew<4><<<ew_ctas<4>(lc.num_sms), 256, 0, s>>>(g, prog);
+    EwProgram p = prog;
+    for (int k = 0; k < p.n_slots; ++k) p.fp[k] = g.field[p.field[k]];
+    const int ns = p.n_slots < 1 ? 1 : p.n_slots;
+    const size_t smem = sizeof(float4) * 2 * kEwThreads * ns;
+    if (g.L == 8) k_ew<8><<<ew_ctas<8>(lc.num_sms, ns), kEwThreads, smem, s>>>(g, p);
+    else k_ew<4><<<ew_ctas<4>(lc.num_sms, ns), kEwThreads, smem, s>>>(g, p);
 }
 
 }  // namespace sg

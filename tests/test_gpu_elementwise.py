@@ -113,3 +113,27 @@ def test_fused_run_stores_only_live_fields():
     for f in (1, 2, 3):
         assert rel_linf(g.read_field(f), og.read_field(f)) <= 2e-5, f
     g.close()
+
+
+DEAD = [
+    (1, 0, -1, 2.0, 0.0, 0.0, 1.0),        # y = 2x + 1: overwritten before any read (dead)
+    (1, 0, 0, 0.0, 0.0, 1.0, 0.0),         # y = x * x
+    (2, 1, 0, 1.0, 1.0, 0.0, 0.0),         # z = y + x: overwritten before any read (dead)
+    (2, -1, -1, 0.0, 0.0, 0.0, 3.0),       # z = 3
+    (4, 2, 1, 1.0, 1.0, 0.0, 0.0),         # grad = z + y
+    (1, -1, 0, 0.0, 0.5, 0.0, 0.0),        # y = 0.5 x (an op reading only its second operand)
+]
+
+
+@pytest.mark.parametrize("L", [8, 4])
+@pytest.mark.parametrize("mode", ["all", "eager"])
+def test_dead_ops_in_a_run(L, mode):
+    """Ops whose results are overwritten unread are dropped from the fused
+    run; the fields equal the oracle's op-by-op results."""
+    import paper_2012_08141_gb300 as sg
+    g, og = setup(L, sg.SG_OPT_EAGER if mode == "eager" else sg.SG_OPT_ALL)
+    run(g, DEAD)
+    oracle_run(og, DEAD)
+    for f in (0, 1, 2, 4):
+        assert rel_linf(g.read_field(f), og.read_field(f)) <= TOL, (mode, f)
+    g.close()
