@@ -1291,6 +1291,25 @@ int sg_read_structure(sg_grid *g, int64_t cap, int64_t *n_leaves, int32_t *leaf_
     return cuda_check(cudaStreamSynchronize(g->stream), "stream synchronize");
 }
 
+// The device address of a host buffer of `bytes` bytes that the device can
+// read and write in place -- page-locked, mapped into the device's address
+// space over its whole range, 16-byte aligned -- or null (then transfers go
+// through the staging buffer with cudaMemcpyAsync).
+void *mapped_host(void *host, size_t bytes)
+{
+    if (!host || bytes == 0 || ((uintptr_t)host & 15)) return nullptr;
+    cudaPointerAttributes a{}, z{};
+    if (cudaPointerGetAttributes(&a, host) != cudaSuccess ||
+        cudaPointerGetAttributes(&z, (char *)host + bytes - 1) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type != cudaMemoryTypeHost || z.type != cudaMemoryTypeHost || !a.devicePointer || !z.devicePointer ||
+        (char *)z.devicePointer != (char *)a.devicePointer + bytes - 1)
+        return nullptr;
+    return a.devicePointer;
+}
+
 int sg_read_field(sg_grid *g, int32_t f, int64_t cap, float *host_vals)
 {
     if (!g || !valid_field(g, f) || !host_vals || cap < 0) return fail(SG_ERR_INVALID, "bad arguments");
@@ -1299,11 +1318,13 @@ int sg_read_field(sg_grid *g, int32_t f, int64_t cap, float *host_vals)
     const long long n = g->host_ctrl->list_n;
     if (n > cap) return fail(SG_ERR_INVALID, "buffer holds %lld leaves, list has %lld", (long long)cap, n);
     if (n == 0) return SG_OK;
-    if ((rc = ensure_staging(g))) return rc;
-    launch_gather_field(g->dev, g->stream, g->phys[f], g->lc);
-    if ((rc = after_launch(g, "gather field"))) return rc;
     const size_t bytes = sizeof(float) * size_t(n) * g->dev.L * g->dev.L * g->dev.L;
-    if ((rc = cuda_check(cudaMemcpyAsync(host_vals, g->dev.staging, bytes, cudaMemcpyDeviceToHost, g->stream), "copy field")))
+    float *direct = (float *)mapped_host(host_vals, bytes);
+    if (!direct && (rc = ensure_staging(g))) return rc;
+    launch_gather_field(g->dev, g->stream, g->phys[f], direct, g->lc);
+    if ((rc = after_launch(g, "gather field"))) return rc;
+    if (!direct && (rc = cuda_check(cudaMemcpyAsync(host_vals, g->dev.staging, bytes, cudaMemcpyDeviceToHost, g->stream),
+                                    "copy field")))
         return rc;
     return cuda_check(cudaStreamSynchronize(g->stream), "stream synchronize");
 }
@@ -1316,11 +1337,17 @@ int sg_write_field(sg_grid *g, int32_t f, const float *host_vals, int64_t n_leav
     const long long n = g->host_ctrl->list_n;
     if (n != n_leaves) return fail(SG_ERR_INVALID, "list has %lld leaves, got %lld", n, (long long)n_leaves);
     if (n == 0) return SG_OK;
-    if ((rc = ensure_staging(g))) return rc;
     const size_t bytes = sizeof(float) * size_t(n) * g->dev.L * g->dev.L * g->dev.L;
-    if ((rc = cuda_check(cudaMemcpyAsync(g->dev.staging, host_vals, bytes, cudaMemcpyHostToDevice, g->stream), "copy field")))
-        return rc;
-    launch_scatter_field(g->dev, g->stream, g->phys[f], g->lc);
+    // a mapped pinned buffer is read by the scatter kernel in place (one pass
+    // over the host link, no staging copy)
+    const float *direct = (const float *)mapped_host(const_cast<float *>(host_vals), bytes);
+    if (!direct) {
+        if ((rc = ensure_staging(g))) return rc;
+        if ((rc = cuda_check(cudaMemcpyAsync(g->dev.staging, host_vals, bytes, cudaMemcpyHostToDevice, g->stream),
+                             "copy field")))
+            return rc;
+    }
+    launch_scatter_field(g->dev, g->stream, g->phys[f], direct, g->lc);
     if ((rc = after_launch(g, "scatter field"))) return rc;
     return cuda_check(cudaStreamSynchronize(g->stream), "stream synchronize");
 }

@@ -119,9 +119,12 @@ void launch_clear_list(const DevGrid &g, cudaStream_t s);
 void launch_region_masks(const DevGrid &g, cudaStream_t s, const LaunchCfg &lc);
 void launch_listgen(const DevGrid &g, cudaStream_t s, int force, unsigned long long call_idx,
                     int num_tiles, int test_wait);
-void launch_gather_field(const DevGrid &g, cudaStream_t s, int f, const LaunchCfg &lc);
+// Field f of the listed leaves to / from a dense list-order buffer: the
+// staging buffer when the pointer is null, else a device-addressable one
+// (16-byte aligned; e.g. mapped pinned host memory, read or written in place).
+void launch_gather_field(const DevGrid &g, cudaStream_t s, int f, float *dst, const LaunchCfg &lc);
 void launch_gather_masks(const DevGrid &g, cudaStream_t s, const LaunchCfg &lc);
-void launch_scatter_field(const DevGrid &g, cudaStream_t s, int f, const LaunchCfg &lc);
+void launch_scatter_field(const DevGrid &g, cudaStream_t s, int f, const float *src, const LaunchCfg &lc);
 
 // ---- stencil kernels (sg_stencil.cu) ----
 // check_act: eager activation-on-write check on every store (Sec. 6.3 off).

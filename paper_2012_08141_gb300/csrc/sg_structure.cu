@@ -524,12 +524,11 @@ void launch_fill_hash(const DevGrid &g, cudaStream_t s, int f, unsigned long lon
 // Host transfers: gather leaves in list order into the staging buffer, and
 // scatter from it (applying the mask so inactive voxels stay 0).
 // ---------------------------------------------------------------------------
-__global__ void k_gather_field(DevGrid g, int f)
+__global__ void k_gather_field(DevGrid g, int f, float4 *__restrict__ dst)
 {
     const long long n = g.ctrl->list_n;
     const int V4 = (g.L * g.L * g.L) >> 2;
     const float4 *src = reinterpret_cast<const float4 *>(g.field[f]);
-    float4 *dst = reinterpret_cast<float4 *>(g.staging);
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n * V4; q += (long long)gridDim.x * blockDim.x) {
         const long long e = q / V4;
         const int r = (int)(q - e * V4);
@@ -537,9 +536,9 @@ __global__ void k_gather_field(DevGrid g, int f)
     }
 }
 
-void launch_gather_field(const DevGrid &g, cudaStream_t s, int f, const LaunchCfg &lc)
+void launch_gather_field(const DevGrid &g, cudaStream_t s, int f, float *dst, const LaunchCfg &lc)
 {
-    k_gather_field<<<lc.num_sms * 4, 256, 0, s>>>(g, f);
+    k_gather_field<<<lc.num_sms * 4, 256, 0, s>>>(g, f, reinterpret_cast<float4 *>(dst ? dst : g.staging));
 }
 
 __global__ void k_gather_masks(DevGrid g)
@@ -557,11 +556,10 @@ void launch_gather_masks(const DevGrid &g, cudaStream_t s, const LaunchCfg &lc)
     k_gather_masks<<<lc.num_sms * 4, 256, 0, s>>>(g);
 }
 
-__global__ void k_scatter_field(DevGrid g, int f)
+__global__ void k_scatter_field(DevGrid g, int f, const float4 *__restrict__ src)
 {
     const long long n = g.ctrl->list_n;
     const int V4 = (g.L * g.L * g.L) >> 2;
-    const float4 *src = reinterpret_cast<const float4 *>(g.staging);
     float4 *dst = reinterpret_cast<float4 *>(g.field[f]);
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n * V4; q += (long long)gridDim.x * blockDim.x) {
         const long long e = q / V4;
@@ -578,9 +576,9 @@ __global__ void k_scatter_field(DevGrid g, int f)
     }
 }
 
-void launch_scatter_field(const DevGrid &g, cudaStream_t s, int f, const LaunchCfg &lc)
+void launch_scatter_field(const DevGrid &g, cudaStream_t s, int f, const float *src, const LaunchCfg &lc)
 {
-    k_scatter_field<<<lc.num_sms * 4, 256, 0, s>>>(g, f);
+    k_scatter_field<<<lc.num_sms * 4, 256, 0, s>>>(g, f, reinterpret_cast<const float4 *>(src ? src : g.staging));
 }
 
 }  // namespace sg
