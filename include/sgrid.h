@@ -309,13 +309,19 @@ int sg_read_structure(sg_grid *g, int64_t cap, int64_t *n_leaves, int32_t *leaf_
                       uint32_t *masks);
 
 /* Implicit sync, then copy field f to host memory in list order, L^3 values
- * per leaf, 0 at inactive voxels.  cap = leaves the buffer holds. */
+ * per leaf, 0 at inactive voxels.  cap = leaves the buffer holds.  A
+ * page-locked buffer mapped into the device's address space (16-byte
+ * aligned) is written in place by the gather kernel; any other buffer gets a
+ * staged copy. */
 int sg_read_field(sg_grid *g, int32_t f, int64_t cap, float *host_vals);
 
 /* Set field f from host memory in list order (n_leaves * L^3 FP32 values;
  * n_leaves must equal the current list length).  Values at inactive voxels
  * are ignored (stored as 0).  The copy is made before the call returns, so
- * the host buffer may be reused at once; pinned memory makes it faster. */
+ * the host buffer may be reused at once.  A page-locked buffer mapped into
+ * the device's address space (16-byte aligned) is read in place by the
+ * scatter kernel, one pass over the host link; any other buffer is first
+ * copied to a device staging buffer. */
 int sg_write_field(sg_grid *g, int32_t f, const float *host_vals, int64_t n_leaves);
 
 /* Replace the whole structure with a saved one (the restore half of a
