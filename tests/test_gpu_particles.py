@@ -260,3 +260,60 @@ def test_p2g_pool_exhaustion():
         g.sync()
     assert e.value.code == sg.SG_ERR_POOL_EXHAUSTED
     g.close()
+
+
+def _spec_from(x, v, N, L):
+    from workload import ParticleSpec
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    v = np.ascontiguousarray(v, dtype=np.float32)
+    return ParticleSpec(N, L, len(x), np.zeros((3, 3)), np.zeros(3), x, v)
+
+
+@pytest.mark.parametrize("L", [4, 8])
+def test_crowded_cells_and_boundaries(L):
+    """Degenerate particle layouts: 6,000 particles inside one cell (a bin
+    several staging chunks long), particles exactly on cell faces and leaf
+    faces (fractional offsets 0 and 0.5), and particles whose stencil lies
+    wholly outside the domain (they touch nothing)."""
+    rng = np.random.default_rng(50 + L)
+    N = 64
+    dx = 1.0 / N
+    crowd = (np.array([20.5, 9.5, 33.5]) + rng.uniform(-0.49, 0.49, size=(6000, 3))) * dx
+    faces = np.array([[i, j, k] for i in (8, 16, 31.5) for j in (0.5, 8.0, 24.0) for k in (1.0, 40.5, 63.5)]) * dx
+    faces = np.repeat(faces, 5, axis=0)
+    outside = np.array([[-0.2, 0.5, 0.5], [0.5, 1.3, 0.5], [0.5, 0.5, -0.5], [1.5, 1.5, 1.5]])
+    x = np.concatenate([crowd, faces, outside])
+    v = rng.normal(0.0, 0.1, size=x.shape)
+    one_step_compare(_spec_from(x, v, N, L), (N // L) ** 3, interior=False)
+
+
+def test_empty_particle_set_is_a_no_op():
+    import torch
+    import paper_2012_08141_gb300 as sg
+    g = sg.Grid(64, 2, 4, max_leaves=64)
+    x = torch.zeros((0, 3), dtype=torch.float32, device="cuda")
+    v = torch.zeros((0, 3), dtype=torch.float32, device="cuda")
+    l0 = g.stats()["launches"]
+    g.p2g(x, v, 1.0, 0, 1)
+    g.g2p(x, v, 1e-3, 1)
+    g.sync()
+    assert g.stats()["launches"] == l0                  # nothing queued, nothing launched
+    assert g.num_leaves() == 0
+    g.close()
+
+
+def test_particles_all_outside_activate_nothing():
+    import torch
+    import paper_2012_08141_gb300 as sg
+    x = np.array([[-0.3, 0.5, 0.5], [0.5, 1.2, 0.5], [2.0, 2.0, 2.0], [0.5, 0.5, -0.04]], dtype=np.float32)
+    v = np.zeros_like(x)
+    g = sg.Grid(64, 2, 4, max_leaves=64)
+    og = oracle.Grid(64, 4, 4)
+    g.p2g(torch.from_numpy(x).cuda(), torch.from_numpy(v).cuda(), 1.0, 0, 1)
+    og.p2g(x.copy(), v.copy(), 1.0, 0, 1)
+    gb, gm = g.read_structure()
+    ob, om = og.structure()
+    np.testing.assert_array_equal(gb, ob)
+    np.testing.assert_array_equal(gm, om)
+    assert gb.size == 0
+    g.close()
