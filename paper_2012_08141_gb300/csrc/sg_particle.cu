@@ -371,15 +371,18 @@ __global__ void __launch_bounds__(256) k_p2g_gather(DevGrid g, const float *__re
             __syncthreads();
             // pass 1: each particle's cell and its rank among the cell's particles
             int rcell[PPT], rrank[PPT], rp[PPT];
+            float rx[PPT][3];
 #pragma unroll
             for (int u = 0; u < PPT; ++u) {
                 const int q = threadIdx.x + u * 256;
                 rcell[u] = -1;
                 if (q >= cnt) continue;
                 const int p = g.perm[c0 + q];
-                const int bi = bspline(__ldg(x + 3 * (long long)p + 0), N).base;
-                const int bj = bspline(__ldg(x + 3 * (long long)p + 1), N).base;
-                const int bk = bspline(__ldg(x + 3 * (long long)p + 2), N).base;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) rx[u][a] = __ldg(x + 3 * (long long)p + a);
+                const int bi = bspline(rx[u][0], N).base;
+                const int bj = bspline(rx[u][1], N).base;
+                const int bk = bspline(rx[u][2], N).base;
                 rcell[u] = ((bi - oi + 2) * C1 + (bj - oj + 2)) * C1 + (bk - ok + 2);
                 rrank[u] = atomicAdd(&s_cnt[rcell[u]], 1);
                 rp[u] = p;
@@ -397,16 +400,16 @@ __global__ void __launch_bounds__(256) k_p2g_gather(DevGrid g, const float *__re
                 if (threadIdx.x == 0) s_start[NC] = carry;
             }
             __syncthreads();
-            // pass 2: stage the particles at their sorted positions (x and v are
-            // read again, from L1)
+            // pass 2: stage the particles at their sorted positions (x kept in
+            // registers from pass 1, v read here)
 #pragma unroll
             for (int u = 0; u < PPT; ++u) {
                 if (rcell[u] < 0) continue;
                 const int pos = s_start[rcell[u]] + rrank[u];
                 const long long p = rp[u];
-                const float fx = bspline(__ldg(x + 3 * p + 0), N).fx;
-                const float fy = bspline(__ldg(x + 3 * p + 1), N).fx;
-                const float fz = bspline(__ldg(x + 3 * p + 2), N).fx;
+                const float fx = bspline(rx[u][0], N).fx;
+                const float fy = bspline(rx[u][1], N).fx;
+                const float fz = bspline(rx[u][2], N).fx;
                 const float mv0 = pmass * __ldg(v + 3 * p + 0), mv1 = pmass * __ldg(v + 3 * p + 1),
                             mv2 = pmass * __ldg(v + 3 * p + 2);
                 s_rec[0][pos] = make_float4(fx, fy, fz, pmass);
