@@ -324,6 +324,20 @@ int sg_read_field(sg_grid *g, int32_t f, int64_t cap, float *host_vals);
  * copied to a device staging buffer. */
 int sg_write_field(sg_grid *g, int32_t f, const float *host_vals, int64_t n_leaves);
 
+/* Active-voxel ("packed") transfers of field f: only the values at active
+ * voxels, in list order and, within a leaf, ascending local index l -- the
+ * order of the set mask bits.  Implicit syncs.  A page-locked buffer mapped
+ * into the device's address space (16-byte aligned) is read or written in
+ * place by the transfer kernel; any other buffer is staged.
+ *
+ * write: n_active must equal the grid's active voxel count (else
+ * SG_ERR_INVALID, nothing written); every inactive voxel of the listed
+ * leaves is set to 0.  The host buffer may be reused when the call returns.
+ * read: *n_active receives the count; if it exceeds cap nothing is copied
+ * and SG_ERR_INVALID is returned. */
+int sg_write_field_active(sg_grid *g, int32_t f, const float *host_vals, int64_t n_active);
+int sg_read_field_active(sg_grid *g, int32_t f, int64_t cap, int64_t *n_active, float *host_vals);
+
 /* Replace the whole structure with a saved one (the restore half of a
  * checkpoint whose save half is sg_read_structure + sg_read_field): leaf_b
  * holds n_leaves root indices in strictly ascending order, each in [0, R^3),

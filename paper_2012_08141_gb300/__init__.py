@@ -110,6 +110,8 @@ def load_library(build: bool = True) -> ctypes.CDLL:
         "sg_read_field": [P, I32, I64, P],
         "sg_write_field": [P, I32, P, I64],
         "sg_write_structure": [P, I64, P, P],
+        "sg_write_field_active": [P, I32, P, I64],
+        "sg_read_field_active": [P, I32, I64, ctypes.POINTER(I64), P],
         "sg_read_sums": [P, P, I64],
         "sg_get_stats": [P, ctypes.POINTER(SgStats)],
         "sg_debug_wait_test": [P],
@@ -373,6 +375,28 @@ class Grid:
         else:
             assert not vals.is_cuda and vals.is_contiguous()
             self._c(self.lib.sg_write_field(self.h, int(f), _ptr(vals), vals.numel() // self.V))
+
+    def write_field_active(self, f: int, vals):
+        """vals: FP32 host array (numpy or torch CPU tensor, pinned is
+        fastest) of the active voxels' values, in list order and mask-bit
+        order within a leaf; inactive voxels become 0."""
+        if isinstance(vals, np.ndarray):
+            a = np.ascontiguousarray(vals, dtype=np.float32).reshape(-1)
+            self._c(self.lib.sg_write_field_active(self.h, int(f), _ptr(a), a.size))
+        else:
+            assert not vals.is_cuda and vals.is_contiguous()
+            self._c(self.lib.sg_write_field_active(self.h, int(f), _ptr(vals), vals.numel()))
+
+    def read_field_active(self, f: int, out: np.ndarray | None = None) -> np.ndarray:
+        """The active voxels' values of field f (FP32, list and mask-bit
+        order); out, if given, is a contiguous FP32 array of at least that
+        many values."""
+        if out is None:
+            out = np.empty(self.num_active(), dtype=np.float32)
+        assert out.dtype == np.float32 and out.flags.c_contiguous
+        got = ctypes.c_int64()
+        self._c(self.lib.sg_read_field_active(self.h, int(f), out.size, ctypes.byref(got), _ptr(out)))
+        return out.reshape(-1)[:got.value]
 
     def write_structure(self, leaf_b, masks):
         """Replace the structure with (leaf_b int32[n] ascending, masks

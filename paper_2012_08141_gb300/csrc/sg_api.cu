@@ -103,6 +103,8 @@ struct sg_grid {
     const void *p2g_x = nullptr;  // positions and count the order array was built for
     long long p2g_n = 0;
     unsigned long long *chk_cnt = nullptr;  // invariant-check counters (allocated at the first check)
+    long long *act_off = nullptr;           // active-voxel transfer offsets, [cap] and [cap / kOffTile + 2]
+    long long *act_tsum = nullptr;
 };
 
 namespace {
@@ -1382,6 +1384,79 @@ int sg_debug_poke(sg_grid *g, int32_t array, int64_t index, uint32_t bits)
     int rc = do_sync(g);
     if (rc) return rc;
     if ((rc = cuda_check(cudaMemcpyAsync(dst, &bits, sizeof bits, cudaMemcpyHostToDevice, g->stream), "poke")))
+        return rc;
+    return cuda_check(cudaStreamSynchronize(g->stream), "stream synchronize");
+}
+
+// Packed positions of every list entry's active voxels (a current list of n
+// entries); returns their total through *total (implicit wait).
+static int active_offsets(sg_grid *g, long long n, long long *total)
+{
+    if (!g->act_off) {
+        g->act_off = (long long *)dev_alloc(g, sizeof(long long) * size_t(g->dev.cap));
+        g->act_tsum = (long long *)dev_alloc(g, sizeof(long long) * size_t(g->dev.cap / kOffTile + 2));
+        if (!g->act_off || !g->act_tsum) return fail(SG_ERR_OOM, "transfer offsets");
+    }
+    launch_active_offsets(g->dev, g->stream, n, g->act_off, g->act_tsum);
+    int rc = after_launch(g, "active offsets");
+    if (rc) return rc;
+    const int ntiles = (int)((n + kOffTile - 1) / kOffTile);
+    if ((rc = cuda_check(cudaMemcpyAsync(total, g->act_tsum + ntiles, sizeof(long long), cudaMemcpyDeviceToHost,
+                                         g->stream),
+                         "read active total")))
+        return rc;
+    return cuda_check(cudaStreamSynchronize(g->stream), "stream synchronize");
+}
+
+int sg_write_field_active(sg_grid *g, int32_t f, const float *host_vals, int64_t n_active)
+{
+    if (!g || !valid_field(g, f) || n_active < 0 || (n_active > 0 && !host_vals))
+        return fail(SG_ERR_INVALID, "bad arguments");
+    int rc = sync_with_list(g);
+    if (rc) return rc;
+    const long long n = g->host_ctrl->list_n;
+    long long total = 0;
+    if (n > 0 && (rc = active_offsets(g, n, &total))) return rc;
+    if (total != n_active)
+        return fail(SG_ERR_INVALID, "the grid has %lld active voxels, got %lld", total, (long long)n_active);
+    if (n == 0) return SG_OK;
+    const size_t bytes = sizeof(float) * size_t(total);
+    const float *direct = total > 0 ? (const float *)mapped_host(const_cast<float *>(host_vals), bytes) : nullptr;
+    if (!direct) {
+        if ((rc = ensure_staging(g))) return rc;
+        if (bytes && (rc = cuda_check(cudaMemcpyAsync(g->dev.staging, host_vals, bytes, cudaMemcpyHostToDevice,
+                                                      g->stream),
+                                      "copy active values")))
+            return rc;
+    }
+    launch_scatter_active(g->dev, g->stream, g->phys[f], direct ? direct : g->dev.staging, g->act_off, g->act_tsum,
+                          g->lc);
+    if ((rc = after_launch(g, "scatter active"))) return rc;
+    return cuda_check(cudaStreamSynchronize(g->stream), "stream synchronize");
+}
+
+int sg_read_field_active(sg_grid *g, int32_t f, int64_t cap, int64_t *n_active, float *host_vals)
+{
+    if (!g || !valid_field(g, f) || cap < 0 || !n_active) return fail(SG_ERR_INVALID, "bad arguments");
+    int rc = sync_with_list(g);
+    if (rc) return rc;
+    const long long n = g->host_ctrl->list_n;
+    long long total = 0;
+    if (n > 0 && (rc = active_offsets(g, n, &total))) return rc;
+    *n_active = total;
+    if (total > cap) return fail(SG_ERR_INVALID, "buffer holds %lld values, the grid has %lld active voxels",
+                                 (long long)cap, total);
+    if (total == 0) return SG_OK;
+    if (!host_vals) return fail(SG_ERR_INVALID, "null buffer");
+    const size_t bytes = sizeof(float) * size_t(total);
+    float *direct = (float *)mapped_host(host_vals, bytes);
+    if (!direct && (rc = ensure_staging(g))) return rc;
+    launch_gather_active(g->dev, g->stream, g->phys[f], direct ? direct : g->dev.staging, g->act_off, g->act_tsum,
+                         g->lc);
+    if ((rc = after_launch(g, "gather active"))) return rc;
+    if (!direct && (rc = cuda_check(cudaMemcpyAsync(host_vals, g->dev.staging, bytes, cudaMemcpyDeviceToHost,
+                                                    g->stream),
+                                    "copy active values")))
         return rc;
     return cuda_check(cudaStreamSynchronize(g->stream), "stream synchronize");
 }

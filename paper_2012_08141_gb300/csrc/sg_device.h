@@ -125,6 +125,16 @@ void launch_listgen(const DevGrid &g, cudaStream_t s, int force, unsigned long l
 void launch_gather_field(const DevGrid &g, cudaStream_t s, int f, float *dst, const LaunchCfg &lc);
 void launch_gather_masks(const DevGrid &g, cudaStream_t s, const LaunchCfg &lc);
 void launch_scatter_field(const DevGrid &g, cudaStream_t s, int f, const float *src, const LaunchCfg &lc);
+// Active-voxel transfers: off[n] and tsum[n / kOffTile + 2] are scratch;
+// launch_active_offsets leaves the packed position of each list entry's first
+// active voxel in off[e] + tsum[e / kOffTile] and the total in
+// tsum[ceil(n / kOffTile)].  src / out hold exactly that many values.
+constexpr int kOffTile = 1024;
+void launch_active_offsets(const DevGrid &g, cudaStream_t s, long long n, long long *off, long long *tsum);
+void launch_scatter_active(const DevGrid &g, cudaStream_t s, int f, const float *src, const long long *off,
+                           const long long *tsum, const LaunchCfg &lc);
+void launch_gather_active(const DevGrid &g, cudaStream_t s, int f, float *out, const long long *off,
+                          const long long *tsum, const LaunchCfg &lc);
 
 // ---- stencil kernels (sg_stencil.cu) ----
 // check_act: eager activation-on-write check on every store (Sec. 6.3 off).

@@ -585,6 +585,156 @@ void launch_scatter_field(const DevGrid &g, cudaStream_t s, int f, const float *
 
 namespace sg {
 
+// ---------------------------------------------------------------------------
+// Transfers of the active voxels only ("packed": list order, ascending local
+// index within a leaf).  off[e] + tsum[e / kOffTile] is the number of active
+// voxels in the list entries before e.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kOffTile) k_active_offsets(DevGrid g, long long n, long long *off, long long *tsum)
+{
+    __shared__ long long s_w[kOffTile / 32];
+    const int lane = lane_id(), warp = threadIdx.x >> 5;
+    const long long e = (long long)blockIdx.x * kOffTile + threadIdx.x;
+    int c = 0;
+    if (e < n) {
+        const int slot = g.list_slot[e];
+        for (int w = 0; w < g.W; ++w) c += __popc(g.mask[(long long)slot * g.W + w]);
+    }
+    const int inc = warp_incl_scan(c);
+    if (lane == 31) s_w[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        const long long v = s_w[lane];
+        long long x = v;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const long long y = __shfl_up_sync(kFull, x, d);
+            if (lane >= d) x += y;
+        }
+        s_w[lane] = x - v;
+    }
+    __syncthreads();
+    const long long ex = s_w[warp] + inc - c;
+    if (e < n) off[e] = ex;
+    if (threadIdx.x == kOffTile - 1) tsum[blockIdx.x] = ex + c;
+}
+
+// Exclusive scan of the tile totals by one CTA, in place; the grand total
+// goes to tsum[ntiles].
+__global__ void __launch_bounds__(1024) k_active_offsets_top(long long *tsum, int ntiles)
+{
+    __shared__ long long s_w[32];
+    __shared__ long long s_carry;
+    const int lane = lane_id(), warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    for (int base = 0; base < ntiles; base += 1024) {
+        const int i = base + threadIdx.x;
+        const long long v = (i < ntiles) ? tsum[i] : 0;
+        long long x = v;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const long long y = __shfl_up_sync(kFull, x, d);
+            if (lane >= d) x += y;
+        }
+        if (lane == 31) s_w[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            const long long wv = s_w[lane];
+            long long z = wv;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const long long y = __shfl_up_sync(kFull, z, d);
+                if (lane >= d) z += y;
+            }
+            s_w[lane] = z - wv;
+        }
+        __syncthreads();
+        const long long ex = s_carry + s_w[warp] + x - v;
+        __syncthreads();
+        if (i < ntiles) tsum[i] = ex;
+        if (threadIdx.x == 1023) s_carry = ex + v;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) tsum[ntiles] = s_carry;
+}
+
+void launch_active_offsets(const DevGrid &g, cudaStream_t s, long long n, long long *off, long long *tsum)
+{
+    const int ntiles = (int)((n + kOffTile - 1) / kOffTile);
+    k_active_offsets<<<ntiles, kOffTile, 0, s>>>(g, n, off, tsum);
+    k_active_offsets_top<<<1, 1024, 0, s>>>(tsum, ntiles);
+}
+
+// Position in the packed array of the first active voxel at or after local
+// index 4r of list entry e (slot `slot`).
+__device__ __forceinline__ long long packed_pos(const DevGrid &g, long long e, int slot, int r, const long long *off,
+                                                const long long *tsum, uint32_t &word, int &sh)
+{
+    const uint32_t *mw = g.mask + (long long)slot * g.W;
+    const int w = r >> 3;
+    sh = (r & 7) * 4;
+    long long pos = off[e] + tsum[e / kOffTile];
+    for (int i = 0; i < w; ++i) pos += __popc(mw[i]);
+    word = mw[w];
+    return pos + __popc(word & ((1u << sh) - 1u));
+}
+
+__global__ void k_scatter_active(DevGrid g, int f, const float *__restrict__ src, const long long *__restrict__ off,
+                                 const long long *__restrict__ tsum)
+{
+    const long long n = g.ctrl->list_n;
+    const int V4 = (g.L * g.L * g.L) >> 2;
+    float4 *dst = reinterpret_cast<float4 *>(g.field[f]);
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n * V4; q += (long long)gridDim.x * blockDim.x) {
+        const long long e = q / V4;
+        const int r = (int)(q - e * V4);
+        const int slot = g.list_slot[e];
+        uint32_t word;
+        int sh;
+        long long pos = packed_pos(g, e, slot, r, off, tsum, word, sh);
+        float4 v;
+        v.x = ((word >> (sh + 0)) & 1u) ? src[pos++] : 0.f;
+        v.y = ((word >> (sh + 1)) & 1u) ? src[pos++] : 0.f;
+        v.z = ((word >> (sh + 2)) & 1u) ? src[pos++] : 0.f;
+        v.w = ((word >> (sh + 3)) & 1u) ? src[pos] : 0.f;
+        dst[(long long)slot * V4 + r] = v;
+    }
+}
+
+__global__ void k_gather_active(DevGrid g, int f, float *__restrict__ out, const long long *__restrict__ off,
+                                const long long *__restrict__ tsum)
+{
+    const long long n = g.ctrl->list_n;
+    const int V4 = (g.L * g.L * g.L) >> 2;
+    const float4 *src = reinterpret_cast<const float4 *>(g.field[f]);
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n * V4; q += (long long)gridDim.x * blockDim.x) {
+        const long long e = q / V4;
+        const int r = (int)(q - e * V4);
+        const int slot = g.list_slot[e];
+        uint32_t word;
+        int sh;
+        long long pos = packed_pos(g, e, slot, r, off, tsum, word, sh);
+        const float4 v = src[(long long)slot * V4 + r];
+        if ((word >> (sh + 0)) & 1u) out[pos++] = v.x;
+        if ((word >> (sh + 1)) & 1u) out[pos++] = v.y;
+        if ((word >> (sh + 2)) & 1u) out[pos++] = v.z;
+        if ((word >> (sh + 3)) & 1u) out[pos] = v.w;
+    }
+}
+
+void launch_scatter_active(const DevGrid &g, cudaStream_t s, int f, const float *src, const long long *off,
+                           const long long *tsum, const LaunchCfg &lc)
+{
+    k_scatter_active<<<lc.num_sms * 4, 256, 0, s>>>(g, f, src, off, tsum);
+}
+
+void launch_gather_active(const DevGrid &g, cudaStream_t s, int f, float *out, const long long *off,
+                          const long long *tsum, const LaunchCfg &lc)
+{
+    k_gather_active<<<lc.num_sms * 4, 256, 0, s>>>(g, f, out, off, tsum);
+}
+
 // Active voxels of the listed leaves: popcount of their mask words.
 __global__ void k_count_active(DevGrid g)
 {

@@ -197,3 +197,63 @@ def test_pinned_transfers_equal_pageable(L):
     g.write_field(1, shifted[1:])                           # 4-byte aligned view: staged
     np.testing.assert_array_equal(g.read_field(0), g.read_field(1))
     g.close()
+
+
+def _bits(m, V):
+    n = m.shape[0]
+    return np.unpackbits(m.view(np.uint8), bitorder="little").reshape(n, V).astype(bool)
+
+
+@pytest.mark.parametrize("L", [8, 4])
+def test_active_value_transfers(L):
+    """Writes and reads of the active voxels only (list order, then mask-bit
+    order) agree bit-exactly with the dense transfers, through pageable and
+    mapped pinned buffers; a wrong count is refused."""
+    import torch
+    import paper_2012_08141_gb300 as sg
+    spec = tiny_shell(7, N=64, L=L)
+    g = sg.Grid(64, int(np.log2(L)), 2, max_leaves=(64 // L) ** 3)
+    g.activate_shell(spec.lo2, spec.hi2, spec.lo_strict)
+    b, m = g.read_structure()
+    vals = leaf_values(7, 64, L, b)
+    packed = vals[_bits(m, g.V)]
+    assert packed.size == g.num_active()
+    g.write_field_active(0, packed)                     # pageable: staged
+    g.write_field(1, vals)
+    np.testing.assert_array_equal(g.read_field(0), g.read_field(1))
+    np.testing.assert_array_equal(g.read_field_active(0), packed)
+    pin = torch.from_numpy(packed).pin_memory()
+    g.fill_hash(0, 3)
+    g.write_field_active(0, pin)                        # pinned: read in place
+    np.testing.assert_array_equal(g.read_field(0), g.read_field(1))
+    out = torch.zeros(packed.size, dtype=torch.float32).pin_memory()
+    np.testing.assert_array_equal(g.read_field_active(1, out=out.numpy()), packed)
+    with pytest.raises(sg.SgError) as e:
+        g.write_field_active(0, packed[:-1])
+    assert e.value.code == sg.SG_ERR_INVALID
+    with pytest.raises(sg.SgError):
+        g.read_field_active(0, out=np.empty(packed.size - 1, np.float32))
+    np.testing.assert_array_equal(g.read_field(0), g.read_field(1))   # the refused write changed nothing
+    g.close()
+
+
+def test_active_value_transfers_band512_and_empty():
+    """26,104 leaves (26 scan tiles): the packed read equals the dense read at
+    the set bits; an empty grid transfers nothing."""
+    import paper_2012_08141_gb300 as sg
+    from workload import band512
+    spec = band512()
+    g = sg.Grid(512, 3, 1, max_leaves=32768)
+    g.activate_shell(spec.lo2, spec.hi2, spec.lo_strict)
+    g.fill_hash(0, 23)
+    b, m = g.read_structure()
+    packed = g.read_field_active(0)
+    assert packed.size == 8047608
+    np.testing.assert_array_equal(packed, g.read_field(0)[_bits(m, g.V)])
+    g.write_field_active(0, packed[::-1].copy())
+    np.testing.assert_array_equal(g.read_field_active(0), packed[::-1])
+    g.close()
+    e = sg.Grid(64, 3, 1, max_leaves=8)
+    assert e.read_field_active(0).size == 0
+    e.write_field_active(0, np.zeros(0, np.float32))
+    e.close()
