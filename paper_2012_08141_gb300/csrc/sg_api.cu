@@ -105,6 +105,8 @@ struct sg_grid {
     unsigned long long *chk_cnt = nullptr;  // invariant-check counters (allocated at the first check)
     long long *act_off = nullptr;           // active-voxel transfer offsets, [cap] and [cap / kOffTile + 2]
     long long *act_tsum = nullptr;
+    unsigned long long act_ver = 0;         // list version the offsets were computed for (0 = never)
+    long long act_total = 0;
 };
 
 namespace {
@@ -1389,9 +1391,16 @@ int sg_debug_poke(sg_grid *g, int32_t array, int64_t index, uint32_t bits)
 }
 
 // Packed positions of every list entry's active voxels (a current list of n
-// entries); returns their total through *total (implicit wait).
+// entries); returns their total through *total (implicit wait).  Kept while
+// the structure is unchanged: the list version keys them.
 static int active_offsets(sg_grid *g, long long n, long long *total)
 {
+    // reused while no activation has touched the structure since (the list
+    // is current and the device dirty flag, read at the last sync, is clear)
+    if (g->act_ver == g->list_ver && g->act_ver != 0 && g->host_ctrl->dirty == 0) {
+        *total = g->act_total;
+        return SG_OK;
+    }
     if (!g->act_off) {
         g->act_off = (long long *)dev_alloc(g, sizeof(long long) * size_t(g->dev.cap));
         g->act_tsum = (long long *)dev_alloc(g, sizeof(long long) * size_t(g->dev.cap / kOffTile + 2));
@@ -1403,9 +1412,12 @@ static int active_offsets(sg_grid *g, long long n, long long *total)
     const int ntiles = (int)((n + kOffTile - 1) / kOffTile);
     if ((rc = cuda_check(cudaMemcpyAsync(total, g->act_tsum + ntiles, sizeof(long long), cudaMemcpyDeviceToHost,
                                          g->stream),
-                         "read active total")))
+                         "read active total")) ||
+        (rc = cuda_check(cudaStreamSynchronize(g->stream), "stream synchronize")))
         return rc;
-    return cuda_check(cudaStreamSynchronize(g->stream), "stream synchronize");
+    g->act_ver = g->list_ver;
+    g->act_total = *total;
+    return SG_OK;
 }
 
 int sg_write_field_active(sg_grid *g, int32_t f, const float *host_vals, int64_t n_active)
@@ -1429,8 +1441,8 @@ int sg_write_field_active(sg_grid *g, int32_t f, const float *host_vals, int64_t
                                       "copy active values")))
             return rc;
     }
-    launch_scatter_active(g->dev, g->stream, g->phys[f], direct ? direct : g->dev.staging, g->act_off, g->act_tsum,
-                          g->lc);
+    launch_scatter_active(g->dev, g->stream, g->phys[f], direct ? direct : g->dev.staging, total, g->act_off,
+                          g->act_tsum, g->lc);
     if ((rc = after_launch(g, "scatter active"))) return rc;
     return cuda_check(cudaStreamSynchronize(g->stream), "stream synchronize");
 }
@@ -1451,8 +1463,8 @@ int sg_read_field_active(sg_grid *g, int32_t f, int64_t cap, int64_t *n_active, 
     const size_t bytes = sizeof(float) * size_t(total);
     float *direct = (float *)mapped_host(host_vals, bytes);
     if (!direct && (rc = ensure_staging(g))) return rc;
-    launch_gather_active(g->dev, g->stream, g->phys[f], direct ? direct : g->dev.staging, g->act_off, g->act_tsum,
-                         g->lc);
+    launch_gather_active(g->dev, g->stream, g->phys[f], direct ? direct : g->dev.staging, total, g->act_off,
+                         g->act_tsum, g->lc);
     if ((rc = after_launch(g, "gather active"))) return rc;
     if (!direct && (rc = cuda_check(cudaMemcpyAsync(host_vals, g->dev.staging, bytes, cudaMemcpyDeviceToHost,
                                                     g->stream),

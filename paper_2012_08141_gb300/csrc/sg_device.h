@@ -131,9 +131,9 @@ void launch_scatter_field(const DevGrid &g, cudaStream_t s, int f, const float *
 // tsum[ceil(n / kOffTile)].  src / out hold exactly that many values.
 constexpr int kOffTile = 1024;
 void launch_active_offsets(const DevGrid &g, cudaStream_t s, long long n, long long *off, long long *tsum);
-void launch_scatter_active(const DevGrid &g, cudaStream_t s, int f, const float *src, const long long *off,
-                           const long long *tsum, const LaunchCfg &lc);
-void launch_gather_active(const DevGrid &g, cudaStream_t s, int f, float *out, const long long *off,
+void launch_scatter_active(const DevGrid &g, cudaStream_t s, int f, const float *src, long long total,
+                           const long long *off, const long long *tsum, const LaunchCfg &lc);
+void launch_gather_active(const DevGrid &g, cudaStream_t s, int f, float *out, long long total, const long long *off,
                           const long long *tsum, const LaunchCfg &lc);
 
 // ---- stencil kernels (sg_stencil.cu) ----

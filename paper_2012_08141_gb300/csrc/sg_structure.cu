@@ -680,8 +680,11 @@ __device__ __forceinline__ long long packed_pos(const DevGrid &g, long long e, i
     return pos + __popc(word & ((1u << sh) - 1u));
 }
 
-__global__ void k_scatter_active(DevGrid g, int f, const float *__restrict__ src, const long long *__restrict__ off,
-                                 const long long *__restrict__ tsum)
+// Positions at or past `total` (the packed buffer's length) are never
+// accessed, so a buffer of exactly `total` values is read in bounds whatever
+// the masks hold.
+__global__ void k_scatter_active(DevGrid g, int f, const float *__restrict__ src, long long total,
+                                 const long long *__restrict__ off, const long long *__restrict__ tsum)
 {
     const long long n = g.ctrl->list_n;
     const int V4 = (g.L * g.L * g.L) >> 2;
@@ -694,16 +697,16 @@ __global__ void k_scatter_active(DevGrid g, int f, const float *__restrict__ src
         int sh;
         long long pos = packed_pos(g, e, slot, r, off, tsum, word, sh);
         float4 v;
-        v.x = ((word >> (sh + 0)) & 1u) ? src[pos++] : 0.f;
-        v.y = ((word >> (sh + 1)) & 1u) ? src[pos++] : 0.f;
-        v.z = ((word >> (sh + 2)) & 1u) ? src[pos++] : 0.f;
-        v.w = ((word >> (sh + 3)) & 1u) ? src[pos] : 0.f;
+        v.x = ((word >> (sh + 0)) & 1u) && pos < total ? src[pos++] : 0.f;
+        v.y = ((word >> (sh + 1)) & 1u) && pos < total ? src[pos++] : 0.f;
+        v.z = ((word >> (sh + 2)) & 1u) && pos < total ? src[pos++] : 0.f;
+        v.w = ((word >> (sh + 3)) & 1u) && pos < total ? src[pos] : 0.f;
         dst[(long long)slot * V4 + r] = v;
     }
 }
 
-__global__ void k_gather_active(DevGrid g, int f, float *__restrict__ out, const long long *__restrict__ off,
-                                const long long *__restrict__ tsum)
+__global__ void k_gather_active(DevGrid g, int f, float *__restrict__ out, long long total,
+                                const long long *__restrict__ off, const long long *__restrict__ tsum)
 {
     const long long n = g.ctrl->list_n;
     const int V4 = (g.L * g.L * g.L) >> 2;
@@ -716,23 +719,23 @@ __global__ void k_gather_active(DevGrid g, int f, float *__restrict__ out, const
         int sh;
         long long pos = packed_pos(g, e, slot, r, off, tsum, word, sh);
         const float4 v = src[(long long)slot * V4 + r];
-        if ((word >> (sh + 0)) & 1u) out[pos++] = v.x;
-        if ((word >> (sh + 1)) & 1u) out[pos++] = v.y;
-        if ((word >> (sh + 2)) & 1u) out[pos++] = v.z;
-        if ((word >> (sh + 3)) & 1u) out[pos] = v.w;
+        if (((word >> (sh + 0)) & 1u) && pos < total) out[pos++] = v.x;
+        if (((word >> (sh + 1)) & 1u) && pos < total) out[pos++] = v.y;
+        if (((word >> (sh + 2)) & 1u) && pos < total) out[pos++] = v.z;
+        if (((word >> (sh + 3)) & 1u) && pos < total) out[pos] = v.w;
     }
 }
 
-void launch_scatter_active(const DevGrid &g, cudaStream_t s, int f, const float *src, const long long *off,
-                           const long long *tsum, const LaunchCfg &lc)
+void launch_scatter_active(const DevGrid &g, cudaStream_t s, int f, const float *src, long long total,
+                           const long long *off, const long long *tsum, const LaunchCfg &lc)
 {
-    k_scatter_active<<<lc.num_sms * 4, 256, 0, s>>>(g, f, src, off, tsum);
+    k_scatter_active<<<lc.num_sms * 4, 256, 0, s>>>(g, f, src, total, off, tsum);
 }
 
-void launch_gather_active(const DevGrid &g, cudaStream_t s, int f, float *out, const long long *off,
+void launch_gather_active(const DevGrid &g, cudaStream_t s, int f, float *out, long long total, const long long *off,
                           const long long *tsum, const LaunchCfg &lc)
 {
-    k_gather_active<<<lc.num_sms * 4, 256, 0, s>>>(g, f, out, off, tsum);
+    k_gather_active<<<lc.num_sms * 4, 256, 0, s>>>(g, f, out, total, off, tsum);
 }
 
 // Active voxels of the listed leaves: popcount of their mask words.

@@ -234,6 +234,17 @@ def test_active_value_transfers(L):
     with pytest.raises(sg.SgError):
         g.read_field_active(0, out=np.empty(packed.size - 1, np.float32))
     np.testing.assert_array_equal(g.read_field(0), g.read_field(1))   # the refused write changed nothing
+    # the structure changes: the packed order follows it
+    g.activate_coords(torch.tensor([[0, 0, 0], [63, 63, 63], [31, 32, 33]], dtype=torch.int32).cuda())
+    b2, m2 = g.read_structure()
+    assert g.num_active() > packed.size
+    with pytest.raises(sg.SgError):
+        g.write_field_active(0, packed)
+    dense = leaf_values(8, 64, L, b2)
+    g.write_field(1, dense)
+    np.testing.assert_array_equal(g.read_field_active(1), dense[_bits(m2, g.V)])
+    g.write_field_active(0, dense[_bits(m2, g.V)])
+    np.testing.assert_array_equal(g.read_field(0), g.read_field(1))
     g.close()
 
 
