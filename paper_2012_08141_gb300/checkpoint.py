@@ -1,12 +1,15 @@
 """Checkpoint and restore of a grid, in one .npz file: the structure (the root
 indices of the allocated leaves, ascending, and their voxel masks) and the
-chosen fields in list order.
+chosen fields' values at the active voxels (list order, mask-bit order within
+a leaf; inactive voxels hold 0 by the library's invariant, so nothing else is
+stored).
 
-Saving is sg_read_structure + sg_read_field; restoring is sg_write_structure
-+ sg_write_field.  Leaf slots are handed out in the saved order, so a restored
-grid lists the same leaves in the same order and holds bit-identical values;
-time stepping continued from it gives the same fields as the original grid.
-The paper has no checkpointing; the format is this library's own.
+Saving is sg_read_structure + sg_read_field_active; restoring is
+sg_write_structure + sg_write_field_active.  Leaf slots are handed out in the
+saved order, so a restored grid lists the same leaves in the same order and
+holds bit-identical values; time stepping continued from it gives the same
+fields as the original grid.  The paper has no checkpointing; the format is
+this library's own.
 """
 from __future__ import annotations
 
@@ -24,9 +27,11 @@ def save(grid: Grid, path: str | os.PathLike, fields=None) -> None:
     fields hold no defined values and are best left out) to path (.npz)."""
     leaf_b, masks = grid.read_structure()
     ids = list(range(grid.n_fields)) if fields is None else [int(f) for f in fields]
-    vals = np.empty((len(ids), leaf_b.size, grid.V), dtype=np.float32)
+    n_active = int(np.unpackbits(masks.view(np.uint8)).sum())
+    vals = np.empty((len(ids), n_active), dtype=np.float32)
     for i, f in enumerate(ids):
-        grid.read_field(f, out=vals[i])
+        got = grid.read_field_active(f, out=vals[i])
+        assert got.size == n_active
     np.savez(path, format=np.int64(FORMAT), res=np.int64(grid.res), leaf_log2=np.int64(grid.leaf_log2),
              n_fields=np.int64(grid.n_fields), max_leaves=np.int64(grid.max_leaves), leaf_b=leaf_b, masks=masks,
              field_ids=np.asarray(ids, dtype=np.int64), fields=vals)
@@ -50,7 +55,7 @@ def restore(grid: Grid, path: str | os.PathLike) -> None:
         raise ValueError(f"checkpoint holds field {max(ids)}, the grid has {grid.n_fields}")
     grid.write_structure(ck["leaf_b"], ck["masks"])
     for i, f in enumerate(ids):
-        grid.write_field(f, ck["fields"][i])
+        grid.write_field_active(f, ck["fields"][i])
 
 
 def load(path: str | os.PathLike, **grid_kwargs) -> Grid:
