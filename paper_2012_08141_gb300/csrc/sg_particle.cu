@@ -346,6 +346,8 @@ __global__ void __launch_bounds__(256) k_p2g_gather(DevGrid g, const float *__re
     __shared__ uint8_t s_hit[NB];
     __shared__ int s_cnt[NC + 1];
     __shared__ int s_start[NC + 1];
+    __shared__ int s_occ[NC];  // the chunk's occupied cells, ascending
+    __shared__ int s_nocc;
     const int N = g.N, R = g.R;
     const float dx = 1.f / (float)N;
     const int warp = threadIdx.x >> 5, lane = lane_id();
@@ -388,16 +390,22 @@ __global__ void __launch_bounds__(256) k_p2g_gather(DevGrid g, const float *__re
                 rp[u] = p;
             }
             __syncthreads();
-            if (threadIdx.x < 32) {  // exclusive scan of the cell counts
-                int carry = 0;
+            if (threadIdx.x < 32) {  // exclusive scan of the cell counts; occupied cells listed
+                int carry = 0, occ = 0;
                 for (int base = 0; base < NC; base += 32) {
                     const int i = base + threadIdx.x;
                     const int vv = (i < NC) ? s_cnt[i] : 0;
                     const int inc = warp_incl_scan(vv);
                     if (i < NC) s_start[i] = carry + inc - vv;
                     carry += __shfl_sync(kFull, inc, 31);
+                    const unsigned m = __ballot_sync(kFull, vv > 0);
+                    if (vv > 0) s_occ[occ + __popc(m & lanemask_lt())] = i;
+                    occ += __popc(m);
                 }
-                if (threadIdx.x == 0) s_start[NC] = carry;
+                if (threadIdx.x == 0) {
+                    s_start[NC] = carry;
+                    s_nocc = occ;
+                }
             }
             __syncthreads();
             // pass 2: stage the particles at their sorted positions (x kept in
@@ -430,9 +438,10 @@ __global__ void __launch_bounds__(256) k_p2g_gather(DevGrid g, const float *__re
                 g.perm[c0 + pos] = rp[u];  // the chunk's order becomes cell order (G2P reads it)
             }
             __syncthreads();
-            for (int cell = warp; cell < NC; cell += NWARP) {
+            const int nocc = s_nocc;
+            for (int oc = warp; oc < nocc; oc += NWARP) {
+                const int cell = s_occ[oc];
                 const int p0 = s_start[cell], p1 = s_start[cell + 1];
-                if (p0 == p1) continue;  // uniform across the warp
                 const int ci = cell / (C1 * C1), cj = (cell / C1) % C1, ck = cell % C1;
                 float m = 0.f, m0 = 0.f, m1 = 0.f, m2 = 0.f;
                 for (int pp = p0; pp < p1; ++pp) {
