@@ -337,7 +337,7 @@ __global__ void __launch_bounds__(256) k_p2g_gather(DevGrid g, const float *__re
 {
     constexpr int B = L + 2, NB = B * B * B, LG2 = (L == 8) ? 3 : 2;
     constexpr int C1 = L + 2, NC = C1 * C1 * C1;  // shifted base cells
-    constexpr int CAP = (L == 8) ? 256 : 512;       // staged particles per chunk
+    constexpr int CAP = (L == 8) ? 256 : (APIC ? 512 : 1024);  // staged particles per chunk
     constexpr int PPT = CAP / 256;                  // staged particles per thread
     constexpr int NREC = APIC ? 4 : 2;              // float4 records per particle
     constexpr int NWARP = 8;
