@@ -117,6 +117,8 @@ typedef struct sg_stats {
     int64_t flushes;
     double bytes_model;      /* algorithmic HBM bytes of the launched stencil,
                                 clear and reduction kernels (whole leaves) */
+    int64_t bounds_reused;   /* MacCormack corrections (per channel) that read the
+                                clamp bounds their forward advection stored */
 } sg_stats;
 
 typedef struct sg_grid sg_grid; /* opaque; owned by the library */

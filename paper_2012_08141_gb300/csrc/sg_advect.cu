@@ -30,6 +30,11 @@ struct AdvectArgs {
     int qtil[kMaxAdvectChannels];     // mac: q~ (fused: its output, -1 = not stored)
     int v0;                           // velocity fields v0 .. v0+2
     float h;                          // dt * N (the forward step)
+    // clamp bounds of the correction, per channel: written by an advection
+    // (the min and max of the 8 values its sample reads) and read by the
+    // correction of the same q, velocity and step instead of tracing again
+    float *lo[kMaxAdvectChannels];
+    float *hi[kMaxAdvectChannels];
 };
 
 // Slot of the leaf holding cell (ci, cj, ck), relative to the list entry's
@@ -133,10 +138,13 @@ __device__ __forceinline__ void backtrace(const DevGrid &g, const int32_t *nb, i
                cr);
 }
 
-// MODE 0: advect (dst = src at the backtrace over h);
+// MODE 0: advect (dst = src at the backtrace over h); with BND the clamp
+//         bounds of each channel's sample are stored in A.lo / A.hi;
 // MODE 1: backward advect of q^ over -h fused with the correction;
 // MODE 2: correction alone (q~ read from its field).
-template <int L, int C, int MODE>
+// In modes 1 and 2, BND reads the clamp bounds from A.lo / A.hi instead of
+// tracing the forward path again.
+template <int L, int C, int MODE, bool BND>
 __global__ void __launch_bounds__(256) k_advect(DevGrid g, AdvectArgs A)
 {
     constexpr int V = L * L * L, LG2 = (L == 8) ? 3 : 2;
@@ -164,10 +172,30 @@ __global__ void __launch_bounds__(256) k_advect(DevGrid g, AdvectArgs A)
                             (float)((bj << LG2) + ((l >> LG2) & (L - 1))) + 0.5f,
                             (float)((bk << LG2) + (l & (L - 1))) + 0.5f};
         Corners<L> fw;
-        backtrace<L>(g, nb, bi, bj, bk, A.v0, A.h, x, idx, fw);
+        if (MODE == 0 || !BND) backtrace<L>(g, nb, bi, bj, bk, A.v0, A.h, x, idx, fw);
         if (MODE == 0) {
 #pragma unroll
-            for (int c = 0; c < C; ++c) g.field[A.dst[c]][idx] = sample<L>(g.field[A.src[c]], fw);
+            for (int c = 0; c < C; ++c) {
+                const float *sf = g.field[A.src[c]];
+                if (!BND) {
+                    g.field[A.dst[c]][idx] = sample<L>(sf, fw);
+                    continue;
+                }
+                float v[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) v[k] = __ldg(sf + fw.off[k]);
+                float smp = 0.f, lo = v[0], hi = v[0];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) smp = fmaf(fw.w[k], v[k], smp);  // the order of sample()
+#pragma unroll
+                for (int k = 1; k < 8; ++k) {
+                    lo = fminf(lo, v[k]);
+                    hi = fmaxf(hi, v[k]);
+                }
+                g.field[A.dst[c]][idx] = smp;
+                A.lo[c][idx] = lo;
+                A.hi[c][idx] = hi;
+            }
             continue;
         }
         float qt[C];
@@ -186,12 +214,19 @@ __global__ void __launch_bounds__(256) k_advect(DevGrid g, AdvectArgs A)
 #pragma unroll
         for (int c = 0; c < C; ++c) {
             const float *qf = g.field[A.src[c]];
-            float lo = __ldg(qf + fw.off[0]), hi = lo;
+            float lo, hi;
+            if (BND) {
+                lo = A.lo[c][idx];
+                hi = A.hi[c][idx];
+            } else {
+                lo = __ldg(qf + fw.off[0]);
+                hi = lo;
 #pragma unroll
-            for (int k = 1; k < 8; ++k) {
-                const float v = __ldg(qf + fw.off[k]);
-                lo = fminf(lo, v);
-                hi = fmaxf(hi, v);
+                for (int k = 1; k < 8; ++k) {
+                    const float v = __ldg(qf + fw.off[k]);
+                    lo = fminf(lo, v);
+                    hi = fmaxf(hi, v);
+                }
             }
             const float r = g.field[A.qhat[c]][idx] + 0.5f * (qf[idx] - qt[c]);
             g.field[A.dst[c]][idx] = fminf(fmaxf(r, lo), hi);
@@ -199,18 +234,26 @@ __global__ void __launch_bounds__(256) k_advect(DevGrid g, AdvectArgs A)
     }
 }
 
+template <int L, int MODE, bool BND>
+void launch_LB(const DevGrid &g, cudaStream_t s, const AdvectArgs &a, int ctas)
+{
+    if (a.C == 1) k_advect<L, 1, MODE, BND><<<ctas, 256, 0, s>>>(g, a);
+    else if (a.C == 2) k_advect<L, 2, MODE, BND><<<ctas, 256, 0, s>>>(g, a);
+    else k_advect<L, 3, MODE, BND><<<ctas, 256, 0, s>>>(g, a);
+}
+
 template <int L, int MODE>
 void launch_L(const DevGrid &g, cudaStream_t s, const AdvectArgs &a, int ctas)
 {
-    if (a.C == 1) k_advect<L, 1, MODE><<<ctas, 256, 0, s>>>(g, a);
-    else if (a.C == 2) k_advect<L, 2, MODE><<<ctas, 256, 0, s>>>(g, a);
-    else k_advect<L, 3, MODE><<<ctas, 256, 0, s>>>(g, a);
+    if (a.lo[0]) launch_LB<L, MODE, true>(g, s, a, ctas);
+    else launch_LB<L, MODE, false>(g, s, a, ctas);
 }
 
 }  // namespace
 
 void launch_advect_group(const DevGrid &g, cudaStream_t s, int mode, int C, const int *dst, const int *src,
-                         const int *qhat, const int *qtil, int v0, float h, const LaunchCfg &lc)
+                         const int *qhat, const int *qtil, int v0, float h, float *const *lo, float *const *hi,
+                         const LaunchCfg &lc)
 {
     AdvectArgs a{};
     a.C = C;
@@ -219,6 +262,8 @@ void launch_advect_group(const DevGrid &g, cudaStream_t s, int mode, int C, cons
         a.src[c] = src[c];
         a.qhat[c] = qhat ? qhat[c] : -1;
         a.qtil[c] = qtil ? qtil[c] : -1;
+        a.lo[c] = lo ? lo[c] : nullptr;
+        a.hi[c] = hi ? hi[c] : nullptr;
     }
     a.v0 = v0;
     a.h = h;

@@ -107,6 +107,7 @@ struct sg_grid {
     long long *act_tsum = nullptr;
     unsigned long long act_ver = 0;         // list version the offsets were computed for (0 = never)
     long long act_total = 0;
+    float *adv_lo[3] = {}, *adv_hi[3] = {}; // advection clamp bounds, (cap + 1) * L^3 each (allocated at first use)
 };
 
 namespace {
@@ -457,6 +458,30 @@ int run_advect_run(sg_grid *g, size_t &i)
             if (!done[a] && a != except) return false;
         return true;
     };
+    // Clamp-bound reuse (with fusion): a forward advection whose q, velocity
+    // and step a later correction of the run shares stores the min and max of
+    // the values its samples read, and the correction reads them instead of
+    // tracing the same path again -- provided no op of the run writes q or the
+    // velocity.  slot_q[s] etc. describe what bound slot s holds.
+    std::vector<int> run_writes;
+    for (int a = 0; a < n; ++a) run_writes.insert(run_writes.end(), W[a].begin(), W[a].end());
+    auto untouched = [&](int q, int v0) {
+        for (int f : run_writes)
+            if (f == q || (f >= v0 && f <= v0 + 2)) return false;
+        return true;
+    };
+    int slot_q[3] = {-1, -1, -1}, slot_v0[3] = {-1, -1, -1};
+    float slot_dt[3] = {0.f, 0.f, 0.f};
+    auto ensure_bounds = [&]() -> int {
+        if (g->dry || g->adv_lo[0]) return SG_OK;
+        const size_t bytes = sizeof(float) * size_t(g->dev.cap + 1) * g->dev.L * g->dev.L * g->dev.L;
+        for (int c = 0; c < 3; ++c) {
+            g->adv_lo[c] = (float *)dev_alloc(g, bytes);
+            g->adv_hi[c] = (float *)dev_alloc(g, bytes);
+            if (!g->adv_lo[c] || !g->adv_hi[c]) return fail(SG_ERR_OOM, "advection bounds");
+        }
+        return SG_OK;
+    };
     auto launch = [&](int mode, const std::vector<int> &ops, const std::vector<int> &macs) -> int {
         int r2;
         if ((r2 = ensure_list(g))) return r2;
@@ -489,7 +514,49 @@ int run_advect_run(sg_grid *g, size_t &i)
             }
         }
         const float h = (mode == 1 ? g->queue[i + macs[0]].f0 : f.f0) * (float)g->dev.N;
-        if (!g->dry) launch_advect_group(g->dev, g->stream, mode, C, dst, src, qh, qt, f.i0, h, g->lc);
+        const float dt = mode == 1 ? g->queue[i + macs[0]].f0 : f.f0;
+        float *lo[3] = {nullptr, nullptr, nullptr}, *hi[3] = {nullptr, nullptr, nullptr};
+        bool bnd = false;
+        if (fuse && mode == 0) {  // store bounds if a later correction can use them
+            for (int c = 0; c < C && !bnd; ++c)
+                for (int m = 0; m < n; ++m) {
+                    const Op &mc = g->queue[i + m];
+                    if (!done[m] && mc.kind == OP_MAC && mc.src == src[c] && mc.i0 == f.i0 && mc.f0 == dt &&
+                        untouched(src[c], f.i0)) {
+                        bnd = true;
+                        break;
+                    }
+                }
+            if (bnd) {
+                if ((r2 = ensure_bounds())) return r2;
+                for (int c = 0; c < 3; ++c) slot_q[c] = -1;
+                for (int c = 0; c < C; ++c) {
+                    lo[c] = g->adv_lo[c];
+                    hi[c] = g->adv_hi[c];
+                    slot_q[c] = src[c];
+                    slot_v0[c] = f.i0;
+                    slot_dt[c] = dt;
+                }
+            }
+        } else if (fuse) {  // a correction: use stored bounds if every channel has them
+            bnd = true;
+            for (int c = 0; c < C && bnd; ++c) {
+                int sl = -1;
+                for (int k = 0; k < 3; ++k)
+                    if (slot_q[k] == src[c] && slot_v0[k] == f.i0 && slot_dt[k] == dt) sl = k;
+                if (sl < 0) bnd = false;
+                else {
+                    lo[c] = g->adv_lo[sl];
+                    hi[c] = g->adv_hi[sl];
+                }
+            }
+            if (!bnd)
+                for (int c = 0; c < 3; ++c) lo[c] = hi[c] = nullptr;
+        }
+        if (bnd) g->stats.bounds_reused += (mode == 0) ? 0 : C;
+        if (!g->dry)
+            launch_advect_group(g->dev, g->stream, mode, C, dst, src, qh, qt, f.i0, h, bnd ? lo : nullptr,
+                                bnd ? hi : nullptr, g->lc);
         g->stats.ops_fused += (int64_t)(mode == 1 ? 2 * C : C) - 1;
         for (int c : ops) done[c] = 1;
         for (int c : macs) done[c] = 1;

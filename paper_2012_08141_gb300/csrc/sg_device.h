@@ -207,8 +207,14 @@ void launch_g2p(const DevGrid &g, cudaStream_t s, float *x, float *v, float *C, 
 // mode 1: backward advection of qhat[c] over -h fused with the correction
 //         dst[c] = clamp(qhat + (src - q~) / 2), q~ stored to qtil[c] if >= 0;
 // mode 2: the correction with q~ read from qtil[c].  C <= 3 channels.
+// lo / hi (or null): per channel, arrays of (cap + 1) * L^3 floats.  Mode 0
+// stores there the clamp bounds of each sample (min and max of the 8 values
+// it reads); modes 1 and 2 read the bounds there instead of tracing the
+// forward path (they must come from a mode-0 launch with the same q,
+// velocity and h, nothing written to q or the velocity since).
 void launch_advect_group(const DevGrid &g, cudaStream_t s, int mode, int C, const int *dst, const int *src,
-                         const int *qhat, const int *qtil, int v0, float h, const LaunchCfg &lc);
+                         const int *qhat, const int *qtil, int v0, float h, float *const *lo, float *const *hi,
+                         const LaunchCfg &lc);
 void launch_activate_tube(const DevGrid &g, cudaStream_t s, long long lo2, long long hi2);
 
 // ---- fused element-wise struct-fors (sg_elementwise.cu) ----

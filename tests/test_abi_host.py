@@ -410,8 +410,35 @@ def test_advection_channel_fusion_launches():
         counts[name] = {k: s1[k] - s0[k] for k in s1}
     assert counts["all"]["launches"] == 2 and counts["all"]["stores_removed"] == 3
     assert counts["all"]["ops_fused"] == 7
-    assert counts["nofuse"]["launches"] == 9
-    assert counts["eager"]["launches"] == 27
+    assert counts["all"]["bounds_reused"] == 3      # each correction reads its forward clamp bounds
+    assert counts["nofuse"]["launches"] == 9 and counts["nofuse"]["bounds_reused"] == 0
+    assert counts["eager"]["launches"] == 27 and counts["eager"]["bounds_reused"] == 0
+
+
+def test_advection_bounds_not_reused_after_a_write():
+    """The clamp bounds of a forward advection are not reused when an op of
+    the run writes the velocity, nor by a correction of another step."""
+    g = sg.Grid(64, 3, 12, max_leaves=1024, dry_run=True)
+    g.activate_tube(1000, 3000)
+    g.list_gen()
+    g.flush()
+    b0 = g.stats()["bounds_reused"]
+    g.advect(4, 3, 0, 1e-3)
+    g.advect(5, 4, 0, -1e-3)
+    g.maccormack(6, 3, 4, 5, 0, 2e-3)          # another step: computes its own bounds
+    g.flush()
+    assert g.stats()["bounds_reused"] == b0
+    g.advect(4, 3, 0, 1e-3)
+    g.advect(5, 4, 0, -1e-3)
+    g.advect(1, 7, 9, 1e-3)                    # writes a velocity component in the same run
+    g.maccormack(6, 3, 4, 5, 0, 1e-3)
+    g.flush()
+    assert g.stats()["bounds_reused"] == b0
+    g.advect(4, 3, 0, 1e-3)
+    g.advect(5, 4, 0, -1e-3)
+    g.maccormack(6, 3, 4, 5, 0, 1e-3)
+    g.flush()
+    assert g.stats()["bounds_reused"] == b0 + 1
 
 
 def test_advection_dependencies_respected():
