@@ -345,6 +345,21 @@ def bench_mpm_apic(torch, sg, steps, warmup, flush_buf, stream):
     return out
 
 
+def vcycle(G):
+    """One V-cycle over the levels G (down: clear, restrict, smooth; up:
+    prolong, smooth, swap), flushed."""
+    for l in range(3):
+        G[l + 1].clear(1)
+        G[l].restrict_to(G[l + 1], 0, 1, 0.125)
+        G[l + 1].diffuse7(1, 0, 0.1)
+    for l in (2, 1, 0):
+        G[l].prolong_from(G[l + 1], 0, 0, 0.5)
+        G[l].diffuse7(0, 2, 0.1)
+        G[l].swap(0, 2)
+    for g in G:
+        g.flush()
+
+
 def bench_multigrid(torch, sg, steps, warmup, flush_buf, stream):
     """V-cycle pattern over four levels (the 512^3 band, then 256^3, 128^3,
     64^3, 8^3 leaves): down, clear b on the coarse level, restrict, smooth;
@@ -363,30 +378,46 @@ def bench_multigrid(torch, sg, steps, warmup, flush_buf, stream):
         G[0].activate_shell(spec.lo2, spec.hi2, spec.lo_strict)
         G[0].fill_hash(0, 3)
 
-        def cycle():
-            for l in range(3):
-                G[l + 1].clear(1)
-                G[l].restrict_to(G[l + 1], 0, 1, 0.125)
-                G[l + 1].diffuse7(1, 0, 0.1)
-            for l in (2, 1, 0):
-                G[l].prolong_from(G[l + 1], 0, 0, 0.5)
-                G[l].diffuse7(0, 2, 0.1)
-                G[l].swap(0, 2)
-            for g in G:
-                g.flush()
-
         stat = lambda key: sum(g.stats()[key] for g in G)
-        cycle()                                    # the first cycle activates the coarse levels
+        vcycle(G)                                  # the first cycle activates the coarse levels
         for g in G:
             g.sync()
         l0, g0 = stat("launches"), stat("listgen_run")
-        ms, _ = time_steps(torch, cycle, steps, warmup, flush_buf, stream)
+        ms, _ = time_steps(torch, lambda: vcycle(G), steps, warmup, flush_buf, stream)
         l1, g1 = stat("launches"), stat("listgen_run")
         n = steps + warmup
         out[name] = {"ms_per_cycle": sum(ms) / len(ms), "launches_per_cycle": (l1 - l0) / n,
                      "listgen_per_cycle": (g1 - g0) / n, "leaves": [g.num_leaves() for g in G]}
         for g in G:
             g.close()
+    # all passes, the cycle recorded as CUDA graphs on a stream of their own:
+    # one graph per swap parity, replayed alternately (one cycle per timed step)
+    gs = torch.cuda.Stream()
+    G = [sg.Grid(512 >> l, 3, 3, max_leaves=32768, max_sums=1, stream=gs) for l in range(4)]
+    G[0].activate_shell(spec.lo2, spec.hi2, spec.lo_strict)
+    G[0].fill_hash(0, 3)
+    vcycle(G)
+    vcycle(G)
+    for g in G:
+        g.sync()
+    graphs = [sg.StepGraph(stream=gs), sg.StepGraph(stream=gs)]
+    for gr in graphs:
+        with gr:
+            vcycle(G)
+    turn = [0]
+
+    def replay():
+        graphs[turn[0] & 1].launch()
+        turn[0] += 1
+
+    ms, _ = time_steps(torch, replay, steps, warmup + (warmup & 1), flush_buf, gs)
+    out["all_passes_graph"] = {"ms_per_cycle": sum(ms) / len(ms), "graph_launches_per_cycle": 1,
+                               "kernels_per_cycle": 15}
+    for gr in graphs:
+        gr.close()
+    for g in G:
+        g.close()
+    out["graph_over_all_passes"] = out["all_passes"]["ms_per_cycle"] / out["all_passes_graph"]["ms_per_cycle"]
     out["no_demotion_over_all_passes"] = out["no_demotion"]["ms_per_cycle"] / out["all_passes"]["ms_per_cycle"]
     out["eager_over_all_passes"] = out["eager"]["ms_per_cycle"] / out["all_passes"]["ms_per_cycle"]
     return out

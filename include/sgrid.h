@@ -340,6 +340,27 @@ int sg_write_field(sg_grid *g, int32_t f, const float *host_vals, int64_t n_leav
 int sg_write_field_active(sg_grid *g, int32_t f, const float *host_vals, int64_t n_active);
 int sg_read_field_active(sg_grid *g, int32_t f, int64_t cap, int64_t *n_active, float *host_vals);
 
+/* ---- CUDA graphs of steady-state steps ----
+ * Record the device work that flushes of grids on `cuda_stream` issue
+ * between sg_graph_begin and sg_graph_end into a graph, and replay it with
+ * sg_graph_launch (on the same stream, in stream order).  Only queued calls
+ * and sg_flush may be made while recording: a call that waits for the device
+ * (sg_sync, reads, implicit syncs) ends the recording with an error, and so
+ * does a change of a grid's structure or a list generation (activation,
+ * deactivation, particle transfers, an activating restriction), since the
+ * host-side list and demotion state would not follow a replay.  Record after
+ * a warm-up step, so the structure and lists are current and every scratch
+ * buffer exists.  Host state (sg_stats, versions) counts the recorded step
+ * once; replays run the same kernels on the same fields: sg_swap is resolved
+ * when a call is queued, so a step that swaps fields needs one graph per
+ * parity.  After a failed recording the grids' contents are undefined.
+ * Errors: SG_ERR_INVALID (null stream, failed recording), SG_ERR_CUDA. */
+typedef struct sg_graph sg_graph;
+int sg_graph_begin(void *cuda_stream);
+int sg_graph_end(void *cuda_stream, sg_graph **out);
+int sg_graph_launch(sg_graph *graph);
+int sg_graph_destroy(sg_graph *graph);
+
 /* Replace the whole structure with a saved one (the restore half of a
  * checkpoint whose save half is sg_read_structure + sg_read_field): leaf_b
  * holds n_leaves root indices in strictly ascending order, each in [0, R^3),

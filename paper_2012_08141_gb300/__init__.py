@@ -127,6 +127,10 @@ def load_library(build: bool = True) -> ctypes.CDLL:
         "sg_batch_destroy": [P],
         "sg_num_active": [P, ctypes.POINTER(I64)],
         "sg_check": [P, ctypes.POINTER(SgCheckReport)],
+        "sg_graph_begin": [P],
+        "sg_graph_end": [P, ctypes.POINTER(P)],
+        "sg_graph_launch": [P],
+        "sg_graph_destroy": [P],
         "sg_debug_poke": [P, I32, I64, U32],
     }
     for name, args in sigs.items():
@@ -456,6 +460,55 @@ def _grid_num_active(self) -> int:
 
 Grid.fill_hash = _grid_fill_hash
 Grid.num_active = _grid_num_active
+
+
+class StepGraph:
+    """A CUDA graph of the device work that flushes issue on one stream
+    between begin() and end() (sg_graph_*): steady-state steps only -- no
+    structure change, list generation or host read while recording."""
+
+    def __init__(self, stream=None):
+        import torch
+        self.lib = load_library()
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.h = None
+
+    def begin(self):
+        _check(self.lib, self.lib.sg_graph_begin(self.stream.cuda_stream))
+        return self
+
+    def end(self):
+        h = ctypes.c_void_p()
+        _check(self.lib, self.lib.sg_graph_end(self.stream.cuda_stream, ctypes.byref(h)))
+        self.h = h
+        return self
+
+    def __enter__(self):
+        return self.begin()
+
+    def __exit__(self, exc_type, exc, tb):
+        if exc_type is None:
+            self.end()
+        else:
+            h = ctypes.c_void_p()
+            self.lib.sg_graph_end(self.stream.cuda_stream, ctypes.byref(h))
+            if h.value:
+                self.lib.sg_graph_destroy(h)
+        return False
+
+    def launch(self):
+        _check(self.lib, self.lib.sg_graph_launch(self.h))
+
+    def close(self):
+        if self.h:
+            self.lib.sg_graph_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Batch:

@@ -150,6 +150,28 @@ int after_launch(sg_grid *g, const char *what)
 
 bool valid_field(const sg_grid *g, int f) { return f >= 0 && f < g->desc.n_fields; }
 
+// True while the grid's stream is being recorded into a graph (sg_graph_begin).
+bool capturing(const sg_grid *g)
+{
+    if (g->dry) return false;
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(g->stream, &st) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return st == cudaStreamCaptureStatusActive;
+}
+
+// A change of the grid's structure (new mask version).  Not allowed inside a
+// graph recording: the host-side list and demotion state would not follow a
+// replay, and list generation numbers its tiles per call.
+int bump_structure(sg_grid *g)
+{
+    g->mask_ver++;
+    if (capturing(g)) return fail(SG_ERR_INVALID, "a change of the structure cannot be recorded in a graph");
+    return SG_OK;
+}
+
 int do_flush(sg_grid *g);
 
 int push(sg_grid *g, Op op)
@@ -165,6 +187,7 @@ double leaf_bytes(const sg_grid *g) { return 4.0 * double(g->dev.L) * g->dev.L *
 // ---- list state ------------------------------------------------------------
 int launch_list(sg_grid *g, bool force, int test_wait)
 {
+    if (capturing(g)) return fail(SG_ERR_INVALID, "list generation cannot be recorded in a graph");
     if (!g->dry) launch_listgen(g->dev, g->stream, force ? 1 : 0, g->lg_calls, g->num_tiles, test_wait);
     g->lg_calls++;
     g->stats.listgen_run++;
@@ -688,9 +711,9 @@ int do_flush(sg_grid *g)
                         else launch_activate_shell(g->dev, g->stream, o.lo2, o.hi2, o.strict);
                     }
                     g->applied_shells.insert(sig);
-                    g->mask_ver++;
                     g->stats.act_launched++;
                     rc = after_launch(g, "activate shell");
+                    if (!rc) rc = bump_structure(g);
                 }
                 ++i;
                 break;
@@ -704,17 +727,17 @@ int do_flush(sg_grid *g)
                         rc = after_launch(g, "set bits");
                     }
                 }
-                g->mask_ver++;
+                if (!rc) rc = bump_structure(g);
                 g->stats.act_launched++;
                 ++i;
                 break;
             }
             case OP_DEACT:
                 if (!g->dry) launch_deactivate_all(g->dev, g->stream);
-                g->mask_ver++;
                 g->applied_shells.clear();
                 g->applied_restrict.clear();
                 rc = after_launch(g, "deactivate");
+                if (!rc) rc = bump_structure(g);
                 ++i;
                 break;
             case OP_LISTGEN:
@@ -754,7 +777,7 @@ int do_flush(sg_grid *g)
                     g->p2g_x = o.p0;
                     g->p2g_n = o.n;
                 }
-                g->mask_ver++;
+                if (!rc) rc = bump_structure(g);
                 g->stats.act_launched++;
                 ++i;
                 break;
@@ -770,7 +793,7 @@ int do_flush(sg_grid *g)
                     launch_g2p2g(o.peer->dev, g->dev, o.bins->dev, g->stream, (float *)o.p1, (float *)o.p2, o.n, o.f0,
                                  o.i0, o.f1, o.i1, o.i2, g->lc);
                 rc = after_launch(g, "g2p2g");
-                g->mask_ver++;
+                if (!rc) rc = bump_structure(g);
                 g->stats.act_launched++;
                 ++i;
                 break;
@@ -1287,8 +1310,8 @@ int sg_restrict(sg_grid *fine, sg_grid *coarse, int32_t f_src, int32_t f_dst, fl
         if (!coarse->dry) launch_alloc_needed(coarse->dev, coarse->stream);
         if ((rc = after_launch(coarse, "restrict: allocate"))) return rc;
         coarse->applied_restrict.insert(key);
-        coarse->mask_ver++;
         coarse->stats.act_launched++;
+        if ((rc = bump_structure(coarse))) return rc;
     }
     if (!coarse->dry)
         launch_restrict(fine->dev, coarse->dev, coarse->stream, fine->phys[f_src], coarse->phys[f_dst], w, !demote,
@@ -1538,6 +1561,65 @@ int sg_read_field_active(sg_grid *g, int32_t f, int64_t cap, int64_t *n_active, 
                                     "copy active values")))
         return rc;
     return cuda_check(cudaStreamSynchronize(g->stream), "stream synchronize");
+}
+
+struct sg_graph {
+    cudaStream_t stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+int sg_graph_begin(void *cuda_stream)
+{
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    if (!s) return fail(SG_ERR_INVALID, "the legacy default stream cannot be recorded");
+    return cuda_check(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed), "begin recording");
+}
+
+int sg_graph_end(void *cuda_stream, sg_graph **out)
+{
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    if (!s || !out) return fail(SG_ERR_INVALID, "null argument");
+    *out = nullptr;
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(s, &graph);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (graph) cudaGraphDestroy(graph);
+        return fail(SG_ERR_INVALID, "recording failed (%s): a call made while recording needed the host",
+                    cudaGetErrorString(e));
+    }
+    sg_graph *gr = new (std::nothrow) sg_graph();
+    if (!gr) {
+        cudaGraphDestroy(graph);
+        return fail(SG_ERR_OOM, "host allocation");
+    }
+    gr->stream = s;
+    gr->graph = graph;
+    int rc = cuda_check(cudaGraphInstantiate(&gr->exec, graph, 0), "instantiate graph");
+    if (rc) {
+        cudaGraphDestroy(graph);
+        delete gr;
+        return rc;
+    }
+    *out = gr;
+    return SG_OK;
+}
+
+int sg_graph_launch(sg_graph *gr)
+{
+    if (!gr) return fail(SG_ERR_INVALID, "null graph");
+    return cuda_check(cudaGraphLaunch(gr->exec, gr->stream), "launch graph");
+}
+
+int sg_graph_destroy(sg_graph *gr)
+{
+    if (!gr) return SG_OK;
+    cudaStreamSynchronize(gr->stream);
+    if (gr->exec) cudaGraphExecDestroy(gr->exec);
+    if (gr->graph) cudaGraphDestroy(gr->graph);
+    delete gr;
+    return SG_OK;
 }
 
 int sg_write_structure(sg_grid *g, int64_t n_leaves, const int32_t *leaf_b, const uint32_t *masks)
