@@ -296,6 +296,7 @@ def bench_particles(torch, sg, steps, warmup, flush_buf, stream):
             "ms_per_step": t * 1e3 / steps, "launches_per_step": launches / steps,
             "l2": "flushed before every timed step (512 MB write)",
             "stream_bytes_per_particle": 72,
+            "stream_hbm_frac": spec.n * 72 * steps / t / 1e9 / peaks()[0],
             "grid_atomics_per_s": spec.n * 27 * 4 * steps / t}
 
 
