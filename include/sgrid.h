@@ -340,6 +340,23 @@ int sg_write_field(sg_grid *g, int32_t f, const float *host_vals, int64_t n_leav
 int sg_write_field_active(sg_grid *g, int32_t f, const float *host_vals, int64_t n_active);
 int sg_read_field_active(sg_grid *g, int32_t f, int64_t cap, int64_t *n_active, float *host_vals);
 
+/* Staged (overlapped) active-voxel uploads.  sg_stage_active starts copying
+ * n_active packed values from host memory into one of the grid's two upload
+ * slots, on a copy stream of the grid's own, and returns a ticket; the copy
+ * runs while device work already queued runs.  host_vals (page-locked, or the
+ * call waits for the copy) is borrowed until the next upload into the same
+ * slot has been staged (that call waits for the earlier copy) or the grid has
+ * been synced after the ticket's write.  A slot is refilled only after the
+ * write that read it has run, so two uploads can be in flight.  sg_write_field_staged queues: field f = the staged
+ * values (as sg_write_field_active); at flush the grid's stream waits for the
+ * copy.  The count must equal the grid's active voxels when the write runs
+ * (else SG_ERR_INVALID at flush, the field unchanged).  When the structure
+ * changed since the packed offsets were last computed, the flush waits for
+ * the device once to compute them.  Errors: SG_ERR_INVALID (arguments, a
+ * ticket replaced by a later upload into its slot), SG_ERR_OOM. */
+int sg_stage_active(sg_grid *g, const float *host_vals, int64_t n_active, int32_t *ticket);
+int sg_write_field_staged(sg_grid *g, int32_t f, int32_t ticket);
+
 /* ---- CUDA graphs of steady-state steps ----
  * Record the device work that flushes of grids on `cuda_stream` issue
  * between sg_graph_begin and sg_graph_end into a graph, and replay it with

@@ -112,6 +112,8 @@ def load_library(build: bool = True) -> ctypes.CDLL:
         "sg_write_structure": [P, I64, P, P],
         "sg_write_field_active": [P, I32, P, I64],
         "sg_read_field_active": [P, I32, I64, ctypes.POINTER(I64), P],
+        "sg_stage_active": [P, P, I64, ctypes.POINTER(I32)],
+        "sg_write_field_staged": [P, I32, I32],
         "sg_read_sums": [P, P, I64],
         "sg_get_stats": [P, ctypes.POINTER(SgStats)],
         "sg_debug_wait_test": [P],
@@ -390,6 +392,26 @@ class Grid:
         else:
             assert not vals.is_cuda and vals.is_contiguous()
             self._c(self.lib.sg_write_field_active(self.h, int(f), _ptr(vals), vals.numel()))
+
+    def stage_active(self, vals) -> int:
+        """Start copying the active voxels' values (a pinned torch CPU tensor
+        or numpy array, borrowed until its write has run) into an upload
+        slot; returns the ticket for write_field_staged."""
+        t = ctypes.c_int32()
+        if isinstance(vals, np.ndarray):
+            vals = np.ascontiguousarray(vals, dtype=np.float32).reshape(-1)
+            self._c(self.lib.sg_stage_active(self.h, _ptr(vals), vals.size, ctypes.byref(t)))
+        else:
+            assert not vals.is_cuda and vals.is_contiguous()
+            self._c(self.lib.sg_stage_active(self.h, _ptr(vals), vals.numel(), ctypes.byref(t)))
+        if not hasattr(self, "_staged"):
+            self._staged = [None, None]
+        self._staged[t.value & 1] = vals   # kept until the slot is staged again
+        return t.value
+
+    def write_field_staged(self, f: int, ticket: int):
+        """Queue: field f = the values staged under ticket."""
+        self._c(self.lib.sg_write_field_staged(self.h, int(f), int(ticket)))
 
     def read_field_active(self, f: int, out: np.ndarray | None = None) -> np.ndarray:
         """The active voxels' values of field f (FP32, list and mask-bit

@@ -53,7 +53,7 @@ int fail(int code, const char *fmt, ...)
 }
 
 enum OpKind { OP_ACT_SHELL, OP_ACT_COORDS, OP_DEACT, OP_LISTGEN, OP_STENCIL, OP_SUM, OP_P2G, OP_GRID_UPDATE, OP_G2P, OP_TEST_WAIT,
-              OP_FILL, OP_G2P2G, OP_EW, OP_ADVECT, OP_MAC };
+              OP_FILL, OP_G2P2G, OP_EW, OP_ADVECT, OP_MAC, OP_WRITE_STAGED };
 
 struct Op {
     OpKind kind;
@@ -108,6 +108,15 @@ struct sg_grid {
     unsigned long long act_ver = 0;         // list version the offsets were computed for (0 = never)
     long long act_total = 0;
     float *adv_lo[3] = {}, *adv_hi[3] = {}; // advection clamp bounds, (cap + 1) * L^3 each (allocated at first use)
+    // staged uploads (sg_stage_active): two slots filled on a copy stream of
+    // the grid's own, each consumed by a queued scatter
+    cudaStream_t copy_stream = nullptr;
+    float *upload[2] = {};
+    cudaEvent_t copied[2] = {}, consumed[2] = {};
+    bool slot_used[2] = {};
+    long long upload_n[2] = {};
+    unsigned upload_seq[2] = {};
+    unsigned next_seq = 1;
 };
 
 namespace {
@@ -692,6 +701,8 @@ int ensure_p2g_scratch(sg_grid *g, long long n)
     return SG_OK;
 }
 
+int run_write_staged(sg_grid *g, const Op &o);
+
 int do_flush(sg_grid *g)
 {
     int rc = SG_OK;
@@ -795,6 +806,10 @@ int do_flush(sg_grid *g)
                 rc = after_launch(g, "g2p2g");
                 if (!rc) rc = bump_structure(g);
                 g->stats.act_launched++;
+                ++i;
+                break;
+            case OP_WRITE_STAGED:
+                rc = run_write_staged(g, o);
                 ++i;
                 break;
             case OP_G2P:
@@ -913,6 +928,70 @@ int ensure_staging(sg_grid *g)
     g->dev.staging_u = (uint32_t *)p;
     g->staging_bytes = need;
     return SG_OK;
+}
+
+// Packed positions of every list entry's active voxels (a current list of n
+// entries); returns their total through *total (implicit wait).  Kept while
+// the structure is unchanged: the list version keys them.
+int active_offsets(sg_grid *g, long long n, long long *total)
+{
+    // reused while no activation has touched the structure since (the list
+    // is current and the device dirty flag, read at the last sync, is clear)
+    if (g->act_ver == g->list_ver && g->act_ver != 0 && g->host_ctrl->dirty == 0) {
+        *total = g->act_total;
+        return SG_OK;
+    }
+    if (!g->act_off) {
+        g->act_off = (long long *)dev_alloc(g, sizeof(long long) * size_t(g->dev.cap));
+        g->act_tsum = (long long *)dev_alloc(g, sizeof(long long) * size_t(g->dev.cap / kOffTile + 2));
+        if (!g->act_off || !g->act_tsum) return fail(SG_ERR_OOM, "transfer offsets");
+    }
+    launch_active_offsets(g->dev, g->stream, n, g->act_off, g->act_tsum);
+    int rc = after_launch(g, "active offsets");
+    if (rc) return rc;
+    const int ntiles = (int)((n + kOffTile - 1) / kOffTile);
+    if ((rc = cuda_check(cudaMemcpyAsync(total, g->act_tsum + ntiles, sizeof(long long), cudaMemcpyDeviceToHost,
+                                         g->stream),
+                         "read active total")) ||
+        (rc = cuda_check(cudaStreamSynchronize(g->stream), "stream synchronize")))
+        return rc;
+    g->act_ver = g->list_ver;
+    g->act_total = *total;
+    return SG_OK;
+}
+
+// The queued half of a staged upload: wait for the slot's copy, check the
+// count and scatter the slot into the field.  The active count comes from the
+// kept offsets when the structure is unchanged since they were computed;
+// otherwise they are computed here, which waits for the device once.
+int run_write_staged(sg_grid *g, const Op &o)
+{
+    const int k = (int)o.slot;
+    if (g->upload_seq[k] != (unsigned)o.i1)
+        return fail(SG_ERR_INVALID, "staged upload %u was replaced by a later one", (unsigned)o.i1);
+    if (g->dry) return after_launch(g, "scatter staged");
+    int rc = ensure_list(g);
+    if (rc) return rc;
+    long long total = 0;
+    if (!(g->act_ver == g->list_ver && g->act_ver != 0 && g->host_ctrl->dirty == 0)) {
+        // the list length, on the host: wait for the work launched so far and
+        // read the control block (no flush -- this runs inside one; device
+        // errors stay latched for the next sync)
+        if ((rc = cuda_check(cudaMemcpyAsync(g->host_ctrl, g->dev.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost,
+                                             g->stream),
+                             "read control block")) ||
+            (rc = cuda_check(cudaStreamSynchronize(g->stream), "stream synchronize")))
+            return rc;
+    }
+    const long long n = g->host_ctrl->list_n;
+    if (n > 0 && (rc = active_offsets(g, n, &total))) return rc;
+    if (total != o.n)
+        return fail(SG_ERR_INVALID, "the grid has %lld active voxels, the upload holds %lld", total, o.n);
+    if (n == 0) return SG_OK;
+    if ((rc = cuda_check(cudaStreamWaitEvent(g->stream, g->copied[k], 0), "wait for the upload"))) return rc;
+    launch_scatter_active(g->dev, g->stream, o.i0, g->upload[k], total, g->act_off, g->act_tsum, g->lc);
+    if ((rc = after_launch(g, "scatter staged"))) return rc;
+    return cuda_check(cudaEventRecord(g->consumed[k], g->stream), "record upload consumed");
 }
 
 }  // namespace
@@ -1035,6 +1114,14 @@ int sg_destroy(sg_grid *g)
     int rc = SG_OK;
     if (!g->dry) {
         rc = cuda_check(cudaStreamSynchronize(g->stream), "stream synchronize");
+        if (g->copy_stream) {
+            cudaStreamSynchronize(g->copy_stream);
+            cudaStreamDestroy(g->copy_stream);
+        }
+        for (int k = 0; k < 2; ++k) {
+            if (g->copied[k]) cudaEventDestroy(g->copied[k]);
+            if (g->consumed[k]) cudaEventDestroy(g->consumed[k]);
+        }
         dev_free_all(g);
         if (g->host_ctrl) cudaFreeHost(g->host_ctrl);
     }
@@ -1480,34 +1567,61 @@ int sg_debug_poke(sg_grid *g, int32_t array, int64_t index, uint32_t bits)
     return cuda_check(cudaStreamSynchronize(g->stream), "stream synchronize");
 }
 
-// Packed positions of every list entry's active voxels (a current list of n
-// entries); returns their total through *total (implicit wait).  Kept while
-// the structure is unchanged: the list version keys them.
-static int active_offsets(sg_grid *g, long long n, long long *total)
+int sg_stage_active(sg_grid *g, const float *host_vals, int64_t n_active, int32_t *ticket)
 {
-    // reused while no activation has touched the structure since (the list
-    // is current and the device dirty flag, read at the last sync, is clear)
-    if (g->act_ver == g->list_ver && g->act_ver != 0 && g->host_ctrl->dirty == 0) {
-        *total = g->act_total;
-        return SG_OK;
+    if (!g || !ticket || n_active < 0 || (n_active > 0 && !host_vals)) return fail(SG_ERR_INVALID, "bad arguments");
+    const long long V = (long long)g->dev.L * g->dev.L * g->dev.L;
+    if (n_active > g->dev.cap * V) return fail(SG_ERR_INVALID, "more values than the pool holds voxels");
+    const int k = (int)(g->next_seq & 1u);
+    const unsigned seq = g->next_seq++;
+    if (!g->dry) {
+        if (!g->copy_stream) {
+            int rc;
+            if ((rc = cuda_check(cudaStreamCreateWithFlags(&g->copy_stream, cudaStreamNonBlocking), "copy stream")))
+                return rc;
+            for (int j = 0; j < 2; ++j)
+                if ((rc = cuda_check(cudaEventCreateWithFlags(&g->copied[j], cudaEventDisableTiming), "event")) ||
+                    (rc = cuda_check(cudaEventCreateWithFlags(&g->consumed[j], cudaEventDisableTiming), "event")))
+                    return rc;
+        }
+        if (!g->upload[k]) {
+            g->upload[k] = (float *)dev_alloc(g, sizeof(float) * size_t(g->dev.cap * V));
+            if (!g->upload[k]) return fail(SG_ERR_OOM, "upload slot");
+        }
+        int rc;
+        // the slot's previous copy has finished reading its host buffer once
+        // this returns (it ran two uploads ago; the wait is normally free)
+        if (g->slot_used[k] &&
+            ((rc = cuda_check(cudaEventSynchronize(g->copied[k]), "previous upload")) ||
+             (rc = cuda_check(cudaStreamWaitEvent(g->copy_stream, g->consumed[k], 0), "wait for the slot"))))
+            return rc;
+        if (n_active > 0 &&
+            (rc = cuda_check(cudaMemcpyAsync(g->upload[k], host_vals, sizeof(float) * size_t(n_active),
+                                             cudaMemcpyHostToDevice, g->copy_stream),
+                             "stage upload")))
+            return rc;
+        if ((rc = cuda_check(cudaEventRecord(g->copied[k], g->copy_stream), "record upload"))) return rc;
+        // until a scatter consumes it, reusing the slot waits for this copy
+        if ((rc = cuda_check(cudaEventRecord(g->consumed[k], g->copy_stream), "record slot"))) return rc;
+        g->slot_used[k] = true;
     }
-    if (!g->act_off) {
-        g->act_off = (long long *)dev_alloc(g, sizeof(long long) * size_t(g->dev.cap));
-        g->act_tsum = (long long *)dev_alloc(g, sizeof(long long) * size_t(g->dev.cap / kOffTile + 2));
-        if (!g->act_off || !g->act_tsum) return fail(SG_ERR_OOM, "transfer offsets");
-    }
-    launch_active_offsets(g->dev, g->stream, n, g->act_off, g->act_tsum);
-    int rc = after_launch(g, "active offsets");
-    if (rc) return rc;
-    const int ntiles = (int)((n + kOffTile - 1) / kOffTile);
-    if ((rc = cuda_check(cudaMemcpyAsync(total, g->act_tsum + ntiles, sizeof(long long), cudaMemcpyDeviceToHost,
-                                         g->stream),
-                         "read active total")) ||
-        (rc = cuda_check(cudaStreamSynchronize(g->stream), "stream synchronize")))
-        return rc;
-    g->act_ver = g->list_ver;
-    g->act_total = *total;
+    g->upload_n[k] = n_active;
+    g->upload_seq[k] = seq;
+    *ticket = (int32_t)seq;
     return SG_OK;
+}
+
+int sg_write_field_staged(sg_grid *g, int32_t f, int32_t ticket)
+{
+    if (!g || !valid_field(g, f) || ticket <= 0) return fail(SG_ERR_INVALID, "bad arguments");
+    const int k = (int)((unsigned)ticket & 1u);
+    if (g->upload_seq[k] != (unsigned)ticket) return fail(SG_ERR_INVALID, "unknown or replaced upload ticket");
+    Op o{OP_WRITE_STAGED};
+    o.i0 = g->phys[f];
+    o.i1 = ticket;
+    o.slot = k;
+    o.n = g->upload_n[k];
+    return push(g, o);
 }
 
 int sg_write_field_active(sg_grid *g, int32_t f, const float *host_vals, int64_t n_active)

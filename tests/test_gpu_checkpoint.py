@@ -268,3 +268,55 @@ def test_active_value_transfers_band512_and_empty():
     assert e.read_field_active(0).size == 0
     e.write_field_active(0, np.zeros(0, np.float32))
     e.close()
+
+
+def test_staged_uploads_overlap_and_match():
+    """Staged uploads (copy on the grid's copy stream, scatter queued) give the
+    same fields as synchronous active-value writes in a pipelined loop where
+    the next input is staged while the current step runs; a count that no
+    longer matches the structure and a replaced ticket are refused."""
+    import torch
+    import paper_2012_08141_gb300 as sg
+    spec = tiny_shell(12, N=64, L=8)
+    mk = lambda: sg.Grid(64, 3, 3, max_leaves=512, max_sums=1, scratch_mask=0b010)
+    a, b = mk(), mk()
+    for g in (a, b):
+        g.activate_shell(spec.lo2, spec.hi2, spec.lo_strict)
+    n = a.num_active()
+    rng = np.random.default_rng(12)
+    inputs = [torch.from_numpy(rng.random(n, dtype=np.float32)).pin_memory() for _ in range(4)]
+    t = a.stage_active(inputs[0])
+    for s in range(4):
+        a.write_field_staged(0, t)
+        a.diffuse7(0, 1, 0.1)
+        a.box27(1, 2)
+        a.reduce_sum(2, 0)
+        a.flush()
+        if s + 1 < 4:
+            t = a.stage_active(inputs[s + 1])          # overlaps the step just queued
+        got = a.read_sums(1)
+        b.write_field_active(0, inputs[s])
+        b.diffuse7(0, 1, 0.1)
+        b.box27(1, 2)
+        b.reduce_sum(2, 0)
+        np.testing.assert_array_equal(got, b.read_sums(1))
+        np.testing.assert_array_equal(a.read_field(2), b.read_field(2))
+    # a ticket whose slot was refilled is refused
+    t1 = a.stage_active(inputs[0])
+    a.stage_active(inputs[1])
+    a.stage_active(inputs[2])                          # same slot as t1
+    with pytest.raises(sg.SgError):
+        a.write_field_staged(0, t1)
+    # the structure changes between staging and writing: refused at the flush
+    before = a.read_field(0)
+    t2 = a.stage_active(inputs[3])
+    a.activate_coords(torch.tensor([[1, 1, 1]], dtype=torch.int32).cuda())
+    a.write_field_staged(0, t2)
+    with pytest.raises(sg.SgError) as e:
+        a.sync()
+    assert e.value.code == sg.SG_ERR_INVALID
+    after = a.read_field(0)                            # field 0 unchanged; the new voxel reads 0
+    assert after.astype(np.float64).sum() == before.astype(np.float64).sum()
+    assert np.count_nonzero(after) == np.count_nonzero(before)
+    a.close()
+    b.close()
