@@ -504,3 +504,26 @@ def test_write_structure_argument_checks():
     b = np.array([1, 5, 7], np.int32)
     assert lib.sg_write_structure(small.h, 3, b.ctypes.data, m.ctypes.data) == sg.SG_ERR_POOL_EXHAUSTED
     assert b"max_leaves" in lib.sg_last_error()
+
+
+def test_staged_upload_tickets():
+    """Tickets name one of two upload slots; a ticket whose slot was refilled,
+    or that was never issued, is refused; a staged write is one queued op."""
+    import numpy as np
+    g = dry(F=2)
+    v = np.zeros(10, np.float32)
+    lib = g.lib
+    t1 = g.stage_active(v)
+    t2 = g.stage_active(v)
+    assert (t1 & 1) != (t2 & 1)
+    g.write_field_staged(0, t2)
+    t3 = g.stage_active(v)                                 # refills t1's slot
+    assert (t3 & 1) == (t1 & 1)
+    assert lib.sg_write_field_staged(g.h, 0, t1) == sg.SG_ERR_INVALID
+    assert lib.sg_write_field_staged(g.h, 0, 12345) == sg.SG_ERR_INVALID
+    assert lib.sg_write_field_staged(g.h, 0, 0) == sg.SG_ERR_INVALID
+    assert lib.sg_write_field_staged(g.h, 7, t3) == sg.SG_ERR_INVALID   # no such field
+    q0 = g.stats()["ops_enqueued"]
+    g.write_field_staged(1, t3)
+    assert g.stats()["ops_enqueued"] == q0 + 1
+    g.flush()
