@@ -352,7 +352,8 @@ int sg_read_field_active(sg_grid *g, int32_t f, int64_t cap, int64_t *n_active, 
  * copy.  The count must equal the grid's active voxels when the write runs
  * (else SG_ERR_INVALID at flush, the field unchanged).  When the structure
  * changed since the packed offsets were last computed, the flush waits for
- * the device once to compute them.  Errors: SG_ERR_INVALID (arguments, a
+ * the device once to compute them.  A staged write cannot be recorded in a
+ * graph (sg_graph_begin).  Errors: SG_ERR_INVALID (arguments, a
  * ticket replaced by a later upload into its slot), SG_ERR_OOM. */
 int sg_stage_active(sg_grid *g, const float *host_vals, int64_t n_active, int32_t *ticket);
 int sg_write_field_staged(sg_grid *g, int32_t f, int32_t ticket);

@@ -970,6 +970,7 @@ int run_write_staged(sg_grid *g, const Op &o)
     if (g->upload_seq[k] != (unsigned)o.i1)
         return fail(SG_ERR_INVALID, "staged upload %u was replaced by a later one", (unsigned)o.i1);
     if (g->dry) return after_launch(g, "scatter staged");
+    if (capturing(g)) return fail(SG_ERR_INVALID, "a staged upload cannot be recorded in a graph");
     int rc = ensure_list(g);
     if (rc) return rc;
     long long total = 0;
