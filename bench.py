@@ -20,6 +20,7 @@ it.  Further legs (skipped with --only fused or on more than one rank):
             sparse_saxpy, autodiff, stencil_reduction) on the 512^3 band;
   advection MacCormack/RK3 advection of 3 channels over the 256^3 tube, all
             passes against no fusion and eager;
+  ablation  the band step with each of the four passes switched off in turn;
   serving   Poisson arrivals of band jobs (1e4..1e7 voxels, 10..200 steps)
             into the continuous-batching server: p50/p99 job latency;
   band1024  the 1024^3 band |dist - 400| < 8, far larger than L2.
@@ -229,6 +230,39 @@ def bench_band1024(torch, sg, steps, warmup, flush_buf, stream):
     g.close()
     return {"workload": "1024^3 band |dist-400|<8, 8^3 leaves", "active_voxels": act, "leaves": n,
             "value": act * steps / t, "ms_per_step": t * 1e3 / steps, "achieved_gbs": ach, "frac": ach / peak}
+
+
+def bench_ablation(torch, sg, x_host, steps, warmup, flush_buf, stream):
+    """The four passes switched off one at a time (Table 3's ablation, on the
+    512^3 band).  The step re-activates the band first, as the paper's steps
+    do, so that activation demotion has an activation to remove: activate,
+    clear, diffuse7, box27, swap, sum."""
+    spec = band512()
+    out = {"workload": "512^3 band, per step: activate (same band), clear, diffuse7, box27, swap, sum",
+           "l2": "flushed before every timed step (512 MB write)"}
+    base = None
+    for name, opts in (("all", sg.SG_OPT_ALL), ("no_lgr", sg.SG_OPT_ALL & ~sg.SG_OPT_LGR),
+                       ("no_ad", sg.SG_OPT_ALL & ~sg.SG_OPT_AD), ("no_fusion", sg.SG_OPT_ALL & ~sg.SG_OPT_FUSE),
+                       ("no_dse", sg.SG_OPT_ALL & ~sg.SG_OPT_DSE), ("eager", sg.SG_OPT_EAGER)):
+        g = setup_band(sg, spec, opts, x_host)
+
+        def step():
+            g.activate_shell(spec.lo2, spec.hi2, spec.lo_strict)
+            band_step(g)
+
+        st0 = g.stats()
+        ms, _ = time_steps(torch, step, steps, warmup, flush_buf, stream)
+        st1 = g.stats()
+        n = steps + warmup
+        row = {"ms_per_step": sum(ms) / len(ms), "launches_per_step": (st1["launches"] - st0["launches"]) / n,
+               "listgen_per_step": (st1["listgen_run"] - st0["listgen_run"]) / n,
+               "activations_per_step": (st1["act_launched"] - st0["act_launched"]) / n}
+        if base is None:
+            base = row["ms_per_step"]
+        row["slowdown"] = row["ms_per_step"] / base
+        out[name] = row
+        g.close()
+    return out
 
 
 def bench_batched(torch, sg, steps, warmup, flush_buf, stream):
@@ -653,6 +687,7 @@ def run_ours(args):
                          ("multigrid", lambda: bench_multigrid(torch, sg, k, 3, flush_buf, stream)),
                          ("micro", lambda: bench_micro(torch, sg, k, 3, flush_buf, stream)),
                          ("advection", lambda: bench_advection(torch, sg, k, 3, flush_buf, stream)),
+                         ("ablation", lambda: bench_ablation(torch, sg, x_host, k, 3, flush_buf, stream)),
                          ("serving", lambda: bench_serving(torch, sg))):
             if args.only not in ("all", name):
                 continue
@@ -784,7 +819,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--variant", type=int, default=0, help="stencil kernel family (0 sweep, 1 smem)")
     ap.add_argument("--only", choices=["all", "fused", "band1024", "batched", "particles", "mpm_apic", "multigrid",
-                                       "micro", "advection", "serving"],
+                                       "micro", "advection", "ablation", "serving"],
                     default="all",
                     help="fused: only the fused headline step; a leg name: the headline step and that leg "
                          "(for profiling runs)")
