@@ -695,8 +695,11 @@ int ensure_p2g_scratch(sg_grid *g, long long n)
     if (n > g->perm_cap) {
         const long long cap = std::max(n, g->perm_cap * 2);
         g->dev.perm = (int32_t *)dev_alloc(g, sizeof(int32_t) * cap);
-        if (!g->dev.perm) return fail(SG_ERR_OOM, "p2g order of %lld particles", cap);
+        g->dev.perm_alt = (int32_t *)dev_alloc(g, sizeof(int32_t) * cap);
+        if (!g->dev.perm || !g->dev.perm_alt) return fail(SG_ERR_OOM, "p2g order of %lld particles", cap);
         g->perm_cap = cap;
+        g->p2g_x = nullptr;  // no valid last order in the new arrays
+        g->p2g_n = 0;
     }
     return SG_OK;
 }
@@ -779,10 +782,12 @@ int do_flush(sg_grid *g)
                 break;
             case OP_P2G:
                 if (!(rc = ensure_p2g_scratch(g, o.n))) {
+                    // the same particles binned before: rebin from their last order
+                    const bool rebin = g->p2g_x == o.p0 && g->p2g_n == o.n;
                     const int k = g->dry ? 7
                                          : launch_p2g_binned(g->dev, g->stream, (const float *)o.p0,
                                                              (const float *)o.p1, (const float *)o.p3, o.n, o.f0,
-                                                             o.i0, o.i1, g->lc);
+                                                             o.i0, o.i1, rebin, g->lc);
                     g->stats.launches += k - 1;
                     rc = after_launch(g, "binned p2g");
                     g->p2g_x = o.p0;

@@ -75,6 +75,7 @@ struct DevGrid {
     int32_t *bin_off;
     int32_t *tile_sum;
     int32_t *perm;
+    int32_t *perm_alt;  // the next binning's order, built from the last one (then swapped)
     int32_t *bin_list;  // the leaves holding particles, in no particular order
 };
 
@@ -191,8 +192,11 @@ void launch_sweep_single(const DevGrid &g, cudaStream_t s, int op, int src, int 
 // for particles whose stencil misses the domain.
 constexpr long long p2g_num_keys(int R) { return 8LL * R * R * R + 1; }
 // C: NULL for PIC, else the APIC matrices (n x 9 FP32, row-major).
-int launch_p2g_binned(const DevGrid &g, cudaStream_t s, const float *x, const float *v, const float *C, long long n,
-                      float pmass, int f_mass, int f_mom0, const LaunchCfg &lc);
+// rebin: the particle order of the last binning of the same particles is
+// valid in g.perm; the new order is built from it in g.perm_alt (fewer
+// conflicting count atomics) and the two are swapped in g.
+int launch_p2g_binned(DevGrid &g, cudaStream_t s, const float *x, const float *v, const float *C, long long n,
+                      float pmass, int f_mass, int f_mom0, bool rebin, const LaunchCfg &lc);
 void launch_grid_update(const DevGrid &g, cudaStream_t s, int f_mass, int f_mom0, float dt,
                         float gz, int bound, const LaunchCfg &lc);
 // binned: use the bins of the last binned P2G over the same particles (the

@@ -202,6 +202,19 @@ __global__ void k_p2g_bin(DevGrid g, const float *__restrict__ x, long long n)
         atomicAdd(&g.bin_count[p2g_key_of(x, p, g.N, g.lg2, g.R)], 1);
 }
 
+// Rebinning: the particles are visited in the last binning's order, so the
+// lanes of a warp mostly share a key (particles move little between steps);
+// one atomic per distinct key in the warp.
+__global__ void k_p2g_rebin(DevGrid g, const float *__restrict__ x, long long n)
+{
+    const int lane = lane_id();
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+        const long long key = p2g_key_of(x, g.perm[q], g.N, g.lg2, g.R);
+        const unsigned peers = __match_any_sync(__activemask(), key);
+        if (lane == __ffs(peers) - 1) atomicAdd(&g.bin_count[key], __popc(peers));
+    }
+}
+
 // Sum of each tile of kBinTile counts; for every occupied key, mark the
 // leaves its particles' stencils reach (the base leaf plus the neighbours in
 // the directions of its reach class) for allocation.
@@ -310,6 +323,23 @@ __global__ void k_p2g_perm(DevGrid g, const float *__restrict__ x, long long n)
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
         const int pos = atomicAdd(&g.bin_count[p2g_key_of(x, p, g.N, g.lg2, g.R)], 1);
         g.perm[pos] = (int)p;
+    }
+}
+
+// The new order from the last one, written to perm_alt (warp-aggregated
+// cursor atomics, as in k_p2g_rebin).
+__global__ void k_p2g_reperm(DevGrid g, const float *__restrict__ x, long long n)
+{
+    const int lane = lane_id();
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+        const int p = g.perm[q];
+        const long long key = p2g_key_of(x, p, g.N, g.lg2, g.R);
+        const unsigned peers = __match_any_sync(__activemask(), key);
+        const int leader = __ffs(peers) - 1;
+        int base = 0;
+        if (lane == leader) base = atomicAdd(&g.bin_count[key], __popc(peers));
+        base = __shfl_sync(peers, base, leader);
+        g.perm_alt[base + __popc(peers & lanemask_lt())] = p;
     }
 }
 
@@ -501,8 +531,8 @@ __global__ void __launch_bounds__(256) k_p2g_gather(DevGrid g, const float *__re
     if (changed) mark_dirty(g);
 }
 
-int launch_p2g_binned(const DevGrid &g, cudaStream_t s, const float *x, const float *v, const float *C, long long n,
-                      float pmass, int f_mass, int f_mom0, const LaunchCfg &lc)
+int launch_p2g_binned(DevGrid &g, cudaStream_t s, const float *x, const float *v, const float *C, long long n,
+                      float pmass, int f_mass, int f_mom0, bool rebin, const LaunchCfg &lc)
 {
     const long long nscan = p2g_num_keys(g.R);
     const int ntiles = (int)((nscan + kBinTile - 1) / kBinTile);
@@ -511,13 +541,21 @@ int launch_p2g_binned(const DevGrid &g, cudaStream_t s, const float *x, const fl
     int launches = 0;
     cudaMemsetAsync(g.bin_count, 0, sizeof(int32_t) * nscan, s);
     cudaMemsetAsync(&g.ctrl->bins_used, 0, sizeof(int32_t), s);
-    k_p2g_bin<<<(unsigned)pblocks, 256, 0, s>>>(g, x, n);
+    if (rebin) k_p2g_rebin<<<(unsigned)pblocks, 256, 0, s>>>(g, x, n);
+    else k_p2g_bin<<<(unsigned)pblocks, 256, 0, s>>>(g, x, n);
     k_bin_scan_tiles<<<ntiles, 256, 0, s>>>(g, nscan);
     launch_alloc_needed(g, s);
     k_bin_scan_top<<<1, 1024, 0, s>>>(g, ntiles);
     k_bin_scan_apply<<<ntiles, 256, 0, s>>>(g, nscan);
     launches += 5;
-    k_p2g_perm<<<(unsigned)pblocks, 256, 0, s>>>(g, x, n);
+    if (rebin) {
+        k_p2g_reperm<<<(unsigned)pblocks, 256, 0, s>>>(g, x, n);
+        int32_t *t = g.perm;  // the new order is now the current one
+        g.perm = g.perm_alt;
+        g.perm_alt = t;
+    } else {
+        k_p2g_perm<<<(unsigned)pblocks, 256, 0, s>>>(g, x, n);
+    }
     ++launches;
 #define SG_GATHER(LL, AP) k_p2g_gather<LL, AP><<<resident_ctas(k_p2g_gather<LL, AP>, lc.num_sms), 256, 0, s>>>( \
         g, x, v, C, pmass, f_mass, f_mom0)
