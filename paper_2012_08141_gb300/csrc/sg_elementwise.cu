@@ -6,6 +6,8 @@
 // values held in a per-thread register file in shared memory, and only the
 // live final values are stored (Sec. 6.5).  An optional reduction of one
 // field, at its place in the run, is fused as well.
+#include <atomic>
+
 #include "sg_common.cuh"
 
 namespace sg {
@@ -130,13 +132,15 @@ __global__ void __launch_bounds__(kEwThreads, 8) k_ew(DevGrid g, EwProgram prog)
 template <int L>
 static int ew_ctas(int num_sms, int n_slots)
 {
-    static int per[kMaxEwSlots + 1] = {};
-    const size_t smem = sizeof(float4) * 2 * kEwThreads * n_slots;
-    if (!per[n_slots] &&
-        (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per[n_slots], k_ew<L>, kEwThreads, smem) != cudaSuccess ||
-         per[n_slots] < 1))
-        per[n_slots] = 1;
-    return per[n_slots] * num_sms;
+    static std::atomic<int> cache[kMaxEwSlots + 1];  // per program size; threads may race to fill it
+    int per = cache[n_slots].load(std::memory_order_relaxed);
+    if (!per) {
+        const size_t smem = sizeof(float4) * 2 * kEwThreads * n_slots;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_ew<L>, kEwThreads, smem) != cudaSuccess || per < 1)
+            per = 1;
+        cache[n_slots].store(per, std::memory_order_relaxed);
+    }
+    return per * num_sms;
 }
 
 void launch_ew(const DevGrid &g, cudaStream_t s, const EwProgram &prog, const LaunchCfg &lc)

@@ -29,6 +29,7 @@
 // A particle whose new base is outside [o-1, o+L], and every particle of the
 // out-of-domain key, is scattered node by node straight into dst with the same
 // in-kernel allocation.
+#include <atomic>
 #include "sg_particle.cuh"
 
 namespace sg {
@@ -416,14 +417,15 @@ void launch_g2p2g_L(const DevGrid &src, const DevGrid &dst, const DevGrid &bins,
                     float dt, int f_vel0, float pmass, int f_mass, int f_mom0, bool pair, int num_sms)
 {
     constexpr size_t bytes = G2P2GSmem<L>::bytes;
-    static int ctas = 0;
-    if (!ctas) {
+    static std::atomic<int> resident;  // CTAs per SM; threads may race to fill it
+    int per = resident.load(std::memory_order_relaxed);
+    if (!per) {
         cudaFuncSetAttribute(k_g2p2g<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-        int per = 1;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_g2p2g<L>, 256, bytes) != cudaSuccess || per < 1)
             per = 1;
-        ctas = per * num_sms;
+        resident.store(per, std::memory_order_relaxed);
     }
+    const int ctas = per * num_sms;
     k_g2p2g<L><<<ctas, 256, bytes, s>>>(src, dst, bins.bin_list, bins.bin_off, bins.bin_count, bins.perm,
                                          &bins.ctrl->bins_used, x, v, dt, f_vel0, pmass, f_mass, f_mom0, pair);
 }

@@ -18,6 +18,7 @@
 // staged loads need no mask; outputs are masked before they are stored, which
 // keeps the invariant.  Other leaf sizes use the generic kernels at the end,
 // which walk the tree for every read.
+#include <atomic>
 #include "sg_common.cuh"
 
 namespace sg {
@@ -414,8 +415,8 @@ __global__ void __launch_bounds__(256) k_generic(DevGrid g, int src, int dst, fl
 // ---------------------------------------------------------------------------
 int stencil_persistent_ctas(int num_sms, int which)
 {
-    static int cache[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    if (cache[which] == 0) {
+    static std::atomic<int> cache[8];  // threads may race to fill it
+    if (cache[which].load(std::memory_order_relaxed) == 0) {
         int per = 1;
         cudaError_t err = cudaSuccess;
         switch (which) {
@@ -426,9 +427,9 @@ int stencil_persistent_ctas(int num_sms, int which)
         }
         if (err != cudaSuccess || per < 1) per = 1;
         if (per > 16) per = 16;
-        cache[which] = per;
+        cache[which].store(per, std::memory_order_relaxed);
     }
-    return cache[which] * num_sms;
+    return cache[which].load(std::memory_order_relaxed) * num_sms;
 }
 
 void launch_clear(const DevGrid &g, cudaStream_t s, int dst, int check_act, const LaunchCfg &lc)

@@ -18,6 +18,7 @@
 // the own leaf's 8 floats in one 256-bit load.  A null neighbour is the zero
 // leaf, so every load is unconditional; an inactive voxel reads 0 because
 // the stored value there is 0.
+#include <atomic>
 #include "sg_common.cuh"
 
 namespace sg {
@@ -396,8 +397,8 @@ __global__ void __launch_bounds__(kSweepThreads, 3) k_sweep_single(DevGrid g, in
 // ---------------------------------------------------------------------------
 static int sweep_ctas(int num_sms, int which)
 {
-    static int cache[4] = {0, 0, 0, 0};
-    if (cache[which] == 0) {
+    static std::atomic<int> cache[4];  // threads may race to fill it
+    if (cache[which].load(std::memory_order_relaxed) == 0) {
         int per = 1;
         cudaError_t err;
         if (which == 0)
@@ -405,9 +406,9 @@ static int sweep_ctas(int num_sms, int which)
         else
             err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sweep_single<SW_BOX27, false, true>, kSweepThreads, 0);
         if (err != cudaSuccess || per < 1) per = 1;
-        cache[which] = per;
+        cache[which].store(per, std::memory_order_relaxed);
     }
-    return cache[which] * num_sms;
+    return cache[which].load(std::memory_order_relaxed) * num_sms;
 }
 
 void launch_sweep_diffuse_box(const DevGrid &g, cudaStream_t s, int src, int tmp, int dst, float coef, int store_tmp,
@@ -475,18 +476,18 @@ __global__ void __launch_bounds__(WARPS * 32, 12 / WARPS) k_batch_diffuse_box(co
 
 int batch_ctas(int num_sms, int warps)
 {
-    static int cache[9] = {0};
+    static std::atomic<int> cache[9];  // threads may race to fill it
     if (warps < 1 || warps > 8) return num_sms;
-    if (cache[warps] == 0) {
+    if (cache[warps].load(std::memory_order_relaxed) == 0) {
         int per = 1;
         cudaError_t err = cudaErrorInvalidValue;
         if (warps == 2) err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_diffuse_box<2>, 64, 0);
         if (warps == 4) err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_diffuse_box<4>, 128, 0);
         if (warps == 8) err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_diffuse_box<8>, 256, 0);
         if (err != cudaSuccess || per < 1) per = 1;
-        cache[warps] = per;
+        cache[warps].store(per, std::memory_order_relaxed);
     }
-    return cache[warps] * num_sms;
+    return cache[warps].load(std::memory_order_relaxed) * num_sms;
 }
 
 void launch_batch_diffuse_box(const BatchGrid *items, int n_grids, int total_tri, float coef, double *acc, int warps,
