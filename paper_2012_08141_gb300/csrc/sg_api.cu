@@ -504,15 +504,17 @@ int run_advect_run(sg_grid *g, size_t &i)
     };
     int slot_q[3] = {-1, -1, -1}, slot_v0[3] = {-1, -1, -1};
     float slot_dt[3] = {0.f, 0.f, 0.f};
-    auto ensure_bounds = [&]() -> int {
-        if (g->dry || g->adv_lo[0]) return SG_OK;
+    // the bound arrays (6 x (cap + 1) x L^3 floats); without the memory for
+    // them the corrections trace the forward path themselves
+    auto ensure_bounds = [&]() -> bool {
+        if (g->dry || g->adv_hi[2]) return true;
         const size_t bytes = sizeof(float) * size_t(g->dev.cap + 1) * g->dev.L * g->dev.L * g->dev.L;
         for (int c = 0; c < 3; ++c) {
-            g->adv_lo[c] = (float *)dev_alloc(g, bytes);
-            g->adv_hi[c] = (float *)dev_alloc(g, bytes);
-            if (!g->adv_lo[c] || !g->adv_hi[c]) return fail(SG_ERR_OOM, "advection bounds");
+            if (!g->adv_lo[c]) g->adv_lo[c] = (float *)dev_alloc(g, bytes);
+            if (!g->adv_hi[c]) g->adv_hi[c] = (float *)dev_alloc(g, bytes);
+            if (!g->adv_lo[c] || !g->adv_hi[c]) return false;
         }
-        return SG_OK;
+        return true;
     };
     auto launch = [&](int mode, const std::vector<int> &ops, const std::vector<int> &macs) -> int {
         int r2;
@@ -559,8 +561,8 @@ int run_advect_run(sg_grid *g, size_t &i)
                         break;
                     }
                 }
+            if (bnd && !ensure_bounds()) bnd = false;
             if (bnd) {
-                if ((r2 = ensure_bounds())) return r2;
                 for (int c = 0; c < 3; ++c) slot_q[c] = -1;
                 for (int c = 0; c < C; ++c) {
                     lo[c] = g->adv_lo[c];
