@@ -184,7 +184,11 @@ int sg_advect(sg_grid *g, int32_t dst, int32_t src, int32_t v0, float dt);
  * velocity and step are one launch of up to three channels sharing the
  * backtrace, and a backward advection whose output a correction reads is
  * fused with it (that output, if scratch and read later by nothing, is not
- * stored) -- the channel fusion of Sec. 8.2. */
+ * stored) -- the channel fusion of Sec. 8.2.  A forward advection of q with
+ * the same velocity and step in the same run, when no op of the run writes q
+ * or the velocity, also stores the clamp bounds, and the correction reads them
+ * instead of tracing the forward path again (identical results;
+ * sg_stats.bounds_reused counts it). */
 int sg_maccormack(sg_grid *g, int32_t dst, int32_t q, int32_t qhat, int32_t qtilde, int32_t v0, float dt);
 
 /* Queue an element-wise struct-for: on every active voxel
