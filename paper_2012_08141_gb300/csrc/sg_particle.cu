@@ -67,17 +67,18 @@ __global__ void __launch_bounds__(256) k_g2p(DevGrid g, float *__restrict__ x, f
 }
 
 // G2P over the bins of the last binned P2G: per leaf, the node velocities of
-// the (L+4)^3 nodes from o - 2 to o + L + 1 (o the leaf origin; every node a
-// stencil with base in [o - 2, o + L - 1] reaches) are staged in shared
-// memory, 0 outside the domain or the allocated leaves, and the leaf's
-// particles read their 27 nodes there.  A particle whose base lies outside
-// that range (its position changed since the binning) reads the grid node by
-// node, as do the particles whose stencil misses the domain (the last key).
+// the (L+2)^3 nodes from o to o + L + 1 (o the leaf origin; every node a
+// stencil with base in [o, o + L - 1] reaches) are staged in shared memory, 0
+// outside the domain or the allocated leaves, and the leaf's particles read
+// their 27 nodes there.  A particle whose base lies outside that range (its
+// position changed since the binning, or a base of -2 / -1 at the low domain
+// face) reads the grid node by node, as do the particles whose stencil misses
+// the domain (the last key).
 template <int L, bool APIC>
 __global__ void __launch_bounds__(256, 4) k_g2p_binned(DevGrid g, float *__restrict__ x, float *__restrict__ v,
                                                        float *__restrict__ C, float dt, int f_mom0, bool pair)
 {
-    constexpr int B = L + 4, NB = B * B * B;
+    constexpr int B = L + 2, NB = B * B * B;  // nodes o .. o + L + 1 of the bin's leaf o
     __shared__ float4 s_u[NB];
     const int N = g.N, R = g.R;
     const float *f0 = g.field[f_mom0], *f1 = g.field[f_mom0 + 1], *f2 = g.field[f_mom0 + 2];
@@ -92,7 +93,7 @@ __global__ void __launch_bounds__(256, 4) k_g2p_binned(DevGrid g, float *__restr
             oi = (int)(b / ((long long)R * R)) * L;
             oj = (int)((b / R) % R) * L;
             ok = (int)(b % R) * L;
-            stage_velocities<L>(g, f0, f1, f2, oi, oj, ok, s_u);
+            stage_velocities_tight<L>(g, f0, f1, f2, oi, oj, ok, s_u);
             __syncthreads();
         } else {
             beg = g.bin_off[oob_key];
@@ -102,11 +103,10 @@ __global__ void __launch_bounds__(256, 4) k_g2p_binned(DevGrid g, float *__restr
             const long long p = g.perm[q];
             const float3 xp = load3(x, p, pair);
             const Spline sx = bspline(xp.x, N), sy = bspline(xp.y, N), sz = bspline(xp.z, N);
-            const int ri = sx.base - oi + 2, rj = sy.base - oj + 2, rk = sz.base - ok + 2;
+            const int ri = sx.base - oi, rj = sy.base - oj, rk = sz.base - ok;
             float3 u;
             float c[9];
-            if (bl < used && (unsigned)ri <= (unsigned)(L + 1) && (unsigned)rj <= (unsigned)(L + 1) &&
-                (unsigned)rk <= (unsigned)(L + 1))
+            if (bl < used && (unsigned)ri < (unsigned)L && (unsigned)rj < (unsigned)L && (unsigned)rk < (unsigned)L)
                 g2p_from_block<B, APIC>(s_u, ri, rj, rk, N, sx, sy, sz, u, c);
             else
                 g2p_from_grid<APIC>(g, f0, f1, f2, sx, sy, sz, u, c);

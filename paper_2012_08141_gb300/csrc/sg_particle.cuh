@@ -156,6 +156,31 @@ __device__ __forceinline__ void stage_velocities(const DevGrid &g, const float *
     }
 }
 
+// The (L+2)^3 nodes from o to o + L + 1 only: every node the stencils of
+// particles with base in the leaf reach (no margin for particles that moved
+// since they were binned).
+template <int L>
+__device__ __forceinline__ void stage_velocities_tight(const DevGrid &g, const float *__restrict__ f0,
+                                                       const float *__restrict__ f1, const float *__restrict__ f2,
+                                                       int oi, int oj, int ok, float4 *s_u)
+{
+    constexpr int LG2 = (L == 8) ? 3 : 2, B = L + 2, NB = B * B * B;
+    const int N = g.N, R = g.R;
+    for (int nd = threadIdx.x; nd < NB; nd += blockDim.x) {
+        const int i = oi + nd / (B * B), j = oj + (nd / B) % B, k = ok + nd % B;
+        float4 u = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (i < N && j < N && k < N) {
+            const int slot = __ldg(g.root + ((long long)(i >> LG2) * R + (j >> LG2)) * R + (k >> LG2));
+            if (slot >= 0) {
+                const long long idx =
+                    ((long long)slot << (3 * LG2)) + (((i & (L - 1)) << LG2) + (j & (L - 1))) * L + (k & (L - 1));
+                u = make_float4(__ldg(f0 + idx), __ldg(f1 + idx), __ldg(f2 + idx), 0.f);
+            }
+        }
+        s_u[nd] = u;
+    }
+}
+
 // G2P of one particle from a staged block of B^3 float4 node velocities (ri,
 // rj, rk: its base relative to the block's first node).  APIC as in
 // g2p_from_grid.
