@@ -674,8 +674,8 @@ def run_ours(args):
     achieved = n_leaves * BYTES_PER_LEAF_FUSED / (avg_ms / 1e3) / 1e9
     achieved_eager = n_leaves * BYTES_PER_LEAF_EAGER / (t_e / len(ms_e)) / 1e9
     kernel_src = os.path.join(ROOT, "paper_2012_08141_gb300", "csrc",
-                              "sg_sweep.cu" if args.variant == 0 else "sg_stencil.cu")
-    traffic = traffic_record(kernel_src)
+                              "sg_stencil.cu" if args.variant == 1 else "sg_sweep.cu")
+    traffic = traffic_record(kernel_src) if args.variant == 0 else None
 
     extra = {}
     if world == 1 and args.only != "fused":
@@ -723,8 +723,8 @@ def run_ours(args):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                          "achieved_active_only": n_active * 8 / (avg_ms / 1e3) / 1e9,
-                         "kernel": ("k_sweep_diffuse_box<false,false,true>" if args.variant == 0
-                                    else "k_diffuse_box<false,false,true>"),
+                         "kernel": {0: "k_sweep_diffuse_box<false,false,true>", 1: "k_diffuse_box<false,false,true>",
+                                    2: "k_sweep_columns<false,false,true>"}[args.variant],
                          "bytes_per_launch": n_leaves * BYTES_PER_LEAF_FUSED},
             "e2e": {"value": world * n_active * e2e_steps / e2e_s if e2e_steps else None, "unit": "voxel-steps/s",
                     "h2d_bytes_per_step": 4 * n_active, "d2h_bytes_per_step": 8},
@@ -817,7 +817,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
-    ap.add_argument("--variant", type=int, default=0, help="stencil kernel family (0 sweep, 1 smem)")
+    ap.add_argument("--variant", type=int, default=0, choices=[0, 1, 2],
+                    help="stencil kernel family (0 sweep, 1 smem, 2 sweep with column-fused step)")
     ap.add_argument("--only", choices=["all", "fused", "band1024", "batched", "particles", "mpm_apic", "multigrid",
                                        "micro", "advection", "ablation", "serving"],
                     default="all",

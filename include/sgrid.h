@@ -408,6 +408,9 @@ int sg_get_stats(sg_grid *g, sg_stats *out);
  * up to FP32 rounding order) ---- */
 #define SG_VARIANT_SWEEP 0 /* register sweep along i, rows via the read-only path */
 #define SG_VARIANT_SMEM 1  /* leaf + halo staged in shared memory */
+#define SG_VARIANT_SWEEP_COLUMNS 2 /* register sweep; the fused step sweeps columns of up
+                                      to three leaves adjacent in i (same results; slower
+                                      on the band: fewer, longer tasks) */
 
 /* Select the stencil kernel family used by ops flushed from now on. */
 int sg_set_stencil_variant(sg_grid *g, int32_t variant);

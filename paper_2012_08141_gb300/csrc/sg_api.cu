@@ -91,6 +91,7 @@ struct sg_grid {
     std::set<std::pair<const sg_grid *, unsigned long long>> applied_restrict;
     unsigned long long lg_calls = 0;
     unsigned long long rmask_ver = 0;  // list version the region masks were built from (0 = never)
+    unsigned long long colgrp_ver = 0; // list version the column records were built from (0 = never)
     int max_fuse = kMaxEwOps;          // element-wise ops per fused launch
     int flush_period = 0;              // flush once the queue holds this many ops (0: on sync / sg_flush only)
     long long known_leaves = 0;
@@ -301,11 +302,15 @@ int run_struct_for_group(sg_grid *g, size_t &i)
         const size_t after = i + (with_sum ? 3 : 2);
         const bool store_t = !(dse && a.dst_scratch && !read_later(g, after, a.dst));
         if (!store_t) g->stats.stores_removed++;
-        if (g->lc.variant == kVariantSweep && g->rmask_ver != g->list_ver) {
-            // region masks are derived from the structure, cached with the list
-            if (!g->dry) launch_region_masks(g->dev, g->stream, g->lc);
+        // region masks (and, for the column sweep, the column records) are
+        // derived from the structure, cached with the list
+        const bool sweep = g->lc.variant == kVariantSweep || g->lc.variant == kVariantSweepColumns;
+        const bool need_cols = g->lc.variant == kVariantSweepColumns && g->colgrp_ver != g->list_ver;
+        if ((sweep && g->rmask_ver != g->list_ver) || need_cols) {
+            if (!g->dry) launch_region_masks(g->dev, g->stream, g->lc, need_cols);
             if ((rc = after_launch(g, "region masks"))) return rc;
             g->rmask_ver = g->list_ver;
+            if (need_cols) g->colgrp_ver = g->list_ver;
         }
         if (!g->dry)
             launch_diffuse_box(g->dev, g->stream, a.src, a.dst, b->dst, a.coef, store_t ? 1 : 0, check,
@@ -1060,6 +1065,9 @@ int sg_create(const sg_desc *desc, void *cuda_stream, sg_grid **out)
         {(void **)&d.list_slot, sizeof(int32_t) * d.cap},
         {(void **)&d.list_b, sizeof(int32_t) * d.cap},
         {(void **)&d.nbr, sizeof(int32_t) * 27 * d.cap},
+        {(void **)&d.ent_of_slot, sizeof(int32_t) * d.cap},
+        {(void **)&d.col_grp, sizeof(int32_t) * 9 * d.cap},
+        {(void **)&d.col_cnt, sizeof(int32_t) * 4},
         {(void **)&d.rmask, (L == 8 ? sizeof(uint32_t) * 40 : size_t(4)) * d.cap},
         {(void **)&d.need, (size_t)nr},
         {(void **)&d.tile_status, sizeof(unsigned long long) * g->num_tiles},
@@ -1795,7 +1803,7 @@ int sg_read_sums(sg_grid *g, double *host, int64_t n)
 
 int sg_set_stencil_variant(sg_grid *g, int32_t variant)
 {
-    if (!g || (variant != SG_VARIANT_SWEEP && variant != SG_VARIANT_SMEM))
+    if (!g || (variant != SG_VARIANT_SWEEP && variant != SG_VARIANT_SMEM && variant != SG_VARIANT_SWEEP_COLUMNS))
         return fail(SG_ERR_INVALID, "bad grid or variant");
     g->lc.variant = variant;
     return SG_OK;
@@ -1918,7 +1926,7 @@ int grid_prepare_batch(sg_grid *g, int src, int tmp, int dst, BatchGrid out[2], 
         g->list_ver = g->mask_ver;
     }
     if (!rc && g->rmask_ver != g->list_ver) {
-        launch_region_masks(g->dev, g->stream, g->lc);
+        launch_region_masks(g->dev, g->stream, g->lc, false);
         rc = after_launch(g, "region masks");
         g->rmask_ver = g->list_ver;
     }

@@ -77,12 +77,20 @@ struct DevGrid {
     int32_t *perm;
     int32_t *perm_alt;  // the next binning's order, built from the last one (then swapped)
     int32_t *bin_list;  // the leaves holding particles, in no particular order
+    // column sweeps of the fused step: list entry of each slot (written by
+    // the list generation), column records bucketed by length and their
+    // counts (built with the region masks); allocated with the grid
+    int32_t *ent_of_slot;
+    int32_t *col_grp;   // [3][cap][3]
+    int32_t *col_cnt;   // [4]
 };
 
 // Stencil kernel families for 8^3 leaves (the autotuner picks one).
 enum StencilVariant : int {
     kVariantSweep = 0,  // register sweep, rows loaded through the read-only path
     kVariantSmem = 1,   // leaf + halo staged in shared memory by plain loads
+    kVariantSweepColumns = 2,  // register sweep; the fused step sweeps columns of
+                               // leaves adjacent in i (see k_sweep_columns)
 };
 
 // Launch shapes chosen by the host.
@@ -117,7 +125,10 @@ void launch_clear_list(const DevGrid &g, cudaStream_t s);
 // 10^3 region around the leaf, the activity bits of the 10 rows ti = 0..9 of
 // that column: row (ti, tj) covers region voxels (ti+1, tj+1, r+1), r = 0..9,
 // as 10 bits; rows 3w..3w+2 are packed into word w of rmask[e][tj][0..3].
-void launch_region_masks(const DevGrid &g, cudaStream_t s, const LaunchCfg &lc);
+// The fused sweep's region masks of the current list; with columns also the
+// column records of the column sweep (ent_of_slot is written by the list
+// generation).
+void launch_region_masks(const DevGrid &g, cudaStream_t s, const LaunchCfg &lc, bool columns);
 void launch_listgen(const DevGrid &g, cudaStream_t s, int force, unsigned long long call_idx,
                     int num_tiles, int test_wait);
 // Field f of the listed leaves to / from a dense list-order buffer: the
@@ -144,6 +155,8 @@ void launch_diffuse7(const DevGrid &g, cudaStream_t s, int src, int dst, float c
                      int check_act, int sum_slot, const LaunchCfg &lc);
 void launch_box27(const DevGrid &g, cudaStream_t s, int src, int dst, int check_act,
                   int sum_slot, const LaunchCfg &lc);
+void launch_sweep_columns(const DevGrid &g, cudaStream_t s, int src, int tmp, int dst, float coef, int store_tmp,
+                          int check_act, int sum_slot, const LaunchCfg &lc);
 void launch_diffuse_box(const DevGrid &g, cudaStream_t s, int src, int tmp, int dst, float coef,
                         int store_tmp, int check_act, int sum_slot, const LaunchCfg &lc);
 void launch_sum(const DevGrid &g, cudaStream_t s, int src, int sum_slot, const LaunchCfg &lc);

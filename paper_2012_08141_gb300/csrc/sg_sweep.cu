@@ -233,6 +233,227 @@ __device__ __forceinline__ float sweep_db_triple(const DevGrid &g, const float *
     }
 }
 
+// ---------------------------------------------------------------------------
+// Column sweeps: the same fused step over a run of G leaves adjacent in i
+// (G <= 3), swept in one pass, so the i-halo planes between them are loaded
+// and the t planes between them computed once: 8G + 4 x planes and 8G + 2 t
+// planes instead of 12G and 10G.  A warp takes three columns of the same G
+// (lanes 10*w + tj as in the triple sweep); the columns come from the list by
+// k_column_groups.  x plane ri of a column: ri < 2 the i-1 neighbour of its
+// first leaf, ri >= 8G + 2 the i+1 neighbour of its last, else leaf
+// (ri - 2) / 8; local plane (ri - 2) & 7.
+// ---------------------------------------------------------------------------
+// One step of the column sweep: t plane s from the x window (xa, xb, xc =
+// planes s, s+1, s+2; ea = the edge row of plane s+1), its j-sums p0, and,
+// from s = 2 on, output plane s - 2 into `own`.  Returns the output sum.
+template <bool STORE_T, bool CHECK, bool SUM>
+__device__ __forceinline__ float column_step(const DevGrid &g, float *__restrict__ y, float *__restrict__ tout,
+                                             float coef, float c6, int tj, bool lo_edge, bool hi_edge, bool outlane,
+                                             bool valid, uint32_t mt, uint32_t mprev, bool out, int own, int t_own,
+                                             int t_plane, int o_plane, const float (&xa)[12], const float (&xb)[12],
+                                             const float (&xc)[12], const float (&ea)[12], float (&p1)[10],
+                                             float (&p2)[10])
+{
+    float up[12], dn[12];
+    shfl_row<12>(xb, up, dn);
+    float t[10];
+#pragma unroll
+    for (int q = 0; q < 10; ++q) {
+        const float jm = lo_edge ? ea[q + 1] : up[q + 1];
+        const float jp = hi_edge ? ea[q + 1] : dn[q + 1];
+        const float nb = ((xb[q] + xb[q + 2]) + (xa[q + 1] + xc[q + 1])) + (jm + jp);
+        t[q] = pick(mt, q, fmaf(coef, nb, c6 * xb[q + 1]));
+    }
+    if (STORE_T && t_plane >= 0 && outlane && valid) {
+        const int orow = t_plane * 8 + (tj - 1);
+        if (CHECK) sweep_check_row(g, t_own, orow, (mt >> 1) & 0xffu);
+        float *o = tout + (long long)t_own * 512 + orow * 8;
+        stg4(o, t[1], t[2], t[3], t[4]);
+        stg4(o + 4, t[5], t[6], t[7], t[8]);
+    }
+    float tu[10], td[10], p0[10];
+#pragma unroll
+    for (int q = 0; q < 10; ++q) {
+        tu[q] = __shfl_up_sync(kFull, t[q], 1);
+        td[q] = __shfl_down_sync(kFull, t[q], 1);
+    }
+#pragma unroll
+    for (int q = 0; q < 10; ++q) p0[q] = (tu[q] + t[q]) + td[q];
+    float part = 0.f;
+    if (out) {
+        float S[10];
+#pragma unroll
+        for (int q = 0; q < 10; ++q) S[q] = (p2[q] + p1[q]) + p0[q];
+        const uint32_t bits = (mprev >> 1) & 0xffu;
+        float o[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) o[k] = pick(bits, k, ((S[k] + S[k + 1]) + S[k + 2]) * (1.f / 27.f));
+        if (outlane && valid) {
+            const int orow = o_plane * 8 + (tj - 1);
+            if (CHECK) sweep_check_row(g, own, orow, bits);
+            float *op = y + (long long)own * 512 + orow * 8;
+            stg4(op, o[0], o[1], o[2], o[3]);
+            stg4(op + 4, o[4], o[5], o[6], o[7]);
+            if (SUM) part = ((o[0] + o[1]) + (o[2] + o[3])) + ((o[4] + o[5]) + (o[6] + o[7]));
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 10; ++q) {
+        p2[q] = p1[q];
+        p1[q] = p0[q];
+    }
+    return part;
+}
+
+__device__ __forceinline__ void slide(float (&xa)[12], float (&xb)[12], float (&xc)[12], const float (&xn)[12],
+                                      float (&ea)[12], const float (&eb)[12])
+{
+#pragma unroll
+    for (int q = 0; q < 12; ++q) {
+        xa[q] = xb[q];
+        xb[q] = xc[q];
+        xc[q] = xn[q];
+        ea[q] = eb[q];
+    }
+}
+
+// The column of G <= 3 leaves (list entries rec[0 .. G-1]) for this lane's
+// sub-warp.  A prologue computes t planes 0 and 1 from the i-1 halo of the
+// first leaf; then a loop over the leaves m computes, in eight unrolled steps
+// each, t planes 8m + 2 .. 8m + 9 and output planes 8m .. 8m + 7 of leaf m.
+// The slots of leaf m ("cur") and of the next leaf, or the i+1 halo after
+// the last one ("nxt"), roll along, so the code is the same for every leaf
+// and every G.
+template <bool STORE_T, bool CHECK, bool SUM>
+__device__ __forceinline__ float sweep_db_column(const DevGrid &g, const float *__restrict__ x, float *__restrict__ y,
+                                                 float *__restrict__ tout, float coef, const int32_t *rec, int G,
+                                                 bool valid)
+{
+    const int lane = lane_id();
+    const int sub = lane / 10;
+    const int tj = lane - sub * 10;
+    const int rj = tj + 1;
+    const int djx = (rj < 2) ? 0 : (rj < 10 ? 1 : 2);
+    const int lj = (rj - 2) & 7;
+    const int lje = (tj == 0) ? 6 : 1;
+    const bool lo_edge = (tj == 0), hi_edge = (tj == 9);
+    const bool outlane = (tj >= 1 && tj <= 8);
+    const float c6 = 1.f - 6.f * coef;
+    const int Z = (int)g.cap;
+    const bool edge = lo_edge || hi_edge;
+    auto slots = [&](int e, int dirow, int (&sl)[3]) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) sl[d] = valid ? __ldg(g.nbr + (long long)e * 27 + dirow * 9 + djx * 3 + d) : Z;
+    };
+    auto row = [&](const int (&sl)[3], int local, float(&v)[12]) { row12v(x, sl[0], sl[1], sl[2], local * 8 + lj, v); };
+    auto erow = [&](const int (&sl)[3], int local, float(&v)[12]) {
+        row12v(x, edge ? sl[0] : Z, edge ? sl[1] : Z, edge ? sl[2] : Z, local * 8 + lje, v);
+    };
+    auto mword = [&](int e, int r) -> uint32_t {
+        return valid ? (__ldg(g.rmask + (long long)e * 40 + tj * 4 + r / 3) >> (10 * (r % 3))) & 0x3ffu : 0u;
+    };
+    int e_cur = valid ? __ldg(rec) : 0;
+    int e_nxt = (valid && G > 1) ? __ldg(rec + 1) : -1;
+    int lo[3], cur[3], nxt[3];
+    slots(e_cur, 0, lo);
+    slots(e_cur, 1, cur);
+    if (G > 1) slots(e_nxt, 1, nxt);
+    else slots(e_cur, 2, nxt);
+    float xa[12], xb[12], xc[12], xn[12], ea[12], eb[12];
+#pragma unroll
+    for (int q = 0; q < 12; ++q) xn[q] = 0.f;
+    row(lo, 6, xa);
+    row(lo, 7, xb);
+    row(cur, 0, xc);
+    erow(lo, 7, ea);
+    float p1[10], p2[10];
+    float part = 0.f;
+    // prologue: t planes 0, 1 (rows 0, 1 of leaf 0's t-region mask)
+    uint32_t m0 = mword(e_cur, 0), m1 = mword(e_cur, 1);
+    row(cur, 1, xn);
+    erow(cur, 0, eb);
+    part += column_step<STORE_T, CHECK, SUM>(g, y, tout, coef, c6, tj, lo_edge, hi_edge, outlane, valid, m0, 0u, false,
+                                              0, 0, -1, 0, xa, xb, xc, ea, p1, p2);
+    slide(xa, xb, xc, xn, ea, eb);
+    row(cur, 2, xn);
+    erow(cur, 1, eb);
+    part += column_step<STORE_T, CHECK, SUM>(g, y, tout, coef, c6, tj, lo_edge, hi_edge, outlane, valid, m1, m0, false,
+                                              0, cur[1], 0, 0, xa, xb, xc, ea, p1, p2);
+    slide(xa, xb, xc, xn, ea, eb);
+    uint32_t mprev = m1;
+    for (int m = 0; m < G; ++m) {
+        const bool last = m == G - 1;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            // x plane 8m + k + 5 (local (k + 3) & 7 of leaf m, or of the next
+            // leaf / the i+1 halo from k = 5); none after the last halo plane
+            if (k <= 4) row(cur, k + 3, xn);
+            else if (!(last && k == 7)) row(nxt, k - 5, xn);
+            // edge row of x plane 8m + k + 4
+            if (k <= 5) erow(cur, k + 2, eb);
+            else erow(nxt, k - 6, eb);
+            // t plane 8m + k + 2: row k + 2 of leaf m's mask, or row 1 of the
+            // next leaf's for k = 7 (row 9 of leaf m after the last leaf)
+            const uint32_t mt = k < 7 ? mword(e_cur, k + 2) : (last ? mword(e_cur, 9) : mword(e_nxt, 1));
+            const int t_own = k < 7 ? cur[1] : nxt[1];
+            const int t_plane = k < 7 ? k + 1 : (last ? -1 : 0);
+            part += column_step<STORE_T, CHECK, SUM>(g, y, tout, coef, c6, tj, lo_edge, hi_edge, outlane, valid, mt,
+                                                      mprev, true, cur[1], t_own, t_plane, k, xa, xb, xc, ea, p1, p2);
+            mprev = mt;
+            slide(xa, xb, xc, xn, ea, eb);
+        }
+        // roll the slots: leaf m + 1 becomes current, the one after it (or
+        // the i+1 halo of the last leaf) next
+        if (!last) {
+#pragma unroll
+            for (int d = 0; d < 3; ++d) cur[d] = nxt[d];
+            e_cur = e_nxt;
+            if (m + 2 < G) {
+                e_nxt = valid ? __ldg(rec + m + 2) : -1;
+                slots(e_nxt, 1, nxt);
+            } else {
+                slots(e_cur, 2, nxt);
+            }
+        }
+    }
+    return part;
+}
+
+// Fused diffuse7 -> box27 (+ sum) over the columns of one grid: the column
+// records are bucketed by length (G = 3, 2, 1 at grp + (G - 1) * cap * 3, three
+// entries each, counts in cnt[G - 1]); warps stride over tasks of three
+// columns of one length, the longest first.
+template <bool STORE_T, bool CHECK, bool SUM>
+__global__ void __launch_bounds__(kSweepThreads, 3) k_sweep_columns(DevGrid g, int src, int tmp, int dst, float coef,
+                                                                   int sum_slot)
+{
+    __shared__ double s_red[kSweepThreads / 32];
+    const long long cap3 = g.cap * 3;
+    const int c3 = g.col_cnt[2], c2 = g.col_cnt[1], c1 = g.col_cnt[0];
+    const int t3 = (c3 + 2) / 3, t2 = (c2 + 2) / 3, t1 = (c1 + 2) / 3;
+    const int warps_total = gridDim.x * (kSweepThreads / 32);
+    const int sub = lane_id() / 10;
+    double acc = 0.0;
+    for (int t = blockIdx.x * (kSweepThreads / 32) + (threadIdx.x >> 5); t < t3 + t2 + t1; t += warps_total) {
+        const int G = t < t3 ? 3 : (t < t3 + t2 ? 2 : 1);
+        const int j = 3 * (t < t3 ? t : (t < t3 + t2 ? t - t3 : t - t3 - t2)) + sub;
+        const int cnt = G == 3 ? c3 : (G == 2 ? c2 : c1);
+        acc += (double)sweep_db_column<STORE_T, CHECK, SUM>(g, g.field[src], g.field[dst], g.field[tmp], coef,
+                                                            g.col_grp + (G - 1) * cap3 + 3LL * j, G,
+                                                            sub < 3 && j < cnt);
+    }
+    if (SUM) {
+        acc = warp_sum(acc);
+        if (lane_id() == 0) s_red[threadIdx.x >> 5] = acc;
+        __syncthreads();
+        double tot = 0.0;
+        if (threadIdx.x == 0)
+            for (int w = 0; w < kSweepThreads / 32; ++w) tot += s_red[w];
+        finish_reduction(g, tot, sum_slot);
+    }
+}
+
+
 // Fused diffuse7 -> box27 (+ sum) over one grid's list: warps stride over
 // leaf triples.
 template <bool STORE_T, bool CHECK, bool SUM>
@@ -403,8 +624,10 @@ static int sweep_ctas(int num_sms, int which)
         cudaError_t err;
         if (which == 0)
             err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sweep_diffuse_box<false, false, true>, kSweepThreads, 0);
-        else
+        else if (which == 1)
             err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sweep_single<SW_BOX27, false, true>, kSweepThreads, 0);
+        else
+            err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sweep_columns<false, false, true>, kSweepThreads, 0);
         if (err != cudaSuccess || per < 1) per = 1;
         cache[which].store(per, std::memory_order_relaxed);
     }
@@ -425,6 +648,22 @@ void launch_sweep_diffuse_box(const DevGrid &g, cudaStream_t s, int src, int tmp
         else { if (sum) SG_SW(false, false, true); else SG_SW(false, false, false); }
     }
 #undef SG_SW
+}
+
+void launch_sweep_columns(const DevGrid &g, cudaStream_t s, int src, int tmp, int dst, float coef, int store_tmp,
+                          int check_act, int sum_slot, const LaunchCfg &lc)
+{
+    const int ctas = sweep_ctas(lc.num_sms, 2);
+    const bool sum = sum_slot >= 0;
+#define SG_SC(ST, CK, SU) k_sweep_columns<ST, CK, SU><<<ctas, kSweepThreads, 0, s>>>(g, src, tmp, dst, coef, sum_slot)
+    if (store_tmp) {
+        if (check_act) { if (sum) SG_SC(true, true, true); else SG_SC(true, true, false); }
+        else { if (sum) SG_SC(true, false, true); else SG_SC(true, false, false); }
+    } else {
+        if (check_act) { if (sum) SG_SC(false, true, true); else SG_SC(false, true, false); }
+        else { if (sum) SG_SC(false, false, true); else SG_SC(false, false, false); }
+    }
+#undef SG_SC
 }
 
 void launch_sweep_single(const DevGrid &g, cudaStream_t s, int op, int src, int dst, float coef, int check_act,

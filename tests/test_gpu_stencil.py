@@ -91,7 +91,7 @@ def run_band(g, og, steps, slot0=0):
     return cur, np.array(sums_ref)
 
 
-@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("variant", [0, 1, 2])
 @pytest.mark.parametrize("mode", list(OPTS))
 def test_band_128_100_steps(mode, variant):
     lo2, hi2 = band_bounds(40.0, 56.0)
@@ -177,7 +177,7 @@ def test_empty_grid():
 def test_ragged_domains(N, r0, r1, strict):
     lo2, hi2 = band_bounds(r0, r1)
     spec = ShellSpec(N, 8, lo2, hi2, strict, 11)
-    for mode, variant in [("fused", 0), ("eager", 0), ("fused", 1), ("eager", 1)]:
+    for mode, variant in [("fused", 0), ("eager", 0), ("fused", 1), ("eager", 1), ("fused", 2)]:
         g, og = shell_pair(spec, n_fields=3, opts=OPTS[mode], scratch_mask=0b010, variant=variant)
         cur, sums_ref = run_band(g, og, 7)
         assert rel_linf(g.read_field(0), og.read_field(cur)) <= TOL
@@ -189,7 +189,7 @@ def test_ragged_domains(N, r0, r1, strict):
 def test_full_domain_boundary_reads_zero():
     """Every voxel active: out-of-domain neighbours read 0 at all six faces."""
     spec = ShellSpec(24, 8, 0, 10 ** 9, False, 2)
-    for mode, variant in [("fused", 0), ("eager", 0), ("fused", 1), ("eager", 1)]:
+    for mode, variant in [("fused", 0), ("eager", 0), ("fused", 1), ("eager", 1), ("fused", 2)]:
         g, og = shell_pair(spec, n_fields=3, opts=OPTS[mode], variant=variant)
         cur, _ = run_band(g, og, 5)
         assert rel_linf(g.read_field(0), og.read_field(cur)) <= TOL
@@ -347,3 +347,38 @@ def test_maximum_resolution_sparse_clusters(L):
         assert np.max(np.abs(sums - sums_ref) / np.maximum(np.abs(sums_ref), 1e-30)) <= TOL
         g.close()
         del og
+
+
+@pytest.mark.parametrize("store_t", [False, True])
+def test_column_sweep_equals_leaf_sweep(store_t):
+    """The column sweep (runs of leaves adjacent in i swept in one pass) and
+    the leaf-at-a-time sweep run the same arithmetic per voxel: fields after
+    five fused steps on the 512^3 band are bit-identical, sums agree to FP32
+    partial-sum rounding; with the intermediate stored (not scratch) that field
+    is bit-identical too."""
+    sg = sgmod()
+    spec = band512()
+    grids = []
+    for variant in (sg.SG_VARIANT_SWEEP_COLUMNS, sg.SG_VARIANT_SWEEP):
+        g = sg.Grid(spec.N, 3, 3, max_leaves=32768, max_sums=5, scratch_mask=0 if store_t else 0b010)
+        g.set_stencil_variant(variant)
+        g.activate_shell(spec.lo2, spec.hi2, spec.lo_strict)
+        g.fill_hash(0, 41)
+        grids.append(g)
+    for s in range(5):
+        for g in grids:
+            g.clear(1)
+            g.diffuse7(0, 1, 0.1)
+            g.box27(1, 2)
+            g.swap(0, 2)
+            g.reduce_sum(0, s)
+            if store_t:
+                g.reduce_sum(1, s)   # reads t later: the intermediate is stored
+            g.flush()
+    a, b = grids
+    np.testing.assert_array_equal(a.read_field(0), b.read_field(0))
+    if store_t:
+        np.testing.assert_array_equal(a.read_field(1), b.read_field(1))
+    np.testing.assert_allclose(a.read_sums(5), b.read_sums(5), rtol=1e-6)
+    for g in grids:
+        g.close()
