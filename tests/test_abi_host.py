@@ -527,3 +527,25 @@ def test_staged_upload_tickets():
     g.write_field_staged(1, t3)
     assert g.stats()["ops_enqueued"] == q0 + 1
     g.flush()
+
+
+def test_stencil_variants_and_their_launch_counts():
+    """Every stencil kernel family keeps the fused band step at one launch;
+    the column sweep builds its column records in the region-mask launch."""
+    with pytest.raises(sg.SgError):
+        dry().set_stencil_variant(3)
+    with pytest.raises(sg.SgError):
+        dry().set_stencil_variant(-1)
+    s = band512()
+    for variant, first in ((sg.SG_VARIANT_SWEEP, 2), (sg.SG_VARIANT_SWEEP_COLUMNS, 2), (sg.SG_VARIANT_SMEM, 1)):
+        g = dry(512)
+        g.set_stencil_variant(variant)
+        g.activate_shell(s.lo2, s.hi2, s.lo_strict)
+        g.list_gen()
+        g.flush()
+        assert [launches(g, lambda: cfg2_step(g, 0)) for _ in range(3)] == [first, 1, 1], variant
+        g.set_stencil_variant(sg.SG_VARIANT_SWEEP if variant != sg.SG_VARIANT_SWEEP else sg.SG_VARIANT_SWEEP_COLUMNS)
+        # switching between the two sweeps: the column records (or the region
+        # masks) are made current once for the unchanged list
+        n = launches(g, lambda: cfg2_step(g, 0))
+        assert n == (1 if variant == sg.SG_VARIANT_SWEEP_COLUMNS else 2), variant
