@@ -724,7 +724,8 @@ def run_ours(args):
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                          "achieved_active_only": n_active * 8 / (avg_ms / 1e3) / 1e9,
                          "kernel": {0: "k_sweep_diffuse_box<false,false,true>", 1: "k_diffuse_box<false,false,true>",
-                                    2: "k_sweep_columns<false,false,true>"}[args.variant],
+                                    2: "k_sweep_columns<false,false,true>",
+                                    3: "k_sweep_jruns<false,false,true>"}[args.variant],
                          "bytes_per_launch": n_leaves * BYTES_PER_LEAF_FUSED},
             "e2e": {"value": world * n_active * e2e_steps / e2e_s if e2e_steps else None, "unit": "voxel-steps/s",
                     "h2d_bytes_per_step": 4 * n_active, "d2h_bytes_per_step": 8},
@@ -817,8 +818,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
-    ap.add_argument("--variant", type=int, default=0, choices=[0, 1, 2],
-                    help="stencil kernel family (0 sweep, 1 smem, 2 sweep with column-fused step)")
+    ap.add_argument("--variant", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="stencil kernel family (0 sweep, 1 smem, 2 sweep over i-columns, 3 sweep over j-runs)")
     ap.add_argument("--only", choices=["all", "fused", "band1024", "batched", "particles", "mpm_apic", "multigrid",
                                        "micro", "advection", "ablation", "serving"],
                     default="all",

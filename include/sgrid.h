@@ -411,6 +411,9 @@ int sg_get_stats(sg_grid *g, sg_stats *out);
 #define SG_VARIANT_SWEEP_COLUMNS 2 /* register sweep; the fused step sweeps columns of up
                                       to three leaves adjacent in i (same results; slower
                                       on the band: fewer, longer tasks) */
+#define SG_VARIANT_SWEEP_JRUNS 3   /* register sweep; the fused step gives each warp
+                                      three leaves from runs adjacent in j, so rows at the
+                                      leaves' shared faces are loaded once (same results) */
 
 /* Select the stencil kernel family used by ops flushed from now on. */
 int sg_set_stencil_variant(sg_grid *g, int32_t variant);

@@ -91,7 +91,8 @@ struct sg_grid {
     std::set<std::pair<const sg_grid *, unsigned long long>> applied_restrict;
     unsigned long long lg_calls = 0;
     unsigned long long rmask_ver = 0;  // list version the region masks were built from (0 = never)
-    unsigned long long colgrp_ver = 0; // list version the column records were built from (0 = never)
+    unsigned long long colgrp_ver = 0; // list version the run records were built from (0 = never)
+    int colgrp_axis = kGroupNone;      // axis they group leaves along
     int max_fuse = kMaxEwOps;          // element-wise ops per fused launch
     int flush_period = 0;              // flush once the queue holds this many ops (0: on sync / sg_flush only)
     long long known_leaves = 0;
@@ -302,15 +303,20 @@ int run_struct_for_group(sg_grid *g, size_t &i)
         const size_t after = i + (with_sum ? 3 : 2);
         const bool store_t = !(dse && a.dst_scratch && !read_later(g, after, a.dst));
         if (!store_t) g->stats.stores_removed++;
-        // region masks (and, for the column sweep, the column records) are
+        // region masks (and, for the grouped sweeps, the run records) are
         // derived from the structure, cached with the list
-        const bool sweep = g->lc.variant == kVariantSweep || g->lc.variant == kVariantSweepColumns;
-        const bool need_cols = g->lc.variant == kVariantSweepColumns && g->colgrp_ver != g->list_ver;
-        if ((sweep && g->rmask_ver != g->list_ver) || need_cols) {
-            if (!g->dry) launch_region_masks(g->dev, g->stream, g->lc, need_cols);
+        const int v = g->lc.variant;
+        const bool sweep = v == kVariantSweep || v == kVariantSweepColumns || v == kVariantSweepJRuns;
+        const int axis = v == kVariantSweepColumns ? kGroupI : (v == kVariantSweepJRuns ? kGroupJ : kGroupNone);
+        const bool need_runs = axis != kGroupNone && (g->colgrp_ver != g->list_ver || g->colgrp_axis != axis);
+        if ((sweep && g->rmask_ver != g->list_ver) || need_runs) {
+            if (!g->dry) launch_region_masks(g->dev, g->stream, g->lc, need_runs ? axis : kGroupNone);
             if ((rc = after_launch(g, "region masks"))) return rc;
             g->rmask_ver = g->list_ver;
-            if (need_cols) g->colgrp_ver = g->list_ver;
+            if (need_runs) {
+                g->colgrp_ver = g->list_ver;
+                g->colgrp_axis = axis;
+            }
         }
         if (!g->dry)
             launch_diffuse_box(g->dev, g->stream, a.src, a.dst, b->dst, a.coef, store_t ? 1 : 0, check,
@@ -1803,7 +1809,7 @@ int sg_read_sums(sg_grid *g, double *host, int64_t n)
 
 int sg_set_stencil_variant(sg_grid *g, int32_t variant)
 {
-    if (!g || (variant != SG_VARIANT_SWEEP && variant != SG_VARIANT_SMEM && variant != SG_VARIANT_SWEEP_COLUMNS))
+    if (!g || variant < SG_VARIANT_SWEEP || variant > SG_VARIANT_SWEEP_JRUNS)
         return fail(SG_ERR_INVALID, "bad grid or variant");
     g->lc.variant = variant;
     return SG_OK;
@@ -1926,7 +1932,7 @@ int grid_prepare_batch(sg_grid *g, int src, int tmp, int dst, BatchGrid out[2], 
         g->list_ver = g->mask_ver;
     }
     if (!rc && g->rmask_ver != g->list_ver) {
-        launch_region_masks(g->dev, g->stream, g->lc, false);
+        launch_region_masks(g->dev, g->stream, g->lc, kGroupNone);
         rc = after_launch(g, "region masks");
         g->rmask_ver = g->list_ver;
     }

@@ -77,9 +77,10 @@ struct DevGrid {
     int32_t *perm;
     int32_t *perm_alt;  // the next binning's order, built from the last one (then swapped)
     int32_t *bin_list;  // the leaves holding particles, in no particular order
-    // column sweeps of the fused step: list entry of each slot (written by
-    // the list generation), column records bucketed by length and their
-    // counts (built with the region masks); allocated with the grid
+    // grouped sweeps of the fused step: list entry of each slot (written by
+    // the list generation), the records of runs of adjacent leaves (along i
+    // for the column sweep, along j for the j-run sweep) bucketed by length,
+    // and their counts (built with the region masks); allocated with the grid
     int32_t *ent_of_slot;
     int32_t *col_grp;   // [3][cap][3]
     int32_t *col_cnt;   // [4]
@@ -91,7 +92,12 @@ enum StencilVariant : int {
     kVariantSmem = 1,   // leaf + halo staged in shared memory by plain loads
     kVariantSweepColumns = 2,  // register sweep; the fused step sweeps columns of
                                // leaves adjacent in i (see k_sweep_columns)
+    kVariantSweepJRuns = 3,    // register sweep; a warp's leaves are runs of leaves
+                               // adjacent in j (see k_sweep_jruns)
 };
+
+// Axis along which launch_region_masks groups adjacent leaves into records.
+enum GroupAxis : int { kGroupNone = 0, kGroupI = 1, kGroupJ = 2 };
 
 // Launch shapes chosen by the host.
 struct LaunchCfg {
@@ -128,7 +134,7 @@ void launch_clear_list(const DevGrid &g, cudaStream_t s);
 // The fused sweep's region masks of the current list; with columns also the
 // column records of the column sweep (ent_of_slot is written by the list
 // generation).
-void launch_region_masks(const DevGrid &g, cudaStream_t s, const LaunchCfg &lc, bool columns);
+void launch_region_masks(const DevGrid &g, cudaStream_t s, const LaunchCfg &lc, int group_axis);
 void launch_listgen(const DevGrid &g, cudaStream_t s, int force, unsigned long long call_idx,
                     int num_tiles, int test_wait);
 // Field f of the listed leaves to / from a dense list-order buffer: the
@@ -157,6 +163,8 @@ void launch_box27(const DevGrid &g, cudaStream_t s, int src, int dst, int check_
                   int sum_slot, const LaunchCfg &lc);
 void launch_sweep_columns(const DevGrid &g, cudaStream_t s, int src, int tmp, int dst, float coef, int store_tmp,
                           int check_act, int sum_slot, const LaunchCfg &lc);
+void launch_sweep_jruns(const DevGrid &g, cudaStream_t s, int src, int tmp, int dst, float coef, int store_tmp,
+                        int check_act, int sum_slot, const LaunchCfg &lc);
 void launch_diffuse_box(const DevGrid &g, cudaStream_t s, int src, int tmp, int dst, float coef,
                         int store_tmp, int check_act, int sum_slot, const LaunchCfg &lc);
 void launch_sum(const DevGrid &g, cudaStream_t s, int src, int sum_slot, const LaunchCfg &lc);

@@ -449,7 +449,7 @@ static void launch_single(const DevGrid &g, cudaStream_t s, int src, int dst, fl
                           int sum_slot, const LaunchCfg &lc)
 {
     const bool sum = sum_slot >= 0;
-    if (g.L == 8 && (lc.variant == kVariantSweep || lc.variant == kVariantSweepColumns)) {
+    if (g.L == 8 && lc.variant != kVariantSmem) {
         launch_sweep_single(g, s, OP, src, dst, coef, check_act, sum_slot, lc);
     } else if (g.L == 8) {
         const int ctas = stencil_persistent_ctas(lc.num_sms, 0);
@@ -493,6 +493,10 @@ void launch_diffuse_box(const DevGrid &g, cudaStream_t s, int src, int tmp, int 
     }
     if (lc.variant == kVariantSweepColumns) {
         launch_sweep_columns(g, s, src, tmp, dst, coef, store_tmp, check_act, sum_slot, lc);
+        return;
+    }
+    if (lc.variant == kVariantSweepJRuns) {
+        launch_sweep_jruns(g, s, src, tmp, dst, coef, store_tmp, check_act, sum_slot, lc);
         return;
     }
     const int ctas = stencil_persistent_ctas(lc.num_sms, 1);

@@ -446,7 +446,7 @@ void launch_listgen(const DevGrid &g, cudaStream_t s, int force, unsigned long l
 // column and k = 10 from the k+1 leaf (local k 0), via the 27-neighbour
 // table (null neighbours are the zero leaf, whose mask is 0).
 // ---------------------------------------------------------------------------
-__global__ void k_region_masks(DevGrid g, int columns)
+__global__ void k_region_masks(DevGrid g, int group_axis)
 {
     const long long n = g.ctrl->list_n;
     const uint8_t *mb = reinterpret_cast<const uint8_t *>(g.mask);
@@ -471,32 +471,33 @@ __global__ void k_region_masks(DevGrid g, int columns)
         }
         g.rmask[e * 40 + tj * 4 + w] = word;
     }
-    if (!columns) return;
-    // The column records of the column sweep: runs of leaves adjacent in i
-    // (root cells b, b + R^2, ... all allocated) cut into pieces of up to
-    // three from the run's lowest leaf; each piece's list entries go to the
-    // bucket of its length (col_cnt zeroed before the launch).
-    const long long R2 = (long long)g.R * g.R;
+    if (group_axis == kGroupNone) return;
+    // The records of the grouped sweeps: runs of leaves adjacent along the
+    // axis (root cells b, b + S, ... all allocated; S = R^2 for i, R for j)
+    // cut into pieces of up to three from the run's lowest leaf; each piece's
+    // list entries, lowest first, go to the bucket of its length (col_cnt
+    // zeroed before the launch).
+    const long long S = group_axis == kGroupI ? (long long)g.R * g.R : (long long)g.R;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
         const long long b = g.list_b[e];
-        const int bi = (int)(b / R2);
-        int p = 0;  // allocated leaves directly below in i
-        while (p < bi && g.root[b - (p + 1) * R2] >= 0) ++p;
+        const int c = (int)((b / S) % g.R);  // the leaf's root coordinate along the axis
+        int p = 0;  // allocated leaves directly below along the axis
+        while (p < c && g.root[b - (p + 1) * S] >= 0) ++p;
         if (p % 3 != 0) continue;
         int len = 1;
-        while (len < 3 && bi + len < g.R && g.root[b + len * R2] >= 0) ++len;
+        while (len < 3 && c + len < g.R && g.root[b + len * S] >= 0) ++len;
         const int j = atomicAdd(&g.col_cnt[len - 1], 1);
         int32_t *rec = g.col_grp + ((long long)(len - 1) * g.cap + j) * 3;
         rec[0] = (int32_t)e;
-        rec[1] = len > 1 ? g.ent_of_slot[g.root[b + R2]] : -1;
-        rec[2] = len > 2 ? g.ent_of_slot[g.root[b + 2 * R2]] : -1;
+        rec[1] = len > 1 ? g.ent_of_slot[g.root[b + S]] : -1;
+        rec[2] = len > 2 ? g.ent_of_slot[g.root[b + 2 * S]] : -1;
     }
 }
 
-void launch_region_masks(const DevGrid &g, cudaStream_t s, const LaunchCfg &lc, bool columns)
+void launch_region_masks(const DevGrid &g, cudaStream_t s, const LaunchCfg &lc, int group_axis)
 {
-    if (columns) cudaMemsetAsync(g.col_cnt, 0, sizeof(int32_t) * 4, s);
-    k_region_masks<<<lc.num_sms * 4, 256, 0, s>>>(g, columns ? 1 : 0);
+    if (group_axis != kGroupNone) cudaMemsetAsync(g.col_cnt, 0, sizeof(int32_t) * 4, s);
+    k_region_masks<<<lc.num_sms * 4, 256, 0, s>>>(g, group_axis);
 }
 
 // ---------------------------------------------------------------------------

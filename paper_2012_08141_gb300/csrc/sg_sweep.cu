@@ -112,21 +112,21 @@ template <int H>
 __device__ __forceinline__ constexpr int plane_li(int ri) { return (ri - H) & 7; }
 
 // ---------------------------------------------------------------------------
-// Fused diffuse7 -> box27 (+ sum).  Three leaves per warp: lanes 10*w + tj,
-// w = 0..2, tj = 0..9 own t-region column tj (region column rj = tj + 1) of
-// leaf w; lanes 30, 31 only take part in shuffles.  Step s = 0..9 computes
-// the t plane ti = s (region plane s + 1) from x planes s, s+1, s+2, forms
-// its j-sums P, and once three P planes exist writes output plane s - 2.
+// Fused diffuse7 -> box27 (+ sum).  A lane owns one t-region column tj of a
+// leaf (region column rj = tj + 1); three leaves per warp.  Step s = 0..9
+// computes the t plane ti = s (region plane s + 1) from x planes s, s+1, s+2,
+// forms its j-sums P, and once three P planes exist writes output plane s - 2.
 // ---------------------------------------------------------------------------
-// One warp, one leaf triple: list entries e0, e0+1, e0+2 of grid g (entries
-// >= n are skipped).  Returns this lane's FP32 sum of the outputs it wrote.
+// One lane's part of a warp's sweep: t-region column tj (0..9) of list entry
+// e, or, if !valid, zero rows that only take part in the shuffles.  For a
+// lane with tj = 1..8 the lanes below and above it in the warp must hold the
+// rows of the same leaf's region at j - 1 and j + 1 (a lane with tj = 0 or 9
+// loads its outer row itself).  Returns this lane's FP32 sum of the outputs
+// it wrote.
 template <bool STORE_T, bool CHECK, bool SUM>
-__device__ __forceinline__ float sweep_db_triple(const DevGrid &g, const float *__restrict__ x, float *__restrict__ y,
-                                                 float *__restrict__ tout, float coef, int e0, int n)
+__device__ __forceinline__ float sweep_db_lane(const DevGrid &g, const float *__restrict__ x, float *__restrict__ y,
+                                               float *__restrict__ tout, float coef, int e, int tj, bool valid)
 {
-    const int lane = lane_id();
-    const int sub = lane / 10;
-    const int tj = lane - sub * 10;
     const int rj = tj + 1;
     const int djx = (rj < 2) ? 0 : (rj < 10 ? 1 : 2);
     const int lj = (rj - 2) & 7;
@@ -136,8 +136,6 @@ __device__ __forceinline__ float sweep_db_triple(const DevGrid &g, const float *
     const float c6 = 1.f - 6.f * coef;
     const int Z = (int)g.cap;  // the zero leaf
     {
-        const int e = e0 + sub;
-        const bool valid = (sub < 3) && (e < n);
         int sl[9];
 #pragma unroll
         for (int q = 0; q < 9; ++q) sl[q] = valid ? __ldg(g.nbr + (long long)e * 27 + (q / 3) * 9 + djx * 3 + (q % 3)) : Z;
@@ -231,6 +229,18 @@ __device__ __forceinline__ float sweep_db_triple(const DevGrid &g, const float *
         }
         return part;
     }
+}
+
+// One warp, one leaf triple: list entries e0, e0+1, e0+2 of grid g (entries
+// >= n are skipped); lanes 10*w + tj, w = 0..2, tj = 0..9 take t-region column
+// tj of leaf w, lanes 30, 31 only take part in the shuffles.
+template <bool STORE_T, bool CHECK, bool SUM>
+__device__ __forceinline__ float sweep_db_triple(const DevGrid &g, const float *__restrict__ x, float *__restrict__ y,
+                                                 float *__restrict__ tout, float coef, int e0, int n)
+{
+    const int sub = lane_id() / 10;
+    const int e = e0 + sub;
+    return sweep_db_lane<STORE_T, CHECK, SUM>(g, x, y, tout, coef, e, lane_id() - sub * 10, sub < 3 && e < n);
 }
 
 // ---------------------------------------------------------------------------
@@ -453,6 +463,71 @@ __global__ void __launch_bounds__(kSweepThreads, 3) k_sweep_columns(DevGrid g, i
     }
 }
 
+// ---------------------------------------------------------------------------
+// j-run sweeps: the same fused step with a warp's three leaves taken from runs
+// of leaves adjacent in j (records built by k_region_masks along j, bucketed
+// by length G = 3, 2, 1).  A run piece of G leaves takes 8G + 2 consecutive
+// lanes, j = -1 .. 8G from its lowest leaf: the rows at the faces between its
+// leaves are each other's own rows, so the edge-row loads there vanish and
+// the rows are loaded once.  Tasks: one piece of three (26 lanes), a piece of
+// two with a piece of one (28 lanes) or alone, or three pieces of one (30
+// lanes, as the triple sweep).  Results are those of the triple sweep: every
+// t and output value takes the same operands in the same order.
+// ---------------------------------------------------------------------------
+// This lane's list entry and t-region column in task t; false for lanes
+// outside every piece.  c3, c2, c1: the bucket counts.
+__device__ __forceinline__ bool jrun_lane(const DevGrid &g, int t, int c3, int c2, int c1, int &e, int &tj)
+{
+    const int lane = lane_id();
+    const long long cap3 = g.cap * 3;
+    const int p = c2 < c1 ? c2 : c1;  // pieces of two paired with a piece of one
+    const int32_t *rec = nullptr;
+    int G = 0, start = 0;
+    if (t < c3) {
+        if (lane < 26) { rec = g.col_grp + 2 * cap3 + 3LL * t; G = 3; }
+    } else if (t < c3 + c2) {
+        const int r = t - c3;
+        if (lane < 18) { rec = g.col_grp + cap3 + 3LL * r; G = 2; }
+        else if (lane < 28 && r < p) { rec = g.col_grp + 3LL * r; G = 1; start = 18; }
+    } else {
+        const int k = lane / 10, q = p + 3 * (t - c3 - c2) + k;
+        if (k < 3 && q < c1) { rec = g.col_grp + 3LL * q; G = 1; start = 10 * k; }
+    }
+    if (!rec) return false;
+    const int jj = lane - start - 1;                    // -1 .. 8G
+    const int m = jj < 0 ? 0 : min(jj >> 3, G - 1);     // the piece's leaf holding this column
+    tj = jj - 8 * m + 1;
+    e = __ldg(rec + m);
+    return true;
+}
+
+template <bool STORE_T, bool CHECK, bool SUM>
+__global__ void __launch_bounds__(kSweepThreads, 3) k_sweep_jruns(DevGrid g, int src, int tmp, int dst, float coef,
+                                                                 int sum_slot)
+{
+    __shared__ double s_red[kSweepThreads / 32];
+    const int c3 = g.col_cnt[2], c2 = g.col_cnt[1], c1 = g.col_cnt[0];
+    const int p = c2 < c1 ? c2 : c1;
+    const int tasks = c3 + c2 + (c1 - p + 2) / 3;
+    const int warps_total = gridDim.x * (kSweepThreads / 32);
+    double acc = 0.0;
+    for (int t = blockIdx.x * (kSweepThreads / 32) + (threadIdx.x >> 5); t < tasks; t += warps_total) {
+        int e = 0, tj = 0;
+        const bool valid = jrun_lane(g, t, c3, c2, c1, e, tj);
+        acc += (double)sweep_db_lane<STORE_T, CHECK, SUM>(g, g.field[src], g.field[dst], g.field[tmp], coef, e, tj,
+                                                          valid);
+    }
+    if (SUM) {
+        acc = warp_sum(acc);
+        if (lane_id() == 0) s_red[threadIdx.x >> 5] = acc;
+        __syncthreads();
+        double tot = 0.0;
+        if (threadIdx.x == 0)
+            for (int w = 0; w < kSweepThreads / 32; ++w) tot += s_red[w];
+        finish_reduction(g, tot, sum_slot);
+    }
+}
+
 
 // Fused diffuse7 -> box27 (+ sum) over one grid's list: warps stride over
 // leaf triples.
@@ -626,8 +701,10 @@ static int sweep_ctas(int num_sms, int which)
             err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sweep_diffuse_box<false, false, true>, kSweepThreads, 0);
         else if (which == 1)
             err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sweep_single<SW_BOX27, false, true>, kSweepThreads, 0);
-        else
+        else if (which == 2)
             err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sweep_columns<false, false, true>, kSweepThreads, 0);
+        else
+            err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sweep_jruns<false, false, true>, kSweepThreads, 0);
         if (err != cudaSuccess || per < 1) per = 1;
         cache[which].store(per, std::memory_order_relaxed);
     }
@@ -664,6 +741,22 @@ void launch_sweep_columns(const DevGrid &g, cudaStream_t s, int src, int tmp, in
         else { if (sum) SG_SC(false, false, true); else SG_SC(false, false, false); }
     }
 #undef SG_SC
+}
+
+void launch_sweep_jruns(const DevGrid &g, cudaStream_t s, int src, int tmp, int dst, float coef, int store_tmp,
+                        int check_act, int sum_slot, const LaunchCfg &lc)
+{
+    const int ctas = sweep_ctas(lc.num_sms, 3);
+    const bool sum = sum_slot >= 0;
+#define SG_SJ(ST, CK, SU) k_sweep_jruns<ST, CK, SU><<<ctas, kSweepThreads, 0, s>>>(g, src, tmp, dst, coef, sum_slot)
+    if (store_tmp) {
+        if (check_act) { if (sum) SG_SJ(true, true, true); else SG_SJ(true, true, false); }
+        else { if (sum) SG_SJ(true, false, true); else SG_SJ(true, false, false); }
+    } else {
+        if (check_act) { if (sum) SG_SJ(false, true, true); else SG_SJ(false, true, false); }
+        else { if (sum) SG_SJ(false, false, true); else SG_SJ(false, false, false); }
+    }
+#undef SG_SJ
 }
 
 void launch_sweep_single(const DevGrid &g, cudaStream_t s, int op, int src, int dst, float coef, int check_act,

@@ -531,21 +531,30 @@ def test_staged_upload_tickets():
 
 def test_stencil_variants_and_their_launch_counts():
     """Every stencil kernel family keeps the fused band step at one launch;
-    the column sweep builds its column records in the region-mask launch."""
+    the grouped sweeps build their run records in the region-mask launch,
+    once per list and axis."""
     with pytest.raises(sg.SgError):
-        dry().set_stencil_variant(3)
+        dry().set_stencil_variant(4)
     with pytest.raises(sg.SgError):
         dry().set_stencil_variant(-1)
     s = band512()
-    for variant, first in ((sg.SG_VARIANT_SWEEP, 2), (sg.SG_VARIANT_SWEEP_COLUMNS, 2), (sg.SG_VARIANT_SMEM, 1)):
+    grouped = (sg.SG_VARIANT_SWEEP_COLUMNS, sg.SG_VARIANT_SWEEP_JRUNS)
+    for variant, first in ((sg.SG_VARIANT_SWEEP, 2), (sg.SG_VARIANT_SWEEP_COLUMNS, 2), (sg.SG_VARIANT_SMEM, 1),
+                           (sg.SG_VARIANT_SWEEP_JRUNS, 2)):
         g = dry(512)
         g.set_stencil_variant(variant)
         g.activate_shell(s.lo2, s.hi2, s.lo_strict)
         g.list_gen()
         g.flush()
         assert [launches(g, lambda: cfg2_step(g, 0)) for _ in range(3)] == [first, 1, 1], variant
-        g.set_stencil_variant(sg.SG_VARIANT_SWEEP if variant != sg.SG_VARIANT_SWEEP else sg.SG_VARIANT_SWEEP_COLUMNS)
-        # switching between the two sweeps: the column records (or the region
-        # masks) are made current once for the unchanged list
-        n = launches(g, lambda: cfg2_step(g, 0))
-        assert n == (1 if variant == sg.SG_VARIANT_SWEEP_COLUMNS else 2), variant
+        # to the leaf sweep: the region masks are made current once, unless a
+        # sweep already built them for the unchanged list
+        g.set_stencil_variant(sg.SG_VARIANT_SWEEP)
+        assert launches(g, lambda: cfg2_step(g, 0)) == (2 if variant == sg.SG_VARIANT_SMEM else 1), variant
+        # to each grouped sweep: records along a new axis are built once
+        built = variant if variant in grouped else None
+        for v in grouped:
+            g.set_stencil_variant(v)
+            first = 1 if built == v else 2
+            assert [launches(g, lambda: cfg2_step(g, 0)) for _ in range(2)] == [first, 1], (variant, v)
+            built = v
