@@ -476,21 +476,43 @@ __global__ void k_region_masks(DevGrid g, int group_axis)
     // axis (root cells b, b + S, ... all allocated; S = R^2 for i, R for j)
     // cut into pieces of up to three from the run's lowest leaf; each piece's
     // list entries, lowest first, go to the bucket of its length (col_cnt
-    // zeroed before the launch).
+    // zeroed before the launch).  A warp takes 32 consecutive list entries and
+    // one atomic per bucket, so records stay in list order within the warp's
+    // chunk: consecutive records are mostly pieces adjacent in k, which the
+    // warps of one CTA then sweep side by side (their k-halo rows are each
+    // other's own rows, shared through L1).
     const long long S = group_axis == kGroupI ? (long long)g.R * g.R : (long long)g.R;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-        const long long b = g.list_b[e];
-        const int c = (int)((b / S) % g.R);  // the leaf's root coordinate along the axis
-        int p = 0;  // allocated leaves directly below along the axis
-        while (p < c && g.root[b - (p + 1) * S] >= 0) ++p;
-        if (p % 3 != 0) continue;
-        int len = 1;
-        while (len < 3 && c + len < g.R && g.root[b + len * S] >= 0) ++len;
-        const int j = atomicAdd(&g.col_cnt[len - 1], 1);
-        int32_t *rec = g.col_grp + ((long long)(len - 1) * g.cap + j) * 3;
-        rec[0] = (int32_t)e;
-        rec[1] = len > 1 ? g.ent_of_slot[g.root[b + S]] : -1;
-        rec[2] = len > 2 ? g.ent_of_slot[g.root[b + 2 * S]] : -1;
+    const int lane = lane_id();
+    const long long stride = (long long)gridDim.x * blockDim.x;  // a multiple of 32: the loop is warp-uniform
+    for (long long e0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) & ~31LL; e0 < n; e0 += stride) {
+        const long long e = e0 + lane;
+        int len = 0;
+        long long b = 0;
+        if (e < n) {
+            b = g.list_b[e];
+            const int c = (int)((b / S) % g.R);  // the leaf's root coordinate along the axis
+            int p = 0;  // allocated leaves directly below along the axis
+            while (p < c && g.root[b - (p + 1) * S] >= 0) ++p;
+            if (p % 3 == 0) {
+                len = 1;
+                while (len < 3 && c + len < g.R && g.root[b + len * S] >= 0) ++len;
+            }
+        }
+        for (int G = 1; G <= 3; ++G) {
+            const unsigned m = __ballot_sync(kFull, len == G);
+            if (!m) continue;
+            const int leader = __ffs(m) - 1;
+            int base = 0;
+            if (lane == leader) base = atomicAdd(&g.col_cnt[G - 1], __popc(m));
+            base = __shfl_sync(kFull, base, leader);
+            if (len == G) {
+                const long long j = base + __popc(m & ((1u << lane) - 1u));
+                int32_t *rec = g.col_grp + ((long long)(G - 1) * g.cap + j) * 3;
+                rec[0] = (int32_t)e;
+                rec[1] = G > 1 ? g.ent_of_slot[g.root[b + S]] : -1;
+                rec[2] = G > 2 ? g.ent_of_slot[g.root[b + 2 * S]] : -1;
+            }
+        }
     }
 }
 
