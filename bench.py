@@ -90,14 +90,20 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def traffic_record(kernel_src: str):
+# the fused band step's kernel for each stencil variant
+KERNEL_NAMES = {0: "k_sweep_diffuse_box<false,false,true>", 1: "k_diffuse_box<false,false,true>",
+                2: "k_sweep_columns<false,false,true>", 3: "k_sweep_jruns<false,false,true>"}
+
+
+def traffic_record(kernel_src: str, kernel: str):
     """DRAM bytes per launch of the fused kernel from the committed ncu summary,
-    or None when the kernel source changed since it was captured."""
+    or None when that summary is of another kernel or the kernel source
+    changed since it was captured."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         rec = json.load(open(p))
         h = hashlib.sha1(open(kernel_src, "rb").read()).hexdigest()
-        if rec.get("kernel_sha1") == h:
+        if rec.get("kernel_sha1") == h and rec.get("kernel") == kernel:
             return rec.get("dram_bytes_per_launch")
     except Exception:
         pass
@@ -164,7 +170,7 @@ class ClockSampler:
 # our arm: band workloads
 # ---------------------------------------------------------------------------
 
-def setup_band(sg, spec, opts, x_host, variant=0, cap=32768):
+def setup_band(sg, spec, opts, x_host, variant=3, cap=32768):
     g = sg.Grid(spec.N, 3, 3, max_leaves=cap, max_sums=1, scratch_mask=0b010)
     g.set_opts(opts)
     g.set_stencil_variant(variant)
@@ -675,7 +681,7 @@ def run_ours(args):
     achieved_eager = n_leaves * BYTES_PER_LEAF_EAGER / (t_e / len(ms_e)) / 1e9
     kernel_src = os.path.join(ROOT, "paper_2012_08141_gb300", "csrc",
                               "sg_stencil.cu" if args.variant == 1 else "sg_sweep.cu")
-    traffic = traffic_record(kernel_src) if args.variant == 0 else None
+    traffic = traffic_record(kernel_src, KERNEL_NAMES[args.variant])
 
     extra = {}
     if world == 1 and args.only != "fused":
@@ -723,9 +729,7 @@ def run_ours(args):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                          "achieved_active_only": n_active * 8 / (avg_ms / 1e3) / 1e9,
-                         "kernel": {0: "k_sweep_diffuse_box<false,false,true>", 1: "k_diffuse_box<false,false,true>",
-                                    2: "k_sweep_columns<false,false,true>",
-                                    3: "k_sweep_jruns<false,false,true>"}[args.variant],
+                         "kernel": KERNEL_NAMES[args.variant],
                          "bytes_per_launch": n_leaves * BYTES_PER_LEAF_FUSED},
             "e2e": {"value": world * n_active * e2e_steps / e2e_s if e2e_steps else None, "unit": "voxel-steps/s",
                     "h2d_bytes_per_step": 4 * n_active, "d2h_bytes_per_step": 8},
@@ -818,7 +822,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
-    ap.add_argument("--variant", type=int, default=0, choices=[0, 1, 2, 3],
+    ap.add_argument("--variant", type=int, default=3, choices=[0, 1, 2, 3],
                     help="stencil kernel family (0 sweep, 1 smem, 2 sweep over i-columns, 3 sweep over j-runs)")
     ap.add_argument("--only", choices=["all", "fused", "band1024", "batched", "particles", "mpm_apic", "multigrid",
                                        "micro", "advection", "ablation", "serving"],

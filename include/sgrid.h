@@ -405,17 +405,19 @@ int sg_read_sums(sg_grid *g, double *host, int64_t n);
 int sg_get_stats(sg_grid *g, sg_stats *out);
 
 /* ---- stencil kernel family for 8^3 leaves (tuning; results are identical
- * up to FP32 rounding order) ---- */
-#define SG_VARIANT_SWEEP 0 /* register sweep along i, rows via the read-only path */
+ * up to FP32 rounding order; the three sweeps give bit-identical fields) ---- */
+#define SG_VARIANT_SWEEP 0 /* register sweep along i, rows via the read-only path; a warp
+                              takes three consecutive list entries */
 #define SG_VARIANT_SMEM 1  /* leaf + halo staged in shared memory */
 #define SG_VARIANT_SWEEP_COLUMNS 2 /* register sweep; the fused step sweeps columns of up
                                       to three leaves adjacent in i (same results; slower
                                       on the band: fewer, longer tasks) */
-#define SG_VARIANT_SWEEP_JRUNS 3   /* register sweep; the fused step gives each warp
-                                      three leaves from runs adjacent in j, so rows at the
-                                      leaves' shared faces are loaded once (same results) */
+#define SG_VARIANT_SWEEP_JRUNS 3   /* the default: register sweep; the fused step gives each
+                                      warp up to three leaves from runs adjacent in j, so rows
+                                      at the leaves' shared faces are loaded once */
 
-/* Select the stencil kernel family used by ops flushed from now on. */
+/* Select the stencil kernel family used by ops flushed from now on (a new grid
+ * uses SG_VARIANT_SWEEP_JRUNS). */
 int sg_set_stencil_variant(sg_grid *g, int32_t variant);
 
 /* Implicit sync, then the number of active voxels of the listed leaves. */

@@ -306,7 +306,7 @@ int run_struct_for_group(sg_grid *g, size_t &i)
         // region masks (and, for the grouped sweeps, the run records) are
         // derived from the structure, cached with the list
         const int v = g->lc.variant;
-        const bool sweep = v == kVariantSweep || v == kVariantSweepColumns || v == kVariantSweepJRuns;
+        const bool sweep = v != kVariantSmem;
         const int axis = v == kVariantSweepColumns ? kGroupI : (v == kVariantSweepJRuns ? kGroupJ : kGroupNone);
         const bool need_runs = axis != kGroupNone && (g->colgrp_ver != g->list_ver || g->colgrp_axis != axis);
         if ((sweep && g->rmask_ver != g->list_ver) || need_runs) {
@@ -1049,6 +1049,7 @@ int sg_create(const sg_desc *desc, void *cuda_stream, sg_grid **out)
     d.cap = desc->max_leaves;
     const long long nr = (long long)d.R * d.R * d.R;
     g->num_tiles = (int)((nr + kListTile - 1) / kListTile);
+    g->lc.variant = kVariantSweepJRuns;
     if (g->dry) {
         g->lc.num_sms = 152;
         g->lc.persistent_ctas = 152;

@@ -86,14 +86,14 @@ struct DevGrid {
     int32_t *col_cnt;   // [4]
 };
 
-// Stencil kernel families for 8^3 leaves (the autotuner picks one).
+// Stencil kernel families for 8^3 leaves (sg_set_stencil_variant picks one).
 enum StencilVariant : int {
     kVariantSweep = 0,  // register sweep, rows loaded through the read-only path
     kVariantSmem = 1,   // leaf + halo staged in shared memory by plain loads
     kVariantSweepColumns = 2,  // register sweep; the fused step sweeps columns of
                                // leaves adjacent in i (see k_sweep_columns)
     kVariantSweepJRuns = 3,    // register sweep; a warp's leaves are runs of leaves
-                               // adjacent in j (see k_sweep_jruns)
+                               // adjacent in j (see k_sweep_jruns); the default
 };
 
 // Axis along which launch_region_masks groups adjacent leaves into records.

@@ -464,58 +464,154 @@ __global__ void __launch_bounds__(kSweepThreads, 3) k_sweep_columns(DevGrid g, i
 }
 
 // ---------------------------------------------------------------------------
-// j-run sweeps: the same fused step with a warp's three leaves taken from runs
-// of leaves adjacent in j (records built by k_region_masks along j, bucketed
-// by length G = 3, 2, 1).  A run piece of G leaves takes 8G + 2 consecutive
-// lanes, j = -1 .. 8G from its lowest leaf: the rows at the faces between its
-// leaves are each other's own rows, so the edge-row loads there vanish and
-// the rows are loaded once.  Tasks: one piece of three (26 lanes), a piece of
-// two with a piece of one (28 lanes) or alone, or three pieces of one (30
-// lanes, as the triple sweep).  Results are those of the triple sweep: every
-// t and output value takes the same operands in the same order.
+// j-run sweeps (the default fused kernel): the same fused step with a warp's
+// leaves taken from runs of leaves adjacent in j (records built by
+// k_region_masks along j, bucketed by length G = 3, 2, 1).  A run piece of G
+// leaves takes 8G + 4 consecutive lanes, j = -2 .. 8G + 1 from its lowest
+// leaf: the rows at the faces between its leaves are lanes' own rows, loaded
+// once, and the two outer lanes only hold the x rows at j = -2 and 8G + 1
+// (t-region columns tj = -1 and 10, whose t is never used), so every t lane
+// takes its j - 1 / j + 1 rows by shuffle and no lane loads or holds an edge
+// row.  That frees the registers for four CTAs per SM.  Tasks: one piece of
+// three (28 lanes), a piece of two with a piece of one (32 lanes) or alone,
+// or two pieces of one.  Every t and output value takes the same operands in
+// the same order as in the triple sweep, so the results are identical.
 // ---------------------------------------------------------------------------
-// This lane's list entry and t-region column in task t; false for lanes
-// outside every piece.  c3, c2, c1: the bucket counts.
+// One lane's part: region column tj (-1 .. 10) of list entry e, or, if
+// !valid, zero rows.  Returns this lane's FP32 sum of the outputs it wrote.
+template <bool STORE_T, bool CHECK, bool SUM>
+__device__ __forceinline__ float sweep_db_jrun_lane(const DevGrid &g, const float *__restrict__ x, float *__restrict__ y,
+                                                 float *__restrict__ tout, float coef, int e, int tj, bool valid)
+{
+    const int rj = tj + 1;  // region column 0..11
+    const int djx = (rj < 2) ? 0 : (rj < 10 ? 1 : 2);
+    const int lj = (rj - 2) & 7;
+    const bool tlane = valid && tj >= 0 && tj <= 9;
+    const bool outlane = valid && tj >= 1 && tj <= 8;
+    const float c6 = 1.f - 6.f * coef;
+    const int Z = (int)g.cap;  // the zero leaf
+    int sl[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) sl[q] = valid ? __ldg(g.nbr + (long long)e * 27 + (q / 3) * 9 + djx * 3 + (q % 3)) : Z;
+    const int own = sl[4];
+    uint4 rm = make_uint4(0u, 0u, 0u, 0u);
+    if (tlane) rm = __ldg(reinterpret_cast<const uint4 *>(g.rmask + (long long)e * 40 + tj * 4));
+    const uint32_t rmw[4] = {rm.x, rm.y, rm.z, rm.w};
+    float xa[12], xb[12], xc[12], xn[12];
+#pragma unroll
+    for (int q = 0; q < 12; ++q) xn[q] = 0.f;
+    row12v(x, sl[0], sl[1], sl[2], plane_li<2>(0) * 8 + lj, xa);
+    row12v(x, sl[0], sl[1], sl[2], plane_li<2>(1) * 8 + lj, xb);
+    row12v(x, sl[3], sl[4], sl[5], plane_li<2>(2) * 8 + lj, xc);
+    float p1[10], p2[10];
+    uint32_t mprev = 0;
+    float part = 0.f;
+#pragma unroll
+    for (int s = 0; s < 10; ++s) {
+        if (s + 3 <= 11) {
+            const int ri = s + 3, dx = plane_di<2>(ri) * 3;
+            row12v(x, sl[dx], sl[dx + 1], sl[dx + 2], plane_li<2>(ri) * 8 + lj, xn);
+        }
+        const uint32_t mt = (rmw[s / 3] >> (10 * (s % 3))) & 0x3ffu;
+        float up[12], dn[12];
+        shfl_row<12>(xb, up, dn);
+        float t[10];
+#pragma unroll
+        for (int q = 0; q < 10; ++q) {
+            const float nb = ((xb[q] + xb[q + 2]) + (xa[q + 1] + xc[q + 1])) + (up[q + 1] + dn[q + 1]);
+            t[q] = pick(mt, q, fmaf(coef, nb, c6 * xb[q + 1]));
+        }
+        if (STORE_T && s >= 1 && s <= 8 && outlane) {
+            const int orow = (s - 1) * 8 + (tj - 1);
+            if (CHECK) sweep_check_row(g, own, orow, (mt >> 1) & 0xffu);
+            float *o = tout + (long long)own * 512 + orow * 8;
+            stg4(o, t[1], t[2], t[3], t[4]);
+            stg4(o + 4, t[5], t[6], t[7], t[8]);
+        }
+        float tu[10], td[10], p0[10];
+#pragma unroll
+        for (int q = 0; q < 10; ++q) {
+            tu[q] = __shfl_up_sync(kFull, t[q], 1);
+            td[q] = __shfl_down_sync(kFull, t[q], 1);
+        }
+#pragma unroll
+        for (int q = 0; q < 10; ++q) p0[q] = (tu[q] + t[q]) + td[q];
+        if (s >= 2) {
+            float S[10];
+#pragma unroll
+            for (int q = 0; q < 10; ++q) S[q] = (p2[q] + p1[q]) + p0[q];
+            const uint32_t bits = (mprev >> 1) & 0xffu;
+            float o[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) o[k] = pick(bits, k, ((S[k] + S[k + 1]) + S[k + 2]) * (1.f / 27.f));
+            if (outlane) {
+                const int orow = (s - 2) * 8 + (tj - 1);
+                if (CHECK) sweep_check_row(g, own, orow, bits);
+                float *op = y + (long long)own * 512 + orow * 8;
+                stg4(op, o[0], o[1], o[2], o[3]);
+                stg4(op + 4, o[4], o[5], o[6], o[7]);
+                if (SUM) part += ((o[0] + o[1]) + (o[2] + o[3])) + ((o[4] + o[5]) + (o[6] + o[7]));
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 10; ++q) {
+            p2[q] = p1[q];
+            p1[q] = p0[q];
+        }
+        mprev = mt;
+#pragma unroll
+        for (int q = 0; q < 12; ++q) {
+            xa[q] = xb[q];
+            xb[q] = xc[q];
+            xc[q] = xn[q];
+        }
+    }
+    return part;
+}
+
+// This lane's list entry and region column (-1 .. 10) in task t; false for
+// lanes outside every piece.  c3, c2, c1: the bucket counts.
 __device__ __forceinline__ bool jrun_lane(const DevGrid &g, int t, int c3, int c2, int c1, int &e, int &tj)
 {
     const int lane = lane_id();
     const long long cap3 = g.cap * 3;
-    const int p = c2 < c1 ? c2 : c1;  // pieces of two paired with a piece of one
+    const int p = c2 < c1 ? c2 : c1;
     const int32_t *rec = nullptr;
     int G = 0, start = 0;
     if (t < c3) {
-        if (lane < 26) { rec = g.col_grp + 2 * cap3 + 3LL * t; G = 3; }
+        if (lane < 28) { rec = g.col_grp + 2 * cap3 + 3LL * t; G = 3; }
     } else if (t < c3 + c2) {
         const int r = t - c3;
-        if (lane < 18) { rec = g.col_grp + cap3 + 3LL * r; G = 2; }
-        else if (lane < 28 && r < p) { rec = g.col_grp + 3LL * r; G = 1; start = 18; }
+        if (lane < 20) { rec = g.col_grp + cap3 + 3LL * r; G = 2; }
+        else if (r < p) { rec = g.col_grp + 3LL * r; G = 1; start = 20; }
     } else {
-        const int k = lane / 10, q = p + 3 * (t - c3 - c2) + k;
-        if (k < 3 && q < c1) { rec = g.col_grp + 3LL * q; G = 1; start = 10 * k; }
+        const int k = lane / 12, q = p + 2 * (t - c3 - c2) + k;
+        if (k < 2 && q < c1) { rec = g.col_grp + 3LL * q; G = 1; start = 12 * k; }
     }
     if (!rec) return false;
-    const int jj = lane - start - 1;                    // -1 .. 8G
-    const int m = jj < 0 ? 0 : min(jj >> 3, G - 1);     // the piece's leaf holding this column
+    const int jj = lane - start - 2;                    // -2 .. 8G + 1
+    const int m = jj < 0 ? 0 : min(jj >> 3, G - 1);
     tj = jj - 8 * m + 1;
     e = __ldg(rec + m);
     return true;
 }
 
 template <bool STORE_T, bool CHECK, bool SUM>
-__global__ void __launch_bounds__(kSweepThreads, 3) k_sweep_jruns(DevGrid g, int src, int tmp, int dst, float coef,
+// Four CTAs of four warps per SM (at most 128 registers a thread).
+__global__ void __launch_bounds__(kSweepThreads, 4) k_sweep_jruns(DevGrid g, int src, int tmp, int dst, float coef,
                                                                  int sum_slot)
 {
     __shared__ double s_red[kSweepThreads / 32];
     const int c3 = g.col_cnt[2], c2 = g.col_cnt[1], c1 = g.col_cnt[0];
     const int p = c2 < c1 ? c2 : c1;
-    const int tasks = c3 + c2 + (c1 - p + 2) / 3;
+    const int tasks = c3 + c2 + (c1 - p + 1) / 2;
     const int warps_total = gridDim.x * (kSweepThreads / 32);
     double acc = 0.0;
     for (int t = blockIdx.x * (kSweepThreads / 32) + (threadIdx.x >> 5); t < tasks; t += warps_total) {
         int e = 0, tj = 0;
         const bool valid = jrun_lane(g, t, c3, c2, c1, e, tj);
-        acc += (double)sweep_db_lane<STORE_T, CHECK, SUM>(g, g.field[src], g.field[dst], g.field[tmp], coef, e, tj,
-                                                          valid);
+        acc += (double)sweep_db_jrun_lane<STORE_T, CHECK, SUM>(g, g.field[src], g.field[dst], g.field[tmp], coef, e, tj,
+                                                            valid);
     }
     if (SUM) {
         acc = warp_sum(acc);

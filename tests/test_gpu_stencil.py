@@ -177,7 +177,7 @@ def test_empty_grid():
 def test_ragged_domains(N, r0, r1, strict):
     lo2, hi2 = band_bounds(r0, r1)
     spec = ShellSpec(N, 8, lo2, hi2, strict, 11)
-    for mode, variant in [("fused", 0), ("eager", 0), ("fused", 1), ("eager", 1), ("fused", 2), ("fused", 3)]:
+    for mode, variant in [("fused", 0), ("eager", 0), ("fused", 1), ("eager", 1), ("fused", 2), ("fused", 3), ("eager", 3)]:
         g, og = shell_pair(spec, n_fields=3, opts=OPTS[mode], scratch_mask=0b010, variant=variant)
         cur, sums_ref = run_band(g, og, 7)
         assert rel_linf(g.read_field(0), og.read_field(cur)) <= TOL
@@ -189,7 +189,7 @@ def test_ragged_domains(N, r0, r1, strict):
 def test_full_domain_boundary_reads_zero():
     """Every voxel active: out-of-domain neighbours read 0 at all six faces."""
     spec = ShellSpec(24, 8, 0, 10 ** 9, False, 2)
-    for mode, variant in [("fused", 0), ("eager", 0), ("fused", 1), ("eager", 1), ("fused", 2), ("fused", 3)]:
+    for mode, variant in [("fused", 0), ("eager", 0), ("fused", 1), ("eager", 1), ("fused", 2), ("fused", 3), ("eager", 3)]:
         g, og = shell_pair(spec, n_fields=3, opts=OPTS[mode], variant=variant)
         cur, _ = run_band(g, og, 5)
         assert rel_linf(g.read_field(0), og.read_field(cur)) <= TOL
