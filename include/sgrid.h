@@ -435,15 +435,16 @@ int sg_fill_hash(sg_grid *g, int32_t f, int64_t seed);
  * A batch binds n (1..1024) live grids with 8^3 leaves.  Each sg_batch_step
  * runs, for every grid, the fused step dst = box27(diffuse7(src, coef)) with
  * the per-grid sum of dst accumulated, as ONE kernel launch over the
- * concatenated leaf lists of all grids (a persistent kernel whose warps
- * stride over leaf triples), then exchanges src and dst in every grid (as
+ * concatenated work of all grids (a persistent kernel whose warps stride
+ * over the grids' j-run pieces, as SG_VARIANT_SWEEP_JRUNS does for one
+ * grid), then exchanges src and dst in every grid (as
  * sg_swap).  The intermediate field tmp is not stored (every grid's tmp is
  * treated as scratch).  Steps are captured as CUDA graphs (one per src/dst
  * parity) unless disabled.  Results equal stepping each grid alone up to
  * FP32 rounding order (the fused kernel body is the same).
  *
- * sg_batch_create flushes every grid, makes its list, neighbour table and
- * region masks current, and synchronizes; the structure of the grids must
+ * sg_batch_create flushes every grid, makes its list, neighbour table,
+ * region masks and j-run records current, and synchronizes; the structure of the grids must
  * not change while the batch exists, and between batch steps the grids
  * must not be used except for reads (which synchronize).  All work runs on
  * cuda_stream.  Descriptor memory comes from grid 0's allocator and is
@@ -455,8 +456,8 @@ int sg_batch_create(sg_grid *const *grids, int32_t n, int32_t src, int32_t tmp, 
 int sg_batch_step(sg_batch *b);
 /* Wait, then copy the n first grids' sums of the last step to host memory. */
 int sg_batch_read_sums(sg_batch *b, double *host, int32_t n);
-/* Warps per CTA of the persistent kernel (2, 4 or 8: 6, 12 or 24 leaves per
- * CTA) and whether steps run as captured CUDA graphs. */
+/* Warps per CTA of the persistent kernel (2, 4 or 8: up to 6, 12 or 24 leaves
+ * per CTA) and whether steps run as captured CUDA graphs. */
 int sg_batch_set(sg_batch *b, int32_t warps_per_cta, int32_t use_graph);
 /* Autotuner: time trial_steps steps with each warps-per-CTA choice (these are
  * real steps: they advance every grid) and keep the fastest. */

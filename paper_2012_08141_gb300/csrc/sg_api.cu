@@ -1932,19 +1932,29 @@ int grid_prepare_batch(sg_grid *g, int src, int tmp, int dst, BatchGrid out[2], 
         rc = launch_list(g, false, 0);
         g->list_ver = g->mask_ver;
     }
-    if (!rc && g->rmask_ver != g->list_ver) {
-        launch_region_masks(g->dev, g->stream, g->lc, kGroupNone);
+    // region masks and the j-run records of the batched kernel
+    const bool need_runs = g->colgrp_ver != g->list_ver || g->colgrp_axis != kGroupJ;
+    if (!rc && (g->rmask_ver != g->list_ver || need_runs)) {
+        launch_region_masks(g->dev, g->stream, g->lc, need_runs ? kGroupJ : kGroupNone);
         rc = after_launch(g, "region masks");
         g->rmask_ver = g->list_ver;
+        if (need_runs) {
+            g->colgrp_ver = g->list_ver;
+            g->colgrp_axis = kGroupJ;
+        }
     }
     if (!rc) {
         launch_count_active(g->dev, g->stream, g->lc);
         rc = after_launch(g, "count active");
     }
     if (!rc) rc = do_sync(g);
+    int32_t cnt[3] = {0, 0, 0};
+    if (!rc)
+        rc = cuda_check(cudaMemcpy(cnt, g->dev.col_cnt, sizeof cnt, cudaMemcpyDeviceToHost), "run record counts");
     if (rc) return rc;
     if (n_active) *n_active = (long long)g->host_ctrl->n_active;
     const int nl = g->host_ctrl->list_n;
+    const int pairs = std::min(cnt[1], cnt[0]);
     for (int p = 0; p < 2; ++p) {
         BatchGrid it{};
         it.g = g->dev;
@@ -1952,6 +1962,10 @@ int grid_prepare_batch(sg_grid *g, int src, int tmp, int dst, BatchGrid out[2], 
         it.y = g->dev.field[g->phys[p == 0 ? dst : src]];
         it.t = g->dev.field[g->phys[tmp]];
         it.n = nl;
+        it.c1 = cnt[0];
+        it.c2 = cnt[1];
+        it.c3 = cnt[2];
+        it.tasks = cnt[2] + cnt[1] + (cnt[0] - pairs + 1) / 2;
         it.tri0 = 0;
         out[p] = it;
     }
@@ -1993,7 +2007,7 @@ int sg_batch_create(sg_grid *const *grids, int32_t n, int32_t src, int32_t tmp, 
             two[p].tri0 = b->total_tri;
             items[p].push_back(two[p]);
         }
-        b->total_tri += (two[0].n + 2) / 3;
+        b->total_tri += two[0].tasks;
         b->total_leaves += two[0].n;
     }
     if (rc) {

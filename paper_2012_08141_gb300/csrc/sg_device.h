@@ -178,7 +178,9 @@ struct BatchGrid {
     float *y;        // box27 output
     float *t;        // intermediate (not stored by the batched kernel)
     int n;           // list length
-    int tri0;        // first global triple index of this grid
+    int c3, c2, c1;  // j-run pieces of three, two and one leaves (records in g.col_grp)
+    int tasks;       // warp tasks of this grid (see k_sweep_jruns)
+    int tri0;        // first global task index of this grid
 };
 // One launch: every grid's fused diffuse7 -> box27 step, per-grid sums
 // added to acc[grid] (acc zeroed by the caller).  warps = warps per CTA.

@@ -249,7 +249,7 @@ int sg_server_tick(sg_server *s)
         Job *j = s->resident[i];
         s->host_items[i] = j->items[j->parity];
         s->host_items[i].tri0 = tri;
-        tri += (j->items[0].n + 2) / 3;
+        tri += j->items[0].tasks;
     }
     if (cudaMemcpyAsync(s->dev_items, s->host_items, sizeof(BatchGrid) * n, cudaMemcpyHostToDevice, s->stream) !=
             cudaSuccess ||

@@ -873,14 +873,14 @@ void launch_sweep_single(const DevGrid &g, cudaStream_t s, int op, int src, int 
 
 // ---------------------------------------------------------------------------
 // Batched fused step: one persistent launch steps many grids.  The global
-// work list is the concatenation of every grid's leaf triples; warps stride
-// over it, find their grid by binary search over the triples' prefix sums
-// (in shared memory) and run the same per-triple body as the single-grid
-// kernel.  Each triple's output sum is added to its grid's FP64 accumulator
+// work list is the concatenation of every grid's j-run tasks; warps stride
+// over it, find their grid by binary search over the tasks' prefix sums (in
+// shared memory) and run the same per-lane body as the single-grid j-run
+// kernel.  Each task's output sum is added to its grid's FP64 accumulator
 // (zeroed before the launch).
 // ---------------------------------------------------------------------------
 template <int WARPS>
-__global__ void __launch_bounds__(WARPS * 32, 12 / WARPS) k_batch_diffuse_box(const BatchGrid *__restrict__ items,
+__global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) k_batch_diffuse_box(const BatchGrid *__restrict__ items,
                                                                               int n_grids, int total_tri, float coef,
                                                                               double *acc)
 {
@@ -896,7 +896,9 @@ __global__ void __launch_bounds__(WARPS * 32, 12 / WARPS) k_batch_diffuse_box(co
             else hi = mid - 1;
         }
         const BatchGrid &it = items[lo];
-        const float part = sweep_db_triple<false, false, true>(it.g, it.x, it.y, it.t, coef, (T - s_off[lo]) * 3, it.n);
+        int e = 0, tj = 0;
+        const bool valid = jrun_lane(it.g, T - s_off[lo], it.c3, it.c2, it.c1, e, tj);
+        const float part = sweep_db_jrun_lane<false, false, true>(it.g, it.x, it.y, it.t, coef, e, tj, valid);
         const double w = warp_sum((double)part);
         if (lane_id() == 0) atomicAdd(&acc[lo], w);
     }

@@ -89,7 +89,8 @@ def test_batch_equals_alone_and_oracle(use_graph):
     for i, s in enumerate(specs):
         ref_sum = run_alone(alone[i], steps)
         assert abs(bsums[i] - ref_sum) <= TOL * abs(ref_sum)
-        assert rel_linf(batched[i].read_field(0), alone[i].read_field(0)) <= TOL
+        # the same per-voxel arithmetic in the same order: identical fields
+        np.testing.assert_array_equal(batched[i].read_field(0), alone[i].read_field(0))
     # the two smallest grids also against the oracle
     for i in np.argsort([g.num_leaves() for g in batched])[:2]:
         s = specs[i]
