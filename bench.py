@@ -41,6 +41,7 @@ import hashlib
 import json
 import math
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -95,15 +96,23 @@ KERNEL_NAMES = {0: "k_sweep_diffuse_box<false,false,true>", 1: "k_diffuse_box<fa
                 2: "k_sweep_columns<false,false,true>", 3: "k_sweep_jruns<false,false,true>"}
 
 
+def code_sha1(path: str) -> str:
+    """sha1 of a C/CUDA source with its comments and blank lines removed: it
+    changes with the code, not with the comments."""
+    src = open(path).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    return hashlib.sha1("\n".join(l.rstrip() for l in src.splitlines() if l.strip()).encode()).hexdigest()
+
+
 def traffic_record(kernel_src: str, kernel: str):
     """DRAM bytes per launch of the fused kernel from the committed ncu summary,
-    or None when that summary is of another kernel or the kernel source
+    or None when that summary is of another kernel or the kernel's code
     changed since it was captured."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         rec = json.load(open(p))
-        h = hashlib.sha1(open(kernel_src, "rb").read()).hexdigest()
-        if rec.get("kernel_sha1") == h and rec.get("kernel") == kernel:
+        if rec.get("kernel_code_sha1") == code_sha1(kernel_src) and rec.get("kernel") == kernel:
             return rec.get("dram_bytes_per_launch")
     except Exception:
         pass

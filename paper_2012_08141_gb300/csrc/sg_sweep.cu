@@ -10,7 +10,9 @@
 //   - x rows come straight from L2/HBM (read-only path), the row of plane
 //     i+3 being requested while plane i is computed;
 //   - the j-1 / j+1 rows are the neighbouring lanes' rows, taken by warp
-//     shuffle; only the two edge lanes of a leaf load their outer row;
+//     shuffle; in the triple sweep the two edge lanes of a leaf load their
+//     outer row, in the j-run sweep (the default fused kernel) lanes of a run
+//     of j-adjacent leaves hold every row, the two outermost lanes x only;
 //   - the 3x3x3 box sum is separable: a j-sum by shuffle, an i-sum over a
 //     sliding window of the last three planes, a k-sum inside the row.
 // A row of the 12^3 (fused) or 10^3 (single) region is gathered from the
