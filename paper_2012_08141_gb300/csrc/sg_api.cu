@@ -1075,6 +1075,8 @@ int sg_create(const sg_desc *desc, void *cuda_stream, sg_grid **out)
         {(void **)&d.ent_of_slot, sizeof(int32_t) * d.cap},
         {(void **)&d.col_grp, sizeof(int32_t) * 9 * d.cap},
         {(void **)&d.col_cnt, sizeof(int32_t) * 4},
+        {(void **)&d.run_stage, sizeof(int4) * d.cap},
+        {(void **)&d.run_chunk, sizeof(int32_t) * 3 * (d.cap / 32 + 1)},
         {(void **)&d.rmask, (L == 8 ? sizeof(uint32_t) * 40 : size_t(4)) * d.cap},
         {(void **)&d.need, (size_t)nr},
         {(void **)&d.tile_status, sizeof(unsigned long long) * g->num_tiles},

@@ -49,7 +49,8 @@ struct Ctrl {
     int32_t timeout_site; // which wait gave up (0 none, 1 look-back, 2 test, 3 leaf allocation)
                           // or, with kErrCheck, 100 + the failed check
     int32_t bins_used;    // leaves holding particles in the last binned P2G
-    int32_t pad[2];
+    uint32_t rr_done;     // run-record CTAs finished (reset by the last)
+    int32_t pad[1];
 };
 
 struct DevGrid {
@@ -84,6 +85,8 @@ struct DevGrid {
     int32_t *ent_of_slot;
     int32_t *col_grp;   // [3][cap][3]
     int32_t *col_cnt;   // [4]
+    int4 *run_stage;    // [cap]: per list entry, (piece length or 0, entry, next entry, the one after)
+    int32_t *run_chunk; // [3][cap / 32 + 1]: pieces of each length per 32-entry list chunk
 };
 
 // Stencil kernel families for 8^3 leaves (sg_set_stencil_variant picks one).

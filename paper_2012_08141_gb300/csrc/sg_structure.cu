@@ -475,21 +475,22 @@ __global__ void k_region_masks(DevGrid g, int group_axis)
     // The records of the grouped sweeps: runs of leaves adjacent along the
     // axis (root cells b, b + S, ... all allocated; S = R^2 for i, R for j)
     // cut into pieces of up to three from the run's lowest leaf; each piece's
-    // list entries, lowest first, go to the bucket of its length (col_cnt
-    // zeroed before the launch).  A warp takes 32 consecutive list entries and
-    // one atomic per bucket, so records stay in list order within the warp's
-    // chunk: consecutive records are mostly pieces adjacent in k, which the
-    // warps of one CTA then sweep side by side (their k-halo rows are each
-    // other's own rows, shared through L1).
+    // list entries, lowest first, go to the bucket of its length, in list
+    // order.  List order keeps the warps that sweep at the same time on
+    // neighbouring leaves, so halo rows are reused through L1 and L2.  In one
+    // launch: every warp classifies 32-entry chunks of the list (the piece
+    // each entry starts, staged per entry) and counts each chunk's pieces by
+    // length; the last CTA to finish scans the chunk counts and writes the
+    // records.  No CTA waits for another.
     const long long S = group_axis == kGroupI ? (long long)g.R * g.R : (long long)g.R;
+    const long long cap_ch = g.cap / 32 + 1;
     const int lane = lane_id();
     const long long stride = (long long)gridDim.x * blockDim.x;  // a multiple of 32: the loop is warp-uniform
     for (long long e0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) & ~31LL; e0 < n; e0 += stride) {
         const long long e = e0 + lane;
         int len = 0;
-        long long b = 0;
         if (e < n) {
-            b = g.list_b[e];
+            const long long b = g.list_b[e];
             const int c = (int)((b / S) % g.R);  // the leaf's root coordinate along the axis
             int p = 0;  // allocated leaves directly below along the axis
             while (p < c && g.root[b - (p + 1) * S] >= 0) ++p;
@@ -497,28 +498,70 @@ __global__ void k_region_masks(DevGrid g, int group_axis)
                 len = 1;
                 while (len < 3 && c + len < g.R && g.root[b + len * S] >= 0) ++len;
             }
+            const int r1 = len > 1 ? g.ent_of_slot[g.root[b + S]] : -1;
+            const int r2 = len > 2 ? g.ent_of_slot[g.root[b + 2 * S]] : -1;
+            g.run_stage[e] = make_int4(len, (int)e, r1, r2);
         }
         for (int G = 1; G <= 3; ++G) {
             const unsigned m = __ballot_sync(kFull, len == G);
-            if (!m) continue;
-            const int leader = __ffs(m) - 1;
-            int base = 0;
-            if (lane == leader) base = atomicAdd(&g.col_cnt[G - 1], __popc(m));
-            base = __shfl_sync(kFull, base, leader);
-            if (len == G) {
-                const long long j = base + __popc(m & ((1u << lane) - 1u));
+            if (lane == 0) g.run_chunk[(G - 1) * cap_ch + e0 / 32] = (int32_t)__popc(m);
+        }
+    }
+    __shared__ int s_last;
+    __shared__ int s_w[32];
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&g.ctrl->rr_done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const long long nch = (n + 31) / 32;
+    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    // exclusive scan of each bucket's chunk counts, in place; totals to col_cnt
+    for (int G = 1; G <= 3; ++G) {
+        int32_t *cnt = g.run_chunk + (G - 1) * cap_ch;
+        const long long per = (nch + blockDim.x - 1) / blockDim.x;
+        const long long lo = threadIdx.x * per, hi = lo + per < nch ? lo + per : nch;
+        int local = 0;
+        for (long long q = lo; q < hi; ++q) local += cnt[q];
+        const int incl = warp_incl_scan(local);
+        if (lane == 31) s_w[warp] = incl;
+        __syncthreads();
+        int base = 0, total = 0;
+        for (int w = 0; w < nw; ++w) {
+            const int v = s_w[w];
+            base += (w < warp) ? v : 0;
+            total += v;
+        }
+        int run = base + incl - local;
+        for (long long q = lo; q < hi; ++q) {
+            const int v = cnt[q];
+            cnt[q] = run;
+            run += v;
+        }
+        if (threadIdx.x == 0) g.col_cnt[G - 1] = total;
+        __syncthreads();
+    }
+    // the records: a warp per chunk, ranks within the chunk by ballot
+    for (long long c = warp; c < nch; c += nw) {
+        const long long e = c * 32 + lane;
+        const int4 st = e < n ? g.run_stage[e] : make_int4(0, 0, -1, -1);
+        for (int G = 1; G <= 3; ++G) {
+            const unsigned m = __ballot_sync(kFull, st.x == G);
+            if (st.x == G) {
+                const long long j = g.run_chunk[(G - 1) * cap_ch + c] + __popc(m & ((1u << lane) - 1u));
                 int32_t *rec = g.col_grp + ((long long)(G - 1) * g.cap + j) * 3;
-                rec[0] = (int32_t)e;
-                rec[1] = G > 1 ? g.ent_of_slot[g.root[b + S]] : -1;
-                rec[2] = G > 2 ? g.ent_of_slot[g.root[b + 2 * S]] : -1;
+                rec[0] = st.y;
+                rec[1] = st.z;
+                rec[2] = st.w;
             }
         }
     }
+    if (threadIdx.x == 0) g.ctrl->rr_done = 0u;
 }
 
 void launch_region_masks(const DevGrid &g, cudaStream_t s, const LaunchCfg &lc, int group_axis)
 {
-    if (group_axis != kGroupNone) cudaMemsetAsync(g.col_cnt, 0, sizeof(int32_t) * 4, s);
     k_region_masks<<<lc.num_sms * 4, 256, 0, s>>>(g, group_axis);
 }
 
