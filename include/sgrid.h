@@ -405,7 +405,7 @@ int sg_read_sums(sg_grid *g, double *host, int64_t n);
 int sg_get_stats(sg_grid *g, sg_stats *out);
 
 /* ---- stencil kernel family for 8^3 leaves (tuning; results are identical
- * up to FP32 rounding order; the three sweeps give bit-identical fields) ---- */
+ * up to FP32 rounding order; the four sweeps give bit-identical fields) ---- */
 #define SG_VARIANT_SWEEP 0 /* register sweep along i, rows via the read-only path; a warp
                               takes three consecutive list entries */
 #define SG_VARIANT_SMEM 1  /* leaf + halo staged in shared memory */
@@ -415,6 +415,13 @@ int sg_get_stats(sg_grid *g, sg_stats *out);
 #define SG_VARIANT_SWEEP_JRUNS 3   /* the default: register sweep; the fused step gives each
                                       warp up to three leaves from runs adjacent in j, so rows
                                       at the leaves' shared faces are loaded once */
+#define SG_VARIANT_SWEEP_TMA 4     /* the j-run tasks of SG_VARIANT_SWEEP_JRUNS with every x row
+                                      of the fused step staged in shared memory by bulk tensor
+                                      copies (two half-regions per warp in flight, completed
+                                      on mbarriers); bit-identical fields to SG_VARIANT_SWEEP_JRUNS.
+                                      Slower than it on the bands: a task needs 60 to 84 small
+                                      copies and each costs about 70 SM cycles of copy-engine
+                                      time.  Other stencil ops use the j-run kernels. */
 
 /* Select the stencil kernel family used by ops flushed from now on (a new grid
  * uses SG_VARIANT_SWEEP_JRUNS). */

@@ -24,7 +24,7 @@ SG_OPT_LGR, SG_OPT_AD, SG_OPT_FUSE, SG_OPT_DSE = 1, 2, 4, 8
 SG_OPT_ALL, SG_OPT_EAGER = 15, 0
 SG_CLEAR, SG_DIFFUSE7, SG_BOX27 = 0, 1, 2
 SG_CREATE_DRY_RUN, SG_CREATE_CHECK = 1, 2
-SG_VARIANT_SWEEP, SG_VARIANT_SMEM, SG_VARIANT_SWEEP_COLUMNS, SG_VARIANT_SWEEP_JRUNS = 0, 1, 2, 3
+SG_VARIANT_SWEEP, SG_VARIANT_SMEM, SG_VARIANT_SWEEP_COLUMNS, SG_VARIANT_SWEEP_JRUNS, SG_VARIANT_SWEEP_TMA = 0, 1, 2, 3, 4
 SG_MAX_FIELDS = 16
 
 _ALLOC = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsgrid.so")
-SOURCES = ["sg_api.cu", "sg_structure.cu", "sg_stencil.cu", "sg_sweep.cu", "sg_particle.cu", "sg_g2p2g.cu", "sg_multigrid.cu", "sg_elementwise.cu", "sg_advect.cu", "sg_noalloc.cu",
+SOURCES = ["sg_api.cu", "sg_structure.cu", "sg_stencil.cu", "sg_sweep.cu", "sg_sweep_tma.cu", "sg_particle.cu", "sg_g2p2g.cu", "sg_multigrid.cu", "sg_elementwise.cu", "sg_advect.cu", "sg_noalloc.cu",
            "sg_serve.cu", "sg_check.cu"]
 HEADERS = ["sg_device.h", "sg_common.cuh", "sg_particle.cuh"]
 GENCODE = ["-gencode", "arch=compute_103a,code=sm_103a"]

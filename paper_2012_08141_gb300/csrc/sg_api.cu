@@ -93,6 +93,7 @@ struct sg_grid {
     unsigned long long rmask_ver = 0;  // list version the region masks were built from (0 = never)
     unsigned long long colgrp_ver = 0; // list version the run records were built from (0 = never)
     int colgrp_axis = kGroupNone;      // axis they group leaves along
+    unsigned long long tma_ver = 0;    // list version the TMA task descriptors were built from (0 = never)
     int max_fuse = kMaxEwOps;          // element-wise ops per fused launch
     int flush_period = 0;              // flush once the queue holds this many ops (0: on sync / sg_flush only)
     long long known_leaves = 0;
@@ -307,7 +308,9 @@ int run_struct_for_group(sg_grid *g, size_t &i)
         // derived from the structure, cached with the list
         const int v = g->lc.variant;
         const bool sweep = v != kVariantSmem;
-        const int axis = v == kVariantSweepColumns ? kGroupI : (v == kVariantSweepJRuns ? kGroupJ : kGroupNone);
+        const bool tma = v == kVariantSweepTma && !store_t && !check;
+        const int axis = v == kVariantSweepColumns ? kGroupI
+                         : ((v == kVariantSweepJRuns || v == kVariantSweepTma) ? kGroupJ : kGroupNone);
         const bool need_runs = axis != kGroupNone && (g->colgrp_ver != g->list_ver || g->colgrp_axis != axis);
         if ((sweep && g->rmask_ver != g->list_ver) || need_runs) {
             if (!g->dry) launch_region_masks(g->dev, g->stream, g->lc, need_runs ? axis : kGroupNone);
@@ -318,9 +321,26 @@ int run_struct_for_group(sg_grid *g, size_t &i)
                 g->colgrp_axis = axis;
             }
         }
-        if (!g->dry)
-            launch_diffuse_box(g->dev, g->stream, a.src, a.dst, b->dst, a.coef, store_t ? 1 : 0, check,
-                               with_sum ? (int)c->slot : -1, g->lc);
+        if (tma && g->tma_ver != g->list_ver) {
+            // the staged kernel's per-task box sources and region masks
+            if (!g->dry && !g->dev.tma_desc) {
+                g->dev.tma_desc = (int32_t *)dev_alloc(g, sizeof(int32_t) * 64 * g->dev.cap);
+                g->dev.tma_rmask = (uint32_t *)dev_alloc(g, sizeof(uint32_t) * 120 * g->dev.cap);
+                if (!g->dev.tma_desc || !g->dev.tma_rmask) return fail(SG_ERR_OOM, "TMA task descriptors");
+            }
+            if (!g->dry) launch_tma_tasks(g->dev, g->stream, g->lc);
+            if ((rc = after_launch(g, "TMA task descriptors"))) return rc;
+            g->tma_ver = g->list_ver;
+        }
+        if (!g->dry) {
+            if (tma) {
+                if (launch_sweep_tma(g->dev, g->stream, a.src, b->dst, a.coef, with_sum ? (int)c->slot : -1, g->lc))
+                    return fail(SG_ERR_CUDA, "TMA-staged step: tensor maps or launch attributes unavailable");
+            } else {
+                launch_diffuse_box(g->dev, g->stream, a.src, a.dst, b->dst, a.coef, store_t ? 1 : 0, check,
+                                   with_sum ? (int)c->slot : -1, g->lc);
+            }
+        }
         g->stats.ops_fused += with_sum ? 2 : 1;
         g->stats.bytes_model += lb * (store_t ? 3.0 : 2.0);
         i = after;
@@ -1812,7 +1832,7 @@ int sg_read_sums(sg_grid *g, double *host, int64_t n)
 
 int sg_set_stencil_variant(sg_grid *g, int32_t variant)
 {
-    if (!g || variant < SG_VARIANT_SWEEP || variant > SG_VARIANT_SWEEP_JRUNS)
+    if (!g || variant < SG_VARIANT_SWEEP || variant > SG_VARIANT_SWEEP_TMA)
         return fail(SG_ERR_INVALID, "bad grid or variant");
     g->lc.variant = variant;
     return SG_OK;

@@ -87,6 +87,11 @@ struct DevGrid {
     int32_t *col_cnt;   // [4]
     int4 *run_stage;    // [cap]: per list entry, (piece length or 0, entry, next entry, the one after)
     int32_t *run_chunk; // [3][cap / 32 + 1]: pieces of each length per 32-entry list chunk
+    // TMA-staged fused step (allocated at its first use): per j-run warp task,
+    // the source slot of each staged box and the kind (64 words), and the
+    // region masks of its leaves (120 words); see k_tma_tasks
+    int32_t *tma_desc;  // [cap][64]
+    uint32_t *tma_rmask; // [cap][120]
 };
 
 // Stencil kernel families for 8^3 leaves (sg_set_stencil_variant picks one).
@@ -96,7 +101,9 @@ enum StencilVariant : int {
     kVariantSweepColumns = 2,  // register sweep; the fused step sweeps columns of
                                // leaves adjacent in i (see k_sweep_columns)
     kVariantSweepJRuns = 3,    // register sweep; a warp's leaves are runs of leaves
-                               // adjacent in j (see k_sweep_jruns); the default
+                               // adjacent in j (see k_sweep_jruns)
+    kVariantSweepTma = 4,      // the j-run tasks with every x row staged in shared
+                               // memory by bulk tensor copies (see k_sweep_tma)
 };
 
 // Axis along which launch_region_masks groups adjacent leaves into records.
@@ -172,6 +179,14 @@ void launch_diffuse_box(const DevGrid &g, cudaStream_t s, int src, int tmp, int 
                         int store_tmp, int check_act, int sum_slot, const LaunchCfg &lc);
 void launch_sum(const DevGrid &g, cudaStream_t s, int src, int sum_slot, const LaunchCfg &lc);
 int stencil_persistent_ctas(int num_sms, int which);
+
+// ---- TMA-staged fused step (sg_sweep_tma.cu), 8^3 leaves ----
+// Task descriptors of the j-run tasks (after launch_region_masks with the
+// j-run records); then the fused diffuse7 -> box27 (+ sum) step, t never
+// stored and no activation checks.  Returns 0, or nonzero if the tensor maps
+// or the launch attributes could not be set up (nothing launched).
+void launch_tma_tasks(const DevGrid &g, cudaStream_t s, const LaunchCfg &lc);
+int launch_sweep_tma(const DevGrid &g, cudaStream_t s, int src, int dst, float coef, int sum_slot, const LaunchCfg &lc);
 
 // ---- batched fused step over many grids (sg_sweep.cu) ----
 constexpr int kMaxBatch = 1024;

@@ -495,7 +495,7 @@ void launch_diffuse_box(const DevGrid &g, cudaStream_t s, int src, int tmp, int 
         launch_sweep_columns(g, s, src, tmp, dst, coef, store_tmp, check_act, sum_slot, lc);
         return;
     }
-    if (lc.variant == kVariantSweepJRuns) {
+    if (lc.variant == kVariantSweepJRuns || lc.variant == kVariantSweepTma) {
         launch_sweep_jruns(g, s, src, tmp, dst, coef, store_tmp, check_act, sum_slot, lc);
         return;
     }

@@ -532,15 +532,16 @@ def test_staged_upload_tickets():
 def test_stencil_variants_and_their_launch_counts():
     """Every stencil kernel family keeps the fused band step at one launch;
     the grouped sweeps build their run records in the region-mask launch,
-    once per list and axis."""
+    once per list and axis; the TMA-staged kernel also lays out its task
+    descriptors once per list."""
     with pytest.raises(sg.SgError):
-        dry().set_stencil_variant(4)
+        dry().set_stencil_variant(5)
     with pytest.raises(sg.SgError):
         dry().set_stencil_variant(-1)
     s = band512()
-    grouped = (sg.SG_VARIANT_SWEEP_COLUMNS, sg.SG_VARIANT_SWEEP_JRUNS)
+    axis = {sg.SG_VARIANT_SWEEP_COLUMNS: "i", sg.SG_VARIANT_SWEEP_JRUNS: "j", sg.SG_VARIANT_SWEEP_TMA: "j"}
     for variant, first in ((sg.SG_VARIANT_SWEEP, 2), (sg.SG_VARIANT_SWEEP_COLUMNS, 2), (sg.SG_VARIANT_SMEM, 1),
-                           (sg.SG_VARIANT_SWEEP_JRUNS, 2)):
+                           (sg.SG_VARIANT_SWEEP_JRUNS, 2), (sg.SG_VARIANT_SWEEP_TMA, 3)):
         g = dry(512)
         g.set_stencil_variant(variant)
         g.activate_shell(s.lo2, s.hi2, s.lo_strict)
@@ -551,10 +552,13 @@ def test_stencil_variants_and_their_launch_counts():
         # sweep already built them for the unchanged list
         g.set_stencil_variant(sg.SG_VARIANT_SWEEP)
         assert launches(g, lambda: cfg2_step(g, 0)) == (2 if variant == sg.SG_VARIANT_SMEM else 1), variant
-        # to each grouped sweep: records along a new axis are built once
-        built = variant if variant in grouped else None
-        for v in grouped:
+        # to each grouped sweep: records along a new axis are built once, the
+        # TMA task descriptors once per list
+        built = axis.get(variant)
+        tma_built = variant == sg.SG_VARIANT_SWEEP_TMA
+        for v in axis:
             g.set_stencil_variant(v)
-            first = 1 if built == v else 2
+            first = 1 + (built != axis[v]) + (v == sg.SG_VARIANT_SWEEP_TMA and not tma_built)
             assert [launches(g, lambda: cfg2_step(g, 0)) for _ in range(2)] == [first, 1], (variant, v)
-            built = v
+            built = axis[v]
+            tma_built = tma_built or v == sg.SG_VARIANT_SWEEP_TMA

@@ -91,7 +91,7 @@ def run_band(g, og, steps, slot0=0):
     return cur, np.array(sums_ref)
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4])
 @pytest.mark.parametrize("mode", list(OPTS))
 def test_band_128_100_steps(mode, variant):
     lo2, hi2 = band_bounds(40.0, 56.0)
@@ -107,8 +107,9 @@ def test_band_128_100_steps(mode, variant):
 
 
 def test_band512_full_size_fused_and_eager():
-    """The full 512^3 band (26,104 leaves): 100 steps fused and eager, every
-    per-step sum and the final field compared with one oracle run."""
+    """The full 512^3 band (26,104 leaves): 100 steps fused (register-sweep,
+    TMA-staged kernels) and eager, every per-step sum and the final field
+    compared with one oracle run."""
     spec = band512()
     og = oracle.Grid(spec.N, spec.L, 3)
     og.activate_shell(spec.lo2, spec.hi2, spec.lo_strict)
@@ -116,10 +117,11 @@ def test_band512_full_size_fused_and_eager():
     assert len(ob) == 26104
     og.write_field(0, leaf_values(spec.seed, spec.N, spec.L, ob))
     grids = {}
-    for mode in ("fused", "eager"):
+    for mode in ("fused", "eager", "fused_tma"):
         sg = sgmod()
         g = sg.Grid(spec.N, 3, 3, max_leaves=32768, max_sums=100, scratch_mask=0b010)
-        g.set_opts(OPTS[mode])
+        g.set_opts(OPTS[mode.split("_")[0]])
+        g.set_stencil_variant(sg.SG_VARIANT_SWEEP_TMA if mode == "fused_tma" else sg.SG_VARIANT_SWEEP_JRUNS)
         g.activate_shell(spec.lo2, spec.hi2, spec.lo_strict)
         g.list_gen()
         gb, gm = g.read_structure()
@@ -177,7 +179,8 @@ def test_empty_grid():
 def test_ragged_domains(N, r0, r1, strict):
     lo2, hi2 = band_bounds(r0, r1)
     spec = ShellSpec(N, 8, lo2, hi2, strict, 11)
-    for mode, variant in [("fused", 0), ("eager", 0), ("fused", 1), ("eager", 1), ("fused", 2), ("fused", 3), ("eager", 3)]:
+    for mode, variant in [("fused", 0), ("eager", 0), ("fused", 1), ("eager", 1), ("fused", 2), ("fused", 3), ("eager", 3),
+                          ("fused", 4)]:
         g, og = shell_pair(spec, n_fields=3, opts=OPTS[mode], scratch_mask=0b010, variant=variant)
         cur, sums_ref = run_band(g, og, 7)
         assert rel_linf(g.read_field(0), og.read_field(cur)) <= TOL
@@ -189,7 +192,8 @@ def test_ragged_domains(N, r0, r1, strict):
 def test_full_domain_boundary_reads_zero():
     """Every voxel active: out-of-domain neighbours read 0 at all six faces."""
     spec = ShellSpec(24, 8, 0, 10 ** 9, False, 2)
-    for mode, variant in [("fused", 0), ("eager", 0), ("fused", 1), ("eager", 1), ("fused", 2), ("fused", 3), ("eager", 3)]:
+    for mode, variant in [("fused", 0), ("eager", 0), ("fused", 1), ("eager", 1), ("fused", 2), ("fused", 3), ("eager", 3),
+                          ("fused", 4)]:
         g, og = shell_pair(spec, n_fields=3, opts=OPTS[mode], variant=variant)
         cur, _ = run_band(g, og, 5)
         assert rel_linf(g.read_field(0), og.read_field(cur)) <= TOL
@@ -349,19 +353,21 @@ def test_maximum_resolution_sparse_clusters(L):
         del og
 
 
-@pytest.mark.parametrize("grouped", ["columns", "jruns"])
+@pytest.mark.parametrize("grouped", ["columns", "jruns", "tma"])
 @pytest.mark.parametrize("store_t", [False, True])
 def test_grouped_sweeps_equal_leaf_sweep(store_t, grouped):
     """The column sweep (runs of leaves adjacent in i swept in one pass), the
-    j-run sweep (a warp's leaves taken from runs adjacent in j) and the
-    leaf-triple sweep run the same arithmetic per voxel: fields after five
-    fused steps on the 512^3 band are bit-identical, sums agree to FP32
+    j-run sweep (a warp's leaves taken from runs adjacent in j), the same
+    j-run tasks with every x row staged in shared memory by bulk tensor copies,
+    and the leaf-triple sweep run the same arithmetic per voxel: fields after
+    five fused steps on the 512^3 band are bit-identical, sums agree to FP32
     partial-sum rounding; with the intermediate stored (not scratch) that field
     is bit-identical too."""
     sg = sgmod()
     spec = band512()
     grids = []
-    first = sg.SG_VARIANT_SWEEP_COLUMNS if grouped == "columns" else sg.SG_VARIANT_SWEEP_JRUNS
+    first = {"columns": sg.SG_VARIANT_SWEEP_COLUMNS, "jruns": sg.SG_VARIANT_SWEEP_JRUNS,
+             "tma": sg.SG_VARIANT_SWEEP_TMA}[grouped]
     for variant in (first, sg.SG_VARIANT_SWEEP):
         g = sg.Grid(spec.N, 3, 3, max_leaves=32768, max_sums=5, scratch_mask=0 if store_t else 0b010)
         g.set_stencil_variant(variant)
@@ -387,7 +393,7 @@ def test_grouped_sweeps_equal_leaf_sweep(store_t, grouped):
         g.close()
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4])
 def test_fused_steps_across_structure_changes(variant):
     """Fused steps; a wider band activated (new leaves, new bits in listed
     leaves, zero-filled); fused steps; everything deactivated and a third band
