@@ -125,13 +125,22 @@ typedef struct sg_grid sg_grid; /* opaque; owned by the library */
 
 /* Create a grid whose device work runs on `cuda_stream` (a cudaStream_t; NULL
  * is the legacy default stream).  All leaves are inactive.  On success *out
- * receives the grid.  Errors: SG_ERR_INVALID (bad desc), SG_ERR_OOM. */
+ * receives the grid.  Errors: SG_ERR_INVALID (bad desc), SG_ERR_OOM.
+ * Passage: Sec. 3.2 and Fig. 3 (a pointer array over dense blocks, every
+ * pointer null while inactive; here the blocks carry a bitmask, the
+ * pointer-over-bitmasked-leaf layout of the benchmarks) and Sec. 4 "States"
+ * (the value, mask, list and allocator states the grid holds; the allocator
+ * state is the leaf pool of max_leaves). */
 int sg_create(const sg_desc *desc, void *cuda_stream, sg_grid **out);
 
-/* Synchronize the grid's stream, then release the grid and its memory. */
+/* Synchronize the grid's stream, then release the grid and its memory.
+ * Passage: Sec. 4 "States" (it ends the grid's states, the allocator state
+ * included; the paper releases them with the program and prints no call). */
 int sg_destroy(sg_grid *g);
 
-/* Select optimizer passes (SG_OPT_* bits) for ops flushed from now on. */
+/* Select optimizer passes (SG_OPT_* bits) for ops flushed from now on.
+ * Passage: Sec. 6.2-6.5 (the four passes) and Sec. 8 Table 3 (the per-pass
+ * ablation, which turns each pass off in turn). */
 int sg_set_opts(sg_grid *g, uint32_t opts);
 
 /* Queue: activate every voxel with lo2 <= D < hi2 (lo2 < D when lo_strict),
@@ -142,10 +151,15 @@ int sg_set_opts(sg_grid *g, uint32_t opts);
 int sg_activate_shell(sg_grid *g, int64_t lo2, int64_t hi2, int32_t lo_strict);
 
 /* Queue: activate n voxels given as int32 (i,j,k) triples in device memory
- * (borrowed).  Triples outside the domain are ignored. */
+ * (borrowed).  Triples outside the domain are ignored.  Passage: Sec. 3.2
+ * item 3 and Fig. 4 (activation on write: a missing leaf is allocated and
+ * zero-filled, the voxel's bit set), modifying the mask and allocator states
+ * of Sec. 4. */
 int sg_activate_coords(sg_grid *g, const int32_t *dev_xyz, int64_t n);
 
-/* Queue: deactivate every voxel and return every leaf to the pool. */
+/* Queue: deactivate every voxel and return every leaf to the pool.
+ * Passage: Sec. 4 "States" (a task that clears the mask and allocator
+ * states); the MLS-MPM case of Sec. 8.3 starts each substep's grid empty. */
 int sg_deactivate_all(sg_grid *g);
 
 /* Queue: (re)generate the active-leaf list and its 27-neighbour table.  With
@@ -156,7 +170,11 @@ int sg_list_gen(sg_grid *g);
 
 /* Queue a struct-for over the active voxels: op is SG_CLEAR (src ignored),
  * SG_DIFFUSE7 (coef used) or SG_BOX27.  src != dst.  Reads of inactive or
- * out-of-domain voxels give 0; dst at inactive voxels stays 0. */
+ * out-of-domain voxels give 0; dst at inactive voxels stays 0.  Passage:
+ * Sec. 3.2 item 1 (sparse struct-for loops over the active voxels, fed by the
+ * list of item 2) and Sec. 4 "States" with Fig. 5 (an inactive voxel reads as
+ * its ambient value 0); the stencils are the microbenchmark kind of Supp.
+ * Sec. 1 (stencil_reduction). */
 int sg_launch_stencil(sg_grid *g, int32_t op, int32_t src, int32_t dst, float coef);
 
 /* Queue activation of a tube along the k axis: every voxel with
@@ -232,13 +250,17 @@ int sg_p2g(sg_grid *g, const float *dev_x, const float *dev_v, int64_t n,
 /* Queue the grid update on active nodes: where mass > 0, v = momentum/mass,
  * v_z -= dt*gz, and along each axis a node with index < bound loses a negative
  * component and one with index > N - bound a positive one; massless nodes get
- * v = 0.  v replaces the momentum in f_mom0..f_mom0+2. */
+ * v = 0.  v replaces the momentum in f_mom0..f_mom0+2.  Passage: Sec. 8.3
+ * and Supp. Sec. 4.3 (the MLS-MPM grid operation between P2G and G2P:
+ * gravity 9.8, the ground along z). */
 int sg_grid_update(sg_grid *g, int32_t f_mass, int32_t f_mom0, float dt,
                    float gz, int32_t bound);
 
 /* Queue G2P: v_p = sum of w * v over the 27 stencil nodes (fields
  * f_mom0..f_mom0+2), then x_p += dt * v_p; dev_x and dev_v (n*3 FP32, device,
- * borrowed) are overwritten. */
+ * borrowed) are overwritten.  Passage: Sec. 8.3 (the G2P task of MLS-MPM,
+ * Fig. 12), with the quadratic B-spline weights of the MLS-MPM method it
+ * cites. */
 int sg_g2p(sg_grid *g, float *dev_x, float *dev_v, int64_t n, float dt, int32_t f_mom0);
 
 /* Queue APIC P2G with activation (the affine transfer of MLS-MPM, Sec. 8.3):
@@ -294,13 +316,19 @@ int sg_restrict(sg_grid *fine, sg_grid *coarse, int32_t f_src, int32_t f_dst, fl
  * flushing as sg_restrict; launched at once on the stream. */
 int sg_prolong(sg_grid *coarse, sg_grid *fine, int32_t f_src, int32_t f_dst, float w);
 
-/* Exchange the storage behind field indices a and b (no device work). */
+/* Exchange the storage behind field indices a and b (no device work).
+ * Passage: Sec. 8.3 (two grids swapped before each substep); the same
+ * ping-pong of value states serves the stencil steps. */
 int sg_swap(sg_grid *g, int32_t a, int32_t b);
 
-/* Optimize and launch every queued op; does not wait (Sec. 7.1). */
+/* Optimize and launch every queued op; does not wait.  Passage: Sec. 7.1
+ * "Flushing" (an explicit, non-blocking flush of the task queue through the
+ * optimizer to the device) and Sec. 5 (lazy kernel launches). */
 int sg_flush(sg_grid *g);
 
-/* Flush, wait for the stream, and return the first latched device error. */
+/* Flush, wait for the stream, and return the first latched device error.
+ * Passage: Sec. 7.1 (an implicit synchronization event flushes the queue;
+ * the evaluation synchronizes after each run, Sec. 8). */
 int sg_sync(sg_grid *g);
 
 /* Implicit sync, then the number of leaves in the (current) list. */
@@ -310,7 +338,9 @@ int sg_num_leaves(sg_grid *g, int64_t *n_leaves);
  * root index of each leaf in ascending order, masks gets L^3/32 uint32 words
  * per leaf (either may be NULL).  cap is the number of leaves the buffers
  * hold; if the list is longer, nothing is copied, *n_leaves is set and
- * SG_ERR_INVALID is returned. */
+ * SG_ERR_INVALID is returned.  Passage: Sec. 4 "States" (the list and mask
+ * states) and Sec. 7.1 (a device-to-host transfer is an implicit
+ * synchronization event). */
 int sg_read_structure(sg_grid *g, int64_t cap, int64_t *n_leaves, int32_t *leaf_b,
                       uint32_t *masks);
 
@@ -318,7 +348,9 @@ int sg_read_structure(sg_grid *g, int64_t cap, int64_t *n_leaves, int32_t *leaf_
  * per leaf, 0 at inactive voxels.  cap = leaves the buffer holds.  A
  * page-locked buffer mapped into the device's address space (16-byte
  * aligned) is written in place by the gather kernel; any other buffer gets a
- * staged copy. */
+ * staged copy.  Passage: Sec. 4 "States" and Fig. 5 (the value state, an
+ * inactive voxel reading 0) and Sec. 7.1 (the read is an implicit
+ * synchronization event). */
 int sg_read_field(sg_grid *g, int32_t f, int64_t cap, float *host_vals);
 
 /* Set field f from host memory in list order (n_leaves * L^3 FP32 values;
@@ -398,10 +430,15 @@ int sg_graph_destroy(sg_graph *graph);
  * changed). */
 int sg_write_structure(sg_grid *g, int64_t n_leaves, const int32_t *leaf_b, const uint32_t *masks);
 
-/* Implicit sync, then copy result slots [0, n) to host memory. */
+/* Implicit sync, then copy result slots [0, n) to host memory.  Passage:
+ * Sec. 7.1 (a device-to-host transfer flushes the queue and synchronizes);
+ * the slots hold reductions such as those of the stencil_reduction
+ * microbenchmark (Supp. Sec. 1). */
 int sg_read_sums(sg_grid *g, double *host, int64_t n);
 
-/* Counters since creation. */
+/* Counters since creation.  Passage: Sec. 8 "Metrics" (tasks launched is
+ * the paper's third metric; list generations and demoted activations are the
+ * counts behind Sec. 8.4's 420,912 -> 8,004 list generations). */
 int sg_get_stats(sg_grid *g, sg_stats *out);
 
 /* ---- stencil kernel family for 8^3 leaves (tuning; results are identical
