@@ -206,11 +206,18 @@ class Grid:
         return int(self.lib.og_activate_tube(self.h, int(lo2), int(hi2)))
 
     def advect(self, dst: int, src: int, v0: int, dt: float):
-        """dst = src at the RK3 backtrace over dt (trilinear, through the mask)."""
+        """dst = src at the RK3 backtrace over dt (trilinear, through the mask).
+        dst must differ from src and the velocity fields v0..v0+2 (the loop
+        writes dst while it reads them)."""
+        if dst == src or v0 <= dst <= v0 + 2:
+            raise ValueError("advect: dst aliases src or a velocity field")
         self.lib.og_advect(self.h, int(dst), int(src), int(v0), float(dt))
 
     def maccormack(self, dst: int, q: int, qhat: int, qtilde: int, v0: int, dt: float):
-        """dst = clamp(qhat + (q - qtilde) / 2) to the forward sample's 8 values of q."""
+        """dst = clamp(qhat + (q - qtilde) / 2) to the forward sample's 8 values of q.
+        dst must differ from q, qhat, qtilde and the velocity fields."""
+        if dst in (q, qhat, qtilde) or v0 <= dst <= v0 + 2:
+            raise ValueError("maccormack: dst aliases an input or a velocity field")
         self.lib.og_maccormack(self.h, int(dst), int(q), int(qhat), int(qtilde), int(v0), float(dt))
 
     def ew(self, dst: int, a: int = -1, b: int = -1, alpha: float = 0.0, beta: float = 0.0, gamma: float = 0.0,

@@ -89,3 +89,53 @@ def test_ten_steps_fused():
     for c in range(3):
         assert rel_linf(g.read_field(3 + 4 * c), og.read_field(3 + 4 * c)) <= 1e-4, c
     g.close()
+
+
+@pytest.mark.parametrize("mode", ["all", "nofuse"])
+def test_clamp_case_matches_oracle(mode):
+    """The case of the oracle's clamp pin (a spike on a ramp, uniform
+    fractional velocity): the library's MacCormack correction, fused with the
+    backward advection (and reading the forward advection's stored bounds) or
+    not, matches the oracle within 2e-5, and where the unclamped correction
+    leaves the forward sample's range the library's value is the clamp bound,
+    not the unclamped value."""
+    import torch
+    import paper_2012_08141_gb300 as sg
+    from advect_cases import clamp_case
+    N = 32
+    dtime, d, dense, m, rr, fw, _, _ = clamp_case(N)
+    r = np.arange(4, 28)
+    box = np.stack(np.meshgrid(r, r, r, indexing="ij"), -1).reshape(-1, 3).astype(np.int32)
+    g = sg.Grid(N, 3, 7, max_leaves=(N // 8) ** 3, scratch_mask=1 << 5)
+    g.set_opts(sg.SG_OPT_ALL if mode == "all" else sg.SG_OPT_ALL & ~sg.SG_OPT_FUSE)
+    og = oracle.Grid(N, 8, 7)
+    xyz = torch.from_numpy(box).cuda()
+    g.activate_coords(xyz)
+    og.activate_coords(box)
+    b, msk = g.read_structure()
+    ob, om = og.structure()
+    np.testing.assert_array_equal(b, ob)
+    np.testing.assert_array_equal(msk, om)
+    cells = oracle.leaf_coords(b, N, 8)
+    u = d / (dtime * N)
+    vals = dense[cells[..., 0], cells[..., 1], cells[..., 2]]
+    for G in (g, og):
+        for a in range(3):
+            G.write_field(1 + a, np.full(cells.shape[:2], u[a]))
+        G.write_field(0, vals)
+        G.advect(4, 0, 1, dtime)        # q^ = q at x - d
+        G.advect(5, 4, 1, -dtime)       # q~ = q^ at x + d (scratch)
+        G.maccormack(6, 0, 4, 5, 1, dtime)
+    got, ref = g.read_field(6), og.read_field(6)
+    assert rel_linf(got, ref) <= TOL
+    # the voxels where the clamp acts, by the definitions
+    dense_got = np.zeros((N, N, N))
+    dense_got[cells[..., 0], cells[..., 1], cells[..., 2]] = got
+    inner = dense_got[m:N - m, m:N - m, m:N - m]
+    acts = (rr < fw[0]) | (rr > fw[1])
+    want = np.clip(rr, fw[0], fw[1])
+    strong = acts & (np.abs(want - rr) > 1e-3)   # clearly clamped
+    assert strong.sum() >= 4
+    np.testing.assert_allclose(inner[acts], want[acts], rtol=0, atol=2e-6)
+    assert np.all(np.abs(inner[strong] - rr[strong]) > 5e-4)
+    g.close()

@@ -14,6 +14,7 @@ import pytest
 import dense_twin as dt
 from sgtest import mask_bits
 import oracle
+from advect_cases import clamp_case
 from workload import band_bounds, band512, leaf_values, spheres_particles, tiny_shell
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_examples.txt")
@@ -630,7 +631,7 @@ def test_maccormack_linear_field_and_clamp():
     q_tilde = q, so the correction returns q_hat exactly; the corrected value
     always lies within the forward sample's 8 values."""
     N, dtime = 32, 0.01
-    g, b, cells = _box_advect_grid(N)
+    g, b, cells = _box_advect_grid(N, F=7)   # q 0, velocity 1..3, q^ 4, q~ 5, result 6
     u = np.array([0.7, -0.35, 1.3]) / (dtime * N)
     for a in range(3):
         g.write_field64(1 + a, np.full(cells.shape[:2], u[a]))
@@ -638,17 +639,44 @@ def test_maccormack_linear_field_and_clamp():
     g.write_field64(0, (cells - 16.0) @ w)
     g.advect(4, 0, 1, dtime)
     g.advect(5, 4, 1, -dtime)
-    g.maccormack(3, 0, 4, 5, 1, dtime)
+    g.maccormack(6, 0, 4, 5, 1, dtime)
     inside = np.all(np.abs(cells - 16.0) < 8, axis=2)
-    np.testing.assert_allclose(g.read_field(3)[inside], g.read_field(4)[inside], rtol=0, atol=1e-12)
+    np.testing.assert_allclose(g.read_field(6)[inside], g.read_field(4)[inside], rtol=0, atol=1e-12)
     # bounds on a rough field
     rng = np.random.default_rng(4)
     g.write_field64(0, rng.uniform(-1, 1, size=cells.shape[:2]))
     g.advect(4, 0, 1, dtime)
     g.advect(5, 4, 1, -dtime)
-    g.maccormack(3, 0, 4, 5, 1, dtime)
-    q, r = g.read_field(0), g.read_field(3)
+    g.maccormack(6, 0, 4, 5, 1, dtime)
+    q, r = g.read_field(0), g.read_field(6)
     assert np.all(r <= max(q.max(), 0.0) + 1e-15) and np.all(r >= min(q.min(), 0.0) - 1e-15)
+
+
+def test_maccormack_clamp_acts_on_the_forward_sample_values():
+    """Near a spike the correction qhat + (q - q~)/2 leaves the range of the
+    forward sample's 8 values of q, and the oracle must clamp it to exactly
+    those 8 (Sec. 8.2, the clamped MacCormack of Selle et al.).  The expected
+    field comes from the definitions on a dense array; the case is chosen so
+    that a clamp to the voxel's own 8 cells or to the 8 cells around the
+    backward sample gives a different field, so either mistake fails."""
+    N = 32
+    dtime, d, dense, m, rr, fw, own, bw = clamp_case(N)
+    want = np.clip(rr, fw[0], fw[1])
+    acts = (rr < fw[0]) | (rr > fw[1])
+    assert acts.sum() >= 8                                     # the clamp acts here
+    assert np.abs(np.clip(rr, own[0], own[1]) - want).max() > 1e-3
+    assert np.abs(np.clip(rr, bw[0], bw[1]) - want).max() > 1e-3
+    g, b, cells = _box_advect_grid(N, F=7)   # q 0, velocity 1..3, q^ 4, q~ 5, result 6
+    idx = cells.astype(np.int64)
+    u = d / (dtime * N)
+    for a in range(3):
+        g.write_field64(1 + a, np.full(cells.shape[:2], u[a]))
+    g.write_field64(0, dense[idx[..., 0], idx[..., 1], idx[..., 2]])
+    g.advect(4, 0, 1, dtime)
+    g.advect(5, 4, 1, -dtime)
+    g.maccormack(6, 0, 4, 5, 1, dtime)
+    got = np.array([[[g.get(6, i, j, k) for k in range(m, N - m)] for j in range(m, N - m)] for i in range(m, N - m)])
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-12)
 
 
 def test_grid_update_hand_case():
