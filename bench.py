@@ -6,6 +6,8 @@ box27(t->y), swap(x,y), sum(x), through the library's queue with every
 inter-kernel pass on (one fused launch).  The eager form (list regenerated
 and activation checked in every kernel, 12 launches per step) is timed beside
 it.  Further legs (skipped with --only fused or on more than one rank):
+  tiny      the 64^3 shell, 20 steps of activate, list generation, diffuse7
+            and swap, all passes against eager: launches per step;
   batched   64 independent band/ball grids, active sizes log-uniform in
             1e3..5e6, one persistent launch per step in a CUDA graph
             (autotuned warps per CTA), against the same grids stepped one
@@ -54,6 +56,7 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 from workload import (ShellSpec, band512, batched_mix, leaf_values, serving_arrivals, spheres_particles,  # noqa: E402
+                      tiny_shell,
                       tube, tube_fields)
 
 METRIC = "active voxel-steps/s"
@@ -279,6 +282,39 @@ def bench_band1024(torch, sg, steps, warmup, flush_buf, stream, variant=3):
     return out
 
 
+def bench_tiny(torch, sg, steps, warmup, flush_buf, stream):
+    """The tiny eager workload: the 64^3 shell of radius 24 +- 2 (seed 0),
+    8^3 leaves; each step activates the shell, regenerates the list, diffuses
+    into a second field (dt k = 0.1) and swaps, with every pass on and in
+    the eager form.  Launch-bound: the figure of merit is launches per step."""
+    spec = tiny_shell(0)
+    out = {"workload": "64^3 shell r=24+-2 h=2, 8^3 leaves: activate, list generation, diffuse7, swap per step",
+           "l2": "flushed before every timed step (512 MB write)"}
+    for mode, opts in (("all", sg.SG_OPT_ALL), ("eager", sg.SG_OPT_EAGER)):
+        g = sg.Grid(spec.N, 3, 2, max_leaves=512)
+        g.set_opts(opts)
+        g.activate_shell(spec.lo2, spec.hi2, spec.lo_strict)
+        g.list_gen()
+        b, _ = g.read_structure()
+        g.write_field(0, leaf_values(spec.seed, spec.N, spec.L, b))
+        act = g.num_active()
+
+        def step():
+            g.activate_shell(spec.lo2, spec.hi2, spec.lo_strict)
+            g.list_gen()
+            g.diffuse7(0, 1, 0.1)
+            g.swap(0, 1)
+            g.flush()
+
+        ms, launches = time_steps(torch, step, steps, warmup, flush_buf, stream, lambda: g.stats()["launches"])
+        t = sum(ms) / 1e3
+        out[mode] = {"ms_per_step": t * 1e3 / steps, "launches_per_step": launches / steps,
+                     "value": act * steps / t, "active_voxels": act}
+        g.close()
+    out["unit"] = "voxel-steps/s"
+    return out
+
+
 def bench_ablation(torch, sg, x_host, steps, warmup, flush_buf, stream):
     """The four passes switched off one at a time (Table 3's ablation, on the
     512^3 band).  The step re-activates the band first, as the paper's steps
@@ -324,7 +360,15 @@ def bench_batched(torch, sg, steps, warmup, flush_buf, stream):
     active = sum(g.num_active() for g in grids)
     leaves = sum(g.num_leaves() for g in grids)
     bt = sg.Batch(grids, 0, 1, 2, 0.1)
+    # every (halo staging, warps per CTA) choice of the autotuner, timed here too
+    cands = {}
+    for staged, wc in ((False, 2), (False, 4), (False, 8), (True, 8)):
+        bt.set_staging(staged)
+        bt.set(wc, True)
+        msc, _ = time_steps(torch, bt.step, max(3, steps // 2), 2, flush_buf, stream)
+        cands[("staged" if staged else "register") + f"_w{wc}"] = sum(msc) / len(msc)
     w = bt.autotune(3)
+    cfg = bt.config()
     l0 = bt.info()["launches"]
     ms, _ = time_steps(torch, bt.step, steps, warmup, flush_buf, stream)
     launches = (bt.info()["launches"] - l0) / (steps + warmup)
@@ -350,7 +394,8 @@ def bench_batched(torch, sg, steps, warmup, flush_buf, stream):
     return {"workload": "64 band/ball grids, active sizes log-uniform 1e3..5e6 (seed 0)", "grids": len(grids),
             "active_voxels": active, "leaves": leaves, "value": active * steps / t_b,
             "ms_per_step": t_b * 1e3 / steps, "launches_per_step": launches, "warps_per_cta": w,
-            "cuda_graph": True, **res,
+            "halo_staging": "shared memory (bulk tensor copies)" if cfg["staged"] else "registers",
+            "autotune_candidates_ms": cands, "cuda_graph": True, **res,
             "over_sequential_eager": (active * steps / t_b) / res["sequential_eager"]["value"]}
 
 
@@ -725,7 +770,8 @@ def run_ours(args):
     extra = {}
     if world == 1 and args.only != "fused":
         k = max(5, min(args.steps, 20))
-        for name, fn in (("band1024", lambda: bench_band1024(torch, sg, k, 3, flush_buf, stream, args.variant)),
+        for name, fn in (("tiny", lambda: bench_tiny(torch, sg, 20, 3, flush_buf, stream)),
+                         ("band1024", lambda: bench_band1024(torch, sg, k, 3, flush_buf, stream, args.variant)),
                          ("batched", lambda: bench_batched(torch, sg, k, 3, flush_buf, stream)),
                          ("particles", lambda: bench_particles(torch, sg, k, 3, flush_buf, stream)),
                          ("mpm_apic", lambda: bench_mpm_apic(torch, sg, k, 3, flush_buf, stream)),
@@ -733,7 +779,7 @@ def run_ours(args):
                          ("micro", lambda: bench_micro(torch, sg, k, 3, flush_buf, stream)),
                          ("advection", lambda: bench_advection(torch, sg, k, 3, flush_buf, stream)),
                          ("ablation", lambda: bench_ablation(torch, sg, x_host, k, 3, flush_buf, stream)),
-                         ("serving", lambda: bench_serving(torch, sg))):
+                         ("serving", lambda: bench_serving(torch, sg, duration=args.serving_duration))):
             if args.only not in ("all", name):
                 continue
             try:
@@ -864,7 +910,9 @@ def main():
     ap.add_argument("--variant", type=int, default=3, choices=[0, 1, 2, 3, 4],
                     help="stencil kernel family (0 sweep, 1 smem, 2 sweep over i-columns, 3 sweep over j-runs, "
                          "4 j-runs staged in shared memory by bulk tensor copies)")
-    ap.add_argument("--only", choices=["all", "fused", "band1024", "batched", "particles", "mpm_apic", "multigrid",
+    ap.add_argument("--serving-duration", type=float, default=2.0,
+                    help="seconds of Poisson arrivals per rate in the serving leg")
+    ap.add_argument("--only", choices=["all", "fused", "tiny", "band1024", "batched", "particles", "mpm_apic", "multigrid",
                                        "micro", "advection", "ablation", "serving"],
                     default="all",
                     help="fused: only the fused headline step; a leg name: the headline step and that leg "

@@ -503,8 +503,21 @@ int sg_batch_read_sums(sg_batch *b, double *host, int32_t n);
 /* Warps per CTA of the persistent kernel (2, 4 or 8: up to 6, 12 or 24 leaves
  * per CTA) and whether steps run as captured CUDA graphs. */
 int sg_batch_set(sg_batch *b, int32_t warps_per_cta, int32_t use_graph);
-/* Autotuner: time trial_steps steps with each warps-per-CTA choice (these are
- * real steps: they advance every grid) and keep the fastest. */
+/* Halo staging of the batched kernel: 0 (the default) the register sweep,
+ * whose lanes read their x rows, halo included, from L2/HBM; 1 every task's
+ * x region (leaves plus halo) staged in shared memory by bulk tensor copies
+ * completed on mbarriers, eight warps per CTA, one CTA per SM (the body of
+ * SG_VARIANT_SWEEP_TMA; warps_per_cta does not apply).  The first switch to 1
+ * builds every grid's task descriptors and tensor maps and synchronizes.
+ * Fields are bit-identical either way. */
+int sg_batch_set_staging(sg_batch *b, int32_t staged);
+/* The launch shape a step uses now (warps per CTA, halo staging). */
+int sg_batch_config(sg_batch *b, int32_t *warps_per_cta, int32_t *staged);
+/* Autotuner: time trial_steps steps with each (halo staging, warps per CTA)
+ * choice -- the register sweep at 2, 4 and 8 warps per CTA and the staged
+ * body -- (these are real steps: they advance every grid) and keep the
+ * fastest; *chosen_warps gets its warps per CTA (sg_batch_config gives
+ * both). */
 int sg_batch_autotune(sg_batch *b, int32_t trial_steps, int32_t *chosen_warps);
 int sg_batch_info(sg_batch *b, int64_t *total_leaves, int64_t *launches, int32_t *warps_per_cta);
 int sg_batch_destroy(sg_batch *b);
@@ -524,7 +537,8 @@ int sg_batch_destroy(sg_batch *b);
  *   2. runs one batched step (one persistent launch, see sg_batch_create)
  *      over every resident job, so jobs admitted while others run share it;
  *   3. retires jobs that reached their step count, keeping their last sum
- *      and their submit / admit / done times (seconds, host steady clock);
+ *      and their submit / admit / done times (seconds, host steady clock),
+ *      and copying their final field to out_values when one is given;
  * and synchronizes the stream once.  A job's result equals the same job run
  * alone up to FP32 rounding order. */
 #define SG_JOB_PENDING 0
@@ -549,6 +563,12 @@ typedef struct sg_job_desc {
     int32_t steps;    /* >= 1 */
     int32_t pad;
     int64_t seed;     /* sg_fill_hash seed, 0 <= seed < 2^24 */
+    float *out_values; /* optional (NULL: none): host buffer that receives the
+                          job's final x at its active voxels when it completes,
+                          packed as sg_read_field_active writes them; owned by
+                          the caller and borrowed until the job is done */
+    int64_t out_cap;   /* values out_values holds; a job with more active
+                          voxels fails at completion instead of writing */
 } sg_job_desc;
 typedef struct sg_job_status {
     int32_t state;      /* SG_JOB_* */
@@ -596,8 +616,11 @@ int sg_server_destroy(sg_server *s);
  * kernel runs, so two calls whose work overlaps on the GPU (different
  * streams, no ordering between them) race and give wrong results.  The first
  * call on a device, with that device current, looks up the array's device
- * address (cudaGetSymbolAddress); make that first call before any stream
- * capture begins.
+ * address (cudaGetSymbolAddress) and keeps it for the process; make that
+ * first call before any stream capture begins.  A reset of the device
+ * (cudaDeviceReset) unloads the library's device code there and makes the
+ * kept address stale, which the library does not detect: do not call this
+ * entry point on a device after resetting it.
  *
  * Returns SG_OK, SG_ERR_INVALID (bad arguments or too many cells) or
  * SG_ERR_CUDA (the address lookup, a memset or the launch failed). */

@@ -125,6 +125,8 @@ def load_library(build: bool = True) -> ctypes.CDLL:
         "sg_batch_read_sums": [P, P, I32],
         "sg_batch_set": [P, I32, I32],
         "sg_batch_autotune": [P, I32, ctypes.POINTER(I32)],
+        "sg_batch_set_staging": [P, I32],
+        "sg_batch_config": [P, ctypes.POINTER(I32), ctypes.POINTER(I32)],
         "sg_batch_info": [P, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I32)],
         "sg_batch_destroy": [P],
         "sg_num_active": [P, ctypes.POINTER(I64)],
@@ -554,7 +556,19 @@ class Batch:
     def set(self, warps_per_cta: int, use_graph: bool = True):
         _check(self.lib, self.lib.sg_batch_set(self.h, int(warps_per_cta), int(bool(use_graph))))
 
+    def set_staging(self, staged: bool):
+        """Halo staging: False the register sweep, True the body staged in
+        shared memory by bulk tensor copies."""
+        _check(self.lib, self.lib.sg_batch_set_staging(self.h, int(bool(staged))))
+
+    def config(self) -> dict:
+        w, st = ctypes.c_int32(), ctypes.c_int32()
+        _check(self.lib, self.lib.sg_batch_config(self.h, ctypes.byref(w), ctypes.byref(st)))
+        return {"warps_per_cta": w.value, "staged": bool(st.value)}
+
     def autotune(self, trial_steps: int = 3) -> int:
+        """Time every (halo staging, warps per CTA) choice and keep the
+        fastest; returns its warps per CTA (config() gives both)."""
         w = ctypes.c_int32()
         _check(self.lib, self.lib.sg_batch_autotune(self.h, int(trial_steps), ctypes.byref(w)))
         return w.value

@@ -94,6 +94,7 @@ struct sg_grid {
     unsigned long long colgrp_ver = 0; // list version the run records were built from (0 = never)
     int colgrp_axis = kGroupNone;      // axis they group leaves along
     unsigned long long tma_ver = 0;    // list version the TMA task descriptors were built from (0 = never)
+    long long tma_entries = 0;         // warp tasks the TMA descriptor arrays hold
     int max_fuse = kMaxEwOps;          // element-wise ops per fused launch
     int flush_period = 0;              // flush once the queue holds this many ops (0: on sync / sg_flush only)
     long long known_leaves = 0;
@@ -161,6 +162,26 @@ int after_launch(sg_grid *g, const char *what)
 }
 
 bool valid_field(const sg_grid *g, int f) { return f >= 0 && f < g->desc.n_fields; }
+
+// Room in the TMA task-descriptor arrays for `entries` warp tasks (a grid's
+// tasks never exceed its list length, nor its pool capacity).  A larger
+// request replaces the arrays; the old ones are released with the grid.
+int ensure_tma_desc(sg_grid *g, long long entries)
+{
+    entries = std::max(1LL, entries);
+    if (g->tma_entries >= entries) return SG_OK;
+    g->dev.tma_desc = (int32_t *)dev_alloc(g, sizeof(int32_t) * 64 * entries);
+    g->dev.tma_rmask = (uint32_t *)dev_alloc(g, sizeof(uint32_t) * 120 * entries);
+    if (!g->dev.tma_desc || !g->dev.tma_rmask) {
+        g->tma_entries = 0;
+        g->dev.tma_desc = nullptr;
+        g->dev.tma_rmask = nullptr;
+        return fail(SG_ERR_OOM, "TMA task descriptors");
+    }
+    g->tma_entries = entries;
+    g->tma_ver = 0;  // fresh arrays hold no descriptors yet
+    return SG_OK;
+}
 
 // True while the grid's stream is being recorded into a graph (sg_graph_begin).
 bool capturing(const sg_grid *g)
@@ -323,11 +344,7 @@ int run_struct_for_group(sg_grid *g, size_t &i)
         }
         if (tma && g->tma_ver != g->list_ver) {
             // the staged kernel's per-task box sources and region masks
-            if (!g->dry && !g->dev.tma_desc) {
-                g->dev.tma_desc = (int32_t *)dev_alloc(g, sizeof(int32_t) * 64 * g->dev.cap);
-                g->dev.tma_rmask = (uint32_t *)dev_alloc(g, sizeof(uint32_t) * 120 * g->dev.cap);
-                if (!g->dev.tma_desc || !g->dev.tma_rmask) return fail(SG_ERR_OOM, "TMA task descriptors");
-            }
+            if (!g->dry && (rc = ensure_tma_desc(g, g->dev.cap))) return rc;
             if (!g->dry) launch_tma_tasks(g->dev, g->stream, g->lc);
             if ((rc = after_launch(g, "TMA task descriptors"))) return rc;
             g->tma_ver = g->list_ver;
@@ -1895,6 +1912,9 @@ struct sg_batch {
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     int num_sms = 0;
     long long launches = 0;
+    int staged = 0;                        // body: 0 register sweep, 1 staged by bulk tensor copies
+    bool staged_ready = false;             // descriptors and tensor maps of the staged body are set up
+    std::vector<BatchGrid> host_items[2];
 };
 
 namespace {
@@ -1913,8 +1933,14 @@ int batch_enqueue(sg_batch *b, int parity)
     const size_t nacc = sizeof(double) * b->grids.size();
     int rc = cuda_check(cudaMemsetAsync(b->dev_acc, 0, nacc, b->stream), "batch accumulator reset");
     if (rc) return rc;
-    launch_batch_diffuse_box(b->dev_items[parity], (int)b->grids.size(), b->total_tri, b->coef, b->dev_acc, b->warps,
-                             b->num_sms, b->stream);
+    if (b->staged) {
+        if (launch_batch_tma(b->dev_items[parity], (int)b->grids.size(), b->total_tri, b->coef, b->dev_acc, b->num_sms,
+                             b->stream))
+            return fail(SG_ERR_CUDA, "staged batched step: launch attributes unavailable");
+    } else {
+        launch_batch_diffuse_box(b->dev_items[parity], (int)b->grids.size(), b->total_tri, b->coef, b->dev_acc,
+                                 b->warps, b->num_sms, b->stream);
+    }
     return cuda_check(cudaPeekAtLastError(), "batched step launch");
 }
 
@@ -2037,6 +2063,8 @@ int sg_batch_create(sg_grid *const *grids, int32_t n, int32_t src, int32_t tmp, 
         return rc;
     }
     sg_grid *g0 = grids[0];
+    b->host_items[0] = items[0];
+    b->host_items[1] = items[1];
     for (int p = 0; p < 2 && !rc; ++p) {
         b->blocks[p] = dev_alloc(g0, sizeof(BatchGrid) * n + (p == 0 ? sizeof(double) * n : 0));
         if (!b->blocks[p]) rc = fail(SG_ERR_OOM, "batch descriptors");
@@ -2063,6 +2091,56 @@ int sg_batch_create(sg_grid *const *grids, int32_t n, int32_t src, int32_t tmp, 
         return rc;
     }
     *out = b;
+    return SG_OK;
+}
+
+// The staged body's inputs, once per batch: every grid's TMA task
+// descriptors (its j-run records are current since sg_batch_create) and the
+// tensor maps over x for both src/dst parities, uploaded with the
+// descriptors of the batch.
+int batch_prepare_staged(sg_batch *b)
+{
+    if (b->staged_ready) return SG_OK;
+    const int n = (int)b->grids.size();
+    int rc;
+    for (sg_grid *g : b->grids) {
+        if ((rc = ensure_tma_desc(g, std::max<long long>(g->host_ctrl->list_n, 1)))) return rc;
+        if (g->tma_ver != g->list_ver) {
+            launch_tma_tasks(g->dev, g->stream, g->lc);
+            if ((rc = after_launch(g, "TMA task descriptors"))) return rc;
+            g->tma_ver = g->list_ver;
+        }
+        if ((rc = cuda_check(cudaStreamSynchronize(g->stream), "stream synchronize"))) return rc;
+    }
+    std::vector<unsigned char> host(size_t(2) * n * kTmaMapsBytes + 64);
+    unsigned char *h = host.data() + ((64 - (reinterpret_cast<uintptr_t>(host.data()) & 63)) & 63);
+    for (int i = 0; i < n; ++i)
+        for (int p = 0; p < 2; ++p)
+            if (!tma_encode_maps(b->host_items[p][i].x, b->grids[i]->dev.cap, h + size_t(2 * i + p) * kTmaMapsBytes))
+                return fail(SG_ERR_CUDA, "tensor maps of batched grid %d could not be encoded", i);
+    unsigned char *dmaps = (unsigned char *)dev_alloc(b->grids[0], size_t(2) * n * kTmaMapsBytes);
+    if (!dmaps) return fail(SG_ERR_OOM, "batch tensor maps");
+    for (int i = 0; i < n; ++i) {
+        const DevGrid &d = b->grids[i]->dev;
+        if (!d.tma_desc || !d.tma_rmask) return fail(SG_ERR_INVALID, "batched grid %d has no TMA task descriptors", i);
+        for (int p = 0; p < 2; ++p) {
+            // the items hold copies of the grids' device descriptors, taken at
+            // sg_batch_create: refresh them so they carry the arrays above
+            b->host_items[p][i].g.tma_desc = d.tma_desc;
+            b->host_items[p][i].g.tma_rmask = d.tma_rmask;
+            b->host_items[p][i].tma_maps = dmaps + size_t(2 * i + p) * kTmaMapsBytes;
+        }
+    }
+    if ((rc = cuda_check(cudaMemcpyAsync(dmaps, h, size_t(2) * n * kTmaMapsBytes, cudaMemcpyHostToDevice, b->stream),
+                         "batch tensor maps")))
+        return rc;
+    for (int p = 0; p < 2; ++p)
+        if ((rc = cuda_check(cudaMemcpyAsync(b->dev_items[p], b->host_items[p].data(), sizeof(BatchGrid) * n,
+                                             cudaMemcpyHostToDevice, b->stream),
+                             "batch descriptors")))
+            return rc;
+    if ((rc = cuda_check(cudaStreamSynchronize(b->stream), "batch sync"))) return rc;
+    b->staged_ready = true;
     return SG_OK;
 }
 
@@ -2113,6 +2191,24 @@ int sg_batch_read_sums(sg_batch *b, double *host, int32_t n)
     return cuda_check(cudaStreamSynchronize(b->stream), "batch sync");
 }
 
+int sg_batch_set_staging(sg_batch *b, int32_t staged)
+{
+    if (!b || (staged != 0 && staged != 1)) return fail(SG_ERR_INVALID, "staged must be 0 or 1");
+    int rc;
+    if (staged && (rc = batch_prepare_staged(b))) return rc;
+    if (staged != b->staged) batch_drop_graphs(b);
+    b->staged = staged;
+    return SG_OK;
+}
+
+int sg_batch_config(sg_batch *b, int32_t *warps_per_cta, int32_t *staged)
+{
+    if (!b) return fail(SG_ERR_INVALID, "null batch");
+    if (warps_per_cta) *warps_per_cta = b->staged ? 8 : b->warps;
+    if (staged) *staged = b->staged;
+    return SG_OK;
+}
+
 int sg_batch_info(sg_batch *b, int64_t *total_leaves, int64_t *launches, int32_t *warps_per_cta)
 {
     if (!b) return fail(SG_ERR_INVALID, "null batch");
@@ -2125,20 +2221,24 @@ int sg_batch_info(sg_batch *b, int64_t *total_leaves, int64_t *launches, int32_t
 int sg_batch_autotune(sg_batch *b, int32_t trial_steps, int32_t *chosen)
 {
     if (!b || trial_steps < 1) return fail(SG_ERR_INVALID, "bad autotune arguments");
-    const int cands[3] = {2, 4, 8};
+    // (halo staging, warps per CTA): the register sweep at 2, 4 and 8 warps
+    // per CTA, and the body staged by bulk tensor copies (eight warps per CTA,
+    // one CTA per SM, fixed by its shared-memory buffers)
+    const int cands[4][2] = {{0, 2}, {0, 4}, {0, 8}, {1, 8}};
     float best = 1e30f;
-    int best_w = b->warps, rc;
+    int best_w = b->warps, best_s = b->staged, rc = SG_OK;
     cudaEvent_t e0, e1;
     if ((rc = cuda_check(cudaEventCreate(&e0), "event"))) return rc;
     if ((rc = cuda_check(cudaEventCreate(&e1), "event"))) {
         cudaEventDestroy(e0);
         return rc;
     }
-    for (int w : cands) {
-        if ((rc = sg_batch_set(b, w, b->use_graph))) break;
+    for (const auto &c : cands) {
+        if ((rc = sg_batch_set_staging(b, c[0]))) break;
+        if ((rc = sg_batch_set(b, c[1], b->use_graph))) break;
         if ((rc = sg_batch_step(b))) break;  // warm-up (and graph capture)
         if ((rc = cuda_check(cudaEventRecord(e0, b->stream), "event"))) break;
-        for (int s = 0; s < trial_steps && !rc; ++s) rc = sg_batch_step(b);
+        for (int st = 0; st < trial_steps && !rc; ++st) rc = sg_batch_step(b);
         if (rc) break;
         if ((rc = cuda_check(cudaEventRecord(e1, b->stream), "event"))) break;
         if ((rc = cuda_check(cudaEventSynchronize(e1), "event sync"))) break;
@@ -2146,13 +2246,14 @@ int sg_batch_autotune(sg_batch *b, int32_t trial_steps, int32_t *chosen)
         cudaEventElapsedTime(&ms, e0, e1);
         if (ms < best) {
             best = ms;
-            best_w = w;
+            best_w = c[1];
+            best_s = c[0];
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc) return rc;
-    if ((rc = sg_batch_set(b, best_w, b->use_graph))) return rc;
+    if ((rc = sg_batch_set_staging(b, best_s)) || (rc = sg_batch_set(b, best_w, b->use_graph))) return rc;
     if (chosen) *chosen = best_w;
     return SG_OK;
 }

@@ -199,12 +199,23 @@ struct BatchGrid {
     int c3, c2, c1;  // j-run pieces of three, two and one leaves (records in g.col_grp)
     int tasks;       // warp tasks of this grid (see k_sweep_jruns)
     int tri0;        // first global task index of this grid
+    const void *tma_maps;  // staged body: 8 tensor maps (1 KB, device memory) over x, else null
 };
 // One launch: every grid's fused diffuse7 -> box27 step, per-grid sums
 // added to acc[grid] (acc zeroed by the caller).  warps = warps per CTA.
 void launch_batch_diffuse_box(const BatchGrid *items, int n_grids, int total_tri, float coef, double *acc, int warps,
                               int num_sms, cudaStream_t s);
 int batch_ctas(int num_sms, int warps);
+// The same step with the staged (TMA) body of sg_sweep_tma.cu: needs every
+// grid's TMA task descriptors (launch_tma_tasks) and tma_maps.  Returns
+// nonzero if the launch attributes could not be set (nothing launched).
+int launch_batch_tma(const BatchGrid *items, int n_grids, int total_tri, float coef, double *acc, int num_sms,
+                     cudaStream_t s);
+constexpr int kTmaMapsBytes = 1024;  // 8 tensor maps of 128 bytes
+// Encode the staged kernel's 8 tensor maps over a field of (cap + 1) 8^3
+// leaves into host memory (kTmaMapsBytes, 64-byte aligned).  False if the
+// driver's encoder is unavailable or refuses.
+bool tma_encode_maps(const float *field, long long cap, void *out);
 
 // ---- active-voxel count of the listed leaves into ctrl->n_active ----
 void launch_count_active(const DevGrid &g, cudaStream_t s, const LaunchCfg &lc);

@@ -200,7 +200,7 @@ int sg_server_create(const sg_server_desc *desc, void *cuda_stream, sg_server **
 int sg_server_submit(sg_server *s, const sg_job_desc *job, int64_t *job_id)
 {
     if (!s || !job || job->res <= 0 || job->res % 8 || job->res > 4096 || job->steps < 1 || job->seed < 0 ||
-        job->seed >= (1LL << 24))
+        job->seed >= (1LL << 24) || job->out_cap < 0)
         return SG_ERR_INVALID;
     Job *j = new (std::nothrow) Job();
     if (!j) return SG_ERR_OOM;
@@ -273,8 +273,19 @@ int sg_server_tick(sg_server *s)
         sg_swap(j->grid, 0, 2);
         j->sum = s->host_acc[i];
         s->stats.voxel_steps += (double)j->n_active;
-        if (j->steps_done >= j->desc.steps) retire(s, j, SG_JOB_DONE);
-        else still.push_back(j);
+        if (j->steps_done >= j->desc.steps) {
+            // the result: field index 0 names the latest x after the swap
+            int state = SG_JOB_DONE;
+            if (j->desc.out_values) {
+                int64_t na = 0;
+                if (j->n_active > j->desc.out_cap ||
+                    sg_read_field_active(j->grid, 0, j->desc.out_cap, &na, j->desc.out_values) != SG_OK)
+                    state = SG_JOB_FAILED;
+            }
+            retire(s, j, state);
+        } else {
+            still.push_back(j);
+        }
     }
     s->resident.swap(still);
     return SG_OK;

@@ -244,7 +244,7 @@ namespace {
 // completing on `bar`.  d0 / d1: desc[u][lane], desc[u][lane + 32].  Called
 // by the whole warp.
 __device__ __forceinline__ void issue_half(int half, int kind, int d0, int d1, uint32_t buf, uint32_t bar,
-                                           const TmaMaps &maps, const uint32_t *rm_src)
+                                           const CUtensorMap *maps, const uint32_t *rm_src)
 {
     const int lane = lane_id();
     const int nbox = kind_nseg(kind) * 6;
@@ -267,7 +267,7 @@ __device__ __forceinline__ void issue_half(int half, int kind, int d0, int d1, u
             const int j0 = lo ? 6 : 0;
             const int k0 = dk1 == 0 ? 4 : 0;
             const uint32_t dst = buf + seg_off(kind, seg) + box_off(full, half, b);
-            tma_box4(dst, &maps.m[mi], k0, j0, i0, slot, bar);
+            tma_box4(dst, maps + mi, k0, j0, i0, slot, bar);
         }
     }
     if (half == 0 && lane == 0) bulk_copy(buf + kHalfBytes, rm_src, kRmaskBytes, bar);
@@ -297,13 +297,82 @@ __device__ __forceinline__ void srow(const uint8_t *segA, const uint8_t *segB, b
 
 }  // namespace
 
-template <bool SUM>
-__global__ void __launch_bounds__(kTmaWarps * 32, 1) k_sweep_tma(DevGrid g, const __grid_constant__ TmaMaps maps,
-                                                                  int src, int dst, float coef, int sum_slot)
+// One warp task as the kernel body sees it: its descriptors, the tensor maps
+// of its source field, its output field, its grid's bucket counts (for the
+// lane layout) and control block (for errors), and where its sum goes.
+struct TmaRef {
+    const int32_t *desc;      // the task's 64 descriptor words
+    const uint32_t *trm;      // the task's 120 region-mask words
+    const CUtensorMap *maps;  // 8 box shapes over the source field
+    float *y;
+    Ctrl *ctrl;
+    int c1, c2, c3;           // bucket counts of the task's grid
+    int t;                    // task index within its grid
+    int gi;                   // grid index (0 for one grid)
+};
+
+// The tasks of one grid.
+struct OneGridTasks {
+    DevGrid g;
+    const CUtensorMap *maps;
+    float *y;
+    int c1, c2, c3, tasks;
+    __device__ __forceinline__ int total() const { return tasks; }
+    __device__ __forceinline__ TmaRef at(int T) const
+    {
+        TmaRef r;
+        r.desc = g.tma_desc + (long long)T * 64;
+        r.trm = g.tma_rmask + (long long)T * 120;
+        r.maps = maps;
+        r.y = y;
+        r.ctrl = g.ctrl;
+        r.c1 = c1; r.c2 = c2; r.c3 = c3;
+        r.t = T;
+        r.gi = 0;
+        return r;
+    }
+};
+
+// The concatenated tasks of a batch of grids; s_off (shared memory) holds
+// each grid's first task index and the total.
+struct BatchTasks {
+    const BatchGrid *items;
+    const int *s_off;
+    int n_grids, total_tasks;
+    __device__ __forceinline__ int total() const { return total_tasks; }
+    __device__ __forceinline__ TmaRef at(int T) const
+    {
+        int lo = 0, hi = n_grids - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_off[mid] <= T) lo = mid;
+            else hi = mid - 1;
+        }
+        const BatchGrid &it = items[lo];
+        const int t = T - s_off[lo];
+        TmaRef r;
+        r.desc = it.g.tma_desc + (long long)t * 64;
+        r.trm = it.g.tma_rmask + (long long)t * 120;
+        r.maps = reinterpret_cast<const CUtensorMap *>(it.tma_maps);
+        r.y = it.y;
+        r.ctrl = it.g.ctrl;
+        r.c1 = it.c1; r.c2 = it.c2; r.c3 = it.c3;
+        r.t = t;
+        r.gi = lo;
+        return r;
+    }
+};
+
+// The per-warp task loop of the staged kernels: warp w of CTA c takes tasks
+// c * kTmaWarps + w + k * W (W warps in the launch), each staged in two
+// halves as described at the top of the file.  Returns this lane's FP64 sum
+// of the outputs it wrote (one grid) or adds each task's warp sum to
+// acc[grid] (batch, acc != null).
+template <bool SUM, class Tasks>
+__device__ __forceinline__ double tma_task_loop(const Tasks &src, float coef, double *acc_batch)
 {
     extern __shared__ uint8_t s_dyn[];
     __shared__ __align__(8) uint64_t s_bar[kTmaWarps][2];
-    __shared__ double s_red[kTmaWarps];
     const int warp = threadIdx.x >> 5, lane = lane_id();
     uint8_t *base = s_dyn + ((128u - (smem_addr(s_dyn) & 127u)) & 127u);
     uint8_t *bufA = base + warp * kWarpBytes;
@@ -317,39 +386,40 @@ __global__ void __launch_bounds__(kTmaWarps * 32, 1) k_sweep_tma(DevGrid g, cons
     }
     __syncwarp();
 
-    const int c3 = g.col_cnt[2], c2 = g.col_cnt[1], c1 = g.col_cnt[0];
-    const int tasks = num_tasks(c3, c2, c1);
+    const int tasks = src.total();
     const int W = gridDim.x * kTmaWarps;
-    float *__restrict__ y = g.field[dst];
     const float c6 = 1.f - 6.f * coef;
-    const int32_t *desc = g.tma_desc;
-    const uint32_t *trm = g.tma_rmask;
     double acc = 0.0;
     bool ok = true;
     uint32_t phase = 0;
     uint32_t issuedA = 0, doneA = 0, issuedB = 0, doneB = 0;  // half copies issued / seen complete
 
-    int t = blockIdx.x * kTmaWarps + warp;
+    int T = blockIdx.x * kTmaWarps + warp;
+    TmaRef cur{}, nxt{}, nn{};
     int dc0 = 0, dc1 = 0, dn0 = 0, dn1 = 0, dnn0 = 0, dnn1 = 0;
-    if (t < tasks) {
-        dc0 = __ldg(desc + (long long)t * 64 + lane);
-        dc1 = __ldg(desc + (long long)t * 64 + 32 + lane);
-        if (t + W < tasks) {
-            dn0 = __ldg(desc + (long long)(t + W) * 64 + lane);
-            dn1 = __ldg(desc + (long long)(t + W) * 64 + 32 + lane);
+    if (T < tasks) {
+        cur = src.at(T);
+        dc0 = __ldg(cur.desc + lane);
+        dc1 = __ldg(cur.desc + 32 + lane);
+        if (T + W < tasks) {
+            nxt = src.at(T + W);
+            dn0 = __ldg(nxt.desc + lane);
+            dn1 = __ldg(nxt.desc + 32 + lane);
         }
-        if (t + 2 * W < tasks) {
-            dnn0 = __ldg(desc + (long long)(t + 2 * W) * 64 + lane);
-            dnn1 = __ldg(desc + (long long)(t + 2 * W) * 64 + 32 + lane);
+        if (T + 2 * W < tasks) {
+            nn = src.at(T + 2 * W);
+            dnn0 = __ldg(nn.desc + lane);
+            dnn1 = __ldg(nn.desc + 32 + lane);
         }
         const int kind = __shfl_sync(kFull, dc1, 31);
-        issue_half(0, kind, dc0, dc1, sA, barA, maps, trm + (long long)t * 120);
-        issue_half(1, kind, dc0, dc1, sB, barB, maps, nullptr);
+        issue_half(0, kind, dc0, dc1, sA, barA, cur.maps, cur.trm);
+        issue_half(1, kind, dc0, dc1, sB, barB, cur.maps, nullptr);
         issuedA = issuedB = 1;
     }
-    for (; t < tasks; t += W) {
-        const int tn = t + W;
+    for (; T < tasks; T += W) {
+        const int Tn = T + W;
         const int kind = __shfl_sync(kFull, dc1, 31);
+        const int c1 = cur.c1, c2 = cur.c2, c3 = cur.c3, t = cur.t;
         // this lane's piece, row and output leaf (the lane layout of k_sweep_jruns)
         int jj, G, sb;
         bool valid, inA;
@@ -383,14 +453,15 @@ __global__ void __launch_bounds__(kTmaWarps * 32, 1) k_sweep_tma(DevGrid g, cons
         const int so = seg_off(kind, seg);
         const uint8_t *segA = bufA + so, *segB = bufB + so;
         const int r16 = row * 16, r32 = row * 32;
+        float *__restrict__ y = cur.y;
         float part = 0.f;
 
         if (mbar_wait(barA, phase)) {
             ++doneA;
         } else {
             ok = false;
-            raise_error(g, kErrTimeout);
-            g.ctrl->timeout_site = 4;
+            atomicOr(&cur.ctrl->err, kErrTimeout);
+            cur.ctrl->timeout_site = 4;
         }
         uint4 rm = make_uint4(0u, 0u, 0u, 0u);
         if (tlane) rm = *reinterpret_cast<const uint4 *>(bufA + kHalfBytes + f * 160 + tj * 16);
@@ -457,16 +528,16 @@ __global__ void __launch_bounds__(kTmaWarps * 32, 1) k_sweep_tma(DevGrid g, cons
         __syncwarp();
         fence_proxy_async();
         const int kn = __shfl_sync(kFull, dn1, 31);
-        if (ok && tn < tasks) {
-            issue_half(0, kn, dn0, dn1, sA, barA, maps, trm + (long long)tn * 120);
+        if (ok && Tn < tasks) {
+            issue_half(0, kn, dn0, dn1, sA, barA, nxt.maps, nxt.trm);
             ++issuedA;
         }
         if (mbar_wait(barB, phase)) {
             ++doneB;
         } else {
             ok = false;
-            raise_error(g, kErrTimeout);
-            g.ctrl->timeout_site = 4;
+            atomicOr(&cur.ctrl->err, kErrTimeout);
+            cur.ctrl->timeout_site = 4;
         }
         SG_TMA_STEP(4)
         SG_TMA_STEP(5)
@@ -477,17 +548,25 @@ __global__ void __launch_bounds__(kTmaWarps * 32, 1) k_sweep_tma(DevGrid g, cons
 #undef SG_TMA_STEP
         __syncwarp();
         fence_proxy_async();
-        if (ok && tn < tasks) {
-            issue_half(1, kn, dn0, dn1, sB, barB, maps, nullptr);
+        if (ok && Tn < tasks) {
+            issue_half(1, kn, dn0, dn1, sB, barB, nxt.maps, nullptr);
             ++issuedB;
         }
-        acc += (double)part;
+        if (acc_batch) {
+            const double w = warp_sum((double)part);
+            if (lane == 0) atomicAdd(&acc_batch[cur.gi], w);
+        } else {
+            acc += (double)part;
+        }
         phase ^= 1u;
+        cur = nxt;
         dc0 = dn0; dc1 = dn1;
+        nxt = nn;
         dn0 = dnn0; dn1 = dnn1;
-        if (tn + 2 * W < tasks) {
-            dnn0 = __ldg(desc + (long long)(tn + 2 * W) * 64 + lane);
-            dnn1 = __ldg(desc + (long long)(tn + 2 * W) * 64 + 32 + lane);
+        if (Tn + 2 * W < tasks) {
+            nn = src.at(Tn + 2 * W);
+            dnn0 = __ldg(nn.desc + lane);
+            dnn1 = __ldg(nn.desc + 32 + lane);
         }
         if (!ok) break;
     }
@@ -496,9 +575,27 @@ __global__ void __launch_bounds__(kTmaWarps * 32, 1) k_sweep_tma(DevGrid g, cons
         if (issuedA > doneA) (void)mbar_wait(barA, doneA & 1u);
         if (issuedB > doneB) (void)mbar_wait(barB, doneB & 1u);
     }
+    return acc;
+}
+
+template <bool SUM>
+__global__ void __launch_bounds__(kTmaWarps * 32, 1) k_sweep_tma(DevGrid g, const __grid_constant__ TmaMaps maps,
+                                                                  int src, int dst, float coef, int sum_slot)
+{
+    __shared__ double s_red[kTmaWarps];
+    OneGridTasks tk;
+    tk.g = g;
+    tk.maps = maps.m;
+    tk.y = g.field[dst];
+    tk.c3 = g.col_cnt[2];
+    tk.c2 = g.col_cnt[1];
+    tk.c1 = g.col_cnt[0];
+    tk.tasks = num_tasks(tk.c3, tk.c2, tk.c1);
+    (void)src;
+    double acc = tma_task_loop<SUM>(tk, coef, nullptr);
     if (SUM) {
         acc = warp_sum(acc);
-        if (lane == 0) s_red[warp] = acc;
+        if (lane_id() == 0) s_red[threadIdx.x >> 5] = acc;
         __syncthreads();
         double tot = 0.0;
         if (threadIdx.x == 0)
@@ -507,10 +604,28 @@ __global__ void __launch_bounds__(kTmaWarps * 32, 1) k_sweep_tma(DevGrid g, cons
     }
 }
 
+// Batched form: every grid's fused step in one launch over the concatenated
+// task lists, each task's warp sum added to acc[grid] (zeroed by the caller).
+__global__ void __launch_bounds__(kTmaWarps * 32, 1) k_batch_tma(const BatchGrid *__restrict__ items, int n_grids,
+                                                                  int total_tasks, float coef, double *acc)
+{
+    __shared__ int s_off[kMaxBatch + 1];
+    for (int i = threadIdx.x; i <= n_grids; i += blockDim.x) s_off[i] = (i < n_grids) ? items[i].tri0 : total_tasks;
+    __syncthreads();
+    BatchTasks tk;
+    tk.items = items;
+    tk.s_off = s_off;
+    tk.n_grids = n_grids;
+    tk.total_tasks = total_tasks;
+    (void)tma_task_loop<true>(tk, coef, acc);
+}
+
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
 namespace {
+
+int sweep_tma_ctas(int num_sms) { return num_sms; }
 
 using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                    const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
@@ -552,12 +667,30 @@ bool make_maps(const float *base, long long cap, TmaMaps &out)
 
 }  // namespace
 
+bool tma_encode_maps(const float *field, long long cap, void *out)
+{
+    static_assert(sizeof(TmaMaps) == kTmaMapsBytes, "tensor map block size");
+    return make_maps(field, cap, *reinterpret_cast<TmaMaps *>(out));
+}
+
+int launch_batch_tma(const BatchGrid *items, int n_grids, int total_tri, float coef, double *acc, int num_sms,
+                     cudaStream_t s)
+{
+    static std::atomic<int> attr_set{0};
+    if (!attr_set.load(std::memory_order_acquire)) {
+        if (cudaFuncSetAttribute(k_batch_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, kTmaSmem) != cudaSuccess)
+            return 1;
+        attr_set.store(1, std::memory_order_release);
+    }
+    k_batch_tma<<<sweep_tma_ctas(num_sms), kTmaWarps * 32, kTmaSmem, s>>>(items, n_grids, total_tri, coef, acc);
+    return 0;
+}
+
 void launch_tma_tasks(const DevGrid &g, cudaStream_t s, const LaunchCfg &lc)
 {
     k_tma_tasks<<<lc.num_sms * 4, 256, 0, s>>>(g);
 }
 
-int sweep_tma_ctas(int num_sms) { return num_sms; }
 
 int launch_sweep_tma(const DevGrid &g, cudaStream_t s, int src, int dst, float coef, int sum_slot, const LaunchCfg &lc)
 {

@@ -8,6 +8,8 @@ from __future__ import annotations
 
 import ctypes
 
+import numpy as np
+
 from . import SgError, load_library
 
 SG_JOB_PENDING, SG_JOB_RUNNING, SG_JOB_DONE, SG_JOB_FAILED = 0, 1, 2, 3
@@ -24,7 +26,7 @@ class ServerDesc(ctypes.Structure):
 class JobDesc(ctypes.Structure):
     _fields_ = [("res", ctypes.c_int32), ("lo_strict", ctypes.c_int32), ("lo2", ctypes.c_int64),
                 ("hi2", ctypes.c_int64), ("steps", ctypes.c_int32), ("pad", ctypes.c_int32),
-                ("seed", ctypes.c_int64)]
+                ("seed", ctypes.c_int64), ("out_values", ctypes.c_void_p), ("out_cap", ctypes.c_int64)]
 
 
 class JobStatus(ctypes.Structure):
@@ -74,6 +76,7 @@ class Server:
         dev, st = torch.cuda.current_device(), self.stream
         self.alloc_calls = 0
         self.live = {}  # device address -> bytes, for leak checks
+        self._outs = []  # result buffers borrowed by submitted jobs
 
         def _alloc(nbytes, ctx):
             i = self.alloc_calls
@@ -97,10 +100,18 @@ class Server:
             raise SgError(rc, "sg_server_create failed")
         self.h = h
 
-    def submit(self, spec, steps: int) -> int:
-        """spec: a workload.ShellSpec with 8^3 leaves."""
+    def submit(self, spec, steps: int, out=None) -> int:
+        """spec: a workload.ShellSpec with 8^3 leaves.  out: optional float32
+        numpy array that receives the job's final x at its active voxels
+        (packed, as Grid.read_field_active returns them) when it completes;
+        it must stay alive until then."""
+        ptr, cap = None, 0
+        if out is not None:
+            assert out.dtype == np.float32 and out.flags.c_contiguous
+            ptr, cap = out.ctypes.data, out.size
+            self._outs.append(out)
         j = JobDesc(int(spec.N), int(bool(spec.lo_strict)), int(spec.lo2), int(spec.hi2), int(steps), 0,
-                    int(spec.seed) % (1 << 24))
+                    int(spec.seed) % (1 << 24), ptr, cap)
         jid = ctypes.c_int64()
         rc = self.lib.sg_server_submit(self.h, ctypes.byref(j), ctypes.byref(jid))
         if rc:

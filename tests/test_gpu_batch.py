@@ -69,8 +69,13 @@ def run_alone(g, steps):
     return g.read_sums(1)[0]
 
 
+@pytest.mark.parametrize("staged", [False, True])
 @pytest.mark.parametrize("use_graph", [True, False])
-def test_batch_equals_alone_and_oracle(use_graph):
+def test_batch_equals_alone_and_oracle(use_graph, staged):
+    """Both halo stagings of the batched kernel (register sweep; x regions
+    staged in shared memory by bulk tensor copies), with and without graphs:
+    every grid's field bit-identical to the grid stepped alone, sums within
+    2e-5, the two smallest grids within 2e-5 of the oracle."""
     sg = sgm()
     specs = batched_mix(7, n_grids=6, lo=1e3, hi=3e5)
     steps = 5
@@ -81,6 +86,8 @@ def test_batch_equals_alone_and_oracle(use_graph):
         alone.append(make_grid(s, n))
     bt = sg.Batch(batched, 0, 1, 2, 0.1)
     bt.set(4, use_graph)
+    bt.set_staging(staged)
+    assert bt.config()["staged"] == staged
     for _ in range(steps):
         bt.step()
     bsums = bt.read_sums()
@@ -110,16 +117,57 @@ def test_batch_equals_alone_and_oracle(use_graph):
 
 
 def test_batch_autotune_picks_a_candidate():
+    """The autotuner times the register sweep at 2, 4 and 8 warps per CTA and
+    the staged body, and keeps one of them."""
     sg = sgm()
     specs = batched_mix(11, n_grids=5, lo=1e3, hi=1e5)
     grids = [make_grid(s, leaves_needed(s)) for s in specs]
     bt = sg.Batch(grids, 0, 1, 2, 0.1)
     w = bt.autotune(2)
     assert w in (2, 4, 8)
-    assert bt.info()["warps_per_cta"] == w
+    cfg = bt.config()
+    assert cfg["warps_per_cta"] == w
+    assert cfg["staged"] in (False, True) and (not cfg["staged"] or w == 8)
     bt.step()
     sums = bt.read_sums()
     assert np.all(np.isfinite(sums)) and np.all(sums > 0)
     bt.close()
     for g in grids:
+        g.close()
+
+
+def test_both_stagings_on_the_64_grid_mix():
+    """The 64-grid mix of the batched workload (active sizes log-uniform in
+    1e3..5e6): three steps with each halo staging on separate copies of the
+    grids give bit-identical fields and sums within 2e-5; the three smallest
+    grids also within 2e-5 of the oracle."""
+    sg = sgm()
+    specs = batched_mix(0, n_grids=64, lo=1e3, hi=5e6)
+    steps = 3
+    sets = []
+    for staged in (False, True):
+        grids = [make_grid(s, leaves_needed(s)) for s in specs]
+        bt = sg.Batch(grids, 0, 1, 2, 0.1)
+        bt.set_staging(staged)
+        for _ in range(steps):
+            bt.step()
+        sets.append((grids, bt.read_sums()))
+        bt.close()
+    (ga, sa), (gb, sb) = sets
+    np.testing.assert_allclose(sb, sa, rtol=TOL)
+    for a, b in zip(ga, gb):
+        np.testing.assert_array_equal(b.read_field(0), a.read_field(0))
+    for i in np.argsort([g.num_leaves() for g in ga])[:3]:
+        s = specs[i]
+        og = oracle.Grid(s.N, s.L, 3)
+        og.activate_shell(s.lo2, s.hi2, s.lo_strict)
+        ob, _ = og.structure()
+        og.write_field(0, leaf_values(s.seed % (1 << 24), s.N, s.L, ob))
+        cur, y = 0, 2
+        for _ in range(steps):
+            og.diffuse7(cur, 1, 0.1)
+            og.box27(1, y)
+            cur, y = y, cur
+        assert rel_linf(gb[i].read_field(0), og.read_field(cur)) <= TOL
+    for g in ga + gb:
         g.close()

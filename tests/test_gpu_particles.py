@@ -317,3 +317,45 @@ def test_particles_all_outside_activate_nothing():
     np.testing.assert_array_equal(gm, om)
     assert gb.size == 0
     g.close()
+
+
+def test_particle_50_steps_full_size():
+    """The particle workload at its stated length: 50 steps (deactivate, P2G,
+    grid update, G2P, dt = 1e-4) on 2M particles, run independently on both
+    sides.  The node set is compared with the union of the 27-node stencils of
+    the GPU's own positions at the first, a middle and the last step; the
+    particle state with the oracle's at the end: velocities within 1e-4 of
+    their scale (the P2G tolerance; each step's G2P interpolates grid
+    velocities that agree to that bound, and the B-spline weights are
+    continuous, so a base node decided differently near a cell face moves
+    the result continuously, not by a jump), positions within 1e-5 (50
+    steps of dt * v with v ~ 0.1-1)."""
+    import torch
+    import paper_2012_08141_gb300 as sg
+    spec = spheres_particles(seed=1)
+    g = sg.Grid(spec.N, 2, 4, max_leaves=262144)
+    og = oracle.Grid(spec.N, spec.L, 4)
+    x = torch.from_numpy(spec.x).cuda()
+    v = torch.from_numpy(spec.v).cuda()
+    ox, ov = spec.x.copy(), spec.v.copy()
+    for step in range(50):
+        check = step in (0, 24, 49)
+        if check:
+            g.sync()  # the queued steps run before the positions are read on the host
+            xs = x.cpu().numpy().copy()
+        g.deactivate_all()
+        g.p2g(x, v, spec.pmass, 0, 1)
+        g.grid_update(0, 1, spec.dt, spec.gravity, spec.bound)
+        if check:
+            g.list_gen()
+            gb, _ = g.read_structure()
+            np.testing.assert_array_equal(gb, stencil_union_leaves(xs, spec.N, spec.L))
+        g.g2p(x, v, spec.dt, 1)
+        og.deactivate_all()
+        og.p2g(ox, ov, spec.pmass, 0, 1)
+        og.grid_update(0, 1, spec.dt, spec.gravity, spec.bound)
+        og.g2p(ox, ov, spec.dt, 1)
+    g.sync()
+    assert rel_linf(v.cpu().numpy(), ov) <= TOL
+    assert np.max(np.abs(x.cpu().numpy().astype(np.float64) - ox)) <= 1e-5
+    g.close()

@@ -4,10 +4,12 @@ Such callers (a process whose device memory belongs to another allocator, or
 a time-critical loop where cudaMalloc/cudaFree would synchronize the device)
 get the active-list compaction without any allocation by the library; its
 scratch is a static device array.  These tests call the entry point through
-the C ABI and check its list against the one the regular grid API produces
-(sg_list_gen + sg_read_structure) for the same structure, on two calls in a
-row, so that the second call also shows the shared scratch is cleared.  The
-file is named to be collected last.
+the C ABI and check its list against the definition computed on the host
+(np.flatnonzero(root >= 0) and the values at those cells), on random pointer
+arrays from one look-back tile up to the largest size the scratch allows, on
+two calls in a row, so that the second call also shows the shared scratch is
+cleared.  One case also compares with the regular grid API's list for a shell.
+The file is named to be collected last.
 """
 import ctypes
 
@@ -52,6 +54,38 @@ def noalloc_list(torch, lib, root_np, cap):
     return slot.cpu().numpy(), lb.cpu().numpy(), int(cnt.item())
 
 
+def check_twice(torch, lib, root):
+    want_b = np.flatnonzero(root >= 0)
+    for _ in range(2):                                  # the second call reuses the scratch
+        got_slot, got_b, n = noalloc_list(torch, lib, root, len(want_b))
+        assert n == len(want_b)
+        np.testing.assert_array_equal(got_b[:n], want_b)
+        np.testing.assert_array_equal(got_slot[:n], root[want_b])
+
+
+@pytest.mark.parametrize("n_cells, density", [(1024, 0.5), (32768, 0.2), (1500 * 1024, 0.01),
+                                              (4194304, 0.03), (4194304 - 1000, 0.6)])
+def test_noalloc_list_is_the_active_cells_in_order(env, n_cells, density):
+    """Random pointer arrays (one tile; 32 tiles; 1,500 tiles, so each tile's
+    look-back walks past many predecessors; the full 4,194,304 cells (4,096
+    tiles); a ragged last tile): the list is exactly the cells with a value
+    >= 0, in ascending order, with their values."""
+    torch, sg, lib = env
+    rng = np.random.default_rng(n_cells)
+    root = np.full(n_cells, -1, dtype=np.int32)
+    act = rng.random(n_cells) < density
+    root[act] = rng.integers(0, 2 ** 31 - 1, size=int(act.sum()), dtype=np.int32)
+    root[0] = 5                                          # first and last cells active
+    root[-1] = 6
+    check_twice(torch, lib, root)
+
+
+def test_noalloc_all_inactive_and_all_active(env):
+    torch, sg, lib = env
+    check_twice(torch, lib, np.full(70000, -1, dtype=np.int32))
+    check_twice(torch, lib, np.arange(70000, dtype=np.int32))
+
+
 def test_noalloc_list_matches_regular_list_two_calls(env):
     torch, sg, lib = env
     rng = np.random.default_rng(0)
@@ -73,6 +107,8 @@ def test_noalloc_list_matches_regular_list_two_calls(env):
 
 
 def test_noalloc_count_beyond_capacity_and_limits(env):
+    """A list longer than cap: the first cap entries and the full count; a
+    size beyond SG_NOALLOC_MAX_CELLS is rejected before any device work."""
     torch, sg, lib = env
     root = np.full(5000, -1, dtype=np.int32)
     root[[3, 17, 1024, 4999]] = [9, 8, 7, 6]
