@@ -47,7 +47,7 @@ class SgStats(ctypes.Structure):
 class SgCheckReport(ctypes.Structure):
     _fields_ = [("root_bad", ctypes.c_int64), ("slot_shared", ctypes.c_int64), ("list_bad", ctypes.c_int64),
                 ("nbr_bad", ctypes.c_int64), ("zero_leaf_bad", ctypes.c_int64), ("inactive_nonzero", ctypes.c_int64),
-                ("leaves", ctypes.c_int64)]
+                ("leaves", ctypes.c_int64), ("ctrl_bad", ctypes.c_int64)]
 
 
 class SgError(RuntimeError):

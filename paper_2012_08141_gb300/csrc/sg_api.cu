@@ -912,6 +912,9 @@ int run_checks(sg_grid *g, sg_check_report *r, bool with_list)
     if ((rc = cuda_check(cudaMemcpyAsync(c, g->chk_cnt, sizeof c, cudaMemcpyDeviceToHost, s), "read check counters")) ||
         (rc = cuda_check(cudaStreamSynchronize(s), "stream synchronize")))
         return rc;
+    // the counters that each launch's last CTA resets must be zero between launches
+    // (host_ctrl was read by the sync before the checks)
+    r->ctrl_bad = (int64_t)(g->host_ctrl->red_ticket != 0u) + (int64_t)(g->host_ctrl->rr_done != 0u);
     r->root_bad = (int64_t)c[kChkRoot];
     r->slot_shared = (int64_t)c[kChkShared];
     r->leaves = (int64_t)c[kChkLeaves];
@@ -946,12 +949,13 @@ int do_sync(sg_grid *g)
         sg_check_report r;
         const bool with_list = g->list_ver == g->mask_ver;
         if ((rc = run_checks(g, &r, with_list))) return rc;
-        if (r.root_bad | r.slot_shared | r.list_bad | r.nbr_bad | r.zero_leaf_bad | r.inactive_nonzero)
+        if (r.root_bad | r.slot_shared | r.list_bad | r.nbr_bad | r.zero_leaf_bad | r.inactive_nonzero | r.ctrl_bad)
             g->latched = fail(SG_ERR_CHECK,
                               "invariant check: root %lld, shared slots %lld, list %lld, neighbours %lld, zero leaf %lld, "
-                              "inactive values %lld",
+                              "inactive values %lld, control counters %lld",
                               (long long)r.root_bad, (long long)r.slot_shared, (long long)r.list_bad,
-                              (long long)r.nbr_bad, (long long)r.zero_leaf_bad, (long long)r.inactive_nonzero);
+                              (long long)r.nbr_bad, (long long)r.zero_leaf_bad, (long long)r.inactive_nonzero,
+                              (long long)r.ctrl_bad);
     }
     if (g->list_ver == g->mask_ver) g->known_leaves = g->host_ctrl->list_n;
     const int out = g->latched;

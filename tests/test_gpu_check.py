@@ -9,7 +9,7 @@ from workload import band_bounds, leaf_values, tiny_shell
 
 pytestmark = pytest.mark.gpu
 
-CLEAN = dict(root_bad=0, slot_shared=0, list_bad=0, nbr_bad=0, zero_leaf_bad=0, inactive_nonzero=0)
+CLEAN = dict(root_bad=0, slot_shared=0, list_bad=0, nbr_bad=0, zero_leaf_bad=0, inactive_nonzero=0, ctrl_bad=0)
 
 
 @pytest.fixture(scope="module", autouse=True)
