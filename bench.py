@@ -25,7 +25,8 @@ it.  Further legs (skipped with --only fused or on more than one rank):
   ablation  the band step with each of the four passes switched off in turn;
   serving   Poisson arrivals of band jobs (1e4..1e7 voxels, 10..200 steps)
             into the continuous-batching server: p50/p99 job latency;
-  band1024  the 1024^3 band |dist - 400| < 8, far larger than L2.
+  band1024  the 1024^3 band |dist - 400| < 8, far larger than L2;
+  restructure the 1024^3 band with its structure changed before every step.
 
 Timing: W untimed warm-up steps, then K timed steps, each bracketed by CUDA
 events on the launching stream; before every timed step of the band
@@ -313,6 +314,38 @@ def bench_tiny(torch, sg, steps, warmup, flush_buf, stream):
         g.close()
     out["unit"] = "voxel-steps/s"
     return out
+
+
+def bench_restructure(torch, sg, steps, warmup, flush_buf, stream):
+    """The 1024^3 band with its structure changed before every fused step:
+    deactivate all, activate one of two bands (radius 400 or 401, h = 8) in
+    turn, so every step regenerates the list and rebuilds the region masks and
+    run records before its fused step.  Times the whole step."""
+    specs = [ShellSpec(1024, 8, int(4 * (r - 8) ** 2), int(4 * (r + 8) ** 2), True, 5, f"band r={r} h=8")
+             for r in (400, 401)]
+    n = max(leaves_of(sg, s) for s in specs)
+    g = sg.Grid(1024, 3, 3, max_leaves=n, max_sums=1, scratch_mask=0b010)
+    k = [0]
+
+    def step():
+        s = specs[k[0] & 1]
+        k[0] += 1
+        g.deactivate_all()
+        g.activate_shell(s.lo2, s.hi2, s.lo_strict)
+        g.list_gen()
+        g.clear(1)
+        g.diffuse7(0, 1, 0.1)
+        g.box27(1, 2)
+        g.swap(0, 2)
+        g.reduce_sum(0, 0)
+        g.flush()
+
+    ms, launches = time_steps(torch, step, steps, warmup, flush_buf, stream, lambda: g.stats()["launches"])
+    g.close()
+    return {"workload": "1024^3 band, structure changed every step (deactivate, activate r = 400 / 401, list, "
+                        "region masks and run records, fused step)", "leaves": n,
+            "ms_per_step": sum(ms) / len(ms), "launches_per_step": launches / steps,
+            "l2": "flushed before every timed step (512 MB write)"}
 
 
 def bench_ablation(torch, sg, x_host, steps, warmup, flush_buf, stream):
@@ -772,6 +805,7 @@ def run_ours(args):
         k = max(5, min(args.steps, 20))
         for name, fn in (("tiny", lambda: bench_tiny(torch, sg, 20, 3, flush_buf, stream)),
                          ("band1024", lambda: bench_band1024(torch, sg, k, 3, flush_buf, stream, args.variant)),
+                         ("restructure", lambda: bench_restructure(torch, sg, k, 3, flush_buf, stream)),
                          ("batched", lambda: bench_batched(torch, sg, k, 3, flush_buf, stream)),
                          ("particles", lambda: bench_particles(torch, sg, k, 3, flush_buf, stream)),
                          ("mpm_apic", lambda: bench_mpm_apic(torch, sg, k, 3, flush_buf, stream)),
@@ -912,7 +946,7 @@ def main():
                          "4 j-runs staged in shared memory by bulk tensor copies)")
     ap.add_argument("--serving-duration", type=float, default=2.0,
                     help="seconds of Poisson arrivals per rate in the serving leg")
-    ap.add_argument("--only", choices=["all", "fused", "tiny", "band1024", "batched", "particles", "mpm_apic", "multigrid",
+    ap.add_argument("--only", choices=["all", "fused", "tiny", "band1024", "restructure", "batched", "particles", "mpm_apic", "multigrid",
                                        "micro", "advection", "ablation", "serving"],
                     default="all",
                     help="fused: only the fused headline step; a leg name: the headline step and that leg "

@@ -648,9 +648,9 @@ typedef struct sg_check_report {
                                  (fields not marked scratch) */
     int64_t leaves;           /* allocated leaves found in the root */
     int64_t ctrl_bad;         /* control-block counters that the last CTA of a kernel resets
-                                 (reduction ticket, run-record ticket) found nonzero between
-                                 launches: a launch that stopped early would leave them so, and
-                                 the next launch would pick the wrong last CTA */
+                                 (the reduction ticket) found nonzero between launches: a
+                                 launch that stopped early would leave them so, and the next
+                                 launch would pick the wrong last CTA */
 } sg_check_report;
 
 /* Implicit sync (with a current list), then run every check and fill *out.

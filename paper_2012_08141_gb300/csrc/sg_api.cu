@@ -94,6 +94,7 @@ struct sg_grid {
     unsigned long long colgrp_ver = 0; // list version the run records were built from (0 = never)
     int colgrp_axis = kGroupNone;      // axis they group leaves along
     unsigned long long tma_ver = 0;    // list version the TMA task descriptors were built from (0 = never)
+    unsigned long long rr_calls = 0;   // region-mask launches (tags their look-back words)
     long long tma_entries = 0;         // warp tasks the TMA descriptor arrays hold
     int max_fuse = kMaxEwOps;          // element-wise ops per fused launch
     int flush_period = 0;              // flush once the queue holds this many ops (0: on sync / sg_flush only)
@@ -334,7 +335,7 @@ int run_struct_for_group(sg_grid *g, size_t &i)
                          : ((v == kVariantSweepJRuns || v == kVariantSweepTma) ? kGroupJ : kGroupNone);
         const bool need_runs = axis != kGroupNone && (g->colgrp_ver != g->list_ver || g->colgrp_axis != axis);
         if ((sweep && g->rmask_ver != g->list_ver) || need_runs) {
-            if (!g->dry) launch_region_masks(g->dev, g->stream, g->lc, need_runs ? axis : kGroupNone);
+            if (!g->dry) launch_region_masks(g->dev, g->stream, g->lc, need_runs ? axis : kGroupNone, ++g->rr_calls);
             if ((rc = after_launch(g, "region masks"))) return rc;
             g->rmask_ver = g->list_ver;
             if (need_runs) {
@@ -914,7 +915,7 @@ int run_checks(sg_grid *g, sg_check_report *r, bool with_list)
         return rc;
     // the counters that each launch's last CTA resets must be zero between launches
     // (host_ctrl was read by the sync before the checks)
-    r->ctrl_bad = (int64_t)(g->host_ctrl->red_ticket != 0u) + (int64_t)(g->host_ctrl->rr_done != 0u);
+    r->ctrl_bad = (int64_t)(g->host_ctrl->red_ticket != 0u);
     r->root_bad = (int64_t)c[kChkRoot];
     r->slot_shared = (int64_t)c[kChkShared];
     r->leaves = (int64_t)c[kChkLeaves];
@@ -1116,8 +1117,7 @@ int sg_create(const sg_desc *desc, void *cuda_stream, sg_grid **out)
         {(void **)&d.ent_of_slot, sizeof(int32_t) * d.cap},
         {(void **)&d.col_grp, sizeof(int32_t) * 9 * d.cap},
         {(void **)&d.col_cnt, sizeof(int32_t) * 4},
-        {(void **)&d.run_stage, sizeof(int4) * d.cap},
-        {(void **)&d.run_chunk, sizeof(int32_t) * 3 * (d.cap / 32 + 1)},
+        {(void **)&d.rr_status, sizeof(unsigned long long) * 3 * (d.cap / 256 + 1)},
         {(void **)&d.rmask, (L == 8 ? sizeof(uint32_t) * 40 : size_t(4)) * d.cap},
         {(void **)&d.need, (size_t)nr},
         {(void **)&d.tile_status, sizeof(unsigned long long) * g->num_tiles},
@@ -1152,6 +1152,9 @@ int sg_create(const sg_desc *desc, void *cuda_stream, sg_grid **out)
     rc = cuda_check(cudaMemsetAsync(d.root, 0xff, sizeof(int32_t) * nr, s), "init root");
     if (!rc) rc = cuda_check(cudaMemsetAsync(d.need, 0, (size_t)nr, s), "init need");
     if (!rc) rc = cuda_check(cudaMemsetAsync(d.tile_status, 0, sizeof(unsigned long long) * g->num_tiles, s), "init status");
+    if (!rc)
+        rc = cuda_check(cudaMemsetAsync(d.rr_status, 0, sizeof(unsigned long long) * 3 * (d.cap / 256 + 1), s),
+                        "init run-record status");
     if (!rc) rc = cuda_check(cudaMemsetAsync(d.sums, 0, sizeof(double) * std::max(1, desc->max_sums), s), "init sums");
     // the zero leaf (slot cap): never allocated, read in place of null neighbours
     if (!rc) rc = cuda_check(cudaMemsetAsync(d.mask + d.W * d.cap, 0, sizeof(uint32_t) * d.W, s), "init zero leaf");
@@ -1987,7 +1990,7 @@ int grid_prepare_batch(sg_grid *g, int src, int tmp, int dst, BatchGrid out[2], 
     // region masks and the j-run records of the batched kernel
     const bool need_runs = g->colgrp_ver != g->list_ver || g->colgrp_axis != kGroupJ;
     if (!rc && (g->rmask_ver != g->list_ver || need_runs)) {
-        launch_region_masks(g->dev, g->stream, g->lc, need_runs ? kGroupJ : kGroupNone);
+        launch_region_masks(g->dev, g->stream, g->lc, need_runs ? kGroupJ : kGroupNone, ++g->rr_calls);
         rc = after_launch(g, "region masks");
         g->rmask_ver = g->list_ver;
         if (need_runs) {

@@ -49,7 +49,7 @@ struct Ctrl {
     int32_t timeout_site; // which wait gave up (0 none, 1 look-back, 2 test, 3 leaf allocation)
                           // or, with kErrCheck, 100 + the failed check
     int32_t bins_used;    // leaves holding particles in the last binned P2G
-    uint32_t rr_done;     // run-record CTAs finished (reset by the last)
+    uint32_t rr_ticket;   // run-record tiles handed out (zeroed before each region-mask launch)
     int32_t pad[1];
 };
 
@@ -85,8 +85,7 @@ struct DevGrid {
     int32_t *ent_of_slot;
     int32_t *col_grp;   // [3][cap][3]
     int32_t *col_cnt;   // [4]
-    int4 *run_stage;    // [cap]: per list entry, (piece length or 0, entry, next entry, the one after)
-    int32_t *run_chunk; // [3][cap / 32 + 1]: pieces of each length per 32-entry list chunk
+    unsigned long long *rr_status; // [cap / 256 + 1][3]: run-record look-back words, per 256-entry tile and length
     // TMA-staged fused step (allocated at its first use): per j-run warp task,
     // the source slot of each staged box and the kind (64 words), and the
     // region masks of its leaves (120 words); see k_tma_tasks
@@ -144,7 +143,10 @@ void launch_clear_list(const DevGrid &g, cudaStream_t s);
 // The fused sweep's region masks of the current list; with columns also the
 // column records of the column sweep (ent_of_slot is written by the list
 // generation).
-void launch_region_masks(const DevGrid &g, cudaStream_t s, const LaunchCfg &lc, int group_axis);
+// call: a per-grid counter of these launches (tags the look-back words, so
+// stale words of earlier launches are ignored without a reset).
+void launch_region_masks(const DevGrid &g, cudaStream_t s, const LaunchCfg &lc, int group_axis,
+                         unsigned long long call);
 void launch_listgen(const DevGrid &g, cudaStream_t s, int force, unsigned long long call_idx,
                     int num_tiles, int test_wait);
 // Field f of the listed leaves to / from a dense list-order buffer: the

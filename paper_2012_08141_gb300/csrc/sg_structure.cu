@@ -9,111 +9,165 @@
 namespace sg {
 
 // ---------------------------------------------------------------------------
-// Activation from the shell predicate.  One warp per root cell: the warp culls
-// the cell when the leaf's bounding box cannot meet the band, otherwise it
-// builds the leaf's mask words with one ballot per 32 voxels, allocates the
-// leaf if the pointer is null (zero-filling every field) and ORs the words in.
+// Activation from the shell predicate.  Each lane of a warp tests one of up
+// to 32 consecutive root cells' bounding boxes against the band; the warp
+// then takes the cells that can meet it one at a time and builds their mask
+// words with one ballot per 32 voxels; the cells with active voxels and a
+// null pointer get new leaves (zero-filled in every field), and the words are
+// ORed into the leaves.  The predicate is
+// exact in 32-bit integers: |2i + 1 - N| < N <= 4096, so D < 3 * 4096^2 <
+// 2^31, and lo2 / hi2 are clamped to [-1, 2^31 - 1] without changing it.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void axis_range(int i0, int L, int N, long long &mn, long long &mx)
+__device__ __forceinline__ void axis_range(int i0, int L, int N, int &mn, int &mx)
 {
-    long long e0 = 2LL * i0 + 1 - N, e1 = 2LL * (i0 + L - 1) + 1 - N;
-    long long lo;
+    const int e0 = 2 * i0 + 1 - N, e1 = 2 * (i0 + L - 1) + 1 - N;
+    int lo;
     if (e0 > 0) lo = e0;
     else if (e1 < 0) lo = -e1;
     else lo = (e0 & 1) ? 1 : 0;  // the progression e0, e0+2, ... crosses zero
-    long long hi = (-e0 > e1) ? -e0 : e1;
+    const int hi = (-e0 > e1) ? -e0 : e1;
     mn += lo * lo;
     mx += hi * hi;
 }
 
-// tube: the predicate ignores the k axis (a cylinder along k through the
-// domain centre) instead of using all three.
-__global__ void __launch_bounds__(256) k_activate_shell(DevGrid g, long long lo2, long long hi2, int strict, int tube)
+__device__ __forceinline__ int clamp_pred(long long v)
 {
-    const int lane = lane_id();
+    return v < -1 ? -1 : (v > 2147483647LL ? 2147483647 : (int)v);
+}
+
+// tube: the predicate ignores the k axis (a cylinder along k through the
+// domain centre) instead of using all three.  cpw: root cells per warp (32 on
+// large domains, where the lanes cull 32 cells at once and the warp's new
+// leaves take their pool slots with one atomic; 1 on small ones, where a warp
+// per cell keeps every cell in flight at once).
+__global__ void __launch_bounds__(256) k_activate_shell(DevGrid g, long long lo2_, long long hi2_, int strict, int tube,
+                                                        int cpw)
+{
+    constexpr int kMaxW = 16;  // mask words of an 8^3 leaf
+    __shared__ uint32_t s_bits[8][32][kMaxW];  // per warp: the mask words of its chunk's cells
+    const int lane = lane_id(), warp = threadIdx.x >> 5;
     const long long nr = (long long)g.R * g.R * g.R;
-    const long long b = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (b >= nr) return;  // warp-uniform
-    const int R = g.R, L = g.L, lg2 = g.lg2, N = g.N;
-    const int bi = (int)(b / ((long long)R * R)), bj = (int)((b / R) % R), bk = (int)(b % R);
-    long long dmin = 0, dmax = 0;
-    axis_range(bi * L, L, N, dmin, dmax);
-    axis_range(bj * L, L, N, dmin, dmax);
-    if (!tube) axis_range(bk * L, L, N, dmin, dmax);
-    const bool lo_possible = strict ? (dmax > lo2) : (dmax >= lo2);
-    if (!lo_possible || dmin >= hi2) return;
-
-    uint32_t bits = 0;
-    for (int w = 0; w < g.W; ++w) {
-        const int l = w * 32 + lane;
-        const int li = l >> (2 * lg2), lj = (l >> lg2) & (L - 1), lk = l & (L - 1);
-        const long long a = 2LL * (bi * L + li) + 1 - N;
-        const long long c = 2LL * (bj * L + lj) + 1 - N;
-        const long long d = 2LL * (bk * L + lk) + 1 - N;
-        const long long D = a * a + c * c + (tube ? 0 : d * d);
-        const bool on = (strict ? (lo2 < D) : (lo2 <= D)) && (D < hi2);
-        const unsigned word = __ballot_sync(kFull, on);
-        if (lane == w) bits = word;
-    }
-    if (!__any_sync(kFull, bits != 0u)) return;
-
-    int slot = 0, fresh = 0;
-    if (lane == 0) {
-        slot = g.root[b];
-        if (slot < 0) {
-            const int s = atomicAdd(&g.ctrl->pool_count, 1);
-            if (s < g.cap) {
-                slot = s;
-                fresh = 1;
+    const int R = g.R, L = g.L, lg2 = g.lg2, N = g.N, W = g.W;
+    const int lo2 = clamp_pred(lo2_), hi2 = clamp_pred(hi2_);
+    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long c0 = ((long long)blockIdx.x * (blockDim.x >> 5) + warp) * cpw; c0 < nr; c0 += warps * cpw) {
+        // lane q < cpw tests cell c0 + q: can its bounding box meet the band?
+        bool cand = false;
+        const long long bq = c0 + lane;
+        if (lane < cpw && bq < nr) {
+            const int bi = (int)(bq / ((long long)R * R)), bj = (int)((bq / R) % R), bk = (int)(bq % R);
+            int dmin = 0, dmax = 0;
+            axis_range(bi * L, L, N, dmin, dmax);
+            axis_range(bj * L, L, N, dmin, dmax);
+            if (!tube) axis_range(bk * L, L, N, dmin, dmax);
+            const bool lo_possible = strict ? (dmax > lo2) : (dmax >= lo2);
+            cand = lo_possible && dmin < hi2;
+        }
+        // the mask words of every candidate, one ballot per 32 voxels
+        bool any_bits = false;  // lane q: cell c0 + q has an active voxel
+        unsigned todo = __ballot_sync(kFull, cand);
+        while (todo) {
+            const int q = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const long long b = c0 + q;
+            const int bi = (int)(b / ((long long)R * R)), bj = (int)((b / R) % R), bk = (int)(b % R);
+            uint32_t bits = 0;
+            for (int w = 0; w < W; ++w) {
+                const int l = w * 32 + lane;
+                const int li = l >> (2 * lg2), lj = (l >> lg2) & (L - 1), lk = l & (L - 1);
+                const int a = 2 * (bi * L + li) + 1 - N;
+                const int c = 2 * (bj * L + lj) + 1 - N;
+                const int d = 2 * (bk * L + lk) + 1 - N;
+                const int D = a * a + c * c + (tube ? 0 : d * d);
+                const bool on = (strict ? (lo2 < D) : (lo2 <= D)) && (D < hi2);
+                const unsigned word = __ballot_sync(kFull, on);
+                if (lane == w) bits = word;
+            }
+            if (lane < W) s_bits[warp][q][lane] = bits;
+            const bool nz = __any_sync(kFull, bits != 0u);
+            if (lane == q) any_bits = nz;
+        }
+        // new leaves for the cells with active voxels and a null pointer: one
+        // pool atomic for the warp, slots by rank
+        int slot = -1;
+        if (any_bits) slot = g.root[c0 + lane];
+        const bool need = any_bits && slot < 0;
+        const unsigned needm = __ballot_sync(kFull, need);
+        int first = 0;
+        if (needm) {
+            if (lane == 0) first = atomicAdd(&g.ctrl->pool_count, __popc(needm));
+            first = __shfl_sync(kFull, first, 0);
+        }
+        bool fresh = false;
+        if (need) {
+            const int sl = first + __popc(needm & lanemask_lt());
+            if (sl < g.cap) {
+                slot = sl;
+                fresh = true;
             } else {
                 raise_error(g, kErrPool);
             }
         }
-    }
-    slot = __shfl_sync(kFull, slot, 0);
-    fresh = __shfl_sync(kFull, fresh, 0);
-    if (slot < 0) return;
-    const int V = L * L * L;
-    if (fresh) {
-        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int f = 0; f < g.F; ++f) {
-            float4 *p = reinterpret_cast<float4 *>(g.field[f] + (long long)slot * V);
-            for (int q = lane; q < V / 4; q += 32) p[q] = z;
-        }
-        if (lane < g.W) g.mask[(long long)slot * g.W + lane] = bits;
         __syncwarp();
-        if (lane == 0) {
-            g.root[b] = slot;
-            mark_dirty(g);
-        }
-    } else {
+        // per cell with active voxels: zero-fill a new leaf and publish it, or
+        // OR the words into the existing leaf
+        unsigned work = __ballot_sync(kFull, any_bits && slot >= 0);
         bool changed = false;
-        if (lane < g.W) {
-            uint32_t *m = &g.mask[(long long)slot * g.W + lane];
-            const uint32_t old = *m, nw = old | bits;
-            if (nw != old) {
-                *m = nw;
+        while (work) {
+            const int q = __ffs(work) - 1;
+            work &= work - 1;
+            const int sq = __shfl_sync(kFull, slot, q);
+            const bool fq = __shfl_sync(kFull, fresh, q);
+            const int V = L * L * L;
+            if (fq) {
+                const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+                for (int f = 0; f < g.F; ++f) {
+                    float4 *p = reinterpret_cast<float4 *>(g.field[f] + (long long)sq * V);
+                    for (int qq = lane; qq < V / 4; qq += 32) p[qq] = z;
+                }
+                if (lane < W) g.mask[(long long)sq * W + lane] = s_bits[warp][q][lane];
+                __syncwarp();
+                if (lane == 0) g.root[c0 + q] = sq;
                 changed = true;
+            } else if (lane < W) {
+                uint32_t *m = &g.mask[(long long)sq * W + lane];
+                const uint32_t old = *m, nw = old | s_bits[warp][q][lane];
+                if (nw != old) {
+                    *m = nw;
+                    changed = true;
+                }
             }
         }
         if (__any_sync(kFull, changed) && lane == 0) mark_dirty(g);
+        __syncwarp();  // s_bits is reused by the next chunk
     }
+}
+
+// Cells per warp and CTAs of 8 warps: 32 cells per warp once the domain has
+// enough of them to fill the GPU that way (then at most 2,432 CTAs, striding
+// over the rest), else a warp per cell and a CTA per 8 cells.
+static void activate_shape(long long nr, int &cpw, int &ctas)
+{
+    constexpr long long kMaxCtas = 2432;
+    cpw = nr >= kMaxCtas * 8 * 32 / 2 ? 32 : 1;
+    const long long want = (nr + 8LL * cpw - 1) / (8LL * cpw);
+    ctas = (int)(cpw == 1 ? (want > 0 ? want : 1) : (want < kMaxCtas ? want : kMaxCtas));
 }
 
 void launch_activate_shell(const DevGrid &g, cudaStream_t s, long long lo2, long long hi2, int strict)
 {
     const long long nr = (long long)g.R * g.R * g.R;
-    const int warps = 8;
-    const long long blocks = (nr + warps - 1) / warps;
-    k_activate_shell<<<(unsigned)blocks, warps * 32, 0, s>>>(g, lo2, hi2, strict, 0);
+    int cpw, ctas;
+    activate_shape(nr, cpw, ctas);
+    k_activate_shell<<<ctas, 256, 0, s>>>(g, lo2, hi2, strict, 0, cpw);
 }
 
 void launch_activate_tube(const DevGrid &g, cudaStream_t s, long long lo2, long long hi2)
 {
     const long long nr = (long long)g.R * g.R * g.R;
-    const int warps = 8;
-    const long long blocks = (nr + warps - 1) / warps;
-    k_activate_shell<<<(unsigned)blocks, warps * 32, 0, s>>>(g, lo2, hi2, 0, 1);
+    int cpw, ctas;
+    activate_shape(nr, cpw, ctas);
+    k_activate_shell<<<ctas, 256, 0, s>>>(g, lo2, hi2, 0, 1, cpw);
 }
 
 // ---------------------------------------------------------------------------
@@ -446,7 +500,7 @@ void launch_listgen(const DevGrid &g, cudaStream_t s, int force, unsigned long l
 // column and k = 10 from the k+1 leaf (local k 0), via the 27-neighbour
 // table (null neighbours are the zero leaf, whose mask is 0).
 // ---------------------------------------------------------------------------
-__global__ void k_region_masks(DevGrid g, int group_axis)
+__global__ void __launch_bounds__(256) k_region_masks(DevGrid g, int group_axis, unsigned long long call)
 {
     const long long n = g.ctrl->list_n;
     const uint8_t *mb = reinterpret_cast<const uint8_t *>(g.mask);
@@ -477,18 +531,27 @@ __global__ void k_region_masks(DevGrid g, int group_axis)
     // cut into pieces of up to three from the run's lowest leaf; each piece's
     // list entries, lowest first, go to the bucket of its length, in list
     // order.  List order keeps the warps that sweep at the same time on
-    // neighbouring leaves, so halo rows are reused through L1 and L2.  In one
-    // launch: every warp classifies 32-entry chunks of the list (the piece
-    // each entry starts, staged per entry) and counts each chunk's pieces by
-    // length; the last CTA to finish scans the chunk counts and writes the
-    // records.  No CTA waits for another.
+    // neighbouring leaves, so halo rows are reused through L1 and L2.  Tiles
+    // of 256 list entries are taken by ticket; in a tile, warp w classifies
+    // entries 32w .. 32w + 31 (the piece each entry starts); the tile's
+    // offset in each bucket comes from a decoupled look-back over the
+    // earlier tiles (three warps, one per length, each waiting only on tiles
+    // whose tickets were handed out earlier, so the waits end; bounded in
+    // time all the same), and every entry's record is written at once.
+    __shared__ int s_tile;
+    __shared__ int s_wcnt[3][8];
+    __shared__ int s_base[3];
     const long long S = group_axis == kGroupI ? (long long)g.R * g.R : (long long)g.R;
-    const long long cap_ch = g.cap / 32 + 1;
-    const int lane = lane_id();
-    const long long stride = (long long)gridDim.x * blockDim.x;  // a multiple of 32: the loop is warp-uniform
-    for (long long e0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) & ~31LL; e0 < n; e0 += stride) {
-        const long long e = e0 + lane;
-        int len = 0;
+    const int lane = lane_id(), warp = threadIdx.x >> 5;
+    const int ntiles = (int)((n + 255) / 256);
+    const unsigned long long tag = (call + 1ull) << 34;
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = (int)atomicAdd(&g.ctrl->rr_ticket, 1u);
+        __syncthreads();
+        const int tile = s_tile;
+        if (tile >= ntiles) break;  // CTA-uniform
+        const long long e = (long long)tile * 256 + threadIdx.x;
+        int len = 0, r1 = -1, r2 = -1;
         if (e < n) {
             const long long b = g.list_b[e];
             const int c = (int)((b / S) % g.R);  // the leaf's root coordinate along the axis
@@ -498,71 +561,79 @@ __global__ void k_region_masks(DevGrid g, int group_axis)
                 len = 1;
                 while (len < 3 && c + len < g.R && g.root[b + len * S] >= 0) ++len;
             }
-            const int r1 = len > 1 ? g.ent_of_slot[g.root[b + S]] : -1;
-            const int r2 = len > 2 ? g.ent_of_slot[g.root[b + 2 * S]] : -1;
-            g.run_stage[e] = make_int4(len, (int)e, r1, r2);
+            r1 = len > 1 ? g.ent_of_slot[g.root[b + S]] : -1;
+            r2 = len > 2 ? g.ent_of_slot[g.root[b + 2 * S]] : -1;
         }
+        unsigned m[3];
+#pragma unroll
         for (int G = 1; G <= 3; ++G) {
-            const unsigned m = __ballot_sync(kFull, len == G);
-            if (lane == 0) g.run_chunk[(G - 1) * cap_ch + e0 / 32] = (int32_t)__popc(m);
+            m[G - 1] = __ballot_sync(kFull, len == G);
+            if (lane == 0) s_wcnt[G - 1][warp] = __popc(m[G - 1]);
         }
-    }
-    __shared__ int s_last;
-    __shared__ int s_w[32];
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) s_last = atomicAdd(&g.ctrl->rr_done, 1u) == gridDim.x - 1;
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    const long long nch = (n + 31) / 32;
-    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    // exclusive scan of each bucket's chunk counts, in place; totals to col_cnt
-    for (int G = 1; G <= 3; ++G) {
-        int32_t *cnt = g.run_chunk + (G - 1) * cap_ch;
-        const long long per = (nch + blockDim.x - 1) / blockDim.x;
-        const long long lo = threadIdx.x * per, hi = lo + per < nch ? lo + per : nch;
-        int local = 0;
-        for (long long q = lo; q < hi; ++q) local += cnt[q];
-        const int incl = warp_incl_scan(local);
-        if (lane == 31) s_w[warp] = incl;
         __syncthreads();
-        int base = 0, total = 0;
-        for (int w = 0; w < nw; ++w) {
-            const int v = s_w[w];
-            base += (w < warp) ? v : 0;
-            total += v;
-        }
-        int run = base + incl - local;
-        for (long long q = lo; q < hi; ++q) {
-            const int v = cnt[q];
-            cnt[q] = run;
-            run += v;
-        }
-        if (threadIdx.x == 0) g.col_cnt[G - 1] = total;
-        __syncthreads();
-    }
-    // the records: a warp per chunk, ranks within the chunk by ballot
-    for (long long c = warp; c < nch; c += nw) {
-        const long long e = c * 32 + lane;
-        const int4 st = e < n ? g.run_stage[e] : make_int4(0, 0, -1, -1);
-        for (int G = 1; G <= 3; ++G) {
-            const unsigned m = __ballot_sync(kFull, st.x == G);
-            if (st.x == G) {
-                const long long j = g.run_chunk[(G - 1) * cap_ch + c] + __popc(m & ((1u << lane) - 1u));
-                int32_t *rec = g.col_grp + ((long long)(G - 1) * g.cap + j) * 3;
-                rec[0] = st.y;
-                rec[1] = st.z;
-                rec[2] = st.w;
+        if (warp < 3) {
+            // bucket warp + 1: the tile's count, published, then its offset
+            const int G1 = warp;
+            int tot = 0;
+            for (int w = 0; w < 8; ++w) tot += s_wcnt[G1][w];
+            unsigned long long *st = g.rr_status + (long long)tile * 3 + G1;
+            if (lane == 0)
+                atomicExch(st, tag | ((tile == 0 ? kFlagIncl : kFlagAgg) << 32) | (unsigned long long)(unsigned)tot);
+            int prefix = 0;
+            if (tile > 0) {
+                int pred = tile - 1;
+                const unsigned long long t_start = global_timer_ns();
+                for (;;) {
+                    const int idx = pred - lane;
+                    unsigned long long w = tag | (kFlagIncl << 32);
+                    if (idx >= 0) {
+                        for (;;) {
+                            w = *(volatile unsigned long long *)(g.rr_status + (long long)idx * 3 + G1);
+                            if ((w >> 34) == (call + 1ull)) break;
+                            if (global_timer_ns() - t_start > kLookbackLimitNs) {
+                                raise_error(g, kErrTimeout);
+                                g.ctrl->timeout_site = 5;
+                                w = tag | (kFlagIncl << 32);
+                                break;
+                            }
+                            __nanosleep(32);
+                        }
+                    }
+                    const unsigned long long flag = (w >> 32) & 3ull;
+                    const int val = (int)(w & 0xffffffffull);
+                    const unsigned im = __ballot_sync(kFull, flag == kFlagIncl);
+                    const int upto = im ? (__ffs(im) - 1) : 31;
+                    prefix += warp_sum(lane <= upto ? val : 0);
+                    if (im) break;
+                    pred -= 32;
+                }
+                if (lane == 0) atomicExch(st, tag | (kFlagIncl << 32) | (unsigned long long)(unsigned)(prefix + tot));
+            }
+            if (lane == 0) {
+                s_base[G1] = prefix;
+                if (tile == ntiles - 1) g.col_cnt[G1] = prefix + tot;
             }
         }
+        __syncthreads();
+        if (len > 0) {
+            int j = s_base[len - 1];
+            for (int w = 0; w < warp; ++w) j += s_wcnt[len - 1][w];
+            j += __popc(m[len - 1] & lanemask_lt());
+            int32_t *rec = g.col_grp + ((long long)(len - 1) * g.cap + j) * 3;
+            rec[0] = (int32_t)e;
+            rec[1] = r1;
+            rec[2] = r2;
+        }
+        __syncthreads();  // s_tile, s_wcnt and s_base are reused by the next tile
     }
-    if (threadIdx.x == 0) g.ctrl->rr_done = 0u;
+    if (n == 0 && blockIdx.x == 0 && threadIdx.x < 3) g.col_cnt[threadIdx.x] = 0;
 }
 
-void launch_region_masks(const DevGrid &g, cudaStream_t s, const LaunchCfg &lc, int group_axis)
+void launch_region_masks(const DevGrid &g, cudaStream_t s, const LaunchCfg &lc, int group_axis,
+                         unsigned long long call)
 {
-    k_region_masks<<<lc.num_sms * 4, 256, 0, s>>>(g, group_axis);
+    if (group_axis != kGroupNone) cudaMemsetAsync(&g.ctrl->rr_ticket, 0, sizeof(uint32_t), s);
+    k_region_masks<<<lc.num_sms * 4, 256, 0, s>>>(g, group_axis, call);
 }
 
 // ---------------------------------------------------------------------------
