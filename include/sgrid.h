@@ -119,6 +119,8 @@ typedef struct sg_stats {
                                 clear and reduction kernels (whole leaves) */
     int64_t bounds_reused;   /* MacCormack corrections (per channel) that read the
                                 clamp bounds their forward advection stored */
+    int64_t velocity_packs;  /* advection runs whose velocity was packed once
+                                for all their launches (one launch each) */
 } sg_stats;
 
 typedef struct sg_grid sg_grid; /* opaque; owned by the library */
@@ -206,7 +208,11 @@ int sg_advect(sg_grid *g, int32_t dst, int32_t src, int32_t v0, float dt);
  * the same velocity and step in the same run, when no op of the run writes q
  * or the velocity, also stores the clamp bounds, and the correction reads them
  * instead of tracing the forward path again (identical results;
- * sg_stats.bounds_reused counts it). */
+ * sg_stats.bounds_reused counts it).  When two or more advections of such a
+ * run share a velocity that no op of the run writes, its three fields are
+ * first packed into one 16-byte value per voxel (one extra launch, counted in
+ * sg_stats.velocity_packs; identical results), so each velocity corner of a
+ * backtrace is one load. */
 int sg_maccormack(sg_grid *g, int32_t dst, int32_t q, int32_t qhat, int32_t qtilde, int32_t v0, float dt);
 
 /* Queue an element-wise struct-for: on every active voxel

@@ -41,7 +41,8 @@ class SgStats(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64), ("listgen_run", ctypes.c_int64), ("listgen_removed", ctypes.c_int64),
                 ("act_launched", ctypes.c_int64), ("act_demoted", ctypes.c_int64), ("ops_enqueued", ctypes.c_int64),
                 ("ops_fused", ctypes.c_int64), ("stores_removed", ctypes.c_int64), ("flushes", ctypes.c_int64),
-                ("bytes_model", ctypes.c_double), ("bounds_reused", ctypes.c_int64)]
+                ("bytes_model", ctypes.c_double), ("bounds_reused", ctypes.c_int64),
+                ("velocity_packs", ctypes.c_int64)]
 
 
 class SgCheckReport(ctypes.Structure):

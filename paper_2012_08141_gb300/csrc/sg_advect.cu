@@ -10,7 +10,13 @@
 // centres; each value is read from its leaf found through the list entry's
 // 27-neighbour table (a null or out-of-domain neighbour is the zero leaf, and
 // a stored value at an inactive voxel is 0, so every read is unconditional),
-// or through the root when the sample lies more than a leaf away.
+// or through the root when the sample lies more than a leaf away.  A warp's 32
+// voxels lie in one leaf (L^3 is a multiple of 32), so lanes 0..26 hold the
+// entry's table and every lookup is a shuffle; element offsets are 32-bit
+// when the fields have fewer than 2^31 elements.
+// With fusion the run's velocity is first packed as one float4 (u, v, w, 0)
+// per value slot, so a velocity corner is one 16-byte load instead of three
+// (the same products summed in the same order: the results are identical).
 // Backtrace: Ralston's RK3, x_back = x - h (2 k1 + 3 k2 + 4 k3) / 9 with
 // k1 = u(x), k2 = u(x - h/2 k1), k3 = u(x - 3h/4 k2).  Correction: q' =
 // q^ + (q - q~) / 2 clamped to the 8 values of q the forward sample uses.
@@ -35,6 +41,7 @@ struct AdvectArgs {
     // correction of the same q, velocity and step instead of tracing again
     float *lo[kMaxAdvectChannels];
     float *hi[kMaxAdvectChannels];
+    const float4 *vel4;               // packed velocity, or null (read the three fields)
 };
 
 // Slot of the leaf holding cell (ci, cj, ck), relative to the list entry's
@@ -55,15 +62,17 @@ __device__ __forceinline__ int leaf_slot(const DevGrid &g, const int32_t *nb, in
 
 // The 8 corners of a sample at p (cell units): their value offsets within a
 // field and trilinear weights.
-template <int L>
+template <int L, typename Off>
 struct Corners {
-    long long off[8];
+    Off off[8];
     float w[8];
 };
 
-template <int L>
-__device__ __forceinline__ void corners(const DevGrid &g, const int32_t *nb, int bi, int bj, int bk, float px,
-                                        float py, float pz, Corners<L> &cr)
+// nbv: lane t < 27 holds entry t of the warp's neighbour table.  Every lane
+// of the warp calls this together (the lookups are shuffles).
+template <int L, typename Off>
+__device__ __forceinline__ void corners(const DevGrid &g, const int32_t *nb, int nbv, int bi, int bj, int bk,
+                                        float px, float py, float pz, Corners<L, Off> &cr)
 {
     constexpr int LG2 = (L == 8) ? 3 : 2;
     const float X = px - 0.5f, Y = py - 0.5f, Z = pz - 0.5f;
@@ -77,31 +86,29 @@ __device__ __forceinline__ void corners(const DevGrid &g, const int32_t *nb, int
     const int li[2] = {i0 & (L - 1), (i0 + 1) & (L - 1)}, lj[2] = {j0 & (L - 1), (j0 + 1) & (L - 1)},
               lk[2] = {k0 & (L - 1), (k0 + 1) & (L - 1)};
     const float wx[2] = {1.f - fx, fx}, wy[2] = {1.f - fy, fy}, wz[2] = {1.f - fz, fz};
+    // within the 27-neighbourhood (the common case): the table entry by
+    // shuffle; lanes whose sample lies further out take the root afterwards
     const bool near = di0 >= -1 && di1 <= 1 && dj0 >= -1 && dj1 <= 1 && dk0 >= -1 && dk1 <= 1;
-    if (near) {  // within the 27-neighbourhood: table lookups only
-        const int ti[2] = {(di0 + 1) * 9, (di1 + 1) * 9}, tj[2] = {(dj0 + 1) * 3, (dj1 + 1) * 3},
-                  tk[2] = {dk0 + 1, dk1 + 1};
+    const int ti[2] = {near ? (di0 + 1) * 9 : 0, near ? (di1 + 1) * 9 : 0},
+              tj[2] = {near ? (dj0 + 1) * 3 : 0, near ? (dj1 + 1) * 3 : 0}, tk[2] = {near ? dk0 + 1 : 0, near ? dk1 + 1 : 0};
+    int slot[8];
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            const int a = c >> 2, b = (c >> 1) & 1, d = c & 1;
-            const int slot = __ldg(nb + ti[a] + tj[b] + tk[d]);
-            cr.off[c] = ((long long)slot << (3 * LG2)) + (((li[a] << LG2) + lj[b]) << LG2) + lk[d];
-            cr.w[c] = wx[a] * wy[b] * wz[d];
-        }
-    } else {
+    for (int c = 0; c < 8; ++c) slot[c] = __shfl_sync(kFull, nbv, ti[c >> 2] + tj[(c >> 1) & 1] + tk[c & 1]);
+    if (!near) {
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            const int a = c >> 2, b = (c >> 1) & 1, d = c & 1;
-            const int ci = i0 + a, cj = j0 + b, ck = k0 + d;
-            const int slot = leaf_slot<L>(g, nb, bi, bj, bk, ci, cj, ck);
-            cr.off[c] = ((long long)slot << (3 * LG2)) + (((li[a] << LG2) + lj[b]) << LG2) + lk[d];
-            cr.w[c] = wx[a] * wy[b] * wz[d];
-        }
+        for (int c = 0; c < 8; ++c)
+            slot[c] = leaf_slot<L>(g, nb, bi, bj, bk, i0 + (c >> 2), j0 + ((c >> 1) & 1), k0 + (c & 1));
+    }
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const int a = c >> 2, b = (c >> 1) & 1, d = c & 1;
+        cr.off[c] = ((Off)slot[c] << (3 * LG2)) + (Off)((((li[a] << LG2) + lj[b]) << LG2) + lk[d]);
+        cr.w[c] = wx[a] * wy[b] * wz[d];
     }
 }
 
-template <int L>
-__device__ __forceinline__ float sample(const float *__restrict__ f, const Corners<L> &cr)
+template <int L, typename Off>
+__device__ __forceinline__ float sample(const float *__restrict__ f, const Corners<L, Off> &cr)
 {
     float s = 0.f;
 #pragma unroll
@@ -109,33 +116,53 @@ __device__ __forceinline__ float sample(const float *__restrict__ f, const Corne
     return s;
 }
 
-template <int L>
-__device__ __forceinline__ void velocity(const DevGrid &g, const int32_t *nb, int bi, int bj, int bk, int v0, float px,
-                                         float py, float pz, float (&u)[3])
+template <int L, typename Off, bool PK>
+__device__ __forceinline__ void velocity(const DevGrid &g, const int32_t *nb, int nbv, int bi, int bj, int bk, int v0,
+                                         const float4 *__restrict__ vel4, float px, float py, float pz, float (&u)[3])
 {
-    Corners<L> cr;
-    corners<L>(g, nb, bi, bj, bk, px, py, pz, cr);
+    Corners<L, Off> cr;
+    corners<L, Off>(g, nb, nbv, bi, bj, bk, px, py, pz, cr);
+    if (PK) {
+        u[0] = u[1] = u[2] = 0.f;
 #pragma unroll
-    for (int a = 0; a < 3; ++a) u[a] = sample<L>(g.field[v0 + a], cr);
+        for (int c = 0; c < 8; ++c) {
+            const float4 w = __ldg(vel4 + cr.off[c]);
+            u[0] = fmaf(cr.w[c], w.x, u[0]);
+            u[1] = fmaf(cr.w[c], w.y, u[1]);
+            u[2] = fmaf(cr.w[c], w.z, u[2]);
+        }
+    } else {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) u[a] = sample<L, Off>(g.field[v0 + a], cr);
+    }
 }
 
 // RK3 backtrace of cell centre x over h; returns the corners of the sample.
 // k1 = u(x) at the cell centre itself is the voxel's stored velocity (the
 // trilinear weights there are 1, 0, ..., 0), read directly at idx.
-template <int L>
-__device__ __forceinline__ void backtrace(const DevGrid &g, const int32_t *nb, int bi, int bj, int bk, int v0, float h,
-                                          const float (&x)[3], long long idx, Corners<L> &cr)
+template <int L, typename Off, bool PK>
+__device__ __forceinline__ void backtrace(const DevGrid &g, const int32_t *nb, int nbv, int bi, int bj, int bk, int v0,
+                                          const float4 *__restrict__ vel4, float h, const float (&x)[3], Off idx,
+                                          Corners<L, Off> &cr)
 {
     float k1[3], k2[3], k3[3];
+    if (PK) {
+        const float4 w = __ldg(vel4 + idx);
+        k1[0] = w.x;
+        k1[1] = w.y;
+        k1[2] = w.z;
+    } else {
 #pragma unroll
-    for (int a = 0; a < 3; ++a) k1[a] = g.field[v0 + a][idx];
-    velocity<L>(g, nb, bi, bj, bk, v0, x[0] - 0.5f * h * k1[0], x[1] - 0.5f * h * k1[1], x[2] - 0.5f * h * k1[2], k2);
-    velocity<L>(g, nb, bi, bj, bk, v0, x[0] - 0.75f * h * k2[0], x[1] - 0.75f * h * k2[1], x[2] - 0.75f * h * k2[2],
-                k3);
+        for (int a = 0; a < 3; ++a) k1[a] = g.field[v0 + a][idx];
+    }
+    velocity<L, Off, PK>(g, nb, nbv, bi, bj, bk, v0, vel4, x[0] - 0.5f * h * k1[0], x[1] - 0.5f * h * k1[1],
+                     x[2] - 0.5f * h * k1[2], k2);
+    velocity<L, Off, PK>(g, nb, nbv, bi, bj, bk, v0, vel4, x[0] - 0.75f * h * k2[0], x[1] - 0.75f * h * k2[1],
+                     x[2] - 0.75f * h * k2[2], k3);
     const float c = h / 9.f;
-    corners<L>(g, nb, bi, bj, bk, x[0] - c * (2.f * k1[0] + 3.f * k2[0] + 4.f * k3[0]),
-               x[1] - c * (2.f * k1[1] + 3.f * k2[1] + 4.f * k3[1]), x[2] - c * (2.f * k1[2] + 3.f * k2[2] + 4.f * k3[2]),
-               cr);
+    corners<L, Off>(g, nb, nbv, bi, bj, bk, x[0] - c * (2.f * k1[0] + 3.f * k2[0] + 4.f * k3[0]),
+                    x[1] - c * (2.f * k1[1] + 3.f * k2[1] + 4.f * k3[1]),
+                    x[2] - c * (2.f * k1[2] + 3.f * k2[2] + 4.f * k3[2]), cr);
 }
 
 // MODE 0: advect (dst = src at the backtrace over h); with BND the clamp
@@ -144,20 +171,23 @@ __device__ __forceinline__ void backtrace(const DevGrid &g, const int32_t *nb, i
 // MODE 2: correction alone (q~ read from its field).
 // In modes 1 and 2, BND reads the clamp bounds from A.lo / A.hi instead of
 // tracing the forward path again.
-template <int L, int C, int MODE, bool BND>
-__global__ void __launch_bounds__(256) k_advect(DevGrid g, AdvectArgs A)
+// PK: the velocity is read from A.vel4 (packed).
+template <int L, int C, int MODE, bool BND, typename Off, bool PK>
+__global__ void __launch_bounds__(256, PK ? 4 : 1) k_advect(DevGrid g, AdvectArgs A)
 {
     constexpr int V = L * L * L, LG2 = (L == 8) ? 3 : 2;
     const long long n = g.ctrl->list_n;
     const int R = g.R;
+    // the loop bound is a multiple of 32 and the stride a multiple of 256, so
+    // a warp's lanes stay together and share one list entry per iteration
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n * V;
          q += (long long)gridDim.x * blockDim.x) {
         const long long e = q >> (3 * LG2);
         const int l = (int)(q & (V - 1));
         const int slot = g.list_slot[e];
-        const long long idx = ((long long)slot << (3 * LG2)) + l;
+        const Off idx = ((Off)slot << (3 * LG2)) + (Off)l;
         const bool act = (g.mask[(long long)slot * g.W + (l >> 5)] >> (l & 31)) & 1u;
-        if (!act) {  // inactive voxels keep 0
+        if (!__any_sync(kFull, act)) {  // inactive voxels keep 0
 #pragma unroll
             for (int c = 0; c < C; ++c) {
                 g.field[A.dst[c]][idx] = 0.f;
@@ -165,20 +195,24 @@ __global__ void __launch_bounds__(256) k_advect(DevGrid g, AdvectArgs A)
             }
             continue;
         }
+        // the inactive lanes of a warp with active voxels trace along (their
+        // reads are in bounds: every corner lies in a table or root leaf) and
+        // store 0
         const int b = g.list_b[e];
         const int bi = b / (R * R), bj = (b / R) % R, bk = b % R;
         const int32_t *nb = g.nbr + e * 27;
+        const int nbv = lane_id() < 27 ? __ldg(nb + lane_id()) : 0;
         const float x[3] = {(float)((bi << LG2) + (l >> (2 * LG2))) + 0.5f,
                             (float)((bj << LG2) + ((l >> LG2) & (L - 1))) + 0.5f,
                             (float)((bk << LG2) + (l & (L - 1))) + 0.5f};
-        Corners<L> fw;
-        if (MODE == 0 || !BND) backtrace<L>(g, nb, bi, bj, bk, A.v0, A.h, x, idx, fw);
+        Corners<L, Off> fw;
+        if (MODE == 0 || !BND) backtrace<L, Off, PK>(g, nb, nbv, bi, bj, bk, A.v0, A.vel4, A.h, x, idx, fw);
         if (MODE == 0) {
 #pragma unroll
             for (int c = 0; c < C; ++c) {
                 const float *sf = g.field[A.src[c]];
                 if (!BND) {
-                    g.field[A.dst[c]][idx] = sample<L>(sf, fw);
+                    g.field[A.dst[c]][idx] = act ? sample<L, Off>(sf, fw) : 0.f;
                     continue;
                 }
                 float v[8];
@@ -192,7 +226,7 @@ __global__ void __launch_bounds__(256) k_advect(DevGrid g, AdvectArgs A)
                     lo = fminf(lo, v[k]);
                     hi = fmaxf(hi, v[k]);
                 }
-                g.field[A.dst[c]][idx] = smp;
+                g.field[A.dst[c]][idx] = act ? smp : 0.f;
                 A.lo[c][idx] = lo;
                 A.hi[c][idx] = hi;
             }
@@ -200,11 +234,11 @@ __global__ void __launch_bounds__(256) k_advect(DevGrid g, AdvectArgs A)
         }
         float qt[C];
         if (MODE == 1) {
-            Corners<L> bw;
-            backtrace<L>(g, nb, bi, bj, bk, A.v0, -A.h, x, idx, bw);
+            Corners<L, Off> bw;
+            backtrace<L, Off, PK>(g, nb, nbv, bi, bj, bk, A.v0, A.vel4, -A.h, x, idx, bw);
 #pragma unroll
             for (int c = 0; c < C; ++c) {
-                qt[c] = sample<L>(g.field[A.qhat[c]], bw);
+                qt[c] = act ? sample<L, Off>(g.field[A.qhat[c]], bw) : 0.f;
                 if (A.qtil[c] >= 0) g.field[A.qtil[c]][idx] = qt[c];
             }
         } else {
@@ -229,31 +263,70 @@ __global__ void __launch_bounds__(256) k_advect(DevGrid g, AdvectArgs A)
                 }
             }
             const float r = g.field[A.qhat[c]][idx] + 0.5f * (qf[idx] - qt[c]);
-            g.field[A.dst[c]][idx] = fminf(fmaxf(r, lo), hi);
+            g.field[A.dst[c]][idx] = act ? fminf(fmaxf(r, lo), hi) : 0.f;
         }
     }
 }
 
-template <int L, int MODE, bool BND>
-void launch_LB(const DevGrid &g, cudaStream_t s, const AdvectArgs &a, int ctas)
+template <int L, int MODE, bool BND, typename Off, bool PK>
+void launch_LBO(const DevGrid &g, cudaStream_t s, const AdvectArgs &a, int ctas)
 {
-    if (a.C == 1) k_advect<L, 1, MODE, BND><<<ctas, 256, 0, s>>>(g, a);
-    else if (a.C == 2) k_advect<L, 2, MODE, BND><<<ctas, 256, 0, s>>>(g, a);
-    else k_advect<L, 3, MODE, BND><<<ctas, 256, 0, s>>>(g, a);
+    if (a.C == 1) k_advect<L, 1, MODE, BND, Off, PK><<<ctas, 256, 0, s>>>(g, a);
+    else if (a.C == 2) k_advect<L, 2, MODE, BND, Off, PK><<<ctas, 256, 0, s>>>(g, a);
+    else k_advect<L, 3, MODE, BND, Off, PK><<<ctas, 256, 0, s>>>(g, a);
 }
 
 template <int L, int MODE>
-void launch_L(const DevGrid &g, cudaStream_t s, const AdvectArgs &a, int ctas)
+void launch_L(const DevGrid &g, cudaStream_t s, AdvectArgs a, int ctas)
 {
-    if (a.lo[0]) launch_LB<L, MODE, true>(g, s, a, ctas);
-    else launch_LB<L, MODE, false>(g, s, a, ctas);
+    // 32-bit element offsets while every offset (the zero leaf's included)
+    // fits; the packed velocity is read by the modes that trace (the fused
+    // schedule's forward and backward launches) with 32-bit offsets
+    const bool wide = (unsigned long long)(g.cap + 1) * (L * L * L) > 0x7fffffffull;
+    if constexpr (MODE != 2) {
+        if (a.vel4 && !wide) {
+            if (a.lo[0]) launch_LBO<L, MODE, true, int, true>(g, s, a, ctas);
+            else launch_LBO<L, MODE, false, int, true>(g, s, a, ctas);
+            return;
+        }
+    }
+    a.vel4 = nullptr;
+    if (a.lo[0]) {
+        if (wide) launch_LBO<L, MODE, true, long long, false>(g, s, a, ctas);
+        else launch_LBO<L, MODE, true, int, false>(g, s, a, ctas);
+    } else {
+        if (wide) launch_LBO<L, MODE, false, long long, false>(g, s, a, ctas);
+        else launch_LBO<L, MODE, false, int, false>(g, s, a, ctas);
+    }
+}
+
+// Packed velocity: vel4[slot * L^3 + l] = (u, v, w, 0) of fields v0..v0+2 for
+// every listed leaf (the zero leaf's block is zero from its allocation).
+template <int L>
+__global__ void __launch_bounds__(256) k_pack_velocity(DevGrid g, int v0, float4 *__restrict__ vel4)
+{
+    constexpr int V = L * L * L, LG2 = (L == 8) ? 3 : 2;
+    const long long n = g.ctrl->list_n;
+    const float *__restrict__ u = g.field[v0], *__restrict__ v = g.field[v0 + 1], *__restrict__ w = g.field[v0 + 2];
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n * V;
+         q += (long long)gridDim.x * blockDim.x) {
+        const long long idx = ((long long)g.list_slot[q >> (3 * LG2)] << (3 * LG2)) + (q & (V - 1));
+        vel4[idx] = make_float4(__ldg(u + idx), __ldg(v + idx), __ldg(w + idx), 0.f);
+    }
 }
 
 }  // namespace
 
+void launch_pack_velocity(const DevGrid &g, cudaStream_t s, int v0, float4 *vel4, const LaunchCfg &lc)
+{
+    const int ctas = lc.num_sms * 8;
+    if (g.L == 8) k_pack_velocity<8><<<ctas, 256, 0, s>>>(g, v0, vel4);
+    else k_pack_velocity<4><<<ctas, 256, 0, s>>>(g, v0, vel4);
+}
+
 void launch_advect_group(const DevGrid &g, cudaStream_t s, int mode, int C, const int *dst, const int *src,
                          const int *qhat, const int *qtil, int v0, float h, float *const *lo, float *const *hi,
-                         const LaunchCfg &lc)
+                         const float4 *vel4, const LaunchCfg &lc)
 {
     AdvectArgs a{};
     a.C = C;
@@ -267,6 +340,7 @@ void launch_advect_group(const DevGrid &g, cudaStream_t s, int mode, int C, cons
     }
     a.v0 = v0;
     a.h = h;
+    a.vel4 = vel4;
     const int ctas = lc.num_sms * 8;
     if (g.L == 8) {
         if (mode == 0) launch_L<8, 0>(g, s, a, ctas);

@@ -113,6 +113,7 @@ struct sg_grid {
     unsigned long long act_ver = 0;         // list version the offsets were computed for (0 = never)
     long long act_total = 0;
     float *adv_lo[3] = {}, *adv_hi[3] = {}; // advection clamp bounds, (cap + 1) * L^3 each (allocated at first use)
+    float4 *adv_vel4 = nullptr;             // packed advection velocity, (cap + 1) * L^3 (allocated at first use)
     // staged uploads (sg_stage_active): two slots filled on a copy stream of
     // the grid's own, each consumed by a queued scatter
     cudaStream_t copy_stream = nullptr;
@@ -565,10 +566,51 @@ int run_advect_run(sg_grid *g, size_t &i)
         }
         return true;
     };
+    // Velocity packing (with fusion): when two or more advections of the run
+    // trace through the velocity of its first advection and no op of the run
+    // writes it, the three fields are packed once (before the first launch
+    // that traces) and every launch with that velocity reads the packed copy.
+    int pack_v0 = -1;
+    bool packed = false;
+    if (fuse) {
+        int tracers = 0;
+        for (int a = 0; a < n; ++a) {
+            const Op &o = g->queue[i + a];
+            if (o.kind != OP_ADVECT) continue;
+            if (pack_v0 < 0) pack_v0 = o.i0;
+            if (o.i0 == pack_v0) ++tracers;
+        }
+        if (tracers < 2) pack_v0 = -1;
+        for (int f : run_writes)
+            if (pack_v0 >= 0 && f >= pack_v0 && f <= pack_v0 + 2) pack_v0 = -1;
+    }
+    auto ensure_vel4 = [&]() -> bool {
+        if (g->dry || g->adv_vel4) return true;
+        const size_t per_leaf = size_t(g->dev.L) * g->dev.L * g->dev.L;
+        g->adv_vel4 = (float4 *)dev_alloc(g, sizeof(float4) * size_t(g->dev.cap + 1) * per_leaf);
+        if (!g->adv_vel4) return false;
+        // the zero leaf's block: never written by the packing, read as zeros
+        return cudaMemsetAsync(g->adv_vel4 + size_t(g->dev.cap) * per_leaf, 0, sizeof(float4) * per_leaf,
+                               g->stream) == cudaSuccess;
+    };
     auto launch = [&](int mode, const std::vector<int> &ops, const std::vector<int> &macs) -> int {
         int r2;
         if ((r2 = ensure_list(g))) return r2;
         const Op &f = g->queue[i + ops[0]];
+        const float4 *vel4 = nullptr;
+        if (pack_v0 >= 0 && f.i0 == pack_v0) {
+            if (!packed) {
+                if (!ensure_vel4()) {
+                    pack_v0 = -1;  // without the memory: read the three fields
+                } else {
+                    if (!g->dry) launch_pack_velocity(g->dev, g->stream, pack_v0, g->adv_vel4, g->lc);
+                    g->stats.velocity_packs++;
+                    packed = true;
+                    if ((r2 = after_launch(g, "velocity packing"))) return r2;
+                }
+            }
+            if (packed) vel4 = g->adv_vel4;
+        }
         int dst[3], src[3], qh[3], qt[3];
         const int C = (int)ops.size();
         for (int c = 0; c < C; ++c) {
@@ -639,7 +681,7 @@ int run_advect_run(sg_grid *g, size_t &i)
         if (bnd) g->stats.bounds_reused += (mode == 0) ? 0 : C;
         if (!g->dry)
             launch_advect_group(g->dev, g->stream, mode, C, dst, src, qh, qt, f.i0, h, bnd ? lo : nullptr,
-                                bnd ? hi : nullptr, g->lc);
+                                bnd ? hi : nullptr, vel4, g->lc);
         g->stats.ops_fused += (int64_t)(mode == 1 ? 2 * C : C) - 1;
         for (int c : ops) done[c] = 1;
         for (int c : macs) done[c] = 1;

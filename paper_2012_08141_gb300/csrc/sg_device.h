@@ -270,9 +270,13 @@ void launch_g2p(const DevGrid &g, cudaStream_t s, float *x, float *v, float *C, 
 // it reads); modes 1 and 2 read the bounds there instead of tracing the
 // forward path (they must come from a mode-0 launch with the same q,
 // velocity and h, nothing written to q or the velocity since).
+// vel4: fields v0..v0+2 packed by launch_pack_velocity since they last
+// changed, or null.
 void launch_advect_group(const DevGrid &g, cudaStream_t s, int mode, int C, const int *dst, const int *src,
                          const int *qhat, const int *qtil, int v0, float h, float *const *lo, float *const *hi,
-                         const LaunchCfg &lc);
+                         const float4 *vel4, const LaunchCfg &lc);
+// vel4 ((cap + 1) * L^3 float4): the listed leaves' velocity (fields v0..v0+2)
+void launch_pack_velocity(const DevGrid &g, cudaStream_t s, int v0, float4 *vel4, const LaunchCfg &lc);
 void launch_activate_tube(const DevGrid &g, cudaStream_t s, long long lo2, long long hi2);
 
 // ---- fused element-wise struct-fors (sg_elementwise.cu) ----

@@ -386,9 +386,10 @@ def test_micro_not_fusible_across_a_stencil():
 def test_advection_channel_fusion_launches():
     """Three channels written channel by channel (forward advect, backward
     advect, correction each): the queue reorders by field dependencies into
-    one forward launch for all channels and one fused backward+correction
-    launch (q~ scratch, not stored) -- against 9 launches without fusion and
-    27 eager (clear-list + list + kernel each)."""
+    one velocity packing, one forward launch for all channels and one fused
+    backward+correction launch (q~ scratch, not stored) -- against 9 launches
+    without fusion and 27 eager (clear-list + list + kernel each), neither of
+    which packs the velocity."""
     def step(g):
         for c in range(3):
             q, qh, qt, qn = 3 + 4 * c, 4 + 4 * c, 5 + 4 * c, 6 + 4 * c
@@ -408,16 +409,19 @@ def test_advection_channel_fusion_launches():
         g.flush()
         s1 = g.stats()
         counts[name] = {k: s1[k] - s0[k] for k in s1}
-    assert counts["all"]["launches"] == 2 and counts["all"]["stores_removed"] == 3
+    assert counts["all"]["launches"] == 3 and counts["all"]["stores_removed"] == 3
+    assert counts["all"]["velocity_packs"] == 1
     assert counts["all"]["ops_fused"] == 7
     assert counts["all"]["bounds_reused"] == 3      # each correction reads its forward clamp bounds
     assert counts["nofuse"]["launches"] == 9 and counts["nofuse"]["bounds_reused"] == 0
     assert counts["eager"]["launches"] == 27 and counts["eager"]["bounds_reused"] == 0
+    assert counts["nofuse"]["velocity_packs"] == 0 and counts["eager"]["velocity_packs"] == 0
 
 
 def test_advection_bounds_not_reused_after_a_write():
     """The clamp bounds of a forward advection are not reused when an op of
-    the run writes the velocity, nor by a correction of another step."""
+    the run writes the velocity, nor by a correction of another step; the
+    velocity is not packed for a run that writes one of its fields."""
     g = sg.Grid(64, 3, 12, max_leaves=1024, dry_run=True)
     g.activate_tube(1000, 3000)
     g.list_gen()
@@ -430,10 +434,12 @@ def test_advection_bounds_not_reused_after_a_write():
     assert g.stats()["bounds_reused"] == b0
     g.advect(4, 3, 0, 1e-3)
     g.advect(5, 4, 0, -1e-3)
+    p0 = g.stats()["velocity_packs"]
     g.advect(1, 7, 9, 1e-3)                    # writes a velocity component in the same run
     g.maccormack(6, 3, 4, 5, 0, 1e-3)
     g.flush()
     assert g.stats()["bounds_reused"] == b0
+    assert g.stats()["velocity_packs"] == p0
     g.advect(4, 3, 0, 1e-3)
     g.advect(5, 4, 0, -1e-3)
     g.maccormack(6, 3, 4, 5, 0, 1e-3)
@@ -455,7 +461,7 @@ def test_advection_dependencies_respected():
     g.maccormack(6, 3, 4, 5, 0, 1e-3)  # m: q' from q, q^, q~
     g.advect(7, 6, 0, 1e-3)          # c: reads q' -> after m
     g.flush()
-    assert g.stats()["launches"] - s0 == 3      # a | b+m fused | c
+    assert g.stats()["launches"] - s0 == 4      # velocity packing | a | b+m fused | c
     lib = sg.load_library()
     assert lib.sg_advect(g.h, 3, 3, 0, 1e-3) == sg.SG_ERR_INVALID            # dst == src
     assert lib.sg_advect(g.h, 1, 3, 0, 1e-3) == sg.SG_ERR_INVALID            # dst is a velocity field
