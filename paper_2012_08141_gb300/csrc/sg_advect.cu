@@ -11,9 +11,9 @@
 // 27-neighbour table (a null or out-of-domain neighbour is the zero leaf, and
 // a stored value at an inactive voxel is 0, so every read is unconditional),
 // or through the root when the sample lies more than a leaf away.  A warp's 32
-// voxels lie in one leaf (L^3 is a multiple of 32), so lanes 0..26 hold the
-// entry's table and every lookup is a shuffle; element offsets are 32-bit
-// when the fields have fewer than 2^31 elements.
+// voxels lie in one leaf (L^3 is a multiple of 32), so the warp copies the
+// entry's table to shared memory once and every lookup is a shared load;
+// element offsets are 32-bit when the fields have fewer than 2^31 elements.
 // With fusion the run's velocity is first packed as one float4 (u, v, w, 0)
 // per value slot, so a velocity corner is one 16-byte load instead of three
 // (the same products summed in the same order: the results are identical).
@@ -68,10 +68,9 @@ struct Corners {
     float w[8];
 };
 
-// nbv: lane t < 27 holds entry t of the warp's neighbour table.  Every lane
-// of the warp calls this together (the lookups are shuffles).
+// tab: the warp's copy of the list entry's neighbour table (shared memory).
 template <int L, typename Off>
-__device__ __forceinline__ void corners(const DevGrid &g, const int32_t *nb, int nbv, int bi, int bj, int bk,
+__device__ __forceinline__ void corners(const DevGrid &g, const int32_t *nb, const int *tab, int bi, int bj, int bk,
                                         float px, float py, float pz, Corners<L, Off> &cr)
 {
     constexpr int LG2 = (L == 8) ? 3 : 2;
@@ -86,14 +85,14 @@ __device__ __forceinline__ void corners(const DevGrid &g, const int32_t *nb, int
     const int li[2] = {i0 & (L - 1), (i0 + 1) & (L - 1)}, lj[2] = {j0 & (L - 1), (j0 + 1) & (L - 1)},
               lk[2] = {k0 & (L - 1), (k0 + 1) & (L - 1)};
     const float wx[2] = {1.f - fx, fx}, wy[2] = {1.f - fy, fy}, wz[2] = {1.f - fz, fz};
-    // within the 27-neighbourhood (the common case): the table entry by
-    // shuffle; lanes whose sample lies further out take the root afterwards
+    // within the 27-neighbourhood (the common case): the table entry; lanes
+    // whose sample lies further out take the root afterwards
     const bool near = di0 >= -1 && di1 <= 1 && dj0 >= -1 && dj1 <= 1 && dk0 >= -1 && dk1 <= 1;
     const int ti[2] = {near ? (di0 + 1) * 9 : 0, near ? (di1 + 1) * 9 : 0},
               tj[2] = {near ? (dj0 + 1) * 3 : 0, near ? (dj1 + 1) * 3 : 0}, tk[2] = {near ? dk0 + 1 : 0, near ? dk1 + 1 : 0};
     int slot[8];
 #pragma unroll
-    for (int c = 0; c < 8; ++c) slot[c] = __shfl_sync(kFull, nbv, ti[c >> 2] + tj[(c >> 1) & 1] + tk[c & 1]);
+    for (int c = 0; c < 8; ++c) slot[c] = tab[ti[c >> 2] + tj[(c >> 1) & 1] + tk[c & 1]];
     if (!near) {
 #pragma unroll
         for (int c = 0; c < 8; ++c)
@@ -117,11 +116,11 @@ __device__ __forceinline__ float sample(const float *__restrict__ f, const Corne
 }
 
 template <int L, typename Off, bool PK>
-__device__ __forceinline__ void velocity(const DevGrid &g, const int32_t *nb, int nbv, int bi, int bj, int bk, int v0,
+__device__ __forceinline__ void velocity(const DevGrid &g, const int32_t *nb, const int *tab, int bi, int bj, int bk, int v0,
                                          const float4 *__restrict__ vel4, float px, float py, float pz, float (&u)[3])
 {
     Corners<L, Off> cr;
-    corners<L, Off>(g, nb, nbv, bi, bj, bk, px, py, pz, cr);
+    corners<L, Off>(g, nb, tab, bi, bj, bk, px, py, pz, cr);
     if (PK) {
         u[0] = u[1] = u[2] = 0.f;
 #pragma unroll
@@ -141,7 +140,7 @@ __device__ __forceinline__ void velocity(const DevGrid &g, const int32_t *nb, in
 // k1 = u(x) at the cell centre itself is the voxel's stored velocity (the
 // trilinear weights there are 1, 0, ..., 0), read directly at idx.
 template <int L, typename Off, bool PK>
-__device__ __forceinline__ void backtrace(const DevGrid &g, const int32_t *nb, int nbv, int bi, int bj, int bk, int v0,
+__device__ __forceinline__ void backtrace(const DevGrid &g, const int32_t *nb, const int *tab, int bi, int bj, int bk, int v0,
                                           const float4 *__restrict__ vel4, float h, const float (&x)[3], Off idx,
                                           Corners<L, Off> &cr)
 {
@@ -155,12 +154,12 @@ __device__ __forceinline__ void backtrace(const DevGrid &g, const int32_t *nb, i
 #pragma unroll
         for (int a = 0; a < 3; ++a) k1[a] = g.field[v0 + a][idx];
     }
-    velocity<L, Off, PK>(g, nb, nbv, bi, bj, bk, v0, vel4, x[0] - 0.5f * h * k1[0], x[1] - 0.5f * h * k1[1],
+    velocity<L, Off, PK>(g, nb, tab, bi, bj, bk, v0, vel4, x[0] - 0.5f * h * k1[0], x[1] - 0.5f * h * k1[1],
                      x[2] - 0.5f * h * k1[2], k2);
-    velocity<L, Off, PK>(g, nb, nbv, bi, bj, bk, v0, vel4, x[0] - 0.75f * h * k2[0], x[1] - 0.75f * h * k2[1],
+    velocity<L, Off, PK>(g, nb, tab, bi, bj, bk, v0, vel4, x[0] - 0.75f * h * k2[0], x[1] - 0.75f * h * k2[1],
                      x[2] - 0.75f * h * k2[2], k3);
     const float c = h / 9.f;
-    corners<L, Off>(g, nb, nbv, bi, bj, bk, x[0] - c * (2.f * k1[0] + 3.f * k2[0] + 4.f * k3[0]),
+    corners<L, Off>(g, nb, tab, bi, bj, bk, x[0] - c * (2.f * k1[0] + 3.f * k2[0] + 4.f * k3[0]),
                     x[1] - c * (2.f * k1[1] + 3.f * k2[1] + 4.f * k3[1]),
                     x[2] - c * (2.f * k1[2] + 3.f * k2[2] + 4.f * k3[2]), cr);
 }
@@ -171,15 +170,18 @@ __device__ __forceinline__ void backtrace(const DevGrid &g, const int32_t *nb, i
 // MODE 2: correction alone (q~ read from its field).
 // In modes 1 and 2, BND reads the clamp bounds from A.lo / A.hi instead of
 // tracing the forward path again.
-// PK: the velocity is read from A.vel4 (packed).
+// PK: the velocity is read from A.vel4 (packed).  Four CTAs per SM (at most
+// 64 registers a thread): the traces are latency-bound.
 template <int L, int C, int MODE, bool BND, typename Off, bool PK>
-__global__ void __launch_bounds__(256, PK ? 4 : 1) k_advect(DevGrid g, AdvectArgs A)
+__global__ void __launch_bounds__(256, 4) k_advect(DevGrid g, AdvectArgs A)
 {
     constexpr int V = L * L * L, LG2 = (L == 8) ? 3 : 2;
     const long long n = g.ctrl->list_n;
     const int R = g.R;
+    __shared__ int s_nb[8][27];
     // the loop bound is a multiple of 32 and the stride a multiple of 256, so
-    // a warp's lanes stay together and share one list entry per iteration
+    // a warp's lanes share one list entry per iteration and all reach the
+    // __syncwarp() around the copy of its table
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n * V;
          q += (long long)gridDim.x * blockDim.x) {
         const long long e = q >> (3 * LG2);
@@ -187,7 +189,12 @@ __global__ void __launch_bounds__(256, PK ? 4 : 1) k_advect(DevGrid g, AdvectArg
         const int slot = g.list_slot[e];
         const Off idx = ((Off)slot << (3 * LG2)) + (Off)l;
         const bool act = (g.mask[(long long)slot * g.W + (l >> 5)] >> (l & 31)) & 1u;
-        if (!__any_sync(kFull, act)) {  // inactive voxels keep 0
+        const int32_t *nb = g.nbr + e * 27;
+        int *tab = s_nb[threadIdx.x >> 5];
+        __syncwarp();
+        if (lane_id() < 27) tab[lane_id()] = __ldg(nb + lane_id());
+        __syncwarp();
+        if (!act) {  // inactive voxels keep 0
 #pragma unroll
             for (int c = 0; c < C; ++c) {
                 g.field[A.dst[c]][idx] = 0.f;
@@ -195,24 +202,19 @@ __global__ void __launch_bounds__(256, PK ? 4 : 1) k_advect(DevGrid g, AdvectArg
             }
             continue;
         }
-        // the inactive lanes of a warp with active voxels trace along (their
-        // reads are in bounds: every corner lies in a table or root leaf) and
-        // store 0
         const int b = g.list_b[e];
         const int bi = b / (R * R), bj = (b / R) % R, bk = b % R;
-        const int32_t *nb = g.nbr + e * 27;
-        const int nbv = lane_id() < 27 ? __ldg(nb + lane_id()) : 0;
         const float x[3] = {(float)((bi << LG2) + (l >> (2 * LG2))) + 0.5f,
                             (float)((bj << LG2) + ((l >> LG2) & (L - 1))) + 0.5f,
                             (float)((bk << LG2) + (l & (L - 1))) + 0.5f};
         Corners<L, Off> fw;
-        if (MODE == 0 || !BND) backtrace<L, Off, PK>(g, nb, nbv, bi, bj, bk, A.v0, A.vel4, A.h, x, idx, fw);
+        if (MODE == 0 || !BND) backtrace<L, Off, PK>(g, nb, tab, bi, bj, bk, A.v0, A.vel4, A.h, x, idx, fw);
         if (MODE == 0) {
 #pragma unroll
             for (int c = 0; c < C; ++c) {
                 const float *sf = g.field[A.src[c]];
                 if (!BND) {
-                    g.field[A.dst[c]][idx] = act ? sample<L, Off>(sf, fw) : 0.f;
+                    g.field[A.dst[c]][idx] = sample<L, Off>(sf, fw);
                     continue;
                 }
                 float v[8];
@@ -226,7 +228,7 @@ __global__ void __launch_bounds__(256, PK ? 4 : 1) k_advect(DevGrid g, AdvectArg
                     lo = fminf(lo, v[k]);
                     hi = fmaxf(hi, v[k]);
                 }
-                g.field[A.dst[c]][idx] = act ? smp : 0.f;
+                g.field[A.dst[c]][idx] = smp;
                 A.lo[c][idx] = lo;
                 A.hi[c][idx] = hi;
             }
@@ -235,10 +237,10 @@ __global__ void __launch_bounds__(256, PK ? 4 : 1) k_advect(DevGrid g, AdvectArg
         float qt[C];
         if (MODE == 1) {
             Corners<L, Off> bw;
-            backtrace<L, Off, PK>(g, nb, nbv, bi, bj, bk, A.v0, A.vel4, -A.h, x, idx, bw);
+            backtrace<L, Off, PK>(g, nb, tab, bi, bj, bk, A.v0, A.vel4, -A.h, x, idx, bw);
 #pragma unroll
             for (int c = 0; c < C; ++c) {
-                qt[c] = act ? sample<L, Off>(g.field[A.qhat[c]], bw) : 0.f;
+                qt[c] = sample<L, Off>(g.field[A.qhat[c]], bw);
                 if (A.qtil[c] >= 0) g.field[A.qtil[c]][idx] = qt[c];
             }
         } else {
@@ -263,7 +265,7 @@ __global__ void __launch_bounds__(256, PK ? 4 : 1) k_advect(DevGrid g, AdvectArg
                 }
             }
             const float r = g.field[A.qhat[c]][idx] + 0.5f * (qf[idx] - qt[c]);
-            g.field[A.dst[c]][idx] = act ? fminf(fmaxf(r, lo), hi) : 0.f;
+            g.field[A.dst[c]][idx] = fminf(fmaxf(r, lo), hi);
         }
     }
 }
