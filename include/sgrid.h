@@ -534,19 +534,26 @@ int sg_batch_destroy(sg_batch *b);
  * (res, lo2, hi2, lo_strict as in sg_activate_shell, 8^3 leaves), initial
  * field values from sg_fill_hash(seed), and `steps` fused steps
  * x <- box27(diffuse7(x, coef)) with the sum of x kept after each step.
- * sg_server_submit only queues a job.  Each sg_server_tick
- *   1. admits pending jobs in submission order while a resident slot is free
- *      and cudaMemGetInfo's free memory covers the job's footprint plus
- *      hbm_reserve (a job that cannot fit even on an idle server fails);
- *      an admitted job's grid is created, activated, listed and filled on
- *      the device and stays resident until the job completes;
- *   2. runs one batched step (one persistent launch, see sg_batch_create)
- *      over every resident job, so jobs admitted while others run share it;
- *   3. retires jobs that reached their step count, keeping their last sum
- *      and their submit / admit / done times (seconds, host steady clock),
- *      and copying their final field to out_values when one is given;
- * and synchronizes the stream once.  A job's result equals the same job run
- * alone up to FP32 rounding order. */
+ * sg_server_submit only queues a job.  Each sg_server_tick waits once, for
+ * the device work the previous tick queued, then
+ *   1. advances the jobs of the previous tick's step and retires those that
+ *      reached their step count, keeping their last sum and their submit /
+ *      admit / done times (seconds, host steady clock), and copying their
+ *      final field to out_values when one is given;
+ *   2. adds the jobs admitted by the previous tick to the resident set;
+ *   3. launches one batched step (one persistent launch, see
+ *      sg_batch_create) over every resident job, so jobs admitted while
+ *      others run share it, and does not wait for it;
+ *   4. while that step runs, admits pending jobs in submission order while a
+ *      slot is free and cudaMemGetInfo's free memory covers the job's
+ *      footprint plus hbm_reserve (a job that cannot fit even on an idle
+ *      server fails): the job's grid is allocated and its creation,
+ *      activation, list, fill and counts are queued behind the step on the
+ *      server's stream; the job stays resident until it completes.
+ * So an admitted job joins the next tick's step, and a job's last step
+ * completes in one tick and is retired by the next.  sg_server_stats.resident
+ * counts admitted jobs.  A job's result equals the same job run alone up to
+ * FP32 rounding order. */
 #define SG_JOB_PENDING 0
 #define SG_JOB_RUNNING 1
 #define SG_JOB_DONE 2

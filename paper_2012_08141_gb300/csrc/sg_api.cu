@@ -1102,9 +1102,9 @@ int run_write_staged(sg_grid *g, const Op &o)
 // ============================================================================
 // C ABI
 // ============================================================================
-extern "C" {
+namespace sg {
 
-int sg_create(const sg_desc *desc, void *cuda_stream, sg_grid **out)
+int grid_create(const sg_desc *desc, void *cuda_stream, sg_grid **out, bool init_sync)
 {
     if (!desc || !out) return fail(SG_ERR_INVALID, "null argument");
     *out = nullptr;
@@ -1208,8 +1208,9 @@ int sg_create(const sg_desc *desc, void *cuda_stream, sg_grid **out)
         std::memcpy(g->host_ctrl, &c, sizeof c);
         rc = cuda_check(cudaMemcpyAsync(d.ctrl, g->host_ctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, s), "init ctrl");
     }
-    if (!rc) rc = cuda_check(cudaStreamSynchronize(s), "init sync");
+    if (!rc && init_sync) rc = cuda_check(cudaStreamSynchronize(s), "init sync");
     if (rc) {
+        cudaStreamSynchronize(s);  // the queued initialisation still reads host_ctrl
         cudaFreeHost(g->host_ctrl);
         dev_free_all(g);
         delete g;
@@ -1217,6 +1218,15 @@ int sg_create(const sg_desc *desc, void *cuda_stream, sg_grid **out)
     }
     *out = g;
     return SG_OK;
+}
+
+}  // namespace sg
+
+extern "C" {
+
+int sg_create(const sg_desc *desc, void *cuda_stream, sg_grid **out)
+{
+    return grid_create(desc, cuda_stream, out, true);
 }
 
 int sg_destroy(sg_grid *g)
@@ -2019,7 +2029,9 @@ namespace sg {
 
 int grid_num_sms(const sg_grid *g) { return g->lc.num_sms; }
 
-int grid_prepare_batch(sg_grid *g, int src, int tmp, int dst, BatchGrid out[2], long long *n_active)
+// The queued part of preparing a grid for the batched step: the queued ops,
+// a current list, the region masks and j-run records, and the active count.
+static int prepare_batch_queue(sg_grid *g, int src, int tmp, int dst)
 {
     if (!g || g->dry || g->dev.L != 8) return fail(SG_ERR_INVALID, "batched grids must be live 8^3-leaf grids");
     if (!valid_field(g, src) || !valid_field(g, tmp) || !valid_field(g, dst) || src == tmp || src == dst || tmp == dst)
@@ -2044,11 +2056,14 @@ int grid_prepare_batch(sg_grid *g, int src, int tmp, int dst, BatchGrid out[2], 
         launch_count_active(g->dev, g->stream, g->lc);
         rc = after_launch(g, "count active");
     }
-    if (!rc) rc = do_sync(g);
-    int32_t cnt[3] = {0, 0, 0};
-    if (!rc)
-        rc = cuda_check(cudaMemcpy(cnt, g->dev.col_cnt, sizeof cnt, cudaMemcpyDeviceToHost), "run record counts");
-    if (rc) return rc;
+    return rc;
+}
+
+// The two parities' descriptors from the host copies of the control block and
+// the run-record counts.
+static void batch_items(sg_grid *g, int src, int tmp, int dst, const int32_t *cnt, BatchGrid out[2],
+                        long long *n_active)
+{
     if (n_active) *n_active = (long long)g->host_ctrl->n_active;
     const int nl = g->host_ctrl->list_n;
     const int pairs = std::min(cnt[1], cnt[0]);
@@ -2066,6 +2081,49 @@ int grid_prepare_batch(sg_grid *g, int src, int tmp, int dst, BatchGrid out[2], 
         it.tri0 = 0;
         out[p] = it;
     }
+}
+
+int grid_prepare_batch(sg_grid *g, int src, int tmp, int dst, BatchGrid out[2], long long *n_active)
+{
+    int rc = prepare_batch_queue(g, src, tmp, dst);
+    if (!rc) rc = do_sync(g);
+    int32_t cnt[3] = {0, 0, 0};
+    if (!rc)
+        rc = cuda_check(cudaMemcpy(cnt, g->dev.col_cnt, sizeof cnt, cudaMemcpyDeviceToHost), "run record counts");
+    if (rc) return rc;
+    batch_items(g, src, tmp, dst, cnt, out, n_active);
+    return SG_OK;
+}
+
+int grid_prepare_batch_async(sg_grid *g, int src, int tmp, int dst, int32_t *cnt)
+{
+    if (g && (g->desc.flags & SG_CREATE_CHECK)) return fail(SG_ERR_INVALID, "checking grids prepare synchronously");
+    int rc = prepare_batch_queue(g, src, tmp, dst);
+    if (!rc)
+        rc = cuda_check(cudaMemcpyAsync(g->host_ctrl, g->dev.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, g->stream),
+                        "read control block");
+    if (!rc)
+        rc = cuda_check(cudaMemcpyAsync(cnt, g->dev.col_cnt, sizeof(int32_t) * 3, cudaMemcpyDeviceToHost, g->stream),
+                        "run record counts");
+    return rc;
+}
+
+int grid_prepare_batch_finish(sg_grid *g, int src, int tmp, int dst, const int32_t *cnt, BatchGrid out[2],
+                              long long *n_active)
+{
+    const int bits = g->host_ctrl->err;
+    if (bits) {
+        cudaMemsetAsync(&g->dev.ctrl->err, 0, sizeof(int32_t), g->stream);
+        cudaStreamSynchronize(g->stream);
+        return map_device_error(bits);
+    }
+    if (g->latched != SG_OK) {
+        const int out_rc = g->latched;
+        g->latched = SG_OK;
+        return out_rc;
+    }
+    if (g->list_ver == g->mask_ver) g->known_leaves = g->host_ctrl->list_n;
+    batch_items(g, src, tmp, dst, cnt, out, n_active);
     return SG_OK;
 }
 

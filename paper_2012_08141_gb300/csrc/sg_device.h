@@ -227,6 +227,18 @@ void launch_count_active(const DevGrid &g, cudaStream_t s, const LaunchCfg &lc);
 // count its active voxels, synchronize, and fill the descriptors of both
 // src/dst parities (tri0 left 0).  Returns an SG_* code.
 int grid_prepare_batch(sg_grid *g, int src, int tmp, int dst, BatchGrid out[2], long long *n_active);
+// The same in two halves, for a caller that overlaps them with other work:
+// _async queues everything on the grid's stream, ending with copies of the
+// control block and the three run-record counts to the host (cnt: pinned);
+// _finish, once the stream has passed them, checks the device error word and
+// fills out[2] and *n_active.  Not for grids created with SG_CREATE_CHECK.
+int grid_prepare_batch_async(sg_grid *g, int src, int tmp, int dst, int32_t *cnt);
+int grid_prepare_batch_finish(sg_grid *g, int src, int tmp, int dst, const int32_t *cnt, BatchGrid out[2],
+                              long long *n_active);
+// sg_create, with the final wait for the grid's initialisation optional
+// (init_sync false: it stays queued on the grid's stream, ahead of any later
+// work there).
+int grid_create(const sg_desc *desc, void *cuda_stream, sg_grid **out, bool init_sync);
 int grid_num_sms(const sg_grid *g);
 
 // ---- device-side fill with the counter-based generator (sg_structure.cu) ----

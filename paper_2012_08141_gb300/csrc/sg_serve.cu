@@ -1,18 +1,26 @@
 // sg_serve.cu -- a continuous-batching request loop for sparse diffusion jobs.
 //
 // Jobs (a shell or band activation, a seed, a step count) are submitted at
-// any time.  Each sg_server_tick:
-//   1. admits pending jobs, first come first served, while a resident slot is
-//      free and the device's free memory (cudaMemGetInfo) covers the job's
-//      footprint plus the configured reserve -- the job's grid is created,
-//      activated, listed and filled on the device and stays resident;
-//   2. runs ONE batched fused step (diffuse7 -> box27 -> sum, the batched
-//      persistent kernel) over every resident job, so jobs admitted while
-//      others are running share the launch;
-//   3. retires jobs whose step count is reached: their last sum is kept, their
-//      grid is destroyed, and submit/admit/done times are recorded (host
-//      steady clock) for latency.
-// Work stays on one stream; each tick ends with one synchronization.
+// any time.  Everything runs on the server's stream, and each sg_server_tick
+// waits once, for the work the previous tick queued:
+//   1. the jobs of the previous tick's step advance, and jobs whose step count
+//      is reached retire -- their last sum is kept, their grid is destroyed,
+//      and submit/admit/done times are recorded (host steady clock);
+//   2. the jobs whose admission the previous tick queued join: their counts
+//      reached the host behind that step;
+//   3. ONE batched fused step (diffuse7 -> box27 -> sum, the batched
+//      persistent kernel) is launched over every resident job, so jobs
+//      admitted while others are running share the launch;
+//   4. while it runs, pending jobs are admitted, first come first served,
+//      while a slot is free and the device's free memory (cudaMemGetInfo)
+//      covers the job's footprint plus the configured reserve: the host
+//      allocates the job's grid and queues its initialisation, activation,
+//      list, fill and count behind the step (the step holds every SM, so the
+//      device runs them when it ends);
+//   5. one event is recorded behind all of it.
+// The host's share of admission (bounds, allocation, launches) thus overlaps
+// the device's step, and the device runs the admitted jobs' kernels between
+// two steps without waiting for the host.
 #include <algorithm>
 #include <chrono>
 #include <cstring>
@@ -46,6 +54,7 @@ struct Job {
     double t_submit = 0, t_admit = 0, t_done = 0;
     sg_grid *grid = nullptr;
     BatchGrid items[2];
+    int cnt_slot = -1;  // its run-record counts in the server's pinned array while joining
 };
 
 // Leaves a shell can touch: root cells whose box can meet the band (the same
@@ -85,6 +94,11 @@ size_t job_footprint(const sg_job_desc &d, long long leaves)
 struct sg_server {
     sg_server_desc desc{};
     cudaStream_t stream = nullptr;
+    cudaEvent_t tick_done = nullptr;  // behind the last tick's step and admissions
+    bool in_flight = false;
+    std::vector<Job *> in_step;       // the jobs of the in-flight step, in item order
+    std::vector<Job *> joining;       // admissions queued behind the in-flight step
+    int32_t *host_cnt = nullptr;      // pinned, 3 run-record counts per joining job
     std::deque<Job *> pending;
     std::vector<Job *> resident;
     std::unordered_map<int64_t, Job *> jobs;
@@ -130,7 +144,8 @@ void retire(sg_server *s, Job *j, int state)
     else s->stats.failed++;
 }
 
-// Create, activate, list and fill a job's grid; returns SG_OK or an error.
+// Create a job's grid and queue its activation, list, fill and the copies of
+// its counts to the host (pinned slot cnt_slot); returns SG_OK or an error.
 int admit(sg_server *s, Job *j, long long leaves)
 {
     sg_desc d{};
@@ -143,16 +158,12 @@ int admit(sg_server *s, Job *j, long long leaves)
     d.alloc = s->desc.alloc;
     d.free = s->desc.free;
     d.alloc_ctx = s->desc.alloc_ctx;
-    int rc = sg_create(&d, (void *)s->stream, &j->grid);
+    int rc = grid_create(&d, (void *)s->stream, &j->grid, false);
     if (rc) return rc;
     if ((rc = sg_activate_shell(j->grid, j->desc.lo2, j->desc.hi2, j->desc.lo_strict))) return rc;
     if ((rc = sg_list_gen(j->grid))) return rc;
     if ((rc = sg_fill_hash(j->grid, 0, j->desc.seed))) return rc;
-    long long na = 0;
-    if ((rc = grid_prepare_batch(j->grid, 0, 1, 2, j->items, &na))) return rc;
-    j->n_active = na;
-    j->n_leaves = j->items[0].n;
-    return SG_OK;
+    return grid_prepare_batch_async(j->grid, 0, 1, 2, s->host_cnt + 3 * j->cnt_slot);
 }
 
 }  // namespace
@@ -193,6 +204,16 @@ int sg_server_create(const sg_server_desc *desc, void *cuda_stream, sg_server **
         delete s;
         return SG_ERR_OOM;
     }
+    if (cudaMallocHost((void **)&s->host_cnt, sizeof(int32_t) * 3 * desc->max_jobs) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->tick_done, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        if (s->host_cnt) cudaFreeHost(s->host_cnt);
+        cudaFreeHost(s->host_items);
+        cudaFreeHost(s->host_acc);
+        srv_free(s, s->dev_block);
+        delete s;
+        return SG_ERR_CUDA;
+    }
     *out = s;
     return SG_OK;
 }
@@ -217,63 +238,28 @@ int sg_server_submit(sg_server *s, const sg_job_desc *job, int64_t *job_id)
 int sg_server_tick(sg_server *s)
 {
     if (!s) return SG_ERR_INVALID;
-    // 1. admission
-    while (!s->pending.empty() && (int)s->resident.size() < s->desc.max_jobs) {
-        Job *j = s->pending.front();
-        const long long bound = shell_leaf_bound(j->desc);
-        size_t free_b = 0, total_b = 0;
-        if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return SG_ERR_CUDA;
-        if (free_b < job_footprint(j->desc, bound) + (size_t)s->desc.hbm_reserve) {
-            if (s->resident.empty()) {  // can never fit: fail it instead of waiting forever
-                s->pending.pop_front();
-                retire(s, j, SG_JOB_FAILED);
+    // the work the previous tick queued: its step, then its admissions
+    if (s->in_flight || !s->joining.empty())
+        if (cudaEventSynchronize(s->tick_done) != cudaSuccess) return SG_ERR_CUDA;
+    // 1. the step's jobs advance; those that reached their count retire
+    if (s->in_flight) {
+        s->in_flight = false;
+        for (size_t i = 0; i < s->in_step.size(); ++i) {
+            Job *j = s->in_step[i];
+            j->steps_done++;
+            j->parity ^= 1;
+            sg_swap(j->grid, 0, 2);
+            j->sum = s->host_acc[i];
+            s->stats.voxel_steps += (double)j->n_active;
+        }
+        s->in_step.clear();
+        std::vector<Job *> still;
+        still.reserve(s->resident.size());
+        for (Job *j : s->resident) {
+            if (j->steps_done < j->desc.steps) {
+                still.push_back(j);
                 continue;
             }
-            s->stats.admission_waits++;
-            break;
-        }
-        s->pending.pop_front();
-        if (admit(s, j, bound) != SG_OK) {
-            retire(s, j, SG_JOB_FAILED);
-            continue;
-        }
-        j->state = SG_JOB_RUNNING;
-        j->t_admit = now_s();
-        s->resident.push_back(j);
-    }
-    if (s->resident.empty()) return SG_OK;
-    // 2. one batched step over every resident job
-    const int n = (int)s->resident.size();
-    int tri = 0;
-    for (int i = 0; i < n; ++i) {
-        Job *j = s->resident[i];
-        s->host_items[i] = j->items[j->parity];
-        s->host_items[i].tri0 = tri;
-        tri += j->items[0].tasks;
-    }
-    if (cudaMemcpyAsync(s->dev_items, s->host_items, sizeof(BatchGrid) * n, cudaMemcpyHostToDevice, s->stream) !=
-            cudaSuccess ||
-        cudaMemsetAsync(s->dev_acc, 0, sizeof(double) * n, s->stream) != cudaSuccess)
-        return SG_ERR_CUDA;
-    launch_batch_diffuse_box(s->dev_items, n, tri, s->desc.coef, s->dev_acc, s->desc.warps_per_cta, s->num_sms,
-                             s->stream);
-    if (cudaPeekAtLastError() != cudaSuccess ||
-        cudaMemcpyAsync(s->host_acc, s->dev_acc, sizeof(double) * n, cudaMemcpyDeviceToHost, s->stream) != cudaSuccess ||
-        cudaStreamSynchronize(s->stream) != cudaSuccess)
-        return SG_ERR_CUDA;
-    s->stats.ticks++;
-    s->stats.launches++;
-    // 3. bookkeeping and retirement
-    std::vector<Job *> still;
-    still.reserve(n);
-    for (int i = 0; i < n; ++i) {
-        Job *j = s->resident[i];
-        j->steps_done++;
-        j->parity ^= 1;
-        sg_swap(j->grid, 0, 2);
-        j->sum = s->host_acc[i];
-        s->stats.voxel_steps += (double)j->n_active;
-        if (j->steps_done >= j->desc.steps) {
             // the result: field index 0 names the latest x after the swap
             int state = SG_JOB_DONE;
             if (j->desc.out_values) {
@@ -283,11 +269,74 @@ int sg_server_tick(sg_server *s)
                     state = SG_JOB_FAILED;
             }
             retire(s, j, state);
-        } else {
-            still.push_back(j);
         }
+        s->resident.swap(still);
     }
-    s->resident.swap(still);
+    // 2. the admissions queued behind that step join
+    for (Job *j : s->joining) {
+        long long na = 0;
+        if (grid_prepare_batch_finish(j->grid, 0, 1, 2, s->host_cnt + 3 * j->cnt_slot, j->items, &na) != SG_OK) {
+            retire(s, j, SG_JOB_FAILED);
+            continue;
+        }
+        j->n_active = na;
+        j->n_leaves = j->items[0].n;
+        s->resident.push_back(j);
+    }
+    s->joining.clear();
+    // 3. one batched step over every resident job
+    const int n = (int)s->resident.size();
+    if (n > 0) {
+        int tri = 0;
+        for (int i = 0; i < n; ++i) {
+            Job *j = s->resident[i];
+            s->host_items[i] = j->items[j->parity];
+            s->host_items[i].tri0 = tri;
+            tri += j->items[0].tasks;
+        }
+        if (cudaMemcpyAsync(s->dev_items, s->host_items, sizeof(BatchGrid) * n, cudaMemcpyHostToDevice, s->stream) !=
+                cudaSuccess ||
+            cudaMemsetAsync(s->dev_acc, 0, sizeof(double) * n, s->stream) != cudaSuccess)
+            return SG_ERR_CUDA;
+        launch_batch_diffuse_box(s->dev_items, n, tri, s->desc.coef, s->dev_acc, s->desc.warps_per_cta, s->num_sms,
+                                 s->stream);
+        if (cudaPeekAtLastError() != cudaSuccess ||
+            cudaMemcpyAsync(s->host_acc, s->dev_acc, sizeof(double) * n, cudaMemcpyDeviceToHost, s->stream) !=
+                cudaSuccess)
+            return SG_ERR_CUDA;
+        s->in_step = s->resident;
+        s->in_flight = true;
+        s->stats.ticks++;
+        s->stats.launches++;
+    }
+    // 4. admission, while the step runs
+    while (!s->pending.empty() && (int)(s->resident.size() + s->joining.size()) < s->desc.max_jobs) {
+        Job *j = s->pending.front();
+        const long long bound = shell_leaf_bound(j->desc);
+        size_t free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return SG_ERR_CUDA;
+        if (free_b < job_footprint(j->desc, bound) + (size_t)s->desc.hbm_reserve) {
+            if (s->resident.empty() && s->joining.empty()) {  // can never fit: fail it instead of waiting forever
+                s->pending.pop_front();
+                retire(s, j, SG_JOB_FAILED);
+                continue;
+            }
+            s->stats.admission_waits++;
+            break;
+        }
+        s->pending.pop_front();
+        j->cnt_slot = (int)s->joining.size();
+        if (admit(s, j, bound) != SG_OK) {
+            retire(s, j, SG_JOB_FAILED);
+            continue;
+        }
+        j->state = SG_JOB_RUNNING;
+        j->t_admit = now_s();
+        s->joining.push_back(j);
+    }
+    // 5. one event behind everything queued
+    if ((s->in_flight || !s->joining.empty()) && cudaEventRecord(s->tick_done, s->stream) != cudaSuccess)
+        return SG_ERR_CUDA;
     return SG_OK;
 }
 
@@ -311,7 +360,7 @@ int sg_server_get_stats(sg_server *s, sg_server_stats *out)
 {
     if (!s || !out) return SG_ERR_INVALID;
     *out = s->stats;
-    out->resident = (int32_t)s->resident.size();
+    out->resident = (int32_t)(s->resident.size() + s->joining.size());
     out->pending = (int32_t)s->pending.size();
     return SG_OK;
 }
@@ -327,6 +376,8 @@ int sg_server_destroy(sg_server *s)
     srv_free(s, s->dev_block);
     if (s->host_items) cudaFreeHost(s->host_items);
     if (s->host_acc) cudaFreeHost(s->host_acc);
+    if (s->host_cnt) cudaFreeHost(s->host_cnt);
+    cudaEventDestroy(s->tick_done);
     delete s;
     return SG_OK;
 }
