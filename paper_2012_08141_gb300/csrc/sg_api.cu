@@ -74,6 +74,11 @@ struct Op {
 
 }  // namespace
 
+// Single stencils switch to the j-run sweep on a list of at least this many
+// leaves, after this many sweeps without its run records.
+constexpr long long kSingleRunsLeaves = 8192;
+constexpr int kSingleRunsAfter = 2;
+
 struct sg_grid {
     sg_desc desc{};
     cudaStream_t stream = nullptr;
@@ -92,6 +97,8 @@ struct sg_grid {
     unsigned long long lg_calls = 0;
     unsigned long long rmask_ver = 0;  // list version the region masks were built from (0 = never)
     unsigned long long colgrp_ver = 0; // list version the run records were built from (0 = never)
+    unsigned long long single_ver = 0; // list version single stencils have swept without run records
+    int single_uses = 0;               // how many times
     int colgrp_axis = kGroupNone;      // axis they group leaves along
     unsigned long long tma_ver = 0;    // list version the TMA task descriptors were built from (0 = never)
     unsigned long long rr_calls = 0;   // region-mask launches (tags their look-back words)
@@ -368,10 +375,37 @@ int run_struct_for_group(sg_grid *g, size_t &i)
     const Op *c = b;
     const bool with_sum = fuse && c && c->kind == OP_SUM && c->src == a.dst;
     const int sum_slot = with_sum ? (int)c->slot : -1;
+    // A single stencil sweeps j-runs (no edge rows) when the run records are
+    // current.  Building them is one launch that saves a few microseconds per
+    // stencil on a large list, so it is done for a reused list (SG_OPT_LGR) of
+    // at least kSingleRunsLeaves leaves (the count at the last sync) that
+    // single stencils have already swept kSingleRunsAfter times -- and never
+    // while the stream is being captured into a graph, which would replay the
+    // one-off build with every launch.
+    LaunchCfg lcs = g->lc;
+    if (g->dev.L == 8 && g->lc.variant == kVariantSweepJRuns) {
+        if (g->colgrp_ver != g->list_ver || g->colgrp_axis != kGroupJ) {
+            if (g->single_ver != g->list_ver) {
+                g->single_ver = g->list_ver;
+                g->single_uses = 0;
+            }
+            cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+            if (!g->dry) cudaStreamIsCapturing(g->stream, &cap);
+            if ((g->opts & SG_OPT_LGR) && ++g->single_uses > kSingleRunsAfter && g->known_leaves >= kSingleRunsLeaves &&
+                cap == cudaStreamCaptureStatusNone) {
+                if (!g->dry) launch_region_masks(g->dev, g->stream, g->lc, kGroupJ, ++g->rr_calls);
+                if ((rc = after_launch(g, "region masks"))) return rc;
+                g->rmask_ver = g->list_ver;
+                g->colgrp_ver = g->list_ver;
+                g->colgrp_axis = kGroupJ;
+            }
+        }
+        lcs.single_runs = (g->colgrp_ver == g->list_ver && g->colgrp_axis == kGroupJ) ? 1 : 0;
+    }
     if (a.op == SG_DIFFUSE7) {
-        if (!g->dry) launch_diffuse7(g->dev, g->stream, a.src, a.dst, a.coef, check, sum_slot, g->lc);
+        if (!g->dry) launch_diffuse7(g->dev, g->stream, a.src, a.dst, a.coef, check, sum_slot, lcs);
     } else {
-        if (!g->dry) launch_box27(g->dev, g->stream, a.src, a.dst, check, sum_slot, g->lc);
+        if (!g->dry) launch_box27(g->dev, g->stream, a.src, a.dst, check, sum_slot, lcs);
     }
     g->stats.bytes_model += 2.0 * lb;
     if (with_sum) g->stats.ops_fused += 1;

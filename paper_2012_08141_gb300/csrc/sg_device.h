@@ -113,6 +113,7 @@ struct LaunchCfg {
     int num_sms;
     int persistent_ctas;  // CTAs of the persistent leaf loops
     int variant;          // StencilVariant
+    int single_runs = 0;  // the j-run records are current: single stencils sweep j-runs
 };
 
 constexpr int kListTile = 1024;  // root cells per compaction CTA
@@ -248,6 +249,7 @@ void launch_fill_hash(const DevGrid &g, cudaStream_t s, int f, unsigned long lon
 void launch_sweep_diffuse_box(const DevGrid &g, cudaStream_t s, int src, int tmp, int dst, float coef,
                               int store_tmp, int check_act, int sum_slot, const LaunchCfg &lc);
 // op: 1 = diffuse7, 2 = box27
+// (with lc.single_runs: the j-run form, k_sweep_single_jruns)
 void launch_sweep_single(const DevGrid &g, cudaStream_t s, int op, int src, int dst, float coef, int check_act,
                          int sum_slot, const LaunchCfg &lc);
 

@@ -787,11 +787,160 @@ __global__ void __launch_bounds__(kSweepThreads, 3) k_sweep_single(DevGrid g, in
 }
 
 // ---------------------------------------------------------------------------
+// Single stencils over j-runs: the layout of the fused j-run sweep for a
+// 1-voxel halo.  A run piece of G leaves takes 8G + 2 consecutive lanes, j =
+// -1 .. 8G from its lowest leaf; the two outer lanes hold only the x rows of
+// the j-neighbour leaves, so every output lane takes its j - 1 / j + 1 rows
+// by shuffle and no lane loads an edge row.  Tasks: one piece of three (26
+// lanes), a piece of two with a piece of one (28 lanes) or alone, or three
+// pieces of one (30 lanes).  Every output takes the same operands in the
+// same order as in k_sweep_single (an edge lane's outer row there is the
+// x-only lane's row here), so the results are identical.
+// ---------------------------------------------------------------------------
+// This lane's list entry and column lj (-1 .. 8, relative to that entry's
+// leaf) in task t; false for lanes outside every piece.
+__device__ __forceinline__ bool jrun1_lane(const DevGrid &g, int t, int c3, int c2, int c1, int &e, int &lj)
+{
+    const int lane = lane_id();
+    const long long cap3 = g.cap * 3;
+    const int p = c2 < c1 ? c2 : c1;
+    const int32_t *rec = nullptr;
+    int G = 0, start = 0;
+    if (t < c3) {
+        if (lane < 26) { rec = g.col_grp + 2 * cap3 + 3LL * t; G = 3; }
+    } else if (t < c3 + c2) {
+        const int r = t - c3;
+        if (lane < 18) { rec = g.col_grp + cap3 + 3LL * r; G = 2; }
+        else if (lane < 28 && r < p) { rec = g.col_grp + 3LL * r; G = 1; start = 18; }
+    } else {
+        const int k = lane / 10, q = p + 3 * (t - c3 - c2) + k;
+        if (k < 3 && q < c1) { rec = g.col_grp + 3LL * q; G = 1; start = 10 * k; }
+    }
+    if (!rec) return false;
+    const int jj = lane - start - 1;                    // -1 .. 8G
+    const int m = jj < 0 ? 0 : min(jj >> 3, G - 1);
+    lj = jj - 8 * m;
+    e = __ldg(rec + m);
+    return true;
+}
+
+template <int OP, bool CHECK, bool SUM>
+__device__ __forceinline__ float sweep_single_jrun_lane(const DevGrid &g, const float *__restrict__ x,
+                                                        float *__restrict__ y, float coef, int e, int lj, bool valid)
+{
+    const uint8_t *__restrict__ mb = reinterpret_cast<const uint8_t *>(g.mask);
+    const int djx = lj < 0 ? 0 : (lj < 8 ? 1 : 2);  // the row's leaf: j-1, own, j+1
+    const int lr = lj & 7;                           // the row's local j there
+    const bool outlane = valid && lj >= 0 && lj <= 7;
+    const float c6 = 1.f - 6.f * coef;
+    const int Z = (int)g.cap;  // the zero leaf
+    int sl[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) sl[q] = valid ? __ldg(g.nbr + (long long)e * 27 + (q / 3) * 9 + djx * 3 + (q % 3)) : Z;
+    const int own = sl[4];  // the entry's own leaf for the output lanes
+    float xa[10], xb[10], xc[10], xn[10];
+#pragma unroll
+    for (int q = 0; q < 10; ++q) xn[q] = 0.f;
+    row10(x, sl[0], sl[1], sl[2], plane_li<1>(0) * 8 + lr, xa);
+    row10(x, sl[3], sl[4], sl[5], plane_li<1>(1) * 8 + lr, xb);
+    row10(x, sl[3], sl[4], sl[5], plane_li<1>(2) * 8 + lr, xc);
+    float p1[10], p2[10];
+    float part = 0.f;
+    if (OP == SW_BOX27) {
+        // j-sums of planes 0 and 1
+        float up[10], dn[10];
+        shfl_row<10>(xa, up, dn);
+#pragma unroll
+        for (int q = 0; q < 10; ++q) p2[q] = (up[q] + xa[q]) + dn[q];
+        shfl_row<10>(xb, up, dn);
+#pragma unroll
+        for (int q = 0; q < 10; ++q) p1[q] = (up[q] + xb[q]) + dn[q];
+    }
+#pragma unroll
+    for (int oi = 0; oi < 8; ++oi) {
+        const uint32_t bits = outlane ? __ldg(mb + (long long)own * 64 + oi * 8 + lr) : 0u;
+        float o[8];
+        if (oi + 3 <= 9) {  // prefetch plane oi + 3
+            const int ri = oi + 3, dx = plane_di<1>(ri) * 3;
+            row10(x, sl[dx], sl[dx + 1], sl[dx + 2], plane_li<1>(ri) * 8 + lr, xn);
+        }
+        float up[10], dn[10];
+        if (OP == SW_DIFFUSE7) {
+            // t on plane oi + 1 from planes oi, oi + 1, oi + 2
+            shfl_row<10>(xb, up, dn);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int q = k + 1;
+                const float nb = ((xb[q - 1] + xb[q + 1]) + (xa[q] + xc[q])) + (up[q] + dn[q]);
+                o[k] = pick(bits, k, fmaf(coef, nb, c6 * xb[q]));
+            }
+#pragma unroll
+            for (int q = 0; q < 10; ++q) {
+                xa[q] = xb[q];
+                xb[q] = xc[q];
+                xc[q] = xn[q];
+            }
+        } else {
+            // j-sum of plane oi + 2; output plane oi
+            float p0[10], S[10];
+            shfl_row<10>(xc, up, dn);
+#pragma unroll
+            for (int q = 0; q < 10; ++q) p0[q] = (up[q] + xc[q]) + dn[q];
+#pragma unroll
+            for (int q = 0; q < 10; ++q) S[q] = (p2[q] + p1[q]) + p0[q];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) o[k] = pick(bits, k, ((S[k] + S[k + 1]) + S[k + 2]) * (1.f / 27.f));
+#pragma unroll
+            for (int q = 0; q < 10; ++q) {
+                p2[q] = p1[q];
+                p1[q] = p0[q];
+                xc[q] = xn[q];
+            }
+        }
+        if (outlane) {
+            const int orow = oi * 8 + lr;
+            if (CHECK) sweep_check_row(g, own, orow, bits);
+            float *op = y + (long long)own * 512 + orow * 8;
+            stg4(op, o[0], o[1], o[2], o[3]);
+            stg4(op + 4, o[4], o[5], o[6], o[7]);
+            if (SUM) part += ((o[0] + o[1]) + (o[2] + o[3])) + ((o[4] + o[5]) + (o[6] + o[7]));
+        }
+    }
+    return part;
+}
+
+template <int OP, bool CHECK, bool SUM>
+__global__ void __launch_bounds__(kSweepThreads, 4) k_sweep_single_jruns(DevGrid g, int src, int dst, float coef,
+                                                                        int sum_slot)
+{
+    __shared__ double s_red[kSweepThreads / 32];
+    const int c3 = g.col_cnt[2], c2 = g.col_cnt[1], c1 = g.col_cnt[0];
+    const int p = c2 < c1 ? c2 : c1;
+    const int tasks = c3 + c2 + (c1 - p + 2) / 3;
+    const int warps_total = gridDim.x * (kSweepThreads / 32);
+    double acc = 0.0;
+    for (int t = blockIdx.x * (kSweepThreads / 32) + (threadIdx.x >> 5); t < tasks; t += warps_total) {
+        int e = 0, lj = 0;
+        const bool valid = jrun1_lane(g, t, c3, c2, c1, e, lj);
+        acc += (double)sweep_single_jrun_lane<OP, CHECK, SUM>(g, g.field[src], g.field[dst], coef, e, lj, valid);
+    }
+    if (SUM) {
+        acc = warp_sum(acc);
+        if (lane_id() == 0) s_red[threadIdx.x >> 5] = acc;
+        __syncthreads();
+        double tot = 0.0;
+        if (threadIdx.x == 0)
+            for (int w = 0; w < kSweepThreads / 32; ++w) tot += s_red[w];
+        finish_reduction(g, tot, sum_slot);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Launch wrappers
 // ---------------------------------------------------------------------------
 static int sweep_ctas(int num_sms, int which)
 {
-    static std::atomic<int> cache[4];  // threads may race to fill it
+    static std::atomic<int> cache[5];  // threads may race to fill it
     if (cache[which].load(std::memory_order_relaxed) == 0) {
         int per = 1;
         cudaError_t err;
@@ -801,8 +950,11 @@ static int sweep_ctas(int num_sms, int which)
             err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sweep_single<SW_BOX27, false, true>, kSweepThreads, 0);
         else if (which == 2)
             err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sweep_columns<false, false, true>, kSweepThreads, 0);
-        else
+        else if (which == 3)
             err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sweep_jruns<false, false, true>, kSweepThreads, 0);
+        else
+            err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sweep_single_jruns<SW_BOX27, false, true>,
+                                                                kSweepThreads, 0);
         if (err != cudaSuccess || per < 1) per = 1;
         cache[which].store(per, std::memory_order_relaxed);
     }
@@ -860,8 +1012,21 @@ void launch_sweep_jruns(const DevGrid &g, cudaStream_t s, int src, int tmp, int 
 void launch_sweep_single(const DevGrid &g, cudaStream_t s, int op, int src, int dst, float coef, int check_act,
                          int sum_slot, const LaunchCfg &lc)
 {
-    const int ctas = sweep_ctas(lc.num_sms, 1);
     const bool sum = sum_slot >= 0;
+    if (lc.single_runs) {
+        const int ctas = sweep_ctas(lc.num_sms, 4);
+#define SG_SR(OP, CK, SU) k_sweep_single_jruns<OP, CK, SU><<<ctas, kSweepThreads, 0, s>>>(g, src, dst, coef, sum_slot)
+        if (op == SW_DIFFUSE7) {
+            if (check_act) { if (sum) SG_SR(SW_DIFFUSE7, true, true); else SG_SR(SW_DIFFUSE7, true, false); }
+            else { if (sum) SG_SR(SW_DIFFUSE7, false, true); else SG_SR(SW_DIFFUSE7, false, false); }
+        } else {
+            if (check_act) { if (sum) SG_SR(SW_BOX27, true, true); else SG_SR(SW_BOX27, true, false); }
+            else { if (sum) SG_SR(SW_BOX27, false, true); else SG_SR(SW_BOX27, false, false); }
+        }
+#undef SG_SR
+        return;
+    }
+    const int ctas = sweep_ctas(lc.num_sms, 1);
 #define SG_SS(OP, CK, SU) k_sweep_single<OP, CK, SU><<<ctas, kSweepThreads, 0, s>>>(g, src, dst, coef, sum_slot)
     if (op == SW_DIFFUSE7) {
         if (check_act) { if (sum) SG_SS(SW_DIFFUSE7, true, true); else SG_SS(SW_DIFFUSE7, true, false); }

@@ -393,6 +393,44 @@ def test_grouped_sweeps_equal_leaf_sweep(store_t, grouped):
         g.close()
 
 
+@pytest.mark.parametrize("mode", ["no_fuse", "no_fuse_no_ad"])
+def test_single_jruns_equal_leaf_sweep(mode):
+    """Without fusion the stencils run one by one; on a large reused list they
+    sweep j-runs from the third stencil on (k_sweep_single_jruns: x-only outer
+    lanes, no edge rows), under the leaf-triple variant k_sweep_single.  Each
+    output takes the same operands in the same order, so six steps on the
+    512^3 band give bit-identical fields and sums; without activation demotion
+    every written row is also checked against the mask (the kernels' checking
+    instances)."""
+    sg = sgmod()
+    spec = band512()
+    opts = 15 & ~4 if mode == "no_fuse" else 15 & ~6
+    grids = []
+    for variant in (sg.SG_VARIANT_SWEEP_JRUNS, sg.SG_VARIANT_SWEEP):
+        g = sg.Grid(spec.N, 3, 3, max_leaves=32768, max_sums=6, scratch_mask=0b010)
+        g.set_opts(opts)
+        g.set_stencil_variant(variant)
+        g.activate_shell(spec.lo2, spec.hi2, spec.lo_strict)
+        g.fill_hash(0, 43)
+        g.sync()                                  # the leaf count the switch looks at
+        grids.append(g)
+    for s in range(6):
+        for g in grids:
+            g.clear(1)
+            g.diffuse7(0, 1, 0.1)
+            g.box27(1, 2)
+            g.swap(0, 2)
+            g.reduce_sum(0, s)
+            g.flush()
+    a, b = grids
+    assert a.stats()["launches"] == b.stats()["launches"] + 1   # the run records, built once
+    np.testing.assert_array_equal(a.read_field(0), b.read_field(0))
+    np.testing.assert_array_equal(a.read_field(1), b.read_field(1))
+    np.testing.assert_array_equal(a.read_sums(6), b.read_sums(6))
+    for g in grids:
+        g.close()
+
+
 @pytest.mark.parametrize("variant", [0, 1, 2, 3, 4])
 def test_fused_steps_across_structure_changes(variant):
     """Fused steps; a wider band activated (new leaves, new bits in listed
