@@ -275,6 +275,56 @@ bool read_later(const sg_grid *g, size_t from, int f)
     return false;
 }
 
+// The physical fields a leaf allocated by the activation at queue[i] is
+// zero-filled in.  With SG_OPT_DSE the fill is a store like any other
+// (Sec. 6.5): it is dead in a field whose next access in the queue is a full
+// overwrite by a struct-for over the (then current) list, and in a field the
+// rest of the flush does not touch that holds a scratch field, whose
+// contents no later flush may read.  A read, a partial write (a staged
+// upload, the particle ops), a fill or a structure change keeps it.
+uint32_t activation_fill_mask(const sg_grid *g, size_t i)
+{
+    const int F = g->dev.F;
+    const uint32_t all = F >= 32 ? 0xffffffffu : ((1u << F) - 1u);
+    if (!(g->opts & SG_OPT_DSE)) return all;
+    uint32_t scratch_phys = 0;
+    for (int f = 0; f < F; ++f)
+        if ((g->desc.scratch_mask >> f) & 1u) scratch_phys |= 1u << g->phys[f];
+    uint32_t mask = 0;
+    for (int pf = 0; pf < F; ++pf) {
+        int first = 0;  // 0: untouched, 1: read or kept, 2: fully overwritten
+        for (size_t k = i + 1; k < g->queue.size() && first == 0; ++k) {
+            const Op &o = g->queue[k];
+            switch (o.kind) {
+                case OP_LISTGEN:
+                    break;
+                case OP_STENCIL:
+                    if (o.op != SG_CLEAR && o.src == pf) first = 1;
+                    else if (o.dst == pf) first = 2;
+                    break;
+                case OP_SUM:
+                    if (o.src == pf) first = 1;
+                    break;
+                case OP_EW:
+                    if (o.src == pf || o.i0 == pf) first = 1;
+                    else if (o.dst == pf) first = 2;
+                    break;
+                case OP_ADVECT:
+                case OP_MAC:
+                    if (o.src == pf || (pf >= o.i0 && pf < o.i0 + 3) || (o.kind == OP_MAC && (o.i1 == pf || o.i2 == pf)))
+                        first = 1;
+                    else if (o.dst == pf) first = 2;
+                    break;
+                default:
+                    first = 1;  // conservative
+            }
+        }
+        const bool dead = first == 2 || (first == 0 && ((scratch_phys >> pf) & 1u));
+        if (!dead) mask |= 1u << pf;
+    }
+    return mask;
+}
+
 // Dead-store test for a clear at queue[i]: the next access to its field in
 // the queue is a full overwrite by a struct-for over the same list.
 bool clear_is_dead(const sg_grid *g, size_t i)
@@ -847,9 +897,13 @@ int do_flush(sg_grid *g)
                 if ((g->opts & SG_OPT_AD) && g->applied_shells.count(sig)) {
                     g->stats.act_demoted++;
                 } else {
+                    const uint32_t fill = activation_fill_mask(g, i);
+                    const int F = g->dev.F;
+                    for (int f = 0; f < F; ++f)
+                        if (!((fill >> f) & 1u)) g->stats.stores_removed++;
                     if (!g->dry) {
-                        if (o.op) launch_activate_tube(g->dev, g->stream, o.lo2, o.hi2);
-                        else launch_activate_shell(g->dev, g->stream, o.lo2, o.hi2, o.strict);
+                        if (o.op) launch_activate_tube(g->dev, g->stream, o.lo2, o.hi2, fill);
+                        else launch_activate_shell(g->dev, g->stream, o.lo2, o.hi2, o.strict, fill);
                     }
                     g->applied_shells.insert(sig);
                     g->stats.act_launched++;

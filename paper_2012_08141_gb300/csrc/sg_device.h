@@ -121,7 +121,11 @@ constexpr int kListThreads = 256;
 constexpr int kSpinLimit = 1 << 22;  // bounded waits: polls before giving up
 
 // ---- structure kernels (sg_structure.cu) ----
-void launch_activate_shell(const DevGrid &g, cudaStream_t s, long long lo2, long long hi2, int strict);
+// fill_mask: the physical fields a newly allocated leaf is zero-filled in
+// (bit f for field f; all of them unless the caller knows a field's zeros are
+// never read).
+void launch_activate_shell(const DevGrid &g, cudaStream_t s, long long lo2, long long hi2, int strict,
+                           uint32_t fill_mask);
 void launch_mark_coords(const DevGrid &g, cudaStream_t s, const int32_t *xyz, long long n);
 void launch_alloc_needed(const DevGrid &g, cudaStream_t s);
 void launch_setbits_coords(const DevGrid &g, cudaStream_t s, const int32_t *xyz, long long n);
@@ -291,7 +295,7 @@ void launch_advect_group(const DevGrid &g, cudaStream_t s, int mode, int C, cons
                          const float4 *vel4, const LaunchCfg &lc);
 // vel4 ((cap + 1) * L^3 float4): the listed leaves' velocity (fields v0..v0+2)
 void launch_pack_velocity(const DevGrid &g, cudaStream_t s, int v0, float4 *vel4, const LaunchCfg &lc);
-void launch_activate_tube(const DevGrid &g, cudaStream_t s, long long lo2, long long hi2);
+void launch_activate_tube(const DevGrid &g, cudaStream_t s, long long lo2, long long hi2, uint32_t fill_mask);
 
 // ---- fused element-wise struct-fors (sg_elementwise.cu) ----
 constexpr int kMaxEwOps = 16;   // ops (and at most one reduction) per fused launch

@@ -40,14 +40,22 @@ __device__ __forceinline__ int clamp_pred(long long v)
 // large domains, where the lanes cull 32 cells at once and the warp's new
 // leaves take their pool slots with one atomic; 1 on small ones, where a warp
 // per cell keeps every cell in flight at once).
+// fill_mask: the (physical) fields a newly allocated leaf is zero-filled in.
+// Cell indices are 32-bit (R^3 <= 2^30).  For 8^3 leaves, word w of a cell
+// holds voxels l = 32w + lane: local i = w / 2 (the same for the whole warp),
+// j = lane / 8 + 4 (w & 1), k = lane & 7, so a lane forms its two j^2 + k^2
+// terms once per cell and each word adds the warp's i^2.
+template <int L>
 __global__ void __launch_bounds__(256) k_activate_shell(DevGrid g, long long lo2_, long long hi2_, int strict, int tube,
-                                                        int cpw)
+                                                        int cpw, uint32_t fill_mask)
 {
+    constexpr int LG2 = (L == 8) ? 3 : 2, W = L * L * L / 32;
     constexpr int kMaxW = 16;  // mask words of an 8^3 leaf
     __shared__ uint32_t s_bits[8][32][kMaxW];  // per warp: the mask words of its chunk's cells
     const int lane = lane_id(), warp = threadIdx.x >> 5;
-    const long long nr = (long long)g.R * g.R * g.R;
-    const int R = g.R, L = g.L, lg2 = g.lg2, N = g.N, W = g.W;
+    const int R = g.R, N = g.N;
+    const unsigned RR = (unsigned)R * (unsigned)R;
+    const long long nr = (long long)R * R * R;
     const int lo2 = clamp_pred(lo2_), hi2 = clamp_pred(hi2_);
     const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
     for (long long c0 = ((long long)blockIdx.x * (blockDim.x >> 5) + warp) * cpw; c0 < nr; c0 += warps * cpw) {
@@ -55,11 +63,12 @@ __global__ void __launch_bounds__(256) k_activate_shell(DevGrid g, long long lo2
         bool cand = false;
         const long long bq = c0 + lane;
         if (lane < cpw && bq < nr) {
-            const int bi = (int)(bq / ((long long)R * R)), bj = (int)((bq / R) % R), bk = (int)(bq % R);
+            const unsigned b = (unsigned)bq, bi = b / RR, rem = b - bi * RR, bj = rem / (unsigned)R,
+                           bk = rem - bj * (unsigned)R;
             int dmin = 0, dmax = 0;
-            axis_range(bi * L, L, N, dmin, dmax);
-            axis_range(bj * L, L, N, dmin, dmax);
-            if (!tube) axis_range(bk * L, L, N, dmin, dmax);
+            axis_range((int)bi * L, L, N, dmin, dmax);
+            axis_range((int)bj * L, L, N, dmin, dmax);
+            if (!tube) axis_range((int)bk * L, L, N, dmin, dmax);
             const bool lo_possible = strict ? (dmax > lo2) : (dmax >= lo2);
             cand = lo_possible && dmin < hi2;
         }
@@ -69,19 +78,35 @@ __global__ void __launch_bounds__(256) k_activate_shell(DevGrid g, long long lo2
         while (todo) {
             const int q = __ffs(todo) - 1;
             todo &= todo - 1;
-            const long long b = c0 + q;
-            const int bi = (int)(b / ((long long)R * R)), bj = (int)((b / R) % R), bk = (int)(b % R);
+            const unsigned b = (unsigned)(c0 + q), bi = b / RR, rem = b - bi * RR, bj = rem / (unsigned)R,
+                           bk = rem - bj * (unsigned)R;
             uint32_t bits = 0;
-            for (int w = 0; w < W; ++w) {
-                const int l = w * 32 + lane;
-                const int li = l >> (2 * lg2), lj = (l >> lg2) & (L - 1), lk = l & (L - 1);
-                const int a = 2 * (bi * L + li) + 1 - N;
-                const int c = 2 * (bj * L + lj) + 1 - N;
-                const int d = 2 * (bk * L + lk) + 1 - N;
-                const int D = a * a + c * c + (tube ? 0 : d * d);
-                const bool on = (strict ? (lo2 < D) : (lo2 <= D)) && (D < hi2);
-                const unsigned word = __ballot_sync(kFull, on);
-                if (lane == w) bits = word;
+            if (L == 8) {
+                const int d = 2 * ((int)bk * 8 + (lane & 7)) + 1 - N;
+                const int dd = tube ? 0 : d * d;
+                const int cA = 2 * ((int)bj * 8 + (lane >> 3)) + 1 - N, cB = cA + 8;
+                const int e0 = cA * cA + dd, e1 = cB * cB + dd;
+#pragma unroll
+                for (int w = 0; w < W; ++w) {
+                    const int a = 2 * ((int)bi * 8 + (w >> 1)) + 1 - N;
+                    const int D = a * a + ((w & 1) ? e1 : e0);
+                    const bool on = (strict ? (lo2 < D) : (lo2 <= D)) && (D < hi2);
+                    const unsigned word = __ballot_sync(kFull, on);
+                    if (lane == w) bits = word;
+                }
+            } else {
+#pragma unroll
+                for (int w = 0; w < W; ++w) {
+                    const int l = w * 32 + lane;
+                    const int li = l >> (2 * LG2), lj = (l >> LG2) & (L - 1), lk = l & (L - 1);
+                    const int a = 2 * ((int)bi * L + li) + 1 - N;
+                    const int c = 2 * ((int)bj * L + lj) + 1 - N;
+                    const int d = 2 * ((int)bk * L + lk) + 1 - N;
+                    const int D = a * a + c * c + (tube ? 0 : d * d);
+                    const bool on = (strict ? (lo2 < D) : (lo2 <= D)) && (D < hi2);
+                    const unsigned word = __ballot_sync(kFull, on);
+                    if (lane == w) bits = word;
+                }
             }
             if (lane < W) s_bits[warp][q][lane] = bits;
             const bool nz = __any_sync(kFull, bits != 0u);
@@ -118,10 +143,11 @@ __global__ void __launch_bounds__(256) k_activate_shell(DevGrid g, long long lo2
             work &= work - 1;
             const int sq = __shfl_sync(kFull, slot, q);
             const bool fq = __shfl_sync(kFull, fresh, q);
-            const int V = L * L * L;
+            constexpr int V = L * L * L;
             if (fq) {
                 const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
                 for (int f = 0; f < g.F; ++f) {
+                    if (!((fill_mask >> f) & 1u)) continue;
                     float4 *p = reinterpret_cast<float4 *>(g.field[f] + (long long)sq * V);
                     for (int qq = lane; qq < V / 4; qq += 32) p[qq] = z;
                 }
@@ -154,20 +180,23 @@ static void activate_shape(long long nr, int &cpw, int &ctas)
     ctas = (int)(cpw == 1 ? (want > 0 ? want : 1) : (want < kMaxCtas ? want : kMaxCtas));
 }
 
-void launch_activate_shell(const DevGrid &g, cudaStream_t s, long long lo2, long long hi2, int strict)
+void launch_activate_shell(const DevGrid &g, cudaStream_t s, long long lo2, long long hi2, int strict,
+                           uint32_t fill_mask)
 {
     const long long nr = (long long)g.R * g.R * g.R;
     int cpw, ctas;
     activate_shape(nr, cpw, ctas);
-    k_activate_shell<<<ctas, 256, 0, s>>>(g, lo2, hi2, strict, 0, cpw);
+    if (g.L == 8) k_activate_shell<8><<<ctas, 256, 0, s>>>(g, lo2, hi2, strict, 0, cpw, fill_mask);
+    else k_activate_shell<4><<<ctas, 256, 0, s>>>(g, lo2, hi2, strict, 0, cpw, fill_mask);
 }
 
-void launch_activate_tube(const DevGrid &g, cudaStream_t s, long long lo2, long long hi2)
+void launch_activate_tube(const DevGrid &g, cudaStream_t s, long long lo2, long long hi2, uint32_t fill_mask)
 {
     const long long nr = (long long)g.R * g.R * g.R;
     int cpw, ctas;
     activate_shape(nr, cpw, ctas);
-    k_activate_shell<<<ctas, 256, 0, s>>>(g, lo2, hi2, 0, 1, cpw);
+    if (g.L == 8) k_activate_shell<8><<<ctas, 256, 0, s>>>(g, lo2, hi2, 0, 1, cpw, fill_mask);
+    else k_activate_shell<4><<<ctas, 256, 0, s>>>(g, lo2, hi2, 0, 1, cpw, fill_mask);
 }
 
 // ---------------------------------------------------------------------------

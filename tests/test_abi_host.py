@@ -145,11 +145,38 @@ def test_band_step_launch_counts():
     f.activate_shell(s.lo2, s.hi2, s.lo_strict)
     f.list_gen()
     f.flush()
+    # the activation's zero-fill of the scratch field t is dead: nothing in
+    # its flush touches t
+    assert f.stats()["stores_removed"] == 1
     # the first fused step also builds the region-mask table cached with the list
     assert [launches(f, lambda: cfg2_step(f, 0)) for _ in range(3)] == [2, 1, 1]
     st = f.stats()
-    assert st["stores_removed"] == 6        # per step: the clear of t and the store of t
+    assert st["stores_removed"] == 1 + 6    # per step: the clear of t and the store of t
     assert st["ops_fused"] == 6             # per step: box27 and the sum ride in diffuse7's kernel
+
+
+def test_activation_zero_fill_is_a_store():
+    """Sec. 6.5 applied to activation: a new leaf's zero-fill in a field is
+    dead when the field's next access in the queue is a full overwrite by a
+    struct-for, or when the rest of the flush leaves a scratch field alone; a
+    field read first (or a non-scratch field left alone) keeps it, and
+    without DSE every fill stays.  Counted in stores_removed."""
+    def removed(opts, body):
+        g = dry(F=4, scratch=0b0010)
+        g.set_opts(opts)
+        s0 = g.stats()["stores_removed"]
+        g.deactivate_all()
+        g.activate_shell(100, 400, False)
+        body(g)
+        g.flush()
+        return g.stats()["stores_removed"] - s0
+    # field 1 scratch: t of the fused step; 2 fully written; 0 read; 3 untouched
+    fused = lambda g: (g.diffuse7(0, 1, 0.1), g.box27(1, 2))
+    assert removed(sg.SG_OPT_ALL, fused) == 2 + 1      # fills of 1 and 2; t's store
+    assert removed(sg.SG_OPT_ALL, lambda g: None) == 1  # only the scratch field's fill
+    assert removed(sg.SG_OPT_ALL, lambda g: g.ew(2, 2, alpha=2.0)) == 1   # 2 read first: kept
+    assert removed(sg.SG_OPT_ALL, lambda g: g.ew(2, 0, alpha=2.0)) == 2   # 2 overwritten
+    assert removed(sg.SG_OPT_ALL & ~sg.SG_OPT_DSE, fused) == 0
 
 
 @pytest.mark.parametrize("opts,expect", [
