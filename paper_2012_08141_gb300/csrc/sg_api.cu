@@ -914,9 +914,12 @@ int do_flush(sg_grid *g)
                 break;
             }
             case OP_ACT_COORDS: {
+                const uint32_t fill = activation_fill_mask(g, i);
+                for (int f = 0; f < g->dev.F; ++f)
+                    if (!((fill >> f) & 1u)) g->stats.stores_removed++;
                 if (!g->dry) launch_mark_coords(g->dev, g->stream, (const int32_t *)o.p0, o.n);
                 if (!(rc = after_launch(g, "mark coords"))) {
-                    if (!g->dry) launch_alloc_needed(g->dev, g->stream);
+                    if (!g->dry) launch_alloc_needed(g->dev, g->stream, fill);
                     if (!(rc = after_launch(g, "allocate"))) {
                         if (!g->dry) launch_setbits_coords(g->dev, g->stream, (const int32_t *)o.p0, o.n);
                         rc = after_launch(g, "set bits");

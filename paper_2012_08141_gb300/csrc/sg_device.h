@@ -127,7 +127,8 @@ constexpr int kSpinLimit = 1 << 22;  // bounded waits: polls before giving up
 void launch_activate_shell(const DevGrid &g, cudaStream_t s, long long lo2, long long hi2, int strict,
                            uint32_t fill_mask);
 void launch_mark_coords(const DevGrid &g, cudaStream_t s, const int32_t *xyz, long long n);
-void launch_alloc_needed(const DevGrid &g, cudaStream_t s);
+// fill_mask as for launch_activate_shell (default: every field)
+void launch_alloc_needed(const DevGrid &g, cudaStream_t s, uint32_t fill_mask = 0xffffffffu);
 void launch_setbits_coords(const DevGrid &g, cudaStream_t s, const int32_t *xyz, long long n);
 void launch_deactivate_all(const DevGrid &g, cudaStream_t s);
 // Invariant checks (sg_check): violation counters, indexed by CheckKind.

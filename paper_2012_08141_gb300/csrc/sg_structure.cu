@@ -224,7 +224,8 @@ void launch_mark_coords(const DevGrid &g, cudaStream_t s, const int32_t *xyz, lo
     k_mark_coords<<<(unsigned)blocks, 256, 0, s>>>(g, xyz, n);
 }
 
-__global__ void __launch_bounds__(256) k_alloc_needed(DevGrid g)
+// fill_mask: the (physical) fields a newly allocated leaf is zero-filled in.
+__global__ void __launch_bounds__(256) k_alloc_needed(DevGrid g, uint32_t fill_mask)
 {
     const long long nr = (long long)g.R * g.R * g.R;
     const int lane = lane_id();
@@ -255,6 +256,7 @@ __global__ void __launch_bounds__(256) k_alloc_needed(DevGrid g)
             const int s = __shfl_sync(kFull, slot, src);
             const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
             for (int f = 0; f < g.F; ++f) {
+                if (!((fill_mask >> f) & 1u)) continue;
                 float4 *p = reinterpret_cast<float4 *>(g.field[f] + (long long)s * V);
                 for (int q = lane; q < V / 4; q += 32) p[q] = z;
             }
@@ -270,12 +272,12 @@ __global__ void __launch_bounds__(256) k_alloc_needed(DevGrid g)
     if (any_alloc) mark_dirty(g);
 }
 
-void launch_alloc_needed(const DevGrid &g, cudaStream_t s)
+void launch_alloc_needed(const DevGrid &g, cudaStream_t s, uint32_t fill_mask)
 {
     const long long nr = (long long)g.R * g.R * g.R;
     long long blocks = (nr + 255) / 256;
     if (blocks > 4096) blocks = 4096;
-    k_alloc_needed<<<(unsigned)blocks, 256, 0, s>>>(g);
+    k_alloc_needed<<<(unsigned)blocks, 256, 0, s>>>(g, fill_mask);
 }
 
 __global__ void k_setbits_coords(DevGrid g, const int32_t *__restrict__ xyz, long long n)
