@@ -152,3 +152,22 @@ def test_injected_allocation_failure_fails_one_job_only():
     assert set(srv.live) <= set(live_a)         # b's partial grid and finished jobs freed
     srv.close()
     assert not srv.live
+
+
+def test_close_with_work_in_flight():
+    """A tick returns with its step running and the next admissions queued
+    behind it; closing the server then waits for that work and frees every
+    grid (each allocation goes through the server's callbacks)."""
+    from paper_2012_08141_gb300.serve import SG_JOB_RUNNING, Server
+    srv = Server(max_jobs=4, hbm_reserve=0, fail_alloc=lambda i, n: False)
+    specs = batched_mix(13, n_grids=3, lo=1e4, hi=5e4)
+    a = srv.submit(specs[0], 5)
+    b = srv.submit(specs[1], 5)
+    srv.tick()                                   # a and b admitted: their work queued
+    srv.tick()                                   # their first step launched, not waited for
+    c = srv.submit(specs[2], 5)
+    srv.tick()                                   # the next step launched, c's admission behind it
+    assert all(srv.job(j)["state"] == SG_JOB_RUNNING for j in (a, b, c))
+    assert srv.stats()["resident"] == 3
+    srv.close()
+    assert not srv.live

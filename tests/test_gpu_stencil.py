@@ -244,6 +244,38 @@ def test_activation_zero_fills_after_values():
     g.close()
 
 
+def test_activation_fill_elimination_on_reused_slots():
+    """After a deactivation the pool's slots still hold the old values.  With
+    dead-store elimination a re-activation zero-fills a new leaf only in the
+    fields the queue reads (or leaves alone) before overwriting them; every
+    non-scratch field then holds exactly what the ops wrote: 0 at inactive
+    voxels, the written values at active ones, zeros where it was read
+    first.  Without DSE every field is filled; the results are the same."""
+    sg = sgmod()
+    A = band_bounds(12.0, 20.0)
+    B = band_bounds(13.0, 21.0)
+    for opts in (15, 15 & ~8):
+        g = sg.Grid(64, 3, 4, max_leaves=512, scratch_mask=0b0010)
+        g.set_opts(opts)
+        g.activate_shell(A[0], A[1], True)
+        for f in range(4):
+            g.ew(f, delta=7.0)                     # stale values in every field's slots
+        g.sync()
+        g.deactivate_all()
+        g.activate_shell(B[0], B[1], True)        # the same slots, other cells
+        g.ew(2, delta=3.0)                         # 2 overwritten first: its fill is dead
+        g.diffuse7(0, 3, 0.1)                      # 0 read first (filled); 3 overwritten
+        g.sync()
+        b, m = g.read_structure()
+        act = mask_bits(m, 512)
+        assert act.sum() > 0
+        v0, v2, v3 = g.read_field(0), g.read_field(2), g.read_field(3)
+        assert np.all(v0 == 0.0)
+        assert np.all(v2[act] == 3.0) and np.all(v2[~act] == 0.0)
+        assert np.all(v3 == 0.0)
+        g.close()
+
+
 def test_deactivate_and_reactivate():
     spec = tiny_shell(1)
     g, og = shell_pair(spec, n_fields=2)
