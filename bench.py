@@ -450,13 +450,39 @@ def bench_particles(torch, sg, steps, warmup, flush_buf, stream):
     g.sync()
     leaves = g.num_leaves()
     g.close()
+    # the same step with the particle arrays (and the caller's ids) reordered
+    # into bin order every 10 steps (sg_sort_particles), the sort inside the
+    # timed steps that run it
+    gs = sg.Grid(spec.N, 2, 4, max_leaves=(spec.N // 4) ** 3, max_sums=1)
+    xs = torch.from_numpy(spec.x).cuda()
+    vs = torch.from_numpy(spec.v).cuda()
+    ids = torch.arange(spec.n, dtype=torch.int64, device="cuda")
+    k = [0]
+
+    def sorted_step():
+        gs.deactivate_all()
+        gs.p2g(xs, vs, spec.pmass, 0, 1)
+        gs.grid_update(0, 1, spec.dt, spec.gravity, spec.bound)
+        gs.g2p(xs, vs, spec.dt, 1)
+        if k[0] % 10 == 0:
+            gs.sort_particles(xs, vs, ids=ids)
+        gs.flush()
+        k[0] += 1
+
+    ms_s, _ = time_steps(torch, sorted_step, max(steps, 20), warmup, flush_buf, stream)
+    gs.sync()
+    gs.close()
+    t_s = sum(ms_s) / 1e3
     return {"workload": "2M particles in 3 spheres, 256^3 grid of 4^3 leaves, P2G+grid update+G2P",
             "particles": spec.n, "leaves": leaves, "value": spec.n * steps / t, "unit": "particle-steps/s",
             "ms_per_step": t * 1e3 / steps, "launches_per_step": launches / steps,
             "l2": "flushed before every timed step (512 MB write)",
             "stream_bytes_per_particle": 72,
             "stream_hbm_frac": spec.n * 72 * steps / t / 1e9 / peaks()[0],
-            "grid_atomics_per_s": spec.n * 27 * 4 * steps / t}
+            "grid_atomics_per_s": spec.n * 27 * 4 * steps / t,
+            "sorted_every_10": {"ms_per_step": t_s * 1e3 / len(ms_s), "value": spec.n * len(ms_s) / t_s,
+                                "unit": "particle-steps/s", "steps": len(ms_s),
+                                "note": "arrays and int64 ids reordered into bin order every 10th step"}}
 
 
 def bench_mpm_apic(torch, sg, steps, warmup, flush_buf, stream):

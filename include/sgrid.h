@@ -302,6 +302,25 @@ int sg_g2p_apic(sg_grid *g, float *dev_x, float *dev_v, float *dev_C, int64_t n,
 int sg_g2p2g(sg_grid *src, sg_grid *dst, float *dev_x, float *dev_v, int64_t n, float dt, int32_t f_vel0,
              float pmass, int32_t f_mass, int32_t f_mom0);
 
+/* Queue a reordering of the particle arrays into the order of the last binned
+ * P2G of the same particles on g (dev_x and n as given to that sg_p2g or
+ * sg_p2g_apic, which must still be current: no other binning of other arrays
+ * since).  dev_x and dev_v (n*3 FP32), dev_C (n*9 FP32, APIC) and dev_ids (n
+ * int64, e.g. the caller's particle numbers) are each permuted in place by
+ * the same permutation -- dev_C and dev_ids may be NULL -- and the binning's
+ * order becomes the identity, so the bins stay valid for sg_g2p, sg_g2p_apic
+ * and sg_g2p2g.  Afterwards the particles of a leaf, and within it of a cell,
+ * are adjacent in memory: the next binnings, the P2G gather and G2P read and
+ * write them in order instead of one scattered 12-byte access each.  The
+ * particle order a caller sees changes; dev_ids says which particle is where.
+ * An addition of this library (the paper keeps particles in their own order);
+ * particles move little per step, so calling it every few steps keeps them
+ * ordered.  One gather kernel per array plus one reset, and a device copy per
+ * array (scratch: 36 bytes per particle, allocated at first use).  Arrays
+ * borrowed until the next sync.  Errors: SG_ERR_INVALID (bad arguments; at
+ * the flush, no current binning of these particles), SG_ERR_OOM. */
+int sg_sort_particles(sg_grid *g, float *dev_x, float *dev_v, float *dev_C, int64_t *dev_ids, int64_t n);
+
 /* Restriction onto a grid of half the edge (the multigrid pattern of Sec. 6.3,
  * Fig. 13): for every active voxel i of `fine`, activate voxel i // 2
  * (componentwise) of `coarse` and add w * fine[f_src][i] to coarse[f_dst]

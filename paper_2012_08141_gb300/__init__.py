@@ -95,6 +95,7 @@ def load_library(build: bool = True) -> ctypes.CDLL:
         "sg_p2g_apic": [P, P, P, P, I64, F, I32, I32],
         "sg_g2p_apic": [P, P, P, P, I64, F, I32],
         "sg_g2p2g": [P, P, P, P, I64, F, I32, F, I32, I32],
+        "sg_sort_particles": [P, P, P, P, P, I64],
         "sg_restrict": [P, P, I32, I32, F],
         "sg_launch_ew": [P, I32, I32, I32, F, F, F, F],
         "sg_activate_tube": [P, I64, I64],
@@ -334,6 +335,17 @@ class Grid:
             assert t.is_cuda and str(t.dtype) == "torch.float32" and t.is_contiguous()
         self._borrowed += [x, v]
         self._c(self.lib.sg_g2p(self.h, _ptr(x), _ptr(v), x.numel() // 3, float(dt), int(f_mom0)))
+
+    def sort_particles(self, x, v, C=None, ids=None):
+        """Queue the reordering of the particle arrays (and C, ids when given:
+        n x 9 float32, n int64) into the order of the last binned P2G of x."""
+        for t in (x, v) + tuple(a for a in (C,) if a is not None):
+            assert t.is_cuda and str(t.dtype) == "torch.float32" and t.is_contiguous()
+        if ids is not None:
+            assert ids.is_cuda and str(ids.dtype) == "torch.int64" and ids.is_contiguous()
+        self._borrowed += [t for t in (x, v, C, ids) if t is not None]
+        self._c(self.lib.sg_sort_particles(self.h, _ptr(x), _ptr(v), _ptr(C) if C is not None else None,
+                                           _ptr(ids) if ids is not None else None, x.numel() // 3))
 
     def swap(self, a: int, b: int):
         self._c(self.lib.sg_swap(self.h, int(a), int(b)))

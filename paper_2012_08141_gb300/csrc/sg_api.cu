@@ -53,7 +53,7 @@ int fail(int code, const char *fmt, ...)
 }
 
 enum OpKind { OP_ACT_SHELL, OP_ACT_COORDS, OP_DEACT, OP_LISTGEN, OP_STENCIL, OP_SUM, OP_P2G, OP_GRID_UPDATE, OP_G2P, OP_TEST_WAIT,
-              OP_FILL, OP_G2P2G, OP_EW, OP_ADVECT, OP_MAC, OP_WRITE_STAGED };
+              OP_FILL, OP_G2P2G, OP_EW, OP_ADVECT, OP_MAC, OP_WRITE_STAGED, OP_SORT_P };
 
 struct Op {
     OpKind kind;
@@ -112,6 +112,8 @@ struct sg_grid {
     Ctrl *host_ctrl = nullptr;  // pinned
     size_t staging_bytes = 0;
     long long perm_cap = 0;  // particles the binned-P2G order array holds
+    void *sort_tmp = nullptr;  // particle reordering scratch, 36 bytes per particle
+    long long sort_cap = 0;
     const void *p2g_x = nullptr;  // positions and count the order array was built for
     long long p2g_n = 0;
     unsigned long long *chk_cnt = nullptr;  // invariant-check counters (allocated at the first check)
@@ -297,6 +299,7 @@ uint32_t activation_fill_mask(const sg_grid *g, size_t i)
             const Op &o = g->queue[k];
             switch (o.kind) {
                 case OP_LISTGEN:
+                case OP_SORT_P:
                     break;
                 case OP_STENCIL:
                     if (o.op != SG_CLEAR && o.src == pf) first = 1;
@@ -1008,6 +1011,29 @@ int do_flush(sg_grid *g)
                 rc = after_launch(g, "g2p");
                 ++i;
                 break;
+            case OP_SORT_P: {
+                if (o.p0 != g->p2g_x || o.n != g->p2g_n) {
+                    rc = fail(SG_ERR_INVALID, "sort_particles: no binned P2G of these particles is current");
+                    ++i;
+                    break;
+                }
+                if (!g->dry && o.n > g->sort_cap) {
+                    g->sort_tmp = dev_alloc(g, (size_t)o.n * 36);
+                    if (!g->sort_tmp) {
+                        rc = fail(SG_ERR_OOM, "particle reordering scratch");
+                        ++i;
+                        break;
+                    }
+                    g->sort_cap = o.n;
+                }
+                const int k = g->dry ? 1 + (o.p0 ? 1 : 0) + (o.p1 ? 1 : 0) + (o.p2 ? 1 : 0) + (o.p3 ? 1 : 0)
+                                     : launch_sort_particles(g->dev, g->stream, (float *)o.p0, (float *)o.p1,
+                                                             (float *)o.p2, (int64_t *)o.p3, o.n, g->sort_tmp, g->lc);
+                g->stats.launches += k - 1;
+                rc = after_launch(g, "sort particles");
+                ++i;
+                break;
+            }
         }
     }
     g->queue.clear();
@@ -1525,6 +1551,20 @@ int sg_grid_update(sg_grid *g, int32_t f_mass, int32_t f_mom0, float dt, float g
 int sg_g2p(sg_grid *g, float *dev_x, float *dev_v, int64_t n, float dt, int32_t f_mom0)
 {
     return sg_g2p_apic(g, dev_x, dev_v, nullptr, n, dt, f_mom0);
+}
+
+int sg_sort_particles(sg_grid *g, float *dev_x, float *dev_v, float *dev_C, int64_t *dev_ids, int64_t n)
+{
+    if (!g || n < 0 || (n > 0 && (!dev_x || !dev_v))) return fail(SG_ERR_INVALID, "bad sort_particles arguments");
+    if (n == 0) return SG_OK;
+    if (n > INT32_MAX) return fail(SG_ERR_INVALID, "at most 2^31 - 1 particles");
+    Op o{OP_SORT_P};
+    o.p0 = dev_x;
+    o.p1 = dev_v;
+    o.p2 = dev_C;
+    o.p3 = dev_ids;
+    o.n = n;
+    return push(g, o);
 }
 
 int sg_g2p_apic(sg_grid *g, float *dev_x, float *dev_v, float *dev_C, int64_t n, float dt, int32_t f_mom0)

@@ -276,6 +276,12 @@ void launch_grid_update(const DevGrid &g, cudaStream_t s, int f_mass, int f_mom0
 // particle order, leaf list and key ranges) to stage each leaf's
 // neighbourhood of node velocities in shared memory; otherwise input order.
 // C: NULL for PIC, else APIC, the matrices written there (n x 9 FP32).
+// The particle arrays (x, v: n x 3 FP32; C: n x 9 FP32; ids: n int64; any of
+// the last two may be null) permuted into the order g.perm of the last
+// binning, in place through tmp (n x 9 x 4 bytes), and g.perm reset to the
+// identity.  Returns the number of kernels launched.
+int launch_sort_particles(DevGrid &g, cudaStream_t s, float *x, float *v, float *C, int64_t *ids, long long n,
+                          void *tmp, const LaunchCfg &lc);
 void launch_g2p(const DevGrid &g, cudaStream_t s, float *x, float *v, float *C, long long n, float dt, int f_mom0,
                 int binned, const LaunchCfg &lc);
 

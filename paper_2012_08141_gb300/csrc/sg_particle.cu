@@ -531,6 +531,49 @@ __global__ void __launch_bounds__(256) k_p2g_gather(DevGrid g, const float *__re
     if (changed) mark_dirty(g);
 }
 
+// ---------------------------------------------------------------------------
+// Particle reordering: the arrays into the order of the last binning, out[q]
+// = in[perm[q]] for nc values per particle (a thread per value, so the writes
+// are coalesced), then the order itself becomes the identity.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_sort_gather(const int32_t *__restrict__ perm, long long n, int nc, const T *__restrict__ in,
+                              T *__restrict__ out)
+{
+    const long long total = n * nc;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long q = e / nc;
+        const int c = (int)(e - q * nc);
+        out[e] = in[(long long)perm[q] * nc + c];
+    }
+}
+
+__global__ void k_iota(int32_t *__restrict__ perm, long long n)
+{
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
+        perm[q] = (int32_t)q;
+}
+
+int launch_sort_particles(DevGrid &g, cudaStream_t s, float *x, float *v, float *C, int64_t *ids, long long n,
+                          void *tmp, const LaunchCfg &lc)
+{
+    const unsigned blocks = (unsigned)(lc.num_sms * 8);
+    int launches = 0;
+    struct Arr { void *p; int nc; bool i64; } arrs[4] = {{x, 3, false}, {v, 3, false}, {C, 9, false}, {ids, 1, true}};
+    for (const Arr &a : arrs) {
+        if (!a.p) continue;
+        if (a.i64)
+            k_sort_gather<long long><<<blocks, 256, 0, s>>>(g.perm, n, a.nc, (const long long *)a.p, (long long *)tmp);
+        else
+            k_sort_gather<float><<<blocks, 256, 0, s>>>(g.perm, n, a.nc, (const float *)a.p, (float *)tmp);
+        ++launches;
+        cudaMemcpyAsync(a.p, tmp, (size_t)n * a.nc * (a.i64 ? 8 : 4), cudaMemcpyDeviceToDevice, s);
+    }
+    k_iota<<<blocks, 256, 0, s>>>(g.perm, n);
+    return launches + 1;
+}
+
 int launch_p2g_binned(DevGrid &g, cudaStream_t s, const float *x, const float *v, const float *C, long long n,
                       float pmass, int f_mass, int f_mom0, bool rebin, const LaunchCfg &lc)
 {

@@ -249,6 +249,27 @@ def test_scratch_read_later_keeps_store():
     assert g.stats()["stores_removed"] == before
 
 
+def test_sort_particles_needs_the_current_binning():
+    """sg_sort_particles reorders the arrays of the last binned P2G on the
+    grid: without one (or for other arrays) the flush fails; with it, one
+    gather per array (x, v, the ids) and the order's reset."""
+    lib = sg.load_library()
+    g = dry(64, 2, 4)
+    x, v, ids, n = ctypes.c_void_p(0x10000), ctypes.c_void_p(0x20000), ctypes.c_void_p(0x40000), 1000
+    assert lib.sg_sort_particles(g.h, x, v, None, None, -1) == sg.SG_ERR_INVALID
+    assert lib.sg_sort_particles(g.h, x, v, None, None, n) == 0          # queued
+    assert lib.sg_flush(g.h) == sg.SG_ERR_INVALID                        # nothing binned yet
+    assert b"binned" in lib.sg_last_error()
+    assert lib.sg_p2g(g.h, x, v, n, 1.0, 0, 1) == 0
+    assert lib.sg_flush(g.h) == 0
+    l0 = g.stats()["launches"]
+    assert lib.sg_sort_particles(g.h, x, v, None, ids, n) == 0
+    assert lib.sg_flush(g.h) == 0
+    assert g.stats()["launches"] - l0 == 4
+    assert lib.sg_sort_particles(g.h, ctypes.c_void_p(0x50000), v, None, None, n) == 0
+    assert lib.sg_flush(g.h) == sg.SG_ERR_INVALID                        # other arrays
+
+
 def test_g2p2g_argument_checks_and_launches():
     """sg_g2p2g: distinct grids of the same geometry, momentum/velocity fields
     consecutive, a binned P2G over the same particles on src or dst; it flushes

@@ -359,3 +359,62 @@ def test_particle_50_steps_full_size():
     assert rel_linf(v.cpu().numpy(), ov) <= TOL
     assert np.max(np.abs(x.cpu().numpy().astype(np.float64) - ox)) <= 1e-5
     g.close()
+
+
+def _bin_keys(x, N, L):
+    """The binning key order of FP32 positions: leaf of the clamped base node
+    (row-major over the root), the ordering sg_sort_particles leaves bins in."""
+    X = (x.astype(np.float32) * np.float32(N)).astype(np.float32)
+    base = np.floor(X - np.float32(0.5)).astype(np.int64)
+    n0 = np.maximum(base, 0)
+    R = N // L
+    return ((n0[:, 0] // L) * R + n0[:, 1] // L) * R + n0[:, 2] // L
+
+
+def test_sort_particles_reorders_and_keeps_the_physics():
+    """Steps with the particle arrays reordered into bin order every other
+    step (sg_sort_particles, the ids carried along) against the oracle's
+    steps on the particles in their own order: after each sort the arrays
+    hold the same particles (bit-exact, by id) grouped by bin, and after five
+    steps every particle's state matches the oracle's by id."""
+    import torch
+    import paper_2012_08141_gb300 as sg
+    spec = spheres_particles(seed=5, n=200000, N=128, L=4, r_min=0.1, r_max=0.25)
+    g = sg.Grid(spec.N, 2, 4, max_leaves=(spec.N // 4) ** 3)
+    og = oracle.Grid(spec.N, spec.L, 4)
+    x = torch.from_numpy(spec.x).cuda()
+    v = torch.from_numpy(spec.v).cuda()
+    ids = torch.arange(spec.n, dtype=torch.int64, device="cuda")
+    ox, ov = spec.x.copy(), spec.v.copy()
+    for s in range(5):
+        g.sync()                                  # the queued steps have run
+        xb = x.cpu().numpy().copy()               # the positions this step bins
+        g.deactivate_all()
+        g.p2g(x, v, spec.pmass, 0, 1)
+        g.grid_update(0, 1, spec.dt, spec.gravity, spec.bound)
+        g.g2p(x, v, spec.dt, 1)
+        og.deactivate_all()
+        og.p2g(ox, ov, spec.pmass, 0, 1)
+        og.grid_update(0, 1, spec.dt, spec.gravity, spec.bound)
+        og.g2p(ox, ov, spec.dt, 1)
+        if s % 2 == 0:
+            g.sync()
+            x_before, v_before, id_before = x.clone(), v.clone(), ids.clone()
+            g.sort_particles(x, v, ids=ids)
+            g.sync()
+            perm_ids = ids.cpu().numpy()
+            assert np.array_equal(np.sort(perm_ids), np.arange(spec.n))
+            # the same particles: position q now holds what sat where its id was
+            where = np.empty(spec.n, np.int64)
+            where[id_before.cpu().numpy()] = np.arange(spec.n)
+            src = where[perm_ids]
+            np.testing.assert_array_equal(x.cpu().numpy(), x_before.cpu().numpy()[src])
+            np.testing.assert_array_equal(v.cpu().numpy(), v_before.cpu().numpy()[src])
+            keys = _bin_keys(xb[src], spec.N, spec.L)   # grouped by the step's bins
+            inside = np.all((xb[src] * spec.N >= 0.5) & (xb[src] * spec.N < spec.N - 1.5), axis=1)
+            assert np.all(np.diff(keys[inside]) >= 0)
+    g.sync()
+    order = ids.cpu().numpy()
+    assert rel_linf(v.cpu().numpy(), ov[order]) <= TOL
+    assert np.max(np.abs(x.cpu().numpy().astype(np.float64) - ox[order])) <= 2e-6
+    g.close()
