@@ -156,3 +156,38 @@ def test_g2p2g_pool_exhaustion_reports():
     assert e.value.code == sg.SG_ERR_POOL_EXHAUSTED
     A.close()
     B.close()
+
+
+def test_g2p2g_steps_after_a_sort():
+    """The fused steps of the test above with the particle arrays reordered
+    into the bin order right after the binned P2G (sg_sort_particles on the
+    grid holding the bins, the ids carried along): the bins stay valid, and
+    after five steps every particle's state matches the oracle's by id."""
+    import torch
+    spec = spheres_particles(seed=39, n=20000, N=64, L=4, r_min=0.1, r_max=0.2)
+    C0 = _affine(spec.n, 40)
+    A, B, oA, x, v, ox, ov = _setup(spec, C0, 4096)
+    ids = torch.arange(spec.n, dtype=torch.int64, device="cuda")
+    C = torch.from_numpy(C0).cuda()
+    A.sort_particles(x, v, C, ids)
+    oB = oracle.Grid(spec.N, spec.L, 4)
+    oC = np.zeros((spec.n, 9), np.float32)
+    for _ in range(5):
+        B.deactivate_all()
+        A.g2p2g(B, x, v, spec.dt, 1, spec.pmass, 0, 1)
+        B.grid_update(0, 1, spec.dt, spec.gravity, spec.bound)
+        A, B = B, A
+        oA.g2p_apic(ox, ov, oC, spec.dt, 1)
+        oB.deactivate_all()
+        oB.p2g_apic(ox, ov, oC, spec.pmass, 0, 1)
+        oB.grid_update(0, 1, spec.dt, spec.gravity, spec.bound)
+        oA, oB = oB, oA
+    A.sync()
+    order = ids.cpu().numpy()
+    assert not np.array_equal(order, np.arange(spec.n))      # the arrays were reordered
+    np.testing.assert_array_equal(C.cpu().numpy(), C0[order])
+    gx, gv = x.cpu().numpy(), v.cpu().numpy()
+    assert rel_linf(gv, ov[order]) <= TOL
+    assert np.max(np.abs(gx.astype(np.float64) - ox[order])) <= 2e-6
+    A.close()
+    B.close()
