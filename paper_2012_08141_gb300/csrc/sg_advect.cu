@@ -213,24 +213,24 @@ __global__ void __launch_bounds__(256, 4) k_advect(DevGrid g, AdvectArgs A)
 #pragma unroll
             for (int c = 0; c < C; ++c) {
                 const float *sf = g.field[A.src[c]];
-                if (!BND) {
+                if constexpr (!BND) {
                     g.field[A.dst[c]][idx] = sample<L, Off>(sf, fw);
-                    continue;
+                } else {
+                    float v[8];
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) v[k] = __ldg(sf + fw.off[k]);
+                    float smp = 0.f, lo = v[0], hi = v[0];
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) smp = fmaf(fw.w[k], v[k], smp);  // the order of sample()
+#pragma unroll
+                    for (int k = 1; k < 8; ++k) {
+                        lo = fminf(lo, v[k]);
+                        hi = fmaxf(hi, v[k]);
+                    }
+                    g.field[A.dst[c]][idx] = smp;
+                    A.lo[c][idx] = lo;
+                    A.hi[c][idx] = hi;
                 }
-                float v[8];
-#pragma unroll
-                for (int k = 0; k < 8; ++k) v[k] = __ldg(sf + fw.off[k]);
-                float smp = 0.f, lo = v[0], hi = v[0];
-#pragma unroll
-                for (int k = 0; k < 8; ++k) smp = fmaf(fw.w[k], v[k], smp);  // the order of sample()
-#pragma unroll
-                for (int k = 1; k < 8; ++k) {
-                    lo = fminf(lo, v[k]);
-                    hi = fmaxf(hi, v[k]);
-                }
-                g.field[A.dst[c]][idx] = smp;
-                A.lo[c][idx] = lo;
-                A.hi[c][idx] = hi;
             }
             continue;
         }
