@@ -395,7 +395,7 @@ __global__ void __launch_bounds__(kListThreads) k_listgen(DevGrid g, int force, 
 {
     __shared__ int s_tile, s_skip, s_prefix;
     __shared__ int s_wsum[kListThreads / 32];
-    __shared__ int s_cells[kListTile];
+    __shared__ uint32_t s_cells[kListTile];  // listed cells' (i, j, k), 10 bits each (R <= 1024)
     const int tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
     const unsigned long long tick0 = call_idx * (unsigned long long)num_tiles;
     const unsigned long long tag = (call_idx + 1ull) << 34;
@@ -470,6 +470,7 @@ __global__ void __launch_bounds__(kListThreads) k_listgen(DevGrid g, int force, 
         }
         __syncthreads();
         const int prefix = s_prefix;
+        const int R = g.R;
         int pos = excl;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -478,19 +479,20 @@ __global__ void __launch_bounds__(kListThreads) k_listgen(DevGrid g, int force, 
                 g.list_slot[prefix + pos] = sl[q];
                 g.list_b[prefix + pos] = b;
                 g.ent_of_slot[sl[q]] = prefix + pos;
-                s_cells[pos] = b;
+                const unsigned ci = (unsigned)b / ((unsigned)R * R), rem = (unsigned)b - ci * ((unsigned)R * R),
+                               cj = rem / (unsigned)R, ck = rem - cj * (unsigned)R;
+                s_cells[pos] = (ci << 20) | (cj << 10) | ck;
                 ++pos;
             }
         }
         if (tile == num_tiles - 1 && tid == 0) g.ctrl->list_n = prefix + total;
         __syncthreads();
-        const int R = g.R;
         for (int idx = tid; idx < total * 27; idx += kListThreads) {
             const int e = idx / 27, q = idx - e * 27;
-            const int b = s_cells[e];
-            const int bi = b / (R * R) + q / 9 - 1;
-            const int bj = (b / R) % R + (q / 3) % 3 - 1;
-            const int bk = b % R + q % 3 - 1;
+            const uint32_t c = s_cells[e];
+            const int bi = (int)(c >> 20) + q / 9 - 1;
+            const int bj = (int)((c >> 10) & 1023u) + (q / 3) % 3 - 1;
+            const int bk = (int)(c & 1023u) + q % 3 - 1;
             int v = -1;
             if ((unsigned)bi < (unsigned)R && (unsigned)bj < (unsigned)R && (unsigned)bk < (unsigned)R)
                 v = g.root[((long long)bi * R + bj) * R + bk];
