@@ -177,6 +177,13 @@ def test_activation_zero_fill_is_a_store():
     assert removed(sg.SG_OPT_ALL, lambda g: g.ew(2, 2, alpha=2.0)) == 1   # 2 read first: kept
     assert removed(sg.SG_OPT_ALL, lambda g: g.ew(2, 0, alpha=2.0)) == 2   # 2 overwritten
     assert removed(sg.SG_OPT_ALL & ~sg.SG_OPT_DSE, fused) == 0
+    # an advection reads its source and the velocity, and writes its output in full
+    g = dry(F=8, scratch=0b01000000)
+    s0 = g.stats()["stores_removed"]
+    g.activate_shell(100, 400, False)
+    g.advect(5, 3, 0, 1e-3)
+    g.flush()
+    assert g.stats()["stores_removed"] - s0 == 2      # 5 overwritten, 6 scratch and untouched
 
 
 @pytest.mark.parametrize("opts,expect", [
