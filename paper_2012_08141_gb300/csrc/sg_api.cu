@@ -876,7 +876,9 @@ int ensure_p2g_scratch(sg_grid *g, long long n)
         const long long cap = std::max(n, g->perm_cap * 2);
         g->dev.perm = (int32_t *)dev_alloc(g, sizeof(int32_t) * cap);
         g->dev.perm_alt = (int32_t *)dev_alloc(g, sizeof(int32_t) * cap);
-        if (!g->dev.perm || !g->dev.perm_alt) return fail(SG_ERR_OOM, "p2g order of %lld particles", cap);
+        g->dev.perm_key = (long long *)dev_alloc(g, sizeof(long long) * cap);
+        if (!g->dev.perm || !g->dev.perm_alt || !g->dev.perm_key)
+            return fail(SG_ERR_OOM, "p2g order of %lld particles", cap);
         g->perm_cap = cap;
         g->p2g_x = nullptr;  // no valid last order in the new arrays
         g->p2g_n = 0;

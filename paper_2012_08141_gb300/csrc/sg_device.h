@@ -77,6 +77,7 @@ struct DevGrid {
     int32_t *tile_sum;
     int32_t *perm;
     int32_t *perm_alt;  // the next binning's order, built from the last one (then swapped)
+    long long *perm_key;  // each particle's key, stored by the count pass for the order pass
     int32_t *bin_list;  // the leaves holding particles, in no particular order
     // grouped sweeps of the fused step: list entry of each slot (written by
     // the list generation), the records of runs of adjacent leaves (along i

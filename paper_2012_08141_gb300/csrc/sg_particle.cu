@@ -196,10 +196,16 @@ __device__ __forceinline__ long long p2g_key_of(const float *__restrict__ x, lon
     return empty ? 8LL * R * R * R : leaf * 8 + cls;
 }
 
+// The count passes store each particle's key (at its position in the order
+// they visit: the particle index here, the last order's slot in the rebin)
+// for the order passes, which then read keys in order instead of positions.
 __global__ void k_p2g_bin(DevGrid g, const float *__restrict__ x, long long n)
 {
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x)
-        atomicAdd(&g.bin_count[p2g_key_of(x, p, g.N, g.lg2, g.R)], 1);
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
+        const long long key = p2g_key_of(x, p, g.N, g.lg2, g.R);
+        g.perm_key[p] = key;
+        atomicAdd(&g.bin_count[key], 1);
+    }
 }
 
 // Rebinning: the particles are visited in the last binning's order, so the
@@ -210,6 +216,7 @@ __global__ void k_p2g_rebin(DevGrid g, const float *__restrict__ x, long long n)
     const int lane = lane_id();
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
         const long long key = p2g_key_of(x, g.perm[q], g.N, g.lg2, g.R);
+        g.perm_key[q] = key;
         const unsigned peers = __match_any_sync(__activemask(), key);
         if (lane == __ffs(peers) - 1) atomicAdd(&g.bin_count[key], __popc(peers));
     }
@@ -318,22 +325,22 @@ __global__ void __launch_bounds__(256) k_bin_scan_apply(DevGrid g, long long nbi
     }
 }
 
-__global__ void k_p2g_perm(DevGrid g, const float *__restrict__ x, long long n)
+__global__ void k_p2g_perm(DevGrid g, long long n)
 {
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
-        const int pos = atomicAdd(&g.bin_count[p2g_key_of(x, p, g.N, g.lg2, g.R)], 1);
+        const int pos = atomicAdd(&g.bin_count[g.perm_key[p]], 1);
         g.perm[pos] = (int)p;
     }
 }
 
 // The new order from the last one, written to perm_alt (warp-aggregated
 // cursor atomics, as in k_p2g_rebin).
-__global__ void k_p2g_reperm(DevGrid g, const float *__restrict__ x, long long n)
+__global__ void k_p2g_reperm(DevGrid g, long long n)
 {
     const int lane = lane_id();
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
         const int p = g.perm[q];
-        const long long key = p2g_key_of(x, p, g.N, g.lg2, g.R);
+        const long long key = g.perm_key[q];
         const unsigned peers = __match_any_sync(__activemask(), key);
         const int leader = __ffs(peers) - 1;
         int base = 0;
@@ -592,12 +599,12 @@ int launch_p2g_binned(DevGrid &g, cudaStream_t s, const float *x, const float *v
     k_bin_scan_apply<<<ntiles, 256, 0, s>>>(g, nscan);
     launches += 5;
     if (rebin) {
-        k_p2g_reperm<<<(unsigned)pblocks, 256, 0, s>>>(g, x, n);
+        k_p2g_reperm<<<(unsigned)pblocks, 256, 0, s>>>(g, n);
         int32_t *t = g.perm;  // the new order is now the current one
         g.perm = g.perm_alt;
         g.perm_alt = t;
     } else {
-        k_p2g_perm<<<(unsigned)pblocks, 256, 0, s>>>(g, x, n);
+        k_p2g_perm<<<(unsigned)pblocks, 256, 0, s>>>(g, n);
     }
     ++launches;
 #define SG_GATHER(LL, AP) k_p2g_gather<LL, AP><<<resident_ctas(k_p2g_gather<LL, AP>, lc.num_sms), 256, 0, s>>>( \
