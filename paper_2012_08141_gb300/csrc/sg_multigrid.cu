@@ -109,6 +109,46 @@ __global__ void __launch_bounds__(256) k_prolong(DevGrid coarse, DevGrid fine, i
     }
 }
 
+// Prolongation over 8^3 leaves, a warp per fine leaf: the leaf's slot, cell
+// and coarse leaf are looked up once; lane t takes voxels 16t .. 16t + 15 (two
+// k-rows, i = t / 4, j = 2t mod 8 and + 1), whose coarse voxels are the four
+// consecutive values of one coarse row, read as one float4; the rows of x
+// move as float4s.  Each active voxel takes the same fma as in k_prolong.
+__global__ void __launch_bounds__(256) k_prolong8(DevGrid coarse, DevGrid fine, int f_src, int f_dst, float w)
+{
+    const long long n = fine.ctrl->list_n;
+    const int Rf = fine.R, Rc = coarse.R;
+    const float *__restrict__ y = coarse.field[f_src];
+    float *__restrict__ x = fine.field[f_dst];
+    const int lane = lane_id();
+    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long e = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); e < n; e += warps) {
+        const int sf = fine.list_slot[e];
+        const int b = fine.list_b[e];
+        const int bi = b / (Rf * Rf), bj = (b / Rf) % Rf, bk = b % Rf;
+        const int sc = coarse.root[((long long)(bi >> 1) * Rc + (bj >> 1)) * Rc + (bk >> 1)];
+        if (sc < 0) continue;  // the coarse voxels read 0 (warp-uniform)
+        const uint32_t bits = (fine.mask[(long long)sf * 16 + (lane >> 1)] >> ((lane & 1) * 16)) & 0xffffu;
+        if (!bits) continue;
+        const int li = lane >> 2, lj = (2 * lane) & 7;
+        const int ci = ((bi & 1) * 8 + li) >> 1, cj = ((bj & 1) * 8 + lj) >> 1, ck0 = (bk & 1) * 4;
+        const float4 yv = *reinterpret_cast<const float4 *>(y + ((long long)sc << 9) + (ci * 8 + cj) * 8 + ck0);
+        const float yk[4] = {yv.x, yv.y, yv.z, yv.w};
+        float4 *xp = reinterpret_cast<float4 *>(x + ((long long)sf << 9) + lane * 16);
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            float4 v = xp[h];
+            float *c = reinterpret_cast<float *>(&v);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int t = 4 * h + u;       // voxel 16 lane + t: k = t mod 8
+                if ((bits >> t) & 1u) c[u] = fmaf(w, yk[(t & 7) >> 1], c[u]);
+            }
+            xp[h] = v;
+        }
+    }
+}
+
 void launch_restrict_mark(const DevGrid &fine, const DevGrid &coarse, cudaStream_t s, const LaunchCfg &lc)
 {
     k_restrict_mark<<<lc.num_sms * 4, 256, 0, s>>>(fine, coarse);
@@ -131,7 +171,7 @@ void launch_prolong(const DevGrid &coarse, const DevGrid &fine, cudaStream_t s, 
                     const LaunchCfg &lc)
 {
     const int ctas = lc.num_sms * 8;
-    if (fine.L == 8) k_prolong<8><<<ctas, 256, 0, s>>>(coarse, fine, f_src, f_dst, w);
+    if (fine.L == 8) k_prolong8<<<ctas, 256, 0, s>>>(coarse, fine, f_src, f_dst, w);
     else k_prolong<4><<<ctas, 256, 0, s>>>(coarse, fine, f_src, f_dst, w);
 }
 
