@@ -149,6 +149,61 @@ __global__ void __launch_bounds__(256) k_prolong8(DevGrid coarse, DevGrid fine, 
     }
 }
 
+// Restriction from 8^3 leaves, a warp per fine leaf: the fine leaf maps onto a
+// 4^3 coarse sub-block, and lane t sums the coarse voxels (ci, cj, 2h) and
+// (ci, cj, 2h + 1), ci = t / 8, cj = (t / 2) mod 4, h = t mod 2.  Their
+// children are the k-half h of fine rows (2ci + a, 2cj + c), one float4 each;
+// both rows of one a share a mask word.  The children are added in the same
+// order as in k_restrict, and the two coarse voxels move as one float2.
+template <bool ACTIVATE>
+__global__ void __launch_bounds__(256) k_restrict8(DevGrid fine, DevGrid coarse, int f_src, int f_dst, float w)
+{
+    const long long n = fine.ctrl->list_n;
+    const int Rf = fine.R, Rc = coarse.R;
+    const float *__restrict__ x = fine.field[f_src];
+    float *y = coarse.field[f_dst];
+    const int lane = lane_id();
+    const int ci = lane >> 3, cj = (lane >> 1) & 3, h = lane & 1;
+    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    bool changed = false;
+    for (long long e = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); e < n; e += warps) {
+        const int sf = fine.list_slot[e], b = fine.list_b[e];
+        const int bi = b / (Rf * Rf), bj = (b / Rf) % Rf, bk = b % Rf;
+        const int sc = coarse.root[((long long)(bi >> 1) * Rc + (bj >> 1)) * Rc + (bk >> 1)];
+        if (sc < 0) continue;  // no active voxel in this leaf, or the coarse pool is exhausted (latched)
+        const uint32_t *mf = fine.mask + (long long)sf * 16;
+        const float *xl = x + ((long long)sf << 9);
+        float s0 = 0.f, s1 = 0.f;
+        uint32_t act = 0;  // bit kk: coarse voxel (ci, cj, 2h + kk) has an active child
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+            const int r0 = (2 * ci + a) * 8 + 2 * cj;  // fine rows r0 and r0 + 1 (c = 0, 1)
+            const uint32_t mw = __ldg(mf + (r0 >> 2));
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const float4 p = __ldg(reinterpret_cast<const float4 *>(xl + (r0 + c) * 8 + 4 * h));
+                s0 += p.x + p.y;  // a stored value at an inactive voxel is 0
+                s1 += p.z + p.w;
+                const uint32_t nib = (mw >> (((r0 + c) & 3) * 8 + 4 * h)) & 0xfu;
+                act |= ((nib & 3u) != 0u) | (((nib >> 2) != 0u) << 1);
+            }
+        }
+        if (!act) continue;
+        const int lc = (((bi & 1) * 4 + ci) * 8 + ((bj & 1) * 4 + cj)) * 8 + (bk & 1) * 4 + 2 * h;
+        if (ACTIVATE) {
+            uint32_t *mw = coarse.mask + (long long)sc * 16 + (lc >> 5);
+            const uint32_t bits = act << (lc & 31);
+            if ((*(volatile uint32_t *)mw & bits) != bits) changed |= (atomicOr(mw, bits) & bits) != bits;
+        }
+        float2 *yp = reinterpret_cast<float2 *>(y + ((long long)sc << 9) + lc);
+        float2 v = *yp;
+        if (act & 1u) v.x = fmaf(w, s0, v.x);
+        if (act & 2u) v.y = fmaf(w, s1, v.y);
+        *yp = v;
+    }
+    if (ACTIVATE && changed) mark_dirty(coarse);
+}
+
 void launch_restrict_mark(const DevGrid &fine, const DevGrid &coarse, cudaStream_t s, const LaunchCfg &lc)
 {
     k_restrict_mark<<<lc.num_sms * 4, 256, 0, s>>>(fine, coarse);
@@ -159,8 +214,8 @@ void launch_restrict(const DevGrid &fine, const DevGrid &coarse, cudaStream_t s,
 {
     const int ctas = lc.num_sms * 8;
     if (fine.L == 8) {
-        if (activate) k_restrict<8, true><<<ctas, 256, 0, s>>>(fine, coarse, f_src, f_dst, w);
-        else k_restrict<8, false><<<ctas, 256, 0, s>>>(fine, coarse, f_src, f_dst, w);
+        if (activate) k_restrict8<true><<<ctas, 256, 0, s>>>(fine, coarse, f_src, f_dst, w);
+        else k_restrict8<false><<<ctas, 256, 0, s>>>(fine, coarse, f_src, f_dst, w);
     } else {
         if (activate) k_restrict<4, true><<<ctas, 256, 0, s>>>(fine, coarse, f_src, f_dst, w);
         else k_restrict<4, false><<<ctas, 256, 0, s>>>(fine, coarse, f_src, f_dst, w);
