@@ -132,3 +132,68 @@ def test_restriction_at_scale_sampled():
     np.testing.assert_array_equal(cb, want.astype(cb.dtype))
     fine.close()
     coarse.close()
+
+
+def _vcycle(levels, fmap, clear, restrict, diffuse, prolong, swap):
+    """The 4-level V-cycle the multigrid benchmark times: down (clear b on the
+    coarse level, restrict x into it, smooth it into x), up (prolong, smooth
+    into a third field, swap).  fmap[l] maps the logical fields (x, b, t) of
+    level l to storage; swap exchanges x and t."""
+    for l in range(3):
+        clear(l + 1, fmap[l + 1][1])
+        restrict(l, fmap[l][0], fmap[l + 1][1], 0.125)
+        diffuse(l + 1, fmap[l + 1][1], fmap[l + 1][0], 0.1)
+    for l in (2, 1, 0):
+        prolong(l, fmap[l + 1][0], fmap[l][0], 0.5)
+        diffuse(l, fmap[l][0], fmap[l][2], 0.1)
+        swap(l)
+
+
+def test_vcycle_full_size_against_oracle():
+    """Three V-cycles over the 512^3 band (26,104 leaves) and its 256^3, 128^3
+    and 64^3 restrictions, with every pass on, in the launch configuration the
+    benchmark times: the first cycle activates the coarse levels, the next two
+    are demoted (Sec. 6.3), and from the third the finest level's smoother runs
+    over the reused list's j-run records.  Every level's structure bit-exact and
+    every field within 2e-5 against the oracle's three cycles."""
+    import paper_2012_08141_gb300 as sg
+    from workload import band512
+    spec = band512()
+    G = [sg.Grid(512 >> l, 3, 3, max_leaves=32768, max_sums=1) for l in range(4)]
+    O = [oracle.Grid(512 >> l, 8, 3) for l in range(4)]
+    for g in G:
+        g.set_opts(sg.SG_OPT_ALL)
+    G[0].activate_shell(spec.lo2, spec.hi2, spec.lo_strict)
+    O[0].activate_shell(spec.lo2, spec.hi2, spec.lo_strict)
+    ob, _ = O[0].structure()
+    vals = leaf_values(3, 512, 8, ob)
+    G[0].write_field(0, vals)
+    O[0].write_field(0, vals)
+    gmap, omap = [[0, 1, 2] for _ in G], [[0, 1, 2] for _ in O]
+
+    def gswap(l):
+        G[l].swap(0, 2)            # the grid's own field names follow the swap
+
+    def oswap(l):
+        omap[l][0], omap[l][2] = omap[l][2], omap[l][0]
+
+    demoted0 = sum(g.stats()["act_demoted"] for g in G)
+    for _ in range(3):
+        _vcycle(G, gmap, lambda l, f: G[l].clear(f), lambda l, s, d, w: G[l].restrict_to(G[l + 1], s, d, w),
+                lambda l, s, d, c: G[l].diffuse7(s, d, c), lambda l, s, d, w: G[l].prolong_from(G[l + 1], s, d, w),
+                gswap)
+        for g in G:
+            g.flush()
+        _vcycle(O, omap, lambda l, f: O[l].clear(f), lambda l, s, d, w: O[l].restrict_to(O[l + 1], s, d, w),
+                lambda l, s, d, c: O[l].diffuse7(s, d, c), lambda l, s, d, w: O[l].prolong_from(O[l + 1], s, d, w),
+                oswap)
+    assert sum(g.stats()["act_demoted"] for g in G) - demoted0 == 6   # three restrictions in each of cycles 2, 3
+    for l in range(4):
+        gb, gm = G[l].read_structure()
+        ob, om = O[l].structure()
+        np.testing.assert_array_equal(gb, ob)
+        np.testing.assert_array_equal(gm, om)
+        for f in range(3):
+            assert rel_linf(G[l].read_field(f), O[l].read_field(omap[l][f])) <= TOL, (l, f)
+    for g in G:
+        g.close()
