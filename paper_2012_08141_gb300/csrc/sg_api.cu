@@ -873,6 +873,7 @@ int ensure_p2g_scratch(sg_grid *g, long long n)
             return fail(SG_ERR_OOM, "p2g bins");
     }
     if (n > g->perm_cap) {
+        // grown geometrically: replaced arrays stay allocated until the grid is destroyed
         const long long cap = std::max(n, g->perm_cap * 2);
         g->dev.perm = (int32_t *)dev_alloc(g, sizeof(int32_t) * cap);
         g->dev.perm_alt = (int32_t *)dev_alloc(g, sizeof(int32_t) * cap);
@@ -1020,13 +1021,16 @@ int do_flush(sg_grid *g)
                     break;
                 }
                 if (!g->dry && o.n > g->sort_cap) {
-                    g->sort_tmp = dev_alloc(g, (size_t)o.n * 36);
+                    // grown geometrically: replaced blocks stay allocated until
+                    // the grid is destroyed, so their total stays below 2x the last
+                    const long long cap = std::max<long long>(o.n, 2 * g->sort_cap);
+                    g->sort_tmp = dev_alloc(g, (size_t)cap * 36);
                     if (!g->sort_tmp) {
                         rc = fail(SG_ERR_OOM, "particle reordering scratch");
                         ++i;
                         break;
                     }
-                    g->sort_cap = o.n;
+                    g->sort_cap = cap;
                 }
                 const int k = g->dry ? 1 + (o.p0 ? 1 : 0) + (o.p1 ? 1 : 0) + (o.p2 ? 1 : 0) + (o.p3 ? 1 : 0)
                                      : launch_sort_particles(g->dev, g->stream, (float *)o.p0, (float *)o.p1,
