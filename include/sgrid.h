@@ -619,6 +619,12 @@ int sg_server_create(const sg_server_desc *desc, void *cuda_stream, sg_server **
 int sg_server_submit(sg_server *s, const sg_job_desc *job, int64_t *job_id);
 int sg_server_tick(sg_server *s);
 int sg_server_job(sg_server *s, int64_t job_id, sg_job_status *out);
+/* Forget a finished job (SG_JOB_DONE or SG_JOB_FAILED): its record is freed
+ * and sg_server_job no longer knows its id.  A server keeps every job's
+ * record until this call or sg_server_destroy, so a long-running server
+ * releases the jobs whose results it has read.  SG_ERR_INVALID for an
+ * unknown id or a job that is still pending or running. */
+int sg_server_release(sg_server *s, int64_t job_id);
 int sg_server_get_stats(sg_server *s, sg_server_stats *out);
 int sg_server_destroy(sg_server *s);
 

@@ -356,6 +356,19 @@ int sg_server_job(sg_server *s, int64_t job_id, sg_job_status *out)
     return SG_OK;
 }
 
+int sg_server_release(sg_server *s, int64_t job_id)
+{
+    if (!s) return SG_ERR_INVALID;
+    auto it = s->jobs.find(job_id);
+    if (it == s->jobs.end()) return SG_ERR_INVALID;
+    Job *j = it->second;
+    // a retired job is in no queue or resident set any more, only in jobs
+    if (j->state != SG_JOB_DONE && j->state != SG_JOB_FAILED) return SG_ERR_INVALID;
+    s->jobs.erase(it);
+    delete j;
+    return SG_OK;
+}
+
 int sg_server_get_stats(sg_server *s, sg_server_stats *out)
 {
     if (!s || !out) return SG_ERR_INVALID;

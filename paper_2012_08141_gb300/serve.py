@@ -50,6 +50,7 @@ def _lib():
             "sg_server_submit": [P, ctypes.POINTER(JobDesc), ctypes.POINTER(ctypes.c_int64)],
             "sg_server_tick": [P],
             "sg_server_job": [P, ctypes.c_int64, ctypes.POINTER(JobStatus)],
+            "sg_server_release": [P, ctypes.c_int64],
             "sg_server_get_stats": [P, ctypes.POINTER(ServerStats)],
             "sg_server_destroy": [P],
         }
@@ -76,7 +77,7 @@ class Server:
         dev, st = torch.cuda.current_device(), self.stream
         self.alloc_calls = 0
         self.live = {}  # device address -> bytes, for leak checks
-        self._outs = []  # result buffers borrowed by submitted jobs
+        self._outs = {}  # job id -> result buffer borrowed by that job
 
         def _alloc(nbytes, ctx):
             i = self.alloc_calls
@@ -109,13 +110,14 @@ class Server:
         if out is not None:
             assert out.dtype == np.float32 and out.flags.c_contiguous
             ptr, cap = out.ctypes.data, out.size
-            self._outs.append(out)
         j = JobDesc(int(spec.N), int(bool(spec.lo_strict)), int(spec.lo2), int(spec.hi2), int(steps), 0,
                     int(spec.seed) % (1 << 24), ptr, cap)
         jid = ctypes.c_int64()
         rc = self.lib.sg_server_submit(self.h, ctypes.byref(j), ctypes.byref(jid))
         if rc:
             raise SgError(rc, "sg_server_submit failed")
+        if out is not None:
+            self._outs[jid.value] = out
         return jid.value
 
     def tick(self):
@@ -129,6 +131,14 @@ class Server:
         if rc:
             raise SgError(rc, "unknown job")
         return {name: getattr(st, name) for name, _ in JobStatus._fields_}
+
+    def release(self, job_id: int):
+        """Forget a finished (done or failed) job: its record is freed and
+        its result buffer no longer held."""
+        rc = self.lib.sg_server_release(self.h, int(job_id))
+        if rc:
+            raise SgError(rc, "sg_server_release: unknown or unfinished job")
+        self._outs.pop(int(job_id), None)
 
     def stats(self) -> dict:
         st = ServerStats()

@@ -171,3 +171,40 @@ def test_close_with_work_in_flight():
     assert srv.stats()["resident"] == 3
     srv.close()
     assert not srv.live
+
+
+def test_release_forgets_finished_jobs_only():
+    """sg_server_release frees a done job's record (its id becomes unknown and
+    its result buffer is no longer held); a pending or running job, an
+    unknown id and a second release are refused; the other jobs and the
+    server's counters are unaffected."""
+    from paper_2012_08141_gb300 import SgError
+    from paper_2012_08141_gb300.serve import SG_JOB_DONE, Server
+    specs = batched_mix(6, n_grids=2, lo=1e4, hi=2e4)
+    srv = Server(max_jobs=1, hbm_reserve=0)           # one slot: the second job waits
+    out = np.zeros(10 ** 6, dtype=np.float32)
+    a = srv.submit(specs[0], 2, out)
+    b = srv.submit(specs[1], 2)
+    with pytest.raises(SgError):
+        srv.release(b)                                # pending
+    srv.tick()
+    with pytest.raises(SgError):
+        srv.release(a)                                # running
+    for _ in range(8):
+        srv.tick()
+    ja, jb = srv.job(a), srv.job(b)
+    assert ja["state"] == SG_JOB_DONE and jb["state"] == SG_JOB_DONE
+    assert ja["sum"] == pytest.approx(alone_sum(specs[0], 2), rel=TOL)
+    srv.release(a)
+    assert a not in srv._outs
+    with pytest.raises(SgError):
+        srv.job(a)
+    with pytest.raises(SgError):
+        srv.release(a)
+    with pytest.raises(SgError):
+        srv.release(10 ** 9)
+    assert srv.job(b)["sum"] == jb["sum"]
+    st = srv.stats()
+    assert st["completed"] == 2 and st["failed"] == 0
+    srv.release(b)
+    srv.close()
