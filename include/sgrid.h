@@ -516,8 +516,9 @@ int sg_fill_hash(sg_grid *g, int32_t f, int64_t seed);
  * region masks and j-run records current, and synchronizes; the structure of the grids must
  * not change while the batch exists, and between batch steps the grids
  * must not be used except for reads (which synchronize).  All work runs on
- * cuda_stream.  Descriptor memory comes from grid 0's allocator and is
- * released with grid 0. */
+ * cuda_stream.  Descriptor memory comes from grid 0's allocator and goes
+ * back to it at sg_batch_destroy, so the grids must outlive the batch:
+ * destroy the batch first. */
 typedef struct sg_batch sg_batch;
 int sg_batch_create(sg_grid *const *grids, int32_t n, int32_t src, int32_t tmp, int32_t dst, float coef,
                     void *cuda_stream, sg_batch **out);

@@ -150,6 +150,18 @@ void *dev_alloc(sg_grid *g, size_t bytes)
     return p;
 }
 
+// Free one of g's blocks and forget it; the caller has made sure that no
+// queued or running work still uses it.
+void dev_release(sg_grid *g, void *p)
+{
+    if (!p) return;
+    const auto it = std::find(g->blocks.begin(), g->blocks.end(), p);
+    if (it == g->blocks.end()) return;
+    g->blocks.erase(it);
+    if (g->desc.free) g->desc.free(p, g->desc.alloc_ctx);
+    else cudaFree(p);
+}
+
 void dev_free_all(sg_grid *g)
 {
     for (void *p : g->blocks) {
@@ -2099,7 +2111,8 @@ struct sg_batch {
     long long total_leaves = 0;
     BatchGrid *dev_items[2] = {nullptr, nullptr};  // parity 0: src -> dst; parity 1: dst -> src
     double *dev_acc = nullptr;
-    void *blocks[2] = {nullptr, nullptr};
+    void *blocks[2] = {nullptr, nullptr};  // descriptors (and sums), from grid 0's allocator
+    void *maps = nullptr;                  // the staged body's tensor maps, from grid 0's allocator
     int parity = 0;
     int warps = 4;
     int use_graph = 1;
@@ -2364,6 +2377,7 @@ int batch_prepare_staged(sg_batch *b)
                 return fail(SG_ERR_CUDA, "tensor maps of batched grid %d could not be encoded", i);
     unsigned char *dmaps = (unsigned char *)dev_alloc(b->grids[0], size_t(2) * n * kTmaMapsBytes);
     if (!dmaps) return fail(SG_ERR_OOM, "batch tensor maps");
+    b->maps = dmaps;
     for (int i = 0; i < n; ++i) {
         const DevGrid &d = b->grids[i]->dev;
         if (!d.tma_desc || !d.tma_rmask) return fail(SG_ERR_INVALID, "batched grid %d has no TMA task descriptors", i);
@@ -2511,7 +2525,13 @@ int sg_batch_destroy(sg_batch *b)
     if (b->ev_in) cudaEventDestroy(b->ev_in);
     if (b->ev_out) cudaEventDestroy(b->ev_out);
     if (b->own) cudaStreamDestroy(b->own);
-    delete b;  // descriptor blocks are released with grid 0
+    // the batch's work has finished: its blocks go back to grid 0's allocator
+    if (!b->grids.empty()) {
+        dev_release(b->grids[0], b->blocks[0]);
+        dev_release(b->grids[0], b->blocks[1]);
+        dev_release(b->grids[0], b->maps);
+    }
+    delete b;
     return rc;
 }
 

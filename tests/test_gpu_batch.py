@@ -171,3 +171,32 @@ def test_both_stagings_on_the_64_grid_mix():
         assert rel_linf(gb[i].read_field(0), og.read_field(cur)) <= TOL
     for g in ga + gb:
         g.close()
+
+
+def test_batch_destroy_returns_its_device_memory():
+    """A batch's descriptor blocks and the staged body's tensor maps come from
+    grid 0's allocator and go back to it at destroy: after the first cycle
+    (which also builds the grids' own neighbour tables and run records),
+    creating, stepping with both bodies and destroying a batch over the same
+    grids leaves the allocated device memory unchanged."""
+    import torch
+    sg = sgm()
+    specs = batched_mix(12, n_grids=3, lo=1e3, hi=1e5)
+    grids = [make_grid(s, leaves_needed(s)) for s in specs]
+
+    def cycle():
+        bt = sg.Batch(grids, 0, 1, 2, 0.1)
+        bt.set_staging(True)
+        bt.step()
+        bt.set_staging(False)
+        bt.step()
+        assert np.all(np.isfinite(bt.read_sums()))
+        bt.close()
+        torch.cuda.synchronize()
+        return torch.cuda.memory_allocated()
+
+    m1 = cycle()
+    assert cycle() == m1
+    assert cycle() == m1
+    for g in grids:
+        g.close()
