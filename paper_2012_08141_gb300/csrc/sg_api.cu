@@ -188,11 +188,13 @@ bool valid_field(const sg_grid *g, int f) { return f >= 0 && f < g->desc.n_field
 
 // Room in the TMA task-descriptor arrays for `entries` warp tasks (a grid's
 // tasks never exceed its list length, nor its pool capacity).  A larger
-// request replaces the arrays; the old ones are released with the grid.
+// request replaces the arrays, grown geometrically up to the pool capacity;
+// the old ones are released with the grid, so they total less than the last.
 int ensure_tma_desc(sg_grid *g, long long entries)
 {
     entries = std::max(1LL, entries);
     if (g->tma_entries >= entries) return SG_OK;
+    entries = std::max(entries, std::min(2 * g->tma_entries, (long long)g->dev.cap));
     g->dev.tma_desc = (int32_t *)dev_alloc(g, sizeof(int32_t) * 64 * entries);
     g->dev.tma_rmask = (uint32_t *)dev_alloc(g, sizeof(uint32_t) * 120 * entries);
     if (!g->dev.tma_desc || !g->dev.tma_rmask) {
