@@ -177,6 +177,12 @@ def test_activation_zero_fill_is_a_store():
     assert removed(sg.SG_OPT_ALL, lambda g: g.ew(2, 2, alpha=2.0)) == 1   # 2 read first: kept
     assert removed(sg.SG_OPT_ALL, lambda g: g.ew(2, 0, alpha=2.0)) == 2   # 2 overwritten
     assert removed(sg.SG_OPT_ALL & ~sg.SG_OPT_DSE, fused) == 0
+    assert removed(sg.SG_OPT_ALL, lambda g: g.reduce_sum(2, 0)) == 1       # 2 read first (a sum): kept
+    assert removed(sg.SG_OPT_ALL, lambda g: g.clear(2)) == 2               # a clear overwrites 2 in full
+    # any other op before a field's first listed access keeps every fill (conservative)
+    assert removed(sg.SG_OPT_ALL, lambda g: g.fill_hash(2, 5)) == 0
+    # 2 overwritten before the fill is reached; the scratch field 1 meets the fill first: kept
+    assert removed(sg.SG_OPT_ALL, lambda g: (g.ew(2, 0, alpha=1.0), g.fill_hash(0, 5))) == 1
     # an advection reads its source and the velocity, and writes its output in full
     g = dry(F=8, scratch=0b01000000)
     s0 = g.stats()["stores_removed"]
@@ -184,6 +190,19 @@ def test_activation_zero_fill_is_a_store():
     g.advect(5, 3, 0, 1e-3)
     g.flush()
     assert g.stats()["stores_removed"] - s0 == 2      # 5 overwritten, 6 scratch and untouched
+    # the MacCormack correction also reads q^ and q~; its output is written in full
+    g = dry(F=8, scratch=0b01000000)
+    s0 = g.stats()["stores_removed"]
+    g.activate_shell(100, 400, False)
+    g.maccormack(7, 3, 4, 5, 0, 1e-3)
+    g.flush()
+    assert g.stats()["stores_removed"] - s0 == 2      # 7 overwritten, 6 scratch; 0-5 read first
+    g = dry(F=8, scratch=0b01010000)                  # 4 scratch too, but read as q^: kept
+    s0 = g.stats()["stores_removed"]
+    g.activate_shell(100, 400, False)
+    g.maccormack(7, 3, 4, 5, 0, 1e-3)
+    g.flush()
+    assert g.stats()["stores_removed"] - s0 == 2
 
 
 @pytest.mark.parametrize("opts,expect", [
