@@ -315,6 +315,9 @@ uint32_t activation_fill_mask(const sg_grid *g, size_t i)
                 case OP_LISTGEN:
                 case OP_SORT_P:
                     break;
+                case OP_FILL:  // sets every voxel of the listed leaves (0 where inactive)
+                    if (o.i0 == pf) first = 2;
+                    break;
                 case OP_STENCIL:
                     if (o.op != SG_CLEAR && o.src == pf) first = 1;
                     else if (o.dst == pf) first = 2;

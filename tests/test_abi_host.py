@@ -179,10 +179,11 @@ def test_activation_zero_fill_is_a_store():
     assert removed(sg.SG_OPT_ALL & ~sg.SG_OPT_DSE, fused) == 0
     assert removed(sg.SG_OPT_ALL, lambda g: g.reduce_sum(2, 0)) == 1       # 2 read first (a sum): kept
     assert removed(sg.SG_OPT_ALL, lambda g: g.clear(2)) == 2               # a clear overwrites 2 in full
+    # a device fill sets every voxel of its field: 2 overwritten, the scratch field untouched
+    assert removed(sg.SG_OPT_ALL, lambda g: g.fill_hash(2, 5)) == 2
+    assert removed(sg.SG_OPT_ALL, lambda g: (g.ew(2, 0, alpha=1.0), g.fill_hash(0, 5))) == 2   # 0 read first
     # any other op before a field's first listed access keeps every fill (conservative)
-    assert removed(sg.SG_OPT_ALL, lambda g: g.fill_hash(2, 5)) == 0
-    # 2 overwritten before the fill is reached; the scratch field 1 meets the fill first: kept
-    assert removed(sg.SG_OPT_ALL, lambda g: (g.ew(2, 0, alpha=1.0), g.fill_hash(0, 5))) == 1
+    assert removed(sg.SG_OPT_ALL, lambda g: g.deactivate_all()) == 0
     # an advection reads its source and the velocity, and writes its output in full
     g = dry(F=8, scratch=0b01000000)
     s0 = g.stats()["stores_removed"]
