@@ -239,7 +239,9 @@ int sg_set_flush_period(sg_grid *g, int32_t ops);
 int sg_set_max_fuse(sg_grid *g, int32_t max_ops);
 
 /* Queue: sum of field src over the active voxels into result slot out_slot
- * (FP64; per-leaf partials are FP32).  Read with sg_read_sums. */
+ * (FP64; per-leaf partials are FP32).  Read with sg_read_sums.  The reduction
+ * of the paper's stencil-and-reduce microbenchmark (Supp. Sec. 1); with task
+ * fusion (Sec. 6.4) it runs inside the stencil kernel that writes src. */
 int sg_reduce_sum(sg_grid *g, int32_t src, int64_t out_slot);
 /* (With SG_OPT_DSE, a reduction whose result slot a later queued reduction
  * overwrites within the same flush is not run: nothing reads it.) */
@@ -500,6 +502,9 @@ int sg_num_active(sg_grid *g, int64_t *n_active);
 int sg_fill_hash(sg_grid *g, int32_t f, int64_t seed);
 
 /* ---- batched stepping: many grids, one persistent launch per step ----
+ *
+ * (Small sparse problems are dominated by per-task launch overhead, Sec. 8.4;
+ * the batch removes it across grids as task fusion does within one.)
  *
  * A batch binds n (1..1024) live grids with 8^3 leaves.  Each sg_batch_step
  * runs, for every grid, the fused step dst = box27(diffuse7(src, coef)) with
