@@ -643,3 +643,25 @@ def test_stencil_variants_and_their_launch_counts():
             assert [launches(g, lambda: cfg2_step(g, 0)) for _ in range(2)] == [first, 1], (variant, v)
             built = axis[v]
             tma_built = tma_built or v == sg.SG_VARIANT_SWEEP_TMA
+
+def test_serving_and_batch_calls_reject_null_handles():
+    """The serving and batch entry points validate their handles before any
+    device work (no GPU needed): a null server or batch is SG_ERR_INVALID,
+    and destroying a null handle is a no-op."""
+    lib = ctypes.CDLL(sg.load_library()._name)   # own handle: the signatures below stay local
+    P, I64 = ctypes.c_void_p, ctypes.c_int64
+    lib.sg_server_release.argtypes = [P, I64]
+    lib.sg_server_job.argtypes = [P, I64, P]
+    lib.sg_server_tick.argtypes = [P]
+    lib.sg_server_destroy.argtypes = [P]
+    lib.sg_batch_step.argtypes = [P]
+    lib.sg_batch_destroy.argtypes = [P]
+    for fn in (lib.sg_server_release, lib.sg_server_job, lib.sg_server_tick, lib.sg_server_destroy,
+               lib.sg_batch_step, lib.sg_batch_destroy):
+        fn.restype = ctypes.c_int
+    assert lib.sg_server_release(None, 1) == sg.SG_ERR_INVALID
+    assert lib.sg_server_job(None, 1, None) == sg.SG_ERR_INVALID
+    assert lib.sg_server_tick(None) == sg.SG_ERR_INVALID
+    assert lib.sg_server_destroy(None) == sg.SG_OK
+    assert lib.sg_batch_step(None) != sg.SG_OK
+    assert lib.sg_batch_destroy(None) == sg.SG_OK
